@@ -1,0 +1,399 @@
+"""Seeded synthetic muSR inputs shared by the oracle tests, the GPU tests and the benchmark.
+
+This module holds no arithmetic of the fitted method: it neither evaluates the
+positron-histogram model nor any cost.  Histograms come from an event-level
+Monte Carlo of a muSR run (Section 4.1 describes the experiment):
+
+  * each muon decays at t ~ Exponential(tau_mu);
+  * it belongs to one signal component k with probability amp_k / sum(amp);
+  * its spin precesses in its own local field: transverse-field (TF)
+    components draw a frequency omega = 2 pi nu + sigma z (z ~ N(0, 1)), so the
+    ensemble dephases; zero-field (ZF) components draw a 3-D static field
+    b ~ N(0, Delta^2 I) and the spin component along the initial polarisation
+    follows (b_z^2 + (b_x^2 + b_y^2) cos(|b| t)) / |b|^2;
+  * a component with rate lambda loses its polarisation at an
+    Exponential(1/lambda) time;
+  * the positron is counted by detector j with probability
+    (1 + a s) / (1 + a), a = sum(amp), s the spin projection on the detector axis
+    (phase phi_j for TF);
+  * a flat Poisson background Nbkg per bin is added.
+
+The relaxation functions (exponential, Gaussian, Kubo-Toyabe) are therefore
+never written down here: they emerge from the field distributions, which is
+what makes fits of these histograms an independent check of the model.  An
+event at time t lands in bin floor(t / dt + t0 + 1/2), so the expected count
+of bin n is the model at the bin's left-edge time t_n = (n - t0) dt to second
+order in dt.
+
+All generators are seeded (numpy PCG64).  Problem descriptions (term lists and
+parameter maps) are plain data consumed by both the oracle and the GPU binding.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+TAU_MU_US = 2.197019  # muon lifetime in microseconds (the value this build fixes)
+
+# --------------------------------------------------------------------------------------------
+# Problem description (plain data)
+# --------------------------------------------------------------------------------------------
+
+Term = Sequence[Tuple[str, Tuple[int, ...]]]
+
+
+@dataclasses.dataclass
+class Problem:
+    """One fit: histograms, time grid, theory term list and parameter map.
+
+    ``terms``: list of terms, each a list of (kind, slots), kind one of AMP,
+    EXP, GAUSS, KT, TFCOS.  Local slot 0 is N0 and slot 1 is Nbkg.
+    ``map``: int32 [H][nslots]; entry >= 0 is a global parameter index, entry
+    < 0 selects ``consts[-1 - entry]``.
+    """
+
+    counts: np.ndarray  # [H][B]
+    t0: np.ndarray  # [H] in bins
+    bin_width_ns: float
+    fit_range_us: Tuple[float, float]
+    terms: List[Term]
+    map: np.ndarray
+    consts: np.ndarray
+    nparams: int
+    truth: np.ndarray
+    names: List[str]
+    name: str = ""
+
+    @property
+    def H(self) -> int:
+        return int(self.counts.shape[0])
+
+    @property
+    def B(self) -> int:
+        return int(self.counts.shape[1])
+
+    @property
+    def nslots(self) -> int:
+        return int(self.map.shape[1])
+
+    def with_counts(self, counts) -> "Problem":
+        return dataclasses.replace(self, counts=counts)
+
+
+@dataclasses.dataclass
+class Component:
+    """One physical signal component of the simulated run."""
+
+    amp: float
+    kind: str = "TF"  # "TF" or "ZF"
+    nu_mhz: float = 0.0
+    sigma: float = 0.0  # TF field-width (Gaussian dephasing rate), 1/us
+    lam: float = 0.0  # depolarisation rate, 1/us
+    delta: float = 0.0  # ZF static field width, 1/us
+
+
+@dataclasses.dataclass
+class Detector:
+    n0: float  # counts per bin at t = 0 without asymmetry
+    nbkg: float  # background counts per bin
+    phase_deg: float
+    t0: float = 0.0
+
+
+# --------------------------------------------------------------------------------------------
+# Event-level Monte Carlo
+# --------------------------------------------------------------------------------------------
+
+def simulate_histogram(rng: np.random.Generator, det: Detector, comps: Sequence[Component],
+                       nbins: int, bin_width_ns: float, chunk: int = 1 << 22) -> np.ndarray:
+    """Counts of one detector, int64 [nbins]."""
+    dt_us = bin_width_ns / 1000.0
+    a_tot = float(sum(c.amp for c in comps))
+    if a_tot < 0:
+        raise ValueError("component amplitudes must be non-negative")
+    probs = np.array([c.amp for c in comps], dtype=np.float64)
+    probs = probs / probs.sum() if a_tot > 0 else np.full(len(comps), 1.0 / max(len(comps), 1))
+    n_muons = rng.poisson(det.n0 * (TAU_MU_US / dt_us) * (1.0 + a_tot))
+    counts = np.zeros(nbins, dtype=np.int64)
+    phase = math.radians(det.phase_deg)
+    done = 0
+    while done < n_muons:
+        m = min(chunk, n_muons - done)
+        done += m
+        t = rng.exponential(TAU_MU_US, m)
+        which = rng.choice(len(comps), size=m, p=probs) if len(comps) > 1 else np.zeros(m, np.int64)
+        s = np.zeros(m)
+        for k, c in enumerate(comps):
+            sel = np.nonzero(which == k)[0]
+            if sel.size == 0:
+                continue
+            tk = t[sel]
+            if c.kind == "TF":
+                omega = 2.0 * math.pi * c.nu_mhz + c.sigma * rng.standard_normal(sel.size)
+                sk = np.cos(omega * tk + phase)
+            elif c.kind == "ZF":
+                b = c.delta * rng.standard_normal((sel.size, 3))
+                b2 = np.einsum("ij,ij->i", b, b)
+                bt2 = b[:, 0] ** 2 + b[:, 1] ** 2
+                sk = (b[:, 2] ** 2 + bt2 * np.cos(np.sqrt(b2) * tk)) / np.maximum(b2, 1e-300)
+            else:
+                raise ValueError(c.kind)
+            if c.lam > 0:
+                alive = rng.exponential(1.0 / c.lam, sel.size) > tk
+                sk = np.where(alive, sk, 0.0)
+            s[sel] = sk
+        keep = rng.random(m) * (1.0 + a_tot) < 1.0 + a_tot * s
+        n = np.floor(t[keep] / dt_us + det.t0 + 0.5).astype(np.int64)
+        n = n[(n >= 0) & (n < nbins)]
+        counts += np.bincount(n, minlength=nbins)[:nbins]
+    if det.nbkg > 0:
+        counts += rng.poisson(det.nbkg, nbins)
+    return counts
+
+
+def simulate(seed: int, dets: Sequence[Detector], comps_per_det: Sequence[Sequence[Component]],
+             nbins: int, bin_width_ns: float, dtype=np.float32) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    out = np.empty((len(dets), nbins), dtype=dtype)
+    for j, (d, comps) in enumerate(zip(dets, comps_per_det)):
+        out[j] = simulate_histogram(rng, d, comps, nbins, bin_width_ns)
+    return out
+
+
+def jitter(truth: np.ndarray, n: int, seed: int, lo: float = 0.8, hi: float = 1.2) -> np.ndarray:
+    """n parameter vectors truth * U(lo, hi), componentwise (seeded)."""
+    rng = np.random.default_rng(seed)
+    return truth[None, :] * rng.uniform(lo, hi, size=(n, truth.size))
+
+
+def start_point(p: "Problem", seed: int, rel: float = 0.02, nu_rel: float = 0.002,
+                phase_deg: float = 5.0) -> np.ndarray:
+    """A fit start near the truth, as a muSR analyst would give it: every parameter within
+    +-rel (relative), frequencies within +-nu_rel (a frequency read off an FFT of the run)
+    and phases within +-phase_deg degrees."""
+    rng = np.random.default_rng(seed)
+    x = p.truth.astype(np.float64).copy()
+    for i, n in enumerate(p.names):
+        if n.startswith("nu"):
+            x[i] *= 1.0 + rng.uniform(-nu_rel, nu_rel)
+        elif n.startswith("phi"):
+            x[i] += rng.uniform(-phase_deg, phase_deg)
+        else:
+            x[i] *= 1.0 + rng.uniform(-rel, rel)
+    return x
+
+
+# --------------------------------------------------------------------------------------------
+# The configurations (sizes and truths of the paper-shaped workloads)
+# --------------------------------------------------------------------------------------------
+
+def _full_range(nbins: int, bin_width_ns: float) -> Tuple[float, float]:
+    """Every bin after the first: the bin at t = 0 only collects events from half its width."""
+    dt_us = bin_width_ns / 1000.0
+    return (0.5 * dt_us, nbins * dt_us)
+
+
+def _jittered(truth, jitter_seed):
+    truth = np.array(truth, dtype=np.float64)
+    if jitter_seed is not None:
+        truth = truth * np.random.default_rng(jitter_seed).uniform(0.8, 1.2, truth.size)
+    return truth
+
+
+def cfg1(nbins: int = 16384, bin_width_ns: float = 0.5, seed: int = 0, dtype=np.int32,
+         n0: float = 300.0, jitter_seed: Optional[int] = None) -> Problem:
+    """Single histogram, A = A0 exp(-lambda t) cos(2 pi nu t + phi); 6 parameters."""
+    names = ["N0", "Nbkg", "A0", "lambda", "nu", "phi"]
+    truth = _jittered([n0, 2.0, 0.25, 0.5, 5.0, 10.0], jitter_seed)
+    terms = [[("AMP", (2,)), ("EXP", (3,)), ("TFCOS", (4, 5))]]
+    mp = np.array([[0, 1, 2, 3, 4, 5]], np.int32)
+    det = Detector(truth[0], truth[1], truth[5])
+    comp = Component(truth[2], "TF", nu_mhz=truth[4], lam=truth[3])
+    counts = simulate(seed, [det], [[comp]], nbins, bin_width_ns, dtype)
+    return Problem(counts, np.zeros(1), bin_width_ns, _full_range(nbins, bin_width_ns), terms, mp,
+                   np.zeros(0), 6, truth, names, "cfg1")
+
+
+def _tf2_map(H: int, first: int, shared: dict, with_kt: bool):
+    """Map rows for the two-term TF model (+ optional KT term)."""
+    rows = []
+    # consts: -1 -> A1 = 0.125, -2 -> A2 = 0.125, -3 -> A3 = 0.05
+    for j in range(H):
+        base = first + 3 * j
+        row = [base + 0, base + 1, -1, shared["lambda"], shared["nu1"], base + 2, -2,
+               shared["sigma"], shared["nu2"]]
+        if with_kt:
+            row += [-3, shared["delta"]]
+        rows.append(row)
+    return np.array(rows, np.int32)
+
+
+def cfg2(nhist: int = 8, nbins: int = 65536, bin_width_ns: float = 0.1953125, seed: int = 2,
+         dtype=np.float32, n0: float = 300.0, jitter_seed: Optional[int] = None) -> Problem:
+    """Global two-term TF fit: shared lambda, sigma, nu1, nu2; per-histogram N0, Nbkg, phase.
+
+    A_j = A1 e^{-lambda t} cos(2 pi (nu1 t + phi_j/360)) + A2 e^{-(sigma t)^2/2} cos(2 pi (nu2 t + phi_j/360)),
+    A1 = A2 = 0.125 fixed; 4 + 3 H parameters (28 for H = 8).
+    """
+    terms = [[("AMP", (2,)), ("EXP", (3,)), ("TFCOS", (4, 5))],
+             [("AMP", (6,)), ("GAUSS", (7,)), ("TFCOS", (8, 5))]]
+    shared = {"lambda": 0, "sigma": 1, "nu1": 2, "nu2": 3}
+    mp = _tf2_map(nhist, 4, shared, False)
+    names = ["lambda", "sigma", "nu1", "nu2"]
+    truth = [0.5, 0.3, 5.0, 5.5]
+    for j in range(nhist):
+        ph = (45.0 * j) % 360.0 if nhist <= 8 else 360.0 * j / nhist
+        names += [f"N0_{j}", f"Nbkg_{j}", f"phi_{j}"]
+        truth += [n0, 2.0, ph]
+    truth = _jittered(truth, jitter_seed)
+    dets, comps = [], []
+    for j in range(nhist):
+        b = 4 + 3 * j
+        dets.append(Detector(truth[b], truth[b + 1], truth[b + 2]))
+        comps.append([Component(0.125, "TF", nu_mhz=truth[2], lam=truth[0]),
+                      Component(0.125, "TF", nu_mhz=truth[3], sigma=truth[1])])
+    counts = simulate(seed, dets, comps, nbins, bin_width_ns, dtype)
+    return Problem(counts, np.zeros(nhist), bin_width_ns, _full_range(nbins, bin_width_ns), terms,
+                   mp, np.array([0.125, 0.125]), len(truth), truth, names, "cfg2")
+
+
+def cfg3(nhist: int = 4, nbins: int = 32768, bin_width_ns: float = 0.390625, seed: int = 3,
+         dtype=np.float32, n0: float = 300.0, jitter_seed: Optional[int] = None) -> Problem:
+    """Zero-field static Gaussian Kubo-Toyabe times an exponential: A = A0 KT(Delta, t) e^{-lambda t}.
+
+    Shared A0, Delta, lambda; per-histogram N0, Nbkg: 3 + 2 H parameters (11 for H = 4).
+    """
+    terms = [[("AMP", (2,)), ("KT", (3,)), ("EXP", (4,))]]
+    rows = [[3 + 2 * j, 4 + 2 * j, 0, 1, 2] for j in range(nhist)]
+    names = ["A0", "Delta", "lambda"]
+    truth = [0.25, 0.3, 0.1]
+    for j in range(nhist):
+        names += [f"N0_{j}", f"Nbkg_{j}"]
+        truth += [n0, 2.0]
+    truth = _jittered(truth, jitter_seed)
+    dets, comps = [], []
+    for j in range(nhist):
+        dets.append(Detector(truth[3 + 2 * j], truth[4 + 2 * j], 0.0))
+        comps.append([Component(truth[0], "ZF", delta=truth[1], lam=truth[2])])
+    counts = simulate(seed, dets, comps, nbins, bin_width_ns, dtype)
+    return Problem(counts, np.zeros(nhist), bin_width_ns, _full_range(nbins, bin_width_ns), terms,
+                   np.array(rows, np.int32), np.zeros(0), len(truth), truth, names, "cfg3")
+
+
+def cfg5(nhist: int = 64, nbins: int = 1 << 20, bin_width_ns: Optional[float] = None, seed: int = 5,
+         dtype=np.float32, n0: float = 2.0, nbkg: float = 0.01) -> Problem:
+    """Large single fit: two-term TF (as cfg2) plus 0.05 KT(Delta, t); 5 + 3 H parameters (197 for H = 64).
+
+    Low statistics (N0 = 2 counts per bin), the maximum-likelihood regime.
+    """
+    if bin_width_ns is None:
+        bin_width_ns = 12800.0 / nbins
+    terms = [[("AMP", (2,)), ("EXP", (3,)), ("TFCOS", (4, 5))],
+             [("AMP", (6,)), ("GAUSS", (7,)), ("TFCOS", (8, 5))],
+             [("AMP", (9,)), ("KT", (10,))]]
+    shared = {"lambda": 0, "sigma": 1, "nu1": 2, "nu2": 3, "delta": 4}
+    mp = _tf2_map(nhist, 5, shared, True)
+    names = ["lambda", "sigma", "nu1", "nu2", "Delta"]
+    truth = [0.5, 0.3, 5.0, 5.5, 0.3]
+    dets, comps = [], []
+    for j in range(nhist):
+        ph = 360.0 * j / nhist
+        names += [f"N0_{j}", f"Nbkg_{j}", f"phi_{j}"]
+        truth += [n0, nbkg, ph]
+        dets.append(Detector(n0, nbkg, ph))
+        comps.append([Component(0.125, "TF", nu_mhz=5.0, lam=0.5),
+                      Component(0.125, "TF", nu_mhz=5.5, sigma=0.3),
+                      Component(0.05, "ZF", delta=0.3)])
+    counts = simulate(seed, dets, comps, nbins, bin_width_ns, dtype)
+    return Problem(counts, np.zeros(nhist), bin_width_ns, _full_range(nbins, bin_width_ns), terms,
+                   mp, np.array([0.125, 0.125, 0.05]), len(truth), np.array(truth), names, "cfg5")
+
+
+def paper_tf16(nhist: int = 16, nbins: int = 81920, bin_width_ns: Optional[float] = None,
+               seed: int = 16, dtype=np.float32, n0: float = 300.0) -> Problem:
+    """The paper's benchmark model (Eq. asymmetry): A_j = A0_j exp(-(sigma t)^2/2) cos(2 pi nu t + phi_j).
+
+    Per detector N0, Nbkg, A0, phi; shared sigma and nu: 4 H + 2 parameters (66 for 16 detectors).
+    """
+    if bin_width_ns is None:
+        bin_width_ns = 12800.0 / nbins
+    terms = [[("AMP", (2,)), ("GAUSS", (3,)), ("TFCOS", (4, 5))]]
+    rows = [[2 + 4 * j, 3 + 4 * j, 4 + 4 * j, 0, 1, 5 + 4 * j] for j in range(nhist)]
+    names = ["sigma", "nu"]
+    truth = [0.3, 10.0]
+    dets, comps = [], []
+    for j in range(nhist):
+        ph = 360.0 * j / nhist
+        a0 = 0.2 + 0.002 * j
+        names += [f"N0_{j}", f"Nbkg_{j}", f"A0_{j}", f"phi_{j}"]
+        truth += [n0, 2.0, a0, ph]
+        dets.append(Detector(n0, 2.0, ph))
+        comps.append([Component(a0, "TF", nu_mhz=10.0, sigma=0.3)])
+    counts = simulate(seed, dets, comps, nbins, bin_width_ns, dtype)
+    return Problem(counts, np.zeros(nhist), bin_width_ns, _full_range(nbins, bin_width_ns), terms,
+                   np.array(rows, np.int32), np.zeros(0), len(truth), np.array(truth), names,
+                   "paper_tf16")
+
+
+CONFIGS = {"cfg1": cfg1, "cfg2": cfg2, "cfg3": cfg3, "cfg5": cfg5, "paper_tf16": paper_tf16}
+
+
+# --------------------------------------------------------------------------------------------
+# Serving request stream (the continuous-batching workload)
+# --------------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Request:
+    arrival_s: float
+    problem: Problem
+    x0: np.ndarray
+    mode: int  # 0 chi^2, 1 -2lnL
+
+
+def serving_pool(n_pool: int, seed: int = 4, hist_range=(1, 64), bin_range=(4096, 262144),
+                 span_ns: float = 12800.0,
+                 dtype=np.float32) -> List[Problem]:
+    """A pool of distinct fits: H ~ logU(hist_range), B ~ logU(bin_range), theory drawn from
+    cfg1/cfg2/cfg3, truths jittered by U(0.8, 1.2).
+
+    N0 is scaled by min(1, 4096 / B) so that every histogram holds about the same
+    number of events whatever its binning (a fixed-length run binned finer).
+    """
+    rng = np.random.default_rng(seed)
+    pool = []
+    for i in range(n_pool):
+        H = int(round(math.exp(rng.uniform(math.log(hist_range[0]), math.log(hist_range[1])))))
+        B = int(round(math.exp(rng.uniform(math.log(bin_range[0]), math.log(bin_range[1])))))
+        kind = int(rng.integers(0, 3))
+        dtw = span_ns / B
+        n0 = 300.0 * min(1.0, 4096.0 / B)
+        sub = int(rng.integers(0, 2**31))
+        jit = int(rng.integers(0, 2**31))
+        if kind == 0:
+            p = cfg1(nbins=B, bin_width_ns=dtw, seed=sub, dtype=dtype, n0=n0, jitter_seed=jit)
+        elif kind == 1:
+            p = cfg2(nhist=H, nbins=B, bin_width_ns=dtw, seed=sub, dtype=dtype, n0=n0, jitter_seed=jit)
+        else:
+            p = cfg3(nhist=H, nbins=B, bin_width_ns=dtw, seed=sub, dtype=dtype, n0=n0, jitter_seed=jit)
+        pool.append(p)
+    return pool
+
+
+def request_stream(pool: Sequence[Problem], n_requests: int, rate_per_s: float, seed: int = 4,
+                   mode_mix: float = 0.5) -> List[Request]:
+    """Poisson arrivals at ``rate_per_s`` (0 or inf: all at t = 0); start points from
+    :func:`start_point` around each fit's (jittered) truth."""
+    rng = np.random.default_rng(seed + 1)
+    t = 0.0
+    out = []
+    for i in range(n_requests):
+        if rate_per_s and math.isfinite(rate_per_s):
+            t += rng.exponential(1.0 / rate_per_s)
+        p = pool[i % len(pool)]
+        x0 = start_point(p, int(rng.integers(0, 2**31)))
+        mode = int(rng.random() < mode_mix)
+        out.append(Request(t, p, x0, mode))
+    return out

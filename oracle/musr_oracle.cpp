@@ -1,0 +1,542 @@
+// musr_oracle.cpp -- plain, slow, single-threaded FP64 CPU oracle for the
+// muSR chi^2 / Poisson -2lnL cost of arXiv 1509.07685, Section 4.
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the reference that the CUDA path is
+// checked against.  Only the test suite, the smoke check and the CPU-baseline
+// leg of the benchmark may load it.  It shares no code, header, table or
+// constant generator with the CUDA library; the two agree only through the
+// definitions of the paper restated below.
+//
+// What it computes (Section 4.1):
+//   Eq. positron_histo   N^j(t) = N0^j exp(-t/tau_mu) [1 + A^j(p, t)] + Nbkg^j
+//                        at discrete times t = n * dt (here t_n = (n - t0_j) * dt)
+//   Eq. chisq            chi^2 = sum_j sum_n (d - N)^2 / d_err^2,  d_err^2 = d
+//                        (read as max(d, 1) so that empty bins are defined)
+//   Eq. log-likelihood   L = 2 sum_j sum_n { (N - d) + d log(d/N)   d > 0
+//                                            (N - d)                d <= 0 }
+//                        (the Poisson deviance; minimised, zero iff N == d)
+//   Eq. asymmetry        A(t) = A0 exp(-(sigma t)^2 / 2) cos(gamma_mu B t + phi)
+//                        generalised to a sum of terms, each a product of the
+//                        primitives AMP, EXP, GAUSS, KT (static Gaussian
+//                        Kubo-Toyabe), TFCOS.
+//
+// Readings of the paper that this oracle fixes (the paper leaves them open):
+//   * tau_mu = 2.197019 us.
+//   * t_n = (n - t0_j) * (bin_width_ns / 1000.0) in microseconds, t0_j in
+//     (possibly fractional) bins; bin n is in the fit when lo <= t_n <= hi.
+//   * TFCOS(nu, phi) = cos(2 pi (nu t + phi / 360)), nu in MHz, phi in degrees
+//     (gamma_mu B = 2 pi nu).
+//   * GAUSS(sigma) = exp(-(sigma t)^2 / 2), EXP(lambda) = exp(-lambda t).
+//   * KT(Delta) = 1/3 + 2/3 (1 - Delta^2 t^2) exp(-Delta^2 t^2 / 2).
+//   * Local slot 0 is N0, slot 1 is Nbkg; terms reference any slot.
+//   * MLE with N <= 0 in a bin with d > 0 is +infinity (status 1).
+//
+// Summation: every sum over bins is Neumaier-compensated, in bin order
+// (histogram-major), so that the oracle's own rounding stays far below the
+// 1e-12 relative tolerance used against the GPU path.
+//
+// The value function is a template on the scalar type so that the same code,
+// instantiated on std::complex<double>, yields the complex-step derivative
+// (Squire & Trapp 1998) used to pin the analytic gradient.
+
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <vector>
+
+namespace {
+
+constexpr double kTauMu = 2.197019;  // muon lifetime in microseconds
+constexpr double kPi = 3.14159265358979323846;
+
+enum PrimKind { kAmp = 1, kExp = 2, kGauss = 3, kKT = 4, kTFCos = 5 };
+constexpr int kMaxPrim = 4;
+
+using cplx = std::complex<double>;
+
+inline double re(double x) { return x; }
+inline double re(const cplx& x) { return x.real(); }
+
+// Neumaier's improvement of Kahan summation, one real accumulator.
+struct Neumaier {
+  double s = 0.0, c = 0.0;
+  void add(double x) {
+    double t = s + x;
+    if (std::fabs(s) >= std::fabs(x))
+      c += (s - t) + x;
+    else
+      c += (x - t) + s;
+    s = t;
+  }
+  double value() const { return s + c; }
+};
+
+// Complex accumulator: real and imaginary parts compensated separately.
+struct NeumaierC {
+  Neumaier r, i;
+  void add(const cplx& x) { r.add(x.real()); i.add(x.imag()); }
+  void add(double x) { r.add(x); }
+  cplx value() const { return cplx(r.value(), i.value()); }
+};
+
+template <class T> struct AccFor;
+template <> struct AccFor<double> { using type = Neumaier; };
+template <> struct AccFor<cplx> { using type = NeumaierC; };
+
+struct Theory {
+  int nterms;
+  const int32_t* nprim;  // [nterms]
+  const int32_t* kind;   // [nterms][kMaxPrim]
+  const int32_t* slot;   // [nterms][kMaxPrim][2]
+};
+
+struct Problem {
+  const double* data;  // [H][B], histogram-major
+  int H;
+  int64_t B;
+  const double* t0;  // [H], in bins
+  double dt_us;
+  double lo, hi;  // fit range, microseconds, closed
+  Theory th;
+  const int32_t* map;  // [H][nslots]: >= 0 global parameter, < 0 -> consts[-1-k]
+  int nslots;
+  const double* consts;
+  int nconsts;
+  int P;
+};
+
+// Time of bin n of histogram h (Section 4.1, t = n * dt, shifted by t0).
+inline double bin_time(const Problem& pb, int h, int64_t n) {
+  return (static_cast<double>(n) - pb.t0[h]) * pb.dt_us;
+}
+
+inline bool in_fit(const Problem& pb, double t) { return pb.lo <= t && t <= pb.hi; }
+
+// Value of local slot s of histogram h for parameter vector x.
+template <class T>
+T slot_value(const Problem& pb, const T* x, int h, int s) {
+  int32_t m = pb.map[static_cast<int64_t>(h) * pb.nslots + s];
+  if (m >= 0) return x[m];
+  return T(pb.consts[-1 - m]);
+}
+
+// One primitive factor of a term of A(t) (Eq. asymmetry and its generalisation).
+template <class T>
+T primitive(int kind, const T& p0, const T& p1, double t) {
+  switch (kind) {
+    case kAmp:
+      return p0;
+    case kExp:
+      return std::exp(-p0 * t);
+    case kGauss:
+      return std::exp(-0.5 * (p0 * t) * (p0 * t));
+    case kKT: {
+      T u = (p0 * t) * (p0 * t);
+      return 1.0 / 3.0 + (2.0 / 3.0) * (1.0 - u) * std::exp(-0.5 * u);
+    }
+    case kTFCos:
+      return std::cos(2.0 * kPi * (p0 * t + p1 / 360.0));
+    default:
+      return T(std::numeric_limits<double>::quiet_NaN());
+  }
+}
+
+// Derivatives of one primitive with respect to its first and second slot.
+inline void primitive_deriv(int kind, double p0, double p1, double t, double* d0, double* d1) {
+  *d0 = 0.0;
+  *d1 = 0.0;
+  switch (kind) {
+    case kAmp:
+      *d0 = 1.0;
+      break;
+    case kExp:
+      *d0 = -t * std::exp(-p0 * t);
+      break;
+    case kGauss:
+      *d0 = -p0 * t * t * std::exp(-0.5 * (p0 * t) * (p0 * t));
+      break;
+    case kKT: {
+      double u = (p0 * t) * (p0 * t);
+      *d0 = (2.0 / 3.0) * p0 * t * t * std::exp(-0.5 * u) * (u - 3.0);
+      break;
+    }
+    case kTFCos: {
+      double s = std::sin(2.0 * kPi * (p0 * t + p1 / 360.0));
+      *d0 = -s * 2.0 * kPi * t;
+      *d1 = -s * 2.0 * kPi / 360.0;
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+inline int nslots_of(int kind) { return kind == kTFCos ? 2 : 1; }
+
+// Eq. positron_histo for histogram h at time t.
+template <class T>
+T model(const Problem& pb, const T* x, int h, double t) {
+  T A = T(0.0);
+  for (int k = 0; k < pb.th.nterms; ++k) {
+    T term = T(1.0);
+    for (int m = 0; m < pb.th.nprim[k]; ++m) {
+      int kind = pb.th.kind[k * kMaxPrim + m];
+      const int32_t* sl = pb.th.slot + (k * kMaxPrim + m) * 2;
+      T p0 = slot_value(pb, x, h, sl[0]);
+      T p1 = nslots_of(kind) == 2 ? slot_value(pb, x, h, sl[1]) : T(0.0);
+      term = term * primitive(kind, p0, p1, t);
+    }
+    A = A + term;
+  }
+  T N0 = slot_value(pb, x, h, 0);
+  T Nbkg = slot_value(pb, x, h, 1);
+  return N0 * std::exp(-t / kTauMu) * (1.0 + A) + Nbkg;
+}
+
+// One bin's contribution to Eq. chisq (mode 0) or Eq. log-likelihood (mode 1).
+// Sets *bad when the likelihood is undefined (N <= 0 where d > 0).
+template <class T>
+T bin_cost(int mode, double d, const T& N, bool* bad) {
+  if (mode == 0) {
+    T r = d - N;
+    return r * r / std::fmax(d, 1.0);
+  }
+  if (d > 0.0) {
+    if (re(N) <= 0.0) {
+      *bad = true;
+      return T(0.0);
+    }
+    return 2.0 * ((N - d) + d * std::log(d / N));
+  }
+  return 2.0 * (N - d);
+}
+
+template <class T>
+int cost_value(const Problem& pb, const T* x, int mode, T* out) {
+  typename AccFor<T>::type acc;
+  bool bad = false;
+  for (int h = 0; h < pb.H; ++h) {
+    const double* row = pb.data + static_cast<int64_t>(h) * pb.B;
+    for (int64_t n = 0; n < pb.B; ++n) {
+      double t = bin_time(pb, h, n);
+      if (!in_fit(pb, t)) continue;
+      T N = model(pb, x, h, t);
+      acc.add(bin_cost(mode, row[n], N, &bad));
+    }
+  }
+  if (bad) {
+    *out = T(std::numeric_limits<double>::infinity());
+    return 1;
+  }
+  *out = acc.value();
+  return 0;
+}
+
+// Value plus analytic gradient: dcost/dx_p = sum over bins of
+// (dcost/dN) * sum over (slot s of hist h mapped to p) dN/d(slot s).
+// gscale[p] accumulates sum |per-bin contribution|, the scale against which
+// the GPU gradient tolerance is stated.
+int cost_grad(const Problem& pb, const double* x, int mode, double* value, double* grad,
+              double* gscale) {
+  Neumaier acc;
+  std::vector<Neumaier> g(pb.P), gs(pb.P);
+  std::vector<double> dslot(pb.nslots);
+  bool bad = false;
+  for (int h = 0; h < pb.H; ++h) {
+    const double* row = pb.data + static_cast<int64_t>(h) * pb.B;
+    double N0 = slot_value(pb, x, h, 0);
+    for (int64_t n = 0; n < pb.B; ++n) {
+      double t = bin_time(pb, h, n);
+      if (!in_fit(pb, t)) continue;
+      double d = row[n];
+      double E = std::exp(-t / kTauMu);
+      // A(t) and the derivative of every slot through the product rule.
+      std::fill(dslot.begin(), dslot.end(), 0.0);
+      double A = 0.0;
+      for (int k = 0; k < pb.th.nterms; ++k) {
+        int np = pb.th.nprim[k];
+        double f[kMaxPrim], p0[kMaxPrim], p1[kMaxPrim];
+        for (int m = 0; m < np; ++m) {
+          int kind = pb.th.kind[k * kMaxPrim + m];
+          const int32_t* sl = pb.th.slot + (k * kMaxPrim + m) * 2;
+          p0[m] = slot_value(pb, x, h, sl[0]);
+          p1[m] = nslots_of(kind) == 2 ? slot_value(pb, x, h, sl[1]) : 0.0;
+          f[m] = primitive(kind, p0[m], p1[m], t);
+        }
+        double term = 1.0;
+        for (int m = 0; m < np; ++m) term *= f[m];
+        A += term;
+        for (int m = 0; m < np; ++m) {
+          int kind = pb.th.kind[k * kMaxPrim + m];
+          const int32_t* sl = pb.th.slot + (k * kMaxPrim + m) * 2;
+          double rest = 1.0;
+          for (int q = 0; q < np; ++q)
+            if (q != m) rest *= f[q];
+          double d0, d1;
+          primitive_deriv(kind, p0[m], p1[m], t, &d0, &d1);
+          dslot[sl[0]] += N0 * E * d0 * rest;
+          if (nslots_of(kind) == 2) dslot[sl[1]] += N0 * E * d1 * rest;
+        }
+      }
+      dslot[0] += E * (1.0 + A);
+      dslot[1] += 1.0;
+      double Nbkg = slot_value(pb, x, h, 1);
+      double N = N0 * E * (1.0 + A) + Nbkg;
+      double W;  // dcost / dN for this bin
+      if (mode == 0) {
+        double r = d - N;
+        acc.add(r * r / std::fmax(d, 1.0));
+        W = -2.0 * r / std::fmax(d, 1.0);
+      } else if (d > 0.0) {
+        if (N <= 0.0) {
+          bad = true;
+          continue;
+        }
+        acc.add(2.0 * ((N - d) + d * std::log(d / N)));
+        W = 2.0 * (1.0 - d / N);
+      } else {
+        acc.add(2.0 * (N - d));
+        W = 2.0;
+      }
+      for (int s = 0; s < pb.nslots; ++s) {
+        int32_t m = pb.map[static_cast<int64_t>(h) * pb.nslots + s];
+        if (m < 0) continue;
+        double c = W * dslot[s];
+        g[m].add(c);
+        gs[m].add(std::fabs(c));
+      }
+    }
+  }
+  for (int p = 0; p < pb.P; ++p) {
+    if (grad) grad[p] = bad ? 0.0 : g[p].value();
+    if (gscale) gscale[p] = gs[p].value();
+  }
+  if (bad) {
+    *value = std::numeric_limits<double>::infinity();
+    return 1;
+  }
+  *value = acc.value();
+  return 0;
+}
+
+Problem make_problem(const double* data, int H, int64_t B, const double* t0, double bin_width_ns,
+                     double lo, double hi, int nterms, const int32_t* nprim, const int32_t* kind,
+                     const int32_t* slot, const int32_t* map, int nslots, const double* consts,
+                     int nconsts, int P) {
+  Problem pb;
+  pb.data = data;
+  pb.H = H;
+  pb.B = B;
+  pb.t0 = t0;
+  pb.dt_us = bin_width_ns / 1000.0;
+  pb.lo = lo;
+  pb.hi = hi;
+  pb.th.nterms = nterms;
+  pb.th.nprim = nprim;
+  pb.th.kind = kind;
+  pb.th.slot = slot;
+  pb.map = map;
+  pb.nslots = nslots;
+  pb.consts = consts;
+  pb.nconsts = nconsts;
+  pb.P = P;
+  return pb;
+}
+
+double inf_norm(const std::vector<double>& v) {
+  double m = 0.0;
+  for (double a : v) m = std::fmax(m, std::fabs(a));
+  return m;
+}
+
+}  // namespace
+
+#define ORACLE_PROBLEM_ARGS                                                                  \
+  const double *data, int H, int64_t B, const double *t0, double bin_width_ns, double lo,   \
+      double hi, int nterms, const int32_t *nprim, const int32_t *kind, const int32_t *slot, \
+      const int32_t *map, int nslots, const double *consts, int nconsts, int P
+#define ORACLE_PROBLEM \
+  make_problem(data, H, B, t0, bin_width_ns, lo, hi, nterms, nprim, kind, slot, map, nslots, consts, nconsts, P)
+
+extern "C" {
+
+// One primitive at time t (Section 4.1, Eq. asymmetry and its generalisation).
+double oracle_primitive(int kind, double p0, double p1, double t) {
+  return primitive<double>(kind, p0, p1, t);
+}
+
+// Eq. positron_histo of histogram h at time t (microseconds).
+double oracle_model(ORACLE_PROBLEM_ARGS, const double* x, int h, double t) {
+  Problem pb = ORACLE_PROBLEM;
+  return model<double>(pb, x, h, t);
+}
+
+// The whole cost (Eq. chisq for mode 0, Eq. log-likelihood for mode 1) and,
+// when grad != NULL, its analytic gradient.  Returns 0, or 1 when the
+// likelihood is +infinity (then *value = +inf and grad is all zeros).
+int oracle_cost(ORACLE_PROBLEM_ARGS, const double* x, int mode, double* value, double* grad,
+                double* gscale) {
+  Problem pb = ORACLE_PROBLEM;
+  if (grad == nullptr && gscale == nullptr) return cost_value<double>(pb, x, mode, value);
+  return cost_grad(pb, x, mode, value, grad, gscale);
+}
+
+// Complex-step derivative of the cost along direction v:
+// Im(cost(x + i h v)) / h, the same value code evaluated in complex arithmetic.
+int oracle_cost_cstep(ORACLE_PROBLEM_ARGS, const double* x, const double* v, double h, int mode,
+                      double* deriv) {
+  Problem pb = ORACLE_PROBLEM;
+  std::vector<cplx> xc(P);
+  for (int p = 0; p < P; ++p) xc[p] = cplx(x[p], h * v[p]);
+  cplx out;
+  int st = cost_value<cplx>(pb, xc.data(), mode, &out);
+  *deriv = out.imag() / h;
+  return st;
+}
+
+// Hessian by central differences of the analytic gradient, symmetrised.
+// step[p] is the difference step of parameter p.  hess is [P][P].
+int oracle_hessian(ORACLE_PROBLEM_ARGS, const double* x, const double* step, int mode,
+                   double* hess) {
+  Problem pb = ORACLE_PROBLEM;
+  std::vector<double> xp(x, x + P), gp(P), gm(P);
+  double f;
+  for (int j = 0; j < P; ++j) {
+    xp[j] = x[j] + step[j];
+    if (cost_grad(pb, xp.data(), mode, &f, gp.data(), nullptr)) return 1;
+    xp[j] = x[j] - step[j];
+    if (cost_grad(pb, xp.data(), mode, &f, gm.data(), nullptr)) return 1;
+    xp[j] = x[j];
+    for (int i = 0; i < P; ++i) hess[i * P + j] = (gp[i] - gm[i]) / (2.0 * step[j]);
+  }
+  for (int i = 0; i < P; ++i)
+    for (int j = 0; j < i; ++j) {
+      double a = 0.5 * (hess[i * P + j] + hess[j * P + i]);
+      hess[i * P + j] = hess[j * P + i] = a;
+    }
+  return 0;
+}
+
+// BFGS minimisation standing in for Minuit2's migrad (Section 4: the
+// minimiser runs on the host and calls the cost once per trial point).
+//   * initial inverse Hessian: diag(1/h_ii) from forward differences of the
+//     analytic gradient (step fd_step[p]); |h_ii| is used, and 1 when h_ii == 0;
+//   * direction p = -Hinv g; if not a descent direction, Hinv is reset;
+//   * backtracking line search from alpha = 1, halving, until the Armijo
+//     condition f_new <= f + 1e-4 alpha g.p holds with f_new finite;
+//   * BFGS inverse update when s.y > 0;
+//   * stop when max|g| <= gtol * max(1, |f|), when a step changes no
+//     parameter, or after maxit iterations.
+// Returns 0 on convergence, 2 when maxit was reached, 3 when the line search
+// failed, 1 when the cost was +inf at the start.
+int oracle_fit(ORACLE_PROBLEM_ARGS, int mode, const double* x0, const double* fd_step, int maxit,
+               double gtol, double* x_out, double* f_out, double* g_out, int* iters_out) {
+  Problem pb = ORACLE_PROBLEM;
+  std::vector<double> x(x0, x0 + P), g(P), xn(P), gn(P), p(P), s(P), y(P), Hy(P);
+  std::vector<double> Hinv(static_cast<size_t>(P) * P, 0.0);
+  double f;
+  int status = 2;
+  int it = 0;
+  if (cost_grad(pb, x.data(), mode, &f, g.data(), nullptr)) {
+    *f_out = f;
+    *iters_out = 0;
+    return 1;
+  }
+  auto reset_hinv = [&]() {
+    std::fill(Hinv.begin(), Hinv.end(), 0.0);
+    for (int j = 0; j < P; ++j) {
+      std::vector<double> xs(x);
+      xs[j] += fd_step[j];
+      double fs;
+      std::vector<double> gsj(P);
+      double hjj = 0.0;
+      if (cost_grad(pb, xs.data(), mode, &fs, gsj.data(), nullptr) == 0)
+        hjj = std::fabs((gsj[j] - g[j]) / fd_step[j]);
+      Hinv[static_cast<size_t>(j) * P + j] = hjj > 0.0 ? 1.0 / hjj : 1.0;
+    }
+  };
+  reset_hinv();
+  for (it = 0; it < maxit; ++it) {
+    if (inf_norm(g) <= gtol * std::fmax(1.0, std::fabs(f))) {
+      status = 0;
+      break;
+    }
+    double gp = 0.0;
+    for (int i = 0; i < P; ++i) {
+      double a = 0.0;
+      for (int j = 0; j < P; ++j) a -= Hinv[static_cast<size_t>(i) * P + j] * g[j];
+      p[i] = a;
+      gp += a * g[i];
+    }
+    if (!(gp < 0.0)) {
+      reset_hinv();
+      gp = 0.0;
+      for (int i = 0; i < P; ++i) {
+        p[i] = -Hinv[static_cast<size_t>(i) * P + i] * g[i];
+        gp += p[i] * g[i];
+      }
+    }
+    double alpha = 1.0, fn = 0.0;
+    bool ok = false;
+    for (int ls = 0; ls < 80; ++ls) {
+      for (int i = 0; i < P; ++i) xn[i] = x[i] + alpha * p[i];
+      int st = cost_grad(pb, xn.data(), mode, &fn, gn.data(), nullptr);
+      if (st == 0 && std::isfinite(fn) && fn <= f + 1e-4 * alpha * gp) {
+        ok = true;
+        break;
+      }
+      alpha *= 0.5;
+    }
+    if (!ok) {
+      status = 3;
+      break;
+    }
+    bool moved = false;
+    double sy = 0.0;
+    for (int i = 0; i < P; ++i) {
+      s[i] = xn[i] - x[i];
+      y[i] = gn[i] - g[i];
+      sy += s[i] * y[i];
+      if (xn[i] != x[i]) moved = true;
+    }
+    x.swap(xn);
+    g.swap(gn);
+    f = fn;
+    if (!moved) {
+      status = 0;
+      break;
+    }
+    if (sy > 0.0) {
+      // Hinv <- (I - rho s y^T) Hinv (I - rho y s^T) + rho s s^T
+      double rho = 1.0 / sy;
+      double yHy = 0.0;
+      for (int i = 0; i < P; ++i) {
+        double a = 0.0;
+        for (int j = 0; j < P; ++j) a += Hinv[static_cast<size_t>(i) * P + j] * y[j];
+        Hy[i] = a;
+        yHy += y[i] * a;
+      }
+      for (int i = 0; i < P; ++i)
+        for (int j = 0; j < P; ++j)
+          Hinv[static_cast<size_t>(i) * P + j] +=
+              -rho * (Hy[i] * s[j] + s[i] * Hy[j]) + (rho * rho * yHy + rho) * s[i] * s[j];
+    }
+  }
+  std::memcpy(x_out, x.data(), sizeof(double) * P);
+  if (g_out) std::memcpy(g_out, g.data(), sizeof(double) * P);
+  *f_out = f;
+  *iters_out = it;
+  return status;
+}
+
+// Neumaier-compensated sum of n doubles, exposed so that the summation itself
+// can be pinned against an exactly rounded sum.
+double oracle_neumaier_sum(const double* v, int64_t n) {
+  Neumaier a;
+  for (int64_t i = 0; i < n; ++i) a.add(v[i]);
+  return a.value();
+}
+
+}  // extern "C"

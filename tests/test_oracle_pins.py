@@ -1,0 +1,307 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by mathematics.
+
+None of these tests re-types the oracle's formulas: every expected value comes
+from a closed form (geometric series of the decay and of the damped cosine), a
+special value (Kubo-Toyabe at 0, at infinity and at its minimum), an exact
+identity (data equal to the model), an optimum known in closed form (constant
+model), an independent differentiation method (complex step, finite
+differences) or an exactly rounded sum.  Each test names the mistake it is
+there to catch.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from musr_inputs import TAU_MU_US, Problem
+
+CHI2, MLE = oracle.CHI2, oracle.MLE
+
+
+def _problem(counts, terms, mp, nparams, bin_width_ns=0.5, t0=None, fit=(0.0, 1e9), consts=()):
+    counts = np.atleast_2d(np.asarray(counts, dtype=np.float64))
+    H = counts.shape[0]
+    return Problem(counts, np.zeros(H) if t0 is None else np.asarray(t0, float), bin_width_ns,
+                   fit, terms, np.atleast_2d(np.asarray(mp, np.int32)),
+                   np.asarray(consts, dtype=np.float64), nparams, np.zeros(nparams),
+                   [f"p{i}" for i in range(nparams)])
+
+
+# ------------------------------------------------------------------------------------------
+# Primitives (Eq. asymmetry and its generalisation)
+# ------------------------------------------------------------------------------------------
+
+def test_kubo_toyabe_special_values():
+    """KT(0) = 1, KT(inf) = 1/3, minimum at t = sqrt(3)/Delta equal to 1/3 - (4/3) e^{-3/2}.
+
+    Catches a wrong exponent factor, a wrong sign of the (1 - Delta^2 t^2) factor and
+    wrong 1/3, 2/3 weights."""
+    from scipy.optimize import minimize_scalar
+    for delta in (0.1, 0.3, 1.7):
+        assert oracle.primitive("KT", delta, 0.0, 0.0) == 1.0
+        assert abs(oracle.primitive("KT", delta, 0.0, 60.0 / delta) - 1.0 / 3.0) < 1e-15
+        res = minimize_scalar(lambda t: oracle.primitive("KT", delta, 0.0, t),
+                              bounds=(0.5 / delta, 4.0 / delta), method="bounded",
+                              options={"xatol": 1e-10})
+        assert abs(res.x - math.sqrt(3.0) / delta) < 1e-4 / delta
+        assert abs(res.fun - (1.0 / 3.0 - (4.0 / 3.0) * math.exp(-1.5))) < 1e-12
+
+
+def test_relaxation_primitives_special_values():
+    """EXP at lambda t = 1 is 1/e; GAUSS at sigma t = sqrt(2) is 1/e (the factor 1/2 of
+    Eq. asymmetry); both are even/odd as they must be."""
+    assert abs(oracle.primitive("EXP", 0.5, 0.0, 2.0) - math.exp(-1.0)) < 4e-16
+    assert abs(oracle.primitive("GAUSS", 0.3, 0.0, math.sqrt(2.0) / 0.3) - math.exp(-1.0)) < 4e-16
+    assert oracle.primitive("GAUSS", -0.3, 0.0, 1.0) == oracle.primitive("GAUSS", 0.3, 0.0, 1.0)
+    assert oracle.primitive("AMP", 0.125, 0.0, 3.0) == 0.125
+
+
+def test_tf_cosine_units():
+    """cos(2 pi (nu t + phi/360)): nu in MHz with t in us, phi in degrees.
+
+    Catches radians/degrees, a missing 2 pi, and a sign error on the phase."""
+    assert abs(oracle.primitive("TFCOS", 1.0, 0.0, 0.25)) < 1e-15  # quarter turn
+    assert abs(oracle.primitive("TFCOS", 1.0, 90.0, 0.0)) < 1e-15
+    assert oracle.primitive("TFCOS", 7.0, 180.0, 0.0) == -1.0
+    assert abs(oracle.primitive("TFCOS", 2.0, 30.0, 0.125) + 0.5) < 1e-15  # cos(pi/2 + pi/6)
+    assert abs(oracle.primitive("TFCOS", 5.0, 10.0, 0.0) - math.cos(math.radians(10.0))) < 1e-16
+
+
+# ------------------------------------------------------------------------------------------
+# Costs in closed form
+# ------------------------------------------------------------------------------------------
+
+def test_data_equal_model_gives_zero():
+    """chi^2 = 0 and -2lnL = 0 when the data equal the model (Eq. chisq, Eq. log-likelihood).
+
+    Catches a wrong sign or a dropped (N - d) term of the likelihood."""
+    terms = [[("AMP", (2,)), ("EXP", (3,)), ("TFCOS", (4, 5))], [("AMP", (6,)), ("KT", (7,))]]
+    mp = [[0, 1, 2, 3, 4, 5, 6, 7]]
+    x = np.array([250.0, 3.0, 0.2, 0.4, 3.0, 20.0, 0.1, 0.5])
+    p = _problem(np.zeros((1, 700)), terms, mp, 8, bin_width_ns=10.0, fit=(0.0, 6.0))
+    dt = p.bin_width_ns / 1000.0
+    d = np.array([[oracle.model(p, x, 0, n * dt) for n in range(700)]])
+    p = p.with_counts(d)
+    for mode in (CHI2, MLE):
+        v, g, gs, st = oracle.cost(p, x, mode)
+        assert st == 0
+        assert abs(v) < 1e-18 * 700 + 1e-20
+        assert np.all(np.abs(g) <= 1e-12 * gs + 1e-300)
+
+
+def test_constant_model_closed_forms():
+    """Constant model N = c (N0 = 0, A = 0) on constant data k:
+    chi^2 = n (k - c)^2 / max(k, 1);  -2lnL = 2 n [(c - k) + k ln(k / c)]  (k > 0), 2 n c (k = 0)."""
+    n = 333
+    for k, c in ((7.0, 5.5), (0.0, 2.5), (1.0, 0.25), (0.5, 3.0)):
+        p = _problem(np.full((1, n), k), [], [[0, 1]], 2, fit=(0.0, 1e9))
+        x = np.array([0.0, c])
+        chi2, _, _, _ = oracle.cost(p, x, CHI2, grad=False)
+        assert chi2 == pytest.approx(n * (k - c) ** 2 / max(k, 1.0), rel=1e-14)
+        mle, _, _, _ = oracle.cost(p, x, MLE, grad=False)
+        ref = 2 * n * ((c - k) + k * math.log(k / c)) if k > 0 else 2 * n * c
+        assert mle == pytest.approx(ref, rel=1e-13)
+
+
+def _geom(a, b, t0, c):
+    """sum_{n=a}^{b} exp((n - t0) c) for real or complex c (closed form)."""
+    m = b - a + 1
+    return np.exp((a - t0) * c) * np.expm1(m * c) / np.expm1(c)
+
+
+def test_exponential_decay_geometric_sum():
+    """Pure decay N = N0 e^{-t/tau}, d = 0: -2lnL = 2 N0 sum r^(n - t0), chi^2 = N0^2 sum r^(2(n - t0)).
+
+    The fit range and t0 are chosen so that the first and last bins are known by hand:
+    dt = 0.5 ns, t0 = 10.25 bins, range [0.01, 1.0] us -> bins 31 .. 2010 (closed range).
+    Catches tau_mu, the ns -> us conversion, the sign of t0 and an open/closed range."""
+    N0 = 123.0
+    p = _problem(np.zeros((1, 4096)), [], [[0, 1]], 2, bin_width_ns=0.5, t0=[10.25],
+                 fit=(0.01, 1.0))
+    x = np.array([N0, 0.0])
+    dt = 0.5e-3
+    S1 = _geom(31, 2010, 10.25, -dt / TAU_MU_US)
+    S2 = _geom(31, 2010, 10.25, -2.0 * dt / TAU_MU_US)
+    mle, _, _, _ = oracle.cost(p, x, MLE, grad=False)
+    chi2, _, _, _ = oracle.cost(p, x, CHI2, grad=False)
+    assert mle == pytest.approx(2.0 * N0 * S1, rel=1e-13)
+    assert chi2 == pytest.approx(N0 * N0 * S2, rel=1e-13)
+
+
+def test_fit_range_is_closed_at_both_ends():
+    """A bin whose time equals lo or hi exactly is in the fit (the range is closed)."""
+    # dt = 1 ns = 1e-3 us (exact products), t0 = 0; t_n = n * 1e-3.  lo = t_4, hi = t_9.
+    p = _problem(np.zeros((1, 16)), [], [[0, 1]], 2, bin_width_ns=1.0, fit=(4 * 1e-3, 9 * 1e-3))
+    mle, _, _, _ = oracle.cost(p, np.array([0.0, 1.0]), MLE, grad=False)
+    assert mle == pytest.approx(2.0 * 6, rel=1e-15)  # bins 4..9, N = Nbkg = 1 each
+
+
+def test_damped_cosine_geometric_sum():
+    """N = N0 e^{-t/tau} [1 + A e^{-lambda t} cos(2 pi (nu t + phi/360))] + Nbkg with d = 0:
+    -2lnL / 2 = N0 S(-dt/tau) + N0 A Re(e^{i phi} S(c)) + Nbkg n, c = (-1/tau - lambda + 2 pi i nu) dt.
+
+    Catches the phase convention, the frequency unit, the sign of lambda, a dropped N0
+    on the asymmetry term and a dropped background."""
+    N0, Nbkg, A, lam, nu, phi = 80.0, 1.5, 0.3, 0.7, 13.0, 37.0
+    terms = [[("AMP", (2,)), ("EXP", (3,)), ("TFCOS", (4, 5))]]
+    p = _problem(np.zeros((1, 5000)), terms, [[0, 1, 2, 3, 4, 5]], 6, bin_width_ns=0.8,
+                 t0=[3.5], fit=(0.0002, 3.0))
+    # t_n = (n - 3.5) * 8e-4 >= 2e-4 -> n >= 3.75 -> first 4; <= 3.0 -> n <= 3753.5 -> last 3753
+    a, b, t0, dt = 4, 3753, 3.5, 0.8e-3
+    c = complex(-1.0 / TAU_MU_US - lam, 2.0 * math.pi * nu) * dt
+    S0 = _geom(a, b, t0, -dt / TAU_MU_US)
+    S1 = _geom(a, b, t0, c)
+    ref = 2.0 * (N0 * S0 + N0 * A * (np.exp(1j * math.radians(phi)) * S1).real + Nbkg * (b - a + 1))
+    mle, _, _, _ = oracle.cost(p, np.array([N0, Nbkg, A, lam, nu, phi]), MLE, grad=False)
+    assert mle == pytest.approx(ref, rel=1e-12)
+
+
+def test_likelihood_undefined_when_model_not_positive():
+    """-2lnL is +inf (status 1) when N <= 0 in a bin with d > 0; d = 0 bins stay finite."""
+    p = _problem(np.array([[0.0, 3.0, 0.0]]), [], [[0, 1]], 2, fit=(0.0, 1e9))
+    v, g, gs, st = oracle.cost(p, np.array([0.0, -1.0]), MLE)
+    assert st == 1 and math.isinf(v) and np.all(g == 0.0)
+    p0 = p.with_counts(np.array([[0.0, 0.0, 0.0]]))
+    v, _, _, st = oracle.cost(p0, np.array([0.0, -1.0]), MLE)
+    assert st == 0 and v == pytest.approx(-6.0)
+    v, _, _, st = oracle.cost(p, np.array([0.0, -1.0]), CHI2)
+    assert st == 0 and np.isfinite(v)
+
+
+def test_costs_are_nonnegative_and_chi2_weights_use_data():
+    """Both costs are >= 0 on Poisson data; the chi^2 variance is max(d, 1) of the data
+    (Neyman), so doubling the model leaves the weights unchanged.  Catches a variance taken
+    from the theory."""
+    rng = np.random.default_rng(11)
+    d = rng.poisson(3.0, size=(2, 300)).astype(float)
+    p = _problem(d, [], [[0, 1], [0, 1]], 2, fit=(0.0, 1e9))
+    for c in (0.5, 3.0, 9.0):
+        for mode in (CHI2, MLE):
+            v, _, _, _ = oracle.cost(p, np.array([0.0, c]), mode, grad=False)
+            assert v >= 0.0
+        chi2, _, _, _ = oracle.cost(p, np.array([0.0, c]), CHI2, grad=False)
+        ref = math.fsum(((dd - c) ** 2 / max(dd, 1.0)) for dd in d.ravel())
+        assert chi2 == pytest.approx(ref, rel=1e-14)
+
+
+def test_neumaier_sum_is_exact_on_cancelling_series():
+    """The compensated sum matches the exactly rounded sum (math.fsum) where naive
+    summation loses every digit."""
+    rng = np.random.default_rng(3)
+    big = rng.uniform(1e15, 1e16, 5000)
+    v = np.concatenate([big, rng.uniform(0, 1, 5000), -big])
+    rng.shuffle(v)
+    assert oracle.neumaier_sum(v) == pytest.approx(math.fsum(v), abs=1e-9)
+
+
+# ------------------------------------------------------------------------------------------
+# Gradient: analytic vs complex step vs central differences
+# ------------------------------------------------------------------------------------------
+
+def _small_problems():
+    import musr_inputs as mi
+    return [
+        mi.cfg1(nbins=700, bin_width_ns=11.0, seed=21, dtype=np.float64),
+        mi.cfg2(nhist=3, nbins=400, bin_width_ns=30.0, seed=22),
+        mi.cfg3(nhist=2, nbins=500, bin_width_ns=25.0, seed=23),
+        mi.cfg5(nhist=2, nbins=600, seed=24, n0=40.0, nbkg=0.5),
+        mi.paper_tf16(nhist=3, nbins=300, seed=25, n0=50.0),
+    ]
+
+
+@pytest.mark.parametrize("mode", [CHI2, MLE])
+def test_gradient_matches_complex_step(mode):
+    """Every component of the analytic gradient equals the complex-step derivative of the
+    value (same model, different differentiation).  Catches a wrong primitive derivative,
+    a wrong chain factor (2 pi / 360, sigma t^2, ...) and a map scatter to the wrong index."""
+    rng = np.random.default_rng(5)
+    for p in _small_problems():
+        x = p.truth * rng.uniform(0.9, 1.1, p.nparams)
+        v, g, gs, st = oracle.cost(p, x, mode)
+        assert st == 0
+        for i in range(p.nparams):
+            e = np.zeros(p.nparams)
+            e[i] = 1.0
+            cs = oracle.cost_cstep(p, x, e, mode)
+            assert abs(cs - g[i]) <= 1e-11 * gs[i] + 1e-300, (p.name, i, cs, g[i], gs[i])
+
+
+def test_gradient_matches_central_differences():
+    """Central differences of the value agree with the analytic gradient to FD accuracy."""
+    import musr_inputs as mi
+    p = mi.cfg3(nhist=2, nbins=300, bin_width_ns=40.0, seed=31)
+    x = p.truth * 1.05
+    for mode in (CHI2, MLE):
+        _, g, gs, _ = oracle.cost(p, x, mode)
+        for i in range(p.nparams):
+            h = 1e-6 * max(abs(x[i]), 1e-3)
+            xp, xm = x.copy(), x.copy()
+            xp[i] += h
+            xm[i] -= h
+            fd = (oracle.cost(p, xp, mode, grad=False)[0] - oracle.cost(p, xm, mode, grad=False)[0]) / (2 * h)
+            assert abs(fd - g[i]) <= 1e-6 * gs[i], (i, fd, g[i])
+
+
+# ------------------------------------------------------------------------------------------
+# The minimiser: optima known in closed form
+# ------------------------------------------------------------------------------------------
+
+def test_fit_constant_model_optima():
+    """The -2lnL optimum of a constant model is c = mean(d); the chi^2 optimum is the
+    weighted mean c = sum(d / w) / sum(1 / w), w = max(d, 1) (= n / sum(1 / w) when every
+    d >= 1).  Pins the minimiser and both gradients at the optimum."""
+    rng = np.random.default_rng(7)
+    d = rng.poisson(4.2, size=(2, 900)).astype(float)
+    p = _problem(d, [], [[0, 1], [0, 1]], 2, fit=(0.0, 1e9))
+    # parameter 0 (N0) is held at 0 through a constant in the map: map slot 0 -> const 0
+    p = Problem(p.counts, p.t0, p.bin_width_ns, p.fit_range_us, [], np.array([[-1, 0], [-1, 0]], np.int32),
+                np.array([0.0]), 1, np.zeros(1), ["c"])
+    r = oracle.fit(p, np.array([1.0]), MLE)
+    assert r["status"] == 0
+    assert r["x"][0] == pytest.approx(d.mean(), rel=1e-9)
+    r = oracle.fit(p, np.array([1.0]), CHI2)
+    assert r["status"] == 0
+    w = np.maximum(d, 1.0)
+    assert r["x"][0] == pytest.approx(np.sum(d / w) / np.sum(1.0 / w), rel=1e-9)
+
+
+def test_sigma_of_constant_model_is_poisson():
+    """At the -2lnL optimum of a constant model, sigma(c) = sqrt(c / n) (Poisson error of a mean)."""
+    rng = np.random.default_rng(8)
+    d = rng.poisson(6.0, size=(1, 2000)).astype(float)
+    p = Problem(d, np.zeros(1), 0.5, (0.0, 1e9), [], np.array([[-1, 0]], np.int32), np.array([0.0]), 1,
+                np.zeros(1), ["c"])
+    c = d.mean()
+    s = oracle.sigmas(p, np.array([c]), MLE)
+    assert s[0] == pytest.approx(math.sqrt(c / d.size), rel=1e-6)
+
+
+# ------------------------------------------------------------------------------------------
+# Parameter layout of the paper's benchmark
+# ------------------------------------------------------------------------------------------
+
+def test_paper_parameter_count_and_map_layout():
+    """Section 4: 16 positron detectors with Eq. asymmetry need 66 fit parameters
+    (tests/golden/paper_parameter_count.txt).  The configs' maps reference every
+    parameter exactly as laid out."""
+    import musr_inputs as mi
+    golden = {}
+    with open(__import__("os").path.join(__import__("os").path.dirname(__file__), "golden",
+                                         "paper_parameter_count.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                k, v = line.split("=")
+                golden[k.strip()] = int(v)
+    p = mi.paper_tf16(nbins=64)
+    assert p.H == golden["detectors"]
+    assert p.nparams == golden["parameters"] == 4 * p.H + 2
+    for cfg, H, P in ((mi.cfg1, 1, 6), (mi.cfg2, 8, 28), (mi.cfg3, 4, 11)):
+        q = cfg(nbins=64) if cfg is mi.cfg1 else cfg(nbins=64, nhist=H)
+        assert q.nparams == P
+        used = set(int(v) for v in q.map.ravel() if v >= 0)
+        assert used == set(range(P))
+    q = mi.cfg5(nhist=64, nbins=64)
+    assert q.nparams == 197
+    assert set(int(v) for v in q.map.ravel() if v >= 0) == set(range(197))
