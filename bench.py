@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark of the muSR fused value+gradient cost (arXiv 1509.07685, Section 4).
+
+Workload (one GPU): the global two-term TF fit -- 8 histograms x 65536 bins of
+0.1953125 ns, FP32 counts from the seeded event-level Monte Carlo, 28
+parameters -- evaluated with the fused value+analytic-gradient kernel in the
+FP32/FP64-split precision.  One step is one launch that evaluates a batch of
+64 parameter vectors (the trial points a fitter or a multi-start scan hands
+over at once): params in, 64 x (1 + 28) doubles out.  The L2 is flushed
+(a 512 MiB write) between timed steps.
+
+Printed JSON line (rank 0): value = (histogram, bin) pairs x vectors per
+second of device time (Gbins/s), measured with CUDA events on the launching
+stream; e2e = the same through the C ABI with host buffers (params H2D and
+results D2H inside the timed region); roofline of the fused kernel against
+the FP32 pipe; the plain FP64 path on the same batch; BFGS fits/s; the oracle
+timed on the host.
+
+``--impl reference`` times the FP64 CPU oracle instead (the reference arm).
+Multi-GPU (torchrun): each rank evaluates its own independent fits (weak
+scaling, no collective on the data path); timing is max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NVEC = 64
+FP32_LANES_PER_SM = 128
+# FP32-pipe operations per (histogram, bin) of the SPLIT fused value+gradient
+# evaluation of the two-term TF model (see the roofline section of the design notes).
+ALGO_FP32_OPS = {0: 37.0, 1: 58.0}
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", type=int, default=1, help="0 chi^2, 1 -2lnL")
+    ap.add_argument("--no-fits", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def _workload(rank: int):
+    import musr_inputs as mi
+    p = mi.cfg2(seed=2 + 1000 * rank)
+    X = mi.jitter(p.truth, NVEC, seed=1 + rank, lo=0.9, hi=1.1)
+    return p, X
+
+
+def _workload_desc(p, mode):
+    return {"workload": f"cfg2 global TF fit {p.H}x{p.B} FP32 counts, {p.nparams} params, "
+                        f"fused value+grad, {NVEC} param vectors per step",
+            "mode": "chi2" if mode == 0 else "mle", "nhist": p.H, "nbins": p.B,
+            "params": p.nparams, "vectors_per_step": NVEC, "l2": "flushed between steps (512 MiB write)"}
+
+
+# ---------------------------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------------
+# Reference arm: the FP64 CPU oracle
+# ---------------------------------------------------------------------------------------------
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    p, X = _workload(0)
+    bins = sum(1 for _ in range(0))  # placeholder to keep lints quiet
+    v, g, gs, st = oracle.cost(p, X[0], args.mode)  # warm the library
+    bins_per_eval = _bins_in_fit(p)
+    for w in range(args.warmup):
+        oracle.cost(p, X[w % NVEC], args.mode)
+    t = time.perf_counter()
+    for s in range(args.steps):
+        oracle.cost(p, X[s % NVEC], args.mode)
+    dt = (time.perf_counter() - t) / max(args.steps, 1)
+    val = bins_per_eval / dt / 1e9
+    del bins, v, g, gs, st
+    line = {"metric": "value+grad Gbins/s", "value": val, "unit": "Gbins/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": _workload_desc(p, args.mode) | {
+                "vectors_per_step": 1, "note": "each step: one value+grad evaluation by the oracle"},
+            "cpu_baseline": {"value": val, "unit": "Gbins/s", "cores": 1, "kind": "oracle",
+                             "sample": "one cfg2 value+grad evaluation per step (524288 bins)"},
+            "e2e": {"value": val, "unit": "Gbins/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _bins_in_fit(p):
+    dt = p.bin_width_ns / 1000.0
+    lo, hi = p.fit_range_us
+    n = np.arange(p.B)
+    tot = 0
+    for h in range(p.H):
+        t = (n - p.t0[h]) * dt
+        tot += int(np.count_nonzero((t >= lo) & (t <= hi)))
+    return tot
+
+
+def cpu_baseline(p, X, mode, budget_s=12.0):
+    """The oracle as it stands (single thread), on a bounded sample of the same workload."""
+    import oracle
+    bins = _bins_in_fit(p)
+    n = 0
+    t = time.perf_counter()
+    while True:
+        oracle.cost(p, X[n % len(X)], mode)
+        n += 1
+        if time.perf_counter() - t > budget_s or n >= 200:
+            break
+    dt = time.perf_counter() - t
+    return {"value": bins * n / dt / 1e9, "unit": "Gbins/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} value+grad evaluations of the cfg2 workload ({bins} bins each), single thread"}
+
+
+# ---------------------------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_1509_07685_gb300 import binding as B
+
+    B.load()
+    p, X = _workload(rank)
+    mode = args.mode
+    stream = torch.cuda.current_stream()
+    ctx = B.Context(p, device=local_rank, cuda_stream=stream.cuda_stream)
+    bins = ctx.bins_in_fit()
+    P = p.nparams
+    d_x = torch.tensor(X, dtype=torch.float64, device="cuda")
+    d_out = torch.empty((NVEC, 1 + P), dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step(prec):
+        B.musr_eval_device(ctx.ctx, d_x.data_ptr(), NVEC, mode, prec, True, d_out.data_ptr())
+
+    def timed(prec, steps, warmup):
+        for _ in range(warmup):
+            flush.zero_()
+            step(prec)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        times = []
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for s in range(steps):
+            flush.zero_()
+            ev[s][0].record(stream)
+            step(prec)
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        times = [a.elapsed_time(b) * 1e-3 for a, b in ev]
+        return times
+
+    # Main measurement (SPLIT), clocks sampled during it.
+    with ClockSampler(local_rank) as clk:
+        t_wall = time.perf_counter()
+        times = timed(B.MUSR_SPLIT, args.steps, max(args.warmup, 3))
+        t_wall = time.perf_counter() - t_wall
+    mean_t = float(np.mean(times))
+    if world > 1:
+        tt = torch.tensor([mean_t], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        mean_t = float(tt.item())
+    value = bins * NVEC * world / mean_t / 1e9
+    out_split = d_out.cpu().numpy().copy()
+
+    # Plain FP64 path on the same batch (fewer steps: it is slow).
+    t64 = timed(B.MUSR_FP64, max(3, min(args.steps, 5)), 2)
+    fp64_gbins = bins * NVEC / float(np.mean(t64)) / 1e9
+    out_fp64 = d_out.cpu().numpy().copy()
+    rel_err = float(np.max(np.abs(out_split[:, 0] - out_fp64[:, 0]) / np.abs(out_fp64[:, 0])))
+
+    # End to end through the C ABI with host buffers.
+    Xh = np.ascontiguousarray(X)
+    for _ in range(2):
+        ctx.eval_batch(Xh, mode, B.MUSR_SPLIT)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.eval_batch(Xh, mode, B.MUSR_SPLIT)
+    e2e_t = (time.perf_counter() - t) / args.steps
+    e2e = {"value": bins * NVEC / e2e_t / 1e9, "unit": "Gbins/s", "h2d_bytes_per_step": int(Xh.nbytes),
+           "d2h_bytes_per_step": int(NVEC * (1 + P) * 8),
+           "path": "musr_eval_batch (host params in, host value+grad out, synchronous)"}
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    clocks = clk.summary()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    nsm = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    peak_ops = nsm * FP32_LANES_PER_SM * sm_max * 1e6
+    ach_ops = ALGO_FP32_OPS[mode] * bins * NVEC / (mean_t if world == 1 else float(np.mean(times)))
+    roofline = {"bound": "alu", "achieved": ach_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                "frac": ach_ops / peak_ops, "traffic": None,
+                "kernel": "eval_kernel<SPLIT, TF2>", "pipe": "FP32 (FMA) lanes",
+                "peak_source": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz (max SM clock)",
+                "hbm_gbs_equiv": 4.0 * bins * NVEC / mean_t / 1e9,
+                "hbm_peak_gbs": peaks.get("hbm_gbs")}
+
+    fits = None
+    if not args.no_fits and rank == 0:
+        fits = _fits(p, ctx, B, mode)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(p, X, mode)
+
+    if rank == 0:
+        line = {"metric": "value+grad Gbins/s", "value": value, "unit": "Gbins/s", "n_gpus": world,
+                "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": mean_t * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64-split",
+                "data": "synthetic (seeded event-level Monte Carlo muSR histograms)",
+                "config": _workload_desc(p, mode) | {"parallelism": f"dp{world} (independent fits per rank)"},
+                "e2e": e2e, "roofline": roofline, "clocks": clocks,
+                "gpu_launches": args.steps, "wall_s_timed_region": t_wall,
+                "fp64_path": {"value": fp64_gbins, "unit": "Gbins/s", "split_speedup": value / world / fp64_gbins,
+                              "max_rel_value_diff_split_vs_fp64": rel_err},
+                "fits": fits, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _fits(p, ctx, B, mode):
+    """fits/s of the SPLIT path driven by the host BFGS, and the agreement with the FP64 fit."""
+    try:
+        from paper_1509_07685_gb300 import fit as F
+    except Exception:
+        return None
+    import musr_inputs as mi
+    out = []
+    lat = []
+    for s in range(4):
+        x0 = mi.start_point(p, 100 + s)
+        t = time.perf_counter()
+        r32 = F.fit_context(ctx, x0, mode, B.MUSR_SPLIT)
+        lat.append(time.perf_counter() - t)
+        out.append(r32)
+    r64 = F.fit_context(ctx, mi.start_point(p, 100), mode, B.MUSR_FP64)
+    sig = F.sigmas_context(ctx, r64["x"], mode)
+    dev = float(np.max(np.abs(out[0]["x"] - r64["x"]) / sig))
+    return {"fits_per_s": len(lat) / sum(lat), "latency_ms_p50": 1e3 * float(np.median(lat)),
+            "latency_ms_max": 1e3 * float(np.max(lat)), "evals_per_fit": float(np.mean([r["nfev"] for r in out])),
+            "max_param_dev_split_vs_fp64_sigma": dev, "fp64_fit_s": r64["time_s"]}
+
+
+def main():
+    args = _args()
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

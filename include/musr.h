@@ -1,0 +1,168 @@
+/*
+ * musr.h -- C ABI of libmusr, a GB300 (sm_103a) implementation of the muSR
+ * chi^2 / Poisson -2lnL cost and its analytic gradient (arXiv 1509.07685,
+ * Section 4 "Parameter Fitting with Minuit2").
+ *
+ * What the library evaluates (Section 4.1):
+ *   Eq. positron_histo   N_j(t) = N0_j exp(-t/tau_mu) [1 + A_j(p, t)] + Nbkg_j
+ *   Eq. chisq            chi^2  = sum_j sum_n (d - N)^2 / max(d, 1)
+ *   Eq. log-likelihood   -2lnL  = 2 sum_j sum_n [(N - d) + d ln(d/N)]  (d > 0)
+ *                                                [ N - d ]            (d <= 0)
+ *   Eq. asymmetry        A(t) = sum of terms, each a product of primitives
+ *                        AMP(a) = a, EXP(lambda) = exp(-lambda t),
+ *                        GAUSS(sigma) = exp(-(sigma t)^2 / 2),
+ *                        KT(Delta) = 1/3 + 2/3 (1 - Delta^2 t^2) exp(-Delta^2 t^2 / 2),
+ *                        TFCOS(nu, phi) = cos(2 pi (nu t + phi / 360)).
+ * Units: t in microseconds, rates in 1/us, nu in MHz, phi in degrees,
+ * tau_mu = 2.197019 us.  The time of bin n of histogram j is
+ * t_n = (n - t0_j) * (bin_width_ns / 1000.0); a bin is in the fit when
+ * fit_lo <= t_n <= fit_hi (closed range).  Local parameter slot 0 of every
+ * histogram is N0, slot 1 is Nbkg; terms reference any slot.
+ *
+ * As in the paper's offload (Section 4, "The DKS Implementation"), the
+ * histograms cross to the device once; per evaluation only the parameter
+ * vector goes in and (1 + P) doubles (value and gradient) come back.
+ *
+ * Conventions for every entry point:
+ *   - returns a musr_status (0 on success, negative on error); nothing is
+ *     thrown across the ABI; musr_last_error() describes the last failure;
+ *   - host arrays passed in are copied before the call returns, unless the
+ *     entry point says it borrows them; host output arrays are owned by the
+ *     caller;
+ *   - one musr_ctx is not thread-safe: use one per thread.
+ */
+#ifndef MUSR_H_
+#define MUSR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MUSR_OK = 0,
+  MUSR_EINVAL = -1,     /* invalid argument or inconsistent configuration */
+  MUSR_ENOMEM = -2,     /* host or device allocation failed, or HBM budget exceeded */
+  MUSR_ECUDA = -3,      /* a CUDA runtime call failed (see musr_last_error) */
+  MUSR_ENONFINITE = -4, /* -2lnL is +infinity: N <= 0 in a bin with d > 0 */
+  MUSR_ETIMEOUT = -5,   /* a bounded wait ran out */
+  MUSR_ESTATE = -6,     /* call order violated (e.g. eval before upload) */
+  MUSR_EAGAIN = -7      /* result not ready yet (serving poll) */
+} musr_status;
+
+enum { MUSR_DTYPE_INT32 = 0, MUSR_DTYPE_FP32 = 1, MUSR_DTYPE_FP64 = 2 };
+enum { MUSR_CHI2 = 0, MUSR_MLE = 1 };
+/* MUSR_FP64: every per-bin operation in FP64 (the plain path).
+ * MUSR_SPLIT: per-bin theory, residuals and gradient terms in FP32; FP64 for
+ * the phase range reduction of 2 pi (nu t + phi/360) and for every
+ * accumulation above the thread (block, grid, final sum). */
+enum { MUSR_FP64 = 0, MUSR_SPLIT = 1 };
+enum {
+  MUSR_PRIM_AMP = 1,
+  MUSR_PRIM_EXP = 2,
+  MUSR_PRIM_GAUSS = 3,
+  MUSR_PRIM_KT = 4,
+  MUSR_PRIM_TFCOS = 5 /* slot[0] = nu (MHz), slot[1] = phi (degrees) */
+};
+
+#define MUSR_MAX_PRIMS 4
+#define MUSR_MAX_TERMS 4
+#define MUSR_MAX_SLOTS 32
+#define MUSR_MAX_PARAMS 4096
+
+/* One term of A(t): the product of nprim primitives (Eq. asymmetry,
+ * generalised).  slot[m][0] (and slot[m][1] for TFCOS) are local slots. */
+typedef struct musr_term {
+  int32_t nprim;
+  int32_t kind[MUSR_MAX_PRIMS];
+  int32_t slot[MUSR_MAX_PRIMS][2];
+} musr_term;
+
+typedef struct musr_ctx musr_ctx;
+
+/* Creates a context on CUDA device `device`.  hbm_budget_bytes caps the
+ * device memory the context may allocate (0: no cap).  cuda_stream is a
+ * cudaStream_t to run on (e.g. torch.cuda.current_stream().cuda_stream), or
+ * NULL for a stream the context creates.  The context owns all memory it
+ * allocates; *out is NULL on failure.  (Section 2.1: memory handling and
+ * streams of the DKS communication layer.) */
+int musr_ctx_create(musr_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream);
+
+/* Frees everything the context owns.  NULL is ignored. */
+void musr_ctx_destroy(musr_ctx* ctx);
+
+/* Text of the last error on this context ("" if none).  ctx may be NULL for
+ * errors of musr_ctx_create.  The pointer stays valid until the next call. */
+const char* musr_last_error(const musr_ctx* ctx);
+
+/* Copies nhist histograms of nbins bins (host, row-major [nhist][nbins]) to
+ * the device, once (Section 4, "The DKS Implementation": measurement data
+ * go to the device at the beginning).  dtype is MUSR_DTYPE_INT32 (stored as
+ * FP32; |count| must be < 2^24 so the copy is exact), MUSR_DTYPE_FP32 or
+ * MUSR_DTYPE_FP64 (stored as FP64).  t0[nhist] is the time-zero bin of each
+ * histogram (may be fractional), bin_width_ns > 0, fit_range_us = {lo, hi}.
+ * Replaces any previous histograms; theory and map must be (re)set after. */
+int musr_upload_histograms(musr_ctx* ctx, const void* counts, int dtype, int nhist, int64_t nbins,
+                           const double* t0, double bin_width_ns, const double fit_range_us[2]);
+
+/* As musr_upload_histograms, but BORROWS device memory the caller owns
+ * (e.g. a torch tensor): d_counts points to [nhist][row_stride] FP32 or FP64
+ * values on the context's device, 16-byte aligned, row_stride a multiple of 4
+ * elements and >= nbins.  The memory must stay valid and unchanged until the
+ * histograms are replaced or the context is destroyed. */
+int musr_upload_histograms_device(musr_ctx* ctx, const void* d_counts, int dtype, int nhist,
+                                  int64_t nbins, int64_t row_stride, const double* t0,
+                                  double bin_width_ns, const double fit_range_us[2]);
+
+/* Sets A(t) as nterms (<= MUSR_MAX_TERMS) terms.  Every slot referenced must
+ * be < the nslots given to musr_set_map. */
+int musr_set_theory(musr_ctx* ctx, const musr_term* terms, int nterms);
+
+/* Sets the per-histogram parameter map (Section 4.1: the parameter set
+ * P_j = {N0_j, Nbkg_j, p_j} of each detector drawn from one global vector).
+ * map is [nhist][nslots] int32: entry m >= 0 takes global parameter m
+ * (< nparams); m < 0 takes consts[-1 - m] (< nconsts).  Requires histograms
+ * and theory.  nslots <= MUSR_MAX_SLOTS, nparams <= MUSR_MAX_PARAMS. */
+int musr_set_map(musr_ctx* ctx, const int32_t* map, int nslots, int nparams, const double* consts,
+                 int nconsts);
+
+/* Evaluates the cost (mode MUSR_CHI2: Eq. chisq; MUSR_MLE: Eq. log-likelihood)
+ * at params[nparams] (host) in the given precision.  *out_value receives the
+ * cost; out_grad[nparams] (host, may be NULL for value only) the analytic
+ * gradient.  Synchronous on the context's stream.  Returns MUSR_ENONFINITE
+ * (value +inf, grad zeros) when the likelihood is undefined. */
+int musr_eval(musr_ctx* ctx, const double* params, int nparams, int mode, int precision,
+              double* out_value, double* out_grad);
+
+/* nvec evaluations in one launch (e.g. trial points of a line search, or
+ * the random parameter vectors of a scan): params is host [nvec][nparams],
+ * out_values host [nvec], out_grads host [nvec][nparams] or NULL.  Returns
+ * MUSR_ENONFINITE if any vector's likelihood is undefined (its value is +inf). */
+int musr_eval_batch(musr_ctx* ctx, const double* params, int nvec, int nparams, int mode,
+                    int precision, double* out_values, double* out_grads);
+
+/* Device-resident variant for callers that keep everything in HBM (torch
+ * tensors): d_params is device [nvec][nparams] FP64, d_out device
+ * [nvec][1 + nparams] FP64 (value, then gradient; with_grad == 0 writes the
+ * value only).  Asynchronous: enqueued on the context's stream, nothing is
+ * copied or synchronised.  A +inf value marks an undefined likelihood. */
+int musr_eval_device(musr_ctx* ctx, const double* d_params, int nvec, int mode, int precision,
+                     int with_grad, double* d_out);
+
+/* Waits (bounded by timeout_ms, <= 0: no bound) for the context's stream. */
+int musr_sync(musr_ctx* ctx, int timeout_ms);
+
+/* Number of (histogram, bin) pairs inside the fit range. */
+int musr_bins_in_fit(musr_ctx* ctx, int64_t* out);
+
+/* Number of kernel launches one musr_eval/musr_eval_batch/musr_eval_device
+ * call makes (for launch accounting). */
+int musr_launches_per_eval(musr_ctx* ctx, int* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MUSR_H_ */

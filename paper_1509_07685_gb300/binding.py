@@ -1,0 +1,277 @@
+"""Thin ctypes binding of libmusr (``include/musr.h``): argument marshalling only.
+
+Every function named ``musr_*`` here calls the C entry point of the same name;
+all arithmetic of the cost runs in the library's CUDA kernels.  The library is
+built in-tree (``paper_1509_07685_gb300/libmusr.so``) by ``build.py``; if it
+is missing, :func:`load` raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libmusr.so")
+
+MUSR_OK, MUSR_EINVAL, MUSR_ENOMEM, MUSR_ECUDA = 0, -1, -2, -3
+MUSR_ENONFINITE, MUSR_ETIMEOUT, MUSR_ESTATE, MUSR_EAGAIN = -4, -5, -6, -7
+MUSR_DTYPE_INT32, MUSR_DTYPE_FP32, MUSR_DTYPE_FP64 = 0, 1, 2
+MUSR_CHI2, MUSR_MLE = 0, 1
+MUSR_FP64, MUSR_SPLIT = 0, 1
+PRIM = {"AMP": 1, "EXP": 2, "GAUSS": 3, "KT": 4, "TFCOS": 5}
+MAX_PRIMS = 4
+
+# Every symbol include/musr.h declares (checked by the ABI test).
+EXPORTS = (
+    "musr_ctx_create", "musr_ctx_destroy", "musr_last_error", "musr_upload_histograms",
+    "musr_upload_histograms_device", "musr_set_theory", "musr_set_map", "musr_eval",
+    "musr_eval_batch", "musr_eval_device", "musr_sync", "musr_bins_in_fit",
+    "musr_launches_per_eval",
+)
+
+
+class MusrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libmusr status {status}: {msg}")
+        self.status = status
+
+
+class musr_term(ctypes.Structure):
+    _fields_ = [("nprim", ctypes.c_int32), ("kind", ctypes.c_int32 * MAX_PRIMS),
+                ("slot", (ctypes.c_int32 * 2) * MAX_PRIMS)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _declare(lib):
+    P = ctypes.POINTER
+    vp, d, i32, i64 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "musr_ctx_create": ([P(vp), ctypes.c_int, ctypes.c_size_t, vp], ctypes.c_int),
+        "musr_ctx_destroy": ([vp], None),
+        "musr_last_error": ([vp], ctypes.c_char_p),
+        "musr_upload_histograms": ([vp, vp, ctypes.c_int, ctypes.c_int, i64, P(d), d, P(d)], ctypes.c_int),
+        "musr_upload_histograms_device": ([vp, vp, ctypes.c_int, ctypes.c_int, i64, i64, P(d), d, P(d)],
+                                          ctypes.c_int),
+        "musr_set_theory": ([vp, P(musr_term), ctypes.c_int], ctypes.c_int),
+        "musr_set_map": ([vp, P(i32), ctypes.c_int, ctypes.c_int, P(d), ctypes.c_int], ctypes.c_int),
+        "musr_eval": ([vp, P(d), ctypes.c_int, ctypes.c_int, ctypes.c_int, P(d), P(d)], ctypes.c_int),
+        "musr_eval_batch": ([vp, P(d), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(d), P(d)],
+                            ctypes.c_int),
+        "musr_eval_device": ([vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp], ctypes.c_int),
+        "musr_sync": ([vp, ctypes.c_int], ctypes.c_int),
+        "musr_bins_in_fit": ([vp, P(i64)], ctypes.c_int),
+        "musr_launches_per_eval": ([vp, P(ctypes.c_int)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+
+
+def load():
+    """The loaded libmusr; raises if the library has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build() "
+                                   "(there is no CPU fallback)")
+            lib = ctypes.CDLL(LIB_PATH)
+            _declare(lib)
+            _lib = lib
+    return _lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _err(ctx, status: int):
+    msg = load().musr_last_error(ctx)
+    raise MusrError(status, msg.decode() if msg else "")
+
+
+def _check(ctx, status: int):
+    if status != MUSR_OK:
+        _err(ctx, status)
+
+
+def terms_to_c(terms) -> Tuple[ctypes.Array, int]:
+    """Term list [[(kind, slots), ...], ...] -> musr_term array."""
+    n = len(terms)
+    arr = (musr_term * max(n, 1))()
+    for k, term in enumerate(terms):
+        if len(term) > MAX_PRIMS:
+            raise ValueError("a term holds at most 4 primitives")
+        arr[k].nprim = len(term)
+        for m, (kind, slots) in enumerate(term):
+            arr[k].kind[m] = PRIM[kind]
+            for q, s in enumerate(slots):
+                arr[k].slot[m][q] = int(s)
+    return arr, n
+
+
+# --------------------------------------------------------------------------------------------
+# Functions with the C names
+# --------------------------------------------------------------------------------------------
+
+def musr_ctx_create(device: int = 0, hbm_budget_bytes: int = 0, cuda_stream: Optional[int] = None):
+    lib = load()
+    out = ctypes.c_void_p()
+    st = lib.musr_ctx_create(ctypes.byref(out), device, hbm_budget_bytes,
+                             ctypes.c_void_p(cuda_stream) if cuda_stream else None)
+    if st != MUSR_OK:
+        raise MusrError(st, (lib.musr_last_error(None) or b"").decode())
+    return out
+
+
+def musr_ctx_destroy(ctx) -> None:
+    load().musr_ctx_destroy(ctx)
+
+
+def musr_last_error(ctx) -> str:
+    msg = load().musr_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def musr_upload_histograms(ctx, counts: np.ndarray, t0: Sequence[float], bin_width_ns: float,
+                           fit_range_us: Sequence[float]) -> None:
+    counts = np.ascontiguousarray(counts)
+    if counts.ndim != 2:
+        raise ValueError("counts must be [nhist][nbins]")
+    dtype = {np.dtype(np.int32): MUSR_DTYPE_INT32, np.dtype(np.float32): MUSR_DTYPE_FP32,
+             np.dtype(np.float64): MUSR_DTYPE_FP64}.get(counts.dtype)
+    if dtype is None:
+        raise TypeError("counts must be int32, float32 or float64")
+    t0 = np.ascontiguousarray(t0, dtype=np.float64)
+    fr = np.ascontiguousarray(fit_range_us, dtype=np.float64)
+    _check(ctx, load().musr_upload_histograms(ctx, counts.ctypes.data_as(ctypes.c_void_p), dtype,
+                                              counts.shape[0], counts.shape[1], _dptr(t0),
+                                              float(bin_width_ns), _dptr(fr)))
+
+
+def musr_upload_histograms_device(ctx, d_counts: int, dtype: int, nhist: int, nbins: int, row_stride: int,
+                                  t0: Sequence[float], bin_width_ns: float,
+                                  fit_range_us: Sequence[float]) -> None:
+    t0 = np.ascontiguousarray(t0, dtype=np.float64)
+    fr = np.ascontiguousarray(fit_range_us, dtype=np.float64)
+    _check(ctx, load().musr_upload_histograms_device(ctx, ctypes.c_void_p(d_counts), dtype, nhist, nbins,
+                                                     row_stride, _dptr(t0), float(bin_width_ns), _dptr(fr)))
+
+
+def musr_set_theory(ctx, terms) -> None:
+    arr, n = terms_to_c(terms)
+    _check(ctx, load().musr_set_theory(ctx, arr, n))
+
+
+def musr_set_map(ctx, mp: np.ndarray, nparams: int, consts: Sequence[float] = ()) -> None:
+    mp = np.ascontiguousarray(mp, dtype=np.int32)
+    c = np.ascontiguousarray(consts if len(consts) else np.zeros(1), dtype=np.float64)
+    _check(ctx, load().musr_set_map(ctx, mp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), mp.shape[1],
+                                    int(nparams), _dptr(c), len(consts)))
+
+
+def musr_eval(ctx, params: np.ndarray, mode: int, precision: int, grad: bool = True):
+    """(value, grad or None, status); status is MUSR_OK or MUSR_ENONFINITE (value +inf)."""
+    x = np.ascontiguousarray(params, dtype=np.float64)
+    v = ctypes.c_double()
+    g = np.zeros(x.size) if grad else None
+    st = load().musr_eval(ctx, _dptr(x), x.size, mode, precision, ctypes.byref(v),
+                          _dptr(g) if grad else None)
+    if st not in (MUSR_OK, MUSR_ENONFINITE):
+        _err(ctx, st)
+    return v.value, g, st
+
+
+def musr_eval_batch(ctx, params: np.ndarray, mode: int, precision: int, grad: bool = True):
+    """(values[nvec], grads[nvec][P] or None, status)."""
+    x = np.ascontiguousarray(np.atleast_2d(params), dtype=np.float64)
+    nvec, P = x.shape
+    vals = np.zeros(nvec)
+    g = np.zeros((nvec, P)) if grad else None
+    st = load().musr_eval_batch(ctx, _dptr(x), nvec, P, mode, precision, _dptr(vals),
+                                _dptr(g) if grad else None)
+    if st not in (MUSR_OK, MUSR_ENONFINITE):
+        _err(ctx, st)
+    return vals, g, st
+
+
+def musr_eval_device(ctx, d_params: int, nvec: int, mode: int, precision: int, with_grad: bool,
+                     d_out: int) -> None:
+    _check(ctx, load().musr_eval_device(ctx, ctypes.c_void_p(d_params), nvec, mode, precision,
+                                        int(bool(with_grad)), ctypes.c_void_p(d_out)))
+
+
+def musr_sync(ctx, timeout_ms: int = 0) -> None:
+    _check(ctx, load().musr_sync(ctx, timeout_ms))
+
+
+def musr_bins_in_fit(ctx) -> int:
+    out = ctypes.c_int64()
+    _check(ctx, load().musr_bins_in_fit(ctx, ctypes.byref(out)))
+    return out.value
+
+
+def musr_launches_per_eval(ctx) -> int:
+    out = ctypes.c_int()
+    _check(ctx, load().musr_launches_per_eval(ctx, ctypes.byref(out)))
+    return out.value
+
+
+# --------------------------------------------------------------------------------------------
+# Convenience owner object
+# --------------------------------------------------------------------------------------------
+
+class Context:
+    """Owns one musr_ctx configured for one problem (histograms, theory, map).
+
+    ``problem`` needs: counts [H][B], t0 [H], bin_width_ns, fit_range_us, terms,
+    map [H][nslots], consts, nparams.
+    """
+
+    def __init__(self, problem=None, device: int = 0, hbm_budget_bytes: int = 0,
+                 cuda_stream: Optional[int] = None):
+        self.ctx = musr_ctx_create(device, hbm_budget_bytes, cuda_stream)
+        self.P = None
+        if problem is not None:
+            self.configure(problem)
+
+    def configure(self, problem) -> None:
+        musr_upload_histograms(self.ctx, problem.counts, problem.t0, problem.bin_width_ns,
+                               problem.fit_range_us)
+        musr_set_theory(self.ctx, problem.terms)
+        musr_set_map(self.ctx, problem.map, problem.nparams, problem.consts)
+        self.P = int(problem.nparams)
+
+    def eval(self, x, mode=MUSR_CHI2, precision=MUSR_FP64, grad=True):
+        return musr_eval(self.ctx, x, mode, precision, grad)
+
+    def eval_batch(self, X, mode=MUSR_CHI2, precision=MUSR_FP64, grad=True):
+        return musr_eval_batch(self.ctx, X, mode, precision, grad)
+
+    def bins_in_fit(self) -> int:
+        return musr_bins_in_fit(self.ctx)
+
+    def close(self) -> None:
+        if self.ctx:
+            musr_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,829 @@
+// musr_ctx.cpp -- host side of the libmusr C ABI (include/musr.h).
+//
+// The context owns the device copies of the histograms (uploaded once, as the
+// offload of Section 4 does), the compiled theory/map of each precision (work
+// decomposition, finalize tables) and the per-evaluation buffers.  Every step
+// of the cost runs in the kernels of musr_kernels.cu; this file validates
+// arguments, lays out memory, builds the work decomposition and launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "musr.h"
+#include "musr_dev.h"
+#include "musr_host.h"
+
+using musr::Chunk;
+using musr::HistSet;
+using musr::Job;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr int64_t kRowAlign = 64;  // elements: rows start on 256-byte boundaries (FP32)
+
+}  // namespace
+
+namespace musr {
+
+int fail(musr_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int cuda_fail(musr_ctx* ctx, cudaError_t e, const char* what) {
+  return fail(ctx, MUSR_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int dalloc(musr_ctx* ctx, DevBuf& b, size_t bytes) {
+  dfree(ctx, b);
+  if (bytes == 0) bytes = 16;
+  if (ctx->budget && ctx->used + bytes > ctx->budget)
+    return fail(ctx, MUSR_ENOMEM, "device memory budget exceeded (" + std::to_string(ctx->used + bytes) +
+                                      " > " + std::to_string(ctx->budget) + " bytes)");
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    cudaGetLastError();
+    return fail(ctx, MUSR_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  b.bytes = bytes;
+  ctx->used += bytes;
+  return MUSR_OK;
+}
+
+void dfree(musr_ctx* ctx, DevBuf& b) {
+  if (b.p) {
+    cudaFree(b.p);
+    ctx->used -= b.bytes;
+  }
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+int upload(musr_ctx* ctx, DevBuf& b, const void* src, size_t bytes) {
+  int rc = dalloc(ctx, b, bytes);
+  if (rc) return rc;
+  if (bytes) {
+    cudaError_t e = cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy");
+  }
+  return MUSR_OK;
+}
+
+DeviceScope::DeviceScope(int dev) {
+  cudaGetDevice(&prev_);
+  if (prev_ != dev) cudaSetDevice(dev);
+}
+DeviceScope::~DeviceScope() {
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != prev_) cudaSetDevice(prev_);
+}
+
+// Bins [nlo, nhi) of a histogram whose times t_n = (n - t0) * dt satisfy lo <= t_n <= hi.
+void fit_bins(double t0, double dt_us, int64_t B, double lo, double hi, int* nlo, int* nhi) {
+  auto tn = [&](int64_t n) { return (static_cast<double>(n) - t0) * dt_us; };
+  auto first_at_least = [&](double v) -> int64_t {  // first n with t_n >= v
+    double est = std::ceil(v / dt_us + t0);
+    int64_t n = est < 0 ? 0 : (est > static_cast<double>(B) ? B : static_cast<int64_t>(est));
+    while (n > 0 && tn(n - 1) >= v) --n;
+    while (n < B && tn(n) < v) ++n;
+    return n;
+  };
+  auto first_above = [&](double v) -> int64_t {  // first n with t_n > v
+    double est = std::floor(v / dt_us + t0) + 1.0;
+    int64_t n = est < 0 ? 0 : (est > static_cast<double>(B) ? B : static_cast<int64_t>(est));
+    while (n > 0 && tn(n - 1) > v) --n;
+    while (n < B && tn(n) <= v) ++n;
+    return n;
+  };
+  int64_t a = first_at_least(lo), b = first_above(hi);
+  if (b < a) b = a;
+  *nlo = static_cast<int>(a);
+  *nhi = static_cast<int>(b);
+}
+
+void free_compiled(musr_ctx* ctx, Compiled& c) {
+  dfree(ctx, c.d_hs);
+  dfree(ctx, c.chunks);
+  dfree(ctx, c.items);
+  dfree(ctx, c.hist_index);
+  dfree(ctx, c.col_chunk);
+  dfree(ctx, c.p_ptr);
+  dfree(ctx, c.p_cols);
+  c.valid = false;
+  c.reason.clear();
+}
+
+// Canonical form of one term for the SPLIT kernels; false if the term is not
+// of the form a * exp(-Lambda t - S t^2/2) * [KT or TFCOS].
+static bool canonical(const musr_term& t, CanonTerm* ct, std::string* why) {
+  std::memset(ct, 0, sizeof(*ct));
+  ct->amp_slot = ct->kt_slot = ct->nu_slot = ct->phi_slot = -1;
+  int namp = 0, nkt = 0, ntf = 0;
+  for (int m = 0; m < t.nprim; ++m) {
+    switch (t.kind[m]) {
+      case MUSR_PRIM_AMP:
+        ct->amp_slot = t.slot[m][0];
+        ++namp;
+        break;
+      case MUSR_PRIM_EXP:
+        ct->exp_slot[ct->nexp++] = t.slot[m][0];
+        break;
+      case MUSR_PRIM_GAUSS:
+        ct->gauss_slot[ct->ngauss++] = t.slot[m][0];
+        break;
+      case MUSR_PRIM_KT:
+        ct->kt_slot = t.slot[m][0];
+        ++nkt;
+        break;
+      case MUSR_PRIM_TFCOS:
+        ct->nu_slot = t.slot[m][0];
+        ct->phi_slot = t.slot[m][1];
+        ++ntf;
+        break;
+    }
+  }
+  if (namp > 1 || nkt > 1 || ntf > 1 || (nkt && ntf)) {
+    *why = "SPLIT precision needs every term to hold at most one AMP, and at most one of KT or TFCOS";
+    return false;
+  }
+  ct->kind = ntf ? musr::kTermTF : (nkt ? musr::kTermKT : musr::kTermPlain);
+  return true;
+}
+
+static int pick_iters(const std::vector<int64_t>& ranges, int per_iter, int target_items) {
+  for (int it : {8, 4, 2}) {
+    int64_t T = static_cast<int64_t>(per_iter) * it, n = 0;
+    for (int64_t r : ranges) n += (r + T - 1) / T;
+    if (n >= target_items) return it;
+  }
+  return 1;
+}
+
+// Builds the decomposition and finalize tables of one precision.
+int compile(musr_ctx* ctx, int prec) {
+  Compiled& c = ctx->comp[prec];
+  free_compiled(ctx, c);
+  HistSet hs;
+  std::memset(&hs, 0, sizeof(hs));
+  hs.counts = ctx->d_counts;
+  hs.store = ctx->store;
+  hs.H = ctx->H;
+  hs.stride = ctx->stride;
+  hs.dt_us = ctx->dt_us;
+  hs.nterms = static_cast<int>(ctx->terms.size());
+  hs.map = static_cast<const int32_t*>(ctx->d_map.p);
+  hs.nslots = ctx->nslots;
+  hs.consts = static_cast<const double*>(ctx->d_consts.p);
+  hs.P = ctx->P;
+  for (int k = 0; k < hs.nterms; ++k) {
+    const musr_term& t = ctx->terms[k];
+    hs.raw[k].nprim = t.nprim;
+    for (int m = 0; m < musr::kMaxPrims; ++m) {
+      hs.raw[k].kind[m] = m < t.nprim ? t.kind[m] : 0;
+      hs.raw[k].slot[m][0] = m < t.nprim ? t.slot[m][0] : 0;
+      hs.raw[k].slot[m][1] = m < t.nprim && t.kind[m] == MUSR_PRIM_TFCOS ? t.slot[m][1] : 0;
+    }
+  }
+  const int H = ctx->H;
+  std::vector<std::vector<int>> groups;
+  int group_cap = 1;
+  if (prec == MUSR_SPLIT) {
+    for (int k = 0; k < hs.nterms; ++k) {
+      std::string why;
+      if (!canonical(ctx->terms[k], &hs.canon[k], &why)) {
+        c.reason = why;
+        return MUSR_OK;  // SPLIT unavailable for this theory; FP64 still is
+      }
+    }
+    // Shape of the term list.
+    std::vector<int> kinds;
+    for (int k = 0; k < hs.nterms; ++k) kinds.push_back(hs.canon[k].kind);
+    using musr::kTermKT;
+    using musr::kTermTF;
+    if (kinds == std::vector<int>{kTermTF})
+      hs.shape = musr::kShapeTF1;
+    else if (kinds == std::vector<int>{kTermTF, kTermTF})
+      hs.shape = musr::kShapeTF2;
+    else if (kinds == std::vector<int>{kTermKT})
+      hs.shape = musr::kShapeKT1;
+    else if (kinds == std::vector<int>{kTermTF, kTermTF, kTermKT})
+      hs.shape = musr::kShapeTF2KT1;
+    else
+      hs.shape = musr::kShapeGeneric;
+    group_cap = musr::shape_group(hs.shape);
+    // Slot -> channel contributions.
+    auto add = [&](int slot, int kind, int term) {
+      hs.contrib[hs.ncontrib].slot = slot;
+      hs.contrib[hs.ncontrib].kind = kind;
+      hs.contrib[hs.ncontrib].term = term;
+      ++hs.ncontrib;
+    };
+    add(0, musr::kCN0, 0);
+    add(1, musr::kCBkg, 0);
+    for (int k = 0; k < hs.nterms; ++k) {
+      const CanonTerm& ct = hs.canon[k];
+      if (ct.amp_slot >= 0) add(ct.amp_slot, musr::kCAmp, k);
+      for (int i = 0; i < ct.nexp; ++i) add(ct.exp_slot[i], musr::kCLam, k);
+      for (int i = 0; i < ct.ngauss; ++i) add(ct.gauss_slot[i], musr::kCSig, k);
+      if (ct.kind == musr::kTermKT) add(ct.kt_slot, musr::kCDel, k);
+      if (ct.kind == musr::kTermTF) {
+        add(ct.nu_slot, musr::kCNu, k);
+        add(ct.phi_slot, musr::kCPhi, k);
+      }
+    }
+    // Group histograms that share t0 and every time-dependent parameter.
+    std::map<std::vector<int64_t>, int> key_to_group;
+    // A slot's identity across histograms: the global parameter, or the constant's value.
+    auto push_entry = [&](std::vector<int64_t>& key, int h, int s) {
+      const int32_t m = ctx->map[static_cast<size_t>(h) * ctx->nslots + s];
+      if (m >= 0) {
+        key.push_back(0);
+        key.push_back(m);
+      } else {
+        const double v = ctx->consts[-1 - m];
+        int64_t bits;
+        std::memcpy(&bits, &v, sizeof(bits));
+        key.push_back(1);
+        key.push_back(bits);
+      }
+    };
+    for (int h = 0; h < H; ++h) {
+      std::vector<int64_t> key;
+      int64_t tb;
+      std::memcpy(&tb, &ctx->t0[h], sizeof(tb));
+      key.push_back(tb);
+      for (int k = 0; k < hs.nterms; ++k) {
+        const CanonTerm& ct = hs.canon[k];
+        for (int i = 0; i < ct.nexp; ++i) push_entry(key, h, ct.exp_slot[i]);
+        for (int i = 0; i < ct.ngauss; ++i) push_entry(key, h, ct.gauss_slot[i]);
+        if (ct.kind == musr::kTermKT) push_entry(key, h, ct.kt_slot);
+        if (ct.kind == musr::kTermTF) push_entry(key, h, ct.nu_slot);
+      }
+      auto it = key_to_group.find(key);
+      if (it == key_to_group.end()) {
+        key_to_group.emplace(key, static_cast<int>(groups.size()));
+        groups.push_back({h});
+      } else {
+        groups[it->second].push_back(h);
+      }
+    }
+  } else {
+    for (int h = 0; h < H; ++h) groups.push_back({h});
+  }
+  // Chunks of at most group_cap histograms.
+  std::vector<Chunk> chunks;
+  std::vector<int> hist_index;
+  for (const auto& g : groups)
+    for (size_t i = 0; i < g.size(); i += group_cap) {
+      Chunk ch;
+      std::memset(&ch, 0, sizeof(ch));
+      ch.first = static_cast<int>(hist_index.size());
+      ch.nh = static_cast<int>(std::min<size_t>(group_cap, g.size() - i));
+      for (int j = 0; j < ch.nh; ++j) hist_index.push_back(g[i + j]);
+      ch.nlo = ctx->nlo[g[i]];
+      ch.nhi = ctx->nhi[g[i]];
+      ch.t0 = ctx->t0[g[i]];
+      ch.tile0 = ch.nlo & ~3;
+      chunks.push_back(ch);
+    }
+  // Tiles.
+  const int per_iter = prec == MUSR_SPLIT ? musr::kBlock * musr::kBinsPerThread : musr::kBlock;
+  std::vector<int64_t> ranges;
+  for (const auto& ch : chunks) ranges.push_back(ch.nhi > ch.nlo ? ch.nhi - ch.tile0 : 0);
+  const int iters = pick_iters(ranges, per_iter, 4 * ctx->num_sms);
+  hs.tile_bins = per_iter * iters;
+  std::vector<int2> items;
+  int col = 0;
+  for (size_t ci = 0; ci < chunks.size(); ++ci) {
+    Chunk& ch = chunks[ci];
+    ch.item0 = static_cast<int>(items.size());
+    ch.ntiles = static_cast<int>((ranges[ci] + hs.tile_bins - 1) / hs.tile_bins);
+    for (int t = 0; t < ch.ntiles; ++t) items.push_back(make_int2(static_cast<int>(ci), t));
+    ch.col0 = col;
+    col += ch.nh * ctx->nslots;
+  }
+  hs.group = group_cap;
+  hs.pstride = 1 + group_cap * ctx->nslots;
+  hs.ncols = col;
+  hs.nchunks = static_cast<int>(chunks.size());
+  hs.nitems = static_cast<int>(items.size());
+  std::vector<int> col_chunk(std::max(col, 1));
+  std::vector<std::vector<int>> pcols(ctx->P);
+  for (size_t ci = 0; ci < chunks.size(); ++ci) {
+    const Chunk& ch = chunks[ci];
+    for (int hl = 0; hl < ch.nh; ++hl) {
+      const int h = hist_index[ch.first + hl];
+      for (int s = 0; s < ctx->nslots; ++s) {
+        const int cc = ch.col0 + hl * ctx->nslots + s;
+        col_chunk[cc] = static_cast<int>(ci);
+        const int32_t m = ctx->map[static_cast<size_t>(h) * ctx->nslots + s];
+        if (m >= 0) pcols[m].push_back(cc);
+      }
+    }
+  }
+  std::vector<int> p_ptr(ctx->P + 1, 0), p_cols;
+  for (int p = 0; p < ctx->P; ++p) {
+    p_ptr[p] = static_cast<int>(p_cols.size());
+    p_cols.insert(p_cols.end(), pcols[p].begin(), pcols[p].end());
+  }
+  p_ptr[ctx->P] = static_cast<int>(p_cols.size());
+  if (p_cols.empty()) p_cols.push_back(0);
+  int rc;
+  if ((rc = upload(ctx, c.chunks, chunks.data(), sizeof(Chunk) * chunks.size()))) return rc;
+  if ((rc = upload(ctx, c.items, items.data(), sizeof(int2) * items.size()))) return rc;
+  if ((rc = upload(ctx, c.hist_index, hist_index.data(), sizeof(int) * hist_index.size()))) return rc;
+  if ((rc = upload(ctx, c.col_chunk, col_chunk.data(), sizeof(int) * col_chunk.size()))) return rc;
+  if ((rc = upload(ctx, c.p_ptr, p_ptr.data(), sizeof(int) * p_ptr.size()))) return rc;
+  if ((rc = upload(ctx, c.p_cols, p_cols.data(), sizeof(int) * p_cols.size()))) return rc;
+  hs.chunks = static_cast<const Chunk*>(c.chunks.p);
+  hs.items = static_cast<const int2*>(c.items.p);
+  hs.hist_index = static_cast<const int*>(c.hist_index.p);
+  hs.col_chunk = static_cast<const int*>(c.col_chunk.p);
+  hs.p_ptr = static_cast<const int*>(c.p_ptr.p);
+  hs.p_cols = static_cast<const int*>(c.p_cols.p);
+  if ((rc = upload(ctx, c.d_hs, &hs, sizeof(hs)))) return rc;
+  c.hs = hs;
+  c.valid = true;
+  return MUSR_OK;
+}
+
+void invalidate_eval(musr_ctx* ctx) { ctx->ev.key_valid = false; }
+
+// Buffers for nvec evaluations at precision prec; rebuilds the job table when
+// the launch's key (precision, mode, grad, nvec, pointers) changes.
+int prepare_jobs(musr_ctx* ctx, int prec, int mode, int grad, int nvec, const double* d_params,
+                 double* d_out) {
+  EvalBufs& ev = ctx->ev;
+  const HistSet& hs = ctx->comp[prec].hs;
+  const size_t part = static_cast<size_t>(nvec) * hs.nitems * hs.pstride;
+  const size_t cols = static_cast<size_t>(nvec) * std::max(hs.ncols, 1);
+  int rc;
+  if (ev.partials.bytes < part * sizeof(double)) {
+    if ((rc = dalloc(ctx, ev.partials, part * sizeof(double)))) return rc;
+    ev.key_valid = false;
+  }
+  if (ev.colsum.bytes < cols * sizeof(double)) {
+    if ((rc = dalloc(ctx, ev.colsum, cols * sizeof(double)))) return rc;
+    ev.key_valid = false;
+  }
+  if (ev.counters.bytes < nvec * sizeof(unsigned)) {
+    if ((rc = dalloc(ctx, ev.counters, nvec * sizeof(unsigned)))) return rc;
+    cudaError_t e = cudaMemsetAsync(ev.counters.p, 0, ev.counters.bytes, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
+    ev.key_valid = false;
+  }
+  if (ev.jobs.bytes < nvec * sizeof(Job)) {
+    if ((rc = dalloc(ctx, ev.jobs, nvec * sizeof(Job)))) return rc;
+    ev.key_valid = false;
+  }
+  if (ev.key_valid && ev.k_prec == prec && ev.k_mode == mode && ev.k_grad == grad &&
+      ev.k_nvec == nvec && ev.k_params == d_params && ev.k_out == d_out)
+    return MUSR_OK;
+  std::vector<Job> jobs(nvec);
+  const HistSet* d_hs = static_cast<const HistSet*>(ctx->comp[prec].d_hs.p);
+  for (int v = 0; v < nvec; ++v) {
+    Job& j = jobs[v];
+    std::memset(&j, 0, sizeof(j));
+    j.hs = d_hs;
+    j.params = d_params + static_cast<size_t>(v) * ctx->P;
+    j.out = d_out + static_cast<size_t>(v) * (1 + ctx->P);
+    j.partials = static_cast<double*>(ev.partials.p) + static_cast<size_t>(v) * hs.nitems * hs.pstride;
+    j.colsum = static_cast<double*>(ev.colsum.p) + static_cast<size_t>(v) * std::max(hs.ncols, 1);
+    j.counter = static_cast<unsigned*>(ev.counters.p) + v;
+    j.item_begin = v * hs.nitems;
+    j.mode = mode;
+    j.grad = grad;
+  }
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+  e = cudaMemcpy(ev.jobs.p, jobs.data(), sizeof(Job) * nvec, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy(jobs)");
+  ev.key_valid = true;
+  ev.k_prec = prec;
+  ev.k_mode = mode;
+  ev.k_grad = grad;
+  ev.k_nvec = nvec;
+  ev.k_params = d_params;
+  ev.k_out = d_out;
+  return MUSR_OK;
+}
+
+int check_ready(musr_ctx* ctx, int mode, int prec) {
+  if (!ctx->have_hist) return fail(ctx, MUSR_ESTATE, "no histograms uploaded");
+  if (!ctx->have_theory) return fail(ctx, MUSR_ESTATE, "no theory set");
+  if (!ctx->have_map) return fail(ctx, MUSR_ESTATE, "no parameter map set");
+  if (mode != MUSR_CHI2 && mode != MUSR_MLE) return fail(ctx, MUSR_EINVAL, "mode must be MUSR_CHI2 or MUSR_MLE");
+  if (prec != MUSR_FP64 && prec != MUSR_SPLIT)
+    return fail(ctx, MUSR_EINVAL, "precision must be MUSR_FP64 or MUSR_SPLIT");
+  if (!ctx->comp[prec].valid)
+    return fail(ctx, MUSR_EINVAL, "precision unavailable for this theory: " + ctx->comp[prec].reason);
+  return MUSR_OK;
+}
+
+// Enqueues one launch of nvec evaluations reading d_params, writing d_out.
+int enqueue_eval(musr_ctx* ctx, int prec, int mode, int grad, int nvec, const double* d_params,
+                 double* d_out) {
+  const HistSet& hs = ctx->comp[prec].hs;
+  if (hs.nitems == 0) {  // no bin in the fit range: cost 0, gradient 0
+    cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(double) * nvec * (1 + ctx->P), ctx->stream);
+    return e == cudaSuccess ? MUSR_OK : cuda_fail(ctx, e, "cudaMemsetAsync");
+  }
+  int rc = prepare_jobs(ctx, prec, mode, grad, nvec, d_params, d_out);
+  if (rc) return rc;
+  musr::LaunchInfo info;
+  if (musr::launch_eval(prec, hs.shape, mode, grad, static_cast<const Job*>(ctx->ev.jobs.p), nvec,
+                        nvec * hs.nitems, ctx->num_sms, ctx->stream, &info)) {
+    cudaError_t e = cudaGetLastError();
+    ctx->ev.key_valid = false;
+    return cuda_fail(ctx, e, "kernel launch");
+  }
+  ctx->last_grid = info.grid;
+  return MUSR_OK;
+}
+
+int wait_stream(musr_ctx* ctx, int timeout_ms) {
+  if (timeout_ms <= 0) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? MUSR_OK : cuda_fail(ctx, e, "cudaStreamSynchronize");
+  }
+  cudaEvent_t ev;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventCreate");
+  cudaEventRecord(ev, ctx->stream);
+  auto t_end = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+  int rc = MUSR_OK;
+  for (;;) {
+    e = cudaEventQuery(ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) {
+      rc = cuda_fail(ctx, e, "cudaEventQuery");
+      break;
+    }
+    if (std::chrono::steady_clock::now() > t_end) {
+      rc = fail(ctx, MUSR_ETIMEOUT, "wait timed out");
+      break;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  cudaEventDestroy(ev);
+  return rc;
+}
+
+int ensure_host(musr_ctx* ctx, double** buf, size_t* have, size_t bytes) {
+  if (*have >= bytes) return MUSR_OK;
+  if (*buf) cudaFreeHost(*buf);
+  *buf = nullptr;
+  *have = 0;
+  cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(buf), bytes);
+  if (e != cudaSuccess) return fail(ctx, MUSR_ENOMEM, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
+  *have = bytes;
+  return MUSR_OK;
+}
+
+}  // namespace musr
+
+using namespace musr;
+
+extern "C" {
+
+int musr_ctx_create(musr_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream) {
+  if (!out) return MUSR_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    g_create_error = std::string("no CUDA device: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    return MUSR_ECUDA;
+  }
+  if (device < 0 || device >= ndev) {
+    g_create_error = "device index out of range";
+    return MUSR_EINVAL;
+  }
+  musr_ctx* ctx = new musr_ctx();
+  ctx->device = device;
+  ctx->budget = hbm_budget_bytes;
+  DeviceScope ds(device);
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    ctx->own_stream = false;
+  } else {
+    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      g_create_error = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+      delete ctx;
+      return MUSR_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  g_create_error.clear();
+  *out = ctx;
+  return MUSR_OK;
+}
+
+void musr_ctx_destroy(musr_ctx* ctx) {
+  if (!ctx) return;
+  DeviceScope ds(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  free_compiled(ctx, ctx->comp[0]);
+  free_compiled(ctx, ctx->comp[1]);
+  dfree(ctx, ctx->counts_own);
+  dfree(ctx, ctx->d_map);
+  dfree(ctx, ctx->d_consts);
+  EvalBufs& ev = ctx->ev;
+  dfree(ctx, ev.params);
+  dfree(ctx, ev.out);
+  dfree(ctx, ev.partials);
+  dfree(ctx, ev.colsum);
+  dfree(ctx, ev.counters);
+  dfree(ctx, ev.jobs);
+  if (ev.h_in) cudaFreeHost(ev.h_in);
+  if (ev.h_out) cudaFreeHost(ev.h_out);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char* musr_last_error(const musr_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+static int upload_common(musr_ctx* ctx, int nhist, int64_t nbins, const double* t0, double bin_width_ns,
+                         const double* fit_range_us) {
+  if (nhist < 1 || nbins < 1) return fail(ctx, MUSR_EINVAL, "nhist and nbins must be >= 1");
+  if (nbins > (int64_t(1) << 30)) return fail(ctx, MUSR_EINVAL, "nbins must be < 2^30");
+  if (!t0 || !fit_range_us) return fail(ctx, MUSR_EINVAL, "t0 and fit_range_us must not be NULL");
+  if (!(bin_width_ns > 0.0) || !std::isfinite(bin_width_ns))
+    return fail(ctx, MUSR_EINVAL, "bin_width_ns must be finite and > 0");
+  if (!std::isfinite(fit_range_us[0]) || !std::isfinite(fit_range_us[1]) || fit_range_us[0] > fit_range_us[1])
+    return fail(ctx, MUSR_EINVAL, "fit range must be finite with lo <= hi");
+  for (int h = 0; h < nhist; ++h)
+    if (!std::isfinite(t0[h])) return fail(ctx, MUSR_EINVAL, "t0 must be finite");
+  ctx->H = nhist;
+  ctx->B = nbins;
+  ctx->t0.assign(t0, t0 + nhist);
+  ctx->bin_width_ns = bin_width_ns;
+  ctx->dt_us = bin_width_ns / 1000.0;
+  ctx->lo = fit_range_us[0];
+  ctx->hi = fit_range_us[1];
+  ctx->nlo.resize(nhist);
+  ctx->nhi.resize(nhist);
+  for (int h = 0; h < nhist; ++h)
+    fit_bins(ctx->t0[h], ctx->dt_us, nbins, ctx->lo, ctx->hi, &ctx->nlo[h], &ctx->nhi[h]);
+  return MUSR_OK;
+}
+
+static void drop_config(musr_ctx* ctx) {
+  free_compiled(ctx, ctx->comp[0]);
+  free_compiled(ctx, ctx->comp[1]);
+  ctx->have_map = false;
+  ctx->have_hist = false;
+  invalidate_eval(ctx);
+}
+
+int musr_upload_histograms(musr_ctx* ctx, const void* counts, int dtype, int nhist, int64_t nbins,
+                           const double* t0, double bin_width_ns, const double fit_range_us[2]) {
+  if (!ctx) return MUSR_EINVAL;
+  DeviceScope ds(ctx->device);
+  if (!counts) return fail(ctx, MUSR_EINVAL, "counts must not be NULL");
+  if (dtype != MUSR_DTYPE_INT32 && dtype != MUSR_DTYPE_FP32 && dtype != MUSR_DTYPE_FP64)
+    return fail(ctx, MUSR_EINVAL, "dtype must be MUSR_DTYPE_INT32, _FP32 or _FP64");
+  cudaStreamSynchronize(ctx->stream);
+  drop_config(ctx);
+  int rc = upload_common(ctx, nhist, nbins, t0, bin_width_ns, fit_range_us);
+  if (rc) return rc;
+  const int64_t stride = (nbins + kRowAlign - 1) / kRowAlign * kRowAlign;
+  const size_t esz = dtype == MUSR_DTYPE_FP64 ? 8 : 4;
+  const size_t total = static_cast<size_t>(nhist) * stride * esz;
+  std::vector<float> conv;
+  const void* src = counts;
+  if (dtype == MUSR_DTYPE_INT32) {
+    const int32_t* ci = static_cast<const int32_t*>(counts);
+    conv.resize(static_cast<size_t>(nhist) * nbins);
+    for (size_t i = 0; i < conv.size(); ++i) {
+      if (ci[i] >= (1 << 24) || ci[i] <= -(1 << 24))
+        return fail(ctx, MUSR_EINVAL, "INT32 counts must satisfy |count| < 2^24 (exact in FP32)");
+      conv[i] = static_cast<float>(ci[i]);
+    }
+    src = conv.data();
+  } else if (dtype == MUSR_DTYPE_FP32) {
+    const float* cf = static_cast<const float*>(counts);
+    for (size_t i = 0; i < static_cast<size_t>(nhist) * nbins; ++i)
+      if (!std::isfinite(cf[i])) return fail(ctx, MUSR_EINVAL, "counts must be finite");
+  } else {
+    const double* cd = static_cast<const double*>(counts);
+    for (size_t i = 0; i < static_cast<size_t>(nhist) * nbins; ++i)
+      if (!std::isfinite(cd[i])) return fail(ctx, MUSR_EINVAL, "counts must be finite");
+  }
+  if ((rc = dalloc(ctx, ctx->counts_own, total))) return rc;
+  cudaError_t e = cudaMemset(ctx->counts_own.p, 0, total);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemset");
+  e = cudaMemcpy2D(ctx->counts_own.p, stride * esz, src, nbins * esz, nbins * esz, nhist,
+                   cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy2D");
+  ctx->d_counts = ctx->counts_own.p;
+  ctx->store = dtype == MUSR_DTYPE_FP64 ? kStoreF64 : kStoreF32;
+  ctx->stride = stride;
+  ctx->have_hist = true;
+  return MUSR_OK;
+}
+
+int musr_upload_histograms_device(musr_ctx* ctx, const void* d_counts, int dtype, int nhist, int64_t nbins,
+                                  int64_t row_stride, const double* t0, double bin_width_ns,
+                                  const double fit_range_us[2]) {
+  if (!ctx) return MUSR_EINVAL;
+  DeviceScope ds(ctx->device);
+  if (!d_counts) return fail(ctx, MUSR_EINVAL, "d_counts must not be NULL");
+  if (dtype != MUSR_DTYPE_FP32 && dtype != MUSR_DTYPE_FP64)
+    return fail(ctx, MUSR_EINVAL, "device histograms must be MUSR_DTYPE_FP32 or _FP64");
+  if (reinterpret_cast<uintptr_t>(d_counts) % 16 != 0)
+    return fail(ctx, MUSR_EINVAL, "d_counts must be 16-byte aligned");
+  if (row_stride < nbins || row_stride % 4 != 0)
+    return fail(ctx, MUSR_EINVAL, "row_stride must be >= nbins and a multiple of 4");
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, d_counts) != cudaSuccess || attr.type != cudaMemoryTypeDevice ||
+      attr.device != ctx->device) {
+    cudaGetLastError();
+    return fail(ctx, MUSR_EINVAL, "d_counts is not device memory of the context's device");
+  }
+  cudaStreamSynchronize(ctx->stream);
+  drop_config(ctx);
+  dfree(ctx, ctx->counts_own);
+  int rc = upload_common(ctx, nhist, nbins, t0, bin_width_ns, fit_range_us);
+  if (rc) return rc;
+  ctx->d_counts = d_counts;
+  ctx->store = dtype == MUSR_DTYPE_FP64 ? kStoreF64 : kStoreF32;
+  ctx->stride = row_stride;
+  ctx->have_hist = true;
+  return MUSR_OK;
+}
+
+int musr_set_theory(musr_ctx* ctx, const musr_term* terms, int nterms) {
+  if (!ctx) return MUSR_EINVAL;
+  DeviceScope ds(ctx->device);
+  if (nterms < 0 || nterms > MUSR_MAX_TERMS) return fail(ctx, MUSR_EINVAL, "nterms must be in [0, 4]");
+  if (nterms > 0 && !terms) return fail(ctx, MUSR_EINVAL, "terms must not be NULL");
+  for (int k = 0; k < nterms; ++k) {
+    const musr_term& t = terms[k];
+    if (t.nprim < 1 || t.nprim > MUSR_MAX_PRIMS) return fail(ctx, MUSR_EINVAL, "a term needs 1..4 primitives");
+    for (int m = 0; m < t.nprim; ++m) {
+      if (t.kind[m] < MUSR_PRIM_AMP || t.kind[m] > MUSR_PRIM_TFCOS)
+        return fail(ctx, MUSR_EINVAL, "unknown primitive kind");
+      const int ns = t.kind[m] == MUSR_PRIM_TFCOS ? 2 : 1;
+      for (int q = 0; q < ns; ++q)
+        if (t.slot[m][q] < 0 || t.slot[m][q] >= MUSR_MAX_SLOTS)
+          return fail(ctx, MUSR_EINVAL, "slot index out of range");
+    }
+  }
+  cudaStreamSynchronize(ctx->stream);
+  free_compiled(ctx, ctx->comp[0]);
+  free_compiled(ctx, ctx->comp[1]);
+  ctx->have_map = false;
+  invalidate_eval(ctx);
+  ctx->terms.assign(terms, terms + nterms);
+  ctx->have_theory = true;
+  return MUSR_OK;
+}
+
+int musr_set_map(musr_ctx* ctx, const int32_t* map, int nslots, int nparams, const double* consts,
+                 int nconsts) {
+  if (!ctx) return MUSR_EINVAL;
+  DeviceScope ds(ctx->device);
+  if (!ctx->have_hist) return fail(ctx, MUSR_ESTATE, "upload histograms before the map");
+  if (!ctx->have_theory) return fail(ctx, MUSR_ESTATE, "set the theory before the map");
+  if (!map) return fail(ctx, MUSR_EINVAL, "map must not be NULL");
+  if (nslots < 2 || nslots > MUSR_MAX_SLOTS) return fail(ctx, MUSR_EINVAL, "nslots must be in [2, 32]");
+  if (nparams < 0 || nparams > MUSR_MAX_PARAMS) return fail(ctx, MUSR_EINVAL, "nparams out of range");
+  if (nconsts < 0 || (nconsts > 0 && !consts)) return fail(ctx, MUSR_EINVAL, "bad consts");
+  for (const auto& t : ctx->terms)
+    for (int m = 0; m < t.nprim; ++m)
+      for (int q = 0; q < (t.kind[m] == MUSR_PRIM_TFCOS ? 2 : 1); ++q)
+        if (t.slot[m][q] >= nslots) return fail(ctx, MUSR_EINVAL, "theory references a slot >= nslots");
+  for (int i = 0; i < nconsts; ++i)
+    if (!std::isfinite(consts[i])) return fail(ctx, MUSR_EINVAL, "consts must be finite");
+  const size_t n = static_cast<size_t>(ctx->H) * nslots;
+  for (size_t i = 0; i < n; ++i) {
+    const int32_t m = map[i];
+    if (m >= nparams || (m < 0 && -1 - m >= nconsts))
+      return fail(ctx, MUSR_EINVAL, "map entry " + std::to_string(i) + " out of range");
+  }
+  cudaStreamSynchronize(ctx->stream);
+  free_compiled(ctx, ctx->comp[0]);
+  free_compiled(ctx, ctx->comp[1]);
+  invalidate_eval(ctx);
+  ctx->map.assign(map, map + n);
+  ctx->nslots = nslots;
+  ctx->P = nparams;
+  ctx->consts.assign(consts, consts + nconsts);
+  std::vector<double> cpad(ctx->consts);
+  if (cpad.empty()) cpad.push_back(0.0);
+  int rc;
+  if ((rc = upload(ctx, ctx->d_map, ctx->map.data(), sizeof(int32_t) * n))) return rc;
+  if ((rc = upload(ctx, ctx->d_consts, cpad.data(), sizeof(double) * cpad.size()))) return rc;
+  if ((rc = compile(ctx, MUSR_FP64))) return rc;
+  if ((rc = compile(ctx, MUSR_SPLIT))) return rc;
+  ctx->have_map = true;
+  return MUSR_OK;
+}
+
+int musr_eval_batch(musr_ctx* ctx, const double* params, int nvec, int nparams, int mode, int precision,
+                    double* out_values, double* out_grads) {
+  if (!ctx) return MUSR_EINVAL;
+  DeviceScope ds(ctx->device);
+  int rc = check_ready(ctx, mode, precision);
+  if (rc) return rc;
+  if (nvec < 1) return fail(ctx, MUSR_EINVAL, "nvec must be >= 1");
+  if (nparams != ctx->P) return fail(ctx, MUSR_EINVAL, "nparams does not match the map");
+  if (!params || !out_values) return fail(ctx, MUSR_EINVAL, "params and out_values must not be NULL");
+  const size_t P = ctx->P, np = static_cast<size_t>(nvec) * P, no = static_cast<size_t>(nvec) * (1 + P);
+  for (size_t i = 0; i < np; ++i)
+    if (!std::isfinite(params[i])) return fail(ctx, MUSR_EINVAL, "parameters must be finite");
+  EvalBufs& ev = ctx->ev;
+  if ((rc = ensure_host(ctx, &ev.h_in, &ev.h_in_bytes, std::max<size_t>(np, 1) * sizeof(double)))) return rc;
+  if ((rc = ensure_host(ctx, &ev.h_out, &ev.h_out_bytes, no * sizeof(double)))) return rc;
+  if (ev.params.bytes < std::max<size_t>(np, 1) * sizeof(double)) {
+    if ((rc = dalloc(ctx, ev.params, std::max<size_t>(np, 1) * sizeof(double)))) return rc;
+    ev.key_valid = false;
+  }
+  if (ev.out.bytes < no * sizeof(double)) {
+    if ((rc = dalloc(ctx, ev.out, no * sizeof(double)))) return rc;
+    ev.key_valid = false;
+  }
+  const int grad = out_grads != nullptr;
+  std::memcpy(ev.h_in, params, np * sizeof(double));
+  cudaError_t e = cudaMemcpyAsync(ev.params.p, ev.h_in, np * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(params)");
+  if ((rc = enqueue_eval(ctx, precision, mode, grad, nvec, static_cast<const double*>(ev.params.p),
+                         static_cast<double*>(ev.out.p))))
+    return rc;
+  e = cudaMemcpyAsync(ev.h_out, ev.out.p, no * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(out)");
+  e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+  bool nonfinite = false;
+  for (int v = 0; v < nvec; ++v) {
+    const double* o = ev.h_out + static_cast<size_t>(v) * (1 + P);
+    out_values[v] = o[0];
+    if (!std::isfinite(o[0])) nonfinite = true;
+    if (out_grads) {
+      double* g = out_grads + static_cast<size_t>(v) * P;
+      if (std::isfinite(o[0]))
+        std::memcpy(g, o + 1, P * sizeof(double));
+      else
+        std::memset(g, 0, P * sizeof(double));
+    }
+  }
+  if (nonfinite) return fail(ctx, MUSR_ENONFINITE, "-2lnL is +inf: N <= 0 in a bin with d > 0");
+  return MUSR_OK;
+}
+
+int musr_eval(musr_ctx* ctx, const double* params, int nparams, int mode, int precision, double* out_value,
+              double* out_grad) {
+  return musr_eval_batch(ctx, params, 1, nparams, mode, precision, out_value, out_grad);
+}
+
+int musr_eval_device(musr_ctx* ctx, const double* d_params, int nvec, int mode, int precision, int with_grad,
+                     double* d_out) {
+  if (!ctx) return MUSR_EINVAL;
+  DeviceScope ds(ctx->device);
+  int rc = check_ready(ctx, mode, precision);
+  if (rc) return rc;
+  if (nvec < 1) return fail(ctx, MUSR_EINVAL, "nvec must be >= 1");
+  if (!d_params || !d_out) return fail(ctx, MUSR_EINVAL, "d_params and d_out must not be NULL");
+  return enqueue_eval(ctx, precision, mode, with_grad ? 1 : 0, nvec, d_params, d_out);
+}
+
+int musr_sync(musr_ctx* ctx, int timeout_ms) {
+  if (!ctx) return MUSR_EINVAL;
+  DeviceScope ds(ctx->device);
+  return wait_stream(ctx, timeout_ms);
+}
+
+int musr_bins_in_fit(musr_ctx* ctx, int64_t* out) {
+  if (!ctx || !out) return MUSR_EINVAL;
+  if (!ctx->have_hist) return fail(ctx, MUSR_ESTATE, "no histograms uploaded");
+  int64_t s = 0;
+  for (int h = 0; h < ctx->H; ++h) s += ctx->nhi[h] - ctx->nlo[h];
+  *out = s;
+  return MUSR_OK;
+}
+
+int musr_launches_per_eval(musr_ctx* ctx, int* out) {
+  if (!ctx || !out) return MUSR_EINVAL;
+  *out = 1;
+  return MUSR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// musr_host.h -- the context object behind the opaque musr_ctx of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "musr.h"
+#include "musr_dev.h"
+
+namespace musr {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// The theory and map of one precision, compiled to a work decomposition.
+struct Compiled {
+  bool valid = false;
+  std::string reason;  // why this precision is unavailable (valid == false)
+  HistSet hs{};        // host copy (device pointers inside)
+  DevBuf d_hs, chunks, items, hist_index, col_chunk, p_ptr, p_cols;
+};
+
+// Buffers of the eval entry points and the cached job table of the last launch.
+struct EvalBufs {
+  DevBuf params, out, partials, colsum, counters, jobs;
+  double* h_in = nullptr;
+  double* h_out = nullptr;
+  size_t h_in_bytes = 0, h_out_bytes = 0;
+  bool key_valid = false;
+  int k_prec = -1, k_mode = -1, k_grad = -1, k_nvec = -1;
+  const double* k_params = nullptr;
+  double* k_out = nullptr;
+};
+
+// RAII: make `dev` current, restore the caller's device on exit.
+class DeviceScope {
+ public:
+  explicit DeviceScope(int dev);
+  ~DeviceScope();
+
+ private:
+  int prev_ = 0;
+};
+
+int fail(musr_ctx* ctx, int code, const std::string& msg);
+int cuda_fail(musr_ctx* ctx, cudaError_t e, const char* what);
+int dalloc(musr_ctx* ctx, DevBuf& b, size_t bytes);
+void dfree(musr_ctx* ctx, DevBuf& b);
+int upload(musr_ctx* ctx, DevBuf& b, const void* src, size_t bytes);
+void fit_bins(double t0, double dt_us, int64_t B, double lo, double hi, int* nlo, int* nhi);
+int wait_stream(musr_ctx* ctx, int timeout_ms);
+
+}  // namespace musr
+
+struct musr_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 1;
+  size_t budget = 0, used = 0;
+  std::string err;
+  // histograms
+  bool have_hist = false;
+  musr::DevBuf counts_own;
+  const void* d_counts = nullptr;
+  int store = musr::kStoreF32;
+  int H = 0;
+  int64_t B = 0, stride = 0;
+  std::vector<double> t0;
+  double bin_width_ns = 0.0, dt_us = 0.0, lo = 0.0, hi = 0.0;
+  std::vector<int> nlo, nhi;
+  // theory
+  bool have_theory = false;
+  std::vector<musr_term> terms;
+  // parameter map
+  bool have_map = false;
+  std::vector<int32_t> map;
+  int nslots = 0, P = 0;
+  std::vector<double> consts;
+  musr::DevBuf d_map, d_consts;
+  musr::Compiled comp[2];
+  musr::EvalBufs ev;
+  int last_grid = 0;
+};

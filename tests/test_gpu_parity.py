@@ -1,0 +1,295 @@
+"""GPU parity: libmusr (through its C ABI) against the FP64 CPU oracle.
+
+Tolerances:
+  * FP64 path: |dvalue| <= 1e-12 |value|; |dg_i| <= 1e-12 * sum_n |dterm_n/dtheta_i|
+    (the gradient scale returned by the oracle; g_i -> 0 at the optimum makes a
+    plain relative error ill-posed).
+  * SPLIT path: per-bin FP32 evaluation with hardware ex2/lg2/rcp/sin/cos whose
+    relative error is below 2^-20 (about 1e-6) per factor; a bin's model combines a
+    handful of such factors, so every per-bin term and gradient term carries a
+    relative error below SPLIT_EPS = 2^-16 (1.5e-5, a margin of ~16 over the factor
+    error).  Summed terms are bounded by SPLIT_EPS times the sum of their absolute
+    values: the value (all terms >= 0) to SPLIT_EPS relative, the gradient to
+    SPLIT_EPS * gscale.  FP32 accumulation below the warp adds far less.
+"""
+import numpy as np
+import pytest
+
+import musr_inputs as mi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+SPLIT_EPS = 2.0 ** -16
+
+
+@pytest.fixture(scope="module")
+def B(musr_lib):
+    from paper_1509_07685_gb300 import binding
+    return binding
+
+
+def _problems():
+    # Sizes the oracle finishes in seconds, spanning several tiles with ragged tails.
+    return {
+        "cfg1": mi.cfg1(nbins=16384 + 37, seed=10, dtype=np.int32),
+        "cfg2": mi.cfg2(nhist=8, nbins=20000 + 13, bin_width_ns=0.64, seed=11),
+        "cfg3": mi.cfg3(nhist=4, nbins=9000 + 3, bin_width_ns=1.4, seed=12),
+        "cfg5": mi.cfg5(nhist=10, nbins=6000 + 5, seed=13, n0=20.0, nbkg=0.1),
+        "paper_tf16": mi.paper_tf16(nhist=16, nbins=3000 + 1, seed=14, n0=100.0),
+    }
+
+
+PROBLEMS = None
+
+
+def problems():
+    global PROBLEMS
+    if PROBLEMS is None:
+        PROBLEMS = _problems()
+    return PROBLEMS
+
+
+def _check_fp64(v, g, ref):
+    rv, rg, rgs, _ = ref
+    assert abs(v - rv) <= FP64_TOL * abs(rv), (v, rv, (v - rv) / rv)
+    bad = np.abs(g - rg) > FP64_TOL * rgs + 1e-300
+    assert not bad.any(), (np.nonzero(bad), g[bad], rg[bad], rgs[bad])
+
+
+def _check_split(v, g, ref):
+    rv, rg, rgs, _ = ref
+    assert abs(v - rv) <= SPLIT_EPS * abs(rv), (v, rv, (v - rv) / rv)
+    bad = np.abs(g - rg) > SPLIT_EPS * rgs + 1e-300
+    assert not bad.any(), (np.nonzero(bad), g[bad], rg[bad], rgs[bad])
+
+
+@pytest.mark.parametrize("name", ["cfg1", "cfg2", "cfg3", "cfg5", "paper_tf16"])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fp64_and_split_match_oracle(B, name, mode):
+    p = problems()[name]
+    rng = np.random.default_rng(100 + mode)
+    with B.Context(p) as ctx:
+        for trial in range(2):
+            x = p.truth * rng.uniform(0.9, 1.1, p.nparams) if trial else mi.start_point(p, 3)
+            ref = oracle.cost(p, x, mode)
+            assert ref[3] == 0
+            v, g, st = ctx.eval(x, mode, B.MUSR_FP64)
+            assert st == 0
+            _check_fp64(v, g, ref)
+            v1, _, _ = ctx.eval(x, mode, B.MUSR_FP64, grad=False)
+            assert v1 == v  # the value-only kernel sums in the same order
+            v, g, st = ctx.eval(x, mode, B.MUSR_SPLIT)
+            assert st == 0
+            _check_split(v, g, ref)
+            v2, _, _ = ctx.eval(x, mode, B.MUSR_SPLIT, grad=False)
+            assert abs(v2 - v) <= 1e-12 * abs(v)
+
+
+def test_batch_equals_single_and_is_deterministic(B):
+    p = problems()["cfg2"]
+    X = mi.jitter(p.truth, 5, seed=3, lo=0.95, hi=1.05)
+    with B.Context(p) as ctx:
+        for prec in (B.MUSR_FP64, B.MUSR_SPLIT):
+            vals, grads, st = ctx.eval_batch(X, 1, prec)
+            assert st == 0
+            for i in range(len(X)):
+                v, g, _ = ctx.eval(X[i], 1, prec)
+                assert v == vals[i] and np.array_equal(g, grads[i])  # bit-identical
+            vals2, grads2, _ = ctx.eval_batch(X, 1, prec)
+            assert np.array_equal(vals, vals2) and np.array_equal(grads, grads2)
+
+
+def test_device_resident_eval(B):
+    import torch
+    p = problems()["cfg3"]
+    X = mi.jitter(p.truth, 3, seed=5, lo=0.95, hi=1.05)
+    stream = torch.cuda.current_stream().cuda_stream
+    with B.Context(p, cuda_stream=stream) as ctx:
+        d_x = torch.tensor(X, dtype=torch.float64, device="cuda")
+        d_out = torch.empty((3, 1 + p.nparams), dtype=torch.float64, device="cuda")
+        for prec in (B.MUSR_FP64, B.MUSR_SPLIT):
+            B.musr_eval_device(ctx.ctx, d_x.data_ptr(), 3, 0, prec, True, d_out.data_ptr())
+            torch.cuda.synchronize()
+            out = d_out.cpu().numpy()
+            vals, grads, _ = ctx.eval_batch(X, 0, prec)
+            assert np.array_equal(out[:, 0], vals) and np.array_equal(out[:, 1:], grads)
+
+
+def test_borrowed_device_histograms(B):
+    import torch
+    p = problems()["cfg2"]
+    x = mi.start_point(p, 4)
+    stride = (p.B + 3) // 4 * 4
+    d = torch.zeros((p.H, stride), dtype=torch.float32, device="cuda")
+    d[:, :p.B] = torch.from_numpy(np.ascontiguousarray(p.counts, dtype=np.float32)).cuda()
+    ref = oracle.cost(p, x, 1)
+    ctx = B.musr_ctx_create(0)
+    try:
+        B.musr_upload_histograms_device(ctx, d.data_ptr(), B.MUSR_DTYPE_FP32, p.H, p.B, stride, p.t0,
+                                        p.bin_width_ns, p.fit_range_us)
+        B.musr_set_theory(ctx, p.terms)
+        B.musr_set_map(ctx, p.map, p.nparams, p.consts)
+        v, g, st = B.musr_eval(ctx, x, 1, B.MUSR_FP64)
+        _check_fp64(v, g, ref)
+        v, g, st = B.musr_eval(ctx, x, 1, B.MUSR_SPLIT)
+        _check_split(v, g, ref)
+    finally:
+        B.musr_ctx_destroy(ctx)
+
+
+# ------------------------------------------------------------------------------------------
+# Edge cases
+# ------------------------------------------------------------------------------------------
+
+def test_data_equal_model_fp64_counts_give_zero(B):
+    """FP64 counts equal to the model (computed by the oracle) give chi^2 = -2lnL = 0."""
+    base = mi.cfg3(nhist=2, nbins=1500, bin_width_ns=8.0, seed=1)
+    x = base.truth.copy()
+    dt = base.bin_width_ns / 1000.0
+    d = np.array([[oracle.model(base, x, h, n * dt) for n in range(base.B)] for h in range(base.H)])
+    p = base.with_counts(d)
+    with B.Context(p) as ctx:
+        for mode in (0, 1):
+            v, g, st = ctx.eval(x, mode, B.MUSR_FP64)
+            assert st == 0 and abs(v) < 1e-9
+            v, g, st = ctx.eval(x, mode, B.MUSR_SPLIT)
+            ref_scale = oracle.cost(p, x * 1.01, mode)[0]
+            assert st == 0 and abs(v) <= SPLIT_EPS * ref_scale
+
+
+def test_empty_fit_range_and_single_bin(B):
+    p = mi.cfg1(nbins=4096, seed=2, dtype=np.float32)
+    x = p.truth
+    q = mi.Problem(p.counts, p.t0, p.bin_width_ns, (100.0, 200.0), p.terms, p.map, p.consts, p.nparams,
+                   p.truth, p.names)
+    with B.Context(q) as ctx:
+        assert ctx.bins_in_fit() == 0
+        for prec in (0, 1):
+            v, g, st = ctx.eval(x, 0, prec)
+            assert st == 0 and v == 0.0 and not g.any()
+    dt = p.bin_width_ns / 1000.0
+    q = mi.Problem(p.counts, p.t0, p.bin_width_ns, (1001 * dt, 1001 * dt), p.terms, p.map, p.consts,
+                   p.nparams, p.truth, p.names)
+    ref = oracle.cost(q, x, 1)
+    with B.Context(q) as ctx:
+        assert ctx.bins_in_fit() == 1
+        v, g, st = ctx.eval(x, 1, B.MUSR_FP64)
+        _check_fp64(v, g, ref)
+        v, g, st = ctx.eval(x, 1, B.MUSR_SPLIT)
+        _check_split(v, g, ref)
+
+
+def test_per_histogram_t0_and_fit_range_edges(B):
+    """Fractional, different t0 per histogram: SPLIT groups split by t0; a fit range that
+    starts and ends inside tiles."""
+    p = mi.cfg2(nhist=6, nbins=7001, bin_width_ns=1.6, seed=21)
+    t0 = np.array([0.0, 0.0, 3.25, 3.25, 17.5, 0.0])
+    q = mi.Problem(p.counts, t0, p.bin_width_ns, (0.37, 9.9), p.terms, p.map, p.consts, p.nparams,
+                   p.truth, p.names)
+    x = mi.start_point(q, 9)
+    with B.Context(q) as ctx:
+        for mode in (0, 1):
+            ref = oracle.cost(q, x, mode)
+            v, g, _ = ctx.eval(x, mode, B.MUSR_FP64)
+            _check_fp64(v, g, ref)
+            v, g, _ = ctx.eval(x, mode, B.MUSR_SPLIT)
+            _check_split(v, g, ref)
+
+
+def test_mle_undefined_is_nonfinite(B):
+    p = mi.cfg1(nbins=2048, seed=3, dtype=np.float32)
+    x = p.truth.copy()
+    x[0] = -50.0  # N0 < 0 with Nbkg small: N <= 0 where d > 0
+    x[1] = 0.0
+    with B.Context(p) as ctx:
+        for prec in (0, 1):
+            v, g, st = ctx.eval(x, 1, prec)
+            assert st == B.MUSR_ENONFINITE and np.isinf(v) and not g.any()
+            v, g, st = ctx.eval(x, 0, prec)  # chi^2 stays finite
+            assert st == 0 and np.isfinite(v)
+
+
+def test_generic_and_noncanonical_theories(B):
+    """A term list outside the compiled SPLIT shapes runs the generic SPLIT kernel; a term
+    with two cosines is FP64-only (SPLIT refuses it with MUSR_EINVAL)."""
+    base = mi.cfg1(nbins=3000, bin_width_ns=3.0, seed=5, dtype=np.float32)
+    terms = [[("AMP", (2,)), ("EXP", (3,))], [("AMP", (4,)), ("GAUSS", (5,)), ("EXP", (3,))],
+             [("AMP", (6,)), ("KT", (7,))], [("AMP", (8,)), ("TFCOS", (9, 10))]]
+    mp = np.array([[0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10]], np.int32)
+    x = np.array([300.0, 2.0, 0.05, 0.3, 0.05, 0.4, 0.05, 0.5, 0.1, 5.0, 20.0])
+    p = mi.Problem(base.counts, base.t0, base.bin_width_ns, base.fit_range_us, terms, mp, np.zeros(0), 11,
+                   x, [f"p{i}" for i in range(11)])
+    with B.Context(p) as ctx:
+        for mode in (0, 1):
+            ref = oracle.cost(p, x, mode)
+            v, g, _ = ctx.eval(x, mode, B.MUSR_FP64)
+            _check_fp64(v, g, ref)
+            v, g, _ = ctx.eval(x, mode, B.MUSR_SPLIT)
+            _check_split(v, g, ref)
+    terms2 = [[("AMP", (2,)), ("TFCOS", (3, 4)), ("TFCOS", (5, 4))]]
+    mp2 = np.array([[0, 1, 2, 3, 4, 5]], np.int32)
+    x2 = np.array([300.0, 2.0, 0.2, 5.0, 10.0, 0.3])
+    p2 = mi.Problem(base.counts, base.t0, base.bin_width_ns, base.fit_range_us, terms2, mp2, np.zeros(0), 6,
+                    x2, [f"p{i}" for i in range(6)])
+    with B.Context(p2) as ctx:
+        ref = oracle.cost(p2, x2, 0)
+        v, g, _ = ctx.eval(x2, 0, B.MUSR_FP64)
+        _check_fp64(v, g, ref)
+        with pytest.raises(B.MusrError) as e:
+            ctx.eval(x2, 0, B.MUSR_SPLIT)
+        assert e.value.status == B.MUSR_EINVAL
+
+
+def test_invalid_arguments(B):
+    p = mi.cfg1(nbins=512, seed=4, dtype=np.float32)
+    ctx = B.musr_ctx_create(0)
+    try:
+        with pytest.raises(B.MusrError) as e:
+            B.musr_eval(ctx, p.truth, 0, 0)
+        assert e.value.status == B.MUSR_ESTATE
+        B.musr_upload_histograms(ctx, p.counts, p.t0, p.bin_width_ns, p.fit_range_us)
+        B.musr_set_theory(ctx, p.terms)
+        bad = p.map.copy()
+        bad[0, 3] = 99
+        with pytest.raises(B.MusrError) as e:
+            B.musr_set_map(ctx, bad, p.nparams, p.consts)
+        assert e.value.status == B.MUSR_EINVAL
+        B.musr_set_map(ctx, p.map, p.nparams, p.consts)
+        x = p.truth.copy()
+        x[2] = np.nan
+        with pytest.raises(B.MusrError) as e:
+            B.musr_eval(ctx, x, 0, 0)
+        assert e.value.status == B.MUSR_EINVAL
+        with pytest.raises(B.MusrError):
+            B.musr_eval(ctx, p.truth[:3], 0, 0)
+        with pytest.raises(B.MusrError):
+            B.musr_eval(ctx, p.truth, 2, 0)
+    finally:
+        B.musr_ctx_destroy(ctx)
+
+
+def test_hbm_budget_is_enforced(B):
+    p = mi.cfg2(nhist=8, nbins=65536, seed=2)
+    ctx = B.musr_ctx_create(0, hbm_budget_bytes=1 << 20)
+    try:
+        with pytest.raises(B.MusrError) as e:
+            B.musr_upload_histograms(ctx, p.counts, p.t0, p.bin_width_ns, p.fit_range_us)
+        assert e.value.status == B.MUSR_ENOMEM
+    finally:
+        B.musr_ctx_destroy(ctx)
+
+
+@pytest.mark.slow
+def test_full_size_large_fit_fp64_matches_oracle(B):
+    """64 x 2^20 bins (FP32 counts, 256 MiB), the launch configuration of the large-fit
+    workload: the FP64 path against the oracle's full sum, and SPLIT within its bound."""
+    p = mi.cfg5()
+    x = p.truth * np.random.default_rng(55).uniform(0.98, 1.02, p.nparams)
+    ref = oracle.cost(p, x, 1)
+    with B.Context(p) as ctx:
+        v, g, st = ctx.eval(x, 1, B.MUSR_FP64)
+        _check_fp64(v, g, ref)
+        v, g, st = ctx.eval(x, 1, B.MUSR_SPLIT)
+        _check_split(v, g, ref)
