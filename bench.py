@@ -200,7 +200,8 @@ def run_ours(args, rank, world, local_rank):
     B.load()
     p, X = _workload(rank)
     mode = args.mode
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     ctx = B.Context(p, device=local_rank, cuda_stream=stream.cuda_stream)
     bins = ctx.bins_in_fit()
     P = p.nparams

@@ -84,8 +84,9 @@ typedef struct musr_ctx musr_ctx;
 
 /* Creates a context on CUDA device `device`.  hbm_budget_bytes caps the
  * device memory the context may allocate (0: no cap).  cuda_stream is a
- * cudaStream_t to run on (e.g. torch.cuda.current_stream().cuda_stream), or
- * NULL for a stream the context creates.  The context owns all memory it
+ * cudaStream_t to run on (e.g. torch.cuda.current_stream().cuda_stream; the
+ * legacy default stream is passed as cudaStreamLegacy, (void*)1), or NULL for
+ * a stream the context creates.  The context owns all memory it
  * allocates; *out is NULL on failure.  (Section 2.1: memory handling and
  * streams of the DKS communication layer.) */
 int musr_ctx_create(musr_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream);

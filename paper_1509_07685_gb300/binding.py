@@ -122,11 +122,20 @@ def terms_to_c(terms) -> Tuple[ctypes.Array, int]:
 # Functions with the C names
 # --------------------------------------------------------------------------------------------
 
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the handle of the legacy default stream
+
+
 def musr_ctx_create(device: int = 0, hbm_budget_bytes: int = 0, cuda_stream: Optional[int] = None):
+    """cuda_stream: None -> the context creates its own stream; an int handle (e.g.
+    torch.cuda.current_stream().cuda_stream) -> run on that stream, where torch's
+    handle 0 (the legacy default stream) is passed on as cudaStreamLegacy."""
     lib = load()
     out = ctypes.c_void_p()
-    st = lib.musr_ctx_create(ctypes.byref(out), device, hbm_budget_bytes,
-                             ctypes.c_void_p(cuda_stream) if cuda_stream else None)
+    if cuda_stream is None:
+        handle = None
+    else:
+        handle = ctypes.c_void_p(cuda_stream if cuda_stream != 0 else CUDA_STREAM_LEGACY)
+    st = lib.musr_ctx_create(ctypes.byref(out), device, hbm_budget_bytes, handle)
     if st != MUSR_OK:
         raise MusrError(st, (lib.musr_last_error(None) or b"").decode())
     return out

@@ -171,9 +171,11 @@ static int pick_iters(const std::vector<int64_t>& ranges, int per_iter, int targ
   return 1;
 }
 
-// Builds the decomposition and finalize tables of one precision.
-int compile(musr_ctx* ctx, int prec) {
-  Compiled& c = ctx->comp[prec];
+// Builds the decomposition and finalize tables of one precision and one
+// decomposition (0: tiles small enough that one evaluation fills the GPU;
+// 1: the largest tiles, for batched launches).
+int compile(musr_ctx* ctx, int prec, int var) {
+  Compiled& c = ctx->comp[prec][var];
   free_compiled(ctx, c);
   HistSet hs;
   std::memset(&hs, 0, sizeof(hs));
@@ -282,11 +284,13 @@ int compile(musr_ctx* ctx, int prec) {
   } else {
     for (int h = 0; h < H; ++h) groups.push_back({h});
   }
-  // Chunks of at most group_cap histograms.
+  // Chunks of at most group_cap histograms; histograms without a bin in the fit
+  // range contribute nothing and get no chunk.
   std::vector<Chunk> chunks;
   std::vector<int> hist_index;
   for (const auto& g : groups)
     for (size_t i = 0; i < g.size(); i += group_cap) {
+      if (ctx->nhi[g[i]] <= ctx->nlo[g[i]]) continue;
       Chunk ch;
       std::memset(&ch, 0, sizeof(ch));
       ch.first = static_cast<int>(hist_index.size());
@@ -298,11 +302,12 @@ int compile(musr_ctx* ctx, int prec) {
       ch.tile0 = ch.nlo & ~3;
       chunks.push_back(ch);
     }
-  // Tiles.
+  // Tiles: at most 16 iterations of the CTA per tile (the SPLIT phase split
+  // needs tile offsets below 2^14 bins).
   const int per_iter = prec == MUSR_SPLIT ? musr::kBlock * musr::kBinsPerThread : musr::kBlock;
   std::vector<int64_t> ranges;
-  for (const auto& ch : chunks) ranges.push_back(ch.nhi > ch.nlo ? ch.nhi - ch.tile0 : 0);
-  const int iters = pick_iters(ranges, per_iter, 4 * ctx->num_sms);
+  for (const auto& ch : chunks) ranges.push_back(ch.nhi - ch.tile0);
+  const int iters = var == 0 ? pick_iters(ranges, per_iter, 4 * ctx->num_sms) : 16;
   hs.tile_bins = per_iter * iters;
   std::vector<int2> items;
   int col = 0;
@@ -315,7 +320,8 @@ int compile(musr_ctx* ctx, int prec) {
     col += ch.nh * ctx->nslots;
   }
   hs.group = group_cap;
-  hs.pstride = 1 + group_cap * ctx->nslots;
+  hs.nch = prec == MUSR_SPLIT ? musr::shape_channels(hs.shape) : musr::kFp64Channels;
+  hs.pstride = 1 + hs.nch;
   hs.ncols = col;
   hs.nchunks = static_cast<int>(chunks.size());
   hs.nitems = static_cast<int>(items.size());
@@ -361,38 +367,46 @@ int compile(musr_ctx* ctx, int prec) {
 
 void invalidate_eval(musr_ctx* ctx) { ctx->ev.key_valid = false; }
 
-// Buffers for nvec evaluations at precision prec; rebuilds the job table when
-// the launch's key (precision, mode, grad, nvec, pointers) changes.
-int prepare_jobs(musr_ctx* ctx, int prec, int mode, int grad, int nvec, const double* d_params,
+// Decomposition for a launch of nvec evaluations: the large tiles when the
+// batch still gives every resident CTA a few items, else the small ones.
+int pick_variant(musr_ctx* ctx, int prec, int nvec) {
+  const Compiled& coarse = ctx->comp[prec][1];
+  const int ctas = ctx->num_sms * 2;
+  return static_cast<int64_t>(nvec) * coarse.hs.nitems >= 3 * ctas ? 1 : 0;
+}
+
+// Buffers for nvec evaluations; rebuilds the job table when the launch's key
+// (precision, decomposition, mode, grad, nvec, pointers) changes.
+int prepare_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, const double* d_params,
                  double* d_out) {
   EvalBufs& ev = ctx->ev;
-  const HistSet& hs = ctx->comp[prec].hs;
+  const HistSet& hs = ctx->comp[prec][var].hs;
   const size_t part = static_cast<size_t>(nvec) * hs.nitems * hs.pstride;
   const size_t cols = static_cast<size_t>(nvec) * std::max(hs.ncols, 1);
+  const size_t nck = static_cast<size_t>(nvec) * std::max(hs.nchunks, 1);
   int rc;
-  if (ev.partials.bytes < part * sizeof(double)) {
-    if ((rc = dalloc(ctx, ev.partials, part * sizeof(double)))) return rc;
+  auto grow = [&](DevBuf& b, size_t bytes, bool zero) -> int {
+    if (b.bytes >= bytes) return MUSR_OK;
+    int r = dalloc(ctx, b, bytes);
+    if (r) return r;
     ev.key_valid = false;
-  }
-  if (ev.colsum.bytes < cols * sizeof(double)) {
-    if ((rc = dalloc(ctx, ev.colsum, cols * sizeof(double)))) return rc;
-    ev.key_valid = false;
-  }
-  if (ev.counters.bytes < nvec * sizeof(unsigned)) {
-    if ((rc = dalloc(ctx, ev.counters, nvec * sizeof(unsigned)))) return rc;
-    cudaError_t e = cudaMemsetAsync(ev.counters.p, 0, ev.counters.bytes, ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
-    ev.key_valid = false;
-  }
-  if (ev.jobs.bytes < nvec * sizeof(Job)) {
-    if ((rc = dalloc(ctx, ev.jobs, nvec * sizeof(Job)))) return rc;
-    ev.key_valid = false;
-  }
-  if (ev.key_valid && ev.k_prec == prec && ev.k_mode == mode && ev.k_grad == grad &&
+    if (zero) {
+      cudaError_t e = cudaMemsetAsync(b.p, 0, b.bytes, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
+    }
+    return MUSR_OK;
+  };
+  if ((rc = grow(ev.partials, part * sizeof(double), false))) return rc;
+  if ((rc = grow(ev.colsum, cols * sizeof(double), false))) return rc;
+  if ((rc = grow(ev.chunk_val, nck * sizeof(double), false))) return rc;
+  if ((rc = grow(ev.chunk_count, nck * sizeof(unsigned), true))) return rc;
+  if ((rc = grow(ev.counters, nvec * sizeof(unsigned), true))) return rc;
+  if ((rc = grow(ev.jobs, nvec * sizeof(Job), false))) return rc;
+  if (ev.key_valid && ev.k_prec == prec && ev.k_var == var && ev.k_mode == mode && ev.k_grad == grad &&
       ev.k_nvec == nvec && ev.k_params == d_params && ev.k_out == d_out)
     return MUSR_OK;
   std::vector<Job> jobs(nvec);
-  const HistSet* d_hs = static_cast<const HistSet*>(ctx->comp[prec].d_hs.p);
+  const HistSet* d_hs = static_cast<const HistSet*>(ctx->comp[prec][var].d_hs.p);
   for (int v = 0; v < nvec; ++v) {
     Job& j = jobs[v];
     std::memset(&j, 0, sizeof(j));
@@ -401,10 +415,13 @@ int prepare_jobs(musr_ctx* ctx, int prec, int mode, int grad, int nvec, const do
     j.out = d_out + static_cast<size_t>(v) * (1 + ctx->P);
     j.partials = static_cast<double*>(ev.partials.p) + static_cast<size_t>(v) * hs.nitems * hs.pstride;
     j.colsum = static_cast<double*>(ev.colsum.p) + static_cast<size_t>(v) * std::max(hs.ncols, 1);
+    j.chunk_val = static_cast<double*>(ev.chunk_val.p) + static_cast<size_t>(v) * std::max(hs.nchunks, 1);
+    j.chunk_count = static_cast<unsigned*>(ev.chunk_count.p) + static_cast<size_t>(v) * std::max(hs.nchunks, 1);
     j.counter = static_cast<unsigned*>(ev.counters.p) + v;
     j.item_begin = v * hs.nitems;
     j.mode = mode;
     j.grad = grad;
+    j.prec = prec;
   }
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
@@ -412,6 +429,7 @@ int prepare_jobs(musr_ctx* ctx, int prec, int mode, int grad, int nvec, const do
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy(jobs)");
   ev.key_valid = true;
   ev.k_prec = prec;
+  ev.k_var = var;
   ev.k_mode = mode;
   ev.k_grad = grad;
   ev.k_nvec = nvec;
@@ -427,20 +445,21 @@ int check_ready(musr_ctx* ctx, int mode, int prec) {
   if (mode != MUSR_CHI2 && mode != MUSR_MLE) return fail(ctx, MUSR_EINVAL, "mode must be MUSR_CHI2 or MUSR_MLE");
   if (prec != MUSR_FP64 && prec != MUSR_SPLIT)
     return fail(ctx, MUSR_EINVAL, "precision must be MUSR_FP64 or MUSR_SPLIT");
-  if (!ctx->comp[prec].valid)
-    return fail(ctx, MUSR_EINVAL, "precision unavailable for this theory: " + ctx->comp[prec].reason);
+  if (!ctx->comp[prec][0].valid)
+    return fail(ctx, MUSR_EINVAL, "precision unavailable for this theory: " + ctx->comp[prec][0].reason);
   return MUSR_OK;
 }
 
 // Enqueues one launch of nvec evaluations reading d_params, writing d_out.
 int enqueue_eval(musr_ctx* ctx, int prec, int mode, int grad, int nvec, const double* d_params,
                  double* d_out) {
-  const HistSet& hs = ctx->comp[prec].hs;
+  const int var = pick_variant(ctx, prec, nvec);
+  const HistSet& hs = ctx->comp[prec][var].hs;
   if (hs.nitems == 0) {  // no bin in the fit range: cost 0, gradient 0
     cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(double) * nvec * (1 + ctx->P), ctx->stream);
     return e == cudaSuccess ? MUSR_OK : cuda_fail(ctx, e, "cudaMemsetAsync");
   }
-  int rc = prepare_jobs(ctx, prec, mode, grad, nvec, d_params, d_out);
+  int rc = prepare_jobs(ctx, prec, var, mode, grad, nvec, d_params, d_out);
   if (rc) return rc;
   musr::LaunchInfo info;
   if (musr::launch_eval(prec, hs.shape, mode, grad, static_cast<const Job*>(ctx->ev.jobs.p), nvec,
@@ -538,8 +557,8 @@ void musr_ctx_destroy(musr_ctx* ctx) {
   if (!ctx) return;
   DeviceScope ds(ctx->device);
   cudaStreamSynchronize(ctx->stream);
-  free_compiled(ctx, ctx->comp[0]);
-  free_compiled(ctx, ctx->comp[1]);
+  for (auto& pc : ctx->comp)
+    for (auto& c : pc) free_compiled(ctx, c);
   dfree(ctx, ctx->counts_own);
   dfree(ctx, ctx->d_map);
   dfree(ctx, ctx->d_consts);
@@ -548,6 +567,8 @@ void musr_ctx_destroy(musr_ctx* ctx) {
   dfree(ctx, ev.out);
   dfree(ctx, ev.partials);
   dfree(ctx, ev.colsum);
+  dfree(ctx, ev.chunk_val);
+  dfree(ctx, ev.chunk_count);
   dfree(ctx, ev.counters);
   dfree(ctx, ev.jobs);
   if (ev.h_in) cudaFreeHost(ev.h_in);
@@ -586,8 +607,8 @@ static int upload_common(musr_ctx* ctx, int nhist, int64_t nbins, const double* 
 }
 
 static void drop_config(musr_ctx* ctx) {
-  free_compiled(ctx, ctx->comp[0]);
-  free_compiled(ctx, ctx->comp[1]);
+  for (auto& pc : ctx->comp)
+    for (auto& c : pc) free_compiled(ctx, c);
   ctx->have_map = false;
   ctx->have_hist = false;
   invalidate_eval(ctx);
@@ -688,8 +709,8 @@ int musr_set_theory(musr_ctx* ctx, const musr_term* terms, int nterms) {
     }
   }
   cudaStreamSynchronize(ctx->stream);
-  free_compiled(ctx, ctx->comp[0]);
-  free_compiled(ctx, ctx->comp[1]);
+  for (auto& pc : ctx->comp)
+    for (auto& c : pc) free_compiled(ctx, c);
   ctx->have_map = false;
   invalidate_eval(ctx);
   ctx->terms.assign(terms, terms + nterms);
@@ -720,8 +741,8 @@ int musr_set_map(musr_ctx* ctx, const int32_t* map, int nslots, int nparams, con
       return fail(ctx, MUSR_EINVAL, "map entry " + std::to_string(i) + " out of range");
   }
   cudaStreamSynchronize(ctx->stream);
-  free_compiled(ctx, ctx->comp[0]);
-  free_compiled(ctx, ctx->comp[1]);
+  for (auto& pc : ctx->comp)
+    for (auto& c : pc) free_compiled(ctx, c);
   invalidate_eval(ctx);
   ctx->map.assign(map, map + n);
   ctx->nslots = nslots;
@@ -732,8 +753,9 @@ int musr_set_map(musr_ctx* ctx, const int32_t* map, int nslots, int nparams, con
   int rc;
   if ((rc = upload(ctx, ctx->d_map, ctx->map.data(), sizeof(int32_t) * n))) return rc;
   if ((rc = upload(ctx, ctx->d_consts, cpad.data(), sizeof(double) * cpad.size()))) return rc;
-  if ((rc = compile(ctx, MUSR_FP64))) return rc;
-  if ((rc = compile(ctx, MUSR_SPLIT))) return rc;
+  for (int prec : {MUSR_FP64, MUSR_SPLIT})
+    for (int var : {0, 1})
+      if ((rc = compile(ctx, prec, var))) return rc;
   ctx->have_map = true;
   return MUSR_OK;
 }

@@ -76,6 +76,7 @@ struct Contrib {
   int term;
 };
 
+// Only chunks with at least one bin in the fit range are listed.
 struct Chunk {
   int first;      // index into HistSet::hist_index of its first histogram
   int nh;         // number of histograms (<= kGroupMax, 1 on the FP64 path)
@@ -113,9 +114,10 @@ struct HistSet {
   const int2* items;       // (chunk, tile) per work item
   int nitems;
   int tile_bins;           // bins per tile
-  int group;               // histograms per chunk at most (row width of partials)
-  int pstride;             // doubles per partial row: 1 + group * nslots
-  int ncols;               // finalize columns: sum over chunks of nh * nslots
+  int group;               // histograms per chunk at most
+  int nch;                 // reduction channels per item (SPLIT: per shape; FP64: 2 + 32)
+  int pstride;             // doubles per partial row: 1 + nch
+  int ncols;               // slot columns: sum over chunks of nh * nslots
   const int* col_chunk;    // [ncols] chunk of each column
   const int* p_ptr;        // [P + 1] CSR: columns contributing to parameter p
   const int* p_cols;
@@ -123,15 +125,17 @@ struct HistSet {
 
 struct Job {
   const HistSet* hs;
-  const double* params;  // [P]
-  double* out;           // [1 + P]
-  double* partials;      // [hs->nitems][hs->pstride]
-  double* colsum;        // [hs->ncols]
-  unsigned int* counter; // zero between launches
-  int item_begin;        // first global item of this job in the launch
-  int mode;              // 0 chi^2, 1 -2lnL
-  int grad;              // 0: value only
-  int pad;
+  const double* params;      // [P]
+  double* out;               // [1 + P]
+  double* partials;          // [hs->nitems][hs->pstride]
+  double* colsum;            // [hs->ncols]
+  double* chunk_val;         // [hs->nchunks]
+  unsigned int* chunk_count; // [hs->nchunks], zero between launches
+  unsigned int* counter;     // zero between launches
+  int item_begin;            // first global item of this job in the launch
+  int mode;                  // 0 chi^2, 1 -2lnL
+  int grad;                  // 0: value only
+  int prec;                  // 0 FP64, 1 SPLIT
 };
 
 // Launchers (host side of musr_kernels.cu).  All enqueue on `stream`.
@@ -142,7 +146,9 @@ struct LaunchInfo {
 int launch_eval(int precision, int shape, int mode, int grad, const Job* d_jobs, int njobs,
                 int total_items, int num_sms, void* stream, LaunchInfo* info);
 int max_ctas_per_sm(int precision, int shape, int mode, int grad);
-// Histograms per chunk of a SPLIT shape.
+// Histograms per chunk, and reduction channels per work item, of a SPLIT shape.
 int shape_group(int shape);
+int shape_channels(int shape);
+constexpr int kFp64Channels = 2 + kMaxTerms * kMaxPrims * 2;
 
 }  // namespace musr

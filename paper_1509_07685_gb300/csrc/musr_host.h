@@ -27,12 +27,12 @@ struct Compiled {
 
 // Buffers of the eval entry points and the cached job table of the last launch.
 struct EvalBufs {
-  DevBuf params, out, partials, colsum, counters, jobs;
+  DevBuf params, out, partials, colsum, chunk_val, chunk_count, counters, jobs;
   double* h_in = nullptr;
   double* h_out = nullptr;
   size_t h_in_bytes = 0, h_out_bytes = 0;
   bool key_valid = false;
-  int k_prec = -1, k_mode = -1, k_grad = -1, k_nvec = -1;
+  int k_prec = -1, k_var = -1, k_mode = -1, k_grad = -1, k_nvec = -1;
   const double* k_params = nullptr;
   double* k_out = nullptr;
 };
@@ -83,7 +83,9 @@ struct musr_ctx {
   int nslots = 0, P = 0;
   std::vector<double> consts;
   musr::DevBuf d_map, d_consts;
-  musr::Compiled comp[2];
+  // [precision][decomposition]: decomposition 0 has small tiles (one evaluation
+  // fills the GPU), 1 has large tiles (batched launches, less per-item overhead).
+  musr::Compiled comp[2][2];
   musr::EvalBufs ev;
   int last_grid = 0;
 };

@@ -7,21 +7,30 @@
 // No tensor cores: nothing here is a contraction.
 //
 // Two paths:
-//   * FP64 ("plain"): one CTA per (histogram, tile); every per-bin operation in
-//     FP64 with the term list interpreted as given (any product of primitives).
-//   * SPLIT: one CTA per (chunk of <= 8 histograms sharing the time grid and
-//     every time-dependent parameter, tile).  For each bin the time-only factors
-//     (muon decay, relaxations, Kubo-Toyabe, the precession's cos/sin) are
-//     computed once and reused by the chunk's histograms; the per-histogram
-//     phase enters by a rotation.  Per-bin work is FP32 (hardware ex2, lg2, rcp,
-//     sin, cos); the precession phase is range-reduced in FP64 once per tile
-//     and carried per bin as an exact FP32 split of the phase step; thread sums
-//     are FP32 (Kahan-compensated for the cost value), every sum above the warp
-//     (block, job) is FP64.
+//   * FP64 ("plain"): one work item is a tile of one histogram; every per-bin
+//     operation in FP64, the term list interpreted as given (any product of
+//     primitives).
+//   * SPLIT: one work item is a tile of a chunk of <= 8 histograms that share
+//     the time grid and every time-dependent parameter.  For each bin the
+//     time-only factors (muon decay, relaxations, Kubo-Toyabe, the precession's
+//     cos/sin) are computed once and reused by the chunk's histograms; the
+//     per-histogram phase enters by a rotation.  Per-bin work is FP32 (hardware
+//     ex2, lg2, rcp, sin, cos); the precession phase is range-reduced in FP64
+//     once per tile and carried per bin as an exact FP32 split of the phase step.
 //
-// Both paths write one FP64 partial row per work item; the CTA that completes
-// a job's last item sums the rows in item order (deterministic) and scatters
-// slot derivatives to global parameters through the map.
+// Reductions.  FP64 runs ~60x slower than FP32 per warp instruction on this
+// GPU, so it is kept where it buys accuracy and out of every per-bin and
+// per-lane path: thread sums are FP32 (the cost value Kahan-compensated), warp
+// sums FP32 (the value as a compensated float-float pair), the sum over the
+// CTA's warps is FP64, and so is every sum over work items, chunks and the
+// final scatter to parameters.
+//
+// Completion.  Each item writes one FP64 row of channel sums.  The CTA that
+// completes a chunk's last item sums the chunk's rows in item order and turns
+// channels into slot derivatives; the CTA that completes a job's last chunk
+// sums the chunks in chunk order and scatters slots to parameters through the
+// map.  The result depends on neither the CTA that ran an item nor on other
+// jobs in the launch.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -33,8 +42,8 @@ namespace {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr float kTwoPiF = 6.28318530717958647692f;
-constexpr float kLog2eF = 1.44269504088896340736f;
 constexpr float kLn2F = 0.69314718055994530942f;
+constexpr float kLog2eF = 1.44269504088896340736f;
 constexpr int kMaxChan = 96;
 
 // ---------------------------------------------------------------------------------------------
@@ -65,7 +74,7 @@ __device__ __forceinline__ float cosa(float x) {
   asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-// Round to nearest integer for |x| < 2^22 with two exact-rounding adds.
+// Round to nearest integer for |x| < 2^22 with two exactly rounded adds.
 __device__ __forceinline__ float rint_small(float x) {
   return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
 }
@@ -80,122 +89,195 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// Warp sum of a float-float pair (hi, lo): Knuth's TwoSum on the hi parts.
+__device__ __forceinline__ void warp_sum_ff(float& hi, float& lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    const float s = __fadd_rn(hi, h2);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(l2, e));
+  }
+}
 
 // Local value of slot s of histogram h.
 __device__ __forceinline__ double slot_value(const HistSet& hs, const double* x, int h, int s) {
-  int m = hs.map[static_cast<int64_t>(h) * hs.nslots + s];
+  const int m = hs.map[static_cast<int64_t>(h) * hs.nslots + s];
   return m >= 0 ? x[m] : hs.consts[-1 - m];
 }
 
 // ---------------------------------------------------------------------------------------------
 // Shared memory
 // ---------------------------------------------------------------------------------------------
-struct FinSmem {
-  double wred[kWarps];
-  int last;
+
+// Chunk-level constants, cached while a CTA stays on one chunk of one job.
+struct ChunkCache {
+  int job, chunk;  // cache key (-1: empty)
+  int nh, nlo, nhi, tile0, item0, ntiles, col0, first;
+  double t0;
+  int row[kGroupMax];
+  double loc[kGroupMax][kMaxSlots];  // local slot values (FP64)
+  // SPLIT per-histogram FP32 constants
+  float n0[kGroupMax], bkg[kGroupMax];
+  float amp[kMaxTerms][kGroupMax], cph[kMaxTerms][kGroupMax], sph[kMaxTerms][kGroupMax];
+  // SPLIT per-term constants of the chunk
+  int kinds[kMaxTerms];
+  float ca[kMaxTerms], cb[kMaxTerms];  // E*X_k = ex2(-(ca t + cb t^2))  (ca includes 1/tau)
+  float dh[kMaxTerms], d2[kMaxTerms];  // KT: g = ex2(-dh t^2), u = d2 t^2
+  float shi[kMaxTerms], slo[kMaxTerms], sstep[kMaxTerms];
+  double nu[kMaxTerms];
+  float aE, dt;
+};
+
+struct TileState {
+  int tile_start;
+  float tbase;
+  float base[kMaxTerms];  // phase (turns, in [-1/2, 1/2]) of each TF term at the tile's first bin
+};
+
+struct Smem {
+  ChunkCache cc;
+  TileState ts;
+  float cred[kWarps][kMaxChan];  // per-warp FP32 channel sums
+  float vred[kWarps][2];         // per-warp float-float value
+  double dred[kWarps][kFp64Channels + 2];
+  double tot[kMaxChan + 1];      // chunk totals in the chunk finalize
+  double wsum[kWarps];
+  int flag;
   int bad;
 };
 
-struct Fp64Smem {
-  double loc[kMaxSlots];
-  double red[kWarps][36];
-  int h, nlo, nhi, tile_start;
-  double t0;
-};
-
-struct SplitSmem {
-  float n0[kGroupMax], bkg[kGroupMax];
-  float amp[kMaxTerms][kGroupMax], cph[kMaxTerms][kGroupMax], sph[kMaxTerms][kGroupMax];
-  int row[kGroupMax];
-  double loc[kGroupMax][kMaxSlots];
-  float ca[kMaxTerms], cb[kMaxTerms];  // EX_k = ex2(-(ca t + cb t^2))  (includes 1/tau)
-  float dh[kMaxTerms], d2[kMaxTerms];  // KT: g = ex2(-dh t^2), u = d2 t^2
-  float shi[kMaxTerms], slo[kMaxTerms], sstep[kMaxTerms], base[kMaxTerms];
-  int kinds[kMaxTerms];
-  float aE, tbase, dt;
-  int nlo, nhi, tile_start, nh, nterms;
-  double red[kWarps][kMaxChan];
-  double chan[kMaxChan];
-};
-
-union KernelSmem {
-  Fp64Smem f64;
-  SplitSmem split;
-};
-
 // ---------------------------------------------------------------------------------------------
-// Job completion: the CTA that finishes the last item of a job reduces its rows.
+// Chunk cache fill (only when a CTA moves to another chunk or job).
 // ---------------------------------------------------------------------------------------------
-__device__ double block_sum_fixed(double v, FinSmem& fs) {
-  v = warp_sum_d(v);
-  int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) fs.wred[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < kWarps; ++i) s += fs.wred[i];
-    fs.wred[0] = s;
-  }
-  __syncthreads();
-  s = fs.wred[0];
-  __syncthreads();
-  return s;
-}
-
-__device__ void finalize_job(const Job& job, const HistSet& hs, FinSmem& fs) {
-  const int ps = hs.pstride;
-  const double* part = job.partials;
-  double v = 0.0;
-  for (int i = threadIdx.x; i < hs.nitems; i += kBlock) v += __ldcg(part + static_cast<int64_t>(i) * ps);
-  double value = block_sum_fixed(v, fs);
-  bool finite = isfinite(value);
-  if (job.grad) {
-    for (int c = threadIdx.x; c < hs.ncols; c += kBlock) {
-      const Chunk ch = hs.chunks[hs.col_chunk[c]];
-      int local = c - ch.col0;
-      double s = 0.0;
-      for (int t = 0; t < ch.ntiles; ++t)
-        s += __ldcg(part + static_cast<int64_t>(ch.item0 + t) * ps + 1 + local);
-      job.colsum[c] = s;
-    }
-    __syncthreads();
-    for (int p = threadIdx.x; p < hs.P; p += kBlock) {
-      double g = 0.0;
-      for (int j = hs.p_ptr[p]; j < hs.p_ptr[p + 1]; ++j) g += job.colsum[hs.p_cols[j]];
-      job.out[1 + p] = finite ? g : 0.0;
-    }
-  }
-  if (threadIdx.x == 0) {
-    job.out[0] = value;
-    *job.counter = 0u;
-  }
-}
-
-// ---------------------------------------------------------------------------------------------
-// FP64 path: one histogram per item, every operation in FP64, term list as given.
-// ---------------------------------------------------------------------------------------------
-template <int MODE, bool GRAD>
-__device__ void fp64_item(const Job& job, const HistSet& hs, int item, Fp64Smem& sm, FinSmem& fs) {
+__device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int chunk_index, int prec,
+                           Smem& sm) {
+  ChunkCache& cc = sm.cc;
   const int tid = threadIdx.x;
   if (tid == 0) {
-    int2 it = hs.items[item];
-    const Chunk ch = hs.chunks[it.x];
-    sm.h = hs.hist_index[ch.first];
-    sm.nlo = ch.nlo;
-    sm.nhi = ch.nhi;
-    sm.tile_start = ch.tile0 + it.y * hs.tile_bins;
-    sm.t0 = ch.t0;
+    const Chunk ch = hs.chunks[chunk_index];
+    cc.job = job_index;
+    cc.chunk = chunk_index;
+    cc.nh = ch.nh;
+    cc.nlo = ch.nlo;
+    cc.nhi = ch.nhi;
+    cc.tile0 = ch.tile0;
+    cc.item0 = ch.item0;
+    cc.ntiles = ch.ntiles;
+    cc.col0 = ch.col0;
+    cc.first = ch.first;
+    cc.t0 = ch.t0;
   }
   __syncthreads();
-  if (tid < hs.nslots) sm.loc[tid] = slot_value(hs, job.params, sm.h, tid);
+  const int nh = cc.nh, nsl = hs.nslots;
+  for (int i = tid; i < nh * nsl; i += kBlock) {
+    const int hl = i / nsl, s = i - hl * nsl;
+    const int h = hs.hist_index[cc.first + hl];
+    cc.loc[hl][s] = slot_value(hs, job.params, h, s);
+    if (s == 0) cc.row[hl] = h;
+  }
   __syncthreads();
+  if (prec == 0) return;
+  const double dt = hs.dt_us;
+  if (tid < nh) {
+    const int hl = tid;
+    cc.n0[hl] = static_cast<float>(cc.loc[hl][0]);
+    cc.bkg[hl] = static_cast<float>(cc.loc[hl][1]);
+#pragma unroll
+    for (int k = 0; k < kMaxTerms; ++k) {
+      float a = 0.0f, c = 1.0f, s = 0.0f;
+      if (k < hs.nterms) {
+        const CanonTerm& ct = hs.canon[k];
+        a = ct.amp_slot >= 0 ? static_cast<float>(cc.loc[hl][ct.amp_slot]) : 1.0f;
+        if (ct.kind == kTermTF) {
+          const double x = cc.loc[hl][ct.phi_slot] * (1.0 / 360.0);  // phase in turns (FP64)
+          const float r = static_cast<float>(x - rint(x));
+          sincospif(2.0f * r, &s, &c);
+        }
+      }
+      cc.amp[k][hl] = a;
+      cc.cph[k][hl] = c;
+      cc.sph[k][hl] = s;
+    }
+  } else if (tid >= 32 && tid < 32 + kMaxTerms) {
+    const int k = tid - 32;
+    cc.kinds[k] = k < hs.nterms ? hs.canon[k].kind : kTermNone;
+    if (k < hs.nterms) {
+      const CanonTerm& ct = hs.canon[k];
+      float lam = 0.0f, S = 0.0f;
+      for (int i = 0; i < ct.nexp; ++i) lam += static_cast<float>(cc.loc[0][ct.exp_slot[i]]);
+      for (int i = 0; i < ct.ngauss; ++i) {
+        const float sg = static_cast<float>(cc.loc[0][ct.gauss_slot[i]]);
+        S = fmaf(sg, sg, S);
+      }
+      cc.ca[k] = kLog2eF * (static_cast<float>(1.0 / kTauMuUs) + lam);
+      cc.cb[k] = kLog2eF * 0.5f * S;
+      if (ct.kind == kTermKT) {
+        const float D = static_cast<float>(cc.loc[0][ct.kt_slot]);
+        cc.d2[k] = D * D;
+        cc.dh[k] = kLog2eF * 0.5f * D * D;
+      } else {
+        cc.d2[k] = cc.dh[k] = 0.0f;
+      }
+      if (ct.kind == kTermTF) {
+        const double nu = cc.loc[0][ct.nu_slot];
+        const double step = nu * dt;  // turns per bin (FP64)
+        // Exact split: hi keeps 10 significant bits, so (bin offset < 2^14) * hi is exact in FP32.
+        const float hi = __uint_as_float(__float_as_uint(static_cast<float>(step)) & 0xFFFFC000u);
+        cc.shi[k] = hi;
+        cc.slo[k] = static_cast<float>(step - static_cast<double>(hi));
+        cc.sstep[k] = static_cast<float>(step);
+        cc.nu[k] = nu;
+      } else {
+        cc.shi[k] = cc.slo[k] = cc.sstep[k] = 0.0f;
+        cc.nu[k] = 0.0;
+      }
+    }
+  } else if (tid == 64) {
+    cc.aE = static_cast<float>(1.4426950408889634 / kTauMuUs);
+    cc.dt = static_cast<float>(dt);
+  }
+  __syncthreads();
+}
 
-  const int h = sm.h, nlo = sm.nlo, nhi = sm.nhi, ts = sm.tile_start;
-  const double t0 = sm.t0, dt = hs.dt_us;
+// Tile-level constants: the tile's first bin time and, in FP64, each precession
+// phase at that bin reduced to [-1/2, 1/2] turns.
+__device__ void load_tile(const HistSet& hs, int tile, int prec, Smem& sm) {
+  const int tid = threadIdx.x;
+  if (tid == 0) sm.ts.tile_start = sm.cc.tile0 + tile * hs.tile_bins;
+  if (prec == 1 && tid >= 32 && tid < 32 + kMaxTerms) {
+    const int k = tid - 32;
+    const int ts = sm.cc.tile0 + tile * hs.tile_bins;
+    const double t_start = (static_cast<double>(ts) - sm.cc.t0) * hs.dt_us;
+    if (k == 0) sm.ts.tbase = static_cast<float>(t_start);
+    float b = 0.0f;
+    if (sm.cc.kinds[k] == kTermTF) {
+      const double x = sm.cc.nu[k] * t_start;
+      b = static_cast<float>(x - rint(x));
+    }
+    sm.ts.base[k] = b;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------------
+// FP64 path: one histogram per chunk, every operation in FP64, term list as given.
+// Row: [value, N0, Nbkg, d/d(term k, primitive m, slot q)...].
+// ---------------------------------------------------------------------------------------------
+template <int MODE, bool GRAD>
+__device__ void fp64_item(const Job& job, const HistSet& hs, int item, Smem& sm) {
+  const int tid = threadIdx.x;
+  const ChunkCache& cc = sm.cc;
+  const int h = cc.row[0], nlo = cc.nlo, nhi = cc.nhi, ts = sm.ts.tile_start;
+  const double t0 = cc.t0, dt = hs.dt_us;
   const int nterms = hs.nterms;
-  const double N0 = sm.loc[0], Nbkg = sm.loc[1];
+  const double N0 = cc.loc[0][0], Nbkg = cc.loc[0][1];
   const float* rowf = static_cast<const float*>(hs.counts) + static_cast<int64_t>(h) * hs.stride;
   const double* rowd = static_cast<const double*>(hs.counts) + static_cast<int64_t>(h) * hs.stride;
+  const int store = hs.store;
 
   double acc_v = 0.0, acc_n0 = 0.0, acc_bkg = 0.0;
   double acc_p[kMaxTerms][kMaxPrims][2];
@@ -204,7 +286,6 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Fp64Smem&
 #pragma unroll
     for (int m = 0; m < kMaxPrims; ++m) acc_p[k][m][0] = acc_p[k][m][1] = 0.0;
   int bad = 0;
-  const int store = hs.store;
 
   const int end = min(nhi, ts + hs.tile_bins);
   for (int n = ts + tid; n < end; n += kBlock) {
@@ -227,7 +308,7 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Fp64Smem&
         df[m][0] = df[m][1] = 0.0;
         if (m >= np) continue;
         const int kind = hs.raw[k].kind[m];
-        const double p0 = sm.loc[hs.raw[k].slot[m][0]];
+        const double p0 = cc.loc[0][hs.raw[k].slot[m][0]];
         if (kind == kAmp) {
           f[m] = p0;
           df[m][0] = 1.0;
@@ -245,7 +326,7 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Fp64Smem&
           f[m] = 1.0 / 3.0 + (2.0 / 3.0) * (1.0 - u) * g;
           df[m][0] = (2.0 / 3.0) * p0 * t * t * g * (u - 3.0);
         } else if (kind == kTFCos) {
-          const double p1 = sm.loc[hs.raw[k].slot[m][1]];
+          const double p1 = cc.loc[0][hs.raw[k].slot[m][1]];
           // Phase in turns, range-reduced exactly before sin/cos.
           const double x = p0 * t + p1 / 360.0;
           const double r = x - rint(x);
@@ -305,16 +386,16 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Fp64Smem&
     }
   }
 
-  // Block reduction in FP64 (warp shuffle, then warps in a fixed order).
+  // Warp (FP64 shuffles), then the CTA's warps in a fixed order (FP64).
   bad = __syncthreads_or(bad);
   const int w = tid >> 5, lane = tid & 31;
-  double r0 = warp_sum_d(acc_v);
-  if (lane == 0) sm.red[w][0] = r0;
+  const double r0 = warp_sum_d(acc_v);
+  if (lane == 0) sm.dred[w][0] = r0;
   if (GRAD) {
-    double r1 = warp_sum_d(acc_n0), r2 = warp_sum_d(acc_bkg);
+    const double r1 = warp_sum_d(acc_n0), r2 = warp_sum_d(acc_bkg);
     if (lane == 0) {
-      sm.red[w][1] = r1;
-      sm.red[w][2] = r2;
+      sm.dred[w][1] = r1;
+      sm.dred[w][2] = r2;
     }
 #pragma unroll
     for (int k = 0; k < kMaxTerms; ++k)
@@ -322,36 +403,32 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Fp64Smem&
       for (int m = 0; m < kMaxPrims; ++m)
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          double r = warp_sum_d(acc_p[k][m][q]);
-          if (lane == 0) sm.red[w][3 + (k * kMaxPrims + m) * 2 + q] = r;
+          const double r = warp_sum_d(acc_p[k][m][q]);
+          if (lane == 0) sm.dred[w][3 + (k * kMaxPrims + m) * 2 + q] = r;
         }
   }
   __syncthreads();
   double* row = job.partials + static_cast<int64_t>(item) * hs.pstride;
-  if (tid == 0) {
+  const int nout = GRAD ? 1 + kFp64Channels : 1;
+  for (int c = tid; c < nout; c += kBlock) {
     double s = 0.0;
-    for (int i = 0; i < kWarps; ++i) s += sm.red[i][0];
-    row[0] = bad ? __longlong_as_double(0x7ff0000000000000LL) : s;
+    for (int i = 0; i < kWarps; ++i) s += sm.dred[i][c];
+    if (c == 0 && bad) s = __longlong_as_double(0x7ff0000000000000LL);
+    row[c] = s;
   }
-  if (GRAD && tid < hs.nslots) {
-    // Channel -> slot: N0 is slot 0, Nbkg slot 1, primitives add to their slots.
-    double tot[3 + kMaxTerms * kMaxPrims * 2];
-    for (int c = 0; c < 3 + kMaxTerms * kMaxPrims * 2; ++c) {
-      double s = 0.0;
-      for (int i = 0; i < kWarps; ++i) s += sm.red[i][c];
-      tot[c] = s;
+}
+
+// FP64 channels -> slot derivatives of the chunk's histogram.
+__device__ double fp64_slot(const HistSet& hs, const double* tot, int s) {
+  double g = 0.0;
+  if (s == 0) g += tot[1];
+  if (s == 1) g += tot[2];
+  for (int k = 0; k < hs.nterms; ++k)
+    for (int m = 0; m < hs.raw[k].nprim; ++m) {
+      if (hs.raw[k].slot[m][0] == s) g += tot[3 + (k * kMaxPrims + m) * 2 + 0];
+      if (hs.raw[k].kind[m] == kTFCos && hs.raw[k].slot[m][1] == s) g += tot[3 + (k * kMaxPrims + m) * 2 + 1];
     }
-    double g = 0.0;
-    if (tid == 0) g += tot[1];
-    if (tid == 1) g += tot[2];
-    for (int k = 0; k < nterms; ++k)
-      for (int m = 0; m < hs.raw[k].nprim; ++m) {
-        if (hs.raw[k].slot[m][0] == tid) g += tot[3 + (k * kMaxPrims + m) * 2 + 0];
-        if (hs.raw[k].kind[m] == kTFCos && hs.raw[k].slot[m][1] == tid)
-          g += tot[3 + (k * kMaxPrims + m) * 2 + 1];
-      }
-    row[1 + tid] = g;
-  }
+  return g;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -362,149 +439,54 @@ struct ShapeT;
 template <>
 struct ShapeT<kShapeGeneric> {
   static constexpr int NT = 4, G = 4;
-  __device__ static int kind(const SplitSmem& sm, int k) { return sm.kinds[k]; }
-  __device__ static int nterms(const SplitSmem& sm) { return sm.nterms; }
+  __device__ static int kind(const ChunkCache& cc, int k) { return cc.kinds[k]; }
+  __device__ static int nterms(const HistSet& hs) { return hs.nterms; }
 };
 template <>
 struct ShapeT<kShapeTF1> {
   static constexpr int NT = 1, G = 8;
-  __device__ static constexpr int kind(const SplitSmem&, int) { return kTermTF; }
-  __device__ static constexpr int nterms(const SplitSmem&) { return 1; }
+  __device__ static constexpr int kind(const ChunkCache&, int) { return kTermTF; }
+  __device__ static constexpr int nterms(const HistSet&) { return 1; }
 };
 template <>
 struct ShapeT<kShapeTF2> {
   static constexpr int NT = 2, G = 8;
-  __device__ static constexpr int kind(const SplitSmem&, int) { return kTermTF; }
-  __device__ static constexpr int nterms(const SplitSmem&) { return 2; }
+  __device__ static constexpr int kind(const ChunkCache&, int) { return kTermTF; }
+  __device__ static constexpr int nterms(const HistSet&) { return 2; }
 };
 template <>
 struct ShapeT<kShapeKT1> {
   static constexpr int NT = 1, G = 8;
-  __device__ static constexpr int kind(const SplitSmem&, int) { return kTermKT; }
-  __device__ static constexpr int nterms(const SplitSmem&) { return 1; }
+  __device__ static constexpr int kind(const ChunkCache&, int) { return kTermKT; }
+  __device__ static constexpr int nterms(const HistSet&) { return 1; }
 };
 template <>
 struct ShapeT<kShapeTF2KT1> {
   static constexpr int NT = 3, G = 4;
-  __device__ static constexpr int kind(const SplitSmem&, int k) { return k < 2 ? kTermTF : kTermKT; }
-  __device__ static constexpr int nterms(const SplitSmem&) { return 3; }
+  __device__ static constexpr int kind(const ChunkCache&, int k) { return k < 2 ? kTermTF : kTermKT; }
+  __device__ static constexpr int nterms(const HistSet&) { return 3; }
+};
+template <int S>
+struct ShapeChan {
+  static constexpr int NPH = 2 + 2 * ShapeT<S>::NT;  // per histogram: N0, bkg, amp[k], phi[k]
+  static constexpr int NSH = 4 * ShapeT<S>::NT;      // shared per term: Lambda, S, nu, Delta
+  static constexpr int N = ShapeT<S>::G * NPH + NSH;
+  static_assert(N <= kMaxChan, "channel count");
 };
 
-// Per-item set-up: local slot values, per-histogram FP32 constants and the
-// shared time-factor coefficients of the chunk, including the FP64 range
-// reduction of each precession phase at the tile's first bin.
-template <int SHAPE>
-__device__ void split_prologue(const Job& job, const HistSet& hs, int item, SplitSmem& sm) {
-  using Sh = ShapeT<SHAPE>;
-  const int tid = threadIdx.x;
-  __shared__ int s_first;
-  __shared__ double s_t0;
-  if (tid == 0) {
-    int2 it = hs.items[item];
-    const Chunk ch = hs.chunks[it.x];
-    sm.nh = ch.nh;
-    sm.nlo = ch.nlo;
-    sm.nhi = ch.nhi;
-    sm.tile_start = ch.tile0 + it.y * hs.tile_bins;
-    sm.nterms = hs.nterms;
-    s_first = ch.first;
-    s_t0 = ch.t0;
-  }
-  __syncthreads();
-  const int nh = sm.nh, nsl = hs.nslots;
-  for (int i = tid; i < nh * nsl; i += kBlock) {
-    int hl = i / nsl, s = i - hl * nsl;
-    int h = hs.hist_index[s_first + hl];
-    sm.loc[hl][s] = slot_value(hs, job.params, h, s);
-    if (s == 0) sm.row[hl] = h;
-  }
-  if (tid < kMaxTerms) sm.kinds[tid] = tid < hs.nterms ? hs.canon[tid].kind : kTermNone;
-  __syncthreads();
-  const double dt = hs.dt_us;
-  const double t_start = (static_cast<double>(sm.tile_start) - s_t0) * dt;
-  if (tid < nh) {
-    const int hl = tid;
-    sm.n0[hl] = static_cast<float>(sm.loc[hl][0]);
-    sm.bkg[hl] = static_cast<float>(sm.loc[hl][1]);
-#pragma unroll
-    for (int k = 0; k < kMaxTerms; ++k) {
-      float a = 0.0f, c = 1.0f, s = 0.0f;
-      if (k < hs.nterms) {
-        const CanonTerm& ct = hs.canon[k];
-        a = ct.amp_slot >= 0 ? static_cast<float>(sm.loc[hl][ct.amp_slot]) : 1.0f;
-        if (ct.kind == kTermTF) {
-          double x = sm.loc[hl][ct.phi_slot] / 360.0;  // phase in turns
-          double r = x - rint(x);
-          sincospif(2.0f * static_cast<float>(r), &s, &c);
-        }
-      }
-      sm.amp[k][hl] = a;
-      sm.cph[k][hl] = c;
-      sm.sph[k][hl] = s;
-    }
-  } else if (tid >= 32 && tid < 32 + kMaxTerms) {
-    const int k = tid - 32;
-    if (k < hs.nterms) {
-      const CanonTerm& ct = hs.canon[k];
-      double lam = 0.0, S = 0.0;
-      for (int i = 0; i < ct.nexp; ++i) lam += sm.loc[0][ct.exp_slot[i]];
-      for (int i = 0; i < ct.ngauss; ++i) {
-        double sg = sm.loc[0][ct.gauss_slot[i]];
-        S += sg * sg;
-      }
-      sm.ca[k] = static_cast<float>(1.4426950408889634 * (1.0 / kTauMuUs + lam));
-      sm.cb[k] = static_cast<float>(1.4426950408889634 * 0.5 * S);
-      if (ct.kind == kTermKT) {
-        double D = sm.loc[0][ct.kt_slot];
-        sm.d2[k] = static_cast<float>(D * D);
-        sm.dh[k] = static_cast<float>(1.4426950408889634 * 0.5 * D * D);
-      } else {
-        sm.d2[k] = sm.dh[k] = 0.0f;
-      }
-      if (ct.kind == kTermTF) {
-        const double nu = sm.loc[0][ct.nu_slot];
-        const double step = nu * dt;  // turns per bin
-        // Exact split: hi keeps 11 significant bits, so (bin offset < 2^13) * hi is exact in FP32.
-        double hi = 0.0;
-        if (step != 0.0) {
-          int e;
-          frexp(step, &e);
-          double sc = ldexp(1.0, 11 - e);
-          hi = trunc(step * sc) / sc;
-        }
-        sm.shi[k] = static_cast<float>(hi);
-        sm.slo[k] = static_cast<float>(step - hi);
-        sm.sstep[k] = static_cast<float>(step);
-        double x = nu * t_start;  // FP64 range reduction at the tile's first bin
-        sm.base[k] = static_cast<float>(x - rint(x));
-      } else {
-        sm.shi[k] = sm.slo[k] = sm.sstep[k] = sm.base[k] = 0.0f;
-      }
-    }
-  } else if (tid == 64) {
-    sm.aE = static_cast<float>(1.4426950408889634 / kTauMuUs);
-    sm.tbase = static_cast<float>(t_start);
-    sm.dt = static_cast<float>(dt);
-  }
-  __syncthreads();
-  (void)Sh::NT;
-}
-
 template <int SHAPE, int MODE, bool GRAD>
-__device__ void split_item(const Job& job, const HistSet& hs, int item, SplitSmem& sm, FinSmem& fs) {
+__device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm) {
   using Sh = ShapeT<SHAPE>;
   constexpr int NT = Sh::NT;
   constexpr int G = Sh::G;
-  constexpr int NPH = 2 + 2 * NT;  // per-histogram channels: N0, bkg, amp[k], phi[k]
-  constexpr int NSH = 4 * NT;      // shared channels per term: lambda, S, nu, Delta
-  static_assert(G * NPH + NSH <= kMaxChan, "channel count");
+  constexpr int NPH = ShapeChan<SHAPE>::NPH;
+  constexpr int NCH = ShapeChan<SHAPE>::N;
 
-  split_prologue<SHAPE>(job, hs, item, sm);
-
+  const ChunkCache& cc = sm.cc;
   const int tid = threadIdx.x;
-  const int nh = sm.nh, nlo = sm.nlo, nhi = sm.nhi, ts = sm.tile_start;
-  const int nterms = Sh::nterms(sm);
-  const float aE = sm.aE, tbase = sm.tbase, dtf = sm.dt;
+  const int nh = cc.nh, nlo = cc.nlo, nhi = cc.nhi, ts = sm.ts.tile_start;
+  const int nterms = Sh::nterms(hs);
+  const float aE = cc.aE, tbase = sm.ts.tbase, dtf = cc.dt;
   const void* __restrict__ counts = hs.counts;
   const int64_t stride = hs.stride;
   const int store = hs.store;
@@ -524,7 +506,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, SplitSme
 
   const int iters = hs.tile_bins / (kBlock * kBinsPerThread);
   for (int it = 0; it < iters; ++it) {
-    const int m0 = it * kBlock * kBinsPerThread + tid * kBinsPerThread;  // offset in tile (< 2^13)
+    const int m0 = it * kBlock * kBinsPerThread + tid * kBinsPerThread;  // offset in tile (< 2^14)
     const int n0 = ts + m0;
     if (n0 >= nhi) break;
     float t[4];
@@ -540,37 +522,33 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, SplitSme
     for (int j = 0; j < 4; ++j) E[j] = ex2a(-aE * t[j]);
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
-      const int kk = Sh::kind(sm, k);
-      if (k >= nterms) {
+      const int kk = Sh::kind(cc, k);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) EXK[k][j] = cs[k][j] = sn[k][j] = dk[k][j] = 0.0f;
-        continue;
-      }
-      const float ca = sm.ca[k], cb = sm.cb[k];
+      for (int j = 0; j < 4; ++j) EXK[k][j] = cs[k][j] = sn[k][j] = dk[k][j] = 0.0f;
+      if (k >= nterms) continue;
+      const float ca = cc.ca[k], cb = cc.cb[k];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const float ex = ex2a(-fmaf(cb, t[j], ca) * t[j]);
         EXK[k][j] = ex;
         cs[k][j] = 1.0f;
-        sn[k][j] = 0.0f;
-        dk[k][j] = 0.0f;
         if (kk == kTermKT) {
           const float tt = t[j] * t[j];
-          const float g = ex2a(-sm.dh[k] * tt);
-          const float u = sm.d2[k] * tt;
+          const float g = ex2a(-cc.dh[k] * tt);
+          const float u = cc.d2[k] * tt;
           EXK[k][j] = ex * fmaf((2.0f / 3.0f) * (1.0f - u), g, 1.0f / 3.0f);
           dk[k][j] = ex * tt * g * (u - 3.0f);
         }
       }
       if (kk == kTermTF) {
         // Phase (turns) of the thread's first bin: base + m0 * step, reduced exactly.
-        float f = static_cast<float>(m0) * sm.shi[k];
+        float f = static_cast<float>(m0) * cc.shi[k];
         f = __fsub_rn(f, rint_small(f));
-        float r = fmaf(static_cast<float>(m0), sm.slo[k], sm.base[k]) + f;
+        float r = fmaf(static_cast<float>(m0), cc.slo[k], sm.ts.base[k]) + f;
         r = __fsub_rn(r, rint_small(r));
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          float rj = fmaf(static_cast<float>(j), sm.sstep[k], r);
+          float rj = fmaf(static_cast<float>(j), cc.sstep[k], r);
           rj = __fsub_rn(rj, rint_small(rj));  // |rj| <= 1/2: sin/cos arguments in [-pi, pi]
           const float a = rj * kTwoPiF;
           cs[k][j] = cosa(a);
@@ -588,7 +566,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, SplitSme
     for (int hl = 0; hl < G; ++hl) {
       if (hl >= nh) break;
       float d[4];
-      const int64_t off = static_cast<int64_t>(sm.row[hl]) * stride + n0;
+      const int64_t off = static_cast<int64_t>(cc.row[hl]) * stride + n0;
       if (store == kStoreF32) {
         const float4 q = __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(counts) + off));
         d[0] = q.x;
@@ -603,27 +581,24 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, SplitSme
         d[2] = static_cast<float>(q1.x);
         d[3] = static_cast<float>(q1.y);
       }
-      const float N0 = sm.n0[hl], Nb = sm.bkg[hl];
+      const float N0 = cc.n0[hl], Nb = cc.bkg[hl];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         float C[NT], Sn[NT], Q[NT];
         float M = E[j];
 #pragma unroll
         for (int k = 0; k < NT; ++k) {
-          if (k >= nterms) {
-            C[k] = Sn[k] = Q[k] = 0.0f;
-            continue;
-          }
-          if (Sh::kind(sm, k) == kTermTF) {
-            const float cp = sm.cph[k][hl], sp = sm.sph[k][hl];
+          C[k] = Sn[k] = Q[k] = 0.0f;
+          if (k >= nterms) continue;
+          if (Sh::kind(cc, k) == kTermTF) {
+            const float cp = cc.cph[k][hl], sp = cc.sph[k][hl];
             C[k] = fmaf(cs[k][j], cp, -sn[k][j] * sp);  // cos(theta + phi)
             Sn[k] = fmaf(sn[k][j], cp, cs[k][j] * sp);  // sin(theta + phi)
           } else {
             C[k] = 1.0f;
-            Sn[k] = 0.0f;
           }
           Q[k] = EXK[k][j] * C[k];
-          M = fmaf(sm.amp[k][hl], Q[k], M);
+          M = fmaf(cc.amp[k][hl], Q[k], M);
         }
         const float N = fmaf(N0, M, Nb);
         const float dd = d[j];
@@ -678,9 +653,9 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, SplitSme
           for (int k = 0; k < NT; ++k) {
             if (k >= nterms) continue;
             ph[hl][2 + k] = fmaf(w, Q[k], ph[hl][2 + k]);
-            const float P = wN0 * sm.amp[k][hl];
+            const float P = wN0 * cc.amp[k][hl];
             U[k][j] = fmaf(P, C[k], U[k][j]);
-            if (Sh::kind(sm, k) == kTermTF) {
+            if (Sh::kind(cc, k) == kTermTF) {
               ph[hl][2 + NT + k] = fmaf(w * Sn[k], EXK[k][j], ph[hl][2 + NT + k]);
               V[k][j] = fmaf(P, Sn[k], V[k][j]);
             }
@@ -693,7 +668,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, SplitSme
 #pragma unroll
       for (int k = 0; k < NT; ++k) {
         if (k >= nterms) continue;
-        const int kk = Sh::kind(sm, k);
+        const int kk = Sh::kind(cc, k);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const float ue = U[k][j] * EXK[k][j];
@@ -706,129 +681,221 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, SplitSme
     }
   }
 
-  // ---- reduction: thread (FP32) -> warp (FP32 for gradient channels, FP64 for the value)
-  //      -> block (FP64, warps in fixed order) -> one FP64 row per item.
+  // ---- thread (FP32) -> warp (FP32; the value as float-float) -> CTA (FP64) -> row.
   bad = __syncthreads_or(bad);
   const int w = tid >> 5, lane = tid & 31;
-  double vt = static_cast<double>(acc_v) - static_cast<double>(acc_c);
-  vt = warp_sum_d(vt);
-  constexpr int VCH = G * NPH + NSH;
-  if (lane == 0) sm.red[w][VCH] = vt;
+  float vh = acc_v, vl = -acc_c;
+  warp_sum_ff(vh, vl);
+  if (lane == 0) {
+    sm.vred[w][0] = vh;
+    sm.vred[w][1] = vl;
+  }
   if (GRAD) {
 #pragma unroll
     for (int hl = 0; hl < G; ++hl)
 #pragma unroll
       for (int q = 0; q < NPH; ++q) {
-        float r = warp_sum_f(ph[hl][q]);
-        if (lane == 0) sm.red[w][hl * NPH + q] = static_cast<double>(r);
+        const float r = warp_sum_f(ph[hl][q]);
+        if (lane == 0) sm.cred[w][hl * NPH + q] = r;
       }
 #pragma unroll
     for (int k = 0; k < NT; ++k)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        float r = warp_sum_f(sh[k][q]);
-        if (lane == 0) sm.red[w][G * NPH + k * 4 + q] = static_cast<double>(r);
+        const float r = warp_sum_f(sh[k][q]);
+        if (lane == 0) sm.cred[w][G * NPH + k * 4 + q] = r;
       }
-  }
-  __syncthreads();
-  for (int c = tid; c <= (GRAD ? VCH : 0); c += kBlock) {
-    const int cc = GRAD ? c : VCH;
-    double s = 0.0;
-    for (int i = 0; i < kWarps; ++i) s += sm.red[i][cc];
-    sm.chan[cc] = s;
   }
   __syncthreads();
   double* row = job.partials + static_cast<int64_t>(item) * hs.pstride;
-  if (tid == 0) {
-    const double val = sm.chan[VCH] * (MODE == 1 ? 2.0 : 1.0);
-    row[0] = bad ? __longlong_as_double(0x7ff0000000000000LL) : val;
+  if (GRAD && tid < NCH) {
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < kWarps; ++i) s += static_cast<double>(sm.cred[i][tid]);
+    row[1 + tid] = s;
   }
-  if (GRAD) {
-    const int nsl = hs.nslots;
-    for (int i = tid; i < G * nsl; i += kBlock) {
-      const int hl = i / nsl, s = i - hl * nsl;
-      double g = 0.0;
-      if (hl < nh) {
-        const double N0 = sm.loc[hl][0];
-        for (int e = 0; e < hs.ncontrib; ++e) {
-          const Contrib c = hs.contrib[e];
-          if (c.slot != s) continue;
-          const int k = c.term;
-          switch (c.kind) {
-            case kCN0:
-              g += 2.0 * sm.chan[hl * NPH + 0];
-              break;
-            case kCBkg:
-              g += 2.0 * sm.chan[hl * NPH + 1];
-              break;
-            case kCAmp:
-              g += 2.0 * N0 * sm.chan[hl * NPH + 2 + k];
-              break;
-            case kCPhi: {
-              const int as = hs.canon[k].amp_slot;
-              const double a = as >= 0 ? sm.loc[hl][as] : 1.0;
-              g += 2.0 * N0 * a * (-kTwoPi / 360.0) * sm.chan[hl * NPH + 2 + NT + k];
-              break;
-            }
-            case kCLam:
-              if (hl == 0) g += 2.0 * sm.chan[G * NPH + k * 4 + 0];
-              break;
-            case kCSig:
-              if (hl == 0) g += 4.0 * sm.loc[0][s] * sm.chan[G * NPH + k * 4 + 1];
-              break;
-            case kCNu:
-              if (hl == 0) g += 2.0 * sm.chan[G * NPH + k * 4 + 2];
-              break;
-            case kCDel:
-              if (hl == 0) g += (4.0 / 3.0) * sm.loc[0][s] * sm.chan[G * NPH + k * 4 + 3];
-              break;
-            default:
-              break;
-          }
-        }
+  if (tid == kBlock - 1) {
+    static_assert(NCH < kBlock - 1, "value thread overlaps a channel thread");
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < kWarps; ++i) s += static_cast<double>(sm.vred[i][0]) + static_cast<double>(sm.vred[i][1]);
+    row[0] = bad ? __longlong_as_double(0x7ff0000000000000LL) : s * (MODE == 1 ? 2.0 : 1.0);
+  }
+}
+
+// SPLIT channels -> derivative of local slot s of chunk histogram hl.
+template <int SHAPE>
+__device__ double split_slot(const HistSet& hs, const ChunkCache& cc, const double* tot, int hl, int s) {
+  constexpr int NT = ShapeT<SHAPE>::NT;
+  constexpr int G = ShapeT<SHAPE>::G;
+  constexpr int NPH = ShapeChan<SHAPE>::NPH;
+  const double* ch = tot + 1;
+  const double N0 = cc.loc[hl][0];
+  double g = 0.0;
+  for (int e = 0; e < hs.ncontrib; ++e) {
+    const Contrib c = hs.contrib[e];
+    if (c.slot != s) continue;
+    const int k = c.term;
+    switch (c.kind) {
+      case kCN0:
+        g += 2.0 * ch[hl * NPH + 0];
+        break;
+      case kCBkg:
+        g += 2.0 * ch[hl * NPH + 1];
+        break;
+      case kCAmp:
+        g += 2.0 * N0 * ch[hl * NPH + 2 + k];
+        break;
+      case kCPhi: {
+        const int as = hs.canon[k].amp_slot;
+        const double a = as >= 0 ? cc.loc[hl][as] : 1.0;
+        g += 2.0 * N0 * a * (-kTwoPi / 360.0) * ch[hl * NPH + 2 + NT + k];
+        break;
       }
-      row[1 + i] = g;
+      case kCLam:
+        if (hl == 0) g += 2.0 * ch[G * NPH + k * 4 + 0];
+        break;
+      case kCSig:
+        if (hl == 0) g += 4.0 * cc.loc[0][s] * ch[G * NPH + k * 4 + 1];
+        break;
+      case kCNu:
+        if (hl == 0) g += 2.0 * ch[G * NPH + k * 4 + 2];
+        break;
+      case kCDel:
+        if (hl == 0) g += (4.0 / 3.0) * cc.loc[0][s] * ch[G * NPH + k * 4 + 3];
+        break;
+      default:
+        break;
     }
   }
-  (void)fs;
+  return g;
 }
 
 // ---------------------------------------------------------------------------------------------
-// Persistent kernel: items of all jobs, strided over the grid.
+// Completion: chunk finalize, then job finalize.
+// ---------------------------------------------------------------------------------------------
+template <int PREC, int SHAPE, bool GRAD>
+__device__ void chunk_finalize(const Job& job, const HistSet& hs, Smem& sm) {
+  const ChunkCache& cc = sm.cc;
+  const int tid = threadIdx.x;
+  const int ps = hs.pstride;
+  const int nout = GRAD ? 1 + hs.nch : 1;
+  const double* part = job.partials + static_cast<int64_t>(cc.item0) * ps;
+  for (int c = tid; c < nout; c += kBlock) {
+    double s = 0.0;
+    for (int t = 0; t < cc.ntiles; ++t) s += __ldcg(part + static_cast<int64_t>(t) * ps + c);
+    sm.tot[c] = s;
+  }
+  __syncthreads();
+  if (GRAD) {
+    const int nsl = hs.nslots;
+    for (int i = tid; i < cc.nh * nsl; i += kBlock) {
+      const int hl = i / nsl, s = i - hl * nsl;
+      double g;
+      if (PREC == 0)
+        g = fp64_slot(hs, sm.tot, s);
+      else
+        g = split_slot<SHAPE>(hs, cc, sm.tot, hl, s);
+      job.colsum[cc.col0 + i] = g;
+    }
+  }
+  if (tid == 0) {
+    job.chunk_val[cc.chunk] = sm.tot[0];
+    job.chunk_count[cc.chunk] = 0u;
+  }
+}
+
+__device__ void job_finalize(const Job& job, const HistSet& hs, Smem& sm) {
+  const int tid = threadIdx.x;
+  double v = 0.0;
+  for (int c = tid; c < hs.nchunks; c += kBlock) v += __ldcg(job.chunk_val + c);
+  v = warp_sum_d(v);
+  if ((tid & 31) == 0) sm.wsum[tid >> 5] = v;
+  __syncthreads();
+  double value = 0.0;
+#pragma unroll
+  for (int i = 0; i < kWarps; ++i) value += sm.wsum[i];
+  const bool finite = isfinite(value);
+  if (job.grad) {
+    for (int p = tid; p < hs.P; p += kBlock) {
+      double g = 0.0;
+      for (int j = hs.p_ptr[p]; j < hs.p_ptr[p + 1]; ++j) g += __ldcg(job.colsum + hs.p_cols[j]);
+      job.out[1 + p] = finite ? g : 0.0;
+    }
+  }
+  if (tid == 0) {
+    job.out[0] = value;
+    *job.counter = 0u;
+  }
+}
+
+template <int PREC, int SHAPE, bool GRAD>
+__device__ void complete_item(const Job& job, const HistSet& hs, Smem& sm) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(job.chunk_count + sm.cc.chunk, 1u);
+    sm.flag = prev == static_cast<unsigned>(sm.cc.ntiles - 1);
+  }
+  __syncthreads();
+  if (!sm.flag) return;
+  __threadfence();
+  chunk_finalize<PREC, SHAPE, GRAD>(job, hs, sm);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(job.counter, 1u);
+    sm.flag = prev == static_cast<unsigned>(hs.nchunks - 1);
+  }
+  __syncthreads();
+  if (!sm.flag) return;
+  __threadfence();
+  job_finalize(job, hs, sm);
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Persistent kernel: each CTA takes a contiguous range of the launch's items.
 // ---------------------------------------------------------------------------------------------
 template <int PREC, int SHAPE, int MODE, bool GRAD>
 __global__ void __launch_bounds__(kBlock) eval_kernel(const Job* __restrict__ jobs, int njobs,
                                                       int total_items) {
-  __shared__ KernelSmem sm;
-  __shared__ FinSmem fs;
-  for (int gi = blockIdx.x; gi < total_items; gi += gridDim.x) {
-    int lo = 0, hi = njobs - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (jobs[mid].item_begin <= gi)
-        lo = mid;
-      else
-        hi = mid - 1;
+  __shared__ Smem sm;
+  const int per = (total_items + gridDim.x - 1) / gridDim.x;
+  const int beg = blockIdx.x * per;
+  const int end = min(total_items, beg + per);
+  if (threadIdx.x == 0) {
+    sm.cc.job = -1;
+    sm.cc.chunk = -1;
+  }
+  __syncthreads();
+  int ji = -1;
+  Job job;
+  for (int gi = beg; gi < end; ++gi) {
+    if (ji < 0 || gi >= job.item_begin + job.hs->nitems) {
+      int lo = 0, hi = njobs - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].item_begin <= gi)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      ji = lo;
+      job = jobs[ji];
     }
-    const Job job = jobs[lo];
     const HistSet& hs = *job.hs;
     const int item = gi - job.item_begin;
+    if (sm.cc.job != ji || item < sm.cc.item0 || item >= sm.cc.item0 + sm.cc.ntiles) {
+      __syncthreads();
+      load_chunk(job, hs, ji, hs.items[item].x, PREC, sm);
+    }
+    load_tile(hs, item - sm.cc.item0, PREC, sm);
     if (PREC == 0)
-      fp64_item<MODE, GRAD>(job, hs, item, sm.f64, fs);
+      fp64_item<MODE, GRAD>(job, hs, item, sm);
     else
-      split_item<SHAPE, MODE, GRAD>(job, hs, item, sm.split, fs);
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const unsigned prev = atomicAdd(job.counter, 1u);
-      fs.last = (prev == static_cast<unsigned>(hs.nitems - 1));
-    }
-    __syncthreads();
-    if (fs.last) {
-      __threadfence();
-      finalize_job(job, hs, fs);
-    }
-    __syncthreads();
+      split_item<SHAPE, MODE, GRAD>(job, hs, item, sm);
+    complete_item<PREC, SHAPE, GRAD>(job, hs, sm);
   }
 }
 
@@ -887,6 +954,21 @@ int shape_group(int shape) {
       return ShapeT<kShapeTF2KT1>::G;
     default:
       return ShapeT<kShapeGeneric>::G;
+  }
+}
+
+int shape_channels(int shape) {
+  switch (shape) {
+    case kShapeTF1:
+      return ShapeChan<kShapeTF1>::N;
+    case kShapeTF2:
+      return ShapeChan<kShapeTF2>::N;
+    case kShapeKT1:
+      return ShapeChan<kShapeKT1>::N;
+    case kShapeTF2KT1:
+      return ShapeChan<kShapeTF2KT1>::N;
+    default:
+      return ShapeChan<kShapeGeneric>::N;
   }
 }
 
