@@ -224,6 +224,10 @@ int compile(musr_ctx* ctx, int prec, int var) {
       hs.shape = musr::kShapeTF2KT1;
     else
       hs.shape = musr::kShapeGeneric;
+    if (musr::amplitudes_constant(hs.canon, hs.nterms, ctx->map.data(), ctx->H, ctx->nslots)) {
+      if (hs.shape == musr::kShapeTF2) hs.shape = musr::kShapeTF2c;
+      if (hs.shape == musr::kShapeTF2KT1) hs.shape = musr::kShapeTF2KT1c;
+    }
     group_cap = musr::shape_group(hs.shape);
     // Slot -> channel contributions.
     auto add = [&](int slot, int kind, int term) {
@@ -307,7 +311,7 @@ int compile(musr_ctx* ctx, int prec, int var) {
   const int per_iter = prec == MUSR_SPLIT ? musr::kBlock * musr::kBinsPerThread : musr::kBlock;
   std::vector<int64_t> ranges;
   for (const auto& ch : chunks) ranges.push_back(ch.nhi - ch.tile0);
-  const int iters = var == 0 ? pick_iters(ranges, per_iter, 4 * ctx->num_sms) : 16;
+  const int iters = var == 0 ? pick_iters(ranges, per_iter, 4 * ctx->num_sms) : musr::coarse_iters(prec);
   hs.tile_bins = per_iter * iters;
   std::vector<int2> items;
   int col = 0;

@@ -23,7 +23,8 @@ namespace musr {
 constexpr double kTauMuUs = 2.197019;  // muon lifetime, microseconds
 constexpr int kBlock = 256;            // threads per CTA
 constexpr int kWarps = kBlock / 32;
-constexpr int kBinsPerThread = 4;      // one 16-byte load of FP32 counts per histogram
+constexpr int kBinsPerThread = 2;      // SPLIT: one 8-byte load of FP32 counts per histogram
+constexpr int kMaxTileBins = 16384;    // SPLIT phase split: bin offsets in a tile stay below 2^14
 constexpr int kGroupMax = 8;           // histograms per SPLIT chunk
 constexpr int kMaxTerms = 4;
 constexpr int kMaxPrims = 4;
@@ -35,7 +36,17 @@ enum PrimKind : int { kAmp = 1, kExp = 2, kGauss = 3, kKT = 4, kTFCos = 5 };
 enum TermKind : int { kTermNone = 0, kTermPlain = 1, kTermTF = 2, kTermKT = 3 };
 
 // SPLIT shape identifiers (which compile-time specialisation runs a HistSet).
-enum Shape : int { kShapeGeneric = 0, kShapeTF1 = 1, kShapeTF2 = 2, kShapeKT1 = 3, kShapeTF2KT1 = 4 };
+// The "c" shapes are the same term lists with every amplitude a constant (no
+// amplitude gradient channels).
+enum Shape : int {
+  kShapeGeneric = 0,
+  kShapeTF1 = 1,
+  kShapeTF2 = 2,
+  kShapeKT1 = 3,
+  kShapeTF2KT1 = 4,
+  kShapeTF2c = 5,
+  kShapeTF2KT1c = 6
+};
 
 // A term as given: the product of nprim primitives (FP64 path).
 struct RawTerm {
@@ -58,6 +69,16 @@ struct CanonTerm {
   int nu_slot;   // kTermTF
   int phi_slot;  // kTermTF
 };
+
+// True when no amplitude slot of the canonical terms maps to a parameter.
+inline bool amplitudes_constant(const CanonTerm* canon, int nterms, const int32_t* map, int H, int nslots) {
+  for (int k = 0; k < nterms; ++k) {
+    if (canon[k].amp_slot < 0) continue;
+    for (int h = 0; h < H; ++h)
+      if (map[static_cast<int64_t>(h) * nslots + canon[k].amp_slot] >= 0) return false;
+  }
+  return true;
+}
 
 // How a SPLIT channel turns into the derivative of one local slot.
 enum ContribKind : int {
@@ -146,6 +167,10 @@ struct LaunchInfo {
 int launch_eval(int precision, int shape, int mode, int grad, const Job* d_jobs, int njobs,
                 int total_items, int num_sms, void* stream, LaunchInfo* info);
 int max_ctas_per_sm(int precision, int shape, int mode, int grad);
+// CTA iterations per tile of the large-tile decomposition (SPLIT: 16384 bins,
+// the phase-split limit; FP64: 4096 bins, whose items are long already).
+inline int coarse_iters(int precision) { return precision == 1 ? kMaxTileBins / (kBlock * kBinsPerThread) : 16; }
+
 // Histograms per chunk, and reduction channels per work item, of a SPLIT shape.
 int shape_group(int shape);
 int shape_channels(int shape);

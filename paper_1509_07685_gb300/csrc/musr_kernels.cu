@@ -436,40 +436,72 @@ __device__ double fp64_slot(const HistSet& hs, const double* tot, int s) {
 // ---------------------------------------------------------------------------------------------
 template <int S>
 struct ShapeT;
+// NT: terms; G: histograms per chunk; AMP: whether amplitude channels are kept
+// (dropped when every amplitude is a constant); NTF: cosine terms; phi(k): the
+// phase channel of term k among the cosine terms.
 template <>
 struct ShapeT<kShapeGeneric> {
-  static constexpr int NT = 4, G = 4;
+  static constexpr int NT = 4, G = 2, NTF = 4;
+  static constexpr bool AMP = true;
   __device__ static int kind(const ChunkCache& cc, int k) { return cc.kinds[k]; }
   __device__ static int nterms(const HistSet& hs) { return hs.nterms; }
+  __device__ static constexpr int phi(int k) { return k; }
 };
 template <>
 struct ShapeT<kShapeTF1> {
-  static constexpr int NT = 1, G = 8;
+  static constexpr int NT = 1, G = 8, NTF = 1;
+  static constexpr bool AMP = true;
   __device__ static constexpr int kind(const ChunkCache&, int) { return kTermTF; }
   __device__ static constexpr int nterms(const HistSet&) { return 1; }
+  __device__ static constexpr int phi(int k) { return k; }
 };
 template <>
 struct ShapeT<kShapeTF2> {
-  static constexpr int NT = 2, G = 8;
+  static constexpr int NT = 2, G = 8, NTF = 2;
+  static constexpr bool AMP = true;
   __device__ static constexpr int kind(const ChunkCache&, int) { return kTermTF; }
   __device__ static constexpr int nterms(const HistSet&) { return 2; }
+  __device__ static constexpr int phi(int k) { return k; }
+};
+template <>
+struct ShapeT<kShapeTF2c> {
+  static constexpr int NT = 2, G = 8, NTF = 2;
+  static constexpr bool AMP = false;
+  __device__ static constexpr int kind(const ChunkCache&, int) { return kTermTF; }
+  __device__ static constexpr int nterms(const HistSet&) { return 2; }
+  __device__ static constexpr int phi(int k) { return k; }
 };
 template <>
 struct ShapeT<kShapeKT1> {
-  static constexpr int NT = 1, G = 8;
+  static constexpr int NT = 1, G = 8, NTF = 0;
+  static constexpr bool AMP = true;
   __device__ static constexpr int kind(const ChunkCache&, int) { return kTermKT; }
   __device__ static constexpr int nterms(const HistSet&) { return 1; }
+  __device__ static constexpr int phi(int) { return 0; }
 };
 template <>
 struct ShapeT<kShapeTF2KT1> {
-  static constexpr int NT = 3, G = 4;
+  static constexpr int NT = 3, G = 4, NTF = 2;
+  static constexpr bool AMP = true;
   __device__ static constexpr int kind(const ChunkCache&, int k) { return k < 2 ? kTermTF : kTermKT; }
   __device__ static constexpr int nterms(const HistSet&) { return 3; }
+  __device__ static constexpr int phi(int k) { return k; }
+};
+template <>
+struct ShapeT<kShapeTF2KT1c> {
+  static constexpr int NT = 3, G = 8, NTF = 2;
+  static constexpr bool AMP = false;
+  __device__ static constexpr int kind(const ChunkCache&, int k) { return k < 2 ? kTermTF : kTermKT; }
+  __device__ static constexpr int nterms(const HistSet&) { return 3; }
+  __device__ static constexpr int phi(int k) { return k; }
 };
 template <int S>
 struct ShapeChan {
-  static constexpr int NPH = 2 + 2 * ShapeT<S>::NT;  // per histogram: N0, bkg, amp[k], phi[k]
-  static constexpr int NSH = 4 * ShapeT<S>::NT;      // shared per term: Lambda, S, nu, Delta
+  // per histogram: N0, bkg, [amp of each term], phase of each cosine term
+  static constexpr int AMP0 = 2;
+  static constexpr int PHI0 = 2 + (ShapeT<S>::AMP ? ShapeT<S>::NT : 0);
+  static constexpr int NPH = PHI0 + ShapeT<S>::NTF;
+  static constexpr int NSH = 4 * ShapeT<S>::NT;  // shared per term: Lambda, S, nu, Delta
   static constexpr int N = ShapeT<S>::G * NPH + NSH;
   static_assert(N <= kMaxChan, "channel count");
 };
@@ -480,7 +512,10 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
   constexpr int NT = Sh::NT;
   constexpr int G = Sh::G;
   constexpr int NPH = ShapeChan<SHAPE>::NPH;
+  constexpr int PHI0 = ShapeChan<SHAPE>::PHI0;
   constexpr int NCH = ShapeChan<SHAPE>::N;
+  constexpr int BPT = kBinsPerThread;  // consecutive bins per thread per iteration
+  static_assert(BPT == 2, "the loads below read float2 / double2");
 
   const ChunkCache& cc = sm.cc;
   const int tid = threadIdx.x;
@@ -504,31 +539,32 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     for (int q = 0; q < 4; ++q) sh[k][q] = 0.0f;
   int bad = 0;
 
-  const int iters = hs.tile_bins / (kBlock * kBinsPerThread);
+  const int iters = hs.tile_bins / (kBlock * BPT);
   for (int it = 0; it < iters; ++it) {
-    const int m0 = it * kBlock * kBinsPerThread + tid * kBinsPerThread;  // offset in tile (< 2^14)
+    const int m0 = it * kBlock * BPT + tid * BPT;  // offset in the tile (< 2^14)
     const int n0 = ts + m0;
     if (n0 >= nhi) break;
-    float t[4];
-    bool valid[4];
+    float t[BPT];
+    bool valid[BPT];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < BPT; ++j) {
       t[j] = fmaf(static_cast<float>(m0 + j), dtf, tbase);
       valid[j] = (n0 + j >= nlo) && (n0 + j < nhi);
     }
-    // Time-only factors of the chunk.
-    float E[4], EXK[NT][4], cs[NT][4], sn[NT][4], dk[NT][4];
+    // Time-only factors of the chunk: E = exp(-t/tau), EXK_k = E X_k K_k, and the
+    // precession (cos, sin) of each TF term without the per-histogram phase.
+    float E[BPT], EXK[NT][BPT], cs[NT][BPT], sn[NT][BPT], dk[NT][BPT];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) E[j] = ex2a(-aE * t[j]);
+    for (int j = 0; j < BPT; ++j) E[j] = ex2a(-aE * t[j]);
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
       const int kk = Sh::kind(cc, k);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) EXK[k][j] = cs[k][j] = sn[k][j] = dk[k][j] = 0.0f;
+      for (int j = 0; j < BPT; ++j) EXK[k][j] = cs[k][j] = sn[k][j] = dk[k][j] = 0.0f;
       if (k >= nterms) continue;
       const float ca = cc.ca[k], cb = cc.cb[k];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < BPT; ++j) {
         const float ex = ex2a(-fmaf(cb, t[j], ca) * t[j]);
         EXK[k][j] = ex;
         cs[k][j] = 1.0f;
@@ -547,7 +583,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
         float r = fmaf(static_cast<float>(m0), cc.slo[k], sm.ts.base[k]) + f;
         r = __fsub_rn(r, rint_small(r));
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < BPT; ++j) {
           float rj = fmaf(static_cast<float>(j), cc.sstep[k], r);
           rj = __fsub_rn(rj, rint_small(rj));  // |rj| <= 1/2: sin/cos arguments in [-pi, pi]
           const float a = rj * kTwoPiF;
@@ -556,34 +592,29 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
         }
       }
     }
-    float U[NT][4], V[NT][4];
+    float U[NT][BPT], V[NT][BPT];
 #pragma unroll
     for (int k = 0; k < NT; ++k)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) U[k][j] = V[k][j] = 0.0f;
+      for (int j = 0; j < BPT; ++j) U[k][j] = V[k][j] = 0.0f;
 
 #pragma unroll
     for (int hl = 0; hl < G; ++hl) {
       if (hl >= nh) break;
-      float d[4];
+      float d[BPT];
       const int64_t off = static_cast<int64_t>(cc.row[hl]) * stride + n0;
       if (store == kStoreF32) {
-        const float4 q = __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(counts) + off));
+        const float2 q = __ldg(reinterpret_cast<const float2*>(static_cast<const float*>(counts) + off));
         d[0] = q.x;
         d[1] = q.y;
-        d[2] = q.z;
-        d[3] = q.w;
       } else {
-        const double2* p = reinterpret_cast<const double2*>(static_cast<const double*>(counts) + off);
-        const double2 q0 = __ldg(p), q1 = __ldg(p + 1);
-        d[0] = static_cast<float>(q0.x);
-        d[1] = static_cast<float>(q0.y);
-        d[2] = static_cast<float>(q1.x);
-        d[3] = static_cast<float>(q1.y);
+        const double2 q = __ldg(reinterpret_cast<const double2*>(static_cast<const double*>(counts) + off));
+        d[0] = static_cast<float>(q.x);
+        d[1] = static_cast<float>(q.y);
       }
       const float N0 = cc.n0[hl], Nb = cc.bkg[hl];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < BPT; ++j) {
         float C[NT], Sn[NT], Q[NT];
         float M = E[j];
 #pragma unroll
@@ -609,29 +640,32 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
           w = r * iv;
           v = r * w;
         } else {
+          const float r = N - dd;
           if (dd > 0.0f) {
             if (N <= 0.0f) {
               bad = 1;
               v = 0.0f;
               w = 0.0f;
             } else {
-              // d [y - ln(1 + y)], y = (N - d)/d: a series in z = y/(2+y) where |z| < 0.2,
-              // y - ln(1+y) = z (y - 2 z^2 (1/3 + z^2/5 + ...)), else y - ln(1 + y) directly.
-              const float y = (N - dd) * rcpa(dd);
-              const float z = y * rcpa(2.0f + y);
-              const float z2 = z * z;
-              float pz = fmaf(z2, 1.0f / 13.0f, 1.0f / 11.0f);
-              pz = fmaf(z2, pz, 1.0f / 9.0f);
-              pz = fmaf(z2, pz, 1.0f / 7.0f);
-              pz = fmaf(z2, pz, 1.0f / 5.0f);
-              pz = fmaf(z2, pz, 1.0f / 3.0f);
-              const float phs = z * fmaf(-2.0f * z2, pz, y);
-              const float phl = y - lg2a(1.0f + y) * kLn2F;
-              v = dd * (fabsf(z) < 0.2f ? phs : phl);
-              w = (N - dd) * rcpa(N);
+              // Half deviance (N - d) - d ln(N/d) with z = (N - d)/(N + d): since
+              // ln(N/d) = 2 atanh(z), it equals z ((N - d) - 2 d z^2 (1/3 + z^2/5 + ...)),
+              // summed to z^10 for |z| < 0.1 (relative truncation < 1e-12); beyond that the
+              // logarithms are taken directly, where no cancellation is left.
+              const float z = r * rcpa(N + dd);
+              if (fabsf(z) < 0.1f) {
+                const float z2 = z * z;
+                float pz = fmaf(z2, 1.0f / 11.0f, 1.0f / 9.0f);
+                pz = fmaf(z2, pz, 1.0f / 7.0f);
+                pz = fmaf(z2, pz, 1.0f / 5.0f);
+                pz = fmaf(z2, pz, 1.0f / 3.0f);
+                v = z * fmaf(-2.0f * dd * z2, pz, r);
+              } else {
+                v = fmaf(-dd * kLn2F, lg2a(N) - lg2a(dd), r);
+              }
+              w = r * rcpa(N);
             }
           } else {
-            v = N - dd;
+            v = r;
             w = 1.0f;
           }
         }
@@ -652,11 +686,12 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
 #pragma unroll
           for (int k = 0; k < NT; ++k) {
             if (k >= nterms) continue;
-            ph[hl][2 + k] = fmaf(w, Q[k], ph[hl][2 + k]);
+            if (Sh::AMP) ph[hl][2 + k] = fmaf(w, Q[k], ph[hl][2 + k]);
             const float P = wN0 * cc.amp[k][hl];
             U[k][j] = fmaf(P, C[k], U[k][j]);
             if (Sh::kind(cc, k) == kTermTF) {
-              ph[hl][2 + NT + k] = fmaf(w * Sn[k], EXK[k][j], ph[hl][2 + NT + k]);
+              const int pc = PHI0 + Sh::phi(k);
+              ph[hl][pc] = fmaf(w * Sn[k], EXK[k][j], ph[hl][pc]);
               V[k][j] = fmaf(P, Sn[k], V[k][j]);
             }
           }
@@ -670,7 +705,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
         if (k >= nterms) continue;
         const int kk = Sh::kind(cc, k);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < BPT; ++j) {
           const float ue = U[k][j] * EXK[k][j];
           sh[k][0] = fmaf(-t[j], ue, sh[k][0]);               // d/dLambda
           sh[k][1] = fmaf(-0.5f * t[j] * t[j], ue, sh[k][1]);  // d/dS
@@ -681,7 +716,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     }
   }
 
-  // ---- thread (FP32) -> warp (FP32; the value as float-float) -> CTA (FP64) -> row.
+  // ---- thread (FP32) -> warp (FP32; the value as float-float) -> CTA (FP64 trees) -> row.
   bad = __syncthreads_or(bad);
   const int w = tid >> 5, lane = tid & 31;
   float vh = acc_v, vl = -acc_c;
@@ -707,18 +742,20 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
       }
   }
   __syncthreads();
+  static_assert(kWarps == 8, "the FP64 trees below sum 8 warps");
   double* row = job.partials + static_cast<int64_t>(item) * hs.pstride;
   if (GRAD && tid < NCH) {
-    double s = 0.0;
+    double a[kWarps];
 #pragma unroll
-    for (int i = 0; i < kWarps; ++i) s += static_cast<double>(sm.cred[i][tid]);
-    row[1 + tid] = s;
+    for (int i = 0; i < kWarps; ++i) a[i] = static_cast<double>(sm.cred[i][tid]);
+    row[1 + tid] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
   }
   if (tid == kBlock - 1) {
     static_assert(NCH < kBlock - 1, "value thread overlaps a channel thread");
-    double s = 0.0;
+    double a[kWarps];
 #pragma unroll
-    for (int i = 0; i < kWarps; ++i) s += static_cast<double>(sm.vred[i][0]) + static_cast<double>(sm.vred[i][1]);
+    for (int i = 0; i < kWarps; ++i) a[i] = static_cast<double>(sm.vred[i][0]) + static_cast<double>(sm.vred[i][1]);
+    const double s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
     row[0] = bad ? __longlong_as_double(0x7ff0000000000000LL) : s * (MODE == 1 ? 2.0 : 1.0);
   }
 }
@@ -729,6 +766,7 @@ __device__ double split_slot(const HistSet& hs, const ChunkCache& cc, const doub
   constexpr int NT = ShapeT<SHAPE>::NT;
   constexpr int G = ShapeT<SHAPE>::G;
   constexpr int NPH = ShapeChan<SHAPE>::NPH;
+  constexpr int PHI0 = ShapeChan<SHAPE>::PHI0;
   const double* ch = tot + 1;
   const double N0 = cc.loc[hl][0];
   double g = 0.0;
@@ -744,12 +782,12 @@ __device__ double split_slot(const HistSet& hs, const ChunkCache& cc, const doub
         g += 2.0 * ch[hl * NPH + 1];
         break;
       case kCAmp:
-        g += 2.0 * N0 * ch[hl * NPH + 2 + k];
+        if (ShapeT<SHAPE>::AMP) g += 2.0 * N0 * ch[hl * NPH + 2 + k];
         break;
       case kCPhi: {
         const int as = hs.canon[k].amp_slot;
         const double a = as >= 0 ? cc.loc[hl][as] : 1.0;
-        g += 2.0 * N0 * a * (-kTwoPi / 360.0) * ch[hl * NPH + 2 + NT + k];
+        g += 2.0 * N0 * a * (-kTwoPi / 360.0) * ch[hl * NPH + PHI0 + ShapeT<SHAPE>::phi(k)];
         break;
       }
       case kCLam:
@@ -858,7 +896,7 @@ __device__ void complete_item(const Job& job, const HistSet& hs, Smem& sm) {
 // Persistent kernel: each CTA takes a contiguous range of the launch's items.
 // ---------------------------------------------------------------------------------------------
 template <int PREC, int SHAPE, int MODE, bool GRAD>
-__global__ void __launch_bounds__(kBlock) eval_kernel(const Job* __restrict__ jobs, int njobs,
+__global__ void __launch_bounds__(kBlock, PREC == 1 ? 2 : 1) eval_kernel(const Job* __restrict__ jobs, int njobs,
                                                       int total_items) {
   __shared__ Smem sm;
   const int per = (total_items + gridDim.x - 1) / gridDim.x;
@@ -952,6 +990,10 @@ int shape_group(int shape) {
       return ShapeT<kShapeKT1>::G;
     case kShapeTF2KT1:
       return ShapeT<kShapeTF2KT1>::G;
+    case kShapeTF2c:
+      return ShapeT<kShapeTF2c>::G;
+    case kShapeTF2KT1c:
+      return ShapeT<kShapeTF2KT1c>::G;
     default:
       return ShapeT<kShapeGeneric>::G;
   }
@@ -967,6 +1009,10 @@ int shape_channels(int shape) {
       return ShapeChan<kShapeKT1>::N;
     case kShapeTF2KT1:
       return ShapeChan<kShapeTF2KT1>::N;
+    case kShapeTF2c:
+      return ShapeChan<kShapeTF2c>::N;
+    case kShapeTF2KT1c:
+      return ShapeChan<kShapeTF2KT1c>::N;
     default:
       return ShapeChan<kShapeGeneric>::N;
   }
@@ -985,6 +1031,10 @@ int launch_eval(int precision, int shape, int mode, int grad, const Job* d_jobs,
       return dispatch_mode<1, kShapeKT1>(mode, grad, d_jobs, njobs, total_items, num_sms, s, info);
     case kShapeTF2KT1:
       return dispatch_mode<1, kShapeTF2KT1>(mode, grad, d_jobs, njobs, total_items, num_sms, s, info);
+    case kShapeTF2c:
+      return dispatch_mode<1, kShapeTF2c>(mode, grad, d_jobs, njobs, total_items, num_sms, s, info);
+    case kShapeTF2KT1c:
+      return dispatch_mode<1, kShapeTF2KT1c>(mode, grad, d_jobs, njobs, total_items, num_sms, s, info);
     default:
       return dispatch_mode<1, kShapeGeneric>(mode, grad, d_jobs, njobs, total_items, num_sms, s, info);
   }
@@ -1001,6 +1051,10 @@ int max_ctas_per_sm(int precision, int shape, int mode, int grad) {
       return occupancy_mode<1, kShapeKT1>(mode, grad);
     case kShapeTF2KT1:
       return occupancy_mode<1, kShapeTF2KT1>(mode, grad);
+    case kShapeTF2c:
+      return occupancy_mode<1, kShapeTF2c>(mode, grad);
+    case kShapeTF2KT1c:
+      return occupancy_mode<1, kShapeTF2KT1c>(mode, grad);
     default:
       return occupancy_mode<1, kShapeGeneric>(mode, grad);
   }
