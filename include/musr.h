@@ -162,6 +162,39 @@ int musr_bins_in_fit(musr_ctx* ctx, int64_t* out);
  * call makes (for launch accounting). */
 int musr_launches_per_eval(musr_ctx* ctx, int* out);
 
+/* The paper has no counterpart to this entry point.
+ *
+ * One evaluation (value and, with with_grad != 0, gradient) that allocates no
+ * memory, for callers that cannot allocate device memory: code inside a
+ * framework whose memory pool owns the GPU and forbids cudaMalloc beside it,
+ * plugins whose host reserves all HBM up front, or loops where the implicit
+ * synchronisation of an allocation is not acceptable.  Such callers cannot
+ * create a musr_ctx (a context allocates), so everything comes from them:
+ * d_counts [nhist][row_stride] FP32 or FP64 on the current device (16-byte
+ * aligned, row_stride a multiple of 4), d_params [nparams] FP64 on the device,
+ * d_out [1 + nparams] FP64 on the device (value, then gradient); t0, the fit
+ * range, terms, map and consts are host arrays, read before the call returns.
+ * Their meaning is that of musr_upload_histograms, musr_set_theory and
+ * musr_set_map.  The call is asynchronous on cuda_stream (NULL: the legacy
+ * default stream); an undefined likelihood writes +inf as the value.
+ *
+ * All scratch (work tables, partial sums, completion counters) lives in one
+ * file-scope device array of MUSR_NOALLOC_SCRATCH_BYTES that every GPU which
+ * loads the library holds until the process exits.  Limits: nhist <= 64,
+ * nparams <= 1024, nconsts <= 256, at most 8192 work items, and the scratch
+ * size; anything beyond returns MUSR_EINVAL without touching the GPU.  The
+ * first call on a device looks up the array's device address (set-up): make
+ * that first call before any stream capture.  Every call on a device uses the
+ * same array and leaves its contents behind (the counters are cleared at the
+ * start of each call): calls that overlap on the GPU race, so serialise them
+ * (one stream, or an event between them). */
+#define MUSR_NOALLOC_SCRATCH_BYTES (8u << 20)
+int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int64_t nbins, int64_t row_stride,
+                      const double* t0, double bin_width_ns, const double fit_range_us[2],
+                      const musr_term* terms, int nterms, const int32_t* map, int nslots, int nparams,
+                      const double* consts, int nconsts, const double* d_params, int mode,
+                      int precision, int with_grad, double* d_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,7 @@ EXPORTS = (
     "musr_ctx_create", "musr_ctx_destroy", "musr_last_error", "musr_upload_histograms",
     "musr_upload_histograms_device", "musr_set_theory", "musr_set_map", "musr_eval",
     "musr_eval_batch", "musr_eval_device", "musr_sync", "musr_bins_in_fit",
-    "musr_launches_per_eval",
+    "musr_launches_per_eval", "musr_eval_noalloc",
 )
 
 
@@ -68,6 +68,9 @@ def _declare(lib):
         "musr_sync": ([vp, ctypes.c_int], ctypes.c_int),
         "musr_bins_in_fit": ([vp, P(i64)], ctypes.c_int),
         "musr_launches_per_eval": ([vp, P(ctypes.c_int)], ctypes.c_int),
+        "musr_eval_noalloc": ([vp, ctypes.c_int, ctypes.c_int, i64, i64, P(d), d, P(d), P(musr_term),
+                               ctypes.c_int, P(i32), ctypes.c_int, ctypes.c_int, P(d), ctypes.c_int, vp,
+                               ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -232,6 +235,24 @@ def musr_launches_per_eval(ctx) -> int:
     out = ctypes.c_int()
     _check(ctx, load().musr_launches_per_eval(ctx, ctypes.byref(out)))
     return out.value
+
+
+def musr_eval_noalloc(d_counts: int, dtype: int, nhist: int, nbins: int, row_stride: int,
+                      t0: Sequence[float], bin_width_ns: float, fit_range_us: Sequence[float], terms,
+                      mp: np.ndarray, nparams: int, consts: Sequence[float], d_params: int, mode: int,
+                      precision: int, with_grad: bool, d_out: int, cuda_stream: Optional[int] = None) -> int:
+    """The allocation-free evaluation (device pointers in and out); returns the status."""
+    t0 = np.ascontiguousarray(t0, dtype=np.float64)
+    fr = np.ascontiguousarray(fit_range_us, dtype=np.float64)
+    arr, n = terms_to_c(terms)
+    mp = np.ascontiguousarray(mp, dtype=np.int32)
+    c = np.ascontiguousarray(consts if len(consts) else np.zeros(1), dtype=np.float64)
+    stream = None if not cuda_stream else ctypes.c_void_p(cuda_stream)
+    return load().musr_eval_noalloc(ctypes.c_void_p(d_counts), dtype, nhist, nbins, row_stride, _dptr(t0),
+                                    float(bin_width_ns), _dptr(fr), arr, n,
+                                    mp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), mp.shape[1],
+                                    int(nparams), _dptr(c), len(consts), ctypes.c_void_p(d_params), mode,
+                                    precision, int(bool(with_grad)), ctypes.c_void_p(d_out), stream)
 
 
 # --------------------------------------------------------------------------------------------

@@ -1,0 +1,65 @@
+"""musr_eval_noalloc, the entry point that allocates nothing, against musr_eval.
+
+Callers that cannot allocate device memory -- a framework whose pool owns the GPU,
+a host that reserves all HBM up front, a loop that cannot afford an allocation's
+synchronisation -- cannot create a context either, so musr_eval_noalloc keeps its
+scratch in a fixed device array inside the library.  This test allocates the
+inputs and outputs with torch (a test may); the entry point itself allocates
+nothing.  Two calls in a row, with different parameters, must each match the
+context path within the parity tolerances: the second call also checks that what
+the first one left in the shared scratch does not leak into its result.
+"""
+import numpy as np
+import pytest
+
+import musr_inputs as mi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+SPLIT_EPS = 2.0 ** -16
+
+
+def test_noalloc_matches_context_on_two_calls_in_a_row(musr_lib):
+    import torch
+
+    from paper_1509_07685_gb300 import binding as B
+    p = mi.cfg2(nhist=6, nbins=12001, bin_width_ns=1.0, seed=61)
+    stride = (p.B + 3) // 4 * 4
+    d_counts = torch.zeros((p.H, stride), dtype=torch.float32, device="cuda")
+    d_counts[:, :p.B] = torch.from_numpy(np.ascontiguousarray(p.counts, dtype=np.float32)).cuda()
+    xs = [mi.start_point(p, 1), mi.start_point(p, 2)]
+    stream = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    with B.Context(p) as ctx:
+        for prec, tol in ((B.MUSR_FP64, FP64_TOL), (B.MUSR_SPLIT, SPLIT_EPS)):
+            for mode in (B.MUSR_CHI2, B.MUSR_MLE):
+                for x in xs:  # two calls in a row on the same scratch
+                    d_x = torch.tensor(x, dtype=torch.float64, device="cuda")
+                    d_out = torch.full((1 + p.nparams,), float("nan"), dtype=torch.float64, device="cuda")
+                    st = B.musr_eval_noalloc(d_counts.data_ptr(), B.MUSR_DTYPE_FP32, p.H, p.B, stride, p.t0,
+                                             p.bin_width_ns, p.fit_range_us, p.terms, p.map, p.nparams,
+                                             p.consts, d_x.data_ptr(), mode, prec, True, d_out.data_ptr(),
+                                             stream)
+                    assert st == B.MUSR_OK
+                    torch.cuda.synchronize()
+                    out = d_out.cpu().numpy()
+                    v, g, _ = ctx.eval(x, mode, prec)
+                    gs = oracle.cost(p, x, mode)[2]
+                    assert abs(out[0] - v) <= tol * abs(v), (prec, mode, out[0], v)
+                    assert np.all(np.abs(out[1:] - g) <= tol * gs + 1e-300), (prec, mode)
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch(musr_lib):
+    import torch
+
+    from paper_1509_07685_gb300 import binding as B
+    p = mi.cfg3(nhist=65, nbins=64, bin_width_ns=200.0, seed=62)  # 65 histograms: above the limit of 64
+    d_counts = torch.zeros((p.H, 64), dtype=torch.float32, device="cuda")
+    d_x = torch.tensor(p.truth, dtype=torch.float64, device="cuda")
+    d_out = torch.zeros(1 + p.nparams, dtype=torch.float64, device="cuda")
+    st = B.musr_eval_noalloc(d_counts.data_ptr(), B.MUSR_DTYPE_FP32, p.H, p.B, 64, p.t0, p.bin_width_ns,
+                             p.fit_range_us, p.terms, p.map, p.nparams, p.consts, d_x.data_ptr(), 0,
+                             B.MUSR_FP64, True, d_out.data_ptr(), None)
+    assert st == B.MUSR_EINVAL
