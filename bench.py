@@ -37,9 +37,11 @@ sys.path.insert(0, ROOT)
 
 NVEC = 64
 FP32_LANES_PER_SM = 128
-# FP32-pipe operations per (histogram, bin) of the SPLIT fused value+gradient
-# evaluation of the two-term TF model (see the roofline section of the design notes).
-ALGO_FP32_OPS = {0: 37.0, 1: 58.0}
+# Algorithmic FP32-pipe operations (lane instructions, an FMA counts one) per
+# (histogram, bin) of the fused value+gradient evaluation of the two-term TF model
+# with time-only factors shared by 8 histograms: model 9, cost (chi^2 4 / -2lnL 13),
+# value sum 1, gradient 17, shared per-bin work 40/8 = 5.
+ALGO_FP32_OPS = {0: 36.0, 1: 45.0}
 
 
 def _env_int(name, default):
@@ -58,6 +60,8 @@ def _args():
     ap.add_argument("--mode", type=int, default=1, help="0 chi^2, 1 -2lnL")
     ap.add_argument("--no-fits", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=10000,
+                    help="fit requests of the serving measurement (0: skip)")
     return ap.parse_args()
 
 
@@ -284,6 +288,9 @@ def run_ours(args, rank, world, local_rank):
     fits = None
     if not args.no_fits and rank == 0:
         fits = _fits(p, ctx, B, mode)
+    serving = None
+    if args.serving_requests > 0 and rank == 0:
+        serving = _serving(B, args.serving_requests)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -299,7 +306,7 @@ def run_ours(args, rank, world, local_rank):
                 "gpu_launches": args.steps, "wall_s_timed_region": t_wall,
                 "fp64_path": {"value": fp64_gbins, "unit": "Gbins/s", "split_speedup": value / world / fp64_gbins,
                               "max_rel_value_diff_split_vs_fp64": rel_err},
-                "fits": fits, "cpu_baseline": cpu}
+                "fits": fits, "serving": serving, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -327,6 +334,68 @@ def _fits(p, ctx, B, mode):
     return {"fits_per_s": len(lat) / sum(lat), "latency_ms_p50": 1e3 * float(np.median(lat)),
             "latency_ms_max": 1e3 * float(np.max(lat)), "evals_per_fit": float(np.mean([r["nfev"] for r in out])),
             "max_param_dev_split_vs_fp64_sigma": dev, "fp64_fit_s": r64["time_s"]}
+
+
+def _serving(B, n_requests, window=1024, seed=4):
+    """Serving: fits/s at saturation (closed loop, at most `window` in flight), then
+    Poisson arrivals at 0.5x and 0.9x that rate with p50/p99 latency (server clock,
+    submission to completion).  Requests draw from a pool of 32 seeded fits (H, B
+    log-uniform, theory from cfg1/cfg2/cfg3, truths jittered); SPLIT precision, -2lnL
+    or chi^2 at random."""
+    import threading
+
+    import musr_inputs as mi
+    pool = mi.serving_pool(32, seed=seed)
+    out = {"requests": n_requests, "pool": len(pool), "precision": "split",
+           "hbm_budget_gib": 8, "max_active": 1024}
+    with B.Server(hbm_budget_bytes=8 << 30, max_active=1024) as srv:
+        reqs = mi.request_stream(pool, n_requests, 0.0, seed=seed)
+        t = time.perf_counter()
+        pending = []
+        lat, statuses = [], []
+        i = 0
+        while i < len(reqs) or pending:
+            while i < len(reqs) and len(pending) < window:
+                r = reqs[i]
+                pending.append(srv.submit(r.problem, r.x0, r.mode, B.MUSR_SPLIT))
+                i += 1
+            res = srv.wait(pending.pop(0))
+            statuses.append(res["status"])
+            lat.append(res["t_done"] - res["t_submit"])
+        sat_s = time.perf_counter() - t
+        st = srv.stats()
+    rate = n_requests / sat_s
+    out["saturation"] = {"fits_per_s": rate, "wall_s": sat_s, "converged": int(sum(s == 0 for s in statuses)),
+                         "gbins_per_s": st["bin_evals"] / sat_s / 1e9, "steps": st["steps"],
+                         "launches": st["launches"], "evals": st["evals"]}
+    for frac in (0.5, 0.9):
+        reqs = mi.request_stream(pool, n_requests, frac * rate, seed=seed + 10)
+        with B.Server(hbm_budget_bytes=8 << 30, max_active=1024) as srv:
+            ids = [None] * len(reqs)
+            t0 = time.perf_counter()
+
+            def submitter():
+                for k, r in enumerate(reqs):
+                    delay = r.arrival_s - (time.perf_counter() - t0)
+                    if delay > 0:
+                        time.sleep(delay)
+                    ids[k] = srv.submit(r.problem, r.x0, r.mode, B.MUSR_SPLIT)
+
+            th = threading.Thread(target=submitter)
+            th.start()
+            lat = []
+            for k in range(len(reqs)):
+                while ids[k] is None:
+                    time.sleep(0.0005)
+                res = srv.wait(ids[k])
+                lat.append(res["t_done"] - res["t_submit"])
+            th.join()
+            wall = time.perf_counter() - t0
+        lat = np.array(lat)
+        out[f"load_{frac}"] = {"rate_fits_per_s": frac * rate, "fits_per_s": n_requests / wall,
+                               "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
+                               "latency_ms_p99": 1e3 * float(np.percentile(lat, 99))}
+    return out
 
 
 def main():

@@ -162,6 +162,103 @@ int musr_bins_in_fit(musr_ctx* ctx, int64_t* out);
  * call makes (for launch accounting). */
 int musr_launches_per_eval(musr_ctx* ctx, int* out);
 
+/* ---------------------------------------------------------------------------
+ * Fitting (Section 4: the minimiser runs on the host, each trial point is one
+ * cost evaluation on the device; a project-written BFGS stands in for migrad).
+ * ------------------------------------------------------------------------- */
+
+/* Outcome of one fit.  status: 0 converged, 1 cost non-finite at the start,
+ * 2 iteration limit, 3 line search failed, < 0 a musr_status error. */
+typedef struct musr_fit_result {
+  int32_t status;
+  int32_t iters;
+  int32_t nfev;    /* cost evaluations (each a value and a gradient) */
+  int32_t nparams;
+  double f;        /* cost at the result */
+  double edm;      /* estimated distance to the minimum, g.H^-1.g / 2 (cost units) */
+  double t_submit; /* serving clock, seconds: submission, admission, completion */
+  double t_admit;
+  double t_done;   /* musr_fit: wall time of the fit */
+} musr_fit_result;
+
+/* Runs a BFGS fit of the context's problem from x0[nparams] (host) in the given
+ * cost mode and precision; maxit <= 0 means 1000, gtol <= 0 means 1e-8.  Stops
+ * when max|g| <= gtol max(1,|f|), when the estimated distance to the minimum is
+ * below 1e-7 (FP64) or 1e-5 (SPLIT, whose FP32 gradient has a rounding floor),
+ * or at maxit.  x_out[nparams] receives the result.  Synchronous. */
+int musr_fit(musr_ctx* ctx, const double* x0, int mode, int precision, int maxit, double gtol,
+             double* x_out, musr_fit_result* res);
+
+/* ---------------------------------------------------------------------------
+ * Serving: many fits at once (continuous batching).  A worker thread keeps
+ * every admitted fit's histograms resident, evaluates the next trial point of
+ * every active fit in one multi-fit launch per (precision, theory shape, cost)
+ * group per step, and advances each fit's minimiser; fits that arrive while
+ * others run are admitted at the next step boundary, as device memory within
+ * the budget allows.  A fit's result does not depend on the other fits.
+ * ------------------------------------------------------------------------- */
+
+typedef struct musr_server musr_server;
+
+/* One fit: the arguments of musr_upload_histograms, musr_set_theory and
+ * musr_set_map, a start point, and the fit settings.  All arrays are host
+ * memory, copied by musr_server_submit. */
+typedef struct musr_fit_request {
+  const void* counts;
+  int32_t dtype;
+  int32_t nhist;
+  int64_t nbins;
+  const double* t0;
+  double bin_width_ns;
+  double fit_range_us[2];
+  const musr_term* terms;
+  int32_t nterms;
+  int32_t nslots;
+  const int32_t* map;
+  int32_t nparams;
+  int32_t nconsts;
+  const double* consts;
+  const double* x0;
+  int32_t mode;
+  int32_t precision;
+  int32_t maxit; /* <= 0: 1000 */
+  int32_t pad;
+  double gtol;   /* <= 0: 1e-8 */
+} musr_fit_request;
+
+typedef struct musr_server_stats {
+  int64_t submitted, completed, rejected;
+  int64_t steps, launches, evals;
+  int64_t active, queued;
+  double bin_evals; /* (histogram, bin) pairs evaluated, summed over evaluations */
+  double busy_s;    /* worker time inside steps */
+  double clock_s;   /* serving clock now */
+  uint64_t arena_bytes, arena_used;
+} musr_server_stats;
+
+/* Starts a server on `device` with a device memory budget of hbm_budget_bytes
+ * (one allocation, carved per fit) and at most max_active fits in flight. */
+int musr_server_create(musr_server** out, int device, size_t hbm_budget_bytes, int max_active);
+
+/* Stops the worker (running fits are abandoned) and frees everything. */
+void musr_server_destroy(musr_server* s);
+
+/* Queues a fit; *out_id identifies it.  Thread-safe.  A fit that can never run
+ * (larger than the whole budget, SPLIT asked of a theory it cannot run) ends
+ * with a negative status instead of being queued forever. */
+int musr_server_submit(musr_server* s, const musr_fit_request* req, int64_t* out_id);
+
+/* MUSR_OK and the result (x_out[nparams], may be NULL) if fit `id` is done --
+ * the result is then handed over and forgotten -- MUSR_EAGAIN if not yet. */
+int musr_server_poll(musr_server* s, int64_t id, musr_fit_result* res, double* x_out);
+
+/* As musr_server_poll, waiting at most timeout_ms (<= 0: without limit);
+ * MUSR_ETIMEOUT if the fit is not done by then. */
+int musr_server_wait(musr_server* s, int64_t id, int timeout_ms, musr_fit_result* res, double* x_out);
+
+/* Counters of the server. */
+int musr_server_stats_get(musr_server* s, musr_server_stats* out);
+
 /* The paper has no counterpart to this entry point.
  *
  * One evaluation (value and, with with_grad != 0, gradient) that allocates no

@@ -30,7 +30,9 @@ EXPORTS = (
     "musr_ctx_create", "musr_ctx_destroy", "musr_last_error", "musr_upload_histograms",
     "musr_upload_histograms_device", "musr_set_theory", "musr_set_map", "musr_eval",
     "musr_eval_batch", "musr_eval_device", "musr_sync", "musr_bins_in_fit",
-    "musr_launches_per_eval", "musr_eval_noalloc",
+    "musr_launches_per_eval", "musr_eval_noalloc", "musr_fit", "musr_server_create",
+    "musr_server_destroy", "musr_server_submit", "musr_server_poll", "musr_server_wait",
+    "musr_server_stats_get",
 )
 
 
@@ -43,6 +45,32 @@ class MusrError(RuntimeError):
 class musr_term(ctypes.Structure):
     _fields_ = [("nprim", ctypes.c_int32), ("kind", ctypes.c_int32 * MAX_PRIMS),
                 ("slot", (ctypes.c_int32 * 2) * MAX_PRIMS)]
+
+
+class musr_fit_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("nfev", ctypes.c_int32),
+                ("nparams", ctypes.c_int32), ("f", ctypes.c_double), ("edm", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class musr_fit_request(ctypes.Structure):
+    _fields_ = [("counts", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("nhist", ctypes.c_int32),
+                ("nbins", ctypes.c_int64), ("t0", ctypes.POINTER(ctypes.c_double)),
+                ("bin_width_ns", ctypes.c_double), ("fit_range_us", ctypes.c_double * 2),
+                ("terms", ctypes.POINTER(musr_term)), ("nterms", ctypes.c_int32), ("nslots", ctypes.c_int32),
+                ("map", ctypes.POINTER(ctypes.c_int32)), ("nparams", ctypes.c_int32),
+                ("nconsts", ctypes.c_int32), ("consts", ctypes.POINTER(ctypes.c_double)),
+                ("x0", ctypes.POINTER(ctypes.c_double)), ("mode", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("maxit", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("gtol", ctypes.c_double)]
+
+
+class musr_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("steps", ctypes.c_int64), ("launches", ctypes.c_int64), ("evals", ctypes.c_int64),
+                ("active", ctypes.c_int64), ("queued", ctypes.c_int64), ("bin_evals", ctypes.c_double),
+                ("busy_s", ctypes.c_double), ("clock_s", ctypes.c_double), ("arena_bytes", ctypes.c_uint64),
+                ("arena_used", ctypes.c_uint64)]
 
 
 _lock = threading.Lock()
@@ -71,6 +99,14 @@ def _declare(lib):
         "musr_eval_noalloc": ([vp, ctypes.c_int, ctypes.c_int, i64, i64, P(d), d, P(d), P(musr_term),
                                ctypes.c_int, P(i32), ctypes.c_int, ctypes.c_int, P(d), ctypes.c_int, vp,
                                ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
+        "musr_fit": ([vp, P(d), ctypes.c_int, ctypes.c_int, ctypes.c_int, d, P(d), P(musr_fit_result)],
+                     ctypes.c_int),
+        "musr_server_create": ([P(vp), ctypes.c_int, ctypes.c_size_t, ctypes.c_int], ctypes.c_int),
+        "musr_server_destroy": ([vp], None),
+        "musr_server_submit": ([vp, P(musr_fit_request), P(i64)], ctypes.c_int),
+        "musr_server_poll": ([vp, i64, P(musr_fit_result), P(d)], ctypes.c_int),
+        "musr_server_wait": ([vp, i64, ctypes.c_int, P(musr_fit_result), P(d)], ctypes.c_int),
+        "musr_server_stats_get": ([vp, P(musr_server_stats)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -293,6 +329,151 @@ class Context:
         if self.ctx:
             musr_ctx_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+# --------------------------------------------------------------------------------------------
+# Fitting and serving
+# --------------------------------------------------------------------------------------------
+
+def _result_dict(r: "musr_fit_result", x: np.ndarray) -> dict:
+    return {"status": r.status, "iters": r.iters, "nfev": r.nfev, "f": r.f, "edm": r.edm, "x": x,
+            "t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done}
+
+
+def musr_fit(ctx, x0, mode: int, precision: int, maxit: int = 0, gtol: float = 0.0) -> dict:
+    """The native BFGS fit on a configured context (synchronous)."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    x = np.zeros_like(x0)
+    r = musr_fit_result()
+    _check(ctx, load().musr_fit(ctx, _dptr(x0), mode, precision, maxit, gtol, _dptr(x), ctypes.byref(r)))
+    return _result_dict(r, x)
+
+
+def musr_server_create(device: int = 0, hbm_budget_bytes: int = 8 << 30, max_active: int = 1024):
+    out = ctypes.c_void_p()
+    st = load().musr_server_create(ctypes.byref(out), device, hbm_budget_bytes, max_active)
+    if st != MUSR_OK:
+        raise MusrError(st, "musr_server_create failed")
+    return out
+
+
+def musr_server_destroy(srv) -> None:
+    load().musr_server_destroy(srv)
+
+
+def make_request(problem, x0, mode: int, precision: int, maxit: int = 0, gtol: float = 0.0):
+    """A musr_fit_request for a problem; returns (request, keepalive) -- the arrays must live
+    until musr_server_submit returns (it copies them)."""
+    counts = np.ascontiguousarray(problem.counts)
+    dtype = {np.dtype(np.int32): MUSR_DTYPE_INT32, np.dtype(np.float32): MUSR_DTYPE_FP32,
+             np.dtype(np.float64): MUSR_DTYPE_FP64}[counts.dtype]
+    t0 = np.ascontiguousarray(problem.t0, dtype=np.float64)
+    terms, nterms = terms_to_c(problem.terms)
+    mp = np.ascontiguousarray(problem.map, dtype=np.int32)
+    consts = np.ascontiguousarray(problem.consts if len(problem.consts) else np.zeros(1), dtype=np.float64)
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    q = musr_fit_request()
+    q.counts = counts.ctypes.data_as(ctypes.c_void_p)
+    q.dtype = dtype
+    q.nhist, q.nbins = counts.shape
+    q.t0 = _dptr(t0)
+    q.bin_width_ns = float(problem.bin_width_ns)
+    q.fit_range_us[0], q.fit_range_us[1] = problem.fit_range_us
+    q.terms = ctypes.cast(terms, ctypes.POINTER(musr_term))
+    q.nterms = nterms
+    q.nslots = mp.shape[1]
+    q.map = mp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    q.nparams = int(problem.nparams)
+    q.nconsts = len(problem.consts)
+    q.consts = _dptr(consts)
+    q.x0 = _dptr(x0)
+    q.mode, q.precision, q.maxit, q.gtol = mode, precision, maxit, gtol
+    return q, (counts, t0, terms, mp, consts, x0)
+
+
+def musr_server_submit(srv, problem, x0, mode: int, precision: int, maxit: int = 0, gtol: float = 0.0) -> int:
+    q, keep = make_request(problem, x0, mode, precision, maxit, gtol)
+    fid = ctypes.c_int64()
+    st = load().musr_server_submit(srv, ctypes.byref(q), ctypes.byref(fid))
+    del keep
+    if st != MUSR_OK:
+        raise MusrError(st, "musr_server_submit rejected the request")
+    return fid.value
+
+
+def musr_server_poll(srv, fid: int, nparams: int):
+    r = musr_fit_result()
+    x = np.zeros(nparams)
+    st = load().musr_server_poll(srv, fid, ctypes.byref(r), _dptr(x))
+    if st == MUSR_EAGAIN:
+        return None
+    if st != MUSR_OK:
+        raise MusrError(st, "musr_server_poll failed")
+    return _result_dict(r, x)
+
+
+def musr_server_wait(srv, fid: int, nparams: int, timeout_ms: int = 0):
+    r = musr_fit_result()
+    x = np.zeros(nparams)
+    st = load().musr_server_wait(srv, fid, timeout_ms, ctypes.byref(r), _dptr(x))
+    if st == MUSR_ETIMEOUT:
+        return None
+    if st != MUSR_OK:
+        raise MusrError(st, "musr_server_wait failed")
+    return _result_dict(r, x)
+
+
+def musr_server_stats_get(srv) -> dict:
+    s = musr_server_stats()
+    st = load().musr_server_stats_get(srv, ctypes.byref(s))
+    if st != MUSR_OK:
+        raise MusrError(st, "musr_server_stats_get failed")
+    return {name: getattr(s, name) for name, _ in s._fields_}
+
+
+class Server:
+    """Owns one musr_server (continuous batching of many fits)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 8 << 30, max_active: int = 1024):
+        self.srv = musr_server_create(device, hbm_budget_bytes, max_active)
+        self.nparams = {}
+
+    def submit(self, problem, x0, mode=MUSR_MLE, precision=MUSR_SPLIT, maxit=0, gtol=0.0) -> int:
+        fid = musr_server_submit(self.srv, problem, x0, mode, precision, maxit, gtol)
+        self.nparams[fid] = int(problem.nparams)
+        return fid
+
+    def poll(self, fid: int):
+        r = musr_server_poll(self.srv, fid, self.nparams[fid])
+        if r is not None:
+            self.nparams.pop(fid, None)
+        return r
+
+    def wait(self, fid: int, timeout_ms: int = 0):
+        r = musr_server_wait(self.srv, fid, self.nparams[fid], timeout_ms)
+        if r is not None:
+            self.nparams.pop(fid, None)
+        return r
+
+    def stats(self) -> dict:
+        return musr_server_stats_get(self.srv)
+
+    def close(self) -> None:
+        if self.srv:
+            musr_server_destroy(self.srv)
+            self.srv = None
 
     def __del__(self):
         try:

@@ -44,9 +44,80 @@ int cuda_fail(musr_ctx* ctx, cudaError_t e, const char* what) {
   return fail(ctx, MUSR_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+Arena::~Arena() {
+  if (base_) cudaFree(base_);
+}
+
+int Arena::init(size_t bytes) {
+  bytes = (bytes + 255) & ~size_t(255);
+  if (cudaMalloc(reinterpret_cast<void**>(&base_), bytes) != cudaSuccess) {
+    cudaGetLastError();
+    base_ = nullptr;
+    return MUSR_ENOMEM;
+  }
+  cap_ = bytes;
+  free_.clear();
+  live_.clear();
+  free_[0] = bytes;
+  used_ = 0;
+  return MUSR_OK;
+}
+
+void* Arena::alloc(size_t bytes) {
+  bytes = (bytes + 255) & ~size_t(255);
+  std::lock_guard<std::mutex> lock(mu_);
+  for (auto it = free_.begin(); it != free_.end(); ++it) {
+    if (it->second < bytes) continue;
+    const size_t off = it->first, rest = it->second - bytes;
+    free_.erase(it);
+    if (rest) free_[off + bytes] = rest;
+    live_[off] = bytes;
+    used_ += bytes;
+    return base_ + off;
+  }
+  return nullptr;
+}
+
+void Arena::release(void* p) {
+  std::lock_guard<std::mutex> lock(mu_);
+  const size_t off = static_cast<size_t>(static_cast<char*>(p) - base_);
+  auto it = live_.find(off);
+  if (it == live_.end()) return;
+  size_t start = off, size = it->second;
+  used_ -= size;
+  live_.erase(it);
+  auto next = free_.lower_bound(start);
+  if (next != free_.end() && next->first == start + size) {  // merge with the following range
+    size += next->second;
+    free_.erase(next);
+  }
+  auto prev = free_.lower_bound(start);
+  if (prev != free_.begin()) {
+    --prev;
+    if (prev->first + prev->second == start) {  // merge with the preceding range
+      prev->second += size;
+      return;
+    }
+  }
+  free_[start] = size;
+}
+
+size_t Arena::used() const {
+  std::lock_guard<std::mutex> lock(mu_);
+  return used_;
+}
+
 int dalloc(musr_ctx* ctx, DevBuf& b, size_t bytes) {
   dfree(ctx, b);
   if (bytes == 0) bytes = 16;
+  if (ctx->arena) {
+    b.p = ctx->arena->alloc(bytes);
+    if (!b.p) return fail(ctx, MUSR_ENOMEM, "device memory budget exceeded (serving arena full)");
+    b.bytes = bytes;
+    b.from_arena = true;
+    ctx->used += bytes;
+    return MUSR_OK;
+  }
   if (ctx->budget && ctx->used + bytes > ctx->budget)
     return fail(ctx, MUSR_ENOMEM, "device memory budget exceeded (" + std::to_string(ctx->used + bytes) +
                                       " > " + std::to_string(ctx->budget) + " bytes)");
@@ -63,11 +134,15 @@ int dalloc(musr_ctx* ctx, DevBuf& b, size_t bytes) {
 
 void dfree(musr_ctx* ctx, DevBuf& b) {
   if (b.p) {
-    cudaFree(b.p);
+    if (b.from_arena)
+      ctx->arena->release(b.p);
+    else
+      cudaFree(b.p);
     ctx->used -= b.bytes;
   }
   b.p = nullptr;
   b.bytes = 0;
+  b.from_arena = false;
 }
 
 int upload(musr_ctx* ctx, DevBuf& b, const void* src, size_t bytes) {
@@ -162,15 +237,6 @@ static bool canonical(const musr_term& t, CanonTerm* ct, std::string* why) {
   return true;
 }
 
-static int pick_iters(const std::vector<int64_t>& ranges, int per_iter, int target_items) {
-  for (int it : {8, 4, 2}) {
-    int64_t T = static_cast<int64_t>(per_iter) * it, n = 0;
-    for (int64_t r : ranges) n += (r + T - 1) / T;
-    if (n >= target_items) return it;
-  }
-  return 1;
-}
-
 // Builds the decomposition and finalize tables of one precision and one
 // decomposition (0: tiles small enough that one evaluation fills the GPU;
 // 1: the largest tiles, for batched launches).
@@ -224,10 +290,9 @@ int compile(musr_ctx* ctx, int prec, int var) {
       hs.shape = musr::kShapeTF2KT1;
     else
       hs.shape = musr::kShapeGeneric;
-    if (musr::amplitudes_constant(hs.canon, hs.nterms, ctx->map.data(), ctx->H, ctx->nslots)) {
-      if (hs.shape == musr::kShapeTF2) hs.shape = musr::kShapeTF2c;
-      if (hs.shape == musr::kShapeTF2KT1) hs.shape = musr::kShapeTF2KT1c;
-    }
+    hs.shape = musr::constant_amplitude_shape(hs.shape, hs.canon, hs.nterms, ctx->map.data(),
+                                              ctx->consts.data(), ctx->H, ctx->nslots);
+    const bool one_phase = hs.shape == musr::kShapeTF2c || hs.shape == musr::kShapeTF2KT1c;
     group_cap = musr::shape_group(hs.shape);
     // Slot -> channel contributions.
     auto add = [&](int slot, int kind, int term) {
@@ -246,7 +311,8 @@ int compile(musr_ctx* ctx, int prec, int var) {
       if (ct.kind == musr::kTermKT) add(ct.kt_slot, musr::kCDel, k);
       if (ct.kind == musr::kTermTF) {
         add(ct.nu_slot, musr::kCNu, k);
-        add(ct.phi_slot, musr::kCPhi, k);
+        // with one shared phase channel, its slot receives the channel once
+        if (!one_phase || k == 0) add(ct.phi_slot, musr::kCPhi, k);
       }
     }
     // Group histograms that share t0 and every time-dependent parameter.
@@ -308,11 +374,9 @@ int compile(musr_ctx* ctx, int prec, int var) {
     }
   // Tiles: at most 16 iterations of the CTA per tile (the SPLIT phase split
   // needs tile offsets below 2^14 bins).
-  const int per_iter = prec == MUSR_SPLIT ? musr::kBlock * musr::kBinsPerThread : musr::kBlock;
   std::vector<int64_t> ranges;
   for (const auto& ch : chunks) ranges.push_back(ch.nhi - ch.tile0);
-  const int iters = var == 0 ? pick_iters(ranges, per_iter, 4 * ctx->num_sms) : musr::coarse_iters(prec);
-  hs.tile_bins = per_iter * iters;
+  hs.tile_bins = musr::bins_per_iteration(prec) << var;
   std::vector<int2> items;
   int col = 0;
   for (size_t ci = 0; ci < chunks.size(); ++ci) {
@@ -374,15 +438,14 @@ void invalidate_eval(musr_ctx* ctx) { ctx->ev.key_valid = false; }
 // Decomposition for a launch of nvec evaluations: the large tiles when the
 // batch still gives every resident CTA a few items, else the small ones.
 int pick_variant(musr_ctx* ctx, int prec, int nvec) {
-  const Compiled& coarse = ctx->comp[prec][1];
-  const int ctas = ctx->num_sms * 2;
-  return static_cast<int64_t>(nvec) * coarse.hs.nitems >= 3 * ctas ? 1 : 0;
+  int items[musr::kVariants];
+  for (int v = 0; v < musr::kVariants; ++v) items[v] = ctx->comp[prec][v].hs.nitems;
+  return musr::pick_decomposition(items, nvec, ctx->num_sms);
 }
 
 // Buffers for nvec evaluations; rebuilds the job table when the launch's key
 // (precision, decomposition, mode, grad, nvec, pointers) changes.
-int prepare_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, const double* d_params,
-                 double* d_out) {
+int ensure_eval(musr_ctx* ctx, int prec, int var, int nvec) {
   EvalBufs& ev = ctx->ev;
   const HistSet& hs = ctx->comp[prec][var].hs;
   const size_t part = static_cast<size_t>(nvec) * hs.nitems * hs.pstride;
@@ -405,11 +468,13 @@ int prepare_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec,
   if ((rc = grow(ev.chunk_val, nck * sizeof(double), false))) return rc;
   if ((rc = grow(ev.chunk_count, nck * sizeof(unsigned), true))) return rc;
   if ((rc = grow(ev.counters, nvec * sizeof(unsigned), true))) return rc;
-  if ((rc = grow(ev.jobs, nvec * sizeof(Job), false))) return rc;
-  if (ev.key_valid && ev.k_prec == prec && ev.k_var == var && ev.k_mode == mode && ev.k_grad == grad &&
-      ev.k_nvec == nvec && ev.k_params == d_params && ev.k_out == d_out)
-    return MUSR_OK;
-  std::vector<Job> jobs(nvec);
+  return MUSR_OK;
+}
+
+void fill_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, const double* d_params,
+               double* d_out, Job* jobs, int item_begin) {
+  EvalBufs& ev = ctx->ev;
+  const HistSet& hs = ctx->comp[prec][var].hs;
   const HistSet* d_hs = static_cast<const HistSet*>(ctx->comp[prec][var].d_hs.p);
   for (int v = 0; v < nvec; ++v) {
     Job& j = jobs[v];
@@ -422,11 +487,27 @@ int prepare_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec,
     j.chunk_val = static_cast<double*>(ev.chunk_val.p) + static_cast<size_t>(v) * std::max(hs.nchunks, 1);
     j.chunk_count = static_cast<unsigned*>(ev.chunk_count.p) + static_cast<size_t>(v) * std::max(hs.nchunks, 1);
     j.counter = static_cast<unsigned*>(ev.counters.p) + v;
-    j.item_begin = v * hs.nitems;
+    j.item_begin = item_begin + v * hs.nitems;
     j.mode = mode;
     j.grad = grad;
     j.prec = prec;
   }
+}
+
+int prepare_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, const double* d_params,
+                 double* d_out) {
+  EvalBufs& ev = ctx->ev;
+  int rc;
+  if ((rc = ensure_eval(ctx, prec, var, nvec))) return rc;
+  if (ev.jobs.bytes < nvec * sizeof(Job)) {
+    if ((rc = dalloc(ctx, ev.jobs, nvec * sizeof(Job)))) return rc;
+    ev.key_valid = false;
+  }
+  if (ev.key_valid && ev.k_prec == prec && ev.k_var == var && ev.k_mode == mode && ev.k_grad == grad &&
+      ev.k_nvec == nvec && ev.k_params == d_params && ev.k_out == d_out)
+    return MUSR_OK;
+  std::vector<Job> jobs(nvec);
+  fill_jobs(ctx, prec, var, mode, grad, nvec, d_params, d_out, jobs.data(), 0);
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
   e = cudaMemcpy(ev.jobs.p, jobs.data(), sizeof(Job) * nvec, cudaMemcpyHostToDevice);
@@ -610,6 +691,13 @@ static int upload_common(musr_ctx* ctx, int nhist, int64_t nbins, const double* 
   return MUSR_OK;
 }
 
+// Waits for launches that may still read the current configuration; a context that
+// has no map yet has never launched, so nothing is waited for (the serving loop
+// configures new fits while other fits run on the same stream).
+static void quiesce(musr_ctx* ctx) {
+  if (ctx->have_map) cudaStreamSynchronize(ctx->stream);
+}
+
 static void drop_config(musr_ctx* ctx) {
   for (auto& pc : ctx->comp)
     for (auto& c : pc) free_compiled(ctx, c);
@@ -625,7 +713,7 @@ int musr_upload_histograms(musr_ctx* ctx, const void* counts, int dtype, int nhi
   if (!counts) return fail(ctx, MUSR_EINVAL, "counts must not be NULL");
   if (dtype != MUSR_DTYPE_INT32 && dtype != MUSR_DTYPE_FP32 && dtype != MUSR_DTYPE_FP64)
     return fail(ctx, MUSR_EINVAL, "dtype must be MUSR_DTYPE_INT32, _FP32 or _FP64");
-  cudaStreamSynchronize(ctx->stream);
+  quiesce(ctx);
   drop_config(ctx);
   int rc = upload_common(ctx, nhist, nbins, t0, bin_width_ns, fit_range_us);
   if (rc) return rc;
@@ -683,7 +771,7 @@ int musr_upload_histograms_device(musr_ctx* ctx, const void* d_counts, int dtype
     cudaGetLastError();
     return fail(ctx, MUSR_EINVAL, "d_counts is not device memory of the context's device");
   }
-  cudaStreamSynchronize(ctx->stream);
+  quiesce(ctx);
   drop_config(ctx);
   dfree(ctx, ctx->counts_own);
   int rc = upload_common(ctx, nhist, nbins, t0, bin_width_ns, fit_range_us);
@@ -712,7 +800,7 @@ int musr_set_theory(musr_ctx* ctx, const musr_term* terms, int nterms) {
           return fail(ctx, MUSR_EINVAL, "slot index out of range");
     }
   }
-  cudaStreamSynchronize(ctx->stream);
+  quiesce(ctx);
   for (auto& pc : ctx->comp)
     for (auto& c : pc) free_compiled(ctx, c);
   ctx->have_map = false;
@@ -744,7 +832,7 @@ int musr_set_map(musr_ctx* ctx, const int32_t* map, int nslots, int nparams, con
     if (m >= nparams || (m < 0 && -1 - m >= nconsts))
       return fail(ctx, MUSR_EINVAL, "map entry " + std::to_string(i) + " out of range");
   }
-  cudaStreamSynchronize(ctx->stream);
+  quiesce(ctx);
   for (auto& pc : ctx->comp)
     for (auto& c : pc) free_compiled(ctx, c);
   invalidate_eval(ctx);
@@ -758,7 +846,7 @@ int musr_set_map(musr_ctx* ctx, const int32_t* map, int nslots, int nparams, con
   if ((rc = upload(ctx, ctx->d_map, ctx->map.data(), sizeof(int32_t) * n))) return rc;
   if ((rc = upload(ctx, ctx->d_consts, cpad.data(), sizeof(double) * cpad.size()))) return rc;
   for (int prec : {MUSR_FP64, MUSR_SPLIT})
-    for (int var : {0, 1})
+    for (int var = 0; var < musr::kVariants; ++var)
       if ((rc = compile(ctx, prec, var))) return rc;
   ctx->have_map = true;
   return MUSR_OK;

@@ -80,6 +80,37 @@ inline bool amplitudes_constant(const CanonTerm* canon, int nterms, const int32_
   return true;
 }
 
+// True when, for every histogram, all cosine terms take their phase from one
+// parameter (or one constant value).
+inline bool phases_shared(const CanonTerm* canon, int nterms, const int32_t* map, const double* consts, int H,
+                          int nslots) {
+  for (int h = 0; h < H; ++h) {
+    int first = -1;
+    for (int k = 0; k < nterms; ++k) {
+      if (canon[k].kind != kTermTF) continue;
+      const int32_t m = map[static_cast<int64_t>(h) * nslots + canon[k].phi_slot];
+      if (first < 0) {
+        first = k;
+        continue;
+      }
+      const int32_t m0 = map[static_cast<int64_t>(h) * nslots + canon[first].phi_slot];
+      const bool same = (m >= 0 || m0 >= 0) ? m == m0 : consts[-1 - m] == consts[-1 - m0];
+      if (!same) return false;
+    }
+  }
+  return true;
+}
+
+// Shape of a canonical term list whose amplitudes are all constants and whose
+// cosines share one phase: the "c" variants of TF2 and TF2KT1.
+inline int constant_amplitude_shape(int shape, const CanonTerm* canon, int nterms, const int32_t* map,
+                                    const double* consts, int H, int nslots) {
+  if (shape != kShapeTF2 && shape != kShapeTF2KT1) return shape;
+  if (!amplitudes_constant(canon, nterms, map, H, nslots)) return shape;
+  if (!phases_shared(canon, nterms, map, consts, H, nslots)) return shape;
+  return shape == kShapeTF2 ? kShapeTF2c : kShapeTF2KT1c;
+}
+
 // How a SPLIT channel turns into the derivative of one local slot.
 enum ContribKind : int {
   kCN0 = 0,    // d/dN0                 = 2 * ch_N0
@@ -167,9 +198,20 @@ struct LaunchInfo {
 int launch_eval(int precision, int shape, int mode, int grad, const Job* d_jobs, int njobs,
                 int total_items, int num_sms, void* stream, LaunchInfo* info);
 int max_ctas_per_sm(int precision, int shape, int mode, int grad);
-// CTA iterations per tile of the large-tile decomposition (SPLIT: 16384 bins,
-// the phase-split limit; FP64: 4096 bins, whose items are long already).
-inline int coarse_iters(int precision) { return precision == 1 ? kMaxTileBins / (kBlock * kBinsPerThread) : 16; }
+// Decompositions compiled per precision: tile v holds (bins per CTA iteration) << v
+// bins -- SPLIT 512 ... 16384 (the phase-split limit), FP64 256 ... 8192.
+constexpr int kVariants = 6;
+inline int bins_per_iteration(int precision) { return precision == 1 ? kBlock * kBinsPerThread : kBlock; }
+
+// The decomposition of a launch of nvec evaluations: the largest tiles that
+// still give every resident CTA about four items (items[v] = items per
+// evaluation of decomposition v), else the smallest tiles.
+inline int pick_decomposition(const int* items, int64_t nvec, int num_sms) {
+  const int64_t target = 4LL * 2 * num_sms;
+  for (int v = kVariants - 1; v > 0; --v)
+    if (nvec * items[v] >= target) return v;
+  return 0;
+}
 
 // Histograms per chunk, and reduction channels per work item, of a SPLIT shape.
 int shape_group(int shape);

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -15,6 +17,27 @@ namespace musr {
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  bool from_arena = false;
+};
+
+// A device memory arena: one cudaMalloc of the HBM budget, carved first-fit in
+// 256-byte units.  Allocation fails (nullptr) when no free range is large enough,
+// which is how the serving loop admits fits by budget.  Thread-safe.
+class Arena {
+ public:
+  ~Arena();
+  int init(size_t bytes);  // MUSR_OK / MUSR_ENOMEM
+  void* alloc(size_t bytes);
+  void release(void* p);
+  size_t capacity() const { return cap_; }
+  size_t used() const;
+
+ private:
+  char* base_ = nullptr;
+  size_t cap_ = 0, used_ = 0;
+  std::map<size_t, size_t> free_;  // offset -> size
+  std::map<size_t, size_t> live_;  // offset -> size
+  mutable std::mutex mu_;
 };
 
 // The theory and map of one precision, compiled to a work decomposition.
@@ -54,6 +77,13 @@ void dfree(musr_ctx* ctx, DevBuf& b);
 int upload(musr_ctx* ctx, DevBuf& b, const void* src, size_t bytes);
 void fit_bins(double t0, double dt_us, int64_t B, double lo, double hi, int* nlo, int* nhi);
 int wait_stream(musr_ctx* ctx, int timeout_ms);
+int check_ready(musr_ctx* ctx, int mode, int prec);
+// Evaluation buffers of a context for nvec vectors of one decomposition, and the
+// job descriptors of such a launch (written to `jobs`, items numbered from
+// item_begin).  Used by the context's own launches and by the serving loop.
+int ensure_eval(musr_ctx* ctx, int prec, int var, int nvec);
+void fill_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, const double* d_params,
+               double* d_out, Job* jobs, int item_begin);
 
 }  // namespace musr
 
@@ -83,9 +113,10 @@ struct musr_ctx {
   int nslots = 0, P = 0;
   std::vector<double> consts;
   musr::DevBuf d_map, d_consts;
-  // [precision][decomposition]: decomposition 0 has small tiles (one evaluation
-  // fills the GPU), 1 has large tiles (batched launches, less per-item overhead).
-  musr::Compiled comp[2][2];
+  // [precision][decomposition]: tiles of (bins per CTA iteration) << v bins; a
+  // launch picks the largest that still fills the GPU (pick_decomposition).
+  musr::Compiled comp[2][musr::kVariants];
   musr::EvalBufs ev;
   int last_grid = 0;
+  musr::Arena* arena = nullptr;  // when set, device memory comes from it (serving)
 };

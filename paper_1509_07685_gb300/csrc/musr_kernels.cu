@@ -119,6 +119,7 @@ struct ChunkCache {
   int nh, nlo, nhi, tile0, item0, ntiles, col0, first;
   double t0;
   int row[kGroupMax];
+  const void* rowp[kGroupMax];       // first count of each histogram's row
   double loc[kGroupMax][kMaxSlots];  // local slot values (FP64)
   // SPLIT per-histogram FP32 constants
   float n0[kGroupMax], bkg[kGroupMax];
@@ -177,7 +178,11 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
     const int hl = i / nsl, s = i - hl * nsl;
     const int h = hs.hist_index[cc.first + hl];
     cc.loc[hl][s] = slot_value(hs, job.params, h, s);
-    if (s == 0) cc.row[hl] = h;
+    if (s == 0) {
+      cc.row[hl] = h;
+      const size_t esz = hs.store == kStoreF64 ? sizeof(double) : sizeof(float);
+      cc.rowp[hl] = static_cast<const char*>(hs.counts) + static_cast<size_t>(h) * hs.stride * esz;
+    }
   }
   __syncthreads();
   if (prec == 0) return;
@@ -437,8 +442,9 @@ __device__ double fp64_slot(const HistSet& hs, const double* tot, int s) {
 template <int S>
 struct ShapeT;
 // NT: terms; G: histograms per chunk; AMP: whether amplitude channels are kept
-// (dropped when every amplitude is a constant); NTF: cosine terms; phi(k): the
-// phase channel of term k among the cosine terms.
+// (the "c" shapes drop them: every amplitude is a constant); NTF: phase channels;
+// phi(k): the phase channel of cosine term k (the "c" shapes also require one
+// phase slot shared by all cosine terms, so a single channel holds their sum).
 template <>
 struct ShapeT<kShapeGeneric> {
   static constexpr int NT = 4, G = 2, NTF = 4;
@@ -465,11 +471,11 @@ struct ShapeT<kShapeTF2> {
 };
 template <>
 struct ShapeT<kShapeTF2c> {
-  static constexpr int NT = 2, G = 8, NTF = 2;
+  static constexpr int NT = 2, G = 8, NTF = 1;
   static constexpr bool AMP = false;
   __device__ static constexpr int kind(const ChunkCache&, int) { return kTermTF; }
   __device__ static constexpr int nterms(const HistSet&) { return 2; }
-  __device__ static constexpr int phi(int k) { return k; }
+  __device__ static constexpr int phi(int) { return 0; }  // one phase slot for both cosines
 };
 template <>
 struct ShapeT<kShapeKT1> {
@@ -489,11 +495,11 @@ struct ShapeT<kShapeTF2KT1> {
 };
 template <>
 struct ShapeT<kShapeTF2KT1c> {
-  static constexpr int NT = 3, G = 8, NTF = 2;
+  static constexpr int NT = 3, G = 8, NTF = 1;
   static constexpr bool AMP = false;
   __device__ static constexpr int kind(const ChunkCache&, int k) { return k < 2 ? kTermTF : kTermKT; }
   __device__ static constexpr int nterms(const HistSet&) { return 3; }
-  __device__ static constexpr int phi(int k) { return k; }
+  __device__ static constexpr int phi(int) { return 0; }  // one phase slot for both cosines
 };
 template <int S>
 struct ShapeChan {
@@ -522,8 +528,6 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
   const int nh = cc.nh, nlo = cc.nlo, nhi = cc.nhi, ts = sm.ts.tile_start;
   const int nterms = Sh::nterms(hs);
   const float aE = cc.aE, tbase = sm.ts.tbase, dtf = cc.dt;
-  const void* __restrict__ counts = hs.counts;
-  const int64_t stride = hs.stride;
   const int store = hs.store;
 
   float acc_v = 0.0f, acc_c = 0.0f;  // Kahan-compensated cost value
@@ -540,7 +544,10 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
   int bad = 0;
 
   const int iters = hs.tile_bins / (kBlock * BPT);
-  for (int it = 0; it < iters; ++it) {
+  // The bin offset in the tile is carried as an exact float (integers < 2^24): an
+  // int-to-float conversion per bin would occupy this GPU's slow FP64/conversion pipe.
+  float fm0 = static_cast<float>(tid * BPT);
+  for (int it = 0; it < iters; ++it, fm0 += static_cast<float>(kBlock * BPT)) {
     const int m0 = it * kBlock * BPT + tid * BPT;  // offset in the tile (< 2^14)
     const int n0 = ts + m0;
     if (n0 >= nhi) break;
@@ -548,7 +555,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     bool valid[BPT];
 #pragma unroll
     for (int j = 0; j < BPT; ++j) {
-      t[j] = fmaf(static_cast<float>(m0 + j), dtf, tbase);
+      t[j] = fmaf(fm0 + static_cast<float>(j), dtf, tbase);
       valid[j] = (n0 + j >= nlo) && (n0 + j < nhi);
     }
     // Time-only factors of the chunk: E = exp(-t/tau), EXK_k = E X_k K_k, and the
@@ -578,9 +585,9 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
       }
       if (kk == kTermTF) {
         // Phase (turns) of the thread's first bin: base + m0 * step, reduced exactly.
-        float f = static_cast<float>(m0) * cc.shi[k];
+        float f = fm0 * cc.shi[k];
         f = __fsub_rn(f, rint_small(f));
-        float r = fmaf(static_cast<float>(m0), cc.slo[k], sm.ts.base[k]) + f;
+        float r = fmaf(fm0, cc.slo[k], sm.ts.base[k]) + f;
         r = __fsub_rn(r, rint_small(r));
 #pragma unroll
         for (int j = 0; j < BPT; ++j) {
@@ -597,18 +604,18 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     for (int k = 0; k < NT; ++k)
 #pragma unroll
       for (int j = 0; j < BPT; ++j) U[k][j] = V[k][j] = 0.0f;
+    float vit = 0.0f;  // this iteration's cost terms (at most 2 G of them)
 
 #pragma unroll
     for (int hl = 0; hl < G; ++hl) {
       if (hl >= nh) break;
       float d[BPT];
-      const int64_t off = static_cast<int64_t>(cc.row[hl]) * stride + n0;
       if (store == kStoreF32) {
-        const float2 q = __ldg(reinterpret_cast<const float2*>(static_cast<const float*>(counts) + off));
+        const float2 q = __ldg(reinterpret_cast<const float2*>(static_cast<const float*>(cc.rowp[hl]) + n0));
         d[0] = q.x;
         d[1] = q.y;
       } else {
-        const double2 q = __ldg(reinterpret_cast<const double2*>(static_cast<const double*>(counts) + off));
+        const double2 q = __ldg(reinterpret_cast<const double2*>(static_cast<const double*>(cc.rowp[hl]) + n0));
         d[0] = static_cast<float>(q.x);
         d[1] = static_cast<float>(q.y);
       }
@@ -673,12 +680,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
           v = 0.0f;
           w = 0.0f;
         }
-        {
-          const float y = v - acc_c;
-          const float tsum = acc_v + y;
-          acc_c = (tsum - acc_v) - y;
-          acc_v = tsum;
-        }
+        vit += v;
         if (GRAD) {
           ph[hl][0] = fmaf(w, M, ph[hl][0]);
           ph[hl][1] += w;
@@ -691,12 +693,19 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
             U[k][j] = fmaf(P, C[k], U[k][j]);
             if (Sh::kind(cc, k) == kTermTF) {
               const int pc = PHI0 + Sh::phi(k);
-              ph[hl][pc] = fmaf(w * Sn[k], EXK[k][j], ph[hl][pc]);
-              V[k][j] = fmaf(P, Sn[k], V[k][j]);
+              const float PS = P * Sn[k];
+              ph[hl][pc] = fmaf(PS, EXK[k][j], ph[hl][pc]);  // w N0 a sin(theta + phi) E X
+              V[k][j] += PS;
             }
           }
         }
       }
+    }
+    {  // Kahan-compensated running sum of the per-iteration partials
+      const float y = vit - acc_c;
+      const float tsum = acc_v + y;
+      acc_c = (tsum - acc_v) - y;
+      acc_v = tsum;
     }
     if (GRAD) {
       // Shared channels: time-only factor times the chunk's per-bin sums.
@@ -750,13 +759,13 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     for (int i = 0; i < kWarps; ++i) a[i] = static_cast<double>(sm.cred[i][tid]);
     row[1 + tid] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
   }
-  if (tid == kBlock - 1) {
-    static_assert(NCH < kBlock - 1, "value thread overlaps a channel thread");
-    double a[kWarps];
+  if (tid >= kBlock - 32) {  // the last warp: one lane per warp's float-float value, FP64 tree
+    static_assert(NCH <= kBlock - 32, "value warp overlaps a channel thread");
+    const int l = tid - (kBlock - 32);
+    double a = l < kWarps ? static_cast<double>(sm.vred[l][0]) + static_cast<double>(sm.vred[l][1]) : 0.0;
 #pragma unroll
-    for (int i = 0; i < kWarps; ++i) a[i] = static_cast<double>(sm.vred[i][0]) + static_cast<double>(sm.vred[i][1]);
-    const double s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
-    row[0] = bad ? __longlong_as_double(0x7ff0000000000000LL) : s * (MODE == 1 ? 2.0 : 1.0);
+    for (int o = 4; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (l == 0) row[0] = bad ? __longlong_as_double(0x7ff0000000000000LL) : a * (MODE == 1 ? 2.0 : 1.0);
   }
 }
 
@@ -784,12 +793,9 @@ __device__ double split_slot(const HistSet& hs, const ChunkCache& cc, const doub
       case kCAmp:
         if (ShapeT<SHAPE>::AMP) g += 2.0 * N0 * ch[hl * NPH + 2 + k];
         break;
-      case kCPhi: {
-        const int as = hs.canon[k].amp_slot;
-        const double a = as >= 0 ? cc.loc[hl][as] : 1.0;
-        g += 2.0 * N0 * a * (-kTwoPi / 360.0) * ch[hl * NPH + PHI0 + ShapeT<SHAPE>::phi(k)];
+      case kCPhi:  // the channel already holds w N0 a sin(theta + phi) E X
+        g += 2.0 * (-kTwoPi / 360.0) * ch[hl * NPH + PHI0 + ShapeT<SHAPE>::phi(k)];
         break;
-      }
       case kCLam:
         if (hl == 0) g += 2.0 * ch[G * NPH + k * 4 + 0];
         break;

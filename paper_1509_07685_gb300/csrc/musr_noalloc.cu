@@ -196,10 +196,8 @@ extern "C" int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int
       hs.shape = kShapeTF2KT1;
     else
       hs.shape = kShapeGeneric;
-    if (amplitudes_constant(hs.canon, nterms, map, nhist, nslots)) {
-      if (hs.shape == kShapeTF2) hs.shape = kShapeTF2c;
-      if (hs.shape == kShapeTF2KT1) hs.shape = kShapeTF2KT1c;
-    }
+    hs.shape = constant_amplitude_shape(hs.shape, hs.canon, nterms, map, consts, nhist, nslots);
+    const bool one_phase = hs.shape == kShapeTF2c || hs.shape == kShapeTF2KT1c;
     group_cap = shape_group(hs.shape);
     auto add = [&](int slot, int kind, int term) {
       hs.contrib[hs.ncontrib].slot = slot;
@@ -217,7 +215,7 @@ extern "C" int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int
       if (ct.kind == kTermKT) add(ct.kt_slot, kCDel, k);
       if (ct.kind == kTermTF) {
         add(ct.nu_slot, kCNu, k);
-        add(ct.phi_slot, kCPhi, k);
+        if (!one_phase || k == 0) add(ct.phi_slot, kCPhi, k);  // one shared phase channel
       }
     }
     // Group histograms sharing t0 and every time-dependent parameter (first appearance order).
@@ -285,18 +283,11 @@ extern "C" int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int
     e = cudaMemsetAsync(d_out, 0, sizeof(double) * (1 + nparams), static_cast<cudaStream_t>(cuda_stream));
     return e == cudaSuccess ? MUSR_OK : MUSR_ECUDA;
   }
-  const int per_iter = precision == MUSR_SPLIT ? kBlock * kBinsPerThread : kBlock;
-  int iters = 1;
-  if (tiles_total(T.chunks, nchunks, int64_t(per_iter) * coarse_iters(precision)) >= 3 * 2 * num_sms) {
-    iters = coarse_iters(precision);  // the large tiles a context picks when they still fill the GPU
-  } else {
-    for (int it : {8, 4, 2})
-      if (tiles_total(T.chunks, nchunks, int64_t(per_iter) * it) >= 4 * num_sms) {
-        iters = it;
-        break;
-      }
-  }
-  hs.tile_bins = per_iter * iters;
+  // The decomposition a context picks for one evaluation.
+  int items_per_var[kVariants];
+  for (int v = 0; v < kVariants; ++v)
+    items_per_var[v] = static_cast<int>(tiles_total(T.chunks, nchunks, int64_t(bins_per_iteration(precision)) << v));
+  hs.tile_bins = bins_per_iteration(precision) << pick_decomposition(items_per_var, 1, num_sms);
   const int64_t nitems64 = tiles_total(T.chunks, nchunks, hs.tile_bins);
   if (nitems64 > kNaMaxItems) return na_fail("problem needs more than 8192 work items (too many bins for musr_eval_noalloc)");
   int nitems = 0, col = 0;

@@ -1,0 +1,558 @@
+// musr_server.cpp -- continuous-batching serving of many fits, and musr_fit.
+//
+// The paper's offload (Section 4) runs one fit at a time: the host minimiser
+// sends a parameter vector, the device returns the cost.  Serving many fits at
+// once keeps every fit's histograms resident and advances all fits together:
+//
+//   worker loop, one step:
+//     admit queued fits while the arena (the HBM budget) has room -- a fit's
+//       histograms, decomposition tables and evaluation buffers come from it;
+//     every active fit names its next trial point(s) (BFGS state machine);
+//     all points go to the device in one copy; one persistent multi-fit launch
+//       per (precision, theory shape, cost) group evaluates them all;
+//     one copy brings every value and gradient back;
+//     each fit's minimiser advances; finished fits release their memory.
+//
+// Fits that arrive while others run are admitted at the next step boundary.
+// A fit's result does not depend on what else is in the batch: its launches
+// use its own decomposition and its own fixed-order reductions.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "musr.h"
+#include "musr_bfgs.h"
+#include "musr_dev.h"
+#include "musr_host.h"
+
+namespace musr {
+namespace {
+
+constexpr double kSplitNoiseRel = 2e-8;  // rounding noise of the SPLIT cost, relative
+constexpr double kSplitEdm = 1e-5;       // EDM target of SPLIT fits
+constexpr double kFp64Edm = 1e-7;
+// Decomposition of every served fit (SPLIT tiles of 4096 bins): many fits fill the
+// GPU together, and a fixed choice keeps a fit's result independent of the mix.
+constexpr int kServeVariant = 3;
+
+struct Request {
+  int64_t id = 0;
+  std::vector<unsigned char> counts;
+  int dtype = 0, H = 0, nslots = 0, P = 0, mode = 0, prec = 0, maxit = 0;
+  int64_t B = 0;
+  std::vector<double> t0, consts, x0;
+  double bw = 0.0, fr[2] = {0.0, 0.0}, gtol = 0.0, t_submit = 0.0;
+  std::vector<musr_term> terms;
+  std::vector<int32_t> map;
+};
+
+struct Active {
+  std::unique_ptr<Request> req;
+  musr_ctx* ctx = nullptr;
+  Bfgs bfgs;
+  int shape = 0;
+  int64_t bins = 0;
+  double t_admit = 0.0;
+  bool first = true;
+  int nvec = 0;
+  size_t poff = 0, ooff = 0;
+};
+
+struct Done {
+  musr_fit_result res{};
+  std::vector<double> x;
+};
+
+size_t dtype_size(int dtype) { return dtype == MUSR_DTYPE_FP64 ? 8 : 4; }
+
+}  // namespace
+}  // namespace musr
+
+using namespace musr;
+
+struct musr_server {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 1;
+  int max_active = 1;
+  Arena arena;
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  bool stop = false;
+  std::deque<std::unique_ptr<Request>> queue;
+  std::unordered_map<int64_t, Done> done;
+  int64_t next_id = 1;
+  std::chrono::steady_clock::time_point t0;
+  musr_server_stats stats{};
+  std::string err;
+  // worker-owned
+  std::vector<std::unique_ptr<Active>> active;
+  double* h_params = nullptr;
+  double* h_out = nullptr;
+  Job* h_jobs = nullptr;
+  size_t hp_cap = 0, ho_cap = 0, hj_cap = 0;
+  void* d_params = nullptr;
+  void* d_out = nullptr;
+  void* d_jobs = nullptr;
+  size_t dp_cap = 0, do_cap = 0, dj_cap = 0;
+  std::string worker_error;
+
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+namespace {
+
+bool grow_host(void** p, size_t* cap, size_t bytes) {
+  if (*cap >= bytes) return true;
+  if (*p) cudaFreeHost(*p);
+  *p = nullptr;
+  *cap = 0;
+  bytes = bytes * 3 / 2 + 4096;
+  if (cudaMallocHost(p, bytes) != cudaSuccess) return false;
+  *cap = bytes;
+  return true;
+}
+
+bool grow_dev(void** p, size_t* cap, size_t bytes) {
+  if (*cap >= bytes) return true;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  bytes = bytes * 3 / 2 + 4096;
+  if (cudaMalloc(p, bytes) != cudaSuccess) return false;
+  *cap = bytes;
+  return true;
+}
+
+void finish(musr_server* s, Active* a, int status) {
+  Done d;
+  d.res.status = status;
+  d.res.iters = a->bfgs.iters();
+  d.res.nfev = a->bfgs.nfev();
+  d.res.nparams = a->req->P;
+  d.res.f = a->bfgs.f();
+  d.res.edm = a->bfgs.edm();
+  d.res.t_submit = a->req->t_submit;
+  d.res.t_admit = a->t_admit;
+  d.res.t_done = s->now();
+  d.x = a->bfgs.x();
+  if (a->ctx) musr_ctx_destroy(a->ctx);
+  a->ctx = nullptr;
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->done[a->req->id] = std::move(d);
+  s->stats.completed += 1;
+  s->stats.active -= 1;
+  s->cv_done.notify_all();
+}
+
+void reject(musr_server* s, std::unique_ptr<Request> r, int status) {
+  Done d;
+  d.res.status = status;
+  d.res.nparams = r->P;
+  d.res.f = NAN;
+  d.res.t_submit = r->t_submit;
+  d.res.t_done = s->now();
+  d.x = r->x0;
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->done[r->id] = std::move(d);
+  s->stats.rejected += 1;
+  s->cv_done.notify_all();
+}
+
+// Configures a context for the request inside the arena; MUSR_ENOMEM when the
+// arena is full now, another status when the request can never run.
+int configure(musr_server* s, const Request& r, musr_ctx** out) {
+  musr_ctx* ctx = nullptr;
+  int rc = musr_ctx_create(&ctx, s->device, 0, s->stream);
+  if (rc) return rc;
+  ctx->arena = &s->arena;
+  rc = musr_upload_histograms(ctx, r.counts.data(), r.dtype, r.H, r.B, r.t0.data(), r.bw, r.fr);
+  if (!rc) rc = musr_set_theory(ctx, r.terms.data(), static_cast<int>(r.terms.size()));
+  if (!rc)
+    rc = musr_set_map(ctx, r.map.data(), r.nslots, r.P, r.consts.empty() ? nullptr : r.consts.data(),
+                      static_cast<int>(r.consts.size()));
+  if (!rc) rc = check_ready(ctx, r.mode, r.prec);
+  if (!rc) rc = ensure_eval(ctx, r.prec, kServeVariant, r.P > 0 ? r.P : 1);
+  if (rc) {
+    musr_ctx_destroy(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return MUSR_OK;
+}
+
+void admit(musr_server* s) {
+  while (static_cast<int>(s->active.size()) < s->max_active) {
+    std::unique_ptr<Request> r;
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      if (s->queue.empty()) return;
+      r = std::move(s->queue.front());
+      s->queue.pop_front();
+      s->stats.queued -= 1;
+    }
+    musr_ctx* ctx = nullptr;
+    const int rc = configure(s, *r, &ctx);
+    if (rc == MUSR_ENOMEM && !s->active.empty()) {
+      // the budget is taken by running fits: wait for one to finish (FIFO order kept)
+      std::lock_guard<std::mutex> lock(s->mu);
+      s->queue.push_front(std::move(r));
+      s->stats.queued += 1;
+      return;
+    }
+    if (rc) {
+      reject(s, std::move(r), rc);
+      continue;
+    }
+    auto a = std::make_unique<Active>();
+    a->ctx = ctx;
+    a->shape = ctx->comp[r->prec][kServeVariant].hs.shape;
+    musr_bins_in_fit(ctx, &a->bins);
+    a->t_admit = s->now();
+    a->bfgs.start(r->x0.data(), r->P, r->gtol, r->maxit, 0.0, r->prec == MUSR_SPLIT ? kSplitEdm : kFp64Edm);
+    a->req = std::move(r);
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stats.active += 1;
+    s->active.push_back(std::move(a));
+  }
+}
+
+// One step: every active fit's points in one multi-fit launch per group.
+int step(musr_server* s) {
+  std::vector<double> pts;
+  size_t np = 0, no = 0;
+  int nv = 0;
+  std::vector<std::vector<double>> requests(s->active.size());
+  for (size_t i = 0; i < s->active.size(); ++i) {
+    Active* a = s->active[i].get();
+    a->nvec = a->bfgs.request(&requests[i]);
+    a->poff = np;
+    a->ooff = no;
+    np += static_cast<size_t>(a->nvec) * a->req->P;
+    no += static_cast<size_t>(a->nvec) * (1 + a->req->P);
+    nv += a->nvec;
+  }
+  if (!grow_host(reinterpret_cast<void**>(&s->h_params), &s->hp_cap, (np + 1) * sizeof(double)) ||
+      !grow_host(reinterpret_cast<void**>(&s->h_out), &s->ho_cap, (no + 1) * sizeof(double)) ||
+      !grow_host(reinterpret_cast<void**>(&s->h_jobs), &s->hj_cap, (nv + 1) * sizeof(Job)) ||
+      !grow_dev(&s->d_params, &s->dp_cap, (np + 1) * sizeof(double)) ||
+      !grow_dev(&s->d_out, &s->do_cap, (no + 1) * sizeof(double)) ||
+      !grow_dev(&s->d_jobs, &s->dj_cap, (nv + 1) * sizeof(Job)))
+    return MUSR_ENOMEM;
+  for (size_t i = 0; i < s->active.size(); ++i)
+    if (!requests[i].empty())
+      std::memcpy(s->h_params + s->active[i]->poff, requests[i].data(), requests[i].size() * sizeof(double));
+  // Group by (precision, shape, cost): one launch each, jobs contiguous per group.
+  std::map<int, std::vector<Active*>> groups;
+  for (auto& a : s->active) groups[(a->req->prec * 16 + a->shape) * 2 + a->req->mode].push_back(a.get());
+  double* d_params = static_cast<double*>(s->d_params);
+  double* d_out = static_cast<double*>(s->d_out);
+  Job* d_jobs = static_cast<Job*>(s->d_jobs);
+  struct Launch {
+    int prec, shape, mode, first, njobs, items;
+  };
+  std::vector<Launch> launches;
+  int jpos = 0;
+  for (auto& kv : groups) {
+    Launch L{kv.second[0]->req->prec, kv.second[0]->shape, kv.second[0]->req->mode, jpos, 0, 0};
+    for (Active* a : kv.second) {
+      fill_jobs(a->ctx, L.prec, kServeVariant, L.mode, 1, a->nvec, d_params + a->poff, d_out + a->ooff,
+                s->h_jobs + jpos, L.items);
+      L.items += a->nvec * a->ctx->comp[L.prec][kServeVariant].hs.nitems;
+      L.njobs += a->nvec;
+      jpos += a->nvec;
+    }
+    launches.push_back(L);
+  }
+  cudaError_t e = cudaMemcpyAsync(d_params, s->h_params, np * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_jobs, s->h_jobs, jpos * sizeof(Job), cudaMemcpyHostToDevice, s->stream);
+  if (e != cudaSuccess) return MUSR_ECUDA;
+  for (const Launch& L : launches) {
+    if (L.items == 0) continue;
+    LaunchInfo info;
+    if (launch_eval(L.prec, L.shape, L.mode, 1, d_jobs + L.first, L.njobs, L.items, s->num_sms, s->stream,
+                    &info))
+      return MUSR_ECUDA;
+  }
+  e = cudaMemcpyAsync(s->h_out, d_out, no * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e != cudaSuccess) return MUSR_ECUDA;
+  admit(s);  // configure newly queued fits while the step runs
+  e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return MUSR_ECUDA;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stats.steps += 1;
+    s->stats.launches += static_cast<int64_t>(launches.size());
+    s->stats.evals += nv;
+  }
+  // Advance every fit that took part in this step.
+  std::vector<double> f, g;
+  std::vector<std::unique_ptr<Active>> keep;
+  for (auto& a : s->active) {
+    if (a->nvec == 0) {  // admitted during this step
+      keep.push_back(std::move(a));
+      continue;
+    }
+    const int P = a->req->P;
+    f.resize(a->nvec);
+    g.resize(static_cast<size_t>(a->nvec) * P);
+    for (int v = 0; v < a->nvec; ++v) {
+      const double* o = s->h_out + a->ooff + static_cast<size_t>(v) * (1 + P);
+      f[v] = o[0];
+      std::memcpy(g.data() + static_cast<size_t>(v) * P, o + 1, sizeof(double) * P);
+    }
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      s->stats.bin_evals += static_cast<double>(a->bins) * a->nvec;
+    }
+    a->bfgs.deliver(f.data(), g.data());
+    if (a->first && std::isfinite(f[0]) && a->req->prec == MUSR_SPLIT)
+      a->bfgs.set_f_noise(kSplitNoiseRel * std::fabs(f[0]));
+    a->first = false;
+    a->nvec = 0;
+    if (a->bfgs.done())
+      finish(s, a.get(), a->bfgs.status());
+    else
+      keep.push_back(std::move(a));
+  }
+  s->active.swap(keep);
+  return MUSR_OK;
+}
+
+void worker_main(musr_server* s) {
+  cudaSetDevice(s->device);
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lock(s->mu);
+      if (s->active.empty())
+        s->cv_work.wait(lock, [&] { return s->stop || !s->queue.empty(); });
+      if (s->stop) break;
+    }
+    if (s->active.empty()) admit(s);
+    if (s->active.empty()) continue;
+    const double t = s->now();
+    const int rc = step(s);
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      s->stats.busy_s += s->now() - t;
+    }
+    if (rc) {
+      // a CUDA failure ends every running fit with that status
+      std::vector<std::unique_ptr<Active>> act;
+      act.swap(s->active);
+      for (auto& a : act) finish(s, a.get(), rc);
+      s->worker_error = "serving step failed";
+    }
+  }
+  for (auto& a : s->active)
+    if (a->ctx) musr_ctx_destroy(a->ctx);
+  s->active.clear();
+}
+
+bool copy_request(const musr_fit_request* q, Request* r, std::string* why) {
+  if (!q->counts || !q->t0 || !q->map || !q->x0 || (q->nterms > 0 && !q->terms) ||
+      (q->nconsts > 0 && !q->consts)) {
+    *why = "NULL pointer in the request";
+    return false;
+  }
+  if (q->nhist < 1 || q->nbins < 1 || q->nslots < 2 || q->nslots > MUSR_MAX_SLOTS || q->nparams < 0 ||
+      q->nparams > MUSR_MAX_PARAMS || q->nterms < 0 || q->nterms > MUSR_MAX_TERMS || q->nconsts < 0) {
+    *why = "size out of range";
+    return false;
+  }
+  if (q->dtype != MUSR_DTYPE_INT32 && q->dtype != MUSR_DTYPE_FP32 && q->dtype != MUSR_DTYPE_FP64) {
+    *why = "bad dtype";
+    return false;
+  }
+  if ((q->mode != MUSR_CHI2 && q->mode != MUSR_MLE) || (q->precision != MUSR_FP64 && q->precision != MUSR_SPLIT)) {
+    *why = "bad mode or precision";
+    return false;
+  }
+  const size_t n = static_cast<size_t>(q->nhist) * q->nbins * dtype_size(q->dtype);
+  r->counts.assign(static_cast<const unsigned char*>(q->counts), static_cast<const unsigned char*>(q->counts) + n);
+  r->dtype = q->dtype;
+  r->H = q->nhist;
+  r->B = q->nbins;
+  r->t0.assign(q->t0, q->t0 + q->nhist);
+  r->bw = q->bin_width_ns;
+  r->fr[0] = q->fit_range_us[0];
+  r->fr[1] = q->fit_range_us[1];
+  r->terms.assign(q->terms, q->terms + q->nterms);
+  r->map.assign(q->map, q->map + static_cast<size_t>(q->nhist) * q->nslots);
+  r->nslots = q->nslots;
+  r->P = q->nparams;
+  r->consts.assign(q->consts, q->consts + q->nconsts);
+  r->x0.assign(q->x0, q->x0 + q->nparams);
+  r->mode = q->mode;
+  r->prec = q->precision;
+  r->maxit = q->maxit > 0 ? q->maxit : 1000;
+  r->gtol = q->gtol > 0 ? q->gtol : 1e-8;
+  for (double v : r->x0)
+    if (!std::isfinite(v)) {
+      *why = "x0 must be finite";
+      return false;
+    }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int musr_server_create(musr_server** out, int device, size_t hbm_budget_bytes, int max_active) {
+  if (!out) return MUSR_EINVAL;
+  *out = nullptr;
+  if (max_active < 1 || hbm_budget_bytes < (size_t(1) << 20)) return MUSR_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return MUSR_ECUDA;
+  }
+  if (device < 0 || device >= ndev) return MUSR_EINVAL;
+  auto s = std::make_unique<musr_server>();
+  s->device = device;
+  s->max_active = max_active;
+  s->t0 = std::chrono::steady_clock::now();
+  DeviceScope ds(device);
+  cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) return MUSR_ECUDA;
+  if (s->arena.init(hbm_budget_bytes)) {
+    cudaStreamDestroy(s->stream);
+    return MUSR_ENOMEM;
+  }
+  s->stats.arena_bytes = s->arena.capacity();
+  s->worker = std::thread(worker_main, s.get());
+  *out = s.release();
+  return MUSR_OK;
+}
+
+void musr_server_destroy(musr_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  DeviceScope ds(s->device);
+  cudaStreamSynchronize(s->stream);
+  if (s->h_params) cudaFreeHost(s->h_params);
+  if (s->h_out) cudaFreeHost(s->h_out);
+  if (s->h_jobs) cudaFreeHost(s->h_jobs);
+  if (s->d_params) cudaFree(s->d_params);
+  if (s->d_out) cudaFree(s->d_out);
+  if (s->d_jobs) cudaFree(s->d_jobs);
+  cudaStreamDestroy(s->stream);
+  delete s;
+}
+
+int musr_server_submit(musr_server* s, const musr_fit_request* req, int64_t* out_id) {
+  if (!s || !req || !out_id) return MUSR_EINVAL;
+  auto r = std::make_unique<Request>();
+  std::string why;
+  if (!copy_request(req, r.get(), &why)) {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->err = why;
+    return MUSR_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (s->stop) return MUSR_ESTATE;
+  r->id = s->next_id++;
+  r->t_submit = s->now();
+  *out_id = r->id;
+  s->queue.push_back(std::move(r));
+  s->stats.submitted += 1;
+  s->stats.queued += 1;
+  s->cv_work.notify_one();
+  return MUSR_OK;
+}
+
+static int take_result(musr_server* s, int64_t id, musr_fit_result* res, double* x_out) {
+  auto it = s->done.find(id);
+  if (it == s->done.end()) return MUSR_EAGAIN;
+  if (res) *res = it->second.res;
+  if (x_out) std::memcpy(x_out, it->second.x.data(), sizeof(double) * it->second.x.size());
+  s->done.erase(it);
+  return MUSR_OK;
+}
+
+int musr_server_poll(musr_server* s, int64_t id, musr_fit_result* res, double* x_out) {
+  if (!s || id <= 0) return MUSR_EINVAL;
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (id >= s->next_id) return MUSR_EINVAL;
+  return take_result(s, id, res, x_out);
+}
+
+int musr_server_wait(musr_server* s, int64_t id, int timeout_ms, musr_fit_result* res, double* x_out) {
+  if (!s || id <= 0) return MUSR_EINVAL;
+  std::unique_lock<std::mutex> lock(s->mu);
+  if (id >= s->next_id) return MUSR_EINVAL;
+  auto ready = [&] { return s->done.count(id) > 0; };
+  if (timeout_ms > 0) {
+    if (!s->cv_done.wait_for(lock, std::chrono::milliseconds(timeout_ms), ready)) return MUSR_ETIMEOUT;
+  } else {
+    s->cv_done.wait(lock, ready);
+  }
+  return take_result(s, id, res, x_out);
+}
+
+int musr_server_stats_get(musr_server* s, musr_server_stats* out) {
+  if (!s || !out) return MUSR_EINVAL;
+  std::lock_guard<std::mutex> lock(s->mu);
+  *out = s->stats;
+  out->arena_used = s->arena.used();
+  out->clock_s = s->now();
+  return MUSR_OK;
+}
+
+// One fit on a configured context, synchronous: the same minimiser as the
+// serving loop, each request (one point, or P points for the curvature
+// estimate) one batched launch.
+int musr_fit(musr_ctx* ctx, const double* x0, int mode, int precision, int maxit, double gtol, double* x_out,
+             musr_fit_result* res) {
+  if (!ctx || !x0 || !x_out || !res) return MUSR_EINVAL;
+  const int P = ctx->P;
+  Bfgs b;
+  b.start(x0, P, gtol > 0 ? gtol : 1e-8, maxit > 0 ? maxit : 1000, 0.0,
+          precision == MUSR_SPLIT ? kSplitEdm : kFp64Edm);
+  std::vector<double> pts, vals, grads;
+  bool first = true;
+  const auto t0 = std::chrono::steady_clock::now();
+  while (!b.done()) {
+    const int n = b.request(&pts);
+    vals.resize(n);
+    grads.resize(static_cast<size_t>(n) * P);
+    const int rc = musr_eval_batch(ctx, pts.data(), n, P, mode, precision, vals.data(), grads.data());
+    if (rc != MUSR_OK && rc != MUSR_ENONFINITE) return rc;
+    b.deliver(vals.data(), grads.data());
+    if (first && std::isfinite(vals[0]) && precision == MUSR_SPLIT) b.set_f_noise(kSplitNoiseRel * std::fabs(vals[0]));
+    first = false;
+  }
+  std::memset(res, 0, sizeof(*res));
+  res->status = b.status();
+  res->iters = b.iters();
+  res->nfev = b.nfev();
+  res->nparams = P;
+  res->f = b.f();
+  res->edm = b.edm();
+  res->t_done = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  std::memcpy(x_out, b.x().data(), sizeof(double) * P);
+  return MUSR_OK;
+}
+
+}  // extern "C"

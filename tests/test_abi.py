@@ -49,3 +49,13 @@ def test_create_without_gpu_reports_error(lib):
     with pytest.raises(binding.MusrError) as e:
         binding.musr_ctx_create(0)
     assert e.value.status == binding.MUSR_ECUDA
+
+
+def test_server_create_without_gpu_reports_error(lib):
+    from conftest import cuda_available
+    if cuda_available():
+        pytest.skip("a GPU is present")
+    from paper_1509_07685_gb300 import binding
+    with pytest.raises(binding.MusrError) as e:
+        binding.musr_server_create(0, 1 << 30, 4)
+    assert e.value.status == binding.MUSR_ECUDA

@@ -88,15 +88,19 @@ def test_fp64_and_split_match_oracle(B, name, mode):
 
 
 def test_batch_equals_single_and_is_deterministic(B):
+    """A batch may use larger tiles than a single evaluation (so its sums run in another
+    order): equal within the path's tolerance.  The same launch repeated is bit-identical."""
     p = problems()["cfg2"]
-    X = mi.jitter(p.truth, 5, seed=3, lo=0.95, hi=1.05)
+    X = mi.jitter(p.truth, 40, seed=3, lo=0.95, hi=1.05)
     with B.Context(p) as ctx:
-        for prec in (B.MUSR_FP64, B.MUSR_SPLIT):
+        for prec, tol in ((B.MUSR_FP64, FP64_TOL), (B.MUSR_SPLIT, SPLIT_EPS)):
             vals, grads, st = ctx.eval_batch(X, 1, prec)
             assert st == 0
-            for i in range(len(X)):
+            for i in range(0, len(X), 7):
                 v, g, _ = ctx.eval(X[i], 1, prec)
-                assert v == vals[i] and np.array_equal(g, grads[i])  # bit-identical
+                gs = oracle.cost(p, X[i], 1)[2]
+                assert abs(v - vals[i]) <= tol * abs(v)
+                assert np.all(np.abs(g - grads[i]) <= tol * gs + 1e-300)
             vals2, grads2, _ = ctx.eval_batch(X, 1, prec)
             assert np.array_equal(vals, vals2) and np.array_equal(grads, grads2)
 
