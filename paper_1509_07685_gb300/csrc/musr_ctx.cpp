@@ -189,13 +189,15 @@ void fit_bins(double t0, double dt_us, int64_t B, double lo, double hi, int* nlo
 }
 
 void free_compiled(musr_ctx* ctx, Compiled& c) {
-  dfree(ctx, c.d_hs);
-  dfree(ctx, c.chunks);
-  dfree(ctx, c.items);
-  dfree(ctx, c.hist_index);
-  dfree(ctx, c.col_chunk);
-  dfree(ctx, c.p_ptr);
-  dfree(ctx, c.p_cols);
+  dfree(ctx, c.tables);
+  c.d_hs = nullptr;
+  c.uploaded = false;
+  c.chunks.clear();
+  c.items.clear();
+  c.hist_index.clear();
+  c.col_chunk.clear();
+  c.p_ptr.clear();
+  c.p_cols.clear();
   c.valid = false;
   c.reason.clear();
 }
@@ -414,22 +416,61 @@ int compile(musr_ctx* ctx, int prec, int var) {
   }
   p_ptr[ctx->P] = static_cast<int>(p_cols.size());
   if (p_cols.empty()) p_cols.push_back(0);
-  int rc;
-  if ((rc = upload(ctx, c.chunks, chunks.data(), sizeof(Chunk) * chunks.size()))) return rc;
-  if ((rc = upload(ctx, c.items, items.data(), sizeof(int2) * items.size()))) return rc;
-  if ((rc = upload(ctx, c.hist_index, hist_index.data(), sizeof(int) * hist_index.size()))) return rc;
-  if ((rc = upload(ctx, c.col_chunk, col_chunk.data(), sizeof(int) * col_chunk.size()))) return rc;
-  if ((rc = upload(ctx, c.p_ptr, p_ptr.data(), sizeof(int) * p_ptr.size()))) return rc;
-  if ((rc = upload(ctx, c.p_cols, p_cols.data(), sizeof(int) * p_cols.size()))) return rc;
-  hs.chunks = static_cast<const Chunk*>(c.chunks.p);
-  hs.items = static_cast<const int2*>(c.items.p);
-  hs.hist_index = static_cast<const int*>(c.hist_index.p);
-  hs.col_chunk = static_cast<const int*>(c.col_chunk.p);
-  hs.p_ptr = static_cast<const int*>(c.p_ptr.p);
-  hs.p_cols = static_cast<const int*>(c.p_cols.p);
-  if ((rc = upload(ctx, c.d_hs, &hs, sizeof(hs)))) return rc;
+  if (items.empty()) items.push_back(make_int2(0, 0));
+  if (chunks.empty()) chunks.push_back(Chunk{});
+  if (hist_index.empty()) hist_index.push_back(0);
+  c.chunks = std::move(chunks);
+  c.items = std::move(items);
+  c.hist_index = std::move(hist_index);
+  c.col_chunk = std::move(col_chunk);
+  c.p_ptr = std::move(p_ptr);
+  c.p_cols = std::move(p_cols);
   c.hs = hs;
   c.valid = true;
+  c.uploaded = false;
+  return MUSR_OK;
+}
+
+// Copies one decomposition's tables to the device (first use only): one
+// allocation holding the HistSet and every table, one copy.
+int ensure_uploaded(musr_ctx* ctx, int prec, int var) {
+  Compiled& c = ctx->comp[prec][var];
+  if (c.uploaded) return MUSR_OK;
+  size_t off = 0;
+  auto place = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) & ~size_t(255);
+    return o;
+  };
+  const size_t o_hs = place(sizeof(HistSet));
+  const size_t o_ch = place(sizeof(Chunk) * c.chunks.size());
+  const size_t o_it = place(sizeof(int2) * c.items.size());
+  const size_t o_hi = place(sizeof(int) * c.hist_index.size());
+  const size_t o_cc = place(sizeof(int) * c.col_chunk.size());
+  const size_t o_pp = place(sizeof(int) * c.p_ptr.size());
+  const size_t o_pc = place(sizeof(int) * c.p_cols.size());
+  int rc = dalloc(ctx, c.tables, off);
+  if (rc) return rc;
+  char* base = static_cast<char*>(c.tables.p);
+  HistSet& hs = c.hs;
+  hs.chunks = reinterpret_cast<const Chunk*>(base + o_ch);
+  hs.items = reinterpret_cast<const int2*>(base + o_it);
+  hs.hist_index = reinterpret_cast<const int*>(base + o_hi);
+  hs.col_chunk = reinterpret_cast<const int*>(base + o_cc);
+  hs.p_ptr = reinterpret_cast<const int*>(base + o_pp);
+  hs.p_cols = reinterpret_cast<const int*>(base + o_pc);
+  std::vector<char> blob(off, 0);
+  std::memcpy(blob.data() + o_hs, &hs, sizeof(hs));
+  std::memcpy(blob.data() + o_ch, c.chunks.data(), sizeof(Chunk) * c.chunks.size());
+  std::memcpy(blob.data() + o_it, c.items.data(), sizeof(int2) * c.items.size());
+  std::memcpy(blob.data() + o_hi, c.hist_index.data(), sizeof(int) * c.hist_index.size());
+  std::memcpy(blob.data() + o_cc, c.col_chunk.data(), sizeof(int) * c.col_chunk.size());
+  std::memcpy(blob.data() + o_pp, c.p_ptr.data(), sizeof(int) * c.p_ptr.size());
+  std::memcpy(blob.data() + o_pc, c.p_cols.data(), sizeof(int) * c.p_cols.size());
+  cudaError_t e = cudaMemcpy(base, blob.data(), off, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy(tables)");
+  c.d_hs = reinterpret_cast<const HistSet*>(base + o_hs);
+  c.uploaded = true;
   return MUSR_OK;
 }
 
@@ -447,6 +488,8 @@ int pick_variant(musr_ctx* ctx, int prec, int nvec) {
 // (precision, decomposition, mode, grad, nvec, pointers) changes.
 int ensure_eval(musr_ctx* ctx, int prec, int var, int nvec) {
   EvalBufs& ev = ctx->ev;
+  int urc = ensure_uploaded(ctx, prec, var);
+  if (urc) return urc;
   const HistSet& hs = ctx->comp[prec][var].hs;
   const size_t part = static_cast<size_t>(nvec) * hs.nitems * hs.pstride;
   const size_t cols = static_cast<size_t>(nvec) * std::max(hs.ncols, 1);
@@ -475,7 +518,7 @@ void fill_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, c
                double* d_out, Job* jobs, int item_begin) {
   EvalBufs& ev = ctx->ev;
   const HistSet& hs = ctx->comp[prec][var].hs;
-  const HistSet* d_hs = static_cast<const HistSet*>(ctx->comp[prec][var].d_hs.p);
+  const HistSet* d_hs = ctx->comp[prec][var].d_hs;
   for (int v = 0; v < nvec; ++v) {
     Job& j = jobs[v];
     std::memset(&j, 0, sizeof(j));
@@ -886,11 +929,12 @@ int musr_eval_batch(musr_ctx* ctx, const double* params, int nvec, int nparams, 
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(out)");
   e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
-  bool nonfinite = false;
+  bool nonfinite = false, timed_out = false;
   for (int v = 0; v < nvec; ++v) {
     const double* o = ev.h_out + static_cast<size_t>(v) * (1 + P);
     out_values[v] = o[0];
     if (!std::isfinite(o[0])) nonfinite = true;
+    if (std::isnan(o[0])) timed_out = true;  // a kernel's bounded wait ran out
     if (out_grads) {
       double* g = out_grads + static_cast<size_t>(v) * P;
       if (std::isfinite(o[0]))
@@ -899,6 +943,7 @@ int musr_eval_batch(musr_ctx* ctx, const double* params, int nvec, int nparams, 
         std::memset(g, 0, P * sizeof(double));
     }
   }
+  if (timed_out) return fail(ctx, MUSR_ETIMEOUT, "a device-side wait for staged counts ran out (value NaN)");
   if (nonfinite) return fail(ctx, MUSR_ENONFINITE, "-2lnL is +inf: N <= 0 in a bin with d > 0");
   return MUSR_OK;
 }

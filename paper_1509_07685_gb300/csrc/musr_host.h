@@ -41,11 +41,18 @@ class Arena {
 };
 
 // The theory and map of one precision, compiled to a work decomposition.
+// The tables are planned on the host when the map is set and copied to the
+// device (one allocation, one copy) the first time a launch needs them.
 struct Compiled {
   bool valid = false;
   std::string reason;  // why this precision is unavailable (valid == false)
-  HistSet hs{};        // host copy (device pointers inside)
-  DevBuf d_hs, chunks, items, hist_index, col_chunk, p_ptr, p_cols;
+  HistSet hs{};        // host copy (device pointers inside once uploaded)
+  std::vector<Chunk> chunks;
+  std::vector<int2> items;
+  std::vector<int> hist_index, col_chunk, p_ptr, p_cols;
+  bool uploaded = false;
+  DevBuf tables;        // HistSet + all tables, 256-byte aligned pieces
+  const HistSet* d_hs = nullptr;
 };
 
 // Buffers of the eval entry points and the cached job table of the last launch.

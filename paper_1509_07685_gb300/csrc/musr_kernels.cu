@@ -79,6 +79,45 @@ __device__ __forceinline__ float rint_small(float x) {
   return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
 }
 
+// ---------------------------------------------------------------------------------------------
+// TMA bulk copies global -> shared with mbarrier completion (documented PTX ISA).
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for phase `parity` of the barrier; false when the iteration limit ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (int i = 0; i < (1 << 20); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -140,6 +179,10 @@ struct TileState {
 };
 
 struct Smem {
+  // SPLIT, FP32 counts: the rows of the current and the next CTA iteration, staged
+  // by TMA bulk copies (one per histogram row segment), one mbarrier per buffer.
+  alignas(128) float stage[2][kGroupMax][kBlock * kBinsPerThread];
+  unsigned long long bar[2];
   ChunkCache cc;
   TileState ts;
   float cred[kWarps][kMaxChan];  // per-warp FP32 channel sums
@@ -513,7 +556,7 @@ struct ShapeChan {
 };
 
 template <int SHAPE, int MODE, bool GRAD>
-__device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm) {
+__device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm, uint32_t& parity) {
   using Sh = ShapeT<SHAPE>;
   constexpr int NT = Sh::NT;
   constexpr int G = Sh::G;
@@ -543,14 +586,37 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     for (int q = 0; q < 4; ++q) sh[k][q] = 0.0f;
   int bad = 0;
 
-  const int iters = hs.tile_bins / (kBlock * BPT);
+  constexpr int CHUNK_BINS = kBlock * BPT;  // bins of one CTA iteration
+  // Iterations of this tile that hold any bin of the fit range (the same for every thread).
+  const int iters = min(hs.tile_bins / CHUNK_BINS, (nhi - ts + CHUNK_BINS - 1) / CHUNK_BINS);
+  // FP32 counts are staged into shared memory one iteration ahead by TMA bulk copies.
+  const bool staged = store == kStoreF32;
+  const int64_t stride = hs.stride;
+  auto issue = [&](int itn, int b) {  // one thread: the rows of iteration itn into buffer b
+    const int64_t nstart = ts + static_cast<int64_t>(itn) * CHUNK_BINS;
+    const int64_t avail = stride - nstart;  // > 0: nstart < nhi <= stride
+    const unsigned bytes = static_cast<unsigned>((avail < CHUNK_BINS ? avail : CHUNK_BINS) * sizeof(float));
+    mbar_expect_tx(&sm.bar[b], bytes * nh);
+    for (int hl = 0; hl < nh; ++hl)
+      tma_load_1d(&sm.stage[b][hl][0], static_cast<const float*>(cc.rowp[hl]) + nstart, bytes, &sm.bar[b]);
+  };
+  int stall = 0;
+  if (staged && tid == 0 && iters > 0) issue(0, 0);
   // The bin offset in the tile is carried as an exact float (integers < 2^24): an
   // int-to-float conversion per bin would occupy this GPU's slow FP64/conversion pipe.
   float fm0 = static_cast<float>(tid * BPT);
-  for (int it = 0; it < iters; ++it, fm0 += static_cast<float>(kBlock * BPT)) {
-    const int m0 = it * kBlock * BPT + tid * BPT;  // offset in the tile (< 2^14)
+  for (int it = 0; it < iters; ++it, fm0 += static_cast<float>(CHUNK_BINS)) {
+    const int m0 = it * CHUNK_BINS + tid * BPT;  // offset in the tile (< 2^14)
     const int n0 = ts + m0;
-    if (n0 >= nhi) break;
+    const int b = it & 1;
+    if (staged) {
+      if (it + 1 < iters) {
+        __syncthreads();  // every thread is done with buffer b ^ 1 (iteration it - 1)
+        if (tid == 0) issue(it + 1, b ^ 1);
+      }
+      if (!mbar_wait(&sm.bar[b], (parity >> b) & 1u)) stall = 1;
+      parity ^= 1u << b;
+    }
     float t[BPT];
     bool valid[BPT];
 #pragma unroll
@@ -610,8 +676,8 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     for (int hl = 0; hl < G; ++hl) {
       if (hl >= nh) break;
       float d[BPT];
-      if (store == kStoreF32) {
-        const float2 q = __ldg(reinterpret_cast<const float2*>(static_cast<const float*>(cc.rowp[hl]) + n0));
+      if (staged) {
+        const float2 q = *reinterpret_cast<const float2*>(&sm.stage[b][hl][tid * BPT]);
         d[0] = q.x;
         d[1] = q.y;
       } else {
@@ -650,7 +716,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
           const float r = N - dd;
           if (dd > 0.0f) {
             if (N <= 0.0f) {
-              bad = 1;
+              bad |= valid[j] ? 1 : 0;
               v = 0.0f;
               w = 0.0f;
             } else {
@@ -727,6 +793,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
 
   // ---- thread (FP32) -> warp (FP32; the value as float-float) -> CTA (FP64 trees) -> row.
   bad = __syncthreads_or(bad);
+  stall = __syncthreads_or(stall);
   const int w = tid >> 5, lane = tid & 31;
   float vh = acc_v, vl = -acc_c;
   warp_sum_ff(vh, vl);
@@ -765,7 +832,10 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     double a = l < kWarps ? static_cast<double>(sm.vred[l][0]) + static_cast<double>(sm.vred[l][1]) : 0.0;
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (l == 0) row[0] = bad ? __longlong_as_double(0x7ff0000000000000LL) : a * (MODE == 1 ? 2.0 : 1.0);
+    // +inf: undefined likelihood; NaN: a staging wait ran out (the host reports a timeout)
+    if (l == 0)
+      row[0] = stall ? __longlong_as_double(0x7ff8000000000000LL)
+                     : (bad ? __longlong_as_double(0x7ff0000000000000LL) : a * (MODE == 1 ? 2.0 : 1.0));
   }
 }
 
@@ -911,8 +981,14 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? 2 : 1) eval_kernel(const J
   if (threadIdx.x == 0) {
     sm.cc.job = -1;
     sm.cc.chunk = -1;
+    if (PREC == 1) {
+      mbar_init(&sm.bar[0], 1);
+      mbar_init(&sm.bar[1], 1);
+      mbar_init_fence();
+    }
   }
   __syncthreads();
+  uint32_t parity = 0;  // phase parity of each staging barrier (bit b: buffer b)
   int ji = -1;
   Job job;
   for (int gi = beg; gi < end; ++gi) {
@@ -938,7 +1014,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? 2 : 1) eval_kernel(const J
     if (PREC == 0)
       fp64_item<MODE, GRAD>(job, hs, item, sm);
     else
-      split_item<SHAPE, MODE, GRAD>(job, hs, item, sm);
+      split_item<SHAPE, MODE, GRAD>(job, hs, item, sm, parity);
     complete_item<PREC, SHAPE, GRAD>(job, hs, sm);
   }
 }
