@@ -55,8 +55,10 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            lib = ctypes.CDLL(_LIB_PATH)
+            # MUSR_ORACLE_LIB: another build of this file (the mutation test plants
+            # mistakes in a copy of the source to show that the pins catch them).
+            path = os.environ.get("MUSR_ORACLE_LIB") or build()
+            lib = ctypes.CDLL(path)
             P = ctypes.POINTER
             d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
             prob = [P(d), ctypes.c_int, i64, P(d), d, d, d, ctypes.c_int, P(i32), P(i32), P(i32),

@@ -1,0 +1,60 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of oracle/musr_oracle.cpp (a dropped term, a
+wrong sign or index, a transposed operand, a wrong constant), builds it into a
+temporary library on the CPU, and runs the pin tests against it: every mutant must
+fail at least one pin.  Nothing here touches the GPU or the CUDA library.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "musr_oracle.cpp")
+
+MUTANTS = {
+    "gauss drops the 1/2": ("return std::exp(-0.5 * (p0 * t) * (p0 * t));", "return std::exp(-(p0 * t) * (p0 * t));"),
+    "phase sign": ("return std::cos(2.0 * kPi * (p0 * t + p1 / 360.0));",
+                   "return std::cos(2.0 * kPi * (p0 * t - p1 / 360.0));"),
+    "phase in radians": ("return std::cos(2.0 * kPi * (p0 * t + p1 / 360.0));",
+                         "return std::cos(2.0 * kPi * p0 * t + p1);"),
+    "muon lifetime": ("constexpr double kTauMu = 2.197019;", "constexpr double kTauMu = 2.19703;"),
+    "log argument transposed": ("return 2.0 * ((N - d) + d * std::log(d / N));",
+                                "return 2.0 * ((N - d) + d * std::log(N / d));"),
+    "background dropped": ("return N0 * std::exp(-t / kTauMu) * (1.0 + A) + Nbkg;",
+                           "return N0 * std::exp(-t / kTauMu) * (1.0 + A);"),
+    "t0 sign": ("return (static_cast<double>(n) - pb.t0[h]) * pb.dt_us;",
+                "return (static_cast<double>(n) + pb.t0[h]) * pb.dt_us;"),
+    "fit range open": ("return pb.lo <= t && t <= pb.hi;", "return pb.lo < t && t < pb.hi;"),
+    "chi2 variance off by one": ("return r * r / std::fmax(d, 1.0);", "return r * r / std::fmax(d + 1.0, 1.0);"),
+    "KT derivative misses a t": ("*d0 = (2.0 / 3.0) * p0 * t * t * std::exp(-0.5 * u) * (u - 3.0);",
+                                 "*d0 = (2.0 / 3.0) * p0 * t * std::exp(-0.5 * u) * (u - 3.0);"),
+    "cosine derivative sign": ("*d0 = -s * 2.0 * kPi * t;", "*d0 = s * 2.0 * kPi * t;"),
+    "phase derivative scale": ("*d1 = -s * 2.0 * kPi / 360.0;", "*d1 = -s * 2.0 * kPi;"),
+    "KT sign": ("return 1.0 / 3.0 + (2.0 / 3.0) * (1.0 - u) * std::exp(-0.5 * u);",
+                "return 1.0 / 3.0 + (2.0 / 3.0) * (1.0 + u) * std::exp(-0.5 * u);"),
+    "no compensation": ("      c += (s - t) + x;\n    else\n      c += (x - t) + s;",
+                        "      c += 0.0;\n    else\n      c += 0.0;"),
+    "map scatter to the wrong index": ("        g[m].add(c);", "        g[(m + 1) % pb.P].add(c);"),
+    "N0 derivative drops the asymmetry": ("      dslot[0] += E * (1.0 + A);", "      dslot[0] += E;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site not found: {name}"
+    mutated = src.replace(old, new, 1)
+    cpp = tmp_path / "mutant.cpp"
+    lib = tmp_path / "mutant.so"
+    cpp.write_text(mutated)
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
+                           "-o", str(lib), str(cpp)])
+    env = dict(os.environ, MUSR_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"no pin caught the mutant '{name}':\n{r.stdout[-2000:]}"
