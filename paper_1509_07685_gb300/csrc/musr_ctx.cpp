@@ -20,6 +20,7 @@
 #include "musr.h"
 #include "musr_dev.h"
 #include "musr_host.h"
+#include "musr_plan.h"
 
 using musr::Chunk;
 using musr::HistSet;
@@ -202,43 +203,6 @@ void free_compiled(musr_ctx* ctx, Compiled& c) {
   c.reason.clear();
 }
 
-// Canonical form of one term for the SPLIT kernels; false if the term is not
-// of the form a * exp(-Lambda t - S t^2/2) * [KT or TFCOS].
-static bool canonical(const musr_term& t, CanonTerm* ct, std::string* why) {
-  std::memset(ct, 0, sizeof(*ct));
-  ct->amp_slot = ct->kt_slot = ct->nu_slot = ct->phi_slot = -1;
-  int namp = 0, nkt = 0, ntf = 0;
-  for (int m = 0; m < t.nprim; ++m) {
-    switch (t.kind[m]) {
-      case MUSR_PRIM_AMP:
-        ct->amp_slot = t.slot[m][0];
-        ++namp;
-        break;
-      case MUSR_PRIM_EXP:
-        ct->exp_slot[ct->nexp++] = t.slot[m][0];
-        break;
-      case MUSR_PRIM_GAUSS:
-        ct->gauss_slot[ct->ngauss++] = t.slot[m][0];
-        break;
-      case MUSR_PRIM_KT:
-        ct->kt_slot = t.slot[m][0];
-        ++nkt;
-        break;
-      case MUSR_PRIM_TFCOS:
-        ct->nu_slot = t.slot[m][0];
-        ct->phi_slot = t.slot[m][1];
-        ++ntf;
-        break;
-    }
-  }
-  if (namp > 1 || nkt > 1 || ntf > 1 || (nkt && ntf)) {
-    *why = "SPLIT precision needs every term to hold at most one AMP, and at most one of KT or TFCOS";
-    return false;
-  }
-  ct->kind = ntf ? musr::kTermTF : (nkt ? musr::kTermKT : musr::kTermPlain);
-  return true;
-}
-
 // Builds the decomposition and finalize tables of one precision and one
 // decomposition (0: tiles small enough that one evaluation fills the GPU;
 // 1: the largest tiles, for batched launches).
@@ -270,53 +234,13 @@ int compile(musr_ctx* ctx, int prec, int var) {
   std::vector<std::vector<int>> groups;
   int group_cap = 1;
   if (prec == MUSR_SPLIT) {
-    for (int k = 0; k < hs.nterms; ++k) {
-      std::string why;
-      if (!canonical(ctx->terms[k], &hs.canon[k], &why)) {
-        c.reason = why;
-        return MUSR_OK;  // SPLIT unavailable for this theory; FP64 still is
-      }
+    const char* why = musr::plan_split(ctx->terms.data(), hs.nterms, ctx->map.data(), H, ctx->nslots,
+                                       ctx->consts.data(), &hs);
+    if (why) {
+      c.reason = why;
+      return MUSR_OK;  // SPLIT unavailable for this theory; FP64 still is
     }
-    // Shape of the term list.
-    std::vector<int> kinds;
-    for (int k = 0; k < hs.nterms; ++k) kinds.push_back(hs.canon[k].kind);
-    using musr::kTermKT;
-    using musr::kTermTF;
-    if (kinds == std::vector<int>{kTermTF})
-      hs.shape = musr::kShapeTF1;
-    else if (kinds == std::vector<int>{kTermTF, kTermTF})
-      hs.shape = musr::kShapeTF2;
-    else if (kinds == std::vector<int>{kTermKT})
-      hs.shape = musr::kShapeKT1;
-    else if (kinds == std::vector<int>{kTermTF, kTermTF, kTermKT})
-      hs.shape = musr::kShapeTF2KT1;
-    else
-      hs.shape = musr::kShapeGeneric;
-    hs.shape = musr::constant_amplitude_shape(hs.shape, hs.canon, hs.nterms, ctx->map.data(),
-                                              ctx->consts.data(), ctx->H, ctx->nslots);
-    const bool one_phase = hs.shape == musr::kShapeTF2c || hs.shape == musr::kShapeTF2KT1c;
     group_cap = musr::shape_group(hs.shape);
-    // Slot -> channel contributions.
-    auto add = [&](int slot, int kind, int term) {
-      hs.contrib[hs.ncontrib].slot = slot;
-      hs.contrib[hs.ncontrib].kind = kind;
-      hs.contrib[hs.ncontrib].term = term;
-      ++hs.ncontrib;
-    };
-    add(0, musr::kCN0, 0);
-    add(1, musr::kCBkg, 0);
-    for (int k = 0; k < hs.nterms; ++k) {
-      const CanonTerm& ct = hs.canon[k];
-      if (ct.amp_slot >= 0) add(ct.amp_slot, musr::kCAmp, k);
-      for (int i = 0; i < ct.nexp; ++i) add(ct.exp_slot[i], musr::kCLam, k);
-      for (int i = 0; i < ct.ngauss; ++i) add(ct.gauss_slot[i], musr::kCSig, k);
-      if (ct.kind == musr::kTermKT) add(ct.kt_slot, musr::kCDel, k);
-      if (ct.kind == musr::kTermTF) {
-        add(ct.nu_slot, musr::kCNu, k);
-        // with one shared phase channel, its slot receives the channel once
-        if (!one_phase || k == 0) add(ct.phi_slot, musr::kCPhi, k);
-      }
-    }
     // Group histograms that share t0 and every time-dependent parameter.
     std::map<std::vector<int64_t>, int> key_to_group;
     // A slot's identity across histograms: the global parameter, or the constant's value.

@@ -35,17 +35,27 @@ enum StoreType : int { kStoreF32 = 1, kStoreF64 = 2 };
 enum PrimKind : int { kAmp = 1, kExp = 2, kGauss = 3, kKT = 4, kTFCos = 5 };
 enum TermKind : int { kTermNone = 0, kTermPlain = 1, kTermTF = 2, kTermKT = 3 };
 
-// SPLIT shape identifiers (which compile-time specialisation runs a HistSet).
-// The "c" shapes are the same term lists with every amplitude a constant (no
-// amplitude gradient channels).
+// SPLIT shapes.  Every model the SPLIT path accepts is, for each histogram j of a
+// chunk, a linear combination of M time-only basis functions B_m(t) with
+// per-histogram coefficients (Eq. positron_histo with A(t) expanded):
+//   N_j(t) = Nbkg_j + sum_m Gam_jm B_m(t),   B_0 = E = exp(-t / tau_mu),
+//   a cosine term k (relaxation R_k):  E R_k cos(2 pi nu_k t), E R_k sin(2 pi nu_k t)
+//                                      with Gam = N0 a_k cos(phi_k), -N0 a_k sin(phi_k);
+//   any other term k:                  E R_k with Gam = N0 a_k.
+// A shape fixes the number of cosine terms (they come first) and other terms at
+// compile time.  The merged ("m") shapes serve term lists whose amplitudes are
+// constants shared by all histograms and whose cosines share one phase per
+// histogram: the amplitudes move into the basis and the terms collapse into
+// M = 3 functions (E + the other terms, the cosine parts, the sine parts).
 enum Shape : int {
-  kShapeGeneric = 0,
-  kShapeTF1 = 1,
-  kShapeTF2 = 2,
-  kShapeKT1 = 3,
-  kShapeTF2KT1 = 4,
-  kShapeTF2c = 5,
-  kShapeTF2KT1c = 6
+  kShapeGeneric = 0,  // up to 4 terms of any kind, two basis functions per term (M = 9)
+  kShapeT1 = 1,       // one cosine term (M = 3)
+  kShapeN1 = 2,       // one term without cosine (M = 2)
+  kShapeT1N1 = 3,     // cosine + other (M = 4)
+  kShapeT2 = 4,       // two cosine terms (M = 5)
+  kShapeT2N1 = 5,     // two cosine terms + other (M = 6)
+  kShapeT2m = 6,      // merged two cosine terms (M = 3)
+  kShapeT2N1m = 7     // merged two cosine terms + other (M = 3)
 };
 
 // A term as given: the product of nprim primitives (FP64 path).
@@ -70,57 +80,18 @@ struct CanonTerm {
   int phi_slot;  // kTermTF
 };
 
-// True when no amplitude slot of the canonical terms maps to a parameter.
-inline bool amplitudes_constant(const CanonTerm* canon, int nterms, const int32_t* map, int H, int nslots) {
-  for (int k = 0; k < nterms; ++k) {
-    if (canon[k].amp_slot < 0) continue;
-    for (int h = 0; h < H; ++h)
-      if (map[static_cast<int64_t>(h) * nslots + canon[k].amp_slot] >= 0) return false;
-  }
-  return true;
-}
-
-// True when, for every histogram, all cosine terms take their phase from one
-// parameter (or one constant value).
-inline bool phases_shared(const CanonTerm* canon, int nterms, const int32_t* map, const double* consts, int H,
-                          int nslots) {
-  for (int h = 0; h < H; ++h) {
-    int first = -1;
-    for (int k = 0; k < nterms; ++k) {
-      if (canon[k].kind != kTermTF) continue;
-      const int32_t m = map[static_cast<int64_t>(h) * nslots + canon[k].phi_slot];
-      if (first < 0) {
-        first = k;
-        continue;
-      }
-      const int32_t m0 = map[static_cast<int64_t>(h) * nslots + canon[first].phi_slot];
-      const bool same = (m >= 0 || m0 >= 0) ? m == m0 : consts[-1 - m] == consts[-1 - m0];
-      if (!same) return false;
-    }
-  }
-  return true;
-}
-
-// Shape of a canonical term list whose amplitudes are all constants and whose
-// cosines share one phase: the "c" variants of TF2 and TF2KT1.
-inline int constant_amplitude_shape(int shape, const CanonTerm* canon, int nterms, const int32_t* map,
-                                    const double* consts, int H, int nslots) {
-  if (shape != kShapeTF2 && shape != kShapeTF2KT1) return shape;
-  if (!amplitudes_constant(canon, nterms, map, H, nslots)) return shape;
-  if (!phases_shared(canon, nterms, map, consts, H, nslots)) return shape;
-  return shape == kShapeTF2 ? kShapeTF2c : kShapeTF2KT1c;
-}
-
 // How a SPLIT channel turns into the derivative of one local slot.
 enum ContribKind : int {
-  kCN0 = 0,    // d/dN0                 = 2 * ch_N0
-  kCBkg = 1,   // d/dNbkg               = 2 * ch_bkg
-  kCAmp = 2,   // d/da_k                = 2 * N0 * ch_amp[k]
-  kCPhi = 3,   // d/dphi_k              = 2 * N0 * a_k * (-2 pi / 360) * ch_phi[k]
-  kCLam = 4,   // d/dlambda (EXP of k)  = 2 * ch_lam[k]           (shared)
-  kCSig = 5,   // d/dsigma  (GAUSS of k)= 4 * sigma * ch_S[k]     (shared)
-  kCNu = 6,    // d/dnu_k               = 2 * ch_nu[k]            (shared)
-  kCDel = 7    // d/dDelta_k            = (4/3) * Delta * ch_D[k] (shared)
+  // per histogram, from G_m = sum_n u B_m and W = sum_n u (u = d(cost/2)/dN):
+  kCN0 = 0,    // d/dN0     = 2 sum_m (Gam_m / N0) G_m
+  kCBkg = 1,   // d/dNbkg   = 2 W
+  kCAmp = 2,   // d/da_k    = 2 sum over the term's basis functions of (dGam/da_k) G
+  kCPhi = 3,   // d/dphi_k  = 2 sum over the term's basis functions of (dGam/dphi_k) G
+  // shared by the chunk (time-only), from the per-term channels:
+  kCLam = 4,   // d/dlambda = 2 ch_Lambda[k]
+  kCSig = 5,   // d/dsigma  = 4 sigma ch_S[k]
+  kCNu = 6,    // d/dnu     = 2 ch_nu[k]
+  kCDel = 7    // d/dDelta  = (4/3) Delta ch_Delta[k]
 };
 struct Contrib {
   int slot;
@@ -150,8 +121,10 @@ struct HistSet {
   // theory
   int nterms;
   RawTerm raw[kMaxTerms];
-  CanonTerm canon[kMaxTerms];
+  CanonTerm canon[kMaxTerms];  // SPLIT: cosine terms first
   int shape;
+  int merged;                  // SPLIT merged shape: amplitudes folded into the basis
+  float bamp[kMaxTerms];       // SPLIT basis amplitude of each term (its constant if merged, else 1)
   int ncontrib;
   Contrib contrib[kMaxContrib];
   // parameter map

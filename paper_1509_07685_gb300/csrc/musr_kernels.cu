@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "musr_dev.h"
 
@@ -45,6 +46,7 @@ constexpr float kTwoPiF = 6.28318530717958647692f;
 constexpr float kLn2F = 0.69314718055994530942f;
 constexpr float kLog2eF = 1.44269504088896340736f;
 constexpr int kMaxChan = 96;
+constexpr int kGamStride = 12;  // floats per histogram row of SPLIT coefficients (M <= 9, plus Nbkg)
 
 // ---------------------------------------------------------------------------------------------
 // PTX approximate transcendentals (documented PTX ISA instructions, FTZ).
@@ -160,14 +162,14 @@ struct ChunkCache {
   int row[kGroupMax];
   const void* rowp[kGroupMax];       // first count of each histogram's row
   double loc[kGroupMax][kMaxSlots];  // local slot values (FP64)
-  // SPLIT per-histogram FP32 constants
-  float n0[kGroupMax], bkg[kGroupMax];
-  float amp[kMaxTerms][kGroupMax], cph[kMaxTerms][kGroupMax], sph[kMaxTerms][kGroupMax];
+  // SPLIT: [Nbkg, Gam_0 .. Gam_{M-1}] of each histogram (16-byte rows: vector loads)
+  alignas(16) float gam[kGroupMax][kGamStride];
   // SPLIT per-term constants of the chunk
   int kinds[kMaxTerms];
   float ca[kMaxTerms], cb[kMaxTerms];  // E*X_k = ex2(-(ca t + cb t^2))  (ca includes 1/tau)
   float dh[kMaxTerms], d2[kMaxTerms];  // KT: g = ex2(-dh t^2), u = d2 t^2
   float shi[kMaxTerms], slo[kMaxTerms], sstep[kMaxTerms];
+  float bamp[kMaxTerms];               // amplitude carried by the basis (merged shapes), else 1
   double nu[kMaxTerms];
   float aE, dt;
 };
@@ -195,10 +197,60 @@ struct Smem {
 };
 
 // ---------------------------------------------------------------------------------------------
+// SPLIT shapes (basis form, see musr_dev.h): NT terms, the first NTF with a cosine (NTF < 0:
+// kinds known at run time only, every term owning two basis functions), M basis functions,
+// at most G histograms per chunk; MERGED: the amplitudes live in the basis, one phase per
+// histogram.  Per work item each histogram keeps NPH = M + 1 channels (G_m = sum u B_m, and
+// W = sum u) and each term 4 shared channels (Lambda, S, nu, Delta).
+// ---------------------------------------------------------------------------------------------
+template <int NT_, int NTF_, int M_, int G_, bool MERGED_>
+struct BasisBase {
+  static constexpr int NT = NT_, NTF = NTF_, M = M_, G = G_;
+  static constexpr bool MERGED = MERGED_;
+  static constexpr int NPH = M + 1;
+  static constexpr int NCH = G * NPH + 4 * NT;
+  // Basis function of term k's cosine part (or of the whole term), and of its sine part.
+  __host__ __device__ static constexpr int bc(int k) {
+    return MERGED ? (k < NTF ? 1 : 0) : (NTF < 0 ? 1 + 2 * k : (k < NTF ? 1 + 2 * k : 1 + 2 * NTF + (k - NTF)));
+  }
+  __host__ __device__ static constexpr int bs(int k) { return MERGED ? 2 : (2 + 2 * k < M ? 2 + 2 * k : M - 1); }
+  // Whether term k has a cosine (compile-time for the fixed shapes).
+  __device__ static bool tf(const int* kinds, int k) { return NTF < 0 ? kinds[k] == kTermTF : k < NTF; }
+  static_assert(NCH <= kMaxChan, "channel count");
+  static_assert(M + 1 <= kGamStride, "coefficient row");
+};
+template <int S>
+struct Basis;
+template <>
+struct Basis<kShapeGeneric> : BasisBase<4, -1, 9, 2, false> {};
+template <>
+struct Basis<kShapeT1> : BasisBase<1, 1, 3, 8, false> {};
+template <>
+struct Basis<kShapeN1> : BasisBase<1, 0, 2, 8, false> {};
+template <>
+struct Basis<kShapeT1N1> : BasisBase<2, 1, 4, 8, false> {};
+template <>
+struct Basis<kShapeT2> : BasisBase<2, 2, 5, 8, false> {};
+template <>
+struct Basis<kShapeT2N1> : BasisBase<3, 2, 6, 6, false> {};
+template <>
+struct Basis<kShapeT2m> : BasisBase<2, 2, 3, 8, true> {};
+template <>
+struct Basis<kShapeT2N1m> : BasisBase<3, 2, 3, 8, true> {};
+
+// cos and sin of a phase given in degrees, reduced to [-1/2, 1/2] turns in FP64.
+__device__ __forceinline__ void phase_cs(double phi_deg, double* c, double* s) {
+  const double x = phi_deg * (1.0 / 360.0);
+  sincospi(2.0 * (x - rint(x)), s, c);
+}
+
+// ---------------------------------------------------------------------------------------------
 // Chunk cache fill (only when a CTA moves to another chunk or job).
 // ---------------------------------------------------------------------------------------------
+template <int SHAPE>
 __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int chunk_index, int prec,
                            Smem& sm) {
+  using Bs = Basis<SHAPE>;
   ChunkCache& cc = sm.cc;
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -231,25 +283,37 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
   if (prec == 0) return;
   const double dt = hs.dt_us;
   if (tid < nh) {
+    // Coefficients of the histogram's basis expansion, computed in FP64 and rounded once.
     const int hl = tid;
-    cc.n0[hl] = static_cast<float>(cc.loc[hl][0]);
-    cc.bkg[hl] = static_cast<float>(cc.loc[hl][1]);
+    double g[kGamStride];
 #pragma unroll
-    for (int k = 0; k < kMaxTerms; ++k) {
-      float a = 0.0f, c = 1.0f, s = 0.0f;
-      if (k < hs.nterms) {
+    for (int i = 0; i < kGamStride; ++i) g[i] = 0.0;
+    const double N0 = cc.loc[hl][0];
+    g[0] = cc.loc[hl][1];
+    g[1] = N0;
+    if (Bs::MERGED) {  // one phase per histogram: that of the first cosine term
+      double c, sn;
+      phase_cs(cc.loc[hl][hs.canon[0].phi_slot], &c, &sn);
+      g[2] = N0 * c;
+      g[3] = -N0 * sn;
+    } else {
+#pragma unroll
+      for (int k = 0; k < Bs::NT; ++k) {
+        if (k >= hs.nterms) break;
         const CanonTerm& ct = hs.canon[k];
-        a = ct.amp_slot >= 0 ? static_cast<float>(cc.loc[hl][ct.amp_slot]) : 1.0f;
+        const double a = ct.amp_slot >= 0 ? cc.loc[hl][ct.amp_slot] : 1.0;
         if (ct.kind == kTermTF) {
-          const double x = cc.loc[hl][ct.phi_slot] * (1.0 / 360.0);  // phase in turns (FP64)
-          const float r = static_cast<float>(x - rint(x));
-          sincospif(2.0f * r, &s, &c);
+          double c, sn;
+          phase_cs(cc.loc[hl][ct.phi_slot], &c, &sn);
+          g[1 + Bs::bc(k)] = N0 * a * c;
+          g[1 + Bs::bs(k)] = -N0 * a * sn;
+        } else {
+          g[1 + Bs::bc(k)] = N0 * a;
         }
       }
-      cc.amp[k][hl] = a;
-      cc.cph[k][hl] = c;
-      cc.sph[k][hl] = s;
     }
+#pragma unroll
+    for (int i = 0; i < kGamStride; ++i) cc.gam[hl][i] = static_cast<float>(g[i]);
   } else if (tid >= 32 && tid < 32 + kMaxTerms) {
     const int k = tid - 32;
     cc.kinds[k] = k < hs.nterms ? hs.canon[k].kind : kTermNone;
@@ -261,6 +325,7 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
         const float sg = static_cast<float>(cc.loc[0][ct.gauss_slot[i]]);
         S = fmaf(sg, sg, S);
       }
+      cc.bamp[k] = hs.bamp[k];
       cc.ca[k] = kLog2eF * (static_cast<float>(1.0 / kTauMuUs) + lam);
       cc.cb[k] = kLog2eF * 0.5f * S;
       if (ct.kind == kTermKT) {
@@ -480,111 +545,42 @@ __device__ double fp64_slot(const HistSet& hs, const double* tot, int s) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// SPLIT path
+// SPLIT path (basis form).  Per bin, the time-only parts: E = exp(-t/tau) and, per term,
+// the piece P_k = a E X_k [KT] (a: the basis amplitude) with its cosine and sine parts for a
+// cosine term.  Per (histogram, bin): N = Nbkg + sum_m Gam_m B_m (M FMAs), the cost term and
+// u = d(cost/2)/dN, then the channels G_m += u B_m, W += u and the per-bin sums
+// V_m = sum_j u_j Gam_jm that carry the shared time parameters' derivatives.
 // ---------------------------------------------------------------------------------------------
-template <int S>
-struct ShapeT;
-// NT: terms; G: histograms per chunk; AMP: whether amplitude channels are kept
-// (the "c" shapes drop them: every amplitude is a constant); NTF: phase channels;
-// phi(k): the phase channel of cosine term k (the "c" shapes also require one
-// phase slot shared by all cosine terms, so a single channel holds their sum).
-template <>
-struct ShapeT<kShapeGeneric> {
-  static constexpr int NT = 4, G = 2, NTF = 4;
-  static constexpr bool AMP = true;
-  __device__ static int kind(const ChunkCache& cc, int k) { return cc.kinds[k]; }
-  __device__ static int nterms(const HistSet& hs) { return hs.nterms; }
-  __device__ static constexpr int phi(int k) { return k; }
-};
-template <>
-struct ShapeT<kShapeTF1> {
-  static constexpr int NT = 1, G = 8, NTF = 1;
-  static constexpr bool AMP = true;
-  __device__ static constexpr int kind(const ChunkCache&, int) { return kTermTF; }
-  __device__ static constexpr int nterms(const HistSet&) { return 1; }
-  __device__ static constexpr int phi(int k) { return k; }
-};
-template <>
-struct ShapeT<kShapeTF2> {
-  static constexpr int NT = 2, G = 8, NTF = 2;
-  static constexpr bool AMP = true;
-  __device__ static constexpr int kind(const ChunkCache&, int) { return kTermTF; }
-  __device__ static constexpr int nterms(const HistSet&) { return 2; }
-  __device__ static constexpr int phi(int k) { return k; }
-};
-template <>
-struct ShapeT<kShapeTF2c> {
-  static constexpr int NT = 2, G = 8, NTF = 1;
-  static constexpr bool AMP = false;
-  __device__ static constexpr int kind(const ChunkCache&, int) { return kTermTF; }
-  __device__ static constexpr int nterms(const HistSet&) { return 2; }
-  __device__ static constexpr int phi(int) { return 0; }  // one phase slot for both cosines
-};
-template <>
-struct ShapeT<kShapeKT1> {
-  static constexpr int NT = 1, G = 8, NTF = 0;
-  static constexpr bool AMP = true;
-  __device__ static constexpr int kind(const ChunkCache&, int) { return kTermKT; }
-  __device__ static constexpr int nterms(const HistSet&) { return 1; }
-  __device__ static constexpr int phi(int) { return 0; }
-};
-template <>
-struct ShapeT<kShapeTF2KT1> {
-  static constexpr int NT = 3, G = 4, NTF = 2;
-  static constexpr bool AMP = true;
-  __device__ static constexpr int kind(const ChunkCache&, int k) { return k < 2 ? kTermTF : kTermKT; }
-  __device__ static constexpr int nterms(const HistSet&) { return 3; }
-  __device__ static constexpr int phi(int k) { return k; }
-};
-template <>
-struct ShapeT<kShapeTF2KT1c> {
-  static constexpr int NT = 3, G = 8, NTF = 1;
-  static constexpr bool AMP = false;
-  __device__ static constexpr int kind(const ChunkCache&, int k) { return k < 2 ? kTermTF : kTermKT; }
-  __device__ static constexpr int nterms(const HistSet&) { return 3; }
-  __device__ static constexpr int phi(int) { return 0; }  // one phase slot for both cosines
-};
-template <int S>
-struct ShapeChan {
-  // per histogram: N0, bkg, [amp of each term], phase of each cosine term
-  static constexpr int AMP0 = 2;
-  static constexpr int PHI0 = 2 + (ShapeT<S>::AMP ? ShapeT<S>::NT : 0);
-  static constexpr int NPH = PHI0 + ShapeT<S>::NTF;
-  static constexpr int NSH = 4 * ShapeT<S>::NT;  // shared per term: Lambda, S, nu, Delta
-  static constexpr int N = ShapeT<S>::G * NPH + NSH;
-  static_assert(N <= kMaxChan, "channel count");
-};
-
 template <int SHAPE, int MODE, bool GRAD>
 __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm, uint32_t& parity) {
-  using Sh = ShapeT<SHAPE>;
-  constexpr int NT = Sh::NT;
-  constexpr int G = Sh::G;
-  constexpr int NPH = ShapeChan<SHAPE>::NPH;
-  constexpr int PHI0 = ShapeChan<SHAPE>::PHI0;
-  constexpr int NCH = ShapeChan<SHAPE>::N;
-  constexpr int BPT = kBinsPerThread;  // consecutive bins per thread per iteration
+  using Bs = Basis<SHAPE>;
+  constexpr int NT = Bs::NT;
+  constexpr int M = Bs::M;
+  constexpr int G = Bs::G;
+  constexpr int NPH = Bs::NPH;
+  constexpr int NCH = Bs::NCH;
+  constexpr int NG4 = (M + 1 + 3) / 4;  // float4 loads per coefficient row
+  constexpr int BPT = kBinsPerThread;   // consecutive bins per thread per iteration
   static_assert(BPT == 2, "the loads below read float2 / double2");
 
   const ChunkCache& cc = sm.cc;
   const int tid = threadIdx.x;
   const int nh = cc.nh, nlo = cc.nlo, nhi = cc.nhi, ts = sm.ts.tile_start;
-  const int nterms = Sh::nterms(hs);
+  const int nterms = Bs::NTF < 0 ? hs.nterms : NT;
   const float aE = cc.aE, tbase = sm.ts.tbase, dtf = cc.dt;
   const int store = hs.store;
 
   float acc_v = 0.0f, acc_c = 0.0f;  // Kahan-compensated cost value
-  float ph[G][NPH];
-  float sh[NT][4];
+  float gacc[G][NPH];                // per histogram: G_m (m < M), W
+  float sh[NT][4];                   // per term: Lambda, S, nu, Delta
 #pragma unroll
   for (int i = 0; i < G; ++i)
 #pragma unroll
-    for (int q = 0; q < NPH; ++q) ph[i][q] = 0.0f;
+    for (int q = 0; q < NPH; ++q) gacc[i][q] = 0.0f;
 #pragma unroll
   for (int k = 0; k < NT; ++k)
 #pragma unroll
     for (int q = 0; q < 4; ++q) sh[k][q] = 0.0f;
-  int bad = 0;
 
   constexpr int CHUNK_BINS = kBlock * BPT;  // bins of one CTA iteration
   // Iterations of this tile that hold any bin of the fit range (the same for every thread).
@@ -621,178 +617,196 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     bool valid[BPT];
 #pragma unroll
     for (int j = 0; j < BPT; ++j) {
-      t[j] = fmaf(fm0 + static_cast<float>(j), dtf, tbase);
+      t[j] = fmaf(__fadd_rn(fm0, static_cast<float>(j)), dtf, tbase);
       valid[j] = (n0 + j >= nlo) && (n0 + j < nhi);
     }
-    // Time-only factors of the chunk: E = exp(-t/tau), EXK_k = E X_k K_k, and the
-    // precession (cos, sin) of each TF term without the per-histogram phase.
-    float E[BPT], EXK[NT][BPT], cs[NT][BPT], sn[NT][BPT], dk[NT][BPT];
+    // Time-only parts of the bin.  Every operation that reaches the cost value is an
+    // explicitly rounded intrinsic: no contraction into FMAs that could differ between the
+    // value-only and the value+gradient instantiations, so both return the same value.
+    float E[BPT], Pc[NT][BPT], Ps[NT][BPT], dK[NT][BPT];
 #pragma unroll
-    for (int j = 0; j < BPT; ++j) E[j] = ex2a(-aE * t[j]);
+    for (int j = 0; j < BPT; ++j) E[j] = ex2a(__fmul_rn(-aE, t[j]));
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
-      const int kk = Sh::kind(cc, k);
 #pragma unroll
-      for (int j = 0; j < BPT; ++j) EXK[k][j] = cs[k][j] = sn[k][j] = dk[k][j] = 0.0f;
+      for (int j = 0; j < BPT; ++j) Pc[k][j] = Ps[k][j] = dK[k][j] = 0.0f;
       if (k >= nterms) continue;
-      const float ca = cc.ca[k], cb = cc.cb[k];
+      const float ca = cc.ca[k], cb = cc.cb[k], ba = cc.bamp[k];
+      const bool istf = Bs::tf(cc.kinds, k);
+      const bool iskt = !istf && cc.kinds[k] == kTermKT;
 #pragma unroll
       for (int j = 0; j < BPT; ++j) {
-        const float ex = ex2a(-fmaf(cb, t[j], ca) * t[j]);
-        EXK[k][j] = ex;
-        cs[k][j] = 1.0f;
-        if (kk == kTermKT) {
-          const float tt = t[j] * t[j];
-          const float g = ex2a(-cc.dh[k] * tt);
-          const float u = cc.d2[k] * tt;
-          EXK[k][j] = ex * fmaf((2.0f / 3.0f) * (1.0f - u), g, 1.0f / 3.0f);
-          dk[k][j] = ex * tt * g * (u - 3.0f);
+        float X = __fmul_rn(ba, ex2a(__fmul_rn(-fmaf(cb, t[j], ca), t[j])));  // a E X_k
+        if (iskt) {
+          const float tt = __fmul_rn(t[j], t[j]);
+          const float g = ex2a(__fmul_rn(-cc.dh[k], tt));
+          const float u = __fmul_rn(cc.d2[k], tt);
+          dK[k][j] = X * tt * g * (u - 3.0f);
+          X = __fmul_rn(X, fmaf(__fmul_rn(2.0f / 3.0f, __fsub_rn(1.0f, u)), g, 1.0f / 3.0f));
         }
+        Pc[k][j] = X;
       }
-      if (kk == kTermTF) {
+      if (istf) {
         // Phase (turns) of the thread's first bin: base + m0 * step, reduced exactly.
-        float f = fm0 * cc.shi[k];
+        float f = __fmul_rn(fm0, cc.shi[k]);
         f = __fsub_rn(f, rint_small(f));
-        float r = fmaf(fm0, cc.slo[k], sm.ts.base[k]) + f;
+        float r = __fadd_rn(fmaf(fm0, cc.slo[k], sm.ts.base[k]), f);
         r = __fsub_rn(r, rint_small(r));
 #pragma unroll
         for (int j = 0; j < BPT; ++j) {
           float rj = fmaf(static_cast<float>(j), cc.sstep[k], r);
           rj = __fsub_rn(rj, rint_small(rj));  // |rj| <= 1/2: sin/cos arguments in [-pi, pi]
-          const float a = rj * kTwoPiF;
-          cs[k][j] = cosa(a);
-          sn[k][j] = sina(a);
+          const float a = __fmul_rn(rj, kTwoPiF);
+          Ps[k][j] = __fmul_rn(Pc[k][j], sina(a));
+          Pc[k][j] = __fmul_rn(Pc[k][j], cosa(a));
         }
       }
     }
-    float U[NT][BPT], V[NT][BPT];
+    // Basis functions.
+    float B[M][BPT];
 #pragma unroll
-    for (int k = 0; k < NT; ++k)
+    for (int m = 0; m < M; ++m)
 #pragma unroll
-      for (int j = 0; j < BPT; ++j) U[k][j] = V[k][j] = 0.0f;
-    float vit = 0.0f;  // this iteration's cost terms (at most 2 G of them)
-
+      for (int j = 0; j < BPT; ++j) B[m][j] = m == 0 ? E[j] : 0.0f;
 #pragma unroll
-    for (int hl = 0; hl < G; ++hl) {
-      if (hl >= nh) break;
-      float d[BPT];
-      if (staged) {
-        const float2 q = *reinterpret_cast<const float2*>(&sm.stage[b][hl][tid * BPT]);
-        d[0] = q.x;
-        d[1] = q.y;
-      } else {
-        const double2 q = __ldg(reinterpret_cast<const double2*>(static_cast<const double*>(cc.rowp[hl]) + n0));
-        d[0] = static_cast<float>(q.x);
-        d[1] = static_cast<float>(q.y);
-      }
-      const float N0 = cc.n0[hl], Nb = cc.bkg[hl];
+    for (int k = 0; k < NT; ++k) {
+      if (k >= nterms) continue;
+      const bool istf = Bs::tf(cc.kinds, k);
 #pragma unroll
       for (int j = 0; j < BPT; ++j) {
-        float C[NT], Sn[NT], Q[NT];
-        float M = E[j];
-#pragma unroll
-        for (int k = 0; k < NT; ++k) {
-          C[k] = Sn[k] = Q[k] = 0.0f;
-          if (k >= nterms) continue;
-          if (Sh::kind(cc, k) == kTermTF) {
-            const float cp = cc.cph[k][hl], sp = cc.sph[k][hl];
-            C[k] = fmaf(cs[k][j], cp, -sn[k][j] * sp);  // cos(theta + phi)
-            Sn[k] = fmaf(sn[k][j], cp, cs[k][j] * sp);  // sin(theta + phi)
+        if (Bs::MERGED) {
+          if (istf) {
+            B[1][j] = __fadd_rn(B[1][j], Pc[k][j]);
+            B[2][j] = __fadd_rn(B[2][j], Ps[k][j]);
           } else {
-            C[k] = 1.0f;
+            B[0][j] = __fadd_rn(B[0][j], Pc[k][j]);
           }
-          Q[k] = EXK[k][j] * C[k];
-          M = fmaf(cc.amp[k][hl], Q[k], M);
-        }
-        const float N = fmaf(N0, M, Nb);
-        const float dd = d[j];
-        float v, w;  // per-bin cost (chi^2, or half the deviance) and d(cost/2)/dN
-        if (MODE == 0) {
-          const float iv = rcpa(fmaxf(dd, 1.0f));
-          const float r = N - dd;
-          w = r * iv;
-          v = r * w;
         } else {
-          const float r = N - dd;
-          if (dd > 0.0f) {
-            if (N <= 0.0f) {
-              bad |= valid[j] ? 1 : 0;
-              v = 0.0f;
-              w = 0.0f;
-            } else {
-              // Half deviance (N - d) - d ln(N/d) with z = (N - d)/(N + d): since
-              // ln(N/d) = 2 atanh(z), it equals z ((N - d) - 2 d z^2 (1/3 + z^2/5 + ...)),
-              // summed to z^10 for |z| < 0.1 (relative truncation < 1e-12); beyond that the
-              // logarithms are taken directly, where no cancellation is left.
-              const float z = r * rcpa(N + dd);
-              if (fabsf(z) < 0.1f) {
-                const float z2 = z * z;
-                float pz = fmaf(z2, 1.0f / 11.0f, 1.0f / 9.0f);
-                pz = fmaf(z2, pz, 1.0f / 7.0f);
-                pz = fmaf(z2, pz, 1.0f / 5.0f);
-                pz = fmaf(z2, pz, 1.0f / 3.0f);
-                v = z * fmaf(-2.0f * dd * z2, pz, r);
-              } else {
-                v = fmaf(-dd * kLn2F, lg2a(N) - lg2a(dd), r);
-              }
-              w = r * rcpa(N);
-            }
-          } else {
-            v = r;
-            w = 1.0f;
-          }
-        }
-        if (!valid[j]) {
-          v = 0.0f;
-          w = 0.0f;
-        }
-        vit += v;
-        if (GRAD) {
-          ph[hl][0] = fmaf(w, M, ph[hl][0]);
-          ph[hl][1] += w;
-          const float wN0 = w * N0;
-#pragma unroll
-          for (int k = 0; k < NT; ++k) {
-            if (k >= nterms) continue;
-            if (Sh::AMP) ph[hl][2 + k] = fmaf(w, Q[k], ph[hl][2 + k]);
-            const float P = wN0 * cc.amp[k][hl];
-            U[k][j] = fmaf(P, C[k], U[k][j]);
-            if (Sh::kind(cc, k) == kTermTF) {
-              const int pc = PHI0 + Sh::phi(k);
-              const float PS = P * Sn[k];
-              ph[hl][pc] = fmaf(PS, EXK[k][j], ph[hl][pc]);  // w N0 a sin(theta + phi) E X
-              V[k][j] += PS;
-            }
-          }
+          B[Bs::bc(k)][j] = Pc[k][j];
+          if (Bs::NTF < 0 || k < Bs::NTF) B[Bs::bs(k)][j] = Ps[k][j];
         }
       }
     }
+
+    float V[M][BPT];
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+#pragma unroll
+      for (int j = 0; j < BPT; ++j) V[m][j] = 0.0f;
+    float vit = 0.0f;  // this iteration's cost terms
+
+    // Per (histogram, bin).  Away from the ends of the fit range every bin of the warp is
+    // valid and the loop runs without masks.
+    const bool all_valid = __all_sync(0xffffffffu, valid[0] && valid[1]);
+    auto hist_loop = [&](auto masked_tag) {
+      constexpr bool MASKED = decltype(masked_tag)::value;
+#pragma unroll
+      for (int hl = 0; hl < G; ++hl) {
+        if (hl >= nh) break;
+        float d[BPT];
+        if (staged) {
+          const float2 q = *reinterpret_cast<const float2*>(&sm.stage[b][hl][tid * BPT]);
+          d[0] = q.x;
+          d[1] = q.y;
+        } else {
+          const double2 q =
+              __ldg(reinterpret_cast<const double2*>(static_cast<const double*>(cc.rowp[hl]) + n0));
+          d[0] = static_cast<float>(q.x);
+          d[1] = static_cast<float>(q.y);
+        }
+        float gm[4 * NG4];  // Nbkg, Gam_0 .. Gam_{M-1}
+#pragma unroll
+        for (int q = 0; q < NG4; ++q) {
+          const float4 x = *reinterpret_cast<const float4*>(&cc.gam[hl][4 * q]);
+          gm[4 * q] = x.x;
+          gm[4 * q + 1] = x.y;
+          gm[4 * q + 2] = x.z;
+          gm[4 * q + 3] = x.w;
+        }
+#pragma unroll
+        for (int j = 0; j < BPT; ++j) {
+          float N = gm[0];
+#pragma unroll
+          for (int m = 0; m < M; ++m) N = fmaf(gm[1 + m], B[m][j], N);
+          const float dd = d[j];
+          float v, u;  // cost term (chi^2, or half the deviance) and d(cost/2)/dN
+          if (MODE == 0) {
+            const float iv = rcpa(fmaxf(dd, 1.0f));
+            const float r = __fsub_rn(N, dd);
+            u = __fmul_rn(r, iv);
+            v = __fmul_rn(r, u);
+          } else {
+            // Half deviance (N - d) - d ln(N/d) = N phi(u), u = 1 - d/N, with
+            // phi(u) = u + (1 - u) ln(1 - u) = sum_{k>=2} u^k / (k (k - 1)): the series to u^8
+            // for |u| < 0.1 (relative truncation < 3e-9, no cancellation), else the logarithm
+            // directly.  d = 0: N.  d > 0 >= N: not finite (+inf or NaN), reported by the host.
+            const float rN = rcpa(N);
+            const float r = __fsub_rn(N, dd);
+            const float uu = __fmul_rn(r, rN);
+            float p = fmaf(uu, 1.0f / 56.0f, 1.0f / 42.0f);
+            p = fmaf(uu, p, 1.0f / 30.0f);
+            p = fmaf(uu, p, 1.0f / 20.0f);
+            p = fmaf(uu, p, 1.0f / 12.0f);
+            p = fmaf(uu, p, 1.0f / 6.0f);
+            p = fmaf(uu, p, 0.5f);
+            const float vs = __fmul_rn(r, __fmul_rn(uu, p));
+            const float vl = fmaf(__fmul_rn(dd, kLn2F), lg2a(__fmul_rn(dd, rN)), r);
+            const bool pos = dd > 0.0f;
+            v = pos ? (fabsf(uu) < 0.1f ? vs : vl) : r;
+            u = pos ? uu : 1.0f;
+          }
+          if (MASKED && !valid[j]) {
+            v = 0.0f;
+            u = 0.0f;
+          }
+          vit = __fadd_rn(vit, v);
+          if (GRAD) {
+#pragma unroll
+            for (int m = 0; m < M; ++m) gacc[hl][m] = fmaf(u, B[m][j], gacc[hl][m]);
+            gacc[hl][M] += u;
+#pragma unroll
+            for (int m = 0; m < M; ++m) V[m][j] = fmaf(u, gm[1 + m], V[m][j]);
+          }
+        }
+      }
+    };
+    if (all_valid)
+      hist_loop(std::false_type{});
+    else
+      hist_loop(std::true_type{});
     {  // Kahan-compensated running sum of the per-iteration partials
-      const float y = vit - acc_c;
-      const float tsum = acc_v + y;
-      acc_c = (tsum - acc_v) - y;
+      const float y = __fsub_rn(vit, acc_c);
+      const float tsum = __fadd_rn(acc_v, y);
+      acc_c = __fsub_rn(__fsub_rn(tsum, acc_v), y);
       acc_v = tsum;
     }
     if (GRAD) {
-      // Shared channels: time-only factor times the chunk's per-bin sums.
+      // Shared channels: derivatives of the time-only pieces against the chunk's per-bin sums.
 #pragma unroll
-      for (int k = 0; k < NT; ++k) {
-        if (k >= nterms) continue;
-        const int kk = Sh::kind(cc, k);
+      for (int j = 0; j < BPT; ++j) {
+        const float mt = -t[j], mh = -0.5f * t[j] * t[j], tp = kTwoPiF * t[j];
 #pragma unroll
-        for (int j = 0; j < BPT; ++j) {
-          const float ue = U[k][j] * EXK[k][j];
-          sh[k][0] = fmaf(-t[j], ue, sh[k][0]);               // d/dLambda
-          sh[k][1] = fmaf(-0.5f * t[j] * t[j], ue, sh[k][1]);  // d/dS
-          if (kk == kTermTF) sh[k][2] = fmaf(-kTwoPiF * t[j] * EXK[k][j], V[k][j], sh[k][2]);
-          if (kk == kTermKT) sh[k][3] = fmaf(U[k][j], dk[k][j], sh[k][3]);
+        for (int k = 0; k < NT; ++k) {
+          if (k >= nterms) continue;
+          const bool istf = Bs::tf(cc.kinds, k);
+          const float Vc = V[Bs::bc(k)][j];
+          float D;
+          if (Bs::NTF < 0 || k < Bs::NTF) {
+            const float Vs = V[Bs::bs(k)][j];
+            D = fmaf(Vc, Pc[k][j], Vs * Ps[k][j]);
+            if (istf) sh[k][2] = fmaf(tp, fmaf(Vs, Pc[k][j], -Vc * Ps[k][j]), sh[k][2]);
+          } else {
+            D = Vc * Pc[k][j];
+          }
+          if (!istf) sh[k][3] = fmaf(Vc, dK[k][j], sh[k][3]);  // zero unless Kubo-Toyabe
+          sh[k][0] = fmaf(mt, D, sh[k][0]);
+          sh[k][1] = fmaf(mh, D, sh[k][1]);
         }
       }
     }
   }
 
   // ---- thread (FP32) -> warp (FP32; the value as float-float) -> CTA (FP64 trees) -> row.
-  bad = __syncthreads_or(bad);
   stall = __syncthreads_or(stall);
   const int w = tid >> 5, lane = tid & 31;
   float vh = acc_v, vl = -acc_c;
@@ -806,7 +820,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     for (int hl = 0; hl < G; ++hl)
 #pragma unroll
       for (int q = 0; q < NPH; ++q) {
-        const float r = warp_sum_f(ph[hl][q]);
+        const float r = warp_sum_f(gacc[hl][q]);
         if (lane == 0) sm.cred[w][hl * NPH + q] = r;
       }
 #pragma unroll
@@ -832,51 +846,83 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     double a = l < kWarps ? static_cast<double>(sm.vred[l][0]) + static_cast<double>(sm.vred[l][1]) : 0.0;
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    // +inf: undefined likelihood; NaN: a staging wait ran out (the host reports a timeout)
+    // NaN: a staging wait ran out (the host reports a timeout); +inf: the likelihood is
+    // undefined (N <= 0 where d > 0) or the parameters were not finite.
     if (l == 0)
       row[0] = stall ? __longlong_as_double(0x7ff8000000000000LL)
-                     : (bad ? __longlong_as_double(0x7ff0000000000000LL) : a * (MODE == 1 ? 2.0 : 1.0));
+                     : (isfinite(a) ? a * (MODE == 1 ? 2.0 : 1.0) : __longlong_as_double(0x7ff0000000000000LL));
   }
 }
 
 // SPLIT channels -> derivative of local slot s of chunk histogram hl.
 template <int SHAPE>
 __device__ double split_slot(const HistSet& hs, const ChunkCache& cc, const double* tot, int hl, int s) {
-  constexpr int NT = ShapeT<SHAPE>::NT;
-  constexpr int G = ShapeT<SHAPE>::G;
-  constexpr int NPH = ShapeChan<SHAPE>::NPH;
-  constexpr int PHI0 = ShapeChan<SHAPE>::PHI0;
-  const double* ch = tot + 1;
+  using Bs = Basis<SHAPE>;
+  const double* gch = tot + 1 + hl * Bs::NPH;  // G_m (m < M), W
+  const double* sch = tot + 1 + Bs::G * Bs::NPH;
   const double N0 = cc.loc[hl][0];
+  constexpr double kDeg = kTwoPi / 360.0;
   double g = 0.0;
   for (int e = 0; e < hs.ncontrib; ++e) {
     const Contrib c = hs.contrib[e];
     if (c.slot != s) continue;
     const int k = c.term;
+    const CanonTerm& ct = hs.canon[k];
     switch (c.kind) {
-      case kCN0:
-        g += 2.0 * ch[hl * NPH + 0];
+      case kCN0: {  // sum_m (dGam_m / dN0) G_m
+        double a = gch[0];
+        if (Bs::MERGED) {
+          double cp, sp;
+          phase_cs(cc.loc[hl][hs.canon[0].phi_slot], &cp, &sp);
+          a += cp * gch[1] - sp * gch[2];
+        } else {
+          for (int kk = 0; kk < hs.nterms && kk < Bs::NT; ++kk) {
+            const CanonTerm& q = hs.canon[kk];
+            const double amp = q.amp_slot >= 0 ? cc.loc[hl][q.amp_slot] : 1.0;
+            if (q.kind == kTermTF) {
+              double cp, sp;
+              phase_cs(cc.loc[hl][q.phi_slot], &cp, &sp);
+              a += amp * (cp * gch[Bs::bc(kk)] - sp * gch[Bs::bs(kk)]);
+            } else {
+              a += amp * gch[Bs::bc(kk)];
+            }
+          }
+        }
+        g += 2.0 * a;
         break;
+      }
       case kCBkg:
-        g += 2.0 * ch[hl * NPH + 1];
+        g += 2.0 * gch[Bs::M];
         break;
-      case kCAmp:
-        if (ShapeT<SHAPE>::AMP) g += 2.0 * N0 * ch[hl * NPH + 2 + k];
+      case kCAmp:  // unmerged shapes only
+        if (!Bs::MERGED) {
+          if (ct.kind == kTermTF) {
+            double cp, sp;
+            phase_cs(cc.loc[hl][ct.phi_slot], &cp, &sp);
+            g += 2.0 * N0 * (cp * gch[Bs::bc(k)] - sp * gch[Bs::bs(k)]);
+          } else {
+            g += 2.0 * N0 * gch[Bs::bc(k)];
+          }
+        }
         break;
-      case kCPhi:  // the channel already holds w N0 a sin(theta + phi) E X
-        g += 2.0 * (-kTwoPi / 360.0) * ch[hl * NPH + PHI0 + ShapeT<SHAPE>::phi(k)];
+      case kCPhi: {
+        double cp, sp;
+        phase_cs(cc.loc[hl][ct.phi_slot], &cp, &sp);
+        const double amp = !Bs::MERGED && ct.amp_slot >= 0 ? cc.loc[hl][ct.amp_slot] : 1.0;
+        g += 2.0 * N0 * amp * kDeg * (-sp * gch[Bs::bc(k)] - cp * gch[Bs::bs(k)]);
         break;
+      }
       case kCLam:
-        if (hl == 0) g += 2.0 * ch[G * NPH + k * 4 + 0];
+        if (hl == 0) g += 2.0 * sch[k * 4 + 0];
         break;
       case kCSig:
-        if (hl == 0) g += 4.0 * cc.loc[0][s] * ch[G * NPH + k * 4 + 1];
+        if (hl == 0) g += 4.0 * cc.loc[0][s] * sch[k * 4 + 1];
         break;
       case kCNu:
-        if (hl == 0) g += 2.0 * ch[G * NPH + k * 4 + 2];
+        if (hl == 0) g += 2.0 * sch[k * 4 + 2];
         break;
       case kCDel:
-        if (hl == 0) g += (4.0 / 3.0) * cc.loc[0][s] * ch[G * NPH + k * 4 + 3];
+        if (hl == 0) g += (4.0 / 3.0) * cc.loc[0][s] * sch[k * 4 + 3];
         break;
       default:
         break;
@@ -1008,7 +1054,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? 2 : 1) eval_kernel(const J
     const int item = gi - job.item_begin;
     if (sm.cc.job != ji || item < sm.cc.item0 || item >= sm.cc.item0 + sm.cc.ntiles) {
       __syncthreads();
-      load_chunk(job, hs, ji, hs.items[item].x, PREC, sm);
+      load_chunk<SHAPE>(job, hs, ji, hs.items[item].x, PREC, sm);
     }
     load_tile(hs, item - sm.cc.item0, PREC, sm);
     if (PREC == 0)
@@ -1062,41 +1108,36 @@ int occupancy_mode(int mode, int grad) {
 
 }  // namespace
 
+#define MUSR_SPLIT_SHAPES(X) \
+  X(kShapeT1)                    \
+  X(kShapeN1)                    \
+  X(kShapeT1N1)                  \
+  X(kShapeT2)                    \
+  X(kShapeT2N1)                  \
+  X(kShapeT2m)                   \
+  X(kShapeT2N1m)
+
 int shape_group(int shape) {
   switch (shape) {
-    case kShapeTF1:
-      return ShapeT<kShapeTF1>::G;
-    case kShapeTF2:
-      return ShapeT<kShapeTF2>::G;
-    case kShapeKT1:
-      return ShapeT<kShapeKT1>::G;
-    case kShapeTF2KT1:
-      return ShapeT<kShapeTF2KT1>::G;
-    case kShapeTF2c:
-      return ShapeT<kShapeTF2c>::G;
-    case kShapeTF2KT1c:
-      return ShapeT<kShapeTF2KT1c>::G;
+#define MUSR_CASE(S) \
+  case S:            \
+    return Basis<S>::G;
+    MUSR_SPLIT_SHAPES(MUSR_CASE)
+#undef MUSR_CASE
     default:
-      return ShapeT<kShapeGeneric>::G;
+      return Basis<kShapeGeneric>::G;
   }
 }
 
 int shape_channels(int shape) {
   switch (shape) {
-    case kShapeTF1:
-      return ShapeChan<kShapeTF1>::N;
-    case kShapeTF2:
-      return ShapeChan<kShapeTF2>::N;
-    case kShapeKT1:
-      return ShapeChan<kShapeKT1>::N;
-    case kShapeTF2KT1:
-      return ShapeChan<kShapeTF2KT1>::N;
-    case kShapeTF2c:
-      return ShapeChan<kShapeTF2c>::N;
-    case kShapeTF2KT1c:
-      return ShapeChan<kShapeTF2KT1c>::N;
+#define MUSR_CASE(S) \
+  case S:            \
+    return Basis<S>::NCH;
+    MUSR_SPLIT_SHAPES(MUSR_CASE)
+#undef MUSR_CASE
     default:
-      return ShapeChan<kShapeGeneric>::N;
+      return Basis<kShapeGeneric>::NCH;
   }
 }
 
@@ -1105,18 +1146,11 @@ int launch_eval(int precision, int shape, int mode, int grad, const Job* d_jobs,
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (precision == 0) return dispatch_mode<0, 0>(mode, grad, d_jobs, njobs, total_items, num_sms, s, info);
   switch (shape) {
-    case kShapeTF1:
-      return dispatch_mode<1, kShapeTF1>(mode, grad, d_jobs, njobs, total_items, num_sms, s, info);
-    case kShapeTF2:
-      return dispatch_mode<1, kShapeTF2>(mode, grad, d_jobs, njobs, total_items, num_sms, s, info);
-    case kShapeKT1:
-      return dispatch_mode<1, kShapeKT1>(mode, grad, d_jobs, njobs, total_items, num_sms, s, info);
-    case kShapeTF2KT1:
-      return dispatch_mode<1, kShapeTF2KT1>(mode, grad, d_jobs, njobs, total_items, num_sms, s, info);
-    case kShapeTF2c:
-      return dispatch_mode<1, kShapeTF2c>(mode, grad, d_jobs, njobs, total_items, num_sms, s, info);
-    case kShapeTF2KT1c:
-      return dispatch_mode<1, kShapeTF2KT1c>(mode, grad, d_jobs, njobs, total_items, num_sms, s, info);
+#define MUSR_CASE(S) \
+  case S:            \
+    return dispatch_mode<1, S>(mode, grad, d_jobs, njobs, total_items, num_sms, s, info);
+    MUSR_SPLIT_SHAPES(MUSR_CASE)
+#undef MUSR_CASE
     default:
       return dispatch_mode<1, kShapeGeneric>(mode, grad, d_jobs, njobs, total_items, num_sms, s, info);
   }
@@ -1125,18 +1159,11 @@ int launch_eval(int precision, int shape, int mode, int grad, const Job* d_jobs,
 int max_ctas_per_sm(int precision, int shape, int mode, int grad) {
   if (precision == 0) return occupancy_mode<0, 0>(mode, grad);
   switch (shape) {
-    case kShapeTF1:
-      return occupancy_mode<1, kShapeTF1>(mode, grad);
-    case kShapeTF2:
-      return occupancy_mode<1, kShapeTF2>(mode, grad);
-    case kShapeKT1:
-      return occupancy_mode<1, kShapeKT1>(mode, grad);
-    case kShapeTF2KT1:
-      return occupancy_mode<1, kShapeTF2KT1>(mode, grad);
-    case kShapeTF2c:
-      return occupancy_mode<1, kShapeTF2c>(mode, grad);
-    case kShapeTF2KT1c:
-      return occupancy_mode<1, kShapeTF2KT1c>(mode, grad);
+#define MUSR_CASE(S) \
+  case S:            \
+    return occupancy_mode<1, S>(mode, grad);
+    MUSR_SPLIT_SHAPES(MUSR_CASE)
+#undef MUSR_CASE
     default:
       return occupancy_mode<1, kShapeGeneric>(mode, grad);
   }

@@ -23,6 +23,7 @@
 #include "musr.h"
 #include "musr_dev.h"
 #include "musr_host.h"
+#include "musr_plan.h"
 
 namespace musr {
 namespace {
@@ -61,38 +62,6 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Rejections return MUSR_EINVAL; the message names the check for readers of this file.
 constexpr int na_fail(const char* /*why*/) { return MUSR_EINVAL; }
-
-bool na_canonical(const musr_term& t, CanonTerm* ct) {
-  std::memset(ct, 0, sizeof(*ct));
-  ct->amp_slot = ct->kt_slot = ct->nu_slot = ct->phi_slot = -1;
-  int namp = 0, nkt = 0, ntf = 0;
-  for (int m = 0; m < t.nprim; ++m) {
-    switch (t.kind[m]) {
-      case MUSR_PRIM_AMP:
-        ct->amp_slot = t.slot[m][0];
-        ++namp;
-        break;
-      case MUSR_PRIM_EXP:
-        ct->exp_slot[ct->nexp++] = t.slot[m][0];
-        break;
-      case MUSR_PRIM_GAUSS:
-        ct->gauss_slot[ct->ngauss++] = t.slot[m][0];
-        break;
-      case MUSR_PRIM_KT:
-        ct->kt_slot = t.slot[m][0];
-        ++nkt;
-        break;
-      case MUSR_PRIM_TFCOS:
-        ct->nu_slot = t.slot[m][0];
-        ct->phi_slot = t.slot[m][1];
-        ++ntf;
-        break;
-    }
-  }
-  if (namp > 1 || nkt > 1 || ntf > 1 || (nkt && ntf)) return false;
-  ct->kind = ntf ? kTermTF : (nkt ? kTermKT : kTermPlain);
-  return true;
-}
 
 int64_t tiles_total(const Chunk* ch, int n, int64_t T) {
   int64_t s = 0;
@@ -181,43 +150,9 @@ extern "C" int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int
   int ngroups = 0;
   int group_cap = 1;
   if (precision == MUSR_SPLIT) {
-    for (int k = 0; k < nterms; ++k)
-      if (!na_canonical(terms[k], &hs.canon[k]))
-        return na_fail("SPLIT precision needs every term to hold at most one AMP, and at most one of KT or TFCOS");
-    int kinds[MUSR_MAX_TERMS];
-    for (int k = 0; k < nterms; ++k) kinds[k] = hs.canon[k].kind;
-    if (nterms == 1 && kinds[0] == kTermTF)
-      hs.shape = kShapeTF1;
-    else if (nterms == 2 && kinds[0] == kTermTF && kinds[1] == kTermTF)
-      hs.shape = kShapeTF2;
-    else if (nterms == 1 && kinds[0] == kTermKT)
-      hs.shape = kShapeKT1;
-    else if (nterms == 3 && kinds[0] == kTermTF && kinds[1] == kTermTF && kinds[2] == kTermKT)
-      hs.shape = kShapeTF2KT1;
-    else
-      hs.shape = kShapeGeneric;
-    hs.shape = constant_amplitude_shape(hs.shape, hs.canon, nterms, map, consts, nhist, nslots);
-    const bool one_phase = hs.shape == kShapeTF2c || hs.shape == kShapeTF2KT1c;
+    if (plan_split(terms, nterms, map, nhist, nslots, consts, &hs))
+      return na_fail("SPLIT precision needs every term to hold at most one AMP, and at most one of KT or TFCOS");
     group_cap = shape_group(hs.shape);
-    auto add = [&](int slot, int kind, int term) {
-      hs.contrib[hs.ncontrib].slot = slot;
-      hs.contrib[hs.ncontrib].kind = kind;
-      hs.contrib[hs.ncontrib].term = term;
-      ++hs.ncontrib;
-    };
-    add(0, kCN0, 0);
-    add(1, kCBkg, 0);
-    for (int k = 0; k < nterms; ++k) {
-      const CanonTerm& ct = hs.canon[k];
-      if (ct.amp_slot >= 0) add(ct.amp_slot, kCAmp, k);
-      for (int i = 0; i < ct.nexp; ++i) add(ct.exp_slot[i], kCLam, k);
-      for (int i = 0; i < ct.ngauss; ++i) add(ct.gauss_slot[i], kCSig, k);
-      if (ct.kind == kTermKT) add(ct.kt_slot, kCDel, k);
-      if (ct.kind == kTermTF) {
-        add(ct.nu_slot, kCNu, k);
-        if (!one_phase || k == 0) add(ct.phi_slot, kCPhi, k);  // one shared phase channel
-      }
-    }
     // Group histograms sharing t0 and every time-dependent parameter (first appearance order).
     int64_t keys[kNaMaxHist][2 + 2 * MUSR_MAX_TERMS * 10];
     int keylen[kNaMaxHist];
