@@ -164,6 +164,7 @@ struct ChunkCache {
   double loc[kGroupMax][kMaxSlots];  // local slot values (FP64)
   // SPLIT: [Nbkg, Gam_0 .. Gam_{M-1}] of each histogram (16-byte rows: vector loads)
   alignas(16) float gam[kGroupMax][kGamStride];
+  double cph[kGroupMax][kMaxTerms], sph[kGroupMax][kMaxTerms];  // cos, sin of each cosine term's phase
   // SPLIT per-term constants of the chunk
   int kinds[kMaxTerms];
   float ca[kMaxTerms], cb[kMaxTerms];  // E*X_k = ex2(-(ca t + cb t^2))  (ca includes 1/tau)
@@ -291,11 +292,16 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
     const double N0 = cc.loc[hl][0];
     g[0] = cc.loc[hl][1];
     g[1] = N0;
+#pragma unroll
+    for (int k = 0; k < kMaxTerms; ++k) {
+      double c = 1.0, sn = 0.0;
+      if (k < hs.nterms && hs.canon[k].kind == kTermTF) phase_cs(cc.loc[hl][hs.canon[k].phi_slot], &c, &sn);
+      cc.cph[hl][k] = c;
+      cc.sph[hl][k] = sn;
+    }
     if (Bs::MERGED) {  // one phase per histogram: that of the first cosine term
-      double c, sn;
-      phase_cs(cc.loc[hl][hs.canon[0].phi_slot], &c, &sn);
-      g[2] = N0 * c;
-      g[3] = -N0 * sn;
+      g[2] = N0 * cc.cph[hl][0];
+      g[3] = -N0 * cc.sph[hl][0];
     } else {
 #pragma unroll
       for (int k = 0; k < Bs::NT; ++k) {
@@ -303,10 +309,8 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
         const CanonTerm& ct = hs.canon[k];
         const double a = ct.amp_slot >= 0 ? cc.loc[hl][ct.amp_slot] : 1.0;
         if (ct.kind == kTermTF) {
-          double c, sn;
-          phase_cs(cc.loc[hl][ct.phi_slot], &c, &sn);
-          g[1 + Bs::bc(k)] = N0 * a * c;
-          g[1 + Bs::bs(k)] = -N0 * a * sn;
+          g[1 + Bs::bc(k)] = N0 * a * cc.cph[hl][k];
+          g[1 + Bs::bs(k)] = -N0 * a * cc.sph[hl][k];
         } else {
           g[1 + Bs::bc(k)] = N0 * a;
         }
@@ -596,8 +600,12 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     for (int hl = 0; hl < nh; ++hl)
       tma_load_1d(&sm.stage[b][hl][0], static_cast<const float*>(cc.rowp[hl]) + nstart, bytes, &sm.bar[b]);
   };
-  int stall = 0;
-  if (staged && tid == 0 && iters > 0) issue(0, 0);
+  int stall = 0;          // a staging wait ran out (CTA-uniform from the next iteration on)
+  unsigned inflight = 0;  // buffers holding a copy this thread has not yet seen complete
+  if (staged && iters > 0) {
+    if (tid == 0) issue(0, 0);
+    inflight = 1u;
+  }
   // The bin offset in the tile is carried as an exact float (integers < 2^24): an
   // int-to-float conversion per bin would occupy this GPU's slow FP64/conversion pipe.
   float fm0 = static_cast<float>(tid * BPT);
@@ -607,11 +615,22 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     const int b = it & 1;
     if (staged) {
       if (it + 1 < iters) {
-        __syncthreads();  // every thread is done with buffer b ^ 1 (iteration it - 1)
-        if (tid == 0) issue(it + 1, b ^ 1);
+        // Every thread is done with buffer b ^ 1 (iteration it - 1).  No copy is issued
+        // once any wait of the CTA has run out.
+        stall = __syncthreads_or(stall);
+        if (!stall) {
+          if (tid == 0) issue(it + 1, b ^ 1);
+          inflight |= 2u >> b;
+        }
       }
-      if (!mbar_wait(&sm.bar[b], (parity >> b) & 1u)) stall = 1;
-      parity ^= 1u << b;
+      if (inflight & (1u << b)) {
+        if (mbar_wait(&sm.bar[b], (parity >> b) & 1u)) {
+          inflight &= ~(1u << b);
+          parity ^= 1u << b;
+        } else {
+          stall = 1;
+        }
+      }
     }
     float t[BPT];
     bool valid[BPT];
@@ -698,31 +717,42 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     // Per (histogram, bin).  Away from the ends of the fit range every bin of the warp is
     // valid and the loop runs without masks.
     const bool all_valid = __all_sync(0xffffffffu, valid[0] && valid[1]);
+    // The counts and the coefficient row of histogram hl (rows past nh are read but unused).
+    auto fetch = [&](int hl, float (&d)[BPT], float (&gm)[4 * NG4]) {
+      if (staged) {
+        const float2 q = *reinterpret_cast<const float2*>(&sm.stage[b][hl][tid * BPT]);
+        d[0] = q.x;
+        d[1] = q.y;
+      } else if (hl < nh) {
+        const double2 q =
+            __ldg(reinterpret_cast<const double2*>(static_cast<const double*>(cc.rowp[hl]) + n0));
+        d[0] = static_cast<float>(q.x);
+        d[1] = static_cast<float>(q.y);
+      }
+#pragma unroll
+      for (int q = 0; q < NG4; ++q) {
+        const float4 x = *reinterpret_cast<const float4*>(&cc.gam[hl][4 * q]);
+        gm[4 * q] = x.x;
+        gm[4 * q + 1] = x.y;
+        gm[4 * q + 2] = x.z;
+        gm[4 * q + 3] = x.w;
+      }
+    };
     auto hist_loop = [&](auto masked_tag) {
       constexpr bool MASKED = decltype(masked_tag)::value;
+      // One histogram ahead: the shared-memory loads of histogram hl + 1 are in flight while
+      // histogram hl is evaluated.
+      float dn[BPT], gn[4 * NG4];
+      fetch(0, dn, gn);
 #pragma unroll
       for (int hl = 0; hl < G; ++hl) {
         if (hl >= nh) break;
-        float d[BPT];
-        if (staged) {
-          const float2 q = *reinterpret_cast<const float2*>(&sm.stage[b][hl][tid * BPT]);
-          d[0] = q.x;
-          d[1] = q.y;
-        } else {
-          const double2 q =
-              __ldg(reinterpret_cast<const double2*>(static_cast<const double*>(cc.rowp[hl]) + n0));
-          d[0] = static_cast<float>(q.x);
-          d[1] = static_cast<float>(q.y);
-        }
-        float gm[4 * NG4];  // Nbkg, Gam_0 .. Gam_{M-1}
+        float d[BPT], gm[4 * NG4];  // counts; Nbkg, Gam_0 .. Gam_{M-1}
 #pragma unroll
-        for (int q = 0; q < NG4; ++q) {
-          const float4 x = *reinterpret_cast<const float4*>(&cc.gam[hl][4 * q]);
-          gm[4 * q] = x.x;
-          gm[4 * q + 1] = x.y;
-          gm[4 * q + 2] = x.z;
-          gm[4 * q + 3] = x.w;
-        }
+        for (int j = 0; j < BPT; ++j) d[j] = dn[j];
+#pragma unroll
+        for (int q = 0; q < 4 * NG4; ++q) gm[q] = gn[q];
+        if (hl + 1 < G) fetch(hl + 1, dn, gn);
 #pragma unroll
         for (int j = 0; j < BPT; ++j) {
           float N = gm[0];
@@ -737,13 +767,15 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
             v = __fmul_rn(r, u);
           } else {
             // Half deviance (N - d) - d ln(N/d) = N phi(u), u = 1 - d/N, with
-            // phi(u) = u + (1 - u) ln(1 - u) = sum_{k>=2} u^k / (k (k - 1)): the series to u^8
-            // for |u| < 0.1 (relative truncation < 3e-9, no cancellation), else the logarithm
+            // phi(u) = u + (1 - u) ln(1 - u) = sum_{k>=2} u^k / (k (k - 1)): the series to u^10
+            // for |u| < 0.2 (relative truncation < 1.3e-8, no cancellation), else the logarithm
             // directly.  d = 0: N.  d > 0 >= N: not finite (+inf or NaN), reported by the host.
             const float rN = rcpa(N);
             const float r = __fsub_rn(N, dd);
             const float uu = __fmul_rn(r, rN);
-            float p = fmaf(uu, 1.0f / 56.0f, 1.0f / 42.0f);
+            float p = fmaf(uu, 1.0f / 90.0f, 1.0f / 72.0f);
+            p = fmaf(uu, p, 1.0f / 56.0f);
+            p = fmaf(uu, p, 1.0f / 42.0f);
             p = fmaf(uu, p, 1.0f / 30.0f);
             p = fmaf(uu, p, 1.0f / 20.0f);
             p = fmaf(uu, p, 1.0f / 12.0f);
@@ -752,7 +784,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
             const float vs = __fmul_rn(r, __fmul_rn(uu, p));
             const float vl = fmaf(__fmul_rn(dd, kLn2F), lg2a(__fmul_rn(dd, rN)), r);
             const bool pos = dd > 0.0f;
-            v = pos ? (fabsf(uu) < 0.1f ? vs : vl) : r;
+            v = pos ? (fabsf(uu) < 0.2f ? vs : vl) : r;
             u = pos ? uu : 1.0f;
           }
           if (MASKED && !valid[j]) {
@@ -806,6 +838,11 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     }
   }
 
+  // After a wait that ran out, wait once more (bounded) for every copy still in flight, so
+  // that none lands in shared memory once the CTA has moved on.
+#pragma unroll
+  for (int bb = 0; bb < 2; ++bb)
+    if ((inflight & (1u << bb)) && mbar_wait(&sm.bar[bb], (parity >> bb) & 1u)) parity ^= 1u << bb;
   // ---- thread (FP32) -> warp (FP32; the value as float-float) -> CTA (FP64 trees) -> row.
   stall = __syncthreads_or(stall);
   const int w = tid >> 5, lane = tid & 31;
@@ -872,17 +909,13 @@ __device__ double split_slot(const HistSet& hs, const ChunkCache& cc, const doub
       case kCN0: {  // sum_m (dGam_m / dN0) G_m
         double a = gch[0];
         if (Bs::MERGED) {
-          double cp, sp;
-          phase_cs(cc.loc[hl][hs.canon[0].phi_slot], &cp, &sp);
-          a += cp * gch[1] - sp * gch[2];
+          a += cc.cph[hl][0] * gch[1] - cc.sph[hl][0] * gch[2];
         } else {
           for (int kk = 0; kk < hs.nterms && kk < Bs::NT; ++kk) {
             const CanonTerm& q = hs.canon[kk];
             const double amp = q.amp_slot >= 0 ? cc.loc[hl][q.amp_slot] : 1.0;
             if (q.kind == kTermTF) {
-              double cp, sp;
-              phase_cs(cc.loc[hl][q.phi_slot], &cp, &sp);
-              a += amp * (cp * gch[Bs::bc(kk)] - sp * gch[Bs::bs(kk)]);
+              a += amp * (cc.cph[hl][kk] * gch[Bs::bc(kk)] - cc.sph[hl][kk] * gch[Bs::bs(kk)]);
             } else {
               a += amp * gch[Bs::bc(kk)];
             }
@@ -897,19 +930,15 @@ __device__ double split_slot(const HistSet& hs, const ChunkCache& cc, const doub
       case kCAmp:  // unmerged shapes only
         if (!Bs::MERGED) {
           if (ct.kind == kTermTF) {
-            double cp, sp;
-            phase_cs(cc.loc[hl][ct.phi_slot], &cp, &sp);
-            g += 2.0 * N0 * (cp * gch[Bs::bc(k)] - sp * gch[Bs::bs(k)]);
+            g += 2.0 * N0 * (cc.cph[hl][k] * gch[Bs::bc(k)] - cc.sph[hl][k] * gch[Bs::bs(k)]);
           } else {
             g += 2.0 * N0 * gch[Bs::bc(k)];
           }
         }
         break;
       case kCPhi: {
-        double cp, sp;
-        phase_cs(cc.loc[hl][ct.phi_slot], &cp, &sp);
         const double amp = !Bs::MERGED && ct.amp_slot >= 0 ? cc.loc[hl][ct.amp_slot] : 1.0;
-        g += 2.0 * N0 * amp * kDeg * (-sp * gch[Bs::bc(k)] - cp * gch[Bs::bs(k)]);
+        g += 2.0 * N0 * amp * kDeg * (-cc.sph[hl][k] * gch[Bs::bc(k)] - cc.cph[hl][k] * gch[Bs::bs(k)]);
         break;
       }
       case kCLam:
@@ -941,11 +970,26 @@ __device__ void chunk_finalize(const Job& job, const HistSet& hs, Smem& sm) {
   const int ps = hs.pstride;
   const int nout = GRAD ? 1 + hs.nch : 1;
   const double* part = job.partials + static_cast<int64_t>(cc.item0) * ps;
-  for (int c = tid; c < nout; c += kBlock) {
-    double s = 0.0;
-    for (int t = 0; t < cc.ntiles; ++t) s += __ldcg(part + static_cast<int64_t>(t) * ps + c);
-    sm.tot[c] = s;
+  // The chunk's item rows, summed per column in item order.  Blocks of rows are first
+  // copied to shared memory by the whole CTA (every load of a block in flight at once; the
+  // staging buffers are idle here), then each column is summed from there.
+  double* buf = reinterpret_cast<double*>(&sm.stage[0][0][0]);
+  constexpr int kBufDoubles = static_cast<int>(sizeof(sm.stage) / sizeof(double));
+  const int rows_per_block = kBufDoubles / nout;
+  double acc = 0.0;
+  for (int t0 = 0; t0 < cc.ntiles; t0 += rows_per_block) {
+    const int nt = min(rows_per_block, cc.ntiles - t0);
+    __syncthreads();
+    for (int i = tid; i < nt * nout; i += kBlock) {
+      const int t = i / nout, c = i - t * nout;
+      buf[i] = __ldcg(part + static_cast<int64_t>(t0 + t) * ps + c);
+    }
+    __syncthreads();
+    if (tid < nout)
+      for (int t = 0; t < nt; ++t) acc += buf[t * nout + tid];
   }
+  static_assert(kMaxChan + 1 <= kBlock, "one thread per column");
+  if (tid < nout) sm.tot[tid] = acc;
   __syncthreads();
   if (GRAD) {
     const int nsl = hs.nslots;
@@ -979,7 +1023,15 @@ __device__ void job_finalize(const Job& job, const HistSet& hs, Smem& sm) {
   if (job.grad) {
     for (int p = tid; p < hs.P; p += kBlock) {
       double g = 0.0;
-      for (int j = hs.p_ptr[p]; j < hs.p_ptr[p + 1]; ++j) g += __ldcg(job.colsum + hs.p_cols[j]);
+      const int j1 = hs.p_ptr[p + 1];
+      for (int j = hs.p_ptr[p]; j < j1; j += 8) {  // eight loads in flight, summed in column order
+        double x[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = j + q < j1 ? __ldcg(job.colsum + hs.p_cols[j + q]) : 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (j + q < j1) g += x[q];
+      }
       job.out[1 + p] = finite ? g : 0.0;
     }
   }
@@ -989,11 +1041,15 @@ __device__ void job_finalize(const Job& job, const HistSet& hs, Smem& sm) {
   }
 }
 
+// Publishes the item's row; the CTA that completes a chunk's last item finalizes the
+// chunk, and the one that completes a job's last chunk finalizes the job.  Release: the
+// CTA barrier orders every thread's row writes before thread 0's fence and counter
+// increment; acquire: the finalizing CTA fences after reading the counter.
 template <int PREC, int SHAPE, bool GRAD>
 __device__ void complete_item(const Job& job, const HistSet& hs, Smem& sm) {
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     const unsigned prev = atomicAdd(job.chunk_count + sm.cc.chunk, 1u);
     sm.flag = prev == static_cast<unsigned>(sm.cc.ntiles - 1);
   }
@@ -1001,9 +1057,9 @@ __device__ void complete_item(const Job& job, const HistSet& hs, Smem& sm) {
   if (!sm.flag) return;
   __threadfence();
   chunk_finalize<PREC, SHAPE, GRAD>(job, hs, sm);
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     const unsigned prev = atomicAdd(job.counter, 1u);
     sm.flag = prev == static_cast<unsigned>(hs.nchunks - 1);
   }
