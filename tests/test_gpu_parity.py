@@ -297,3 +297,99 @@ def test_full_size_large_fit_fp64_matches_oracle(B):
         _check_fp64(v, g, ref)
         v, g, st = ctx.eval(x, 1, B.MUSR_SPLIT)
         _check_split(v, g, ref)
+
+
+# ------------------------------------------------------------------------------------------
+# Every SPLIT shape (musr_plan.h): term lists chosen so that each compiled shape runs, on
+# several histograms (a chunk that is not full) with a ragged bin count.
+# ------------------------------------------------------------------------------------------
+
+def _build(terms, slots, H, nbins=2500 + 7, bw=2.0, seed=0):
+    """A problem from slot descriptors: ("hist", v) a parameter per histogram, ("shared", v)
+    one parameter, ("const", v) one constant, ("const_h", [v_j]) a constant per histogram.
+    Counts are Poisson draws of the oracle's model at the truth."""
+    params, consts, rows = [], [], [[0] * len(slots) for _ in range(H)]
+    for s, (kind, v) in enumerate(slots):
+        if kind == "shared":
+            params.append(v)
+            for j in range(H):
+                rows[j][s] = len(params) - 1
+        elif kind == "hist":
+            for j in range(H):
+                params.append(v * (1.0 + 0.05 * j) if s != 1 else v)
+                rows[j][s] = len(params) - 1
+        elif kind == "const":
+            consts.append(v)
+            for j in range(H):
+                rows[j][s] = -len(consts)
+        else:  # const_h
+            for j in range(H):
+                consts.append(v[j])
+                rows[j][s] = -len(consts)
+    truth = np.array(params)
+    mp = np.array(rows, np.int32)
+    dummy = np.zeros((H, nbins), np.float32)
+    p0 = mi.Problem(dummy, np.zeros(H), bw, (bw / 2000.0, nbins * bw / 1000.0), terms, mp, np.array(consts),
+                    len(params), truth, [f"p{i}" for i in range(len(params))])
+    dt = bw / 1000.0
+    lam = np.array([[oracle.model(p0, truth, h, n * dt) for n in range(nbins)] for h in range(H)])
+    counts = np.random.default_rng(seed).poisson(np.maximum(lam, 0.0)).astype(np.float32)
+    return p0.with_counts(counts)
+
+
+def _shape_cases():
+    N0, BKG = ("hist", 120.0), ("hist", 1.5)
+    cases = {}
+    # one cosine term and one other term, amplitudes per histogram (T1N1)
+    cases["T1N1"] = ([[("AMP", (2,)), ("EXP", (3,)), ("TFCOS", (4, 5))], [("AMP", (6,)), ("KT", (7,))]],
+                     [N0, BKG, ("hist", 0.2), ("shared", 0.4), ("shared", 1.5), ("hist", 30.0),
+                      ("shared", 0.05), ("shared", 0.35)])
+    # two cosine terms with their own phases (T2, unmerged)
+    cases["T2"] = ([[("AMP", (2,)), ("EXP", (3,)), ("TFCOS", (4, 5))],
+                    [("AMP", (6,)), ("GAUSS", (7,)), ("TFCOS", (8, 9))]],
+                   [N0, BKG, ("const", 0.12), ("shared", 0.5), ("shared", 1.2), ("hist", 20.0),
+                    ("const", 0.1), ("shared", 0.3), ("shared", 1.7), ("hist", 75.0)])
+    # T2 plus an exponential with a fitted amplitude (T2N1, unmerged)
+    cases["T2N1"] = (cases["T2"][0] + [[("AMP", (10,)), ("EXP", (11,))]],
+                     cases["T2"][1] + [("shared", 0.06), ("shared", 0.8)])
+    # shared phase, constant shared amplitudes, plus a plain exponential: merged with a plain term
+    cases["T2N1m"] = ([[("AMP", (2,)), ("EXP", (3,)), ("TFCOS", (4, 5))],
+                       [("AMP", (6,)), ("GAUSS", (7,)), ("TFCOS", (8, 5))],
+                       [("AMP", (9,)), ("EXP", (10,))]],
+                      [N0, BKG, ("const", 0.12), ("shared", 0.5), ("shared", 1.2), ("hist", 20.0),
+                       ("const", 0.1), ("shared", 0.3), ("shared", 1.7), ("const", 0.05), ("shared", 0.9)])
+    # shared phase but amplitudes that differ between histograms: not merged (T2)
+    cases["T2_const_h"] = ([[("AMP", (2,)), ("EXP", (3,)), ("TFCOS", (4, 5))],
+                            [("AMP", (6,)), ("GAUSS", (7,)), ("TFCOS", (8, 5))]],
+                           [N0, BKG, ("const_h", [0.10, 0.12, 0.14, 0.16, 0.18]), ("shared", 0.5),
+                            ("shared", 1.2), ("hist", 20.0), ("const", 0.1), ("shared", 0.3),
+                            ("shared", 1.7)])
+    # two terms without cosine (generic)
+    cases["generic_N2"] = ([[("AMP", (2,)), ("EXP", (3,))], [("AMP", (4,)), ("GAUSS", (5,)), ("KT", (6,))]],
+                           [N0, BKG, ("hist", 0.15), ("shared", 0.4), ("shared", 0.1), ("shared", 0.6),
+                            ("shared", 0.3)])
+    # three cosine terms (generic)
+    cases["generic_T3"] = ([[("AMP", (2,)), ("EXP", (3,)), ("TFCOS", (4, 5))],
+                            [("AMP", (6,)), ("GAUSS", (7,)), ("TFCOS", (8, 5))],
+                            [("AMP", (9,)), ("TFCOS", (10, 11))]],
+                           [N0, BKG, ("shared", 0.1), ("shared", 0.5), ("shared", 1.2), ("hist", 20.0),
+                            ("shared", 0.08), ("shared", 0.3), ("shared", 1.7), ("shared", 0.05),
+                            ("shared", 0.45), ("hist", 60.0)])
+    return cases
+
+
+@pytest.mark.parametrize("name", sorted(_shape_cases()))
+def test_every_split_shape_matches_oracle(B, name):
+    terms, slots = _shape_cases()[name]
+    p = _build(terms, slots, H=5, seed=sum(map(ord, name)))
+    x = p.truth * np.random.default_rng(7).uniform(0.97, 1.03, p.nparams)
+    with B.Context(p) as ctx:
+        for mode in (0, 1):
+            ref = oracle.cost(p, x, mode)
+            assert ref[3] == 0
+            v, g, _ = ctx.eval(x, mode, B.MUSR_FP64)
+            _check_fp64(v, g, ref)
+            v, g, _ = ctx.eval(x, mode, B.MUSR_SPLIT)
+            _check_split(v, g, ref)
+            v2, _, _ = ctx.eval(x, mode, B.MUSR_SPLIT, grad=False)
+            assert v2 == v
