@@ -405,7 +405,7 @@ void invalidate_eval(musr_ctx* ctx) { ctx->ev.key_valid = false; }
 int pick_variant(musr_ctx* ctx, int prec, int nvec) {
   int items[musr::kVariants];
   for (int v = 0; v < musr::kVariants; ++v) items[v] = ctx->comp[prec][v].hs.nitems;
-  return musr::pick_decomposition(items, nvec, ctx->num_sms);
+  return musr::pick_decomposition(items, nvec, prec, ctx->num_sms);
 }
 
 // Buffers for nvec evaluations; rebuilds the job table when the launch's key

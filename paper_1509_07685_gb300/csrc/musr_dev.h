@@ -176,14 +176,34 @@ int max_ctas_per_sm(int precision, int shape, int mode, int grad);
 constexpr int kVariants = 6;
 inline int bins_per_iteration(int precision) { return precision == 1 ? kBlock * kBinsPerThread : kBlock; }
 
-// The decomposition of a launch of nvec evaluations: the largest tiles that
-// still give every resident CTA about four items (items[v] = items per
-// evaluation of decomposition v), else the smallest tiles.
-inline int pick_decomposition(const int* items, int64_t nvec, int num_sms) {
-  const int64_t target = 4LL * 2 * num_sms;
-  for (int v = kVariants - 1; v > 0; --v)
-    if (nvec * items[v] >= target) return v;
-  return 0;
+// The decomposition of a launch of nvec evaluations (items[v]: work items of one
+// evaluation with decomposition v).  Each CTA of the persistent grid takes
+// ceil(items / grid) consecutive items; an item costs its iterations (1 << v for tiles of
+// decomposition v) plus a fixed overhead worth item_cost iterations (row reduction,
+// completion, staging start-up).  The pick minimises the busiest CTA's time; ties go to
+// the smaller tiles.
+inline int pick_decomposition(const int* items, int64_t nvec, int grid, double item_cost) {
+  int best = 0;
+  double best_t = 0.0;
+  for (int v = 0; v < kVariants; ++v) {
+    const int64_t total = nvec * items[v];
+    const int64_t per = (total + grid - 1) / grid;
+    const double t = static_cast<double>(per) * (static_cast<double>(1 << v) + item_cost);
+    if (v == 0 || t < best_t) {
+      best = v;
+      best_t = t;
+    }
+  }
+  return best;
+}
+// Per-item overhead in CTA iterations (measured on GB300), and the persistent grid: the
+// SPLIT kernels run two CTAs per SM, the FP64 kernels one.
+constexpr double kSplitItemCost = 1.3;
+constexpr double kFp64ItemCost = 0.1;
+inline int persistent_grid(int precision, int num_sms) { return num_sms * (precision == 1 ? 2 : 1); }
+inline int pick_decomposition(const int* items, int64_t nvec, int precision, int num_sms) {
+  return pick_decomposition(items, nvec, persistent_grid(precision, num_sms),
+                            precision == 1 ? kSplitItemCost : kFp64ItemCost);
 }
 
 // Histograms per chunk, and reduction channels per work item, of a SPLIT shape.

@@ -222,7 +222,7 @@ extern "C" int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int
   int items_per_var[kVariants];
   for (int v = 0; v < kVariants; ++v)
     items_per_var[v] = static_cast<int>(tiles_total(T.chunks, nchunks, int64_t(bins_per_iteration(precision)) << v));
-  hs.tile_bins = bins_per_iteration(precision) << pick_decomposition(items_per_var, 1, num_sms);
+  hs.tile_bins = bins_per_iteration(precision) << pick_decomposition(items_per_var, 1, precision, num_sms);
   const int64_t nitems64 = tiles_total(T.chunks, nchunks, hs.tile_bins);
   if (nitems64 > kNaMaxItems) return na_fail("problem needs more than 8192 work items (too many bins for musr_eval_noalloc)");
   int nitems = 0, col = 0;
