@@ -12,9 +12,9 @@ over at once): params in, 64 x (1 + 28) doubles out.  The L2 is flushed
 Printed JSON line (rank 0): value = (histogram, bin) pairs x vectors per
 second of device time (Gbins/s), measured with CUDA events on the launching
 stream; e2e = the same through the C ABI with host buffers (params H2D and
-results D2H inside the timed region); roofline of the fused kernel against
-the FP32 pipe; the plain FP64 path on the same batch; BFGS fits/s; the oracle
-timed on the host.
+results D2H inside the timed region); roofline of the fused kernel against the
+SM instruction-issue rate; the plain FP64 path on the same batch; BFGS fits/s;
+the serving loop; the oracle timed on the host cores.
 
 ``--impl reference`` times the FP64 CPU oracle instead (the reference arm).
 Multi-GPU (torchrun): each rank evaluates its own independent fits (weak
@@ -37,12 +37,34 @@ sys.path.insert(0, ROOT)
 
 NVEC = 64
 LOAD_S = 1.5  # seconds of untimed back-to-back steps under the clock sampler before the timed ones
-FP32_LANES_PER_SM = 128
-# Algorithmic FP32-pipe operations (lane instructions, an FMA counts one) per
-# (histogram, bin) of the fused value+gradient evaluation of the two-term TF model
-# with time-only factors shared by 8 histograms: model 9, cost (chi^2 4 / -2lnL 13),
-# value sum 1, gradient 17, shared per-bin work 40/8 = 5.
-ALGO_FP32_OPS = {0: 36.0, 1: 45.0}
+# Roofline of the fused SPLIT kernel.  It is bound by instruction issue (one warp
+# instruction per SM sub-partition per clock: 152 SMs x 4 x 32 lanes x clock), not by HBM
+# (the batch re-reads one 2 MiB histogram set).  Algorithmic lane instructions per
+# (histogram, bin) of the basis form for the two-term TF model with a shared phase per
+# histogram (M = 3 basis functions, 8 histograms share the per-bin work), value+gradient:
+#   per (histogram, bin): 1 shared-memory load (two per two bins), 3 FMA for N,
+#     cost (-2lnL: reciprocal, residual, u, 10-term series, log branch 4, 5 compares and
+#     selects = 22; chi^2: max, reciprocal, residual, u, value = 5), 1 value add,
+#     7 gradient accumulations (G_m, W, V_m);
+#   per bin / 8: time 2, E 2, per cosine term 17 (exponent 4, phase 9, sin and cos 2,
+#     cosine and sine parts 2), basis sums 2, value compensation 2, shared channels 17.
+ALGO_INST = {0: 24.0, 1: 41.0}
+LANES_PER_SMSP, SMSP_PER_SM = 32, 4
+# DRAM bytes of one launch of the timed kernel from an ncu capture of this workload
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid for the kernel source it was taken on.
+TRAFFIC = {"kernel_sha256": "91e3b05a2e1f57fc61ce69be250df5f1c54166d36cef7c8a5ca42e68401dc66b", "bytes": 2228736}
+
+
+def _traffic():
+    """Per-launch DRAM bytes of the timed kernel (ncu), or None when the kernel source has
+    changed since the capture."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1509_07685_gb300", "csrc", "musr_kernels.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return TRAFFIC["bytes"] if TRAFFIC["kernel_sha256"] == sha else None
 
 
 def _env_int(name, default):
@@ -63,6 +85,9 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=10000,
                     help="fit requests of the serving measurement (0: skip)")
+    ap.add_argument("--precision-report", action="store_true",
+                    help="instead of timing: the SPLIT path's error against FP64 for every config "
+                         "(cost value, gradient, fitted parameters in units of sigma)")
     return ap.parse_args()
 
 
@@ -333,14 +358,20 @@ def run_ours(args, rank, world, local_rank):
     clocks = clk.summary() | {"window": f"{LOAD_S} s of back-to-back steps, then the timed steps"}
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     nsm = torch.cuda.get_device_properties(local_rank).multi_processor_count
-    peak_ops = nsm * FP32_LANES_PER_SM * sm_max * 1e6
-    ach_ops = ALGO_FP32_OPS[mode] * bins * NVEC / (mean_t if world == 1 else float(np.mean(times)))
-    roofline = {"bound": "alu", "achieved": ach_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                "frac": ach_ops / peak_ops, "traffic": None,
-                "kernel": "eval_kernel<SPLIT, TF2>", "pipe": "FP32 (FMA) lanes",
-                "peak_source": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz (max SM clock)",
-                "hbm_gbs_equiv": 4.0 * bins * NVEC / mean_t / 1e9,
-                "hbm_peak_gbs": peaks.get("hbm_gbs")}
+    peak_inst = nsm * SMSP_PER_SM * LANES_PER_SMSP * sm_max * 1e6
+    t_kernel = mean_t if world == 1 else float(np.mean(times))
+    ach_inst = ALGO_INST[mode] * bins * NVEC / t_kernel
+    algo_bytes = 4 * p.H * p.B + 8 * NVEC * (P + 1 + P)  # counts once, params in, value+grad out
+    roofline = {"bound": "alu", "achieved": ach_inst / 1e12, "peak": peak_inst / 1e12, "unit": "Tinst/s",
+                "frac": ach_inst / peak_inst, "traffic": _traffic(),
+                "kernel": f"eval_kernel<SPLIT, two TF terms merged (M = 3), {'MLE' if mode else 'chi2'}, grad>",
+                "measure": "lane instructions of the algorithm per (histogram, bin) x (histogram, bin) pairs "
+                           "per launch / CUDA-event time of the launch",
+                "instructions_per_hist_bin": ALGO_INST[mode],
+                "peak_source": f"instruction issue: {nsm} SMs x {SMSP_PER_SM} sub-partitions x "
+                               f"{LANES_PER_SMSP} lanes x {sm_max:.0f} MHz (max SM clock)",
+                "algorithmic_bytes": algo_bytes,
+                "hbm_frac": algo_bytes / t_kernel / 1e9 / float(peaks.get("hbm_gbs", 6800.0))}
 
     fits = None
     if not args.no_fits and rank == 0:
@@ -455,8 +486,55 @@ def _serving(B, n_requests, window=1024, seed=4):
     return out
 
 
+def precision_report(args):
+    """Error of the FP32/FP64-split path against FP64, per configuration and mode: the cost
+    value (relative), the gradient (|dg_i| / gradient scale_i, the scale from the oracle),
+    and BFGS fits from the same start point (|x_split - x_fp64| / sigma_i, sigma from the
+    FP64 Hessian at the FP64 optimum).  The plain FP64 GPU path is the reference for values
+    and fits (it matches the oracle to 1e-12; checked here on the value)."""
+    import torch
+    import musr_inputs as mi
+    import oracle
+    from paper_1509_07685_gb300 import binding as B
+    from paper_1509_07685_gb300 import fit as F
+    torch.cuda.set_device(0)
+    B.load()
+    cfgs = {"cfg1": mi.cfg1(), "cfg2": mi.cfg2(), "cfg3": mi.cfg3(), "cfg5": mi.cfg5(), "paper_tf16": mi.paper_tf16()}
+    out = {}
+    for name, p in cfgs.items():
+        with B.Context(p) as ctx:
+            for mode in (0, 1):
+                x = mi.start_point(p, 100)
+                ref = oracle.cost(p, x, mode)
+                v64, g64, _ = ctx.eval(x, mode, B.MUSR_FP64)
+                v32, g32, _ = ctx.eval(x, mode, B.MUSR_SPLIT)
+                r64 = F.fit_context(ctx, x, mode, B.MUSR_FP64)
+                r32 = F.fit_context(ctx, x, mode, B.MUSR_SPLIT)
+                with np.errstate(invalid="ignore"):
+                    sig = F.sigmas_context(ctx, r64["x"], mode)
+                ok = np.isfinite(sig)  # sigma needs a positive-definite FP64 Hessian at the optimum
+                dev = np.where(ok, np.abs(r32["x"] - r64["x"]) / np.where(ok, sig, 1.0), np.nan)
+                vf64, _, _ = ctx.eval(r64["x"], mode, B.MUSR_FP64)
+                vf32, _, _ = ctx.eval(r64["x"], mode, B.MUSR_SPLIT)
+                out[f"{name}/{'mle' if mode else 'chi2'}"] = {
+                    "fp64_value_rel_err_vs_oracle": abs(v64 - ref[0]) / abs(ref[0]),
+                    "split_value_rel_err": abs(v32 - v64) / abs(v64),
+                    "split_value_rel_err_at_optimum": abs(vf32 - vf64) / abs(vf64),
+                    "split_grad_err_over_scale": float(np.max(np.abs(g32 - g64) / ref[2])),
+                    "fit_max_dev_sigma": float(np.nanmax(dev)) if ok.any() else None,
+                    "params_without_sigma": int((~ok).sum()),
+                    "fit_dev_sigma_by_param": {n: float(d) for n, d in zip(p.names, dev)} if p.nparams <= 32 else None,
+                    "fit_status": [int(r64["status"]), int(r32["status"])],
+                    "params": p.nparams}
+                print(name, mode, json.dumps(out[f"{name}/{'mle' if mode else 'chi2'}"])[:300], flush=True)
+    print(json.dumps({"precision_report": out}), flush=True)
+
+
 def main():
     args = _args()
+    if args.precision_report:
+        precision_report(args)
+        return
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)
     local_rank = _env_int("LOCAL_RANK", 0)
