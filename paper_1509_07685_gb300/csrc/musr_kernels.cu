@@ -120,6 +120,14 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
   return false;
 }
 
+// Counter increment with acquire-release semantics at GPU scope (PTX atom.acq_rel).
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -239,10 +247,15 @@ struct Basis<kShapeT2m> : BasisBase<2, 2, 3, 8, true> {};
 template <>
 struct Basis<kShapeT2N1m> : BasisBase<3, 2, 3, 8, true> {};
 
-// cos and sin of a phase given in degrees, reduced to [-1/2, 1/2] turns in FP64.
+// cos and sin of a phase given in degrees: reduced to [-1/2, 1/2] turns in FP64, then
+// evaluated in FP32 (the SPLIT coefficients and their derivatives need no more; FP64
+// sincospi is slow on this GPU and sits on the latency path of every chunk).
 __device__ __forceinline__ void phase_cs(double phi_deg, double* c, double* s) {
   const double x = phi_deg * (1.0 / 360.0);
-  sincospi(2.0 * (x - rint(x)), s, c);
+  float sf, cf;
+  sincospif(2.0f * static_cast<float>(x - rint(x)), &sf, &cf);
+  *c = cf;
+  *s = sf;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -970,26 +983,29 @@ __device__ void chunk_finalize(const Job& job, const HistSet& hs, Smem& sm) {
   const int ps = hs.pstride;
   const int nout = GRAD ? 1 + hs.nch : 1;
   const double* part = job.partials + static_cast<int64_t>(cc.item0) * ps;
-  // The chunk's item rows, summed per column in item order.  Blocks of rows are first
-  // copied to shared memory by the whole CTA (every load of a block in flight at once; the
-  // staging buffers are idle here), then each column is summed from there.
-  double* buf = reinterpret_cast<double*>(&sm.stage[0][0][0]);
-  constexpr int kBufDoubles = static_cast<int>(sizeof(sm.stage) / sizeof(double));
-  const int rows_per_block = kBufDoubles / nout;
-  double acc = 0.0;
-  for (int t0 = 0; t0 < cc.ntiles; t0 += rows_per_block) {
-    const int nt = min(rows_per_block, cc.ntiles - t0);
-    __syncthreads();
-    for (int i = tid; i < nt * nout; i += kBlock) {
-      const int t = i / nout, c = i - t * nout;
-      buf[i] = __ldcg(part + static_cast<int64_t>(t0 + t) * ps + c);
-    }
-    __syncthreads();
-    if (tid < nout)
-      for (int t = 0; t < nt; ++t) acc += buf[t * nout + tid];
-  }
+  // The chunk's item rows, summed per column in a fixed order: each column's rows are cut
+  // into `tpc` contiguous segments, one thread sums a segment (its loads all in flight),
+  // then the segment sums are added in segment order.  The order depends only on the
+  // chunk's tile count, not on which CTA ran which item.
   static_assert(kMaxChan + 1 <= kBlock, "one thread per column");
-  if (tid < nout) sm.tot[tid] = acc;
+  // (the segmentation follows the value+gradient row width in both kernels, so that the
+  // value-only kernel sums the value column in the same order)
+  const int tpc = max(1, min(kBlock / (1 + hs.nch), cc.ntiles));  // threads (segments) per column
+  double* seg = reinterpret_cast<double*>(&sm.stage[0][0][0]);  // [nout][tpc], idle staging space
+  if (tid < nout * tpc) {
+    const int c = tid / tpc, k = tid - c * tpc;
+    const int t0 = static_cast<int>(static_cast<int64_t>(cc.ntiles) * k / tpc);
+    const int t1 = static_cast<int>(static_cast<int64_t>(cc.ntiles) * (k + 1) / tpc);
+    double a = 0.0;
+    for (int t = t0; t < t1; ++t) a += __ldcg(part + static_cast<int64_t>(t) * ps + c);
+    seg[c * tpc + k] = a;
+  }
+  __syncthreads();
+  if (tid < nout) {
+    double a = 0.0;
+    for (int k = 0; k < tpc; ++k) a += seg[tid * tpc + k];
+    sm.tot[tid] = a;
+  }
   __syncthreads();
   if (GRAD) {
     const int nsl = hs.nslots;
@@ -1043,29 +1059,28 @@ __device__ void job_finalize(const Job& job, const HistSet& hs, Smem& sm) {
 
 // Publishes the item's row; the CTA that completes a chunk's last item finalizes the
 // chunk, and the one that completes a job's last chunk finalizes the job.  Release: the
-// CTA barrier orders every thread's row writes before thread 0's fence and counter
-// increment; acquire: the finalizing CTA fences after reading the counter.
+// CTA barrier orders every thread's row writes before thread 0's acquire-release counter
+// increment (cumulative over what the barrier ordered before it); acquire: that same
+// atomic, and a fence by every thread of the finalizing CTA.
 template <int PREC, int SHAPE, bool GRAD>
 __device__ void complete_item(const Job& job, const HistSet& hs, Smem& sm) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned prev = atomicAdd(job.chunk_count + sm.cc.chunk, 1u);
+    const unsigned prev = atom_add_acq_rel(job.chunk_count + sm.cc.chunk, 1u);
     sm.flag = prev == static_cast<unsigned>(sm.cc.ntiles - 1);
   }
   __syncthreads();
   if (!sm.flag) return;
-  __threadfence();
+  fence_acq_rel();
   chunk_finalize<PREC, SHAPE, GRAD>(job, hs, sm);
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned prev = atomicAdd(job.counter, 1u);
+    const unsigned prev = atom_add_acq_rel(job.counter, 1u);
     sm.flag = prev == static_cast<unsigned>(hs.nchunks - 1);
   }
   __syncthreads();
   if (!sm.flag) return;
-  __threadfence();
+  fence_acq_rel();
   job_finalize(job, hs, sm);
   __syncthreads();
 }
