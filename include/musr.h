@@ -234,6 +234,9 @@ typedef struct musr_server_stats {
   double busy_s;    /* worker time inside steps */
   double clock_s;   /* serving clock now */
   uint64_t arena_bytes, arena_used;
+  double minimizer_s; /* worker time in the fits' minimiser steps (trial points, updates) */
+  double admit_s;     /* worker time admitting fits (contexts, uploads), overlapped with the device */
+  double wait_s;      /* worker time waiting for the device */
 } musr_server_stats;
 
 /* Starts a server on `device` with a device memory budget of hbm_budget_bytes

@@ -70,7 +70,8 @@ class musr_server_stats(ctypes.Structure):
                 ("steps", ctypes.c_int64), ("launches", ctypes.c_int64), ("evals", ctypes.c_int64),
                 ("active", ctypes.c_int64), ("queued", ctypes.c_int64), ("bin_evals", ctypes.c_double),
                 ("busy_s", ctypes.c_double), ("clock_s", ctypes.c_double), ("arena_bytes", ctypes.c_uint64),
-                ("arena_used", ctypes.c_uint64)]
+                ("arena_used", ctypes.c_uint64), ("minimizer_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("wait_s", ctypes.c_double)]
 
 
 _lock = threading.Lock()

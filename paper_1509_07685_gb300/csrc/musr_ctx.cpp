@@ -687,25 +687,31 @@ int musr_upload_histograms(musr_ctx* ctx, const void* counts, int dtype, int nhi
   const int64_t stride = (nbins + kRowAlign - 1) / kRowAlign * kRowAlign;
   const size_t esz = dtype == MUSR_DTYPE_FP64 ? 8 : 4;
   const size_t total = static_cast<size_t>(nhist) * stride * esz;
+  // Checks (and the INT32 -> FP32 conversion) as branch-free loops the compiler vectorises.
   std::vector<float> conv;
   const void* src = counts;
+  const size_t n = static_cast<size_t>(nhist) * nbins;
   if (dtype == MUSR_DTYPE_INT32) {
     const int32_t* ci = static_cast<const int32_t*>(counts);
-    conv.resize(static_cast<size_t>(nhist) * nbins);
-    for (size_t i = 0; i < conv.size(); ++i) {
-      if (ci[i] >= (1 << 24) || ci[i] <= -(1 << 24))
-        return fail(ctx, MUSR_EINVAL, "INT32 counts must satisfy |count| < 2^24 (exact in FP32)");
-      conv[i] = static_cast<float>(ci[i]);
+    conv.resize(n);
+    int bad = 0;
+    for (size_t i = 0; i < n; ++i) {
+      const int32_t v = ci[i];
+      bad |= static_cast<int>(v >= (1 << 24)) | static_cast<int>(v <= -(1 << 24));
+      conv[i] = static_cast<float>(v);
     }
+    if (bad) return fail(ctx, MUSR_EINVAL, "INT32 counts must satisfy |count| < 2^24 (exact in FP32)");
     src = conv.data();
   } else if (dtype == MUSR_DTYPE_FP32) {
     const float* cf = static_cast<const float*>(counts);
-    for (size_t i = 0; i < static_cast<size_t>(nhist) * nbins; ++i)
-      if (!std::isfinite(cf[i])) return fail(ctx, MUSR_EINVAL, "counts must be finite");
+    int bad = 0;
+    for (size_t i = 0; i < n; ++i) bad |= static_cast<int>(!(std::fabs(cf[i]) <= 3.4028234663852886e38f));
+    if (bad) return fail(ctx, MUSR_EINVAL, "counts must be finite");
   } else {
     const double* cd = static_cast<const double*>(counts);
-    for (size_t i = 0; i < static_cast<size_t>(nhist) * nbins; ++i)
-      if (!std::isfinite(cd[i])) return fail(ctx, MUSR_EINVAL, "counts must be finite");
+    int bad = 0;
+    for (size_t i = 0; i < n; ++i) bad |= static_cast<int>(!(std::fabs(cd[i]) <= 1.7976931348623157e308));
+    if (bad) return fail(ctx, MUSR_EINVAL, "counts must be finite");
   }
   if ((rc = dalloc(ctx, ctx->counts_own, total))) return rc;
   cudaError_t e = cudaMemset(ctx->counts_own.p, 0, total);

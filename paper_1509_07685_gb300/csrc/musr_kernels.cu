@@ -997,7 +997,14 @@ __device__ void chunk_finalize(const Job& job, const HistSet& hs, Smem& sm) {
     const int t0 = static_cast<int>(static_cast<int64_t>(cc.ntiles) * k / tpc);
     const int t1 = static_cast<int>(static_cast<int64_t>(cc.ntiles) * (k + 1) / tpc);
     double a = 0.0;
-    for (int t = t0; t < t1; ++t) a += __ldcg(part + static_cast<int64_t>(t) * ps + c);
+    for (int t = t0; t < t1; t += 8) {  // eight rows' loads in flight, added in row order
+      double x[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = t + q < t1 ? __ldcg(part + static_cast<int64_t>(t + q) * ps + c) : 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (t + q < t1) a += x[q];
+    }
     seg[c * tpc + k] = a;
   }
   __syncthreads();
@@ -1074,6 +1081,11 @@ __device__ void complete_item(const Job& job, const HistSet& hs, Smem& sm) {
   fence_acq_rel();
   chunk_finalize<PREC, SHAPE, GRAD>(job, hs, sm);
   __syncthreads();
+  if (hs.nchunks == 1) {  // the chunk was the job's only one: no second counter
+    job_finalize(job, hs, sm);
+    __syncthreads();
+    return;
+  }
   if (threadIdx.x == 0) {
     const unsigned prev = atom_add_acq_rel(job.counter, 1u);
     sm.flag = prev == static_cast<unsigned>(hs.nchunks - 1);

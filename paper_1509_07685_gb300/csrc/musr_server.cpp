@@ -18,9 +18,12 @@
 // use its own decomposition and its own fixed-order reductions.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <functional>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -45,6 +48,7 @@ constexpr double kFp64Edm = 1e-7;
 // Decomposition of every served fit (SPLIT tiles of 4096 bins): many fits fill the
 // GPU together, and a fixed choice keeps a fit's result independent of the mix.
 constexpr int kServeVariant = 3;
+constexpr int kAdmitBatch = 32;  // fits configured together by the helper threads
 
 struct Request {
   int64_t id = 0;
@@ -67,6 +71,78 @@ struct Active {
   bool first = true;
   int nvec = 0;
   size_t poff = 0, ooff = 0;
+  std::vector<double> pts, f, g;  // this step's trial points, values and gradients
+};
+
+// Helper threads that run fn(i) for i in [0, n) together with the calling thread (the
+// fits' minimiser steps are independent of one another).
+class TaskPool {
+ public:
+  // Helper threads make `device` their current CUDA device (admission uploads from them).
+  TaskPool(int nthreads, int device) {
+    for (int t = 0; t < nthreads; ++t)
+      th_.emplace_back([this, device] {
+        cudaSetDevice(device);
+        loop();
+      });
+  }
+  ~TaskPool() {
+    {
+      std::lock_guard<std::mutex> l(mu_);
+      stop_ = true;
+      ++gen_;
+    }
+    cv_.notify_all();
+    for (auto& t : th_) t.join();
+  }
+  void run(int n, const std::function<void(int)>& fn) {
+    if (n <= 0) return;
+    if (th_.empty() || n == 1) {
+      for (int i = 0; i < n; ++i) fn(i);
+      return;
+    }
+    {
+      std::lock_guard<std::mutex> l(mu_);
+      fn_ = &fn;
+      n_ = n;
+      next_.store(0);
+      pending_ = static_cast<int>(th_.size());
+      ++gen_;
+    }
+    cv_.notify_all();
+    work();
+    std::unique_lock<std::mutex> l(mu_);
+    done_.wait(l, [&] { return pending_ == 0; });
+    fn_ = nullptr;
+  }
+
+ private:
+  void work() {
+    for (int i; (i = next_.fetch_add(1)) < n_;) (*fn_)(i);
+  }
+  void loop() {
+    uint64_t seen = 0;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> l(mu_);
+        cv_.wait(l, [&] { return gen_ != seen; });
+        seen = gen_;
+        if (stop_) return;
+      }
+      work();
+      std::lock_guard<std::mutex> l(mu_);
+      if (--pending_ == 0) done_.notify_one();
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex mu_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int)>* fn_ = nullptr;
+  int n_ = 0;
+  std::atomic<int> next_{0};
+  int pending_ = 0;
+  uint64_t gen_ = 0;
+  bool stop_ = false;
 };
 
 struct Done {
@@ -88,6 +164,8 @@ struct musr_server {
   int max_active = 1;
   Arena arena;
   std::thread worker;
+  std::unique_ptr<TaskPool> pool;  // helpers of the worker (minimiser steps, admission)
+  bool admit_serial = false;       // the last parallel admission found the arena full
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   bool stop = false;
@@ -195,51 +273,94 @@ int configure(musr_server* s, const Request& r, musr_ctx** out) {
   return MUSR_OK;
 }
 
+// Moves a configured request into the active set.
+void activate(musr_server* s, std::unique_ptr<Request> r, musr_ctx* ctx) {
+  auto a = std::make_unique<Active>();
+  a->ctx = ctx;
+  a->shape = ctx->comp[r->prec][kServeVariant].hs.shape;
+  musr_bins_in_fit(ctx, &a->bins);
+  a->t_admit = s->now();
+  a->bfgs.start(r->x0.data(), r->P, r->gtol, r->maxit, 0.0, r->prec == MUSR_SPLIT ? kSplitEdm : kFp64Edm);
+  a->req = std::move(r);
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->stats.active += 1;
+  s->active.push_back(std::move(a));
+}
+
+// Device memory a request needs at most: its counts, and evaluation buffers for P + 1
+// simultaneous points (the minimiser's widest step) with a generous bound on work items.
+size_t estimate_bytes(const Request& r) {
+  const size_t stride = static_cast<size_t>((r.B + 63) / 64 * 64);
+  const size_t counts = static_cast<size_t>(r.H) * stride * (r.dtype == MUSR_DTYPE_FP64 ? 8 : 4);
+  const size_t items = (static_cast<size_t>(r.H) + 1) * (static_cast<size_t>(r.B) / 2048 + 2);
+  const size_t rows = items * static_cast<size_t>(r.P + 1) * 100 * sizeof(double);  // <= 100 doubles a row
+  return counts + rows + (size_t(4) << 20);
+}
+
+// Admits queued fits, first come first served, while there are free slots and the arena
+// (the HBM budget) has room.  When the arena clearly holds a whole batch, the batch is
+// configured by the helper threads in parallel (uploads and planning overlap); otherwise
+// one at a time, so that a fit that waits for memory keeps its place.
 void admit(musr_server* s) {
-  while (static_cast<int>(s->active.size()) < s->max_active) {
-    std::unique_ptr<Request> r;
+  for (;;) {
+    const int room = s->max_active - static_cast<int>(s->active.size());
+    if (room <= 0) return;
+    std::vector<std::unique_ptr<Request>> batch;
     {
       std::lock_guard<std::mutex> lock(s->mu);
       if (s->queue.empty()) return;
-      r = std::move(s->queue.front());
-      s->queue.pop_front();
-      s->stats.queued -= 1;
+      size_t need = 0;
+      const size_t free_bytes = s->arena.capacity() - s->arena.used();
+      const int cap = s->admit_serial ? 1 : std::min(room, kAdmitBatch);
+      while (!s->queue.empty() && static_cast<int>(batch.size()) < cap) {
+        const size_t e = estimate_bytes(*s->queue.front());
+        if (!batch.empty() && need + e > free_bytes / 2) break;
+        need += e;
+        batch.push_back(std::move(s->queue.front()));
+        s->queue.pop_front();
+        s->stats.queued -= 1;
+      }
     }
-    musr_ctx* ctx = nullptr;
-    const int rc = configure(s, *r, &ctx);
-    if (rc == MUSR_ENOMEM && !s->active.empty()) {
-      // the budget is taken by running fits: wait for one to finish (FIFO order kept)
-      std::lock_guard<std::mutex> lock(s->mu);
-      s->queue.push_front(std::move(r));
-      s->stats.queued += 1;
-      return;
+    s->admit_serial = false;
+    const int n = static_cast<int>(batch.size());
+    std::vector<musr_ctx*> ctxs(n, nullptr);
+    std::vector<int> rcs(n, MUSR_OK);
+    s->pool->run(n, [&](int i) { rcs[i] = configure(s, *batch[i], &ctxs[i]); });
+    for (int i = 0; i < n; ++i) {
+      if (rcs[i] == MUSR_ENOMEM && (!s->active.empty() || n > 1)) {
+        // The arena is full now: this fit and every later one of the batch go back to the
+        // head of the queue in order (their memory released); retry one at a time.
+        std::lock_guard<std::mutex> lock(s->mu);
+        for (int j = n - 1; j >= i; --j) {
+          if (ctxs[j]) musr_ctx_destroy(ctxs[j]);
+          s->queue.push_front(std::move(batch[j]));
+          s->stats.queued += 1;
+        }
+        s->admit_serial = true;
+        if (!s->active.empty()) return;  // wait for a running fit to release memory
+        break;
+      }
+      if (rcs[i]) {
+        reject(s, std::move(batch[i]), rcs[i]);
+        continue;
+      }
+      activate(s, std::move(batch[i]), ctxs[i]);
     }
-    if (rc) {
-      reject(s, std::move(r), rc);
-      continue;
-    }
-    auto a = std::make_unique<Active>();
-    a->ctx = ctx;
-    a->shape = ctx->comp[r->prec][kServeVariant].hs.shape;
-    musr_bins_in_fit(ctx, &a->bins);
-    a->t_admit = s->now();
-    a->bfgs.start(r->x0.data(), r->P, r->gtol, r->maxit, 0.0, r->prec == MUSR_SPLIT ? kSplitEdm : kFp64Edm);
-    a->req = std::move(r);
-    std::lock_guard<std::mutex> lock(s->mu);
-    s->stats.active += 1;
-    s->active.push_back(std::move(a));
   }
 }
 
 // One step: every active fit's points in one multi-fit launch per group.
 int step(musr_server* s) {
-  std::vector<double> pts;
   size_t np = 0, no = 0;
   int nv = 0;
-  std::vector<std::vector<double>> requests(s->active.size());
+  const double t_req = s->now();
+  s->pool->run(static_cast<int>(s->active.size()), [&](int i) {
+    Active* a = s->active[i].get();
+    a->nvec = a->bfgs.request(&a->pts);
+  });
+  double t_min = s->now() - t_req;
   for (size_t i = 0; i < s->active.size(); ++i) {
     Active* a = s->active[i].get();
-    a->nvec = a->bfgs.request(&requests[i]);
     a->poff = np;
     a->ooff = no;
     np += static_cast<size_t>(a->nvec) * a->req->P;
@@ -254,8 +375,9 @@ int step(musr_server* s) {
       !grow_dev(&s->d_jobs, &s->dj_cap, (nv + 1) * sizeof(Job)))
     return MUSR_ENOMEM;
   for (size_t i = 0; i < s->active.size(); ++i)
-    if (!requests[i].empty())
-      std::memcpy(s->h_params + s->active[i]->poff, requests[i].data(), requests[i].size() * sizeof(double));
+    if (s->active[i]->nvec > 0)
+      std::memcpy(s->h_params + s->active[i]->poff, s->active[i]->pts.data(),
+                  static_cast<size_t>(s->active[i]->nvec) * s->active[i]->req->P * sizeof(double));
   // Group by (precision, shape, cost): one launch each, jobs contiguous per group.
   std::map<int, std::vector<Active*>> groups;
   for (auto& a : s->active) groups[(a->req->prec * 16 + a->shape) * 2 + a->req->mode].push_back(a.get());
@@ -291,46 +413,62 @@ int step(musr_server* s) {
   }
   e = cudaMemcpyAsync(s->h_out, d_out, no * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e != cudaSuccess) return MUSR_ECUDA;
+  const double t_adm = s->now();
   admit(s);  // configure newly queued fits while the step runs
+  const double t_wait = s->now();
   e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return MUSR_ECUDA;
+  const double t_del = s->now();
   {
     std::lock_guard<std::mutex> lock(s->mu);
     s->stats.steps += 1;
     s->stats.launches += static_cast<int64_t>(launches.size());
     s->stats.evals += nv;
+    s->stats.admit_s += t_wait - t_adm;
+    s->stats.wait_s += t_del - t_wait;
   }
-  // Advance every fit that took part in this step.
-  std::vector<double> f, g;
+  // Advance every fit that took part in this step (in parallel: fits are independent),
+  // then retire the finished ones.
+  s->pool->run(static_cast<int>(s->active.size()), [&](int i) {
+    Active* a = s->active[i].get();
+    if (a->nvec == 0) return;  // admitted during this step
+    const int P = a->req->P;
+    a->f.resize(a->nvec);
+    a->g.resize(static_cast<size_t>(a->nvec) * P);
+    for (int v = 0; v < a->nvec; ++v) {
+      const double* o = s->h_out + a->ooff + static_cast<size_t>(v) * (1 + P);
+      a->f[v] = o[0];
+      std::memcpy(a->g.data() + static_cast<size_t>(v) * P, o + 1, sizeof(double) * P);
+    }
+    a->bfgs.deliver(a->f.data(), a->g.data());
+    if (a->first && std::isfinite(a->f[0]) && a->req->prec == MUSR_SPLIT)
+      a->bfgs.set_f_noise(kSplitNoiseRel * std::fabs(a->f[0]));
+    a->first = false;
+  });
   std::vector<std::unique_ptr<Active>> keep;
+  double bin_evals = 0.0;
   for (auto& a : s->active) {
     if (a->nvec == 0) {  // admitted during this step
       keep.push_back(std::move(a));
       continue;
     }
-    const int P = a->req->P;
-    f.resize(a->nvec);
-    g.resize(static_cast<size_t>(a->nvec) * P);
-    for (int v = 0; v < a->nvec; ++v) {
-      const double* o = s->h_out + a->ooff + static_cast<size_t>(v) * (1 + P);
-      f[v] = o[0];
-      std::memcpy(g.data() + static_cast<size_t>(v) * P, o + 1, sizeof(double) * P);
-    }
-    {
-      std::lock_guard<std::mutex> lock(s->mu);
-      s->stats.bin_evals += static_cast<double>(a->bins) * a->nvec;
-    }
-    a->bfgs.deliver(f.data(), g.data());
-    if (a->first && std::isfinite(f[0]) && a->req->prec == MUSR_SPLIT)
-      a->bfgs.set_f_noise(kSplitNoiseRel * std::fabs(f[0]));
-    a->first = false;
+    bin_evals += static_cast<double>(a->bins) * a->nvec;
     a->nvec = 0;
     if (a->bfgs.done())
       finish(s, a.get(), a->bfgs.status());
     else
       keep.push_back(std::move(a));
   }
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stats.bin_evals += bin_evals;
+  }
   s->active.swap(keep);
+  t_min += s->now() - t_del;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stats.minimizer_s += t_min;
+  }
   return MUSR_OK;
 }
 
@@ -436,6 +574,8 @@ int musr_server_create(musr_server** out, int device, size_t hbm_budget_bytes, i
     return MUSR_ENOMEM;
   }
   s->stats.arena_bytes = s->arena.capacity();
+  const unsigned hw = std::thread::hardware_concurrency();
+  s->pool = std::make_unique<TaskPool>(hw > 2 ? static_cast<int>(std::min(hw - 2, 15u)) : 0, device);
   s->worker = std::thread(worker_main, s.get());
   *out = s.release();
   return MUSR_OK;
