@@ -146,12 +146,44 @@ void dfree(musr_ctx* ctx, DevBuf& b) {
   b.from_arena = false;
 }
 
+// Host -> device copy on the calling thread's own stream, complete on return.  Uploads
+// from several threads (the serving loop admits fits in parallel) then overlap instead of
+// queueing on the legacy default stream, and never wait for a context's evaluations.
+cudaError_t copy_h2d(void* dst, const void* src, size_t bytes) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, cudaStreamPerThread);
+  return e == cudaSuccess ? cudaStreamSynchronize(cudaStreamPerThread) : e;
+}
+
+// A pinned host buffer per thread, reused across uploads (grows, freed at thread exit).
+struct PinnedScratch {
+  void* p = nullptr;
+  size_t cap = 0;
+  ~PinnedScratch() {
+    if (p) cudaFreeHost(p);
+  }
+  void* get(size_t bytes) {
+    if (bytes <= cap) return p;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    const size_t want = std::max(bytes + bytes / 2, size_t(1) << 20);
+    if (cudaHostAlloc(&p, want, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return nullptr;
+    }
+    cap = want;
+    return p;
+  }
+};
+thread_local PinnedScratch tl_pinned;
+
 int upload(musr_ctx* ctx, DevBuf& b, const void* src, size_t bytes) {
   int rc = dalloc(ctx, b, bytes);
   if (rc) return rc;
   if (bytes) {
-    cudaError_t e = cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy");
+    cudaError_t e = copy_h2d(b.p, src, bytes);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync");
   }
   return MUSR_OK;
 }
@@ -200,6 +232,7 @@ void free_compiled(musr_ctx* ctx, Compiled& c) {
   c.p_ptr.clear();
   c.p_cols.clear();
   c.valid = false;
+  c.planned = false;
   c.reason.clear();
 }
 
@@ -238,6 +271,7 @@ int compile(musr_ctx* ctx, int prec, int var) {
                                        ctx->consts.data(), &hs);
     if (why) {
       c.reason = why;
+      c.planned = true;
       return MUSR_OK;  // SPLIT unavailable for this theory; FP64 still is
     }
     group_cap = musr::shape_group(hs.shape);
@@ -351,8 +385,14 @@ int compile(musr_ctx* ctx, int prec, int var) {
   c.p_cols = std::move(p_cols);
   c.hs = hs;
   c.valid = true;
+  c.planned = true;
   c.uploaded = false;
   return MUSR_OK;
+}
+
+// Plans one decomposition the first time a launch needs it (host work only).
+int ensure_compiled(musr_ctx* ctx, int prec, int var) {
+  return ctx->comp[prec][var].planned ? MUSR_OK : compile(ctx, prec, var);
 }
 
 // Copies one decomposition's tables to the device (first use only): one
@@ -360,6 +400,8 @@ int compile(musr_ctx* ctx, int prec, int var) {
 int ensure_uploaded(musr_ctx* ctx, int prec, int var) {
   Compiled& c = ctx->comp[prec][var];
   if (c.uploaded) return MUSR_OK;
+  int crc = ensure_compiled(ctx, prec, var);
+  if (crc) return crc;
   size_t off = 0;
   auto place = [&](size_t bytes) {
     const size_t o = off;
@@ -391,8 +433,8 @@ int ensure_uploaded(musr_ctx* ctx, int prec, int var) {
   std::memcpy(blob.data() + o_cc, c.col_chunk.data(), sizeof(int) * c.col_chunk.size());
   std::memcpy(blob.data() + o_pp, c.p_ptr.data(), sizeof(int) * c.p_ptr.size());
   std::memcpy(blob.data() + o_pc, c.p_cols.data(), sizeof(int) * c.p_cols.size());
-  cudaError_t e = cudaMemcpy(base, blob.data(), off, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy(tables)");
+  cudaError_t e = copy_h2d(base, blob.data(), off);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(tables)");
   c.d_hs = reinterpret_cast<const HistSet*>(base + o_hs);
   c.uploaded = true;
   return MUSR_OK;
@@ -404,7 +446,10 @@ void invalidate_eval(musr_ctx* ctx) { ctx->ev.key_valid = false; }
 // batch still gives every resident CTA a few items, else the small ones.
 int pick_variant(musr_ctx* ctx, int prec, int nvec) {
   int items[musr::kVariants];
-  for (int v = 0; v < musr::kVariants; ++v) items[v] = ctx->comp[prec][v].hs.nitems;
+  for (int v = 0; v < musr::kVariants; ++v) {
+    ensure_compiled(ctx, prec, v);
+    items[v] = ctx->comp[prec][v].hs.nitems;
+  }
   return musr::pick_decomposition(items, nvec, prec, ctx->num_sms);
 }
 
@@ -477,8 +522,8 @@ int prepare_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec,
   fill_jobs(ctx, prec, var, mode, grad, nvec, d_params, d_out, jobs.data(), 0);
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
-  e = cudaMemcpy(ev.jobs.p, jobs.data(), sizeof(Job) * nvec, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy(jobs)");
+  e = copy_h2d(ev.jobs.p, jobs.data(), sizeof(Job) * nvec);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(jobs)");
   ev.key_valid = true;
   ev.k_prec = prec;
   ev.k_var = var;
@@ -497,8 +542,8 @@ int check_ready(musr_ctx* ctx, int mode, int prec) {
   if (mode != MUSR_CHI2 && mode != MUSR_MLE) return fail(ctx, MUSR_EINVAL, "mode must be MUSR_CHI2 or MUSR_MLE");
   if (prec != MUSR_FP64 && prec != MUSR_SPLIT)
     return fail(ctx, MUSR_EINVAL, "precision must be MUSR_FP64 or MUSR_SPLIT");
-  if (!ctx->comp[prec][0].valid)
-    return fail(ctx, MUSR_EINVAL, "precision unavailable for this theory: " + ctx->comp[prec][0].reason);
+  if (prec == MUSR_SPLIT && !ctx->split_reason.empty())
+    return fail(ctx, MUSR_EINVAL, "precision unavailable for this theory: " + ctx->split_reason);
   return MUSR_OK;
 }
 
@@ -687,38 +732,54 @@ int musr_upload_histograms(musr_ctx* ctx, const void* counts, int dtype, int nhi
   const int64_t stride = (nbins + kRowAlign - 1) / kRowAlign * kRowAlign;
   const size_t esz = dtype == MUSR_DTYPE_FP64 ? 8 : 4;
   const size_t total = static_cast<size_t>(nhist) * stride * esz;
-  // Checks (and the INT32 -> FP32 conversion) as branch-free loops the compiler vectorises.
-  std::vector<float> conv;
-  const void* src = counts;
-  const size_t n = static_cast<size_t>(nhist) * nbins;
-  if (dtype == MUSR_DTYPE_INT32) {
-    const int32_t* ci = static_cast<const int32_t*>(counts);
-    conv.resize(n);
-    int bad = 0;
-    for (size_t i = 0; i < n; ++i) {
-      const int32_t v = ci[i];
-      bad |= static_cast<int>(v >= (1 << 24)) | static_cast<int>(v <= -(1 << 24));
-      conv[i] = static_cast<float>(v);
-    }
-    if (bad) return fail(ctx, MUSR_EINVAL, "INT32 counts must satisfy |count| < 2^24 (exact in FP32)");
-    src = conv.data();
-  } else if (dtype == MUSR_DTYPE_FP32) {
-    const float* cf = static_cast<const float*>(counts);
-    int bad = 0;
-    for (size_t i = 0; i < n; ++i) bad |= static_cast<int>(!(std::fabs(cf[i]) <= 3.4028234663852886e38f));
-    if (bad) return fail(ctx, MUSR_EINVAL, "counts must be finite");
-  } else {
-    const double* cd = static_cast<const double*>(counts);
-    int bad = 0;
-    for (size_t i = 0; i < n; ++i) bad |= static_cast<int>(!(std::fabs(cd[i]) <= 1.7976931348623157e308));
-    if (bad) return fail(ctx, MUSR_EINVAL, "counts must be finite");
+  // The device image of the counts (row stride, zero padding, INT32 converted to FP32) is
+  // built in one pass with the checks (branch-free loops the compiler vectorises), in a
+  // pinned buffer of this thread that is reused, then copied in one transfer.
+  const size_t n_row = static_cast<size_t>(nbins), s_row = static_cast<size_t>(stride);
+  std::vector<unsigned char> pageable;
+  void* img = total <= (size_t(64) << 20) ? tl_pinned.get(total) : nullptr;
+  if (!img) {
+    pageable.resize(total);
+    img = pageable.data();
   }
+  int bad = 0;
+  for (int h = 0; h < nhist; ++h) {
+    if (dtype == MUSR_DTYPE_INT32) {
+      const int32_t* ci = static_cast<const int32_t*>(counts) + h * n_row;
+      float* d = static_cast<float*>(img) + h * s_row;
+      for (size_t i = 0; i < n_row; ++i) {
+        const int32_t v = ci[i];
+        bad |= static_cast<int>(v >= (1 << 24)) | static_cast<int>(v <= -(1 << 24));
+        d[i] = static_cast<float>(v);
+      }
+      for (size_t i = n_row; i < s_row; ++i) d[i] = 0.0f;
+    } else if (dtype == MUSR_DTYPE_FP32) {
+      const float* cf = static_cast<const float*>(counts) + h * n_row;
+      float* d = static_cast<float*>(img) + h * s_row;
+      for (size_t i = 0; i < n_row; ++i) {
+        const float v = cf[i];
+        bad |= static_cast<int>(!(std::fabs(v) <= 3.4028234663852886e38f));
+        d[i] = v;
+      }
+      for (size_t i = n_row; i < s_row; ++i) d[i] = 0.0f;
+    } else {
+      const double* cd = static_cast<const double*>(counts) + h * n_row;
+      double* d = static_cast<double*>(img) + h * s_row;
+      for (size_t i = 0; i < n_row; ++i) {
+        const double v = cd[i];
+        bad |= static_cast<int>(!(std::fabs(v) <= 1.7976931348623157e308));
+        d[i] = v;
+      }
+      for (size_t i = n_row; i < s_row; ++i) d[i] = 0.0;
+    }
+  }
+  if (bad)
+    return fail(ctx, MUSR_EINVAL,
+                dtype == MUSR_DTYPE_INT32 ? "INT32 counts must satisfy |count| < 2^24 (exact in FP32)"
+                                          : "counts must be finite");
   if ((rc = dalloc(ctx, ctx->counts_own, total))) return rc;
-  cudaError_t e = cudaMemset(ctx->counts_own.p, 0, total);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemset");
-  e = cudaMemcpy2D(ctx->counts_own.p, stride * esz, src, nbins * esz, nbins * esz, nhist,
-                   cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy2D");
+  cudaError_t e = copy_h2d(ctx->counts_own.p, img, total);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(counts)");
   ctx->d_counts = ctx->counts_own.p;
   ctx->store = dtype == MUSR_DTYPE_FP64 ? kStoreF64 : kStoreF32;
   ctx->stride = stride;
@@ -818,9 +879,15 @@ int musr_set_map(musr_ctx* ctx, const int32_t* map, int nslots, int nparams, con
   int rc;
   if ((rc = upload(ctx, ctx->d_map, ctx->map.data(), sizeof(int32_t) * n))) return rc;
   if ((rc = upload(ctx, ctx->d_consts, cpad.data(), sizeof(double) * cpad.size()))) return rc;
-  for (int prec : {MUSR_FP64, MUSR_SPLIT})
-    for (int var = 0; var < musr::kVariants; ++var)
-      if ((rc = compile(ctx, prec, var))) return rc;
+  // Decompositions are planned when a launch first needs one; whether the SPLIT path
+  // can run this theory at all is decided now.
+  {
+    HistSet probe;
+    std::memset(&probe, 0, sizeof(probe));
+    const char* why = musr::plan_split(ctx->terms.data(), static_cast<int>(ctx->terms.size()), ctx->map.data(),
+                                       ctx->H, ctx->nslots, ctx->consts.data(), &probe);
+    ctx->split_reason = why ? why : "";
+  }
   ctx->have_map = true;
   return MUSR_OK;
 }

@@ -44,6 +44,7 @@ class Arena {
 // The tables are planned on the host when the map is set and copied to the
 // device (one allocation, one copy) the first time a launch needs them.
 struct Compiled {
+  bool planned = false;  // compile() has run since the map was set
   bool valid = false;
   std::string reason;  // why this precision is unavailable (valid == false)
   HistSet hs{};        // host copy (device pointers inside once uploaded)
@@ -118,6 +119,7 @@ struct musr_ctx {
   bool have_map = false;
   std::vector<int32_t> map;
   int nslots = 0, P = 0;
+  std::string split_reason;  // why the SPLIT path cannot run this theory (empty: it can)
   std::vector<double> consts;
   musr::DevBuf d_map, d_consts;
   // [precision][decomposition]: tiles of (bins per CTA iteration) << v bins; a

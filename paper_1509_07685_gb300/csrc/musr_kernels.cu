@@ -726,6 +726,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
 #pragma unroll
       for (int j = 0; j < BPT; ++j) V[m][j] = 0.0f;
     float vit = 0.0f;  // this iteration's cost terms
+    float2 vit2 = make_float2(0.0f, 0.0f);  // ... per bin of the thread
 
     // Per (histogram, bin).  Away from the ends of the fit range every bin of the warp is
     // valid and the loop runs without masks.
@@ -766,51 +767,54 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
 #pragma unroll
         for (int q = 0; q < 4 * NG4; ++q) gm[q] = gn[q];
         if (hl + 1 < G) fetch(hl + 1, dn, gn);
+        {  // the thread's two bins as one float2: packed FP32 (two lanes' work per instruction)
+          const float2 dd2 = make_float2(d[0], d[1]);
+          float2 N2 = make_float2(gm[0], gm[0]);
 #pragma unroll
-        for (int j = 0; j < BPT; ++j) {
-          float N = gm[0];
-#pragma unroll
-          for (int m = 0; m < M; ++m) N = fmaf(gm[1 + m], B[m][j], N);
-          const float dd = d[j];
-          float v, u;  // cost term (chi^2, or half the deviance) and d(cost/2)/dN
+          for (int m = 0; m < M; ++m)
+            N2 = __ffma2_rn(make_float2(gm[1 + m], gm[1 + m]), make_float2(B[m][0], B[m][1]), N2);
+          const float2 r2 = __fadd2_rn(N2, make_float2(-dd2.x, -dd2.y));
+          float2 v2, u2;
           if (MODE == 0) {
-            const float iv = rcpa(fmaxf(dd, 1.0f));
-            const float r = __fsub_rn(N, dd);
-            u = __fmul_rn(r, iv);
-            v = __fmul_rn(r, u);
+            const float2 iv2 = make_float2(rcpa(fmaxf(dd2.x, 1.0f)), rcpa(fmaxf(dd2.y, 1.0f)));
+            u2 = __fmul2_rn(r2, iv2);
+            v2 = __fmul2_rn(r2, u2);
           } else {
-            // Half deviance (N - d) - d ln(N/d) = N phi(u), u = 1 - d/N, with
-            // phi(u) = u + (1 - u) ln(1 - u) = sum_{k>=2} u^k / (k (k - 1)): the series to u^10
-            // for |u| < 0.2 (relative truncation < 1.3e-8, no cancellation), else the logarithm
-            // directly.  d = 0: N.  d > 0 >= N: not finite (+inf or NaN), reported by the host.
-            const float rN = rcpa(N);
-            const float r = __fsub_rn(N, dd);
-            const float uu = __fmul_rn(r, rN);
-            float p = fmaf(uu, 1.0f / 90.0f, 1.0f / 72.0f);
-            p = fmaf(uu, p, 1.0f / 56.0f);
-            p = fmaf(uu, p, 1.0f / 42.0f);
-            p = fmaf(uu, p, 1.0f / 30.0f);
-            p = fmaf(uu, p, 1.0f / 20.0f);
-            p = fmaf(uu, p, 1.0f / 12.0f);
-            p = fmaf(uu, p, 1.0f / 6.0f);
-            p = fmaf(uu, p, 0.5f);
-            const float vs = __fmul_rn(r, __fmul_rn(uu, p));
-            const float vl = fmaf(__fmul_rn(dd, kLn2F), lg2a(__fmul_rn(dd, rN)), r);
-            const bool pos = dd > 0.0f;
-            v = pos ? (fabsf(uu) < 0.2f ? vs : vl) : r;
-            u = pos ? uu : 1.0f;
+            const float2 rN2 = make_float2(rcpa(N2.x), rcpa(N2.y));
+            const float2 uu2 = __fmul2_rn(r2, rN2);
+            float2 p2 = __ffma2_rn(uu2, make_float2(1.0f / 90.0f, 1.0f / 90.0f), make_float2(1.0f / 72.0f, 1.0f / 72.0f));
+            p2 = __ffma2_rn(uu2, p2, make_float2(1.0f / 56.0f, 1.0f / 56.0f));
+            p2 = __ffma2_rn(uu2, p2, make_float2(1.0f / 42.0f, 1.0f / 42.0f));
+            p2 = __ffma2_rn(uu2, p2, make_float2(1.0f / 30.0f, 1.0f / 30.0f));
+            p2 = __ffma2_rn(uu2, p2, make_float2(1.0f / 20.0f, 1.0f / 20.0f));
+            p2 = __ffma2_rn(uu2, p2, make_float2(1.0f / 12.0f, 1.0f / 12.0f));
+            p2 = __ffma2_rn(uu2, p2, make_float2(1.0f / 6.0f, 1.0f / 6.0f));
+            p2 = __ffma2_rn(uu2, p2, make_float2(0.5f, 0.5f));
+            const float2 vs2 = __fmul2_rn(r2, __fmul2_rn(uu2, p2));
+            const float2 x2 = __fmul2_rn(dd2, rN2);
+            const float2 vl2 = __ffma2_rn(__fmul2_rn(dd2, make_float2(kLn2F, kLn2F)),
+                                          make_float2(lg2a(x2.x), lg2a(x2.y)), r2);
+            const bool p0 = dd2.x > 0.0f, p1 = dd2.y > 0.0f;
+            v2.x = p0 ? (fabsf(uu2.x) < 0.2f ? vs2.x : vl2.x) : r2.x;
+            v2.y = p1 ? (fabsf(uu2.y) < 0.2f ? vs2.y : vl2.y) : r2.y;
+            u2.x = p0 ? uu2.x : 1.0f;
+            u2.y = p1 ? uu2.y : 1.0f;
           }
-          if (MASKED && !valid[j]) {
-            v = 0.0f;
-            u = 0.0f;
+          if (MASKED) {
+            if (!valid[0]) v2.x = u2.x = 0.0f;
+            if (!valid[1]) v2.y = u2.y = 0.0f;
           }
-          vit = __fadd_rn(vit, v);
+          vit2 = __fadd2_rn(vit2, v2);
           if (GRAD) {
 #pragma unroll
-            for (int m = 0; m < M; ++m) gacc[hl][m] = fmaf(u, B[m][j], gacc[hl][m]);
-            gacc[hl][M] += u;
+            for (int m = 0; m < M; ++m) gacc[hl][m] = fmaf(u2.y, B[m][1], fmaf(u2.x, B[m][0], gacc[hl][m]));
+            gacc[hl][M] = (gacc[hl][M] + u2.x) + u2.y;
 #pragma unroll
-            for (int m = 0; m < M; ++m) V[m][j] = fmaf(u, gm[1 + m], V[m][j]);
+            for (int m = 0; m < M; ++m) {
+              const float2 Vm = __ffma2_rn(u2, make_float2(gm[1 + m], gm[1 + m]), make_float2(V[m][0], V[m][1]));
+              V[m][0] = Vm.x;
+              V[m][1] = Vm.y;
+            }
           }
         }
       }
@@ -819,6 +823,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
       hist_loop(std::false_type{});
     else
       hist_loop(std::true_type{});
+    vit = __fadd_rn(vit2.x, vit2.y);
     {  // Kahan-compensated running sum of the per-iteration partials
       const float y = __fsub_rn(vit, acc_c);
       const float tsum = __fadd_rn(acc_v, y);

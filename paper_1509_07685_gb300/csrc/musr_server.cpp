@@ -300,9 +300,12 @@ size_t estimate_bytes(const Request& r) {
 // Admits queued fits, first come first served, while there are free slots and the arena
 // (the HBM budget) has room.  When the arena clearly holds a whole batch, the batch is
 // configured by the helper threads in parallel (uploads and planning overlap); otherwise
-// one at a time, so that a fit that waits for memory keeps its place.
-void admit(musr_server* s) {
-  for (;;) {
+// one at a time, so that a fit that waits for memory keeps its place.  With
+// during_step, admission stops after the first batch once the device has finished the
+// step's work, so that admitting barely lengthens a step (the rest waits for the next).
+void admit(musr_server* s, bool during_step = false) {
+  for (bool first = true;; first = false) {
+    if (during_step && !first && cudaStreamQuery(s->stream) == cudaSuccess) return;
     const int room = s->max_active - static_cast<int>(s->active.size());
     if (room <= 0) return;
     std::vector<std::unique_ptr<Request>> batch;
@@ -414,7 +417,7 @@ int step(musr_server* s) {
   e = cudaMemcpyAsync(s->h_out, d_out, no * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e != cudaSuccess) return MUSR_ECUDA;
   const double t_adm = s->now();
-  admit(s);  // configure newly queued fits while the step runs
+  admit(s, true);  // configure newly queued fits while the step runs
   const double t_wait = s->now();
   e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return MUSR_ECUDA;
