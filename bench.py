@@ -52,7 +52,7 @@ ALGO_INST = {0: 24.0, 1: 41.0}
 LANES_PER_SMSP, SMSP_PER_SM = 32, 4
 # DRAM bytes of one launch of the timed kernel from an ncu capture of this workload
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid for the kernel source it was taken on.
-TRAFFIC = {"kernel_sha256": "91e3b05a2e1f57fc61ce69be250df5f1c54166d36cef7c8a5ca42e68401dc66b", "bytes": 2228736}
+TRAFFIC = {"kernel_sha256": "3883925c0b25cc7875f05757b8b663127e8646d27641732b5308e04589377c5f", "bytes": 2218752}
 
 
 def _traffic():
