@@ -15,6 +15,7 @@ Every function here follows Section 4.1 of the paper:
   * Eq. log-likelihood  -- :func:`cost` with ``mode=1``
   * Eq. asymmetry       -- :func:`primitive` (the primitive factors of A(t))
   * the host-side minimiser that replaces migrad -- :func:`fit`
+  * the Gauss-Newton matrix of the cost (error estimates) -- :func:`gauss_newton`
 
 Pins (see ``tests/test_oracle_*.py``): closed-form sums of exponential and
 damped-cosine models, constant models, Kubo-Toyabe special values, the
@@ -73,6 +74,8 @@ def _load():
             lib.oracle_cost_cstep.restype = ctypes.c_int
             lib.oracle_hessian.argtypes = prob + [P(d), P(d), ctypes.c_int, P(d)]
             lib.oracle_hessian.restype = ctypes.c_int
+            lib.oracle_gauss_newton.argtypes = prob + [P(d), ctypes.c_int, P(d)]
+            lib.oracle_gauss_newton.restype = ctypes.c_int
             lib.oracle_fit.argtypes = prob + [ctypes.c_int, P(d), P(d), ctypes.c_int, d, P(d), P(d),
                                               P(d), P(ctypes.c_int)]
             lib.oracle_fit.restype = ctypes.c_int
@@ -185,6 +188,18 @@ def hessian(prob, x, mode: int = CHI2, steps=None) -> np.ndarray:
                                 _ptr(H, ctypes.c_double))
     if rc:
         raise FloatingPointError("cost is +inf near x")
+    return H
+
+
+def gauss_newton(prob, x, mode: int = CHI2) -> np.ndarray:
+    """Gauss-Newton matrix sum_bins (d^2 cost/dN^2) J J^T, J the parameter gradient of N
+    (Eq. chisq: d^2/dN^2 = 2/max(d,1); Eq. log-likelihood: 2 d / N^2)."""
+    a = _Args(prob)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    H = np.zeros((prob.nparams, prob.nparams))
+    rc = _load().oracle_gauss_newton(*a.args, _ptr(x, ctypes.c_double), mode, _ptr(H, ctypes.c_double))
+    if rc:
+        raise FloatingPointError("-2lnL undefined at x")
     return H
 
 

@@ -234,6 +234,43 @@ int cost_value(const Problem& pb, const T* x, int mode, T* out) {
   return 0;
 }
 
+// Expected count N of histogram h at time t (Eq. positron_histo) and its derivative with
+// respect to every local slot, through the product rule of each term.
+double model_and_slot_derivs(const Problem& pb, const double* x, int h, double t, double* dslot) {
+  const double N0 = slot_value(pb, x, h, 0);
+  const double E = std::exp(-t / kTauMu);
+  std::fill(dslot, dslot + pb.nslots, 0.0);
+  double A = 0.0;
+  for (int k = 0; k < pb.th.nterms; ++k) {
+    int np = pb.th.nprim[k];
+    double f[kMaxPrim], p0[kMaxPrim], p1[kMaxPrim];
+    for (int m = 0; m < np; ++m) {
+      int kind = pb.th.kind[k * kMaxPrim + m];
+      const int32_t* sl = pb.th.slot + (k * kMaxPrim + m) * 2;
+      p0[m] = slot_value(pb, x, h, sl[0]);
+      p1[m] = nslots_of(kind) == 2 ? slot_value(pb, x, h, sl[1]) : 0.0;
+      f[m] = primitive(kind, p0[m], p1[m], t);
+    }
+    double term = 1.0;
+    for (int m = 0; m < np; ++m) term *= f[m];
+    A += term;
+    for (int m = 0; m < np; ++m) {
+      int kind = pb.th.kind[k * kMaxPrim + m];
+      const int32_t* sl = pb.th.slot + (k * kMaxPrim + m) * 2;
+      double rest = 1.0;
+      for (int q = 0; q < np; ++q)
+        if (q != m) rest *= f[q];
+      double d0, d1;
+      primitive_deriv(kind, p0[m], p1[m], t, &d0, &d1);
+      dslot[sl[0]] += N0 * E * d0 * rest;
+      if (nslots_of(kind) == 2) dslot[sl[1]] += N0 * E * d1 * rest;
+    }
+  }
+  dslot[0] += E * (1.0 + A);
+  dslot[1] += 1.0;
+  return N0 * E * (1.0 + A) + slot_value(pb, x, h, 1);
+}
+
 // Value plus analytic gradient: dcost/dx_p = sum over bins of
 // (dcost/dN) * sum over (slot s of hist h mapped to p) dN/d(slot s).
 // gscale[p] accumulates sum |per-bin contribution|, the scale against which
@@ -246,44 +283,11 @@ int cost_grad(const Problem& pb, const double* x, int mode, double* value, doubl
   bool bad = false;
   for (int h = 0; h < pb.H; ++h) {
     const double* row = pb.data + static_cast<int64_t>(h) * pb.B;
-    double N0 = slot_value(pb, x, h, 0);
     for (int64_t n = 0; n < pb.B; ++n) {
       double t = bin_time(pb, h, n);
       if (!in_fit(pb, t)) continue;
       double d = row[n];
-      double E = std::exp(-t / kTauMu);
-      // A(t) and the derivative of every slot through the product rule.
-      std::fill(dslot.begin(), dslot.end(), 0.0);
-      double A = 0.0;
-      for (int k = 0; k < pb.th.nterms; ++k) {
-        int np = pb.th.nprim[k];
-        double f[kMaxPrim], p0[kMaxPrim], p1[kMaxPrim];
-        for (int m = 0; m < np; ++m) {
-          int kind = pb.th.kind[k * kMaxPrim + m];
-          const int32_t* sl = pb.th.slot + (k * kMaxPrim + m) * 2;
-          p0[m] = slot_value(pb, x, h, sl[0]);
-          p1[m] = nslots_of(kind) == 2 ? slot_value(pb, x, h, sl[1]) : 0.0;
-          f[m] = primitive(kind, p0[m], p1[m], t);
-        }
-        double term = 1.0;
-        for (int m = 0; m < np; ++m) term *= f[m];
-        A += term;
-        for (int m = 0; m < np; ++m) {
-          int kind = pb.th.kind[k * kMaxPrim + m];
-          const int32_t* sl = pb.th.slot + (k * kMaxPrim + m) * 2;
-          double rest = 1.0;
-          for (int q = 0; q < np; ++q)
-            if (q != m) rest *= f[q];
-          double d0, d1;
-          primitive_deriv(kind, p0[m], p1[m], t, &d0, &d1);
-          dslot[sl[0]] += N0 * E * d0 * rest;
-          if (nslots_of(kind) == 2) dslot[sl[1]] += N0 * E * d1 * rest;
-        }
-      }
-      dslot[0] += E * (1.0 + A);
-      dslot[1] += 1.0;
-      double Nbkg = slot_value(pb, x, h, 1);
-      double N = N0 * E * (1.0 + A) + Nbkg;
+      double N = model_and_slot_derivs(pb, x, h, t, dslot.data());
       double W;  // dcost / dN for this bin
       if (mode == 0) {
         double r = d - N;
@@ -318,6 +322,50 @@ int cost_grad(const Problem& pb, const double* x, int mode, double* value, doubl
     return 1;
   }
   *value = acc.value();
+  return 0;
+}
+
+// Gauss-Newton matrix of the cost: sum over bins of (d^2 cost / dN^2) J J^T, with J the
+// parameter gradient of N (the second-derivative term of N dropped).  d^2/dN^2 of the bin
+// cost is 2 / max(d, 1) for Eq. chisq and 2 d / N^2 for Eq. log-likelihood (0 when d <= 0).
+// gn is [P][P]; returns 1 (gn zeros) when the likelihood is undefined.
+int gauss_newton(const Problem& pb, const double* x, int mode, double* gn) {
+  const int P = pb.P;
+  std::vector<Neumaier> acc(static_cast<size_t>(P) * P);
+  std::vector<double> dslot(pb.nslots), J(P);
+  for (int h = 0; h < pb.H; ++h) {
+    const double* row = pb.data + static_cast<int64_t>(h) * pb.B;
+    for (int64_t n = 0; n < pb.B; ++n) {
+      double t = bin_time(pb, h, n);
+      if (!in_fit(pb, t)) continue;
+      double d = row[n];
+      double N = model_and_slot_derivs(pb, x, h, t, dslot.data());
+      double c2;
+      if (mode == 0) {
+        c2 = 2.0 / std::fmax(d, 1.0);
+      } else if (d > 0.0) {
+        if (N <= 0.0) {
+          std::fill(gn, gn + static_cast<size_t>(P) * P, 0.0);
+          return 1;
+        }
+        c2 = 2.0 * d / (N * N);
+      } else {
+        c2 = 0.0;
+      }
+      std::fill(J.begin(), J.end(), 0.0);
+      for (int s = 0; s < pb.nslots; ++s) {
+        int32_t m = pb.map[static_cast<int64_t>(h) * pb.nslots + s];
+        if (m >= 0) J[m] += dslot[s];
+      }
+      for (int p = 0; p < P; ++p) {
+        if (J[p] == 0.0) continue;
+        for (int q = p; q < P; ++q) acc[static_cast<size_t>(p) * P + q].add(c2 * J[p] * J[q]);
+      }
+    }
+  }
+  for (int p = 0; p < P; ++p)
+    for (int q = p; q < P; ++q) gn[static_cast<size_t>(p) * P + q] = gn[static_cast<size_t>(q) * P + p] =
+                                    acc[static_cast<size_t>(p) * P + q].value();
   return 0;
 }
 
@@ -417,6 +465,12 @@ int oracle_hessian(ORACLE_PROBLEM_ARGS, const double* x, const double* step, int
       hess[i * P + j] = hess[j * P + i] = a;
     }
   return 0;
+}
+
+// Gauss-Newton matrix [P][P] at x (see gauss_newton above).
+int oracle_gauss_newton(ORACLE_PROBLEM_ARGS, const double* x, int mode, double* gn) {
+  Problem pb = ORACLE_PROBLEM;
+  return gauss_newton(pb, x, mode, gn);
 }
 
 // BFGS minimisation standing in for Minuit2's migrad (Section 4: the

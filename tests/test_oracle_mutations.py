@@ -38,19 +38,27 @@ MUTANTS = {
     "no compensation": ("      c += (s - t) + x;\n    else\n      c += (x - t) + s;",
                         "      c += 0.0;\n    else\n      c += 0.0;"),
     "map scatter to the wrong index": ("        g[m].add(c);", "        g[(m + 1) % pb.P].add(c);"),
-    "N0 derivative drops the asymmetry": ("      dslot[0] += E * (1.0 + A);", "      dslot[0] += E;"),
+    "N0 derivative drops the asymmetry": ("  dslot[0] += E * (1.0 + A);", "  dslot[0] += E;"),
+    "Gauss-Newton weight of -2lnL": ("        c2 = 2.0 * d / (N * N);", "        c2 = 2.0 / N;"),
+    "Gauss-Newton weight of chi^2": ("        c2 = 2.0 / std::fmax(d, 1.0);", "        c2 = 1.0 / std::fmax(d, 1.0);"),
 }
 
 
+SCRATCH = os.path.join(ROOT, "tests", "_mutants")  # git-ignored
+
+
 @pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_catch_planted_mistake(name, tmp_path):
+def test_pins_catch_planted_mistake(name):
     old, new = MUTANTS[name]
     src = open(SRC).read()
     assert src.count(old) >= 1, f"mutation site not found: {name}"
     mutated = src.replace(old, new, 1)
-    cpp = tmp_path / "mutant.cpp"
-    lib = tmp_path / "mutant.so"
-    cpp.write_text(mutated)
+    os.makedirs(SCRATCH, exist_ok=True)
+    tag = "".join(c if c.isalnum() else "_" for c in name)
+    cpp = os.path.join(SCRATCH, tag + ".cpp")
+    lib = os.path.join(SCRATCH, tag + ".so")
+    with open(cpp, "w") as f:
+        f.write(mutated)
     subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
                            "-o", str(lib), str(cpp)])
     env = dict(os.environ, MUSR_ORACLE_LIB=str(lib))

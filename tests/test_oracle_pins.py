@@ -305,3 +305,40 @@ def test_paper_parameter_count_and_map_layout():
     q = mi.cfg5(nhist=64, nbins=64)
     assert q.nparams == 197
     assert set(int(v) for v in q.map.ravel() if v >= 0) == set(range(197))
+
+
+# ------------------------------------------------------------------------------------------
+# Gauss-Newton matrix (error estimates)
+# ------------------------------------------------------------------------------------------
+
+def test_gauss_newton_equals_hessian_when_data_equal_model():
+    """Where the data equal the model, d cost/dN = 0 in every bin, so the Gauss-Newton matrix
+    is the exact Hessian: it matches central differences of the analytic gradient.  Catches a
+    wrong weight (d^2 cost/dN^2) or a wrong Jacobian."""
+    terms = [[("AMP", (2,)), ("EXP", (3,)), ("TFCOS", (4, 5))], [("AMP", (6,)), ("KT", (7,))],
+             [("AMP", (8,)), ("GAUSS", (9,))]]
+    mp = [[0, 1, 2, 3, 4, 5, 6, 7, 8, 9]]
+    x = np.array([250.0, 3.0, 0.2, 0.4, 3.0, 20.0, 0.1, 0.5, 0.08, 0.7])
+    p = _problem(np.zeros((1, 700)), terms, mp, 10, bin_width_ns=10.0, fit=(0.0, 6.0))
+    dt = p.bin_width_ns / 1000.0
+    p = p.with_counts(np.array([[oracle.model(p, x, 0, n * dt) for n in range(700)]]))
+    for mode in (CHI2, MLE):
+        gn = oracle.gauss_newton(p, x, mode)
+        h = oracle.hessian(p, x, mode, steps=1e-6 * np.maximum(np.abs(x), 1e-2))
+        scale = np.sqrt(np.outer(np.diag(gn), np.diag(gn)))
+        assert np.all(np.abs(gn - h) <= 1e-6 * scale + 1e-9), np.max(np.abs(gn - h) / scale)
+        assert np.allclose(gn, gn.T, rtol=1e-14, atol=0)
+        assert np.linalg.eigvalsh(gn).min() > -1e-9 * np.abs(gn).max()
+
+
+def test_gauss_newton_of_constant_model_closed_form():
+    """N = c on any data: sum 2/max(d,1) for chi^2 and sum 2d/c^2 for -2lnL (the model is
+    linear in c, so this is also the exact second derivative)."""
+    rng = np.random.default_rng(11)
+    d = rng.poisson(3.0, size=(2, 500)).astype(float)
+    p = Problem(d, np.zeros(2), 0.5, (0.0, 1e9), [], np.array([[-1, 0], [-1, 0]], np.int32), np.array([0.0]), 1,
+                np.zeros(1), ["c"])
+    c = 2.75
+    assert oracle.gauss_newton(p, np.array([c]), CHI2)[0, 0] == pytest.approx(
+        np.sum(2.0 / np.maximum(d, 1.0)), rel=1e-14)
+    assert oracle.gauss_newton(p, np.array([c]), MLE)[0, 0] == pytest.approx(np.sum(2.0 * d / c**2), rel=1e-14)
