@@ -137,6 +137,26 @@ int musr_set_map(musr_ctx* ctx, const int32_t* map, int nslots, int nparams, con
 int musr_eval(musr_ctx* ctx, const double* params, int nparams, int mode, int precision,
               double* out_value, double* out_grad);
 
+/* Gauss-Newton products for parameter error estimates (Section 4.1: the
+ * minimiser's parameter errors come from the curvature of the cost).  With J the
+ * parameter gradient of every bin's expected count N (Eq. positron_histo), the
+ * Gauss-Newton matrix is H = sum over bins of (d^2 cost / dN^2) J J^T, where
+ * d^2/dN^2 is 2/max(d,1) for Eq. chisq and 2d/N^2 for Eq. log-likelihood (the
+ * Hessian of the cost without the term in d cost/dN, which vanishes where the
+ * model fits).  For each of ndir directions v (host dirs[ndir][nparams]) at host
+ * params[nparams]: out[ndir][1 + nparams] (host) receives v^T H v and H v.
+ * One launch for all directions; synchronous on the context's stream.
+ * Returns MUSR_ENONFINITE (row zeros after an infinite first entry) where the
+ * likelihood is undefined. */
+int musr_gn_product(musr_ctx* ctx, const double* params, int nparams, const double* dirs, int ndir, int mode,
+                    int precision, double* out);
+
+/* The whole Gauss-Newton matrix at params: out[nparams][nparams] (host),
+ * symmetrised (H + H^T)/2 from the products with every unit vector (one launch).
+ * The parameter errors of a fit at its optimum are sqrt(2 (H^-1)_ii) (both costs
+ * are -2 ln L scaled, so a change of 1 in the cost is one standard deviation). */
+int musr_gauss_newton(musr_ctx* ctx, const double* params, int nparams, int mode, int precision, double* out);
+
 /* nvec evaluations in one launch (e.g. trial points of a line search, or
  * the random parameter vectors of a scan): params is host [nvec][nparams],
  * out_values host [nvec], out_grads host [nvec][nparams] or NULL.  Returns

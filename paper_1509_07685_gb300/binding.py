@@ -29,7 +29,8 @@ MAX_PRIMS = 4
 EXPORTS = (
     "musr_ctx_create", "musr_ctx_destroy", "musr_last_error", "musr_upload_histograms",
     "musr_upload_histograms_device", "musr_set_theory", "musr_set_map", "musr_eval",
-    "musr_eval_batch", "musr_eval_device", "musr_sync", "musr_bins_in_fit",
+    "musr_eval_batch", "musr_eval_device", "musr_sync", "musr_bins_in_fit", "musr_gn_product",
+    "musr_gauss_newton",
     "musr_launches_per_eval", "musr_eval_noalloc", "musr_fit", "musr_server_create",
     "musr_server_destroy", "musr_server_submit", "musr_server_poll", "musr_server_wait",
     "musr_server_stats_get",
@@ -95,6 +96,9 @@ def _declare(lib):
                             ctypes.c_int),
         "musr_eval_device": ([vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp], ctypes.c_int),
         "musr_sync": ([vp, ctypes.c_int], ctypes.c_int),
+        "musr_gn_product": ([vp, P(d), ctypes.c_int, P(d), ctypes.c_int, ctypes.c_int, ctypes.c_int, P(d)],
+                            ctypes.c_int),
+        "musr_gauss_newton": ([vp, P(d), ctypes.c_int, ctypes.c_int, ctypes.c_int, P(d)], ctypes.c_int),
         "musr_bins_in_fit": ([vp, P(i64)], ctypes.c_int),
         "musr_launches_per_eval": ([vp, P(ctypes.c_int)], ctypes.c_int),
         "musr_eval_noalloc": ([vp, ctypes.c_int, ctypes.c_int, i64, i64, P(d), d, P(d), P(musr_term),
@@ -252,6 +256,27 @@ def musr_eval_batch(ctx, params: np.ndarray, mode: int, precision: int, grad: bo
     return vals, g, st
 
 
+def musr_gn_product(ctx, params, dirs, mode: int, precision: int):
+    """(vHv[ndir], Hv[ndir][P], status): Gauss-Newton products at params along each row of dirs."""
+    x = np.ascontiguousarray(params, dtype=np.float64)
+    v = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+    ndir, P = v.shape
+    out = np.zeros((ndir, 1 + P))
+    st = load().musr_gn_product(ctx, _dptr(x), P, _dptr(v), ndir, mode, precision, _dptr(out))
+    if st not in (MUSR_OK, MUSR_ENONFINITE):
+        _err(ctx, st)
+    return out[:, 0].copy(), out[:, 1:].copy(), st
+
+
+def musr_gauss_newton(ctx, params, mode: int, precision: int) -> np.ndarray:
+    """The Gauss-Newton matrix [P][P] of the cost at params."""
+    x = np.ascontiguousarray(params, dtype=np.float64)
+    P = x.size
+    out = np.zeros((P, P))
+    _check(ctx, load().musr_gauss_newton(ctx, _dptr(x), P, mode, precision, _dptr(out)))
+    return out
+
+
 def musr_eval_device(ctx, d_params: int, nvec: int, mode: int, precision: int, with_grad: bool,
                      d_out: int) -> None:
     _check(ctx, load().musr_eval_device(ctx, ctypes.c_void_p(d_params), nvec, mode, precision,
@@ -322,6 +347,12 @@ class Context:
 
     def eval_batch(self, X, mode=MUSR_CHI2, precision=MUSR_FP64, grad=True):
         return musr_eval_batch(self.ctx, X, mode, precision, grad)
+
+    def gauss_newton(self, x, mode=MUSR_CHI2, precision=MUSR_FP64) -> np.ndarray:
+        return musr_gauss_newton(self.ctx, x, mode, precision)
+
+    def gn_product(self, x, dirs, mode=MUSR_CHI2, precision=MUSR_FP64):
+        return musr_gn_product(self.ctx, x, dirs, mode, precision)
 
     def bins_in_fit(self) -> int:
         return musr_bins_in_fit(self.ctx)

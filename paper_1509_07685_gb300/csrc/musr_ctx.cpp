@@ -484,7 +484,7 @@ int ensure_eval(musr_ctx* ctx, int prec, int var, int nvec) {
 }
 
 void fill_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, const double* d_params,
-               double* d_out, Job* jobs, int item_begin) {
+               double* d_out, Job* jobs, int item_begin, const double* d_dirs) {
   EvalBufs& ev = ctx->ev;
   const HistSet& hs = ctx->comp[prec][var].hs;
   const HistSet* d_hs = ctx->comp[prec][var].d_hs;
@@ -503,11 +503,12 @@ void fill_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, c
     j.mode = mode;
     j.grad = grad;
     j.prec = prec;
+    j.dir = d_dirs ? d_dirs + static_cast<size_t>(v) * ctx->P : nullptr;
   }
 }
 
 int prepare_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, const double* d_params,
-                 double* d_out) {
+                 double* d_out, const double* d_dirs) {
   EvalBufs& ev = ctx->ev;
   int rc;
   if ((rc = ensure_eval(ctx, prec, var, nvec))) return rc;
@@ -516,10 +517,10 @@ int prepare_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec,
     ev.key_valid = false;
   }
   if (ev.key_valid && ev.k_prec == prec && ev.k_var == var && ev.k_mode == mode && ev.k_grad == grad &&
-      ev.k_nvec == nvec && ev.k_params == d_params && ev.k_out == d_out)
+      ev.k_nvec == nvec && ev.k_params == d_params && ev.k_out == d_out && ev.k_dirs == d_dirs)
     return MUSR_OK;
   std::vector<Job> jobs(nvec);
-  fill_jobs(ctx, prec, var, mode, grad, nvec, d_params, d_out, jobs.data(), 0);
+  fill_jobs(ctx, prec, var, mode, grad, nvec, d_params, d_out, jobs.data(), 0, d_dirs);
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
   e = copy_h2d(ev.jobs.p, jobs.data(), sizeof(Job) * nvec);
@@ -532,6 +533,7 @@ int prepare_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec,
   ev.k_nvec = nvec;
   ev.k_params = d_params;
   ev.k_out = d_out;
+  ev.k_dirs = d_dirs;
   return MUSR_OK;
 }
 
@@ -549,14 +551,14 @@ int check_ready(musr_ctx* ctx, int mode, int prec) {
 
 // Enqueues one launch of nvec evaluations reading d_params, writing d_out.
 int enqueue_eval(musr_ctx* ctx, int prec, int mode, int grad, int nvec, const double* d_params,
-                 double* d_out) {
+                 double* d_out, const double* d_dirs = nullptr) {
   const int var = pick_variant(ctx, prec, nvec);
   const HistSet& hs = ctx->comp[prec][var].hs;
   if (hs.nitems == 0) {  // no bin in the fit range: cost 0, gradient 0
     cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(double) * nvec * (1 + ctx->P), ctx->stream);
     return e == cudaSuccess ? MUSR_OK : cuda_fail(ctx, e, "cudaMemsetAsync");
   }
-  int rc = prepare_jobs(ctx, prec, var, mode, grad, nvec, d_params, d_out);
+  int rc = prepare_jobs(ctx, prec, var, mode, grad, nvec, d_params, d_out, d_dirs);
   if (rc) return rc;
   musr::LaunchInfo info;
   if (musr::launch_eval(prec, hs.shape, mode, grad, static_cast<const Job*>(ctx->ev.jobs.p), nvec,
@@ -942,6 +944,83 @@ int musr_eval_batch(musr_ctx* ctx, const double* params, int nvec, int nparams, 
   }
   if (timed_out) return fail(ctx, MUSR_ETIMEOUT, "a device-side wait for staged counts ran out (value NaN)");
   if (nonfinite) return fail(ctx, MUSR_ENONFINITE, "-2lnL is +inf: N <= 0 in a bin with d > 0");
+  return MUSR_OK;
+}
+
+int musr_gn_product(musr_ctx* ctx, const double* params, int nparams, const double* dirs, int ndir, int mode,
+                    int precision, double* out) {
+  if (!ctx) return MUSR_EINVAL;
+  DeviceScope ds(ctx->device);
+  int rc = check_ready(ctx, mode, precision);
+  if (rc) return rc;
+  if (ndir < 1) return fail(ctx, MUSR_EINVAL, "ndir must be >= 1");
+  if (nparams != ctx->P) return fail(ctx, MUSR_EINVAL, "nparams does not match the map");
+  if (!params || !dirs || !out) return fail(ctx, MUSR_EINVAL, "params, dirs and out must not be NULL");
+  const size_t P = ctx->P, nd = static_cast<size_t>(ndir) * P, no = static_cast<size_t>(ndir) * (1 + P);
+  for (size_t i = 0; i < P; ++i)
+    if (!std::isfinite(params[i])) return fail(ctx, MUSR_EINVAL, "parameters must be finite");
+  for (size_t i = 0; i < nd; ++i)
+    if (!std::isfinite(dirs[i])) return fail(ctx, MUSR_EINVAL, "directions must be finite");
+  EvalBufs& ev = ctx->ev;
+  // params repeated for every direction (one job each), then the directions
+  const size_t nin = std::max<size_t>(2 * nd, 1);
+  if ((rc = ensure_host(ctx, &ev.h_in, &ev.h_in_bytes, nin * sizeof(double)))) return rc;
+  if ((rc = ensure_host(ctx, &ev.h_out, &ev.h_out_bytes, no * sizeof(double)))) return rc;
+  if (ev.params.bytes < std::max<size_t>(nd, 1) * sizeof(double)) {
+    if ((rc = dalloc(ctx, ev.params, std::max<size_t>(nd, 1) * sizeof(double)))) return rc;
+    ev.key_valid = false;
+  }
+  if (ev.dirs.bytes < std::max<size_t>(nd, 1) * sizeof(double)) {
+    if ((rc = dalloc(ctx, ev.dirs, std::max<size_t>(nd, 1) * sizeof(double)))) return rc;
+    ev.key_valid = false;
+  }
+  if (ev.out.bytes < no * sizeof(double)) {
+    if ((rc = dalloc(ctx, ev.out, no * sizeof(double)))) return rc;
+    ev.key_valid = false;
+  }
+  for (int v = 0; v < ndir; ++v) std::memcpy(ev.h_in + static_cast<size_t>(v) * P, params, P * sizeof(double));
+  std::memcpy(ev.h_in + nd, dirs, nd * sizeof(double));
+  cudaError_t e = cudaMemcpyAsync(ev.params.p, ev.h_in, nd * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ev.dirs.p, ev.h_in + nd, nd * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(params, dirs)");
+  if ((rc = enqueue_eval(ctx, precision, mode + 2, 1, ndir, static_cast<const double*>(ev.params.p),
+                         static_cast<double*>(ev.out.p), static_cast<const double*>(ev.dirs.p))))
+    return rc;
+  e = cudaMemcpyAsync(ev.h_out, ev.out.p, no * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(out)");
+  e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+  bool nonfinite = false, timed_out = false;
+  for (int v = 0; v < ndir; ++v) {
+    const double* o = ev.h_out + static_cast<size_t>(v) * (1 + P);
+    double* r = out + static_cast<size_t>(v) * (1 + P);
+    r[0] = o[0];
+    if (std::isnan(o[0])) timed_out = true;
+    if (!std::isfinite(o[0])) {
+      nonfinite = true;
+      std::memset(r + 1, 0, P * sizeof(double));
+    } else {
+      std::memcpy(r + 1, o + 1, P * sizeof(double));
+    }
+  }
+  if (timed_out) return fail(ctx, MUSR_ETIMEOUT, "a device-side wait for staged counts ran out (value NaN)");
+  if (nonfinite) return fail(ctx, MUSR_ENONFINITE, "-2lnL undefined: N <= 0 in a bin with d > 0");
+  return MUSR_OK;
+}
+
+int musr_gauss_newton(musr_ctx* ctx, const double* params, int nparams, int mode, int precision, double* out) {
+  if (!ctx) return MUSR_EINVAL;
+  if (!out) return fail(ctx, MUSR_EINVAL, "out must not be NULL");
+  if (nparams != ctx->P || nparams < 1) return fail(ctx, MUSR_EINVAL, "nparams does not match the map");
+  const size_t P = nparams;
+  std::vector<double> dirs(P * P, 0.0), prod(P * (P + 1));
+  for (size_t i = 0; i < P; ++i) dirs[i * P + i] = 1.0;
+  const int rc = musr_gn_product(ctx, params, nparams, dirs.data(), nparams, mode, precision, prod.data());
+  if (rc) return rc;
+  for (size_t i = 0; i < P; ++i)
+    for (size_t j = 0; j < P; ++j)  // column j of H is the product with unit vector j
+      out[i * P + j] = 0.5 * (prod[j * (P + 1) + 1 + i] + prod[i * (P + 1) + 1 + j]);
   return MUSR_OK;
 }
 

@@ -158,9 +158,10 @@ struct Job {
   unsigned int* chunk_count; // [hs->nchunks], zero between launches
   unsigned int* counter;     // zero between launches
   int item_begin;            // first global item of this job in the launch
-  int mode;                  // 0 chi^2, 1 -2lnL
+  int mode;                  // 0 chi^2, 1 -2lnL; 2, 3: their Gauss-Newton product (needs dir)
   int grad;                  // 0: value only
   int prec;                  // 0 FP64, 1 SPLIT
+  const double* dir;         // [P] direction v of a Gauss-Newton product, else nullptr
 };
 
 // Launchers (host side of musr_kernels.cu).  All enqueue on `stream`.

@@ -58,13 +58,14 @@ struct Compiled {
 
 // Buffers of the eval entry points and the cached job table of the last launch.
 struct EvalBufs {
-  DevBuf params, out, partials, colsum, chunk_val, chunk_count, counters, jobs;
+  DevBuf params, out, partials, colsum, chunk_val, chunk_count, counters, jobs, dirs;
   double* h_in = nullptr;
   double* h_out = nullptr;
   size_t h_in_bytes = 0, h_out_bytes = 0;
   bool key_valid = false;
   int k_prec = -1, k_var = -1, k_mode = -1, k_grad = -1, k_nvec = -1;
   const double* k_params = nullptr;
+  const double* k_dirs = nullptr;
   double* k_out = nullptr;
 };
 
@@ -91,7 +92,7 @@ int check_ready(musr_ctx* ctx, int mode, int prec);
 // item_begin).  Used by the context's own launches and by the serving loop.
 int ensure_eval(musr_ctx* ctx, int prec, int var, int nvec);
 void fill_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, const double* d_params,
-               double* d_out, Job* jobs, int item_begin);
+               double* d_out, Job* jobs, int item_begin, const double* d_dirs = nullptr);
 
 }  // namespace musr
 

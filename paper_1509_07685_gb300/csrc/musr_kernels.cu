@@ -170,9 +170,15 @@ struct ChunkCache {
   int row[kGroupMax];
   const void* rowp[kGroupMax];       // first count of each histogram's row
   double loc[kGroupMax][kMaxSlots];  // local slot values (FP64)
+  double ldir[kGroupMax][kMaxSlots]; // local slot components of a Gauss-Newton direction (else 0)
   // SPLIT: [Nbkg, Gam_0 .. Gam_{M-1}] of each histogram (16-byte rows: vector loads)
   alignas(16) float gam[kGroupMax][kGamStride];
   double cph[kGroupMax][kMaxTerms], sph[kGroupMax][kMaxTerms];  // cos, sin of each cosine term's phase
+  // SPLIT Gauss-Newton products: [v_Nbkg, dGam_0 .. dGam_{M-1}] along the direction v, and per
+  // term the directional derivatives of its exponent rates (-t dLambda - t^2 dSigma), of its
+  // frequency and (scaled by 2/3 Delta) of its Kubo-Toyabe width
+  alignas(16) float gdot[kGroupMax][kGamStride];
+  float dlam[kMaxTerms], dsig[kMaxTerms], dnu[kMaxTerms], ddel[kMaxTerms];
   // SPLIT per-term constants of the chunk
   int kinds[kMaxTerms];
   float ca[kMaxTerms], cb[kMaxTerms];  // E*X_k = ex2(-(ca t + cb t^2))  (ca includes 1/tau)
@@ -287,6 +293,8 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
     const int hl = i / nsl, s = i - hl * nsl;
     const int h = hs.hist_index[cc.first + hl];
     cc.loc[hl][s] = slot_value(hs, job.params, h, s);
+    const int mi = hs.map[static_cast<int64_t>(h) * hs.nslots + s];
+    cc.ldir[hl][s] = job.dir && mi >= 0 ? job.dir[mi] : 0.0;
     if (s == 0) {
       cc.row[hl] = h;
       const size_t esz = hs.store == kStoreF64 ? sizeof(double) : sizeof(float);
@@ -331,6 +339,41 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
     }
 #pragma unroll
     for (int i = 0; i < kGamStride; ++i) cc.gam[hl][i] = static_cast<float>(g[i]);
+    // Directional derivative of the coefficients along a Gauss-Newton direction (zeros without).
+    double gd[kGamStride];
+#pragma unroll
+    for (int i = 0; i < kGamStride; ++i) gd[i] = 0.0;
+    if (job.dir) {
+      constexpr double kDeg = kTwoPi / 360.0;
+      const double vN0 = cc.ldir[hl][0];
+      gd[0] = cc.ldir[hl][1];
+      gd[1] = vN0;
+      if (Bs::MERGED) {
+        const double vph = cc.ldir[hl][hs.canon[0].phi_slot] * kDeg;
+        const double c = cc.cph[hl][0], sn = cc.sph[hl][0];
+        gd[2] = vN0 * c - N0 * sn * vph;
+        gd[3] = -vN0 * sn - N0 * c * vph;
+      } else {
+#pragma unroll
+        for (int k = 0; k < Bs::NT; ++k) {
+          if (k >= hs.nterms) break;
+          const CanonTerm& ct = hs.canon[k];
+          const double a = ct.amp_slot >= 0 ? cc.loc[hl][ct.amp_slot] : 1.0;
+          const double va = ct.amp_slot >= 0 ? cc.ldir[hl][ct.amp_slot] : 0.0;
+          const double dNa = vN0 * a + N0 * va;  // d(N0 a) along v
+          if (ct.kind == kTermTF) {
+            const double vph = cc.ldir[hl][ct.phi_slot] * kDeg;
+            const double c = cc.cph[hl][k], sn = cc.sph[hl][k];
+            gd[1 + Bs::bc(k)] = dNa * c - N0 * a * sn * vph;
+            gd[1 + Bs::bs(k)] = -dNa * sn - N0 * a * c * vph;
+          } else {
+            gd[1 + Bs::bc(k)] = dNa;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kGamStride; ++i) cc.gdot[hl][i] = static_cast<float>(gd[i]);
   } else if (tid >= 32 && tid < 32 + kMaxTerms) {
     const int k = tid - 32;
     cc.kinds[k] = k < hs.nterms ? hs.canon[k].kind : kTermNone;
@@ -343,6 +386,17 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
         S = fmaf(sg, sg, S);
       }
       cc.bamp[k] = hs.bamp[k];
+      {  // directional derivatives of the term's shared parameters (Gauss-Newton products)
+        double dl = 0.0, ds = 0.0;
+        for (int i = 0; i < ct.nexp; ++i) dl += cc.ldir[0][ct.exp_slot[i]];
+        for (int i = 0; i < ct.ngauss; ++i) ds += cc.loc[0][ct.gauss_slot[i]] * cc.ldir[0][ct.gauss_slot[i]];
+        cc.dlam[k] = static_cast<float>(dl);
+        cc.dsig[k] = static_cast<float>(ds);
+        cc.dnu[k] = ct.kind == kTermTF ? static_cast<float>(cc.ldir[0][ct.nu_slot]) : 0.0f;
+        cc.ddel[k] = ct.kind == kTermKT
+                         ? static_cast<float>((2.0 / 3.0) * cc.loc[0][ct.kt_slot] * cc.ldir[0][ct.kt_slot])
+                         : 0.0f;
+      }
       cc.ca[k] = kLog2eF * (static_cast<float>(1.0 / kTauMuUs) + lam);
       cc.cb[k] = kLog2eF * 0.5f * S;
       if (ct.kind == kTermKT) {
@@ -397,6 +451,9 @@ __device__ void load_tile(const HistSet& hs, int tile, int prec, Smem& sm) {
 // FP64 path: one histogram per chunk, every operation in FP64, term list as given.
 // Row: [value, N0, Nbkg, d/d(term k, primitive m, slot q)...].
 // ---------------------------------------------------------------------------------------------
+// MODE 2 and 3: the Gauss-Newton product H v of chi^2 and -2lnL for the direction v of the
+// job: per bin N' = J v (the directional derivative of N) and dcost/dN replaced by
+// (d^2 cost/dN^2) N', so that the gradient channels accumulate H v; the value is v^T H v.
 template <int MODE, bool GRAD>
 __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Smem& sm) {
   const int tid = threadIdx.x;
@@ -483,7 +540,30 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Smem& sm)
     }
     const double N = N0 * E * (1.0 + A) + Nbkg;
     double v, W;  // per-bin cost and dcost/dN
-    if (MODE == 0) {
+    if (MODE >= 2) {  // Gauss-Newton product: N' = J v, W = (d^2 cost/dN^2) N', v = W N'
+      double Nd = E * (1.0 + A) * cc.ldir[0][0] + cc.ldir[0][1];
+#pragma unroll
+      for (int k = 0; k < kMaxTerms; ++k) {
+        const int np = k < nterms ? hs.raw[k].nprim : 0;
+#pragma unroll
+        for (int m = 0; m < kMaxPrims; ++m) {
+          if (m >= np) continue;
+          Nd += N0 * E * gd[k][m][0] * cc.ldir[0][hs.raw[k].slot[m][0]];
+          if (hs.raw[k].kind[m] == kTFCos) Nd += N0 * E * gd[k][m][1] * cc.ldir[0][hs.raw[k].slot[m][1]];
+        }
+      }
+      double c2;
+      if (MODE == 2) {
+        c2 = 2.0 / fmax(d, 1.0);
+      } else if (d > 0.0) {
+        if (N <= 0.0) bad = 1;
+        c2 = N > 0.0 ? 2.0 * d / (N * N) : 0.0;
+      } else {
+        c2 = 0.0;
+      }
+      W = c2 * Nd;
+      v = W * Nd;
+    } else if (MODE == 0) {
       const double r = d - N;
       const double iv = 1.0 / fmax(d, 1.0);
       v = r * r * iv;
@@ -720,6 +800,46 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
       }
     }
 
+    // Gauss-Newton products: the basis functions' directional derivatives along v.
+    constexpr bool GN = MODE >= 2;
+    float Bd[GN ? M : 1][BPT];
+    if (GN) {
+#pragma unroll
+      for (int m = 0; m < (GN ? M : 1); ++m)
+#pragma unroll
+        for (int j = 0; j < BPT; ++j) Bd[m][j] = 0.0f;
+#pragma unroll
+      for (int k = 0; k < NT; ++k) {
+        if (k >= nterms) continue;
+        const bool istf = Bs::tf(cc.kinds, k);
+#pragma unroll
+        for (int j = 0; j < BPT; ++j) {
+          const float g = -t[j] * fmaf(t[j], cc.dsig[k], cc.dlam[k]);  // d ln(X_k) along v
+          const float w = kTwoPiF * t[j] * cc.dnu[k];                    // d theta_k along v
+          const float dc = fmaf(Pc[k][j], g, -Ps[k][j] * w);
+          const float ds = fmaf(Ps[k][j], g, Pc[k][j] * w);
+          const float dn = fmaf(Pc[k][j], g, cc.ddel[k] * dK[k][j]);   // a term without cosine
+          if (Bs::MERGED) {
+            if (istf) {
+              Bd[1 % (GN ? M : 1)][j] += dc;
+              Bd[2 % (GN ? M : 1)][j] += ds;
+            } else {
+              Bd[0][j] += dn;
+            }
+          } else if (Bs::NTF < 0 || k < Bs::NTF) {
+            if (istf) {
+              Bd[Bs::bc(k) % (GN ? M : 1)][j] = dc;
+              Bd[Bs::bs(k) % (GN ? M : 1)][j] = ds;
+            } else {
+              Bd[Bs::bc(k) % (GN ? M : 1)][j] = dn;
+            }
+          } else {
+            Bd[Bs::bc(k) % (GN ? M : 1)][j] = dn;
+          }
+        }
+      }
+    }
+
     float V[M][BPT];
 #pragma unroll
     for (int m = 0; m < M; ++m)
@@ -732,6 +852,16 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     // valid and the loop runs without masks.
     const bool all_valid = __all_sync(0xffffffffu, valid[0] && valid[1]);
     // The counts and the coefficient row of histogram hl (rows past nh are read but unused).
+    auto fetch_dot = [&](int hl, float (&gd)[4 * NG4]) {
+#pragma unroll
+      for (int q = 0; q < NG4; ++q) {
+        const float4 x = *reinterpret_cast<const float4*>(&cc.gdot[hl][4 * q]);
+        gd[4 * q] = x.x;
+        gd[4 * q + 1] = x.y;
+        gd[4 * q + 2] = x.z;
+        gd[4 * q + 3] = x.w;
+      }
+    };
     auto fetch = [&](int hl, float (&d)[BPT], float (&gm)[4 * NG4]) {
       if (staged) {
         const float2 q = *reinterpret_cast<const float2*>(&sm.stage[b][hl][tid * BPT]);
@@ -767,6 +897,39 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
 #pragma unroll
         for (int q = 0; q < 4 * NG4; ++q) gm[q] = gn[q];
         if (hl + 1 < G) fetch(hl + 1, dn, gn);
+        if (GN) {  // Gauss-Newton product: N' = J v, u = (d^2 (cost/2)/dN^2) N', value u N'
+          float gdv[4 * NG4];
+          fetch_dot(hl, gdv);
+#pragma unroll
+          for (int j = 0; j < BPT; ++j) {
+            float N = gm[0], Nd = gdv[0];
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+              N = fmaf(gm[1 + m], B[m][j], N);
+              Nd = fmaf(gdv[1 + m], B[m][j], fmaf(gm[1 + m], Bd[m % (GN ? M : 1)][j], Nd));
+            }
+            const float dd = d[j];
+            float w;
+            bool undefined = false;
+            if (MODE == 2) {
+              w = rcpa(fmaxf(dd, 1.0f));
+            } else {
+              const float rN = rcpa(N);
+              undefined = dd > 0.0f && !(N > 0.0f);
+              w = dd > 0.0f ? dd * rN * rN : 0.0f;
+            }
+            float u = w * Nd;
+            float v = undefined ? __int_as_float(0x7f800000) : u * Nd;
+            if (MASKED && !valid[j]) u = v = 0.0f;
+            vit2.x += v;
+#pragma unroll
+            for (int m = 0; m < M; ++m) gacc[hl][m] = fmaf(u, B[m][j], gacc[hl][m]);
+            gacc[hl][M] += u;
+#pragma unroll
+            for (int m = 0; m < M; ++m) V[m][j] = fmaf(u, gm[1 + m], V[m][j]);
+          }
+          continue;
+        }
         {  // the thread's two bins as one float2: packed FP32 (two lanes' work per instruction)
           const float2 dd2 = make_float2(d[0], d[1]);
           float2 N2 = make_float2(gm[0], gm[0]);
@@ -905,7 +1068,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     // undefined (N <= 0 where d > 0) or the parameters were not finite.
     if (l == 0)
       row[0] = stall ? __longlong_as_double(0x7ff8000000000000LL)
-                     : (isfinite(a) ? a * (MODE == 1 ? 2.0 : 1.0) : __longlong_as_double(0x7ff0000000000000LL));
+                     : (isfinite(a) ? a * (MODE == 0 ? 1.0 : 2.0) : __longlong_as_double(0x7ff0000000000000LL));
   }
 }
 
@@ -1181,6 +1344,8 @@ int occupancy_one() {
 template <int PREC, int SHAPE>
 int dispatch_mode(int mode, int grad, const Job* j, int n, int items, int sms, cudaStream_t s,
                   LaunchInfo* info) {
+  if (mode == 2) return launch_one<PREC, SHAPE, 2, true>(j, n, items, sms, s, info);
+  if (mode == 3) return launch_one<PREC, SHAPE, 3, true>(j, n, items, sms, s, info);
   if (mode == 0)
     return grad ? launch_one<PREC, SHAPE, 0, true>(j, n, items, sms, s, info)
                 : launch_one<PREC, SHAPE, 0, false>(j, n, items, sms, s, info);
@@ -1190,6 +1355,8 @@ int dispatch_mode(int mode, int grad, const Job* j, int n, int items, int sms, c
 
 template <int PREC, int SHAPE>
 int occupancy_mode(int mode, int grad) {
+  if (mode == 2) return occupancy_one<PREC, SHAPE, 2, true>();
+  if (mode == 3) return occupancy_one<PREC, SHAPE, 3, true>();
   if (mode == 0) return grad ? occupancy_one<PREC, SHAPE, 0, true>() : occupancy_one<PREC, SHAPE, 0, false>();
   return grad ? occupancy_one<PREC, SHAPE, 1, true>() : occupancy_one<PREC, SHAPE, 1, false>();
 }

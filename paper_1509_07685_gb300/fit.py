@@ -170,6 +170,14 @@ def sigmas_context(ctx: "B.Context", x, mode: int) -> np.ndarray:
     return np.sqrt(np.diag(2.0 * np.linalg.inv(H)))
 
 
+def sigmas_gauss_newton(ctx: "B.Context", x, mode: int, precision: int = B.MUSR_SPLIT) -> np.ndarray:
+    """sigma_i = sqrt(2 (H^-1)_ii) with H the Gauss-Newton matrix from the fused kernel (one launch);
+    NaN where H is not positive definite."""
+    H = ctx.gauss_newton(x, mode, precision)
+    with np.errstate(invalid="ignore"):
+        return np.sqrt(np.diag(2.0 * np.linalg.inv(H)))
+
+
 def fd_gradient_batch(ctx: "B.Context", x, mode: int, precision: int, steps=None):
     """Central finite-difference gradient: 2P + 1 cost evaluations (one batched launch,
     value only) -- the cost of a gradient without the fused analytic kernel."""
