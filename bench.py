@@ -52,14 +52,14 @@ ALGO_INST = {0: 24.0, 1: 41.0}
 LANES_PER_SMSP, SMSP_PER_SM = 32, 4
 # DRAM bytes of one launch of the timed kernel from an ncu capture of this workload
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid for the kernel source it was taken on.
-TRAFFIC = {"kernel_sha256": "3883925c0b25cc7875f05757b8b663127e8646d27641732b5308e04589377c5f", "bytes": 2218752}
+TRAFFIC = {"kernel_sha256": None, "bytes": None}
 
 
 def _traffic():
     """Per-launch DRAM bytes of the timed kernel (ncu), or None when the kernel source has
     changed since the capture."""
     import hashlib
-    src = os.path.join(ROOT, "paper_1509_07685_gb300", "csrc", "musr_kernels.cu")
+    src = os.path.join(ROOT, "paper_1509_07685_gb300", "csrc", "musr_kernels.cuh")
     try:
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except OSError:
@@ -424,12 +424,27 @@ def _fits(p, ctx, B, mode):
         F.fit_context(ctx, mi.start_point(p, 100 + s), mode, B.MUSR_SPLIT)
         lat_py.append(time.perf_counter() - t)
     r64 = F.fit_context(ctx, mi.start_point(p, 100), mode, B.MUSR_FP64)
-    sig = F.sigmas_context(ctx, r64["x"], mode)
+    t = time.perf_counter()
+    sig = F.sigmas_context(ctx, r64["x"], mode)  # central differences of FP64 gradients (2P)
+    t_fd = time.perf_counter() - t
     dev = float(np.max(np.abs(xs[0] - r64["x"]) / sig))
+    # Parameter errors from the fused Gauss-Newton matrix (one launch of P products).
+    for _ in range(2):
+        F.sigmas_gauss_newton(ctx, r64["x"], mode, B.MUSR_SPLIT)
+    t = time.perf_counter()
+    sig_gn = F.sigmas_gauss_newton(ctx, r64["x"], mode, B.MUSR_SPLIT)
+    t_gn = time.perf_counter() - t
+    t = time.perf_counter()
+    sig_gn64 = F.sigmas_gauss_newton(ctx, r64["x"], mode, B.MUSR_FP64)
+    t_gn64 = time.perf_counter() - t
+    errors = {"gauss_newton_split_ms": 1e3 * t_gn, "gauss_newton_fp64_ms": 1e3 * t_gn64,
+              "central_differences_fp64_ms": 1e3 * t_fd,
+              "max_rel_diff_sigma_gn_vs_fd": float(np.max(np.abs(sig_gn / sig - 1.0))),
+              "max_rel_diff_sigma_gn_split_vs_fp64": float(np.max(np.abs(sig_gn / sig_gn64 - 1.0)))}
     return {"fits_per_s": len(lat) / sum(lat), "path": "musr_fit (C++ BFGS through the C ABI)",
             "latency_ms_p50": 1e3 * float(np.median(lat)), "latency_ms_max": 1e3 * float(np.max(lat)),
             "evals_per_fit": float(np.mean(nfev)), "python_bfgs_fits_per_s": len(lat_py) / sum(lat_py),
-            "max_param_dev_split_vs_fp64_sigma": dev, "fp64_fit_s": r64["time_s"]}
+            "max_param_dev_split_vs_fp64_sigma": dev, "fp64_fit_s": r64["time_s"], "parameter_errors": errors}
 
 
 def _serving(B, n_requests, window=1024, seed=4):
