@@ -88,11 +88,11 @@ class Component:
     """One physical signal component of the simulated run."""
 
     amp: float
-    kind: str = "TF"  # "TF" or "ZF"
+    kind: str = "TF"  # "TF", "ZF" (static Gaussian fields) or "ZFL" (static Lorentzian fields)
     nu_mhz: float = 0.0
     sigma: float = 0.0  # TF field-width (Gaussian dephasing rate), 1/us
     lam: float = 0.0  # depolarisation rate, 1/us
-    delta: float = 0.0  # ZF static field width, 1/us
+    delta: float = 0.0  # ZF / ZFL static field width, 1/us
 
 
 @dataclasses.dataclass
@@ -134,8 +134,12 @@ def simulate_histogram(rng: np.random.Generator, det: Detector, comps: Sequence[
             if c.kind == "TF":
                 omega = 2.0 * math.pi * c.nu_mhz + c.sigma * rng.standard_normal(sel.size)
                 sk = np.cos(omega * tk + phase)
-            elif c.kind == "ZF":
+            elif c.kind in ("ZF", "ZFL"):
+                # fields in units of gamma_mu: Gaussian, or the 3-D Lorentzian of dilute moments
+                # (a multivariate Cauchy: a Gaussian vector divided by |N(0, 1)|)
                 b = c.delta * rng.standard_normal((sel.size, 3))
+                if c.kind == "ZFL":
+                    b /= np.abs(rng.standard_normal((sel.size, 1)))
                 b2 = np.einsum("ij,ij->i", b, b)
                 bt2 = b[:, 0] ** 2 + b[:, 1] ** 2
                 sk = (b[:, 2] ** 2 + bt2 * np.cos(np.sqrt(b2) * tk)) / np.maximum(b2, 1e-300)
@@ -281,6 +285,24 @@ def cfg3(nhist: int = 4, nbins: int = 32768, bin_width_ns: float = 0.390625, see
     counts = simulate(seed, dets, comps, nbins, bin_width_ns, dtype)
     return Problem(counts, np.zeros(nhist), bin_width_ns, _full_range(nbins, bin_width_ns), terms,
                    np.array(rows, np.int32), np.zeros(0), len(truth), truth, names, "cfg3")
+
+
+def lkt_zf(nhist: int = 2, nbins: int = 1600, bin_width_ns: float = 8.0, seed: int = 7,
+           dtype=np.float64, n0: float = 3000.0) -> Problem:
+    """Zero-field static Lorentzian Kubo-Toyabe: A = A0 LKT(a, t); shared A0, a; per-histogram
+    N0, Nbkg (2 + 2 H parameters)."""
+    terms = [[("AMP", (2,)), ("LKT", (3,))]]
+    rows = [[2 + 2 * j, 3 + 2 * j, 0, 1] for j in range(nhist)]
+    names = ["A0", "a"]
+    truth = [0.22, 0.6]
+    for j in range(nhist):
+        names += [f"N0_{j}", f"Nbkg_{j}"]
+        truth += [n0, 2.0]
+    dets = [Detector(truth[2 + 2 * j], truth[3 + 2 * j], 0.0) for j in range(nhist)]
+    comps = [[Component(truth[0], "ZFL", delta=truth[1])] for _ in range(nhist)]
+    counts = simulate(seed, dets, comps, nbins, bin_width_ns, dtype)
+    return Problem(counts, np.zeros(nhist), bin_width_ns, _full_range(nbins, bin_width_ns), terms,
+                   np.array(rows, np.int32), np.zeros(0), len(truth), np.array(truth), names, "lkt_zf")
 
 
 def cfg5(nhist: int = 64, nbins: int = 1 << 20, bin_width_ns: Optional[float] = None, seed: int = 5,

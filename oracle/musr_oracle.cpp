@@ -28,6 +28,8 @@
 //     (gamma_mu B = 2 pi nu).
 //   * GAUSS(sigma) = exp(-(sigma t)^2 / 2), EXP(lambda) = exp(-lambda t).
 //   * KT(Delta) = 1/3 + 2/3 (1 - Delta^2 t^2) exp(-Delta^2 t^2 / 2).
+//   * LKT(a) = 1/3 + 2/3 (1 - a t) exp(-a t), the static Lorentzian Kubo-Toyabe
+//     relaxation (a: the Lorentzian field width times gamma_mu).
 //   * Local slot 0 is N0, slot 1 is Nbkg; terms reference any slot.
 //   * MLE with N <= 0 in a bin with d > 0 is +infinity (status 1).
 //
@@ -51,7 +53,7 @@ namespace {
 constexpr double kTauMu = 2.197019;  // muon lifetime in microseconds
 constexpr double kPi = 3.14159265358979323846;
 
-enum PrimKind { kAmp = 1, kExp = 2, kGauss = 3, kKT = 4, kTFCos = 5 };
+enum PrimKind { kAmp = 1, kExp = 2, kGauss = 3, kKT = 4, kTFCos = 5, kLKT = 6 };
 constexpr int kMaxPrim = 4;
 
 using cplx = std::complex<double>;
@@ -138,6 +140,10 @@ T primitive(int kind, const T& p0, const T& p1, double t) {
     }
     case kTFCos:
       return std::cos(2.0 * kPi * (p0 * t + p1 / 360.0));
+    case kLKT: {
+      T u = p0 * t;
+      return 1.0 / 3.0 + (2.0 / 3.0) * (1.0 - u) * std::exp(-u);
+    }
     default:
       return T(std::numeric_limits<double>::quiet_NaN());
   }
@@ -166,6 +172,11 @@ inline void primitive_deriv(int kind, double p0, double p1, double t, double* d0
       double s = std::sin(2.0 * kPi * (p0 * t + p1 / 360.0));
       *d0 = -s * 2.0 * kPi * t;
       *d1 = -s * 2.0 * kPi / 360.0;
+      break;
+    }
+    case kLKT: {
+      double u = p0 * t;
+      *d0 = (2.0 / 3.0) * t * std::exp(-u) * (u - 2.0);
       break;
     }
     default:

@@ -1,8 +1,8 @@
 """Fit consistency of the oracle on event-level Monte Carlo data.
 
 The generator (musr_inputs) never writes down a relaxation function: exponential,
-Gaussian and Kubo-Toyabe relaxation emerge from depolarisation times and field
-distributions of simulated muons.  If the oracle's model dropped the 1/2 of the
+Gaussian, Gaussian and Lorentzian Kubo-Toyabe relaxation emerge from depolarisation times
+and field distributions of simulated muons.  If the oracle's model dropped the 1/2 of the
 Gaussian, mis-stated the Kubo-Toyabe form, took the phase in radians or shifted the
 time grid, the fitted parameters would sit many sigma away from the truth.
 """
@@ -37,7 +37,7 @@ def _pulls(p, mode, seed=1):
     return (x - p.truth) / s
 
 
-@pytest.mark.parametrize("name,mode", [("cfg1", 0), ("cfg2", 1), ("cfg3", 1), ("paper_tf16", 1)])
+@pytest.mark.parametrize("name,mode", [("cfg1", 0), ("cfg2", 1), ("cfg3", 1), ("paper_tf16", 1), ("lkt_zf", 1)])
 def test_fit_recovers_truth(name, mode):
     """High-statistics fits land within a few sigma of the simulated truth.  (The chi^2
     case uses a histogram without sparse tails: Neyman's variance d biases low-count
@@ -48,6 +48,8 @@ def test_fit_recovers_truth(name, mode):
         p = mi.cfg2(nhist=2, nbins=1600, bin_width_ns=8.0, seed=102, n0=2000.0)
     elif name == "cfg3":
         p = mi.cfg3(nhist=2, nbins=1600, bin_width_ns=8.0, seed=103, n0=3000.0)
+    elif name == "lkt_zf":  # the relaxation emerges from simulated 3-D Lorentzian fields
+        p = mi.lkt_zf(nhist=2, nbins=1600, bin_width_ns=8.0, seed=105, n0=3000.0)
     else:
         p = mi.paper_tf16(nhist=2, nbins=1600, seed=104, n0=3000.0)
     z = _pulls(p, mode)

@@ -39,6 +39,10 @@ MUTANTS = {
                         "      c += 0.0;\n    else\n      c += 0.0;"),
     "map scatter to the wrong index": ("        g[m].add(c);", "        g[(m + 1) % pb.P].add(c);"),
     "N0 derivative drops the asymmetry": ("  dslot[0] += E * (1.0 + A);", "  dslot[0] += E;"),
+    "Lorentzian KT sign": ("return 1.0 / 3.0 + (2.0 / 3.0) * (1.0 - u) * std::exp(-u);",
+                           "return 1.0 / 3.0 + (2.0 / 3.0) * (1.0 + u) * std::exp(-u);"),
+    "Lorentzian KT derivative": ("*d0 = (2.0 / 3.0) * t * std::exp(-u) * (u - 2.0);",
+                                 "*d0 = (2.0 / 3.0) * t * std::exp(-u) * (u - 3.0);"),
     "Gauss-Newton weight of -2lnL": ("        c2 = 2.0 * d / (N * N);", "        c2 = 2.0 / N;"),
     "Gauss-Newton weight of chi^2": ("        c2 = 2.0 / std::fmax(d, 1.0);", "        c2 = 1.0 / std::fmax(d, 1.0);"),
 }

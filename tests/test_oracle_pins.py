@@ -48,6 +48,21 @@ def test_kubo_toyabe_special_values():
         assert abs(res.fun - (1.0 / 3.0 - (4.0 / 3.0) * math.exp(-1.5))) < 1e-12
 
 
+def test_lorentzian_kubo_toyabe_special_values():
+    """LKT(0) = 1, LKT(inf) = 1/3, LKT(1/a) = 1/3 exactly (the factor 1 - a t vanishes), and the
+    minimum at t = 2/a equal to 1/3 - (2/3) e^{-2}.  Catches a squared argument, a wrong sign of
+    the (1 - a t) factor and wrong 1/3, 2/3 weights."""
+    from scipy.optimize import minimize_scalar
+    for a in (0.2, 0.6, 2.5):
+        assert oracle.primitive("LKT", a, 0.0, 0.0) == 1.0
+        assert abs(oracle.primitive("LKT", a, 0.0, 80.0 / a) - 1.0 / 3.0) < 1e-15
+        assert abs(oracle.primitive("LKT", a, 0.0, 1.0 / a) - 1.0 / 3.0) < 1e-16
+        res = minimize_scalar(lambda t: oracle.primitive("LKT", a, 0.0, t), bounds=(0.5 / a, 5.0 / a),
+                              method="bounded", options={"xatol": 1e-10})
+        assert abs(res.x - 2.0 / a) < 1e-4 / a
+        assert abs(res.fun - (1.0 / 3.0 - (2.0 / 3.0) * math.exp(-2.0))) < 1e-12
+
+
 def test_relaxation_primitives_special_values():
     """EXP at lambda t = 1 is 1/e; GAUSS at sigma t = sqrt(2) is 1/e (the factor 1/2 of
     Eq. asymmetry); both are even/odd as they must be."""
@@ -225,6 +240,26 @@ def test_gradient_matches_complex_step(mode):
             e[i] = 1.0
             cs = oracle.cost_cstep(p, x, e, mode)
             assert abs(cs - g[i]) <= 1e-11 * gs[i] + 1e-300, (p.name, i, cs, g[i], gs[i])
+
+
+@pytest.mark.parametrize("mode", [CHI2, MLE])
+def test_gradient_matches_complex_step_lorentzian(mode):
+    """The same check for a theory with the Lorentzian Kubo-Toyabe primitive (alone and
+    multiplied by other relaxations)."""
+    import musr_inputs as mi
+    p = mi.lkt_zf(nhist=2, nbins=500, bin_width_ns=25.0, seed=26, n0=200.0)
+    terms = [[("AMP", (2,)), ("LKT", (3,))], [("AMP", (4,)), ("LKT", (5,)), ("EXP", (6,))]]
+    rows = [[0, 1, 2, 3, 4, 5, 6], [7, 8, 2, 3, 4, 5, 6]]
+    q = Problem(p.counts, p.t0, p.bin_width_ns, p.fit_range_us, terms, np.array(rows, np.int32), np.zeros(0), 9,
+                np.zeros(9), [f"p{i}" for i in range(9)])
+    x = np.array([200.0, 2.0, 0.15, 0.6, 0.08, 1.1, 0.3, 190.0, 2.5])
+    v, g, gs, st = oracle.cost(q, x, mode)
+    assert st == 0
+    for i in range(q.nparams):
+        e = np.zeros(q.nparams)
+        e[i] = 1.0
+        cs = oracle.cost_cstep(q, x, e, mode)
+        assert abs(cs - g[i]) <= 1e-11 * gs[i] + 1e-300, (i, cs, g[i], gs[i])
 
 
 def test_gradient_matches_central_differences():
