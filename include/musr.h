@@ -64,7 +64,8 @@ enum {
   MUSR_PRIM_EXP = 2,
   MUSR_PRIM_GAUSS = 3,
   MUSR_PRIM_KT = 4,
-  MUSR_PRIM_TFCOS = 5 /* slot[0] = nu (MHz), slot[1] = phi (degrees) */
+  MUSR_PRIM_TFCOS = 5, /* slot[0] = nu (MHz), slot[1] = phi (degrees) */
+  MUSR_PRIM_LKT = 6    /* static Lorentzian Kubo-Toyabe 1/3 + 2/3 (1 - a t) exp(-a t); slot[0] = a (1/us) */
 };
 
 #define MUSR_MAX_PRIMS 4

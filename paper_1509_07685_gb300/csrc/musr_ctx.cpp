@@ -300,7 +300,7 @@ int compile(musr_ctx* ctx, int prec, int var) {
         const CanonTerm& ct = hs.canon[k];
         for (int i = 0; i < ct.nexp; ++i) push_entry(key, h, ct.exp_slot[i]);
         for (int i = 0; i < ct.ngauss; ++i) push_entry(key, h, ct.gauss_slot[i]);
-        if (ct.kind == musr::kTermKT) push_entry(key, h, ct.kt_slot);
+        if (ct.kind == musr::kTermKT || ct.kind == musr::kTermLKT) push_entry(key, h, ct.kt_slot);
         if (ct.kind == musr::kTermTF) push_entry(key, h, ct.nu_slot);
       }
       auto it = key_to_group.find(key);
@@ -828,7 +828,7 @@ int musr_set_theory(musr_ctx* ctx, const musr_term* terms, int nterms) {
     const musr_term& t = terms[k];
     if (t.nprim < 1 || t.nprim > MUSR_MAX_PRIMS) return fail(ctx, MUSR_EINVAL, "a term needs 1..4 primitives");
     for (int m = 0; m < t.nprim; ++m) {
-      if (t.kind[m] < MUSR_PRIM_AMP || t.kind[m] > MUSR_PRIM_TFCOS)
+      if (t.kind[m] < MUSR_PRIM_AMP || t.kind[m] > MUSR_PRIM_LKT)
         return fail(ctx, MUSR_EINVAL, "unknown primitive kind");
       const int ns = t.kind[m] == MUSR_PRIM_TFCOS ? 2 : 1;
       for (int q = 0; q < ns; ++q)

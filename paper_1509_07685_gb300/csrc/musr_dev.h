@@ -32,8 +32,8 @@ constexpr int kMaxSlots = 32;
 constexpr int kMaxContrib = 64;
 
 enum StoreType : int { kStoreF32 = 1, kStoreF64 = 2 };
-enum PrimKind : int { kAmp = 1, kExp = 2, kGauss = 3, kKT = 4, kTFCos = 5 };
-enum TermKind : int { kTermNone = 0, kTermPlain = 1, kTermTF = 2, kTermKT = 3 };
+enum PrimKind : int { kAmp = 1, kExp = 2, kGauss = 3, kKT = 4, kTFCos = 5, kLKT = 6 };
+enum TermKind : int { kTermNone = 0, kTermPlain = 1, kTermTF = 2, kTermKT = 3, kTermLKT = 4 };
 
 // SPLIT shapes.  Every model the SPLIT path accepts is, for each histogram j of a
 // chunk, a linear combination of M time-only basis functions B_m(t) with
@@ -66,16 +66,16 @@ struct RawTerm {
 };
 
 // A term in canonical form (SPLIT path):
-//   a * exp(-Lambda t - S t^2 / 2) * [KT(Delta, t)] * [cos(2 pi (nu t + phi / 360))]
+//   a * exp(-Lambda t - S t^2 / 2) * [KT(Delta, t) or LKT(a, t)] * [cos(2 pi (nu t + phi / 360))]
 // with Lambda the sum of its EXP rates and S the sum of its squared GAUSS widths.
 struct CanonTerm {
-  int kind;  // kTermPlain, kTermTF, kTermKT
+  int kind;  // kTermPlain, kTermTF, kTermKT, kTermLKT
   int amp_slot;  // -1: no AMP factor
   int nexp;
   int exp_slot[kMaxPrims];
   int ngauss;
   int gauss_slot[kMaxPrims];
-  int kt_slot;   // kTermKT
+  int kt_slot;   // kTermKT: Delta; kTermLKT: a
   int nu_slot;   // kTermTF
   int phi_slot;  // kTermTF
 };
@@ -91,7 +91,8 @@ enum ContribKind : int {
   kCLam = 4,   // d/dlambda = 2 ch_Lambda[k]
   kCSig = 5,   // d/dsigma  = 4 sigma ch_S[k]
   kCNu = 6,    // d/dnu     = 2 ch_nu[k]
-  kCDel = 7    // d/dDelta  = (4/3) Delta ch_Delta[k]
+  kCDel = 7,   // d/dDelta  = (4/3) Delta ch_Delta[k]
+  kCLkt = 8    // d/da (Lorentzian KT) = (4/3) ch_Delta[k]
 };
 struct Contrib {
   int slot;

@@ -400,7 +400,7 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
         cc.dnu[k] = ct.kind == kTermTF ? static_cast<float>(cc.ldir[0][ct.nu_slot]) : 0.0f;
         cc.ddel[k] = ct.kind == kTermKT
                          ? static_cast<float>((2.0 / 3.0) * cc.loc[0][ct.kt_slot] * cc.ldir[0][ct.kt_slot])
-                         : 0.0f;
+                         : (ct.kind == kTermLKT ? static_cast<float>((2.0 / 3.0) * cc.ldir[0][ct.kt_slot]) : 0.0f);
       }
       cc.ca[k] = kLog2eF * (static_cast<float>(1.0 / kTauMuUs) + lam);
       cc.cb[k] = kLog2eF * 0.5f * S;
@@ -408,6 +408,10 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
         const float D = static_cast<float>(cc.loc[0][ct.kt_slot]);
         cc.d2[k] = D * D;
         cc.dh[k] = kLog2eF * 0.5f * D * D;
+      } else if (ct.kind == kTermLKT) {  // g = ex2(-dh t) = exp(-a t), u = d2 t = a t
+        const float a = static_cast<float>(cc.loc[0][ct.kt_slot]);
+        cc.d2[k] = a;
+        cc.dh[k] = kLog2eF * a;
       } else {
         cc.d2[k] = cc.dh[k] = 0.0f;
       }
@@ -517,6 +521,11 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Smem& sm)
           const double g = exp(-0.5 * u);
           f[m] = 1.0 / 3.0 + (2.0 / 3.0) * (1.0 - u) * g;
           df[m][0] = (2.0 / 3.0) * p0 * t * t * g * (u - 3.0);
+        } else if (kind == kLKT) {
+          const double u = p0 * t;
+          const double g = exp(-u);
+          f[m] = 1.0 / 3.0 + (2.0 / 3.0) * (1.0 - u) * g;
+          df[m][0] = (2.0 / 3.0) * t * g * (u - 2.0);
         } else if (kind == kTFCos) {
           const double p1 = cc.loc[0][hs.raw[k].slot[m][1]];
           // Phase in turns, range-reduced exactly before sin/cos.
@@ -751,6 +760,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
       const float ca = cc.ca[k], cb = cc.cb[k], ba = cc.bamp[k];
       const bool istf = Bs::tf(cc.kinds, k);
       const bool iskt = !istf && cc.kinds[k] == kTermKT;
+      const bool islkt = !istf && cc.kinds[k] == kTermLKT;
 #pragma unroll
       for (int j = 0; j < BPT; ++j) {
         float X = __fmul_rn(ba, ex2a(__fmul_rn(-fmaf(cb, t[j], ca), t[j])));  // a E X_k
@@ -759,6 +769,11 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
           const float g = ex2a(__fmul_rn(-cc.dh[k], tt));
           const float u = __fmul_rn(cc.d2[k], tt);
           dK[k][j] = X * tt * g * (u - 3.0f);
+          X = __fmul_rn(X, fmaf(__fmul_rn(2.0f / 3.0f, __fsub_rn(1.0f, u)), g, 1.0f / 3.0f));
+        } else if (islkt) {  // static Lorentzian Kubo-Toyabe
+          const float g = ex2a(__fmul_rn(-cc.dh[k], t[j]));
+          const float u = __fmul_rn(cc.d2[k], t[j]);
+          dK[k][j] = X * t[j] * g * (u - 2.0f);
           X = __fmul_rn(X, fmaf(__fmul_rn(2.0f / 3.0f, __fsub_rn(1.0f, u)), g, 1.0f / 3.0f));
         }
         Pc[k][j] = X;
@@ -1135,6 +1150,9 @@ __device__ double split_slot(const HistSet& hs, const ChunkCache& cc, const doub
         break;
       case kCNu:
         if (hl == 0) g += 2.0 * sch[k * 4 + 2];
+        break;
+      case kCLkt:
+        if (hl == 0) g += (4.0 / 3.0) * sch[k * 4 + 3];
         break;
       case kCDel:
         if (hl == 0) g += (4.0 / 3.0) * cc.loc[0][s] * sch[k * 4 + 3];

@@ -100,7 +100,7 @@ extern "C" int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int
   for (int k = 0; k < nterms; ++k) {
     if (terms[k].nprim < 1 || terms[k].nprim > MUSR_MAX_PRIMS) return na_fail("a term needs 1..4 primitives");
     for (int m = 0; m < terms[k].nprim; ++m) {
-      if (terms[k].kind[m] < MUSR_PRIM_AMP || terms[k].kind[m] > MUSR_PRIM_TFCOS) return na_fail("unknown primitive");
+      if (terms[k].kind[m] < MUSR_PRIM_AMP || terms[k].kind[m] > MUSR_PRIM_LKT) return na_fail("unknown primitive");
       for (int q = 0; q < (terms[k].kind[m] == MUSR_PRIM_TFCOS ? 2 : 1); ++q)
         if (terms[k].slot[m][q] < 0 || terms[k].slot[m][q] >= nslots) return na_fail("slot index out of range");
     }
@@ -177,7 +177,7 @@ extern "C" int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int
         const CanonTerm& ct = hs.canon[k];
         for (int i = 0; i < ct.nexp; ++i) push(ct.exp_slot[i]);
         for (int i = 0; i < ct.ngauss; ++i) push(ct.gauss_slot[i]);
-        if (ct.kind == kTermKT) push(ct.kt_slot);
+        if (ct.kind == kTermKT || ct.kind == kTermLKT) push(ct.kt_slot);
         if (ct.kind == kTermTF) push(ct.nu_slot);
       }
       keylen[h] = n;

@@ -13,11 +13,11 @@
 namespace musr {
 
 // Canonical form of one term; false if the term is not
-// a * exp(-Lambda t - S t^2/2) * [KT or TFCOS] with at most one AMP.
+// a * exp(-Lambda t - S t^2/2) * [KT, LKT or TFCOS] with at most one AMP.
 inline bool canonical_term(const musr_term& t, CanonTerm* ct) {
   std::memset(ct, 0, sizeof(*ct));
   ct->amp_slot = ct->kt_slot = ct->nu_slot = ct->phi_slot = -1;
-  int namp = 0, nkt = 0, ntf = 0;
+  int namp = 0, nkt = 0, nlkt = 0, ntf = 0;
   for (int m = 0; m < t.nprim; ++m) {
     switch (t.kind[m]) {
       case MUSR_PRIM_AMP:
@@ -39,10 +39,14 @@ inline bool canonical_term(const musr_term& t, CanonTerm* ct) {
         ct->phi_slot = t.slot[m][1];
         ++ntf;
         break;
+      case MUSR_PRIM_LKT:
+        ct->kt_slot = t.slot[m][0];
+        ++nlkt;
+        break;
     }
   }
-  if (namp > 1 || nkt > 1 || ntf > 1 || (nkt && ntf)) return false;
-  ct->kind = ntf ? kTermTF : (nkt ? kTermKT : kTermPlain);
+  if (namp > 1 || nkt + nlkt + ntf > 1) return false;
+  ct->kind = ntf ? kTermTF : (nkt ? kTermKT : (nlkt ? kTermLKT : kTermPlain));
   return true;
 }
 
@@ -106,7 +110,7 @@ inline const char* plan_split(const musr_term* terms, int nterms, const int32_t*
   CanonTerm canon[kMaxTerms];
   for (int k = 0; k < nterms; ++k)
     if (!canonical_term(terms[k], &canon[k]))
-      return "SPLIT precision needs every term to hold at most one AMP, and at most one of KT or TFCOS";
+      return "SPLIT precision needs every term to hold at most one AMP, and at most one of KT, LKT or TFCOS";
   // Cosine terms first (the model is a sum: the order of its terms is free).
   int ntf = 0, nn = 0;
   hs->nterms = nterms;
@@ -151,6 +155,7 @@ inline const char* plan_split(const musr_term* terms, int nterms, const int32_t*
     for (int i = 0; i < ct.nexp; ++i) add(ct.exp_slot[i], kCLam, k);
     for (int i = 0; i < ct.ngauss; ++i) add(ct.gauss_slot[i], kCSig, k);
     if (ct.kind == kTermKT) add(ct.kt_slot, kCDel, k);
+    if (ct.kind == kTermLKT) add(ct.kt_slot, kCLkt, k);
     if (ct.kind == kTermTF) {
       add(ct.nu_slot, kCNu, k);
       // merged: one phase per histogram, whose slot receives the derivative once

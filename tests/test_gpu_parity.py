@@ -368,6 +368,22 @@ def _shape_cases():
     cases["generic_N2"] = ([[("AMP", (2,)), ("EXP", (3,))], [("AMP", (4,)), ("GAUSS", (5,)), ("KT", (6,))]],
                            [N0, BKG, ("hist", 0.15), ("shared", 0.4), ("shared", 0.1), ("shared", 0.6),
                             ("shared", 0.3)])
+    # static Lorentzian Kubo-Toyabe terms: alone with an exponential (N1), beside a cosine term
+    # (T1N1), as the third term of a merged list (T2N1m), and beside two other terms (generic)
+    cases["N1_lkt"] = ([[("AMP", (2,)), ("LKT", (3,)), ("EXP", (4,))]],
+                       [N0, BKG, ("shared", 0.2), ("shared", 0.7), ("shared", 0.1)])
+    cases["T1N1_lkt"] = ([[("AMP", (2,)), ("EXP", (3,)), ("TFCOS", (4, 5))], [("AMP", (6,)), ("LKT", (7,))]],
+                         [N0, BKG, ("hist", 0.2), ("shared", 0.4), ("shared", 1.5), ("hist", 30.0),
+                          ("shared", 0.05), ("shared", 0.9)])
+    cases["T2N1m_lkt"] = ([[("AMP", (2,)), ("EXP", (3,)), ("TFCOS", (4, 5))],
+                           [("AMP", (6,)), ("GAUSS", (7,)), ("TFCOS", (8, 5))],
+                           [("AMP", (9,)), ("LKT", (10,))]],
+                          [N0, BKG, ("const", 0.12), ("shared", 0.5), ("shared", 1.2), ("hist", 20.0),
+                           ("const", 0.1), ("shared", 0.3), ("shared", 1.7), ("const", 0.05), ("shared", 0.6)])
+    cases["generic_lkt"] = ([[("AMP", (2,)), ("LKT", (3,))], [("AMP", (4,)), ("KT", (5,))],
+                             [("AMP", (6,)), ("EXP", (7,))]],
+                            [N0, BKG, ("shared", 0.1), ("shared", 0.8), ("shared", 0.08), ("shared", 0.4),
+                             ("hist", 0.05), ("shared", 0.3)])
     # three cosine terms (generic)
     cases["generic_T3"] = ([[("AMP", (2,)), ("EXP", (3,)), ("TFCOS", (4, 5))],
                             [("AMP", (6,)), ("GAUSS", (7,)), ("TFCOS", (8, 5))],
