@@ -1,0 +1,83 @@
+"""Host-only logic of the library, on the CPU: the BFGS state machine behind musr_fit and
+the serving loop (musr_bfgs.h), the planning of the SPLIT kernels (musr_plan.h: canonical
+terms, shape, merging, slot contributions) and the decomposition cost model (musr_dev.h).
+tests/host_logic.cpp drives the headers; g++ builds it with the CUDA vector types only."""
+import json
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "tests", "host_logic.cpp")
+EXE = os.path.join(ROOT, "tests", "_build", "host_logic")  # git-ignored
+CSRC = os.path.join(ROOT, "paper_1509_07685_gb300", "csrc")
+
+# SPLIT shapes and term kinds as numbered in musr_dev.h
+SHAPE = {"generic": 0, "T1": 1, "N1": 2, "T1N1": 3, "T2": 4, "T2N1": 5, "T2m": 6, "T2N1m": 7}
+TERM = {"plain": 1, "tf": 2, "kt": 3, "lkt": 4}
+C_AMP, C_PHI, C_DEL, C_LKT = 2, 3, 7, 8
+
+
+def _cuda_include():
+    for d in ("/usr/local/cuda/include", os.path.join(os.environ.get("CUDA_HOME", ""), "include")):
+        if os.path.exists(os.path.join(d, "vector_types.h")):
+            return d
+    pytest.skip("CUDA headers not found")
+
+
+@pytest.fixture(scope="module")
+def run():
+    deps = [SRC] + [os.path.join(CSRC, f) for f in ("musr_bfgs.h", "musr_plan.h", "musr_dev.h")] + \
+        [os.path.join(ROOT, "include", "musr.h")]
+    if not os.path.exists(EXE) or os.path.getmtime(EXE) < max(os.path.getmtime(d) for d in deps):
+        os.makedirs(os.path.dirname(EXE), exist_ok=True)
+        subprocess.check_call(["g++", "-std=c++17", "-O1", "-Wall", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
+                               "-I", _cuda_include(), "-o", EXE, SRC])
+
+    def _run(what):
+        out = subprocess.run([EXE, what], capture_output=True, text=True, check=True).stdout
+        return {d["name"] if d["name"] != "pick" else d["nvec"]: d for d in map(json.loads, out.splitlines())}
+    return _run
+
+
+def test_bfgs_state_machine_minimises(run):
+    r = run("bfgs")
+    q = r["quadratic"]
+    assert q["status"] == 0
+    assert np.allclose(q["x"], [1.5, -2.0, 0.25, 3.0], atol=1e-6)
+    # the start point, then the P points of the diagonal curvature estimate, then single trials
+    assert q["first_requests"][:3] == [1, 4, 1]
+    rb = r["rosenbrock"]
+    assert rb["status"] == 0 and np.allclose(rb["x"], [1.0, 1.0], atol=1e-6) and rb["f"] < 1e-12
+    nf = r["nonfinite"]
+    assert nf["status"] == 1 and nf["nfev"] == 1
+
+
+def test_split_planning(run):
+    r = run("plan")
+    m = r["tf2_merged"]
+    assert m["ok"] and m["shape"] == SHAPE["T2m"] and m["merged"] == 1
+    assert m["bamp"] == pytest.approx([0.125, 0.1], rel=1e-7)
+    kinds = [c[1] for c in m["contrib"]]
+    assert kinds.count(C_PHI) == 1 and C_AMP not in kinds  # one shared phase, constant amplitudes
+    for name in ("tf2_own_phases", "tf2_amp_per_hist"):
+        assert r[name]["shape"] == SHAPE["T2"] and r[name]["merged"] == 0
+    assert [c[1] for c in r["tf2_own_phases"]["contrib"]].count(C_PHI) == 2
+    k = r["kt_then_tf"]  # the cosine term moves first
+    assert k["shape"] == SHAPE["T1N1"] and k["kinds"] == [TERM["tf"], TERM["kt"]]
+    assert [3, C_DEL, 1] in k["contrib"]
+    lk = r["lkt"]
+    assert lk["shape"] == SHAPE["N1"] and lk["kinds"] == [TERM["lkt"]] and [3, C_LKT, 0] in lk["contrib"]
+    assert not r["two_cosines"]["ok"]
+    g = r["generic4"]
+    assert g["shape"] == SHAPE["generic"] and g["kinds"] == [TERM["tf"], TERM["plain"], TERM["plain"], TERM["kt"]]
+
+
+def test_decomposition_cost_model(run):
+    r = run("pick")
+    for nvec, d in r.items():
+        costs = d["costs"]
+        assert d["v"] == int(np.argmin(costs))  # the first (smallest-tile) minimum
+    assert r[1]["v"] == 0 and r[8]["v"] == 2 and r[64]["v"] == 5
