@@ -482,7 +482,9 @@ def _serving(B, n_requests, window=1024, seed=4):
                          "gbins_per_s": st["bin_evals"] / sat_s / 1e9, "steps": st["steps"],
                          "launches": st["launches"], "evals": st["evals"],
                          "worker_s": {"busy": st["busy_s"], "minimizer": st["minimizer_s"],
-                                      "admit": st["admit_s"], "device_wait": st["wait_s"]}}
+                                      "admit": st["admit_s"], "device_wait": st["wait_s"]},
+                         "configure_thread_s": {"context": st["cfg_create_s"], "upload": st["cfg_upload_s"],
+                                                "plan": st["cfg_plan_s"], "buffers": st["cfg_buffers_s"]}}
     for frac in (0.5, 0.9):
         reqs = mi.request_stream(pool, n_requests, frac * rate, seed=seed + 10)
         with B.Server(hbm_budget_bytes=8 << 30, max_active=1024) as srv:

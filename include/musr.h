@@ -105,7 +105,10 @@ const char* musr_last_error(const musr_ctx* ctx);
  * FP32; |count| must be < 2^24 so the copy is exact), MUSR_DTYPE_FP32 or
  * MUSR_DTYPE_FP64 (stored as FP64).  t0[nhist] is the time-zero bin of each
  * histogram (may be fractional), bin_width_ns > 0, fit_range_us = {lo, hi}.
- * Replaces any previous histograms; theory and map must be (re)set after. */
+ * Replaces any previous histograms; theory and map must be (re)set after.
+ * The rows are copied as they are and checked on the device (a count that is
+ * not finite, or an INT32 count beyond 2^24, gives MUSR_EINVAL and no
+ * histograms).  Synchronous: the caller may reuse `counts` when it returns. */
 int musr_upload_histograms(musr_ctx* ctx, const void* counts, int dtype, int nhist, int64_t nbins,
                            const double* t0, double bin_width_ns, const double fit_range_us[2]);
 
@@ -223,7 +226,11 @@ typedef struct musr_server musr_server;
 
 /* One fit: the arguments of musr_upload_histograms, musr_set_theory and
  * musr_set_map, a start point, and the fit settings.  All arrays are host
- * memory, copied by musr_server_submit. */
+ * memory, copied by musr_server_submit -- except the counts when flags holds
+ * MUSR_REQ_BORROW_COUNTS: then the server reads them when it admits the fit,
+ * and the caller keeps them valid and unchanged until the fit's result has
+ * been taken (musr_server_poll / musr_server_wait) or the server destroyed. */
+#define MUSR_REQ_BORROW_COUNTS 1
 typedef struct musr_fit_request {
   const void* counts;
   int32_t dtype;
@@ -243,7 +250,7 @@ typedef struct musr_fit_request {
   int32_t mode;
   int32_t precision;
   int32_t maxit; /* <= 0: 1000 */
-  int32_t pad;
+  int32_t flags; /* 0 or MUSR_REQ_BORROW_COUNTS */
   double gtol;   /* <= 0: 1e-8 */
 } musr_fit_request;
 
@@ -258,6 +265,11 @@ typedef struct musr_server_stats {
   double minimizer_s; /* worker time in the fits' minimiser steps (trial points, updates) */
   double admit_s;     /* worker time admitting fits (contexts, uploads), overlapped with the device */
   double wait_s;      /* worker time waiting for the device */
+  /* time configuring admitted fits, summed over the threads that did it: the context,
+   * the histogram upload (enqueueing its copy and device check), theory + map +
+   * planning, and the device tables and evaluation buffers with the wait for all of
+   * the fit's setup work on the device */
+  double cfg_create_s, cfg_upload_s, cfg_plan_s, cfg_buffers_s;
 } musr_server_stats;
 
 /* Starts a server on `device` with a device memory budget of hbm_budget_bytes

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(PKG, "libmusr.so")
 MUSR_OK, MUSR_EINVAL, MUSR_ENOMEM, MUSR_ECUDA = 0, -1, -2, -3
 MUSR_ENONFINITE, MUSR_ETIMEOUT, MUSR_ESTATE, MUSR_EAGAIN = -4, -5, -6, -7
 MUSR_DTYPE_INT32, MUSR_DTYPE_FP32, MUSR_DTYPE_FP64 = 0, 1, 2
+MUSR_REQ_BORROW_COUNTS = 1  # musr_fit_request.flags: the server reads the caller's counts at admission
 MUSR_CHI2, MUSR_MLE = 0, 1
 MUSR_FP64, MUSR_SPLIT = 0, 1
 PRIM = {"AMP": 1, "EXP": 2, "GAUSS": 3, "KT": 4, "TFCOS": 5, "LKT": 6}
@@ -62,7 +63,7 @@ class musr_fit_request(ctypes.Structure):
                 ("map", ctypes.POINTER(ctypes.c_int32)), ("nparams", ctypes.c_int32),
                 ("nconsts", ctypes.c_int32), ("consts", ctypes.POINTER(ctypes.c_double)),
                 ("x0", ctypes.POINTER(ctypes.c_double)), ("mode", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("maxit", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("maxit", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("gtol", ctypes.c_double)]
 
 
@@ -72,7 +73,9 @@ class musr_server_stats(ctypes.Structure):
                 ("active", ctypes.c_int64), ("queued", ctypes.c_int64), ("bin_evals", ctypes.c_double),
                 ("busy_s", ctypes.c_double), ("clock_s", ctypes.c_double), ("arena_bytes", ctypes.c_uint64),
                 ("arena_used", ctypes.c_uint64), ("minimizer_s", ctypes.c_double), ("admit_s", ctypes.c_double),
-                ("wait_s", ctypes.c_double)]
+                ("wait_s", ctypes.c_double), ("cfg_create_s", ctypes.c_double),
+                ("cfg_upload_s", ctypes.c_double), ("cfg_plan_s", ctypes.c_double),
+                ("cfg_buffers_s", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -405,9 +408,10 @@ def musr_server_destroy(srv) -> None:
     load().musr_server_destroy(srv)
 
 
-def make_request(problem, x0, mode: int, precision: int, maxit: int = 0, gtol: float = 0.0):
-    """A musr_fit_request for a problem; returns (request, keepalive) -- the arrays must live
-    until musr_server_submit returns (it copies them)."""
+def make_request(problem, x0, mode: int, precision: int, maxit: int = 0, gtol: float = 0.0, borrow: bool = False):
+    """A musr_fit_request for a problem; returns (request, keepalive).  The arrays must live
+    until musr_server_submit returns (it copies them); with borrow the counts are lent to
+    the server (MUSR_REQ_BORROW_COUNTS) and must live, unchanged, until the result is taken."""
     counts = np.ascontiguousarray(problem.counts)
     dtype = {np.dtype(np.int32): MUSR_DTYPE_INT32, np.dtype(np.float32): MUSR_DTYPE_FP32,
              np.dtype(np.float64): MUSR_DTYPE_FP64}[counts.dtype]
@@ -432,17 +436,20 @@ def make_request(problem, x0, mode: int, precision: int, maxit: int = 0, gtol: f
     q.consts = _dptr(consts)
     q.x0 = _dptr(x0)
     q.mode, q.precision, q.maxit, q.gtol = mode, precision, maxit, gtol
+    q.flags = MUSR_REQ_BORROW_COUNTS if borrow else 0
     return q, (counts, t0, terms, mp, consts, x0)
 
 
-def musr_server_submit(srv, problem, x0, mode: int, precision: int, maxit: int = 0, gtol: float = 0.0) -> int:
-    q, keep = make_request(problem, x0, mode, precision, maxit, gtol)
+def musr_server_submit(srv, problem, x0, mode: int, precision: int, maxit: int = 0, gtol: float = 0.0,
+                       borrow: bool = False):
+    """Submits one fit; returns (id, lent) -- lent is the counts array the server borrowed
+    (None without borrow), which the caller keeps until the result is taken."""
+    q, keep = make_request(problem, x0, mode, precision, maxit, gtol, borrow)
     fid = ctypes.c_int64()
     st = load().musr_server_submit(srv, ctypes.byref(q), ctypes.byref(fid))
-    del keep
     if st != MUSR_OK:
         raise MusrError(st, "musr_server_submit rejected the request")
-    return fid.value
+    return fid.value, (keep[0] if borrow else None)
 
 
 def musr_server_poll(srv, fid: int, nparams: int):
@@ -476,27 +483,34 @@ def musr_server_stats_get(srv) -> dict:
 
 
 class Server:
-    """Owns one musr_server (continuous batching of many fits)."""
+    """Owns one musr_server (continuous batching of many fits).  submit lends each fit's
+    counts to the server (no copy) and keeps the array referenced until the result has been
+    taken; the caller must not modify it meanwhile (borrow=False copies instead)."""
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 8 << 30, max_active: int = 1024):
         self.srv = musr_server_create(device, hbm_budget_bytes, max_active)
         self.nparams = {}
+        self.lent = {}
 
-    def submit(self, problem, x0, mode=MUSR_MLE, precision=MUSR_SPLIT, maxit=0, gtol=0.0) -> int:
-        fid = musr_server_submit(self.srv, problem, x0, mode, precision, maxit, gtol)
+    def submit(self, problem, x0, mode=MUSR_MLE, precision=MUSR_SPLIT, maxit=0, gtol=0.0, borrow=True) -> int:
+        fid, lent = musr_server_submit(self.srv, problem, x0, mode, precision, maxit, gtol, borrow)
         self.nparams[fid] = int(problem.nparams)
+        if lent is not None:
+            self.lent[fid] = lent
         return fid
 
     def poll(self, fid: int):
         r = musr_server_poll(self.srv, fid, self.nparams[fid])
         if r is not None:
             self.nparams.pop(fid, None)
+            self.lent.pop(fid, None)
         return r
 
     def wait(self, fid: int, timeout_ms: int = 0):
         r = musr_server_wait(self.srv, fid, self.nparams[fid], timeout_ms)
         if r is not None:
             self.nparams.pop(fid, None)
+            self.lent.pop(fid, None)
         return r
 
     def stats(self) -> dict:

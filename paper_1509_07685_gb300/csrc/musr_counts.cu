@@ -1,0 +1,73 @@
+// musr_counts.cu -- the device image of uploaded histograms (the measured counts d_n^j of
+// Eq. chi2 and Eq. mlh, Section 4.1): the rows arrive from the host as they are, one row
+// per histogram at the device row stride; this kernel converts them in place to the stored
+// type, zeroes each row's padding and flags values the store cannot hold, so the host makes
+// one copy and no pass over the data.
+#include <cstdint>
+
+#include "musr.h"
+#include "musr_dev.h"
+
+namespace musr {
+namespace {
+
+// One thread per element of [H][stride], grid-stride.  INT32 counts become FP32 (exact
+// below 2^24); FP32 and FP64 are checked for finiteness.  A bad element writes seq to
+// *flag (host-mapped memory), which the host compares after the stream has finished.
+template <int DTYPE>
+__global__ void __launch_bounds__(256) prepare_counts_kernel(void* buf, int64_t nbins, int64_t stride,
+                                                             int64_t total, unsigned* flag, unsigned seq) {
+  bool bad = false;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const bool pad = e % stride >= nbins;
+    if (DTYPE == MUSR_DTYPE_INT32) {
+      int32_t* p = static_cast<int32_t*>(buf) + e;
+      const int32_t v = pad ? 0 : *p;
+      bad |= v >= (1 << 24) || v <= -(1 << 24);
+      *reinterpret_cast<float*>(p) = static_cast<float>(v);
+    } else if (DTYPE == MUSR_DTYPE_FP32) {
+      float* p = static_cast<float*>(buf) + e;
+      if (pad) {
+        *p = 0.0f;
+      } else {
+        const float v = *p;
+        bad |= !(fabsf(v) <= 3.4028234663852886e38f);
+      }
+    } else {
+      double* p = static_cast<double*>(buf) + e;
+      if (pad) {
+        *p = 0.0;
+      } else {
+        const double v = *p;
+        bad |= !(fabs(v) <= 1.7976931348623157e308);
+      }
+    }
+  }
+  if (bad) *reinterpret_cast<volatile unsigned*>(flag) = seq;
+}
+
+}  // namespace
+
+int launch_prepare_counts(void* buf, int dtype, int nhist, int64_t nbins, int64_t stride, unsigned* flag,
+                          unsigned seq, int num_sms, void* stream_) {
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const int64_t total = static_cast<int64_t>(nhist) * stride;
+  if (total <= 0) return 0;
+  const int64_t want = (total + 255) / 256;
+  const int grid = static_cast<int>(want < 8LL * num_sms ? want : 8LL * num_sms);
+  switch (dtype) {
+    case MUSR_DTYPE_INT32:
+      prepare_counts_kernel<MUSR_DTYPE_INT32><<<grid, 256, 0, stream>>>(buf, nbins, stride, total, flag, seq);
+      break;
+    case MUSR_DTYPE_FP32:
+      prepare_counts_kernel<MUSR_DTYPE_FP32><<<grid, 256, 0, stream>>>(buf, nbins, stride, total, flag, seq);
+      break;
+    default:
+      prepare_counts_kernel<MUSR_DTYPE_FP64><<<grid, 256, 0, stream>>>(buf, nbins, stride, total, flag, seq);
+      break;
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace musr

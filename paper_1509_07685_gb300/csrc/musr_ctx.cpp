@@ -154,29 +154,34 @@ cudaError_t copy_h2d(void* dst, const void* src, size_t bytes) {
   return e == cudaSuccess ? cudaStreamSynchronize(cudaStreamPerThread) : e;
 }
 
-// A pinned host buffer per thread, reused across uploads (grows, freed at thread exit).
-struct PinnedScratch {
-  void* p = nullptr;
-  size_t cap = 0;
-  ~PinnedScratch() {
-    if (p) cudaFreeHost(p);
+// A host-mapped word per thread that device-side checks of an upload write to: each check
+// gets a new sequence number, so a word left from an earlier upload never matches.
+struct CheckFlag {
+  unsigned* host = nullptr;
+  unsigned* dev = nullptr;
+  unsigned seq = 0;
+  ~CheckFlag() {
+    if (host) cudaFreeHost(host);
   }
-  void* get(size_t bytes) {
-    if (bytes <= cap) return p;
-    if (p) cudaFreeHost(p);
-    p = nullptr;
-    cap = 0;
-    const size_t want = std::max(bytes + bytes / 2, size_t(1) << 20);
-    if (cudaHostAlloc(&p, want, cudaHostAllocDefault) != cudaSuccess) {
-      cudaGetLastError();
-      p = nullptr;
-      return nullptr;
+  bool ready() {
+    if (host) return true;
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, 64, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) return false;
+    host = static_cast<unsigned*>(p);
+    *host = 0;
+    void* d = nullptr;
+    if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess) {
+      cudaFreeHost(p);
+      host = nullptr;
+      return false;
     }
-    cap = want;
-    return p;
+    dev = static_cast<unsigned*>(d);
+    return true;
   }
+  unsigned next() { return ++seq == 0 ? ++seq : seq; }
+  bool raised(unsigned s) const { return *static_cast<volatile unsigned*>(host) == s; }
 };
-thread_local PinnedScratch tl_pinned;
+thread_local CheckFlag tl_flag;
 
 int upload(musr_ctx* ctx, DevBuf& b, const void* src, size_t bytes) {
   int rc = dalloc(ctx, b, bytes);
@@ -223,6 +228,7 @@ void fit_bins(double t0, double dt_us, int64_t B, double lo, double hi, int* nlo
 
 void free_compiled(musr_ctx* ctx, Compiled& c) {
   dfree(ctx, c.tables);
+  std::vector<char>().swap(c.blob);
   c.d_hs = nullptr;
   c.uploaded = false;
   c.chunks.clear();
@@ -250,10 +256,8 @@ int compile(musr_ctx* ctx, int prec, int var) {
   hs.stride = ctx->stride;
   hs.dt_us = ctx->dt_us;
   hs.nterms = static_cast<int>(ctx->terms.size());
-  hs.map = static_cast<const int32_t*>(ctx->d_map.p);
   hs.nslots = ctx->nslots;
-  hs.consts = static_cast<const double*>(ctx->d_consts.p);
-  hs.P = ctx->P;
+  hs.P = ctx->P;  // map and consts: device copies in the tables (ensure_uploaded)
   for (int k = 0; k < hs.nterms; ++k) {
     const musr_term& t = ctx->terms[k];
     hs.raw[k].nprim = t.nprim;
@@ -395,8 +399,9 @@ int ensure_compiled(musr_ctx* ctx, int prec, int var) {
   return ctx->comp[prec][var].planned ? MUSR_OK : compile(ctx, prec, var);
 }
 
-// Copies one decomposition's tables to the device (first use only): one
-// allocation holding the HistSet and every table, one copy.
+// Copies one decomposition's tables to the device (first use only): one allocation
+// holding the HistSet, every table and the parameter map and constants, one copy,
+// enqueued on the context's stream ahead of the launches that read it.
 int ensure_uploaded(musr_ctx* ctx, int prec, int var) {
   Compiled& c = ctx->comp[prec][var];
   if (c.uploaded) return MUSR_OK;
@@ -408,6 +413,7 @@ int ensure_uploaded(musr_ctx* ctx, int prec, int var) {
     off += (bytes + 255) & ~size_t(255);
     return o;
   };
+  const size_t nconsts = std::max<size_t>(ctx->consts.size(), 1);
   const size_t o_hs = place(sizeof(HistSet));
   const size_t o_ch = place(sizeof(Chunk) * c.chunks.size());
   const size_t o_it = place(sizeof(int2) * c.items.size());
@@ -415,6 +421,8 @@ int ensure_uploaded(musr_ctx* ctx, int prec, int var) {
   const size_t o_cc = place(sizeof(int) * c.col_chunk.size());
   const size_t o_pp = place(sizeof(int) * c.p_ptr.size());
   const size_t o_pc = place(sizeof(int) * c.p_cols.size());
+  const size_t o_mp = place(sizeof(int32_t) * ctx->map.size());
+  const size_t o_cs = place(sizeof(double) * nconsts);
   int rc = dalloc(ctx, c.tables, off);
   if (rc) return rc;
   char* base = static_cast<char*>(c.tables.p);
@@ -425,7 +433,10 @@ int ensure_uploaded(musr_ctx* ctx, int prec, int var) {
   hs.col_chunk = reinterpret_cast<const int*>(base + o_cc);
   hs.p_ptr = reinterpret_cast<const int*>(base + o_pp);
   hs.p_cols = reinterpret_cast<const int*>(base + o_pc);
-  std::vector<char> blob(off, 0);
+  hs.map = reinterpret_cast<const int32_t*>(base + o_mp);
+  hs.consts = reinterpret_cast<const double*>(base + o_cs);
+  std::vector<char>& blob = c.blob;  // kept until the tables are freed: the copy's source
+  blob.assign(off, 0);
   std::memcpy(blob.data() + o_hs, &hs, sizeof(hs));
   std::memcpy(blob.data() + o_ch, c.chunks.data(), sizeof(Chunk) * c.chunks.size());
   std::memcpy(blob.data() + o_it, c.items.data(), sizeof(int2) * c.items.size());
@@ -433,7 +444,10 @@ int ensure_uploaded(musr_ctx* ctx, int prec, int var) {
   std::memcpy(blob.data() + o_cc, c.col_chunk.data(), sizeof(int) * c.col_chunk.size());
   std::memcpy(blob.data() + o_pp, c.p_ptr.data(), sizeof(int) * c.p_ptr.size());
   std::memcpy(blob.data() + o_pc, c.p_cols.data(), sizeof(int) * c.p_cols.size());
-  cudaError_t e = copy_h2d(base, blob.data(), off);
+  std::memcpy(blob.data() + o_mp, ctx->map.data(), sizeof(int32_t) * ctx->map.size());
+  if (!ctx->consts.empty()) std::memcpy(blob.data() + o_cs, ctx->consts.data(), sizeof(double) * ctx->consts.size());
+  cudaError_t e = cudaMemcpyAsync(base, blob.data(), off, cudaMemcpyHostToDevice,
+                                  ctx->setup_stream ? ctx->setup_stream : ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(tables)");
   c.d_hs = reinterpret_cast<const HistSet*>(base + o_hs);
   c.uploaded = true;
@@ -470,7 +484,7 @@ int ensure_eval(musr_ctx* ctx, int prec, int var, int nvec) {
     if (r) return r;
     ev.key_valid = false;
     if (zero) {
-      cudaError_t e = cudaMemsetAsync(b.p, 0, b.bytes, ctx->stream);
+      cudaError_t e = cudaMemsetAsync(b.p, 0, b.bytes, ctx->setup_stream ? ctx->setup_stream : ctx->stream);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
     }
     return MUSR_OK;
@@ -655,12 +669,10 @@ int musr_ctx_create(musr_ctx** out, int device, size_t hbm_budget_bytes, void* c
 void musr_ctx_destroy(musr_ctx* ctx) {
   if (!ctx) return;
   DeviceScope ds(ctx->device);
-  cudaStreamSynchronize(ctx->stream);
+  if (!ctx->owner_waited) cudaStreamSynchronize(ctx->stream);
   for (auto& pc : ctx->comp)
     for (auto& c : pc) free_compiled(ctx, c);
   dfree(ctx, ctx->counts_own);
-  dfree(ctx, ctx->d_map);
-  dfree(ctx, ctx->d_consts);
   EvalBufs& ev = ctx->ev;
   dfree(ctx, ev.params);
   dfree(ctx, ev.out);
@@ -691,6 +703,7 @@ static int upload_common(musr_ctx* ctx, int nhist, int64_t nbins, const double* 
     return fail(ctx, MUSR_EINVAL, "fit range must be finite with lo <= hi");
   for (int h = 0; h < nhist; ++h)
     if (!std::isfinite(t0[h])) return fail(ctx, MUSR_EINVAL, "t0 must be finite");
+  ctx->check_flag = nullptr;
   ctx->H = nhist;
   ctx->B = nbins;
   ctx->t0.assign(t0, t0 + nhist);
@@ -734,60 +747,51 @@ int musr_upload_histograms(musr_ctx* ctx, const void* counts, int dtype, int nhi
   const int64_t stride = (nbins + kRowAlign - 1) / kRowAlign * kRowAlign;
   const size_t esz = dtype == MUSR_DTYPE_FP64 ? 8 : 4;
   const size_t total = static_cast<size_t>(nhist) * stride * esz;
-  // The device image of the counts (row stride, zero padding, INT32 converted to FP32) is
-  // built in one pass with the checks (branch-free loops the compiler vectorises), in a
-  // pinned buffer of this thread that is reused, then copied in one transfer.
-  const size_t n_row = static_cast<size_t>(nbins), s_row = static_cast<size_t>(stride);
-  std::vector<unsigned char> pageable;
-  void* img = total <= (size_t(64) << 20) ? tl_pinned.get(total) : nullptr;
-  if (!img) {
-    pageable.resize(total);
-    img = pageable.data();
-  }
-  int bad = 0;
-  for (int h = 0; h < nhist; ++h) {
-    if (dtype == MUSR_DTYPE_INT32) {
-      const int32_t* ci = static_cast<const int32_t*>(counts) + h * n_row;
-      float* d = static_cast<float*>(img) + h * s_row;
-      for (size_t i = 0; i < n_row; ++i) {
-        const int32_t v = ci[i];
-        bad |= static_cast<int>(v >= (1 << 24)) | static_cast<int>(v <= -(1 << 24));
-        d[i] = static_cast<float>(v);
-      }
-      for (size_t i = n_row; i < s_row; ++i) d[i] = 0.0f;
-    } else if (dtype == MUSR_DTYPE_FP32) {
-      const float* cf = static_cast<const float*>(counts) + h * n_row;
-      float* d = static_cast<float*>(img) + h * s_row;
-      for (size_t i = 0; i < n_row; ++i) {
-        const float v = cf[i];
-        bad |= static_cast<int>(!(std::fabs(v) <= 3.4028234663852886e38f));
-        d[i] = v;
-      }
-      for (size_t i = n_row; i < s_row; ++i) d[i] = 0.0f;
-    } else {
-      const double* cd = static_cast<const double*>(counts) + h * n_row;
-      double* d = static_cast<double*>(img) + h * s_row;
-      for (size_t i = 0; i < n_row; ++i) {
-        const double v = cd[i];
-        bad |= static_cast<int>(!(std::fabs(v) <= 1.7976931348623157e308));
-        d[i] = v;
-      }
-      for (size_t i = n_row; i < s_row; ++i) d[i] = 0.0;
-    }
-  }
-  if (bad)
-    return fail(ctx, MUSR_EINVAL,
-                dtype == MUSR_DTYPE_INT32 ? "INT32 counts must satisfy |count| < 2^24 (exact in FP32)"
-                                          : "counts must be finite");
+  // The rows go to the device as they are, at the device row stride, in one copy; a kernel
+  // then converts INT32 to FP32 in place, zeroes the padding and flags counts the store
+  // cannot hold.  The host makes no pass over the data.
   if ((rc = dalloc(ctx, ctx->counts_own, total))) return rc;
-  cudaError_t e = copy_h2d(ctx->counts_own.p, img, total);
+  cudaStream_t st = ctx->setup_stream ? ctx->setup_stream : cudaStreamPerThread;
+  const size_t row = static_cast<size_t>(nbins) * esz;
+  cudaError_t e = stride == nbins
+                      ? cudaMemcpyAsync(ctx->counts_own.p, counts, total, cudaMemcpyHostToDevice, st)
+                      : cudaMemcpy2DAsync(ctx->counts_own.p, static_cast<size_t>(stride) * esz, counts, row, row,
+                                          static_cast<size_t>(nhist), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(counts)");
+  CheckFlag& flag = tl_flag;
+  if (!flag.ready()) return cuda_fail(ctx, cudaGetLastError(), "cudaHostAlloc(check flag)");
+  const unsigned seq = flag.next();
+  if (launch_prepare_counts(ctx->counts_own.p, dtype, nhist, nbins, stride, flag.dev, seq, ctx->num_sms, st))
+    return cuda_fail(ctx, cudaGetLastError(), "prepare_counts launch");
+  ctx->check_flag = flag.host;
+  ctx->check_seq = seq;
+  ctx->check_dtype = dtype;
   ctx->d_counts = ctx->counts_own.p;
   ctx->store = dtype == MUSR_DTYPE_FP64 ? kStoreF64 : kStoreF32;
   ctx->stride = stride;
   ctx->have_hist = true;
-  return MUSR_OK;
+  if (ctx->setup_stream) return MUSR_OK;  // the caller waits and reads the check
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "prepare_counts");
+  return finish_upload_check(ctx);
 }
+
+}  // extern "C"
+
+int musr::finish_upload_check(musr_ctx* ctx) {
+  if (!ctx->check_flag) return MUSR_OK;
+  const bool bad = *static_cast<const volatile unsigned*>(ctx->check_flag) == ctx->check_seq;
+  ctx->check_flag = nullptr;
+  if (!bad) return MUSR_OK;
+  drop_config(ctx);
+  dfree(ctx, ctx->counts_own);
+  ctx->d_counts = nullptr;
+  return fail(ctx, MUSR_EINVAL,
+              ctx->check_dtype == MUSR_DTYPE_INT32 ? "INT32 counts must satisfy |count| < 2^24 (exact in FP32)"
+                                                   : "counts must be finite");
+}
+
+extern "C" {
 
 int musr_upload_histograms_device(musr_ctx* ctx, const void* d_counts, int dtype, int nhist, int64_t nbins,
                                   int64_t row_stride, const double* t0, double bin_width_ns,
@@ -876,11 +880,6 @@ int musr_set_map(musr_ctx* ctx, const int32_t* map, int nslots, int nparams, con
   ctx->nslots = nslots;
   ctx->P = nparams;
   ctx->consts.assign(consts, consts + nconsts);
-  std::vector<double> cpad(ctx->consts);
-  if (cpad.empty()) cpad.push_back(0.0);
-  int rc;
-  if ((rc = upload(ctx, ctx->d_map, ctx->map.data(), sizeof(int32_t) * n))) return rc;
-  if ((rc = upload(ctx, ctx->d_consts, cpad.data(), sizeof(double) * cpad.size()))) return rc;
   // Decompositions are planned when a launch first needs one; whether the SPLIT path
   // can run this theory at all is decided now.
   {

@@ -173,6 +173,11 @@ struct LaunchInfo {
 int launch_eval(int precision, int shape, int mode, int grad, const Job* d_jobs, int njobs,
                 int total_items, int num_sms, void* stream, LaunchInfo* info);
 int max_ctas_per_sm(int precision, int shape, int mode, int grad);
+// Turns raw histogram rows copied to buf ([nhist][stride], dtype as uploaded) into the
+// stored image in place: INT32 -> FP32, zero padding beyond nbins; writes seq to *flag
+// (host-mapped) if a count is not representable (|INT32| >= 2^24, non-finite float).
+int launch_prepare_counts(void* buf, int dtype, int nhist, int64_t nbins, int64_t stride, unsigned* flag,
+                          unsigned seq, int num_sms, void* stream);
 // Decompositions compiled per precision: tile v holds (bins per CTA iteration) << v
 // bins -- SPLIT 512 ... 16384 (the phase-split limit), FP64 256 ... 8192.
 constexpr int kVariants = 6;

@@ -52,7 +52,8 @@ struct Compiled {
   std::vector<int2> items;
   std::vector<int> hist_index, col_chunk, p_ptr, p_cols;
   bool uploaded = false;
-  DevBuf tables;        // HistSet + all tables, 256-byte aligned pieces
+  DevBuf tables;        // HistSet + all tables + map + consts, 256-byte aligned pieces
+  std::vector<char> blob;  // host image of `tables`, the source of their copy
   const HistSet* d_hs = nullptr;
 };
 
@@ -87,10 +88,16 @@ int upload(musr_ctx* ctx, DevBuf& b, const void* src, size_t bytes);
 void fit_bins(double t0, double dt_us, int64_t B, double lo, double hi, int* nlo, int* nhi);
 int wait_stream(musr_ctx* ctx, int timeout_ms);
 int check_ready(musr_ctx* ctx, int mode, int prec);
+// Plans one decomposition the first time a launch needs it (host work only).
+int ensure_compiled(musr_ctx* ctx, int prec, int var);
 // Evaluation buffers of a context for nvec vectors of one decomposition, and the
 // job descriptors of such a launch (written to `jobs`, items numbered from
 // item_begin).  Used by the context's own launches and by the serving loop.
 int ensure_eval(musr_ctx* ctx, int prec, int var, int nvec);
+// Reads the device check of the last histogram upload once the stream it ran on has
+// finished: MUSR_EINVAL (and no histograms) if a count was not representable.  Uploads
+// made with setup_stream set leave the check for the caller to read.
+int finish_upload_check(musr_ctx* ctx);
 void fill_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, const double* d_params,
                double* d_out, Job* jobs, int item_begin, const double* d_dirs = nullptr);
 
@@ -122,11 +129,21 @@ struct musr_ctx {
   int nslots = 0, P = 0;
   std::string split_reason;  // why the SPLIT path cannot run this theory (empty: it can)
   std::vector<double> consts;
-  musr::DevBuf d_map, d_consts;
   // [precision][decomposition]: tiles of (bins per CTA iteration) << v bins; a
   // launch picks the largest that still fills the GPU (pick_decomposition).
   musr::Compiled comp[2][musr::kVariants];
   musr::EvalBufs ev;
   int last_grid = 0;
   musr::Arena* arena = nullptr;  // when set, device memory comes from it (serving)
+  // Stream of one-time setup work (histogram copy and check, tables, zeroed buffers);
+  // null: the histogram upload waits on the calling thread's stream and the rest goes
+  // on `stream`.  The serving loop sets it while it configures a fit, then waits once.
+  cudaStream_t setup_stream = nullptr;
+  // Set by an owner that has already waited for all of this context's device work (the
+  // serving loop, which shares one stream among many contexts): destroy does not wait.
+  bool owner_waited = false;
+  // Device check of the last histogram upload, not read yet (see finish_upload_check).
+  const unsigned* check_flag = nullptr;
+  unsigned check_seq = 0;
+  int check_dtype = 0;
 };

@@ -4,16 +4,19 @@
 // sends a parameter vector, the device returns the cost.  Serving many fits at
 // once keeps every fit's histograms resident and advances all fits together:
 //
-//   worker loop, one step:
-//     admit queued fits while the arena (the HBM budget) has room -- a fit's
+//   the active fits are split into two lanes that the device evaluates in turn;
+//   worker loop, one half-step for lane L:
+//     every fit of lane L names its next trial point(s) (BFGS state machine);
+//     its points go to the device in one copy; one persistent multi-fit launch
+//       per (precision, theory shape, cost) group evaluates them all, and one copy
+//       brings every value and gradient back -- queued behind the other lane's work;
+//     queued fits are admitted while the arena (the HBM budget) has room -- a fit's
 //       histograms, decomposition tables and evaluation buffers come from it;
-//     every active fit names its next trial point(s) (BFGS state machine);
-//     all points go to the device in one copy; one persistent multi-fit launch
-//       per (precision, theory shape, cost) group evaluates them all;
-//     one copy brings every value and gradient back;
-//     each fit's minimiser advances; finished fits release their memory.
+//     the other lane's results are waited for, its fits' minimisers advance, and
+//       finished fits release their memory.
+//   So the device evaluates one lane while the host advances the other.
 //
-// Fits that arrive while others run are admitted at the next step boundary.
+// Fits that arrive while others run join the lighter lane at the next half-step.
 // A fit's result does not depend on what else is in the batch: its launches
 // use its own decomposition and its own fixed-order reductions.
 #include <cuda_runtime.h>
@@ -52,7 +55,8 @@ constexpr int kAdmitBatch = 32;  // fits configured together by the helper threa
 
 struct Request {
   int64_t id = 0;
-  std::vector<unsigned char> counts;
+  std::vector<unsigned char> counts_copy;  // empty when the caller lends the counts
+  const void* counts = nullptr;            // counts_copy.data() or the caller's buffer
   int dtype = 0, H = 0, nslots = 0, P = 0, mode = 0, prec = 0, maxit = 0;
   int64_t B = 0;
   std::vector<double> t0, consts, x0;
@@ -66,7 +70,9 @@ struct Active {
   musr_ctx* ctx = nullptr;
   Bfgs bfgs;
   int shape = 0;
+  int lane = 0;
   int64_t bins = 0;
+  double load = 0.0;  // device work of one evaluation, (histogram, bin) pairs x (1 + P)
   double t_admit = 0.0;
   bool first = true;
   int nvec = 0;
@@ -153,6 +159,24 @@ struct Done {
 size_t dtype_size(int dtype) { return dtype == MUSR_DTYPE_FP64 ? 8 : 4; }
 
 }  // namespace
+
+// One of the two groups of active fits that the device evaluates in turn: its launch
+// buffers (host pinned and device) and the event that marks its results on the host.
+struct Lane {
+  std::vector<Active*> launched;  // fits whose points are on the device
+  double* h_params = nullptr;
+  double* h_out = nullptr;
+  Job* h_jobs = nullptr;
+  size_t hp_cap = 0, ho_cap = 0, hj_cap = 0;
+  void* d_params = nullptr;
+  void* d_out = nullptr;
+  void* d_jobs = nullptr;
+  size_t dp_cap = 0, do_cap = 0, dj_cap = 0;
+  cudaEvent_t done = nullptr;
+  bool in_flight = false;
+  double load = 0.0;  // sum of its fits' Active::load
+};
+
 }  // namespace musr
 
 using namespace musr;
@@ -177,14 +201,8 @@ struct musr_server {
   std::string err;
   // worker-owned
   std::vector<std::unique_ptr<Active>> active;
-  double* h_params = nullptr;
-  double* h_out = nullptr;
-  Job* h_jobs = nullptr;
-  size_t hp_cap = 0, ho_cap = 0, hj_cap = 0;
-  void* d_params = nullptr;
-  void* d_out = nullptr;
-  void* d_jobs = nullptr;
-  size_t dp_cap = 0, do_cap = 0, dj_cap = 0;
+  musr::Lane lanes[2];
+  int next_lane = 0;
   std::string worker_error;
 
   double now() const {
@@ -193,6 +211,15 @@ struct musr_server {
 };
 
 namespace {
+
+// Destroys a served fit's context.  Callers guarantee that none of its device work is
+// pending (its lane's results were waited for, or it never launched and its setup was
+// waited for), so the shared stream -- busy with the other lane -- is not waited on.
+void release(musr_ctx* ctx) {
+  if (!ctx) return;
+  ctx->owner_waited = true;
+  musr_ctx_destroy(ctx);
+}
 
 bool grow_host(void** p, size_t* cap, size_t bytes) {
   if (*cap >= bytes) return true;
@@ -228,7 +255,7 @@ void finish(musr_server* s, Active* a, int status) {
   d.res.t_admit = a->t_admit;
   d.res.t_done = s->now();
   d.x = a->bfgs.x();
-  if (a->ctx) musr_ctx_destroy(a->ctx);
+  release(a->ctx);
   a->ctx = nullptr;
   std::lock_guard<std::mutex> lock(s->mu);
   s->done[a->req->id] = std::move(d);
@@ -254,19 +281,40 @@ void reject(musr_server* s, std::unique_ptr<Request> r, int status) {
 // Configures a context for the request inside the arena; MUSR_ENOMEM when the
 // arena is full now, another status when the request can never run.
 int configure(musr_server* s, const Request& r, musr_ctx** out) {
+  double t[5];
+  t[0] = s->now();
   musr_ctx* ctx = nullptr;
   int rc = musr_ctx_create(&ctx, s->device, 0, s->stream);
   if (rc) return rc;
   ctx->arena = &s->arena;
-  rc = musr_upload_histograms(ctx, r.counts.data(), r.dtype, r.H, r.B, r.t0.data(), r.bw, r.fr);
+  // Every setup copy and kernel of this fit goes on this thread's stream, waited for
+  // once at the end (the serving stream keeps running the current step meanwhile).
+  ctx->setup_stream = cudaStreamPerThread;
+  t[1] = s->now();
+  rc = musr_upload_histograms(ctx, r.counts, r.dtype, r.H, r.B, r.t0.data(), r.bw, r.fr);
+  t[2] = s->now();
   if (!rc) rc = musr_set_theory(ctx, r.terms.data(), static_cast<int>(r.terms.size()));
   if (!rc)
     rc = musr_set_map(ctx, r.map.data(), r.nslots, r.P, r.consts.empty() ? nullptr : r.consts.data(),
                       static_cast<int>(r.consts.size()));
   if (!rc) rc = check_ready(ctx, r.mode, r.prec);
+  if (!rc) rc = ensure_compiled(ctx, r.prec, kServeVariant);
+  t[3] = s->now();
   if (!rc) rc = ensure_eval(ctx, r.prec, kServeVariant, r.P > 0 ? r.P : 1);
+  // wait even after a failure: nothing may still write to memory the context gives back
+  const cudaError_t e = cudaStreamSynchronize(cudaStreamPerThread);
+  if (!rc) rc = e == cudaSuccess ? finish_upload_check(ctx) : cuda_fail(ctx, e, "fit setup");
+  ctx->setup_stream = nullptr;
+  t[4] = s->now();
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stats.cfg_create_s += t[1] - t[0];
+    s->stats.cfg_upload_s += t[2] - t[1];
+    s->stats.cfg_plan_s += t[3] - t[2];
+    s->stats.cfg_buffers_s += t[4] - t[3];
+  }
   if (rc) {
-    musr_ctx_destroy(ctx);
+    release(ctx);
     return rc;
   }
   *out = ctx;
@@ -279,8 +327,14 @@ void activate(musr_server* s, std::unique_ptr<Request> r, musr_ctx* ctx) {
   a->ctx = ctx;
   a->shape = ctx->comp[r->prec][kServeVariant].hs.shape;
   musr_bins_in_fit(ctx, &a->bins);
+  a->load = static_cast<double>(a->bins) * (1 + r->P);
+  a->lane = s->lanes[0].load <= s->lanes[1].load ? 0 : 1;
+  s->lanes[a->lane].load += a->load;
   a->t_admit = s->now();
   a->bfgs.start(r->x0.data(), r->P, r->gtol, r->maxit, 0.0, r->prec == MUSR_SPLIT ? kSplitEdm : kFp64Edm);
+  // the counts are on the device now: drop the host copy (or forget the caller's buffer)
+  std::vector<unsigned char>().swap(r->counts_copy);
+  r->counts = nullptr;
   a->req = std::move(r);
   std::lock_guard<std::mutex> lock(s->mu);
   s->stats.active += 1;
@@ -335,7 +389,7 @@ void admit(musr_server* s, bool during_step = false) {
         // head of the queue in order (their memory released); retry one at a time.
         std::lock_guard<std::mutex> lock(s->mu);
         for (int j = n - 1; j >= i; --j) {
-          if (ctxs[j]) musr_ctx_destroy(ctxs[j]);
+          release(ctxs[j]);
           s->queue.push_front(std::move(batch[j]));
           s->stats.queued += 1;
         }
@@ -352,94 +406,107 @@ void admit(musr_server* s, bool during_step = false) {
   }
 }
 
-// One step: every active fit's points in one multi-fit launch per group.
-int step(musr_server* s) {
+// Launches lane L: each of its fits names its next trial point(s), and all of them are
+// evaluated by one multi-fit launch per group, queued on the stream behind whatever the
+// other lane has in flight; the results come back to the lane's pinned buffer.
+int launch_lane(musr_server* s, int L) {
+  Lane& lane = s->lanes[L];
+  std::vector<Active*> fits;
+  for (auto& a : s->active)
+    if (a->lane == L) fits.push_back(a.get());
+  lane.launched.clear();
+  if (fits.empty()) return MUSR_OK;
+  const double t_req = s->now();
+  s->pool->run(static_cast<int>(fits.size()), [&](int i) { fits[i]->nvec = fits[i]->bfgs.request(&fits[i]->pts); });
+  const double t_min = s->now() - t_req;
   size_t np = 0, no = 0;
   int nv = 0;
-  const double t_req = s->now();
-  s->pool->run(static_cast<int>(s->active.size()), [&](int i) {
-    Active* a = s->active[i].get();
-    a->nvec = a->bfgs.request(&a->pts);
-  });
-  double t_min = s->now() - t_req;
-  for (size_t i = 0; i < s->active.size(); ++i) {
-    Active* a = s->active[i].get();
+  for (Active* a : fits) {
+    if (a->nvec == 0) continue;
     a->poff = np;
     a->ooff = no;
     np += static_cast<size_t>(a->nvec) * a->req->P;
     no += static_cast<size_t>(a->nvec) * (1 + a->req->P);
     nv += a->nvec;
+    lane.launched.push_back(a);
   }
-  if (!grow_host(reinterpret_cast<void**>(&s->h_params), &s->hp_cap, (np + 1) * sizeof(double)) ||
-      !grow_host(reinterpret_cast<void**>(&s->h_out), &s->ho_cap, (no + 1) * sizeof(double)) ||
-      !grow_host(reinterpret_cast<void**>(&s->h_jobs), &s->hj_cap, (nv + 1) * sizeof(Job)) ||
-      !grow_dev(&s->d_params, &s->dp_cap, (np + 1) * sizeof(double)) ||
-      !grow_dev(&s->d_out, &s->do_cap, (no + 1) * sizeof(double)) ||
-      !grow_dev(&s->d_jobs, &s->dj_cap, (nv + 1) * sizeof(Job)))
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stats.minimizer_s += t_min;
+  }
+  if (lane.launched.empty()) return MUSR_OK;
+  if (!grow_host(reinterpret_cast<void**>(&lane.h_params), &lane.hp_cap, (np + 1) * sizeof(double)) ||
+      !grow_host(reinterpret_cast<void**>(&lane.h_out), &lane.ho_cap, (no + 1) * sizeof(double)) ||
+      !grow_host(reinterpret_cast<void**>(&lane.h_jobs), &lane.hj_cap, (nv + 1) * sizeof(Job)) ||
+      !grow_dev(&lane.d_params, &lane.dp_cap, (np + 1) * sizeof(double)) ||
+      !grow_dev(&lane.d_out, &lane.do_cap, (no + 1) * sizeof(double)) ||
+      !grow_dev(&lane.d_jobs, &lane.dj_cap, (nv + 1) * sizeof(Job)))
     return MUSR_ENOMEM;
-  for (size_t i = 0; i < s->active.size(); ++i)
-    if (s->active[i]->nvec > 0)
-      std::memcpy(s->h_params + s->active[i]->poff, s->active[i]->pts.data(),
-                  static_cast<size_t>(s->active[i]->nvec) * s->active[i]->req->P * sizeof(double));
+  if (!lane.done && cudaEventCreateWithFlags(&lane.done, cudaEventDisableTiming) != cudaSuccess) return MUSR_ECUDA;
+  for (Active* a : lane.launched)
+    std::memcpy(lane.h_params + a->poff, a->pts.data(), static_cast<size_t>(a->nvec) * a->req->P * sizeof(double));
   // Group by (precision, shape, cost): one launch each, jobs contiguous per group.
   std::map<int, std::vector<Active*>> groups;
-  for (auto& a : s->active) groups[(a->req->prec * 16 + a->shape) * 2 + a->req->mode].push_back(a.get());
-  double* d_params = static_cast<double*>(s->d_params);
-  double* d_out = static_cast<double*>(s->d_out);
-  Job* d_jobs = static_cast<Job*>(s->d_jobs);
+  for (Active* a : lane.launched) groups[(a->req->prec * 16 + a->shape) * 2 + a->req->mode].push_back(a);
+  double* d_params = static_cast<double*>(lane.d_params);
+  double* d_out = static_cast<double*>(lane.d_out);
+  Job* d_jobs = static_cast<Job*>(lane.d_jobs);
   struct Launch {
     int prec, shape, mode, first, njobs, items;
   };
   std::vector<Launch> launches;
   int jpos = 0;
   for (auto& kv : groups) {
-    Launch L{kv.second[0]->req->prec, kv.second[0]->shape, kv.second[0]->req->mode, jpos, 0, 0};
+    Launch Lc{kv.second[0]->req->prec, kv.second[0]->shape, kv.second[0]->req->mode, jpos, 0, 0};
     for (Active* a : kv.second) {
-      fill_jobs(a->ctx, L.prec, kServeVariant, L.mode, 1, a->nvec, d_params + a->poff, d_out + a->ooff,
-                s->h_jobs + jpos, L.items);
-      L.items += a->nvec * a->ctx->comp[L.prec][kServeVariant].hs.nitems;
-      L.njobs += a->nvec;
+      fill_jobs(a->ctx, Lc.prec, kServeVariant, Lc.mode, 1, a->nvec, d_params + a->poff, d_out + a->ooff,
+                lane.h_jobs + jpos, Lc.items);
+      Lc.items += a->nvec * a->ctx->comp[Lc.prec][kServeVariant].hs.nitems;
+      Lc.njobs += a->nvec;
       jpos += a->nvec;
     }
-    launches.push_back(L);
+    launches.push_back(Lc);
   }
-  cudaError_t e = cudaMemcpyAsync(d_params, s->h_params, np * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+  cudaError_t e = cudaMemcpyAsync(d_params, lane.h_params, np * sizeof(double), cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_jobs, s->h_jobs, jpos * sizeof(Job), cudaMemcpyHostToDevice, s->stream);
+    e = cudaMemcpyAsync(d_jobs, lane.h_jobs, jpos * sizeof(Job), cudaMemcpyHostToDevice, s->stream);
   if (e != cudaSuccess) return MUSR_ECUDA;
-  for (const Launch& L : launches) {
-    if (L.items == 0) continue;
+  for (const Launch& Lc : launches) {
+    if (Lc.items == 0) continue;
     LaunchInfo info;
-    if (launch_eval(L.prec, L.shape, L.mode, 1, d_jobs + L.first, L.njobs, L.items, s->num_sms, s->stream,
+    if (launch_eval(Lc.prec, Lc.shape, Lc.mode, 1, d_jobs + Lc.first, Lc.njobs, Lc.items, s->num_sms, s->stream,
                     &info))
       return MUSR_ECUDA;
   }
-  e = cudaMemcpyAsync(s->h_out, d_out, no * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  e = cudaMemcpyAsync(lane.h_out, d_out, no * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(lane.done, s->stream);
   if (e != cudaSuccess) return MUSR_ECUDA;
-  const double t_adm = s->now();
-  admit(s, true);  // configure newly queued fits while the step runs
+  lane.in_flight = true;
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->stats.steps += 1;
+  s->stats.launches += static_cast<int64_t>(launches.size());
+  s->stats.evals += nv;
+  return MUSR_OK;
+}
+
+// Waits for lane L's results, advances its fits' minimisers (in parallel: fits are
+// independent) and retires the finished ones.
+int deliver_lane(musr_server* s, int L) {
+  Lane& lane = s->lanes[L];
+  if (!lane.in_flight) return MUSR_OK;
   const double t_wait = s->now();
-  e = cudaStreamSynchronize(s->stream);
+  const cudaError_t e = cudaEventSynchronize(lane.done);
+  lane.in_flight = false;
   if (e != cudaSuccess) return MUSR_ECUDA;
   const double t_del = s->now();
-  {
-    std::lock_guard<std::mutex> lock(s->mu);
-    s->stats.steps += 1;
-    s->stats.launches += static_cast<int64_t>(launches.size());
-    s->stats.evals += nv;
-    s->stats.admit_s += t_wait - t_adm;
-    s->stats.wait_s += t_del - t_wait;
-  }
-  // Advance every fit that took part in this step (in parallel: fits are independent),
-  // then retire the finished ones.
-  s->pool->run(static_cast<int>(s->active.size()), [&](int i) {
-    Active* a = s->active[i].get();
-    if (a->nvec == 0) return;  // admitted during this step
+  const std::vector<Active*>& fits = lane.launched;
+  s->pool->run(static_cast<int>(fits.size()), [&](int i) {
+    Active* a = fits[i];
     const int P = a->req->P;
     a->f.resize(a->nvec);
     a->g.resize(static_cast<size_t>(a->nvec) * P);
     for (int v = 0; v < a->nvec; ++v) {
-      const double* o = s->h_out + a->ooff + static_cast<size_t>(v) * (1 + P);
+      const double* o = lane.h_out + a->ooff + static_cast<size_t>(v) * (1 + P);
       a->f[v] = o[0];
       std::memcpy(a->g.data() + static_cast<size_t>(v) * P, o + 1, sizeof(double) * P);
     }
@@ -448,60 +515,83 @@ int step(musr_server* s) {
       a->bfgs.set_f_noise(kSplitNoiseRel * std::fabs(a->f[0]));
     a->first = false;
   });
-  std::vector<std::unique_ptr<Active>> keep;
   double bin_evals = 0.0;
-  for (auto& a : s->active) {
-    if (a->nvec == 0) {  // admitted during this step
-      keep.push_back(std::move(a));
-      continue;
-    }
+  bool retired = false;
+  for (Active* a : fits) {
     bin_evals += static_cast<double>(a->bins) * a->nvec;
     a->nvec = 0;
-    if (a->bfgs.done())
-      finish(s, a.get(), a->bfgs.status());
-    else
-      keep.push_back(std::move(a));
+    if (a->bfgs.done()) {
+      lane.load -= a->load;
+      finish(s, a, a->bfgs.status());
+      retired = true;
+    }
   }
-  {
-    std::lock_guard<std::mutex> lock(s->mu);
-    s->stats.bin_evals += bin_evals;
+  lane.launched.clear();
+  if (retired) {
+    std::vector<std::unique_ptr<Active>> keep;
+    for (auto& a : s->active)
+      if (a->ctx) keep.push_back(std::move(a));
+    s->active.swap(keep);
   }
-  s->active.swap(keep);
-  t_min += s->now() - t_del;
-  {
-    std::lock_guard<std::mutex> lock(s->mu);
-    s->stats.minimizer_s += t_min;
-  }
+  if (s->lanes[0].launched.empty() && s->lanes[1].launched.empty() && s->active.empty())
+    s->lanes[0].load = s->lanes[1].load = 0.0;  // no drift from rounding
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->stats.bin_evals += bin_evals;
+  s->stats.wait_s += t_del - t_wait;
+  s->stats.minimizer_s += s->now() - t_del;
   return MUSR_OK;
+}
+
+// Ends every running fit with `status` after a failed launch or wait.
+void fail_all(musr_server* s, int status) {
+  cudaStreamSynchronize(s->stream);
+  cudaGetLastError();
+  for (auto& ln : s->lanes) {
+    ln.in_flight = false;
+    ln.launched.clear();
+    ln.load = 0.0;
+  }
+  std::vector<std::unique_ptr<Active>> act;
+  act.swap(s->active);
+  for (auto& a : act) finish(s, a.get(), status);
+  s->worker_error = "serving step failed";
 }
 
 void worker_main(musr_server* s) {
   cudaSetDevice(s->device);
   for (;;) {
+    const bool idle = s->active.empty() && !s->lanes[0].in_flight && !s->lanes[1].in_flight;
     {
       std::unique_lock<std::mutex> lock(s->mu);
-      if (s->active.empty())
-        s->cv_work.wait(lock, [&] { return s->stop || !s->queue.empty(); });
+      if (idle) s->cv_work.wait(lock, [&] { return s->stop || !s->queue.empty(); });
       if (s->stop) break;
     }
-    if (s->active.empty()) admit(s);
-    if (s->active.empty()) continue;
+    if (idle) {
+      admit(s);
+      if (s->active.empty()) continue;
+    }
+    // Half-step: launch lane L behind the other lane's work, admit while the device
+    // runs, then take the other lane's results.
+    const int L = s->next_lane;
+    s->next_lane = 1 - L;
     const double t = s->now();
-    const int rc = step(s);
+    int rc = launch_lane(s, L);
+    if (!rc) {
+      const double t_adm = s->now();
+      admit(s, true);
+      const double t_adm_end = s->now();
+      std::lock_guard<std::mutex> lock(s->mu);
+      s->stats.admit_s += t_adm_end - t_adm;
+    }
+    if (!rc) rc = deliver_lane(s, 1 - L);
     {
       std::lock_guard<std::mutex> lock(s->mu);
       s->stats.busy_s += s->now() - t;
     }
-    if (rc) {
-      // a CUDA failure ends every running fit with that status
-      std::vector<std::unique_ptr<Active>> act;
-      act.swap(s->active);
-      for (auto& a : act) finish(s, a.get(), rc);
-      s->worker_error = "serving step failed";
-    }
+    if (rc) fail_all(s, rc);  // a CUDA failure ends every running fit with that status
   }
-  for (auto& a : s->active)
-    if (a->ctx) musr_ctx_destroy(a->ctx);
+  cudaStreamSynchronize(s->stream);
+  for (auto& a : s->active) release(a->ctx);
   s->active.clear();
 }
 
@@ -525,7 +615,17 @@ bool copy_request(const musr_fit_request* q, Request* r, std::string* why) {
     return false;
   }
   const size_t n = static_cast<size_t>(q->nhist) * q->nbins * dtype_size(q->dtype);
-  r->counts.assign(static_cast<const unsigned char*>(q->counts), static_cast<const unsigned char*>(q->counts) + n);
+  if (q->flags & ~MUSR_REQ_BORROW_COUNTS) {
+    *why = "unknown request flags";
+    return false;
+  }
+  if (q->flags & MUSR_REQ_BORROW_COUNTS) {
+    r->counts = q->counts;
+  } else {
+    r->counts_copy.assign(static_cast<const unsigned char*>(q->counts),
+                          static_cast<const unsigned char*>(q->counts) + n);
+    r->counts = r->counts_copy.data();
+  }
   r->dtype = q->dtype;
   r->H = q->nhist;
   r->B = q->nbins;
@@ -594,12 +694,15 @@ void musr_server_destroy(musr_server* s) {
   if (s->worker.joinable()) s->worker.join();
   DeviceScope ds(s->device);
   cudaStreamSynchronize(s->stream);
-  if (s->h_params) cudaFreeHost(s->h_params);
-  if (s->h_out) cudaFreeHost(s->h_out);
-  if (s->h_jobs) cudaFreeHost(s->h_jobs);
-  if (s->d_params) cudaFree(s->d_params);
-  if (s->d_out) cudaFree(s->d_out);
-  if (s->d_jobs) cudaFree(s->d_jobs);
+  for (auto& ln : s->lanes) {
+    if (ln.h_params) cudaFreeHost(ln.h_params);
+    if (ln.h_out) cudaFreeHost(ln.h_out);
+    if (ln.h_jobs) cudaFreeHost(ln.h_jobs);
+    if (ln.d_params) cudaFree(ln.d_params);
+    if (ln.d_out) cudaFree(ln.d_out);
+    if (ln.d_jobs) cudaFree(ln.d_jobs);
+    if (ln.done) cudaEventDestroy(ln.done);
+  }
   cudaStreamDestroy(s->stream);
   delete s;
 }

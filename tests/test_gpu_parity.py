@@ -274,6 +274,45 @@ def test_invalid_arguments(B):
         B.musr_ctx_destroy(ctx)
 
 
+def test_upload_checks_counts_on_device(B):
+    """Counts are copied as they are and checked on the device: a non-finite float or an
+    INT32 count beyond 2^24 anywhere (here the last bin of the last row, in a row length
+    that is not a multiple of the device row stride) fails with MUSR_EINVAL and leaves no
+    histograms; the limits themselves pass, and a valid upload afterwards evaluates as
+    the oracle does."""
+    p = mi.cfg1(nbins=1000, seed=6, dtype=np.float32)
+    ctx = B.musr_ctx_create(0)
+    try:
+        for dtype, bad in ((np.float32, np.nan), (np.float32, np.inf), (np.float32, -np.inf),
+                           (np.float64, np.nan), (np.float64, np.inf),
+                           (np.int32, 1 << 24), (np.int32, -(1 << 24)), (np.int32, np.iinfo(np.int32).max)):
+            c = np.ascontiguousarray(np.tile(p.counts[0].astype(dtype), (3, 1)))
+            c[-1, -1] = bad
+            with pytest.raises(B.MusrError) as e:
+                B.musr_upload_histograms(ctx, c, np.zeros(3), p.bin_width_ns, p.fit_range_us)
+            assert e.value.status == B.MUSR_EINVAL, (dtype, bad)
+            B.musr_set_theory(ctx, p.terms)
+            with pytest.raises(B.MusrError) as e:  # no histograms
+                B.musr_set_map(ctx, np.tile(p.map, (3, 1)), p.nparams, p.consts)
+            assert e.value.status == B.MUSR_ESTATE
+        for dtype, edge in ((np.int32, (1 << 24) - 1), (np.int32, -(1 << 24) + 1),
+                            (np.float32, np.finfo(np.float32).max), (np.float64, np.finfo(np.float64).max)):
+            c = np.ascontiguousarray(p.counts[0].astype(dtype)[None, :])
+            c[0, -1] = edge
+            B.musr_upload_histograms(ctx, c, p.t0, p.bin_width_ns, p.fit_range_us)
+        c = np.ascontiguousarray(p.counts[0].astype(np.int32)[None, :])
+        B.musr_upload_histograms(ctx, c, p.t0, p.bin_width_ns, p.fit_range_us)
+        B.musr_set_theory(ctx, p.terms)
+        B.musr_set_map(ctx, p.map, p.nparams, p.consts)
+        q = mi.Problem(c, p.t0, p.bin_width_ns, p.fit_range_us, p.terms, p.map, p.consts, p.nparams, p.truth,
+                       p.names)
+        for mode in (0, 1):
+            v, g, _ = B.musr_eval(ctx, p.truth, mode, B.MUSR_FP64)
+            _check_fp64(v, g, oracle.cost(q, p.truth, mode))
+    finally:
+        B.musr_ctx_destroy(ctx)
+
+
 def test_hbm_budget_is_enforced(B):
     p = mi.cfg2(nhist=8, nbins=65536, seed=2)
     ctx = B.musr_ctx_create(0, hbm_budget_bytes=1 << 20)

@@ -60,6 +60,28 @@ def test_results_identical_alone_and_in_mix(B):
     assert st["completed"] == len(pool) and st["steps"] > 0 and st["launches"] >= st["steps"]
 
 
+def test_borrowed_and_copied_counts_give_the_same_fits(B):
+    """A request that lends its counts (read at admission) and one whose counts are copied
+    at submission give bit-identical fits; unknown request flags are refused."""
+    pool = _small_pool()
+    starts = [mi.start_point(p, 40 + i) for i, (p, _, _) in enumerate(pool)]
+    res = {}
+    for borrow in (False, True):
+        with B.Server(hbm_budget_bytes=1 << 30, max_active=64) as srv:
+            ids = [srv.submit(p, x0, mode, prec, borrow=borrow) for (p, mode, prec), x0 in zip(pool, starts)]
+            res[borrow] = [srv.wait(fid, timeout_ms=120000) for fid in ids]
+            assert not srv.lent
+    for a, b in zip(res[False], res[True]):
+        assert a["status"] == 0 and b["status"] == 0
+        assert np.array_equal(a["x"], b["x"]) and a["nfev"] == b["nfev"]
+    p, mode, prec = pool[0]
+    with B.Server(hbm_budget_bytes=1 << 28) as srv:
+        q, keep = B.make_request(p, starts[0], mode, prec)
+        q.flags = 2
+        fid = B.ctypes.c_int64()
+        assert B.load().musr_server_submit(srv.srv, B.ctypes.byref(q), B.ctypes.byref(fid)) == B.MUSR_EINVAL
+
+
 def test_admission_by_budget_and_rejection(B):
     # ~0.7 MB per fit: a 2 MiB budget holds about two of them at a time
     p = mi.cfg2(nhist=8, nbins=20000, bin_width_ns=0.64, seed=311)
