@@ -4,6 +4,7 @@
 // type, zeroes each row's padding and flags values the store cannot hold, so the host makes
 // one copy and no pass over the data.
 #include <cstdint>
+#include <type_traits>
 
 #include "musr.h"
 #include "musr_dev.h"
@@ -47,7 +48,63 @@ __global__ void __launch_bounds__(256) prepare_counts_kernel(void* buf, int64_t 
   if (bad) *reinterpret_cast<volatile unsigned*>(flag) = seq;
 }
 
+// The same from a packed copy of the rows ([nhist][nbins], dtype as uploaded) into the
+// image, row h moved left by shift[h] bins: img[h][j] = raw[h][j + shift[h]] while that
+// bin exists, else 0.  Every raw value is checked, also those the shift leaves out.
+template <int DTYPE>
+__global__ void __launch_bounds__(256) prepare_shifted_kernel(const void* raw, void* img, const int64_t* shift,
+                                                              int64_t nbins, int64_t stride, int64_t total,
+                                                              int64_t nraw, unsigned* flag, unsigned seq) {
+  using Out = typename std::conditional<DTYPE == MUSR_DTYPE_FP64, double, float>::type;
+  using In = typename std::conditional<DTYPE == MUSR_DTYPE_INT32, int32_t,
+                                       typename std::conditional<DTYPE == MUSR_DTYPE_FP64, double, float>::type>::type;
+  const In* src = static_cast<const In*>(raw);
+  Out* dst = static_cast<Out*>(img);
+  const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t first = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  for (int64_t e = first; e < total; e += step) {
+    const int64_t h = e / stride, j = e - h * stride, n = j + shift[h];
+    dst[e] = j < nbins && n < nbins ? static_cast<Out>(src[h * nbins + n]) : Out(0);
+  }
+  bool bad = false;
+  for (int64_t e = first; e < nraw; e += step) {
+    const In v = src[e];
+    if (DTYPE == MUSR_DTYPE_INT32)
+      bad |= v >= (1 << 24) || v <= -(1 << 24);
+    else if (DTYPE == MUSR_DTYPE_FP32)
+      bad |= !(fabsf(static_cast<float>(v)) <= 3.4028234663852886e38f);
+    else
+      bad |= !(fabs(static_cast<double>(v)) <= 1.7976931348623157e308);
+  }
+  if (bad) *reinterpret_cast<volatile unsigned*>(flag) = seq;
+}
+
 }  // namespace
+
+int launch_prepare_counts_shifted(const void* raw, void* img, const int64_t* shift, int dtype, int nhist,
+                                  int64_t nbins, int64_t stride, unsigned* flag, unsigned seq, int num_sms,
+                                  void* stream_) {
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const int64_t total = static_cast<int64_t>(nhist) * stride, nraw = static_cast<int64_t>(nhist) * nbins;
+  if (total <= 0) return 0;
+  const int64_t want = (total + 255) / 256;
+  const int grid = static_cast<int>(want < 8LL * num_sms ? want : 8LL * num_sms);
+  switch (dtype) {
+    case MUSR_DTYPE_INT32:
+      prepare_shifted_kernel<MUSR_DTYPE_INT32>
+          <<<grid, 256, 0, stream>>>(raw, img, shift, nbins, stride, total, nraw, flag, seq);
+      break;
+    case MUSR_DTYPE_FP32:
+      prepare_shifted_kernel<MUSR_DTYPE_FP32>
+          <<<grid, 256, 0, stream>>>(raw, img, shift, nbins, stride, total, nraw, flag, seq);
+      break;
+    default:
+      prepare_shifted_kernel<MUSR_DTYPE_FP64>
+          <<<grid, 256, 0, stream>>>(raw, img, shift, nbins, stride, total, nraw, flag, seq);
+      break;
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
 
 int launch_prepare_counts(void* buf, int dtype, int nhist, int64_t nbins, int64_t stride, unsigned* flag,
                           unsigned seq, int num_sms, void* stream_) {

@@ -226,6 +226,28 @@ void fit_bins(double t0, double dt_us, int64_t B, double lo, double hi, int* nlo
   *nhi = static_cast<int>(b);
 }
 
+// Whole-bin shifts that put histograms on a common time grid: histogram h moves left by
+// floor(t0_h) - min_h floor(t0_h) bins (histograms whose t0 have equal fractions then
+// share t0), never past its first bin in the fit window (no fitted bin is dropped).
+// Histograms without a bin in the window stay.
+std::vector<int64_t> grid_shifts(const musr_ctx* ctx) {
+  std::vector<int64_t> shift(ctx->H, 0);
+  double fmin = 0.0;
+  bool any = false;
+  for (int h = 0; h < ctx->H; ++h)
+    if (ctx->nhi[h] > ctx->nlo[h]) {
+      const double f = std::floor(ctx->t0[h]);
+      fmin = any ? std::min(fmin, f) : f;
+      any = true;
+    }
+  for (int h = 0; h < ctx->H && any; ++h)
+    if (ctx->nhi[h] > ctx->nlo[h]) {
+      const double d = std::floor(ctx->t0[h]) - fmin;  // >= 0
+      shift[h] = std::min<int64_t>(d < 1e18 ? static_cast<int64_t>(d) : ctx->nlo[h], ctx->nlo[h]);
+    }
+  return shift;
+}
+
 void free_compiled(musr_ctx* ctx, Compiled& c) {
   dfree(ctx, c.tables);
   std::vector<char>().swap(c.blob);
@@ -279,7 +301,7 @@ int compile(musr_ctx* ctx, int prec, int var) {
       return MUSR_OK;  // SPLIT unavailable for this theory; FP64 still is
     }
     group_cap = musr::shape_group(hs.shape);
-    // Group histograms that share t0 and every time-dependent parameter.
+    // Group histograms that share t0, the fit window and every time-dependent parameter.
     std::map<std::vector<int64_t>, int> key_to_group;
     // A slot's identity across histograms: the global parameter, or the constant's value.
     auto push_entry = [&](std::vector<int64_t>& key, int h, int s) {
@@ -298,8 +320,19 @@ int compile(musr_ctx* ctx, int prec, int var) {
     for (int h = 0; h < H; ++h) {
       std::vector<int64_t> key;
       int64_t tb;
-      std::memcpy(&tb, &ctx->t0[h], sizeof(tb));
-      key.push_back(tb);
+      // t0 to 2^-24 bins: a smaller difference in time zero (below 2^-24 bin widths in
+      // every time) is far below the FP32 resolution of the shared per-bin factors
+      const double q = std::nearbyint(ctx->t0[h] * 16777216.0);
+      if (std::fabs(q) < 4e18) {
+        key.push_back(0);
+        key.push_back(static_cast<int64_t>(q));
+      } else {
+        std::memcpy(&tb, &ctx->t0[h], sizeof(tb));
+        key.push_back(1);
+        key.push_back(tb);
+      }
+      key.push_back(ctx->nlo[h]);
+      key.push_back(ctx->nhi[h]);
       for (int k = 0; k < hs.nterms; ++k) {
         const CanonTerm& ct = hs.canon[k];
         for (int i = 0; i < ct.nexp; ++i) push_entry(key, h, ct.exp_slot[i]);
@@ -673,6 +706,7 @@ void musr_ctx_destroy(musr_ctx* ctx) {
   for (auto& pc : ctx->comp)
     for (auto& c : pc) free_compiled(ctx, c);
   dfree(ctx, ctx->counts_own);
+  dfree(ctx, ctx->upload_scratch);
   EvalBufs& ev = ctx->ev;
   dfree(ctx, ev.params);
   dfree(ctx, ev.out);
@@ -704,6 +738,8 @@ static int upload_common(musr_ctx* ctx, int nhist, int64_t nbins, const double* 
   for (int h = 0; h < nhist; ++h)
     if (!std::isfinite(t0[h])) return fail(ctx, MUSR_EINVAL, "t0 must be finite");
   ctx->check_flag = nullptr;
+  dfree(ctx, ctx->upload_scratch);
+  ctx->shift.clear();
   ctx->H = nhist;
   ctx->B = nbins;
   ctx->t0.assign(t0, t0 + nhist);
@@ -747,22 +783,47 @@ int musr_upload_histograms(musr_ctx* ctx, const void* counts, int dtype, int nhi
   const int64_t stride = (nbins + kRowAlign - 1) / kRowAlign * kRowAlign;
   const size_t esz = dtype == MUSR_DTYPE_FP64 ? 8 : 4;
   const size_t total = static_cast<size_t>(nhist) * stride * esz;
-  // The rows go to the device as they are, at the device row stride, in one copy; a kernel
-  // then converts INT32 to FP32 in place, zeroes the padding and flags counts the store
-  // cannot hold.  The host makes no pass over the data.
+  // Rows whose time-zero bins differ by whole bins are moved onto one grid (the time
+  // factors of histograms on a common grid are evaluated once for all of them).
+  std::vector<int64_t> shift = grid_shifts(ctx);
+  const bool shifted = std::any_of(shift.begin(), shift.end(), [](int64_t v) { return v != 0; });
+  // The rows go to the device as they are, in one copy; a kernel then converts INT32 to
+  // FP32, zeroes the padding and flags counts the store cannot hold.  The host makes no
+  // pass over the data.  Unshifted rows go straight to the device image at its row
+  // stride (converted in place); shifted ones to a packed scratch copy first.
   if ((rc = dalloc(ctx, ctx->counts_own, total))) return rc;
   cudaStream_t st = ctx->setup_stream ? ctx->setup_stream : cudaStreamPerThread;
   const size_t row = static_cast<size_t>(nbins) * esz;
-  cudaError_t e = stride == nbins
-                      ? cudaMemcpyAsync(ctx->counts_own.p, counts, total, cudaMemcpyHostToDevice, st)
-                      : cudaMemcpy2DAsync(ctx->counts_own.p, static_cast<size_t>(stride) * esz, counts, row, row,
-                                          static_cast<size_t>(nhist), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(counts)");
   CheckFlag& flag = tl_flag;
   if (!flag.ready()) return cuda_fail(ctx, cudaGetLastError(), "cudaHostAlloc(check flag)");
   const unsigned seq = flag.next();
-  if (launch_prepare_counts(ctx->counts_own.p, dtype, nhist, nbins, stride, flag.dev, seq, ctx->num_sms, st))
-    return cuda_fail(ctx, cudaGetLastError(), "prepare_counts launch");
+  cudaError_t e;
+  if (!shifted) {
+    e = stride == nbins ? cudaMemcpyAsync(ctx->counts_own.p, counts, total, cudaMemcpyHostToDevice, st)
+                        : cudaMemcpy2DAsync(ctx->counts_own.p, static_cast<size_t>(stride) * esz, counts, row, row,
+                                            static_cast<size_t>(nhist), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(counts)");
+    if (launch_prepare_counts(ctx->counts_own.p, dtype, nhist, nbins, stride, flag.dev, seq, ctx->num_sms, st))
+      return cuda_fail(ctx, cudaGetLastError(), "prepare_counts launch");
+  } else {
+    const size_t raw = (row * nhist + 255) & ~size_t(255);
+    if ((rc = dalloc(ctx, ctx->upload_scratch, raw + sizeof(int64_t) * nhist))) return rc;
+    char* sp = static_cast<char*>(ctx->upload_scratch.p);
+    ctx->shift = std::move(shift);  // the copy's source, kept until the check is read
+    e = cudaMemcpyAsync(sp, counts, row * nhist, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(sp + raw, ctx->shift.data(), sizeof(int64_t) * nhist, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(counts)");
+    if (launch_prepare_counts_shifted(sp, ctx->counts_own.p, reinterpret_cast<const int64_t*>(sp + raw), dtype,
+                                      nhist, nbins, stride, flag.dev, seq, ctx->num_sms, st))
+      return cuda_fail(ctx, cudaGetLastError(), "prepare_counts launch");
+    // the device grid: t0 and the fit window move with the row (whole bins, exact)
+    for (int h = 0; h < nhist; ++h) {
+      ctx->t0[h] -= static_cast<double>(ctx->shift[h]);
+      ctx->nlo[h] -= static_cast<int>(ctx->shift[h]);
+      ctx->nhi[h] -= static_cast<int>(ctx->shift[h]);
+    }
+  }
   ctx->check_flag = flag.host;
   ctx->check_seq = seq;
   ctx->check_dtype = dtype;
@@ -782,6 +843,7 @@ int musr::finish_upload_check(musr_ctx* ctx) {
   if (!ctx->check_flag) return MUSR_OK;
   const bool bad = *static_cast<const volatile unsigned*>(ctx->check_flag) == ctx->check_seq;
   ctx->check_flag = nullptr;
+  dfree(ctx, ctx->upload_scratch);
   if (!bad) return MUSR_OK;
   drop_config(ctx);
   dfree(ctx, ctx->counts_own);

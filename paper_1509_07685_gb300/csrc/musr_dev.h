@@ -178,6 +178,11 @@ int max_ctas_per_sm(int precision, int shape, int mode, int grad);
 // (host-mapped) if a count is not representable (|INT32| >= 2^24, non-finite float).
 int launch_prepare_counts(void* buf, int dtype, int nhist, int64_t nbins, int64_t stride, unsigned* flag,
                           unsigned seq, int num_sms, void* stream);
+// The same from packed raw rows ([nhist][nbins]) into img ([nhist][stride]), row h moved
+// left by shift[h] >= 0 bins (device array): img[h][j] = raw[h][j + shift[h]] or 0.
+int launch_prepare_counts_shifted(const void* raw, void* img, const int64_t* shift, int dtype, int nhist,
+                                  int64_t nbins, int64_t stride, unsigned* flag, unsigned seq, int num_sms,
+                                  void* stream);
 // Decompositions compiled per precision: tile v holds (bins per CTA iteration) << v
 // bins -- SPLIT 512 ... 16384 (the phase-split limit), FP64 256 ... 8192.
 constexpr int kVariants = 6;

@@ -144,6 +144,8 @@ struct musr_ctx {
   bool owner_waited = false;
   // Device check of the last histogram upload, not read yet (see finish_upload_check).
   const unsigned* check_flag = nullptr;
+  musr::DevBuf upload_scratch;     // packed rows of a shifted upload, until the check is read
+  std::vector<int64_t> shift;      // whole bins each histogram's row moved left on the device
   unsigned check_seq = 0;
   int check_dtype = 0;
 };

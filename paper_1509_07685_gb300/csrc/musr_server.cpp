@@ -345,7 +345,14 @@ void activate(musr_server* s, std::unique_ptr<Request> r, musr_ctx* ctx) {
 // simultaneous points (the minimiser's widest step) with a generous bound on work items.
 size_t estimate_bytes(const Request& r) {
   const size_t stride = static_cast<size_t>((r.B + 63) / 64 * 64);
-  const size_t counts = static_cast<size_t>(r.H) * stride * (r.dtype == MUSR_DTYPE_FP64 ? 8 : 4);
+  const size_t esz = r.dtype == MUSR_DTYPE_FP64 ? 8 : 4;
+  size_t counts = static_cast<size_t>(r.H) * stride * esz;
+  // histograms moved onto a common time grid pass through a packed scratch copy
+  for (double t : r.t0)
+    if (std::floor(t) != std::floor(r.t0[0])) {
+      counts += static_cast<size_t>(r.H) * static_cast<size_t>(r.B) * esz + 8 * static_cast<size_t>(r.H) + 256;
+      break;
+    }
   const size_t items = (static_cast<size_t>(r.H) + 1) * (static_cast<size_t>(r.B) / 2048 + 2);
   const size_t rows = items * static_cast<size_t>(r.P + 1) * 100 * sizeof(double);  // <= 100 doubles a row
   return counts + rows + (size_t(4) << 20);

@@ -12,6 +12,8 @@ Tolerances:
     values: the value (all terms >= 0) to SPLIT_EPS relative, the gradient to
     SPLIT_EPS * gscale.  FP32 accumulation below the warp adds far less.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -309,6 +311,65 @@ def test_upload_checks_counts_on_device(B):
         for mode in (0, 1):
             v, g, _ = B.musr_eval(ctx, p.truth, mode, B.MUSR_FP64)
             _check_fp64(v, g, oracle.cost(q, p.truth, mode))
+    finally:
+        B.musr_ctx_destroy(ctx)
+
+
+# Per-detector time-zero bins.  Histograms whose t0 differ by whole bins are moved onto one
+# time grid on the device (and share the time factors there); the cost is the same sum.
+T0_CASES = {
+    "integer": lambda H: np.arange(H, dtype=float),
+    "multiple_of_4": lambda H: 4.0 * np.arange(H),
+    "equal_fractions": lambda H: np.arange(H) + 0.5,
+    "equal_fractions_inexact": lambda H: np.arange(H) + 0.37,  # (h + 0.37) - h is not exactly 0.37
+    "mixed_fractions": lambda H: 3.0 + 0.25 * np.arange(H),
+    "negative": lambda H: np.arange(H) - 3.0,
+    "one_beyond_the_data": lambda H: np.where(np.arange(H) == H - 1, 5100.0, np.arange(H, dtype=float)),
+    "large_offsets": lambda H: 997.0 * np.arange(H),
+}
+
+
+@pytest.mark.parametrize("case", sorted(T0_CASES))
+@pytest.mark.parametrize("window", [(0.05, 9.0), (-0.02, 9.9)])
+def test_per_detector_t0_offsets(B, case, window):
+    base = mi.paper_tf16(nhist=6, nbins=5000, bin_width_ns=2.0, seed=77)
+    p = dataclasses.replace(base, t0=T0_CASES[case](6), fit_range_us=window)
+    x = mi.start_point(p, 3)
+    X = mi.jitter(x, 5, seed=4, lo=0.97, hi=1.03)
+    with B.Context(p) as ctx:
+        for mode in (0, 1):
+            ref = oracle.cost(p, x, mode)
+            v, g, _ = ctx.eval(x, mode, B.MUSR_FP64)
+            _check_fp64(v, g, ref)
+            v, g, _ = ctx.eval(x, mode, B.MUSR_SPLIT)
+            _check_split(v, g, ref)
+            vals, grads, st = ctx.eval_batch(X, mode, B.MUSR_SPLIT)
+            assert st == 0
+            for i in (0, 4):
+                _check_split(vals[i], grads[i], oracle.cost(p, X[i], mode))
+
+
+def test_shifted_upload_every_dtype_and_check(B):
+    """The shifted upload path in each dtype, and its check of every value: a NaN in bins
+    the shift leaves out of the device image (before a histogram's fit window) still fails."""
+    base = mi.paper_tf16(nhist=4, nbins=3001, bin_width_ns=3.0, seed=78)
+    t0 = np.array([0.0, 2.0, 5.0, 9.0])
+    x = mi.start_point(base, 1)
+    for dtype in (np.int32, np.float32, np.float64):
+        p = dataclasses.replace(base, counts=np.ascontiguousarray(base.counts.astype(dtype)), t0=t0,
+                                fit_range_us=(0.01, 8.5))
+        with B.Context(p) as ctx:
+            for mode in (0, 1):
+                ref = oracle.cost(p, x, mode)
+                v, g, _ = ctx.eval(x, mode, B.MUSR_FP64)
+                _check_fp64(v, g, ref)
+    bad = np.ascontiguousarray(base.counts.astype(np.float32))
+    bad[3, 2] = np.nan  # bin 2 of the histogram with t0 = 9 bins: moved out of the image
+    ctx = B.musr_ctx_create(0)
+    try:
+        with pytest.raises(B.MusrError) as e:
+            B.musr_upload_histograms(ctx, bad, t0, base.bin_width_ns, (0.01, 8.5))
+        assert e.value.status == B.MUSR_EINVAL
     finally:
         B.musr_ctx_destroy(ctx)
 
