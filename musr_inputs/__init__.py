@@ -360,6 +360,66 @@ def paper_tf16(nhist: int = 16, nbins: int = 81920, bin_width_ns: Optional[float
                    "paper_tf16")
 
 
+@dataclasses.dataclass
+class AsymmetryProblem:
+    """A fit of asymmetry data: forward / backward histogram pairs ([H][B] each) with the
+    relative efficiency alpha and constant backgrounds of each pair; theory and map as for
+    histograms, with local slot 0 the scale and slot 1 the baseline of T = N0 A(t) + Nbkg."""
+
+    forward: np.ndarray
+    backward: np.ndarray
+    alpha: np.ndarray  # [H]
+    bkg_f: np.ndarray  # [H] counts per bin
+    bkg_b: np.ndarray
+    t0: np.ndarray
+    bin_width_ns: float
+    fit_range_us: Tuple[float, float]
+    terms: List[Term]
+    map: np.ndarray
+    consts: np.ndarray
+    nparams: int
+    truth: np.ndarray
+    names: List[str]
+    name: str = ""
+
+    @property
+    def H(self) -> int:
+        return int(self.forward.shape[0])
+
+    @property
+    def B(self) -> int:
+        return int(self.forward.shape[1])
+
+    @property
+    def nslots(self) -> int:
+        return int(self.map.shape[1])
+
+
+def asym_tf(npairs: int = 2, nbins: int = 8192, bin_width_ns: float = 1.0, seed: int = 21, n0: float = 400.0,
+            eff_b: float = 0.85, nbkg: float = 3.0, dtype=np.float32) -> AsymmetryProblem:
+    """Transverse-field asymmetry fit: detector pairs at phases phi_k and phi_k + 180 deg, the
+    backward detector with efficiency eff_b (so alpha = 1 / eff_b), one TF component with
+    Gaussian damping.  Model A = A0 exp(-(sigma t)^2 / 2) cos(2 pi (nu t + phi_k / 360)),
+    shared A0, sigma, nu, a phase per pair; scale 1 and baseline 0 (constants)."""
+    comps = [Component(0.22, "TF", nu_mhz=3.0, sigma=0.4)]
+    dets, cps, phis = [], [], []
+    for k in range(npairs):
+        ph = 20.0 + 90.0 * k
+        phis.append(ph)
+        dets += [Detector(n0, nbkg, ph), Detector(n0 * eff_b, nbkg, ph + 180.0)]
+        cps += [comps, comps]
+    h = simulate(seed, dets, cps, nbins, bin_width_ns, dtype)
+    terms = [[("AMP", (2,)), ("GAUSS", (3,)), ("TFCOS", (4, 5))]]
+    rows = [[-1, -2, 0, 1, 2, 3 + k] for k in range(npairs)]
+    names = ["A0", "sigma", "nu"] + [f"phi_{k}" for k in range(npairs)]
+    truth = [0.22, 0.4, 3.0] + phis
+    return AsymmetryProblem(np.ascontiguousarray(h[0::2]), np.ascontiguousarray(h[1::2]),
+                            np.full(npairs, 1.0 / eff_b), np.full(npairs, nbkg), np.full(npairs, nbkg),
+                            np.zeros(npairs), bin_width_ns, _full_range(nbins, bin_width_ns), terms,
+                            np.array(rows, np.int32), np.array([1.0, 0.0]), len(truth), np.array(truth), names,
+                            "asym_tf")
+
+
 CONFIGS = {"cfg1": cfg1, "cfg2": cfg2, "cfg3": cfg3, "cfg5": cfg5, "paper_tf16": paper_tf16}
 
 

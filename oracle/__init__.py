@@ -63,7 +63,7 @@ def _load():
             P = ctypes.POINTER
             d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
             prob = [P(d), ctypes.c_int, i64, P(d), d, d, d, ctypes.c_int, P(i32), P(i32), P(i32),
-                    P(i32), ctypes.c_int, P(d), ctypes.c_int, ctypes.c_int]
+                    P(i32), ctypes.c_int, P(d), ctypes.c_int, ctypes.c_int, P(d), ctypes.c_int]
             lib.oracle_primitive.argtypes = [ctypes.c_int, d, d, d]
             lib.oracle_primitive.restype = d
             lib.oracle_model.argtypes = prob + [P(d), ctypes.c_int, d]
@@ -79,6 +79,8 @@ def _load():
             lib.oracle_fit.argtypes = prob + [ctypes.c_int, P(d), P(d), ctypes.c_int, d, P(d), P(d),
                                               P(d), P(ctypes.c_int)]
             lib.oracle_fit.restype = ctypes.c_int
+            lib.oracle_asymmetry.argtypes = [P(d), P(d), ctypes.c_int, i64, P(d), P(d), P(d), P(d), P(d)]
+            lib.oracle_asymmetry.restype = None
             lib.oracle_neumaier_sum.argtypes = [P(d), i64]
             lib.oracle_neumaier_sum.restype = d
             _lib = lib
@@ -112,10 +114,18 @@ def theory_arrays(terms):
 
 
 class _Args:
-    """Keeps the marshalled arrays alive for one call."""
+    """Keeps the marshalled arrays alive for one call.  Asymmetry problems (forward /
+    backward pairs) enter as their asymmetry values and weights, computed here by
+    oracle_asymmetry, with the decay envelope off."""
 
     def __init__(self, prob):
-        self.data = np.ascontiguousarray(prob.counts, dtype=np.float64)
+        if hasattr(prob, "forward"):
+            self.data, self.weight = asymmetry(prob.forward, prob.backward, prob.alpha, prob.bkg_f, prob.bkg_b)
+            envelope = 0
+        else:
+            self.data = np.ascontiguousarray(prob.counts, dtype=np.float64)
+            self.weight = None
+            envelope = 1
         H, B = self.data.shape
         self.t0 = np.ascontiguousarray(prob.t0, dtype=np.float64).reshape(H)
         self.nprim, self.kind, self.slot = theory_arrays(prob.terms)
@@ -125,14 +135,30 @@ class _Args:
         self.consts = np.ascontiguousarray(
             prob.consts if len(prob.consts) else np.zeros(1), dtype=np.float64)
         lo, hi = prob.fit_range_us
-        P = ctypes.POINTER
         self.args = [
             _ptr(self.data, ctypes.c_double), H, B, _ptr(self.t0, ctypes.c_double),
             float(prob.bin_width_ns), float(lo), float(hi), len(prob.terms),
             _ptr(self.nprim, ctypes.c_int32), _ptr(self.kind, ctypes.c_int32),
             _ptr(self.slot, ctypes.c_int32), _ptr(self.map, ctypes.c_int32), self.map.shape[1],
-            _ptr(self.consts, ctypes.c_double), len(prob.consts), int(prob.nparams)]
-        del P
+            _ptr(self.consts, ctypes.c_double), len(prob.consts), int(prob.nparams),
+            None if self.weight is None else _ptr(self.weight, ctypes.c_double), envelope]
+
+
+def asymmetry(forward, backward, alpha, bkg_f, bkg_b):
+    """(a, w) [H][B]: asymmetry of forward / backward pairs and its chi^2 weight 1/sigma_a^2
+    (oracle_asymmetry)."""
+    F = np.ascontiguousarray(forward, dtype=np.float64)
+    Bk = np.ascontiguousarray(backward, dtype=np.float64)
+    H, B = F.shape
+    al = np.ascontiguousarray(alpha, dtype=np.float64).reshape(H)
+    bf = np.ascontiguousarray(bkg_f, dtype=np.float64).reshape(H)
+    bb = np.ascontiguousarray(bkg_b, dtype=np.float64).reshape(H)
+    a = np.zeros((H, B))
+    w = np.zeros((H, B))
+    _load().oracle_asymmetry(_ptr(F, ctypes.c_double), _ptr(Bk, ctypes.c_double), H, B, _ptr(al, ctypes.c_double),
+                             _ptr(bf, ctypes.c_double), _ptr(bb, ctypes.c_double), _ptr(a, ctypes.c_double),
+                             _ptr(w, ctypes.c_double))
+    return a, w
 
 
 def primitive(kind: str, p0: float, p1: float, t: float) -> float:

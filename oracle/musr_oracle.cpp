@@ -33,6 +33,17 @@
 //   * Local slot 0 is N0, slot 1 is Nbkg; terms reference any slot.
 //   * MLE with N <= 0 in a bin with d > 0 is +infinity (status 1).
 //
+// Asymmetry data (the form A(t) of Eq. asymmetry is measured directly): a forward /
+// backward histogram pair (F, B) with relative efficiency alpha and constant backgrounds
+// gives, with f = F - bkg_F and b = B - bkg_B,
+//     a = (f - alpha b) / (f + alpha b),
+//     sigma_a^2 = 4 alpha^2 (b^2 var F + f^2 var B) / (f + alpha b)^4
+// (first-order propagation of Poisson errors, each count's variance read as
+// max(count, 1) like Eq. chisq's d_err^2), weight w = 1 / sigma_a^2, and w = 0 where
+// f + alpha b <= 0.  The model of asymmetry data drops the decay envelope:
+//     T(t) = N0 A(t) + Nbkg   (N0 a scale, usually the constant 1; Nbkg a baseline),
+// and the cost is chi^2 = sum w (a - T)^2.  -2lnL is not defined for it (status 2).
+//
 // Summation: every sum over bins is Neumaier-compensated, in bin order
 // (histogram-major), so that the oracle's own rounding stays far below the
 // 1e-12 relative tolerance used against the GPU path.
@@ -95,7 +106,9 @@ struct Theory {
 };
 
 struct Problem {
-  const double* data;  // [H][B], histogram-major
+  const double* data;  // [H][B], histogram-major (counts, or asymmetry values)
+  const double* weight;  // [H][B] chi^2 weights of asymmetry data; nullptr for counts
+  int envelope;          // 1: Eq. positron_histo; 0: asymmetry model N0 A + Nbkg
   int H;
   int64_t B;
   const double* t0;  // [H], in bins
@@ -203,15 +216,18 @@ T model(const Problem& pb, const T* x, int h, double t) {
   }
   T N0 = slot_value(pb, x, h, 0);
   T Nbkg = slot_value(pb, x, h, 1);
+  if (!pb.envelope) return N0 * A + Nbkg;
   return N0 * std::exp(-t / kTauMu) * (1.0 + A) + Nbkg;
 }
 
 // One bin's contribution to Eq. chisq (mode 0) or Eq. log-likelihood (mode 1).
+// w >= 0 is the given chi^2 weight of asymmetry data (w < 0: counts).
 // Sets *bad when the likelihood is undefined (N <= 0 where d > 0).
 template <class T>
-T bin_cost(int mode, double d, const T& N, bool* bad) {
+T bin_cost(int mode, double d, double w, const T& N, bool* bad) {
   if (mode == 0) {
     T r = d - N;
+    if (w >= 0.0) return w * r * r;
     return r * r / std::fmax(d, 1.0);
   }
   if (d > 0.0) {
@@ -224,17 +240,23 @@ T bin_cost(int mode, double d, const T& N, bool* bad) {
   return 2.0 * (N - d);
 }
 
+// The chi^2 weight of bin n of histogram h: given for asymmetry data, else -1.
+inline double bin_weight(const Problem& pb, int h, int64_t n) {
+  return pb.weight ? pb.weight[static_cast<int64_t>(h) * pb.B + n] : -1.0;
+}
+
 template <class T>
 int cost_value(const Problem& pb, const T* x, int mode, T* out) {
   typename AccFor<T>::type acc;
   bool bad = false;
+  if (pb.weight && mode != 0) return 2;
   for (int h = 0; h < pb.H; ++h) {
     const double* row = pb.data + static_cast<int64_t>(h) * pb.B;
     for (int64_t n = 0; n < pb.B; ++n) {
       double t = bin_time(pb, h, n);
       if (!in_fit(pb, t)) continue;
       T N = model(pb, x, h, t);
-      acc.add(bin_cost(mode, row[n], N, &bad));
+      acc.add(bin_cost(mode, row[n], bin_weight(pb, h, n), N, &bad));
     }
   }
   if (bad) {
@@ -249,7 +271,7 @@ int cost_value(const Problem& pb, const T* x, int mode, T* out) {
 // respect to every local slot, through the product rule of each term.
 double model_and_slot_derivs(const Problem& pb, const double* x, int h, double t, double* dslot) {
   const double N0 = slot_value(pb, x, h, 0);
-  const double E = std::exp(-t / kTauMu);
+  const double E = pb.envelope ? std::exp(-t / kTauMu) : 1.0;
   std::fill(dslot, dslot + pb.nslots, 0.0);
   double A = 0.0;
   for (int k = 0; k < pb.th.nterms; ++k) {
@@ -277,6 +299,11 @@ double model_and_slot_derivs(const Problem& pb, const double* x, int h, double t
       if (nslots_of(kind) == 2) dslot[sl[1]] += N0 * E * d1 * rest;
     }
   }
+  if (!pb.envelope) {  // asymmetry model N0 A + Nbkg
+    dslot[0] += A;
+    dslot[1] += 1.0;
+    return N0 * A + slot_value(pb, x, h, 1);
+  }
   dslot[0] += E * (1.0 + A);
   dslot[1] += 1.0;
   return N0 * E * (1.0 + A) + slot_value(pb, x, h, 1);
@@ -292,6 +319,7 @@ int cost_grad(const Problem& pb, const double* x, int mode, double* value, doubl
   std::vector<Neumaier> g(pb.P), gs(pb.P);
   std::vector<double> dslot(pb.nslots);
   bool bad = false;
+  if (pb.weight && mode != 0) return 2;
   for (int h = 0; h < pb.H; ++h) {
     const double* row = pb.data + static_cast<int64_t>(h) * pb.B;
     for (int64_t n = 0; n < pb.B; ++n) {
@@ -300,7 +328,12 @@ int cost_grad(const Problem& pb, const double* x, int mode, double* value, doubl
       double d = row[n];
       double N = model_and_slot_derivs(pb, x, h, t, dslot.data());
       double W;  // dcost / dN for this bin
-      if (mode == 0) {
+      const double w = bin_weight(pb, h, n);
+      if (mode == 0 && w >= 0.0) {  // asymmetry data: the given weight
+        double r = d - N;
+        acc.add(w * r * r);
+        W = -2.0 * w * r;
+      } else if (mode == 0) {
         double r = d - N;
         acc.add(r * r / std::fmax(d, 1.0));
         W = -2.0 * r / std::fmax(d, 1.0);
@@ -344,6 +377,7 @@ int gauss_newton(const Problem& pb, const double* x, int mode, double* gn) {
   const int P = pb.P;
   std::vector<Neumaier> acc(static_cast<size_t>(P) * P);
   std::vector<double> dslot(pb.nslots), J(P);
+  if (pb.weight && mode != 0) return 2;
   for (int h = 0; h < pb.H; ++h) {
     const double* row = pb.data + static_cast<int64_t>(h) * pb.B;
     for (int64_t n = 0; n < pb.B; ++n) {
@@ -352,7 +386,10 @@ int gauss_newton(const Problem& pb, const double* x, int mode, double* gn) {
       double d = row[n];
       double N = model_and_slot_derivs(pb, x, h, t, dslot.data());
       double c2;
-      if (mode == 0) {
+      const double w = bin_weight(pb, h, n);
+      if (mode == 0 && w >= 0.0) {
+        c2 = 2.0 * w;
+      } else if (mode == 0) {
         c2 = 2.0 / std::fmax(d, 1.0);
       } else if (d > 0.0) {
         if (N <= 0.0) {
@@ -383,9 +420,11 @@ int gauss_newton(const Problem& pb, const double* x, int mode, double* gn) {
 Problem make_problem(const double* data, int H, int64_t B, const double* t0, double bin_width_ns,
                      double lo, double hi, int nterms, const int32_t* nprim, const int32_t* kind,
                      const int32_t* slot, const int32_t* map, int nslots, const double* consts,
-                     int nconsts, int P) {
+                     int nconsts, int P, const double* weight, int envelope) {
   Problem pb;
   pb.data = data;
+  pb.weight = weight;
+  pb.envelope = envelope;
   pb.H = H;
   pb.B = B;
   pb.t0 = t0;
@@ -415,9 +454,11 @@ double inf_norm(const std::vector<double>& v) {
 #define ORACLE_PROBLEM_ARGS                                                                  \
   const double *data, int H, int64_t B, const double *t0, double bin_width_ns, double lo,   \
       double hi, int nterms, const int32_t *nprim, const int32_t *kind, const int32_t *slot, \
-      const int32_t *map, int nslots, const double *consts, int nconsts, int P
-#define ORACLE_PROBLEM \
-  make_problem(data, H, B, t0, bin_width_ns, lo, hi, nterms, nprim, kind, slot, map, nslots, consts, nconsts, P)
+      const int32_t *map, int nslots, const double *consts, int nconsts, int P, const double *weight,  \
+      int envelope
+#define ORACLE_PROBLEM                                                                                  \
+  make_problem(data, H, B, t0, bin_width_ns, lo, hi, nterms, nprim, kind, slot, map, nslots, consts, nconsts, P, \
+               weight, envelope)
 
 extern "C" {
 
@@ -594,6 +635,26 @@ int oracle_fit(ORACLE_PROBLEM_ARGS, int mode, const double* x0, const double* fd
   *f_out = f;
   *iters_out = it;
   return status;
+}
+
+// Asymmetry a and chi^2 weight w of npairs forward / backward histogram pairs (see the
+// header): F, B, a, w are [npairs][nbins]; alpha, bkg_f, bkg_b are [npairs].
+void oracle_asymmetry(const double* F, const double* B, int npairs, int64_t nbins, const double* alpha,
+                      const double* bkg_f, const double* bkg_b, double* a, double* w) {
+  for (int k = 0; k < npairs; ++k)
+    for (int64_t n = 0; n < nbins; ++n) {
+      const int64_t i = static_cast<int64_t>(k) * nbins + n;
+      const double f = F[i] - bkg_f[k], b = B[i] - bkg_b[k], al = alpha[k];
+      const double D = f + al * b;
+      if (!(D > 0.0)) {
+        a[i] = 0.0;
+        w[i] = 0.0;
+        continue;
+      }
+      a[i] = (f - al * b) / D;
+      const double var = 4.0 * al * al * (b * b * std::fmax(F[i], 1.0) + f * f * std::fmax(B[i], 1.0)) / (D * D * D * D);
+      w[i] = var > 0.0 ? 1.0 / var : 0.0;
+    }
 }
 
 // Neumaier-compensated sum of n doubles, exposed so that the summation itself

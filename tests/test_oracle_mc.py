@@ -80,3 +80,27 @@ def test_time_offset_t0_recovered():
                    np.zeros(0), 6, np.array([3000.0, 2.0, 0.25, 0.5, 5.0, 30.0]), base.names, "t0")
     z = _pulls(p, 1)
     assert np.all(np.abs(z) < 4.5), dict(zip(p.names, np.round(z, 2)))
+
+
+def test_asymmetry_fit_recovers_truth():
+    """A chi^2 fit of the asymmetry of simulated forward / backward pairs (the backward
+    detector 15 % less efficient, alpha = 1 / 0.85, background subtracted) lands within a
+    few sigma of the simulated truth."""
+    p = mi.asym_tf(npairs=2, nbins=1600, bin_width_ns=5.0, seed=106, n0=3000.0)
+    z = _pulls(p, 0)
+    assert np.all(np.abs(z) < 4.5), dict(zip(p.names, np.round(z, 2)))
+
+
+def test_asymmetry_pulls_have_unit_spread():
+    """Over independent seeds the pulls of the asymmetry fit's amplitude and rate have mean ~ 0
+    and spread ~ 1: the weights are the inverse variances of the asymmetry (a weight off by a
+    constant factor would scale the spread by its square root)."""
+    zs = []
+    for seed in range(14):
+        p = mi.asym_tf(npairs=1, nbins=1000, bin_width_ns=6.0, seed=300 + seed, n0=1500.0)
+        z = _pulls(p, 0)
+        zs.append([z[0], z[1]])  # A0, sigma
+    zs = np.array(zs)
+    assert np.all(np.abs(zs.mean(axis=0)) < 3.0 / np.sqrt(len(zs)) + 0.25)
+    sd = zs.std(axis=0, ddof=1)
+    assert np.all((sd > 0.5) & (sd < 1.6)), sd

@@ -44,6 +44,15 @@ MUTANTS = {
     "Lorentzian KT derivative": ("*d0 = (2.0 / 3.0) * t * std::exp(-u) * (u - 2.0);",
                                  "*d0 = (2.0 / 3.0) * t * std::exp(-u) * (u - 3.0);"),
     "Gauss-Newton weight of -2lnL": ("        c2 = 2.0 * d / (N * N);", "        c2 = 2.0 / N;"),
+    "asymmetry variance drops the 4": ("const double var = 4.0 * al * al *", "const double var = al * al *"),
+    "asymmetry alpha on the forward count": ("a[i] = (f - al * b) / D;", "a[i] = (al * f - b) / D;"),
+    "asymmetry variances exchanged": ("(b * b * std::fmax(F[i], 1.0) + f * f * std::fmax(B[i], 1.0))",
+                                      "(b * b * std::fmax(B[i], 1.0) + f * f * std::fmax(F[i], 1.0))"),
+    "asymmetry model keeps the envelope": ("  if (!pb.envelope) return N0 * A + Nbkg;\n", ""),
+    "asymmetry slot derivatives keep the envelope": ("const double E = pb.envelope ? std::exp(-t / kTauMu) : 1.0;",
+                                                     "const double E = std::exp(-t / kTauMu);"),
+    "asymmetry weight missing from the gradient": ("        W = -2.0 * w * r;", "        W = -2.0 * r;"),
+    "asymmetry scale derivative": ("    dslot[0] += A;", "    dslot[0] += 1.0 + A;"),
     "Gauss-Newton weight of chi^2": ("        c2 = 2.0 / std::fmax(d, 1.0);", "        c2 = 1.0 / std::fmax(d, 1.0);"),
 }
 

@@ -377,3 +377,114 @@ def test_gauss_newton_of_constant_model_closed_form():
     assert oracle.gauss_newton(p, np.array([c]), CHI2)[0, 0] == pytest.approx(
         np.sum(2.0 / np.maximum(d, 1.0)), rel=1e-14)
     assert oracle.gauss_newton(p, np.array([c]), MLE)[0, 0] == pytest.approx(np.sum(2.0 * d / c**2), rel=1e-14)
+
+
+# ------------------------------------------------------------------------------------------
+# Asymmetry data: forward / backward pairs, a = (f - alpha b) / (f + alpha b)
+# ------------------------------------------------------------------------------------------
+
+def _asym(F, Bk, alpha, bkg_f, bkg_b, terms, mp, nparams, consts=(), bin_width_ns=1.0, fit=(0.0, 1e9)):
+    from musr_inputs import AsymmetryProblem
+    F = np.atleast_2d(np.asarray(F, dtype=np.float64))
+    Bk = np.atleast_2d(np.asarray(Bk, dtype=np.float64))
+    H = F.shape[0]
+    return AsymmetryProblem(F, Bk, np.asarray(alpha, float).reshape(H), np.asarray(bkg_f, float).reshape(H),
+                            np.asarray(bkg_b, float).reshape(H), np.zeros(H), bin_width_ns, fit, terms,
+                            np.atleast_2d(np.asarray(mp, np.int32)), np.asarray(consts, dtype=np.float64), nparams,
+                            np.zeros(nparams), [f"p{i}" for i in range(nparams)])
+
+
+def test_asymmetry_of_an_exact_pair():
+    """A pair built from an asymmetry T (F = K (1 + T) + bkg_F, B = K (1 - T) / alpha + bkg_B)
+    gives a = T to rounding: the backgrounds are subtracted and alpha scales the backward
+    count.  A bin without signal (f + alpha b <= 0) gets weight 0.  Catches alpha on the
+    wrong count, a sign flip and a background not subtracted."""
+    rng = np.random.default_rng(3)
+    T = rng.uniform(-0.6, 0.6, size=(2, 500))
+    K = rng.uniform(50.0, 5000.0, size=(2, 500))
+    alpha, bf, bb = np.array([1.3, 0.8]), np.array([4.0, 0.5]), np.array([2.5, 7.0])
+    F = K * (1.0 + T) + bf[:, None]
+    Bk = K * (1.0 - T) / alpha[:, None] + bb[:, None]
+    a, w = oracle.asymmetry(F, Bk, alpha, bf, bb)
+    assert np.max(np.abs(a - T)) < 1e-13
+    assert np.all(w > 0.0)
+    a0, w0 = oracle.asymmetry(np.array([[4.0, 3.0]]), np.array([[2.5, 1.0]]), [1.3], [4.0], [2.5])
+    assert w0[0, 0] == 0.0 and w0[0, 1] == 0.0
+
+
+def test_asymmetry_weight_is_the_inverse_poisson_variance():
+    """1/w at the expected counts equals the variance of the asymmetry over Poisson draws of
+    the pair (first-order error propagation; at these counts the higher orders are below
+    0.1 %).  Catches a dropped factor 4 or alpha^2, the forward and backward variances
+    exchanged, and background-subtracted counts used as the variances."""
+    rng = np.random.default_rng(11)
+    for lf, lb, al, bf, bb in ((9000.0, 4000.0, 1.3, 300.0, 150.0), (2500.0, 6000.0, 0.7, 0.0, 900.0)):
+        n = 400000
+        Fs = rng.poisson(lf, n).astype(np.float64)[None, :]
+        Bs = rng.poisson(lb, n).astype(np.float64)[None, :]
+        a, _ = oracle.asymmetry(Fs, Bs, [al], [bf], [bb])
+        _, w = oracle.asymmetry(np.array([[lf]]), np.array([[lb]]), [al], [bf], [bb])
+        assert np.var(a) * w[0, 0] == pytest.approx(1.0, abs=0.015), (lf, lb, np.var(a) * w[0, 0])
+
+
+def test_asymmetry_constant_data_and_baseline_optimum():
+    """Constant asymmetry data are fitted exactly by a constant amplitude with scale 1 and
+    baseline 0 (chi^2 = 0 at amplitude = the data value), which only holds when the model of
+    asymmetry data carries no decay envelope; with a baseline alone the optimum is the
+    weighted mean sum(w a) / sum(w).  -2lnL is refused for asymmetry data (status 2)."""
+    rng = np.random.default_rng(13)
+    K = rng.uniform(200.0, 900.0, size=(2, 600))
+    al = np.array([1.1, 0.9])
+    F = K * 1.3
+    Bk = K * 0.7 / al[:, None]
+    p = _asym(F, Bk, al, [0.0, 0.0], [0.0, 0.0], [[("AMP", (2,))]], [[-1, -2, 0], [-1, -2, 0]], 1,
+              consts=(1.0, 0.0), bin_width_ns=20.0)
+    r = oracle.fit(p, np.array([0.1]), CHI2)
+    assert r["status"] == 0 and r["x"][0] == pytest.approx(0.3, abs=1e-10) and r["f"] < 1e-18
+    assert oracle.cost(p, np.array([0.3]), MLE)[3] == 2
+    Fn = rng.poisson(500.0, size=(2, 800)).astype(float)
+    Bn = rng.poisson(450.0, size=(2, 800)).astype(float)
+    q = _asym(Fn, Bn, al, [3.0, 1.0], [2.0, 4.0], [], [[-1, 0], [-1, 0]], 1, consts=(1.0,), bin_width_ns=20.0)
+    a, w = oracle.asymmetry(Fn, Bn, al, [3.0, 1.0], [2.0, 4.0])
+    r = oracle.fit(q, np.array([0.0]), CHI2)
+    assert r["status"] == 0 and r["x"][0] == pytest.approx(np.sum(w * a) / np.sum(w), rel=1e-9)
+
+
+def test_asymmetry_gradient_matches_complex_step():
+    """The analytic gradient of the asymmetry chi^2 equals the complex-step derivative, with
+    the scale and the baseline fitted too.  Catches the envelope left in the slot
+    derivatives and a weight missing from the gradient."""
+    import musr_inputs as mi
+    p = mi.asym_tf(npairs=2, nbins=500, bin_width_ns=16.0, seed=27, n0=300.0)
+    terms = [[("AMP", (2,)), ("GAUSS", (3,)), ("TFCOS", (4, 5))], [("AMP", (6,)), ("EXP", (7,))]]
+    rows = [[0, 1, 2, 3, 4, 5, 6, 7], [0, 1, 2, 3, 4, 8, 6, 7]]
+    import dataclasses
+    q = dataclasses.replace(p, terms=terms, map=np.array(rows, np.int32), consts=np.zeros(0), nparams=9,
+                            truth=np.zeros(9), names=[f"p{i}" for i in range(9)])
+    x = np.array([0.95, 0.01, 0.2, 0.45, 3.05, 21.0, 0.04, 0.3, 108.0])
+    v, g, gs, st = oracle.cost(q, x, CHI2)
+    assert st == 0 and v > 0
+    for i in range(q.nparams):
+        e = np.zeros(q.nparams)
+        e[i] = 1.0
+        cs = oracle.cost_cstep(q, x, e, CHI2)
+        assert abs(cs - g[i]) <= 1e-11 * gs[i] + 1e-300, (i, cs, g[i], gs[i])
+
+
+def test_asymmetry_gauss_newton_equals_hessian_when_data_equal_model():
+    """Pairs built from the asymmetry model itself: there the Gauss-Newton matrix (weight 2 w)
+    is the exact Hessian of the chi^2, which central differences of the gradient measure."""
+    import dataclasses
+    import musr_inputs as mi
+    p = mi.asym_tf(npairs=2, nbins=300, bin_width_ns=25.0, seed=28, n0=300.0)
+    t = (np.arange(p.B) - p.t0[0]) * p.bin_width_ns / 1000.0
+    T = np.array([[oracle.model(p, p.truth, h, tt) for tt in t] for h in range(p.H)])
+    K = 800.0
+    F = K * (1.0 + T) + p.bkg_f[:, None]
+    Bk = K * (1.0 - T) / p.alpha[:, None] + p.bkg_b[:, None]
+    q = dataclasses.replace(p, forward=F, backward=Bk)
+    assert oracle.cost(q, p.truth, CHI2)[0] < 1e-20
+    Hg = oracle.gauss_newton(q, p.truth, CHI2)
+    Hc = oracle.hessian(q, p.truth, CHI2)
+    scale = np.sqrt(np.outer(np.diag(Hg), np.diag(Hg)))
+    assert np.max(np.abs(Hg - Hc) / scale) < 1e-6
