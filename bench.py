@@ -375,9 +375,10 @@ def run_ours(args, rank, world, local_rank):
                 "algorithmic_bytes": algo_bytes,
                 "hbm_frac": algo_bytes / t_kernel / 1e9 / float(peaks.get("hbm_gbs", 6800.0))}
 
-    fits = None
+    fits = asym = None
     if not args.no_fits and rank == 0:
         fits = _fits(p, ctx, B, mode)
+        asym = _asymmetry(B, flush, stream)
     serving = None
     if args.serving_requests > 0 and rank == 0:
         serving = _serving(B, args.serving_requests)
@@ -396,11 +397,48 @@ def run_ours(args, rank, world, local_rank):
                 "gpu_launches": args.steps, "wall_s_timed_region": t_wall,
                 "fp64_path": {"value": fp64_gbins, "unit": "Gbins/s", "split_speedup": value / world / fp64_gbins,
                               "max_rel_value_diff_split_vs_fp64": rel_err},
-                "fits": fits, "serving": serving, "cpu_baseline": cpu}
+                "fits": fits, "asymmetry": asym, "serving": serving, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _asymmetry(B, flush, stream, steps=10):
+    """Asymmetry-form fit of the paper's 16 detectors as 8 forward / backward pairs (81920
+    bins each): value+grad of the weighted chi^2 for 64 parameter vectors per launch,
+    SPLIT and FP64 (CUDA events on the launching stream, L2 flushed between launches)."""
+    import torch
+    import musr_inputs as mi
+    p = mi.asym_tf(npairs=8, nbins=81920, bin_width_ns=12800.0 / 81920, seed=31, n0=60.0)
+    X = mi.jitter(p.truth, NVEC, seed=5, lo=0.97, hi=1.03)
+    out = {"workload": "8 forward/backward pairs x 81920 bins (the 16 detectors of the paper's benchmark), "
+                       "chi^2 of the asymmetry, fused value+grad, 64 parameter vectors per launch",
+           "params": int(p.nparams)}
+    with torch.cuda.stream(stream):
+        with B.Context(p, cuda_stream=stream.cuda_stream) as ctx:
+            bins = ctx.bins_in_fit()
+            dx = torch.tensor(X, dtype=torch.float64, device="cuda")
+            do = torch.empty((NVEC, 1 + p.nparams), dtype=torch.float64, device="cuda")
+            res = {}
+            for prec, name in ((B.MUSR_SPLIT, "split"), (B.MUSR_FP64, "fp64")):
+                for _ in range(3):
+                    B.musr_eval_device(ctx.ctx, dx.data_ptr(), NVEC, 0, prec, True, do.data_ptr())
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(steps if prec == B.MUSR_SPLIT else 3)]
+                for a, b in ev:
+                    flush.zero_()
+                    a.record(stream)
+                    B.musr_eval_device(ctx.ctx, dx.data_ptr(), NVEC, 0, prec, True, do.data_ptr())
+                    b.record(stream)
+                torch.cuda.synchronize()
+                t = float(np.mean([a.elapsed_time(b) * 1e-3 for a, b in ev]))
+                out[f"{name}_gbins_per_s"] = bins * NVEC / t / 1e9
+                res[name] = do.cpu().numpy().copy()
+    out["split_speedup"] = out["split_gbins_per_s"] / out["fp64_gbins_per_s"]
+    out["max_rel_value_diff_split_vs_fp64"] = float(np.max(np.abs(res["split"][:, 0] - res["fp64"][:, 0]) /
+                                                           np.abs(res["fp64"][:, 0])))
+    return out
 
 
 def _fits(p, ctx, B, mode):

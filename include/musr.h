@@ -112,6 +112,28 @@ const char* musr_last_error(const musr_ctx* ctx);
 int musr_upload_histograms(musr_ctx* ctx, const void* counts, int dtype, int nhist, int64_t nbins,
                            const double* t0, double bin_width_ns, const double fit_range_us[2]);
 
+/* Uploads asymmetry data instead of histograms (the asymmetry A(t) of
+ * Eq. asymmetry measured directly): npairs forward / backward histogram pairs,
+ * forward and backward host arrays [npairs][nbins] in `dtype` (as for
+ * musr_upload_histograms), the relative efficiency alpha[npairs] > 0 and the
+ * constant backgrounds bkg_forward[npairs], bkg_backward[npairs] (counts per
+ * bin) of each pair.  On the device, with f = F - bkg_F and b = B - bkg_B,
+ *     a = (f - alpha b) / (f + alpha b),
+ *     w = 1 / sigma_a^2,  sigma_a^2 = 4 alpha^2 (b^2 max(F,1) + f^2 max(B,1))
+ *                                     / (f + alpha b)^4
+ * (first-order propagation of the Poisson errors of F and B), w = 0 where
+ * f + alpha b <= 0; a and w are kept in FP64.  The context then evaluates the
+ * asymmetry model T(t) = N0 A(t) + Nbkg (no decay envelope: local slot 0 is a
+ * scale, usually mapped to the constant 1, slot 1 a baseline) with the cost
+ * chi^2 = sum w (a - T)^2: mode MUSR_CHI2 only (MUSR_MLE gives MUSR_EINVAL);
+ * Gauss-Newton products at MUSR_FP64 precision only.  t0, bin_width_ns and
+ * fit_range_us as for musr_upload_histograms; counts are checked the same way.
+ * Replaces any previous data; theory and map must be (re)set after.
+ * Synchronous: the caller may reuse its arrays when it returns. */
+int musr_upload_asymmetry(musr_ctx* ctx, const void* forward, const void* backward, int dtype, int npairs,
+                          int64_t nbins, const double* t0, double bin_width_ns, const double fit_range_us[2],
+                          const double* alpha, const double* bkg_forward, const double* bkg_backward);
+
 /* As musr_upload_histograms, but BORROWS device memory the caller owns
  * (e.g. a torch tensor): d_counts points to [nhist][row_stride] FP32 or FP64
  * values on the context's device, 16-byte aligned, row_stride a multiple of 4

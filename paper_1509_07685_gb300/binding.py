@@ -29,7 +29,7 @@ MAX_PRIMS = 4
 # Every symbol include/musr.h declares (checked by the ABI test).
 EXPORTS = (
     "musr_ctx_create", "musr_ctx_destroy", "musr_last_error", "musr_upload_histograms",
-    "musr_upload_histograms_device", "musr_set_theory", "musr_set_map", "musr_eval",
+    "musr_upload_asymmetry", "musr_upload_histograms_device", "musr_set_theory", "musr_set_map", "musr_eval",
     "musr_eval_batch", "musr_eval_device", "musr_sync", "musr_bins_in_fit", "musr_gn_product",
     "musr_gauss_newton",
     "musr_launches_per_eval", "musr_eval_noalloc", "musr_fit", "musr_server_create",
@@ -90,6 +90,8 @@ def _declare(lib):
         "musr_ctx_destroy": ([vp], None),
         "musr_last_error": ([vp], ctypes.c_char_p),
         "musr_upload_histograms": ([vp, vp, ctypes.c_int, ctypes.c_int, i64, P(d), d, P(d)], ctypes.c_int),
+        "musr_upload_asymmetry": ([vp, vp, vp, ctypes.c_int, ctypes.c_int, i64, P(d), d, P(d), P(d), P(d), P(d)],
+                                  ctypes.c_int),
         "musr_upload_histograms_device": ([vp, vp, ctypes.c_int, ctypes.c_int, i64, i64, P(d), d, P(d)],
                                           ctypes.c_int),
         "musr_set_theory": ([vp, P(musr_term), ctypes.c_int], ctypes.c_int),
@@ -211,6 +213,28 @@ def musr_upload_histograms(ctx, counts: np.ndarray, t0: Sequence[float], bin_wid
     _check(ctx, load().musr_upload_histograms(ctx, counts.ctypes.data_as(ctypes.c_void_p), dtype,
                                               counts.shape[0], counts.shape[1], _dptr(t0),
                                               float(bin_width_ns), _dptr(fr)))
+
+
+def musr_upload_asymmetry(ctx, forward: np.ndarray, backward: np.ndarray, t0: Sequence[float], bin_width_ns: float,
+                          fit_range_us: Sequence[float], alpha: Sequence[float], bkg_forward: Sequence[float],
+                          bkg_backward: Sequence[float]) -> None:
+    F = np.ascontiguousarray(forward)
+    Bk = np.ascontiguousarray(backward, dtype=F.dtype)
+    if F.ndim != 2 or Bk.shape != F.shape:
+        raise ValueError("forward and backward must both be [npairs][nbins]")
+    dtype = {np.dtype(np.int32): MUSR_DTYPE_INT32, np.dtype(np.float32): MUSR_DTYPE_FP32,
+             np.dtype(np.float64): MUSR_DTYPE_FP64}.get(F.dtype)
+    if dtype is None:
+        raise TypeError("counts must be int32, float32 or float64")
+    H = F.shape[0]
+    t0 = np.ascontiguousarray(t0, dtype=np.float64).reshape(H)
+    fr = np.ascontiguousarray(fit_range_us, dtype=np.float64)
+    al = np.ascontiguousarray(alpha, dtype=np.float64).reshape(H)
+    bf = np.ascontiguousarray(bkg_forward, dtype=np.float64).reshape(H)
+    bb = np.ascontiguousarray(bkg_backward, dtype=np.float64).reshape(H)
+    _check(ctx, load().musr_upload_asymmetry(ctx, F.ctypes.data_as(ctypes.c_void_p), Bk.ctypes.data_as(ctypes.c_void_p),
+                                             dtype, H, F.shape[1], _dptr(t0), float(bin_width_ns), _dptr(fr),
+                                             _dptr(al), _dptr(bf), _dptr(bb)))
 
 
 def musr_upload_histograms_device(ctx, d_counts: int, dtype: int, nhist: int, nbins: int, row_stride: int,
@@ -339,8 +363,12 @@ class Context:
             self.configure(problem)
 
     def configure(self, problem) -> None:
-        musr_upload_histograms(self.ctx, problem.counts, problem.t0, problem.bin_width_ns,
-                               problem.fit_range_us)
+        if hasattr(problem, "forward"):  # asymmetry data (forward / backward pairs)
+            musr_upload_asymmetry(self.ctx, problem.forward, problem.backward, problem.t0, problem.bin_width_ns,
+                                  problem.fit_range_us, problem.alpha, problem.bkg_f, problem.bkg_b)
+        else:
+            musr_upload_histograms(self.ctx, problem.counts, problem.t0, problem.bin_width_ns,
+                                   problem.fit_range_us)
         musr_set_theory(self.ctx, problem.terms)
         musr_set_map(self.ctx, problem.map, problem.nparams, problem.consts)
         self.P = int(problem.nparams)

@@ -1,4 +1,4 @@
-// musr_counts.cu -- the device image of uploaded histograms (the measured counts d_n^j of
+// musr_counts.cu -- the device image of uploaded histograms and asymmetry data (the measured counts d_n^j of
 // Eq. chi2 and Eq. mlh, Section 4.1): the rows arrive from the host as they are, one row
 // per histogram at the device row stride; this kernel converts them in place to the stored
 // type, zeroes each row's padding and flags values the store cannot hold, so the host makes
@@ -79,7 +79,81 @@ __global__ void __launch_bounds__(256) prepare_shifted_kernel(const void* raw, v
   if (bad) *reinterpret_cast<volatile unsigned*>(flag) = seq;
 }
 
+// Asymmetry data from packed forward / backward rows (raw: F [nhist][nbins], then B; dtype
+// as uploaded) into a and w ([nhist][stride], FP64), row h moved left by shift[h] bins:
+//   f = F - bkg_f, b = B - bkg_b, D = f + alpha b,
+//   a = (f - alpha b) / D,  w = 1 / sigma_a^2,
+//   sigma_a^2 = 4 alpha^2 (b^2 max(F, 1) + f^2 max(B, 1)) / D^4
+// (first-order propagation of the Poisson errors of F and B), a = w = 0 where D <= 0 and
+// in the padding.  par holds alpha, bkg_f, bkg_b ([3][nhist]).  Every raw count is checked.
+template <int DTYPE>
+__global__ void __launch_bounds__(256) prepare_asymmetry_kernel(const void* raw, const int64_t* shift,
+                                                                const double* par, int nhist, int64_t nbins,
+                                                                int64_t stride, double* a, double* w,
+                                                                unsigned* flag, unsigned seq) {
+  using In = typename std::conditional<DTYPE == MUSR_DTYPE_INT32, int32_t,
+                                       typename std::conditional<DTYPE == MUSR_DTYPE_FP64, double, float>::type>::type;
+  const In* F = static_cast<const In*>(raw);
+  const In* Bk = F + static_cast<int64_t>(nhist) * nbins;
+  const int64_t total = static_cast<int64_t>(nhist) * stride, nraw = 2 * static_cast<int64_t>(nhist) * nbins;
+  const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t first = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  for (int64_t e = first; e < total; e += step) {
+    const int64_t h = e / stride, j = e - h * stride, n = j + shift[h];
+    double av = 0.0, wv = 0.0;
+    if (j < nbins && n < nbins) {
+      const double Fc = static_cast<double>(F[h * nbins + n]), Bc = static_cast<double>(Bk[h * nbins + n]);
+      const double al = par[h], f = Fc - par[nhist + h], b = Bc - par[2 * nhist + h];
+      const double D = f + al * b;
+      if (D > 0.0) {
+        av = (f - al * b) / D;
+        const double D2 = D * D;
+        const double var = 4.0 * al * al * (b * b * fmax(Fc, 1.0) + f * f * fmax(Bc, 1.0)) / (D2 * D2);
+        wv = var > 0.0 ? 1.0 / var : 0.0;
+      }
+    }
+    a[e] = av;
+    w[e] = wv;
+  }
+  bool bad = false;
+  for (int64_t e = first; e < nraw; e += step) {
+    const In v = F[e];  // F and B are contiguous
+    if (DTYPE == MUSR_DTYPE_INT32)
+      bad |= v >= (1 << 24) || v <= -(1 << 24);
+    else if (DTYPE == MUSR_DTYPE_FP32)
+      bad |= !(fabsf(static_cast<float>(v)) <= 3.4028234663852886e38f);
+    else
+      bad |= !(fabs(static_cast<double>(v)) <= 1.7976931348623157e308);
+  }
+  if (bad) *reinterpret_cast<volatile unsigned*>(flag) = seq;
+}
+
 }  // namespace
+
+int launch_prepare_asymmetry(const void* raw, const int64_t* shift, const double* par, int dtype, int nhist,
+                             int64_t nbins, int64_t stride, double* a, double* w, unsigned* flag, unsigned seq,
+                             int num_sms, void* stream_) {
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const int64_t total = static_cast<int64_t>(nhist) * stride;
+  if (total <= 0) return 0;
+  const int64_t want = (total + 255) / 256;
+  const int grid = static_cast<int>(want < 8LL * num_sms ? want : 8LL * num_sms);
+  switch (dtype) {
+    case MUSR_DTYPE_INT32:
+      prepare_asymmetry_kernel<MUSR_DTYPE_INT32>
+          <<<grid, 256, 0, stream>>>(raw, shift, par, nhist, nbins, stride, a, w, flag, seq);
+      break;
+    case MUSR_DTYPE_FP32:
+      prepare_asymmetry_kernel<MUSR_DTYPE_FP32>
+          <<<grid, 256, 0, stream>>>(raw, shift, par, nhist, nbins, stride, a, w, flag, seq);
+      break;
+    default:
+      prepare_asymmetry_kernel<MUSR_DTYPE_FP64>
+          <<<grid, 256, 0, stream>>>(raw, shift, par, nhist, nbins, stride, a, w, flag, seq);
+      break;
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
 
 int launch_prepare_counts_shifted(const void* raw, void* img, const int64_t* shift, int dtype, int nhist,
                                   int64_t nbins, int64_t stride, unsigned* flag, unsigned seq, int num_sms,

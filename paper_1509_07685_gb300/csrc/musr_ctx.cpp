@@ -274,6 +274,8 @@ int compile(musr_ctx* ctx, int prec, int var) {
   std::memset(&hs, 0, sizeof(hs));
   hs.counts = ctx->d_counts;
   hs.store = ctx->store;
+  hs.weights = ctx->asym ? static_cast<const double*>(ctx->weights_own.p) : nullptr;
+  hs.envelope = ctx->asym ? 0 : 1;
   hs.H = ctx->H;
   hs.stride = ctx->stride;
   hs.dt_us = ctx->dt_us;
@@ -294,7 +296,7 @@ int compile(musr_ctx* ctx, int prec, int var) {
   int group_cap = 1;
   if (prec == MUSR_SPLIT) {
     const char* why = musr::plan_split(ctx->terms.data(), hs.nterms, ctx->map.data(), H, ctx->nslots,
-                                       ctx->consts.data(), &hs);
+                                       ctx->consts.data(), &hs, !ctx->asym);
     if (why) {
       c.reason = why;
       c.planned = true;
@@ -591,6 +593,8 @@ int check_ready(musr_ctx* ctx, int mode, int prec) {
   if (mode != MUSR_CHI2 && mode != MUSR_MLE) return fail(ctx, MUSR_EINVAL, "mode must be MUSR_CHI2 or MUSR_MLE");
   if (prec != MUSR_FP64 && prec != MUSR_SPLIT)
     return fail(ctx, MUSR_EINVAL, "precision must be MUSR_FP64 or MUSR_SPLIT");
+  if (ctx->asym && mode != MUSR_CHI2)
+    return fail(ctx, MUSR_EINVAL, "asymmetry data have the chi^2 cost only (MUSR_CHI2)");
   if (prec == MUSR_SPLIT && !ctx->split_reason.empty())
     return fail(ctx, MUSR_EINVAL, "precision unavailable for this theory: " + ctx->split_reason);
   return MUSR_OK;
@@ -599,6 +603,7 @@ int check_ready(musr_ctx* ctx, int mode, int prec) {
 // Enqueues one launch of nvec evaluations reading d_params, writing d_out.
 int enqueue_eval(musr_ctx* ctx, int prec, int mode, int grad, int nvec, const double* d_params,
                  double* d_out, const double* d_dirs = nullptr) {
+  if (ctx->asym && prec == MUSR_SPLIT && mode == MUSR_CHI2) mode = 4;  // SPLIT kernels: weighted chi^2
   const int var = pick_variant(ctx, prec, nvec);
   const HistSet& hs = ctx->comp[prec][var].hs;
   if (hs.nitems == 0) {  // no bin in the fit range: cost 0, gradient 0
@@ -707,6 +712,7 @@ void musr_ctx_destroy(musr_ctx* ctx) {
     for (auto& c : pc) free_compiled(ctx, c);
   dfree(ctx, ctx->counts_own);
   dfree(ctx, ctx->upload_scratch);
+  dfree(ctx, ctx->weights_own);
   EvalBufs& ev = ctx->ev;
   dfree(ctx, ev.params);
   dfree(ctx, ev.out);
@@ -740,6 +746,8 @@ static int upload_common(musr_ctx* ctx, int nhist, int64_t nbins, const double* 
   ctx->check_flag = nullptr;
   dfree(ctx, ctx->upload_scratch);
   ctx->shift.clear();
+  ctx->asym = false;
+  dfree(ctx, ctx->weights_own);
   ctx->H = nhist;
   ctx->B = nbins;
   ctx->t0.assign(t0, t0 + nhist);
@@ -847,6 +855,8 @@ int musr::finish_upload_check(musr_ctx* ctx) {
   if (!bad) return MUSR_OK;
   drop_config(ctx);
   dfree(ctx, ctx->counts_own);
+  dfree(ctx, ctx->weights_own);
+  ctx->asym = false;
   ctx->d_counts = nullptr;
   return fail(ctx, MUSR_EINVAL,
               ctx->check_dtype == MUSR_DTYPE_INT32 ? "INT32 counts must satisfy |count| < 2^24 (exact in FP32)"
@@ -854,6 +864,73 @@ int musr::finish_upload_check(musr_ctx* ctx) {
 }
 
 extern "C" {
+
+int musr_upload_asymmetry(musr_ctx* ctx, const void* forward, const void* backward, int dtype, int npairs,
+                          int64_t nbins, const double* t0, double bin_width_ns, const double fit_range_us[2],
+                          const double* alpha, const double* bkg_forward, const double* bkg_backward) {
+  if (!ctx) return MUSR_EINVAL;
+  DeviceScope ds(ctx->device);
+  if (!forward || !backward) return fail(ctx, MUSR_EINVAL, "forward and backward must not be NULL");
+  if (!alpha || !bkg_forward || !bkg_backward)
+    return fail(ctx, MUSR_EINVAL, "alpha, bkg_forward and bkg_backward must not be NULL");
+  if (dtype != MUSR_DTYPE_INT32 && dtype != MUSR_DTYPE_FP32 && dtype != MUSR_DTYPE_FP64)
+    return fail(ctx, MUSR_EINVAL, "dtype must be MUSR_DTYPE_INT32, _FP32 or _FP64");
+  quiesce(ctx);
+  drop_config(ctx);
+  int rc = upload_common(ctx, npairs, nbins, t0, bin_width_ns, fit_range_us);
+  if (rc) return rc;
+  for (int h = 0; h < npairs; ++h)
+    if (!(alpha[h] > 0.0) || !std::isfinite(alpha[h]) || !std::isfinite(bkg_forward[h]) ||
+        !std::isfinite(bkg_backward[h]))
+      return fail(ctx, MUSR_EINVAL, "alpha must be finite and > 0, the backgrounds finite");
+  const int64_t stride = (nbins + kRowAlign - 1) / kRowAlign * kRowAlign;
+  const size_t esz = dtype == MUSR_DTYPE_FP64 ? 8 : 4;
+  const size_t row = static_cast<size_t>(nbins) * esz, H = static_cast<size_t>(npairs);
+  const size_t image = H * stride * sizeof(double);
+  if ((rc = dalloc(ctx, ctx->counts_own, image))) return rc;
+  if ((rc = dalloc(ctx, ctx->weights_own, image))) return rc;
+  // Scratch: the raw forward rows, the raw backward rows, the row shifts, alpha and the
+  // backgrounds; one kernel turns them into a and w on the device (FP64).
+  const size_t raw = (2 * row * H + 255) & ~size_t(255), o_par = raw + ((8 * H + 255) & ~size_t(255));
+  if ((rc = dalloc(ctx, ctx->upload_scratch, o_par + 3 * sizeof(double) * H))) return rc;
+  char* sp = static_cast<char*>(ctx->upload_scratch.p);
+  ctx->shift = grid_shifts(ctx);
+  ctx->asym_par.assign(alpha, alpha + H);
+  ctx->asym_par.insert(ctx->asym_par.end(), bkg_forward, bkg_forward + H);
+  ctx->asym_par.insert(ctx->asym_par.end(), bkg_backward, bkg_backward + H);
+  cudaStream_t st = ctx->setup_stream ? ctx->setup_stream : cudaStreamPerThread;
+  cudaError_t e = cudaMemcpyAsync(sp, forward, row * H, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sp + row * H, backward, row * H, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sp + raw, ctx->shift.data(), 8 * H, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(sp + o_par, ctx->asym_par.data(), 3 * sizeof(double) * H, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(asymmetry pairs)");
+  CheckFlag& flag = tl_flag;
+  if (!flag.ready()) return cuda_fail(ctx, cudaGetLastError(), "cudaHostAlloc(check flag)");
+  const unsigned seq = flag.next();
+  if (launch_prepare_asymmetry(sp, reinterpret_cast<const int64_t*>(sp + raw),
+                               reinterpret_cast<const double*>(sp + o_par), dtype, npairs, nbins, stride,
+                               static_cast<double*>(ctx->counts_own.p), static_cast<double*>(ctx->weights_own.p),
+                               flag.dev, seq, ctx->num_sms, st))
+    return cuda_fail(ctx, cudaGetLastError(), "prepare_asymmetry launch");
+  for (int h = 0; h < npairs; ++h) {  // the device grid (see musr_upload_histograms)
+    ctx->t0[h] -= static_cast<double>(ctx->shift[h]);
+    ctx->nlo[h] -= static_cast<int>(ctx->shift[h]);
+    ctx->nhi[h] -= static_cast<int>(ctx->shift[h]);
+  }
+  ctx->check_flag = flag.host;
+  ctx->check_seq = seq;
+  ctx->check_dtype = dtype;
+  ctx->d_counts = ctx->counts_own.p;
+  ctx->store = kStoreF64;
+  ctx->stride = stride;
+  ctx->asym = true;
+  ctx->have_hist = true;
+  if (ctx->setup_stream) return MUSR_OK;  // the caller waits and reads the check
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "prepare_asymmetry");
+  return finish_upload_check(ctx);
+}
 
 int musr_upload_histograms_device(musr_ctx* ctx, const void* d_counts, int dtype, int nhist, int64_t nbins,
                                   int64_t row_stride, const double* t0, double bin_width_ns,
@@ -948,7 +1025,7 @@ int musr_set_map(musr_ctx* ctx, const int32_t* map, int nslots, int nparams, con
     HistSet probe;
     std::memset(&probe, 0, sizeof(probe));
     const char* why = musr::plan_split(ctx->terms.data(), static_cast<int>(ctx->terms.size()), ctx->map.data(),
-                                       ctx->H, ctx->nslots, ctx->consts.data(), &probe);
+                                       ctx->H, ctx->nslots, ctx->consts.data(), &probe, !ctx->asym);
     ctx->split_reason = why ? why : "";
   }
   ctx->have_map = true;
@@ -1014,6 +1091,8 @@ int musr_gn_product(musr_ctx* ctx, const double* params, int nparams, const doub
   DeviceScope ds(ctx->device);
   int rc = check_ready(ctx, mode, precision);
   if (rc) return rc;
+  if (ctx->asym && precision == MUSR_SPLIT)
+    return fail(ctx, MUSR_EINVAL, "Gauss-Newton products of asymmetry data run at MUSR_FP64 precision");
   if (ndir < 1) return fail(ctx, MUSR_EINVAL, "ndir must be >= 1");
   if (nparams != ctx->P) return fail(ctx, MUSR_EINVAL, "nparams does not match the map");
   if (!params || !dirs || !out) return fail(ctx, MUSR_EINVAL, "params, dirs and out must not be NULL");

@@ -145,6 +145,10 @@ struct musr_ctx {
   // Device check of the last histogram upload, not read yet (see finish_upload_check).
   const unsigned* check_flag = nullptr;
   musr::DevBuf upload_scratch;     // packed rows of a shifted upload, until the check is read
+  // asymmetry data (musr_upload_asymmetry): d_counts holds a, weights_own the chi^2 weights
+  bool asym = false;
+  musr::DevBuf weights_own;
+  std::vector<double> asym_par;    // alpha, bkg_f, bkg_b of the pairs, the source of their copy
   std::vector<int64_t> shift;      // whole bins each histogram's row moved left on the device
   unsigned check_seq = 0;
   int check_dtype = 0;

@@ -174,6 +174,7 @@ struct ChunkCache {
   double t0;
   int row[kGroupMax];
   const void* rowp[kGroupMax];       // first count of each histogram's row
+  const double* roww[kGroupMax];     // first chi^2 weight of the row (asymmetry data), else nullptr
   double loc[kGroupMax][kMaxSlots];  // local slot values (FP64)
   double ldir[kGroupMax][kMaxSlots]; // local slot components of a Gauss-Newton direction (else 0)
   // SPLIT: [Nbkg, Gam_0 .. Gam_{M-1}] of each histogram (16-byte rows: vector loads)
@@ -304,6 +305,7 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
       cc.row[hl] = h;
       const size_t esz = hs.store == kStoreF64 ? sizeof(double) : sizeof(float);
       cc.rowp[hl] = static_cast<const char*>(hs.counts) + static_cast<size_t>(h) * hs.stride * esz;
+      cc.roww[hl] = hs.weights ? hs.weights + static_cast<size_t>(h) * hs.stride : nullptr;
     }
   }
   __syncthreads();
@@ -317,7 +319,7 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
     for (int i = 0; i < kGamStride; ++i) g[i] = 0.0;
     const double N0 = cc.loc[hl][0];
     g[0] = cc.loc[hl][1];
-    g[1] = N0;
+    g[1] = hs.envelope ? N0 : 0.0;  // the basis function E carries the 1 of (1 + A)
 #pragma unroll
     for (int k = 0; k < kMaxTerms; ++k) {
       double c = 1.0, sn = 0.0;
@@ -352,7 +354,7 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
       constexpr double kDeg = kTwoPi / 360.0;
       const double vN0 = cc.ldir[hl][0];
       gd[0] = cc.ldir[hl][1];
-      gd[1] = vN0;
+      gd[1] = hs.envelope ? vN0 : 0.0;
       if (Bs::MERGED) {
         const double vph = cc.ldir[hl][hs.canon[0].phi_slot] * kDeg;
         const double c = cc.cph[hl][0], sn = cc.sph[hl][0];
@@ -402,7 +404,9 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
                          ? static_cast<float>((2.0 / 3.0) * cc.loc[0][ct.kt_slot] * cc.ldir[0][ct.kt_slot])
                          : (ct.kind == kTermLKT ? static_cast<float>((2.0 / 3.0) * cc.ldir[0][ct.kt_slot]) : 0.0f);
       }
-      cc.ca[k] = kLog2eF * (static_cast<float>(1.0 / kTauMuUs) + lam);
+      // the term's exponent carries the decay envelope E = exp(-t / tau_mu) (none for the
+      // asymmetry model)
+      cc.ca[k] = kLog2eF * ((hs.envelope ? static_cast<float>(1.0 / kTauMuUs) : 0.0f) + lam);
       cc.cb[k] = kLog2eF * 0.5f * S;
       if (ct.kind == kTermKT) {
         const float D = static_cast<float>(cc.loc[0][ct.kt_slot]);
@@ -430,7 +434,8 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
       }
     }
   } else if (tid == 64) {
-    cc.aE = static_cast<float>(1.4426950408889634 / kTauMuUs);
+    // log2(e) / tau_mu: E = 2^(-aE t); without the decay envelope E = 1
+    cc.aE = hs.envelope ? static_cast<float>(1.4426950408889634 / kTauMuUs) : 0.0f;
     cc.dt = static_cast<float>(dt);
   }
   __syncthreads();
@@ -489,7 +494,9 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Smem& sm)
     // Bin time (Section 4.1: t = n dt, shifted by t0).
     const double t = (static_cast<double>(n) - t0) * dt;
     const double d = store == kStoreF64 ? rowd[n] : static_cast<double>(rowf[n]);
-    const double E = exp(-t / kTauMuUs);
+    const double E = hs.envelope ? exp(-t / kTauMuUs) : 1.0;
+    // chi^2 weight: 1 / max(d, 1) for counts (Eq. chisq), given for asymmetry data
+    const double iv = hs.weights ? hs.weights[static_cast<int64_t>(h) * hs.stride + n] : 1.0 / fmax(d, 1.0);
     // gd[k][m][q]: derivative of term k with respect to slot q of primitive m.
     double gd[kMaxTerms][kMaxPrims][2];
     double A = 0.0;
@@ -552,10 +559,11 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Smem& sm)
         }
       }
     }
-    const double N = N0 * E * (1.0 + A) + Nbkg;
+    const double Ae = hs.envelope ? 1.0 + A : A;  // (1 + A), or A for the asymmetry model
+    const double N = N0 * E * Ae + Nbkg;
     double v, W;  // per-bin cost and dcost/dN
-    if (MODE >= 2) {  // Gauss-Newton product: N' = J v, W = (d^2 cost/dN^2) N', v = W N'
-      double Nd = E * (1.0 + A) * cc.ldir[0][0] + cc.ldir[0][1];
+    if (MODE == 2 || MODE == 3) {  // Gauss-Newton product: N' = J v, W = (d^2 cost/dN^2) N', v = W N'
+      double Nd = E * Ae * cc.ldir[0][0] + cc.ldir[0][1];
 #pragma unroll
       for (int k = 0; k < kMaxTerms; ++k) {
         const int np = k < nterms ? hs.raw[k].nprim : 0;
@@ -568,7 +576,7 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Smem& sm)
       }
       double c2;
       if (MODE == 2) {
-        c2 = 2.0 / fmax(d, 1.0);
+        c2 = 2.0 * iv;
       } else if (d > 0.0) {
         if (N <= 0.0) bad = 1;
         c2 = N > 0.0 ? 2.0 * d / (N * N) : 0.0;
@@ -579,7 +587,6 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Smem& sm)
       v = W * Nd;
     } else if (MODE == 0) {
       const double r = d - N;
-      const double iv = 1.0 / fmax(d, 1.0);
       v = r * r * iv;
       W = -2.0 * r * iv;
     } else if (d > 0.0) {
@@ -597,7 +604,7 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Smem& sm)
     }
     acc_v += v;
     if (GRAD) {
-      acc_n0 += W * E * (1.0 + A);
+      acc_n0 += W * E * Ae;
       acc_bkg += W;
       const double wNE = W * N0 * E;
 #pragma unroll
@@ -821,7 +828,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     }
 
     // Gauss-Newton products: the basis functions' directional derivatives along v.
-    constexpr bool GN = MODE >= 2;
+    constexpr bool GN = MODE == 2 || MODE == 3;
     float Bd[GN ? M : 1][BPT];
     if (GN) {
 #pragma unroll
@@ -958,8 +965,15 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
             N2 = __ffma2_rn(make_float2(gm[1 + m], gm[1 + m]), make_float2(B[m][0], B[m][1]), N2);
           const float2 r2 = __fadd2_rn(N2, make_float2(-dd2.x, -dd2.y));
           float2 v2, u2;
-          if (MODE == 0) {
-            const float2 iv2 = make_float2(rcpa(fmaxf(dd2.x, 1.0f)), rcpa(fmaxf(dd2.y, 1.0f)));
+          if (MODE == 0 || MODE == 4) {
+            // chi^2 weight: 1 / max(d, 1) (Eq. chisq), or the asymmetry data's own (MODE 4)
+            float2 iv2;
+            if (MODE == 4) {
+              const double2 wq = __ldg(reinterpret_cast<const double2*>(cc.roww[hl] + n0));
+              iv2 = make_float2(static_cast<float>(wq.x), static_cast<float>(wq.y));
+            } else {
+              iv2 = make_float2(rcpa(fmaxf(dd2.x, 1.0f)), rcpa(fmaxf(dd2.y, 1.0f)));
+            }
             u2 = __fmul2_rn(r2, iv2);
             v2 = __fmul2_rn(r2, u2);
           } else {
@@ -1088,7 +1102,8 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     // undefined (N <= 0 where d > 0) or the parameters were not finite.
     if (l == 0)
       row[0] = stall ? __longlong_as_double(0x7ff8000000000000LL)
-                     : (isfinite(a) ? a * (MODE == 0 ? 1.0 : 2.0) : __longlong_as_double(0x7ff0000000000000LL));
+                     : (isfinite(a) ? a * (MODE == 0 || MODE == 4 ? 1.0 : 2.0)
+                                    : __longlong_as_double(0x7ff0000000000000LL));
   }
 }
 
@@ -1108,7 +1123,7 @@ __device__ double split_slot(const HistSet& hs, const ChunkCache& cc, const doub
     const CanonTerm& ct = hs.canon[k];
     switch (c.kind) {
       case kCN0: {  // sum_m (dGam_m / dN0) G_m
-        double a = gch[0];
+        double a = hs.envelope ? gch[0] : 0.0;  // Gam_0 = N0 only with the decay envelope
         if (Bs::MERGED) {
           a += cc.cph[hl][0] * gch[1] - cc.sph[hl][0] * gch[2];
         } else {
@@ -1369,6 +1384,9 @@ int dispatch_mode(int mode, int grad, const Job* j, int n, int items, int sms, c
                   LaunchInfo* info) {
   if (mode == 2) return launch_one<PREC, SHAPE, 2, true>(j, n, items, sms, s, info);
   if (mode == 3) return launch_one<PREC, SHAPE, 3, true>(j, n, items, sms, s, info);
+  if (PREC == 1 && mode == 4)  // weighted chi^2 of asymmetry data (SPLIT)
+    return grad ? launch_one<PREC, SHAPE, PREC == 1 ? 4 : 0, true>(j, n, items, sms, s, info)
+                : launch_one<PREC, SHAPE, PREC == 1 ? 4 : 0, false>(j, n, items, sms, s, info);
   if (mode == 0)
     return grad ? launch_one<PREC, SHAPE, 0, true>(j, n, items, sms, s, info)
                 : launch_one<PREC, SHAPE, 0, false>(j, n, items, sms, s, info);
@@ -1380,6 +1398,9 @@ template <int PREC, int SHAPE>
 int occupancy_mode(int mode, int grad) {
   if (mode == 2) return occupancy_one<PREC, SHAPE, 2, true>();
   if (mode == 3) return occupancy_one<PREC, SHAPE, 3, true>();
+  if (PREC == 1 && mode == 4)
+    return grad ? occupancy_one<PREC, SHAPE, PREC == 1 ? 4 : 0, true>()
+                : occupancy_one<PREC, SHAPE, PREC == 1 ? 4 : 0, false>();
   if (mode == 0) return grad ? occupancy_one<PREC, SHAPE, 0, true>() : occupancy_one<PREC, SHAPE, 0, false>();
   return grad ? occupancy_one<PREC, SHAPE, 1, true>() : occupancy_one<PREC, SHAPE, 1, false>();
 }

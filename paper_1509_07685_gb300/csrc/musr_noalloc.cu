@@ -130,6 +130,7 @@ extern "C" int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int
   HistSet& hs = T.hs;
   std::memset(&hs, 0, sizeof(hs));
   hs.store = dtype == MUSR_DTYPE_FP64 ? kStoreF64 : kStoreF32;
+  hs.envelope = 1;  // histograms of counts (Eq. positron_histo)
   hs.H = nhist;
   hs.stride = row_stride;
   hs.dt_us = bin_width_ns / 1000.0;

@@ -104,8 +104,10 @@ inline bool shared_constant_amplitude(const CanonTerm& ct, const int32_t* map, c
 // Plans the SPLIT path of a theory and map into hs (canon in cosine-first order,
 // nterms, shape, merged, bamp, contributions).  Returns nullptr, or why the SPLIT
 // path cannot evaluate this theory (the FP64 path still can).
+// Without the decay envelope (asymmetry data) no shape is merged: a merged shape folds the
+// non-cosine terms into the basis function that carries the 1 of (1 + A).
 inline const char* plan_split(const musr_term* terms, int nterms, const int32_t* map, int H, int nslots,
-                              const double* consts, HistSet* hs) {
+                              const double* consts, HistSet* hs, bool envelope = true) {
   if (nterms > kMaxTerms) return "at most 4 terms";
   CanonTerm canon[kMaxTerms];
   for (int k = 0; k < nterms; ++k)
@@ -120,7 +122,7 @@ inline const char* plan_split(const musr_term* terms, int nterms, const int32_t*
     if (canon[k].kind != kTermTF) hs->canon[ntf + nn++] = canon[k];
   // Merged: every amplitude one shared constant, one phase per histogram.
   double amp[kMaxTerms];
-  bool merged = ntf == 2 && nn <= 1 && phases_shared(hs->canon, nterms, map, consts, H, nslots);
+  bool merged = envelope && ntf == 2 && nn <= 1 && phases_shared(hs->canon, nterms, map, consts, H, nslots);
   for (int k = 0; k < nterms && merged; ++k)
     merged = shared_constant_amplitude(hs->canon[k], map, consts, H, nslots, &amp[k]);
   hs->merged = merged ? 1 : 0;
