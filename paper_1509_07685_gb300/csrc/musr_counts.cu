@@ -85,12 +85,14 @@ __global__ void __launch_bounds__(256) prepare_shifted_kernel(const void* raw, v
 //   a = (f - alpha b) / D,  w = 1 / sigma_a^2,
 //   sigma_a^2 = 4 alpha^2 (b^2 max(F, 1) + f^2 max(B, 1)) / D^4
 // (first-order propagation of the Poisson errors of F and B), a = w = 0 where D <= 0 and
-// in the padding.  par holds alpha, bkg_f, bkg_b ([3][nhist]).  Every raw count is checked.
+// in the padding.  par holds alpha, bkg_f, bkg_b ([3][nhist]).  a32 and w32 receive FP32
+// copies (the SPLIT kernels' operands).  Every raw count is checked.
 template <int DTYPE>
 __global__ void __launch_bounds__(256) prepare_asymmetry_kernel(const void* raw, const int64_t* shift,
                                                                 const double* par, int nhist, int64_t nbins,
                                                                 int64_t stride, double* a, double* w,
-                                                                unsigned* flag, unsigned seq) {
+                                                                float* a32, float* w32, unsigned* flag,
+                                                                unsigned seq) {
   using In = typename std::conditional<DTYPE == MUSR_DTYPE_INT32, int32_t,
                                        typename std::conditional<DTYPE == MUSR_DTYPE_FP64, double, float>::type>::type;
   const In* F = static_cast<const In*>(raw);
@@ -114,6 +116,8 @@ __global__ void __launch_bounds__(256) prepare_asymmetry_kernel(const void* raw,
     }
     a[e] = av;
     w[e] = wv;
+    a32[e] = static_cast<float>(av);
+    w32[e] = static_cast<float>(wv);
   }
   bool bad = false;
   for (int64_t e = first; e < nraw; e += step) {
@@ -131,8 +135,8 @@ __global__ void __launch_bounds__(256) prepare_asymmetry_kernel(const void* raw,
 }  // namespace
 
 int launch_prepare_asymmetry(const void* raw, const int64_t* shift, const double* par, int dtype, int nhist,
-                             int64_t nbins, int64_t stride, double* a, double* w, unsigned* flag, unsigned seq,
-                             int num_sms, void* stream_) {
+                             int64_t nbins, int64_t stride, double* a, double* w, float* a32, float* w32,
+                             unsigned* flag, unsigned seq, int num_sms, void* stream_) {
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
   const int64_t total = static_cast<int64_t>(nhist) * stride;
   if (total <= 0) return 0;
@@ -141,15 +145,15 @@ int launch_prepare_asymmetry(const void* raw, const int64_t* shift, const double
   switch (dtype) {
     case MUSR_DTYPE_INT32:
       prepare_asymmetry_kernel<MUSR_DTYPE_INT32>
-          <<<grid, 256, 0, stream>>>(raw, shift, par, nhist, nbins, stride, a, w, flag, seq);
+          <<<grid, 256, 0, stream>>>(raw, shift, par, nhist, nbins, stride, a, w, a32, w32, flag, seq);
       break;
     case MUSR_DTYPE_FP32:
       prepare_asymmetry_kernel<MUSR_DTYPE_FP32>
-          <<<grid, 256, 0, stream>>>(raw, shift, par, nhist, nbins, stride, a, w, flag, seq);
+          <<<grid, 256, 0, stream>>>(raw, shift, par, nhist, nbins, stride, a, w, a32, w32, flag, seq);
       break;
     default:
       prepare_asymmetry_kernel<MUSR_DTYPE_FP64>
-          <<<grid, 256, 0, stream>>>(raw, shift, par, nhist, nbins, stride, a, w, flag, seq);
+          <<<grid, 256, 0, stream>>>(raw, shift, par, nhist, nbins, stride, a, w, a32, w32, flag, seq);
       break;
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;

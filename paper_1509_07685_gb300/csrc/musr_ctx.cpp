@@ -274,8 +274,13 @@ int compile(musr_ctx* ctx, int prec, int var) {
   std::memset(&hs, 0, sizeof(hs));
   hs.counts = ctx->d_counts;
   hs.store = ctx->store;
-  hs.weights = ctx->asym ? static_cast<const double*>(ctx->weights_own.p) : nullptr;
+  hs.weights = ctx->asym ? ctx->weights_own.p : nullptr;
   hs.envelope = ctx->asym ? 0 : 1;
+  if (ctx->asym && prec == MUSR_SPLIT) {  // FP32 copies: a staged like counts, w beside it
+    hs.counts = ctx->asym32_own.p;
+    hs.store = kStoreF32;
+    hs.weights = static_cast<const float*>(ctx->asym32_own.p) + static_cast<size_t>(ctx->H) * ctx->stride;
+  }
   hs.H = ctx->H;
   hs.stride = ctx->stride;
   hs.dt_us = ctx->dt_us;
@@ -713,6 +718,7 @@ void musr_ctx_destroy(musr_ctx* ctx) {
   dfree(ctx, ctx->counts_own);
   dfree(ctx, ctx->upload_scratch);
   dfree(ctx, ctx->weights_own);
+  dfree(ctx, ctx->asym32_own);
   EvalBufs& ev = ctx->ev;
   dfree(ctx, ev.params);
   dfree(ctx, ev.out);
@@ -748,6 +754,7 @@ static int upload_common(musr_ctx* ctx, int nhist, int64_t nbins, const double* 
   ctx->shift.clear();
   ctx->asym = false;
   dfree(ctx, ctx->weights_own);
+  dfree(ctx, ctx->asym32_own);
   ctx->H = nhist;
   ctx->B = nbins;
   ctx->t0.assign(t0, t0 + nhist);
@@ -856,6 +863,7 @@ int musr::finish_upload_check(musr_ctx* ctx) {
   drop_config(ctx);
   dfree(ctx, ctx->counts_own);
   dfree(ctx, ctx->weights_own);
+  dfree(ctx, ctx->asym32_own);
   ctx->asym = false;
   ctx->d_counts = nullptr;
   return fail(ctx, MUSR_EINVAL,
@@ -889,6 +897,7 @@ int musr_upload_asymmetry(musr_ctx* ctx, const void* forward, const void* backwa
   const size_t image = H * stride * sizeof(double);
   if ((rc = dalloc(ctx, ctx->counts_own, image))) return rc;
   if ((rc = dalloc(ctx, ctx->weights_own, image))) return rc;
+  if ((rc = dalloc(ctx, ctx->asym32_own, image))) return rc;  // [2][H][stride] FP32
   // Scratch: the raw forward rows, the raw backward rows, the row shifts, alpha and the
   // backgrounds; one kernel turns them into a and w on the device (FP64).
   const size_t raw = (2 * row * H + 255) & ~size_t(255), o_par = raw + ((8 * H + 255) & ~size_t(255));
@@ -911,7 +920,8 @@ int musr_upload_asymmetry(musr_ctx* ctx, const void* forward, const void* backwa
   if (launch_prepare_asymmetry(sp, reinterpret_cast<const int64_t*>(sp + raw),
                                reinterpret_cast<const double*>(sp + o_par), dtype, npairs, nbins, stride,
                                static_cast<double*>(ctx->counts_own.p), static_cast<double*>(ctx->weights_own.p),
-                               flag.dev, seq, ctx->num_sms, st))
+                               static_cast<float*>(ctx->asym32_own.p),
+                               static_cast<float*>(ctx->asym32_own.p) + H * stride, flag.dev, seq, ctx->num_sms, st))
     return cuda_fail(ctx, cudaGetLastError(), "prepare_asymmetry launch");
   for (int h = 0; h < npairs; ++h) {  // the device grid (see musr_upload_histograms)
     ctx->t0[h] -= static_cast<double>(ctx->shift[h]);

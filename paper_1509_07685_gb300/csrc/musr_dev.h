@@ -116,9 +116,10 @@ struct HistSet {
   // histograms: [H][stride] in FP32 or FP64
   const void* counts;
   int store;
-  // asymmetry data (forward / backward pairs): counts holds the asymmetry a (FP64) and
-  // weights the chi^2 weight w = 1 / sigma_a^2 (FP64, [H][stride]); nullptr for counts
-  const double* weights;
+  // asymmetry data (forward / backward pairs): counts holds the asymmetry a and weights the
+  // chi^2 weight w = 1 / sigma_a^2 ([H][stride]; FP64 on the FP64 path, FP32 on the SPLIT
+  // path, in the store's type); nullptr for counts
+  const void* weights;
   int envelope;  // 1: N0 exp(-t / tau_mu) (1 + A) + Nbkg; 0: the asymmetry model N0 A + Nbkg
   int H;
   int64_t stride;
@@ -186,10 +187,11 @@ int launch_prepare_counts(void* buf, int dtype, int nhist, int64_t nbins, int64_
 // left by shift[h] >= 0 bins (device array): img[h][j] = raw[h][j + shift[h]] or 0.
 // Asymmetry a and chi^2 weight w ([nhist][stride], FP64) of forward / backward pairs from
 // packed raw rows (F then B, [nhist][nbins] each), row h moved left by shift[h] bins;
-// par = alpha, bkg_f, bkg_b ([3][nhist], device).  Flags counts the store cannot hold.
+// par = alpha, bkg_f, bkg_b ([3][nhist], device); a32, w32: FP32 copies.  Flags counts the
+// store cannot hold.
 int launch_prepare_asymmetry(const void* raw, const int64_t* shift, const double* par, int dtype, int nhist,
-                             int64_t nbins, int64_t stride, double* a, double* w, unsigned* flag, unsigned seq,
-                             int num_sms, void* stream);
+                             int64_t nbins, int64_t stride, double* a, double* w, float* a32, float* w32,
+                             unsigned* flag, unsigned seq, int num_sms, void* stream);
 int launch_prepare_counts_shifted(const void* raw, void* img, const int64_t* shift, int dtype, int nhist,
                                   int64_t nbins, int64_t stride, unsigned* flag, unsigned seq, int num_sms,
                                   void* stream);

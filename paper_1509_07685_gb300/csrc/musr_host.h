@@ -148,6 +148,7 @@ struct musr_ctx {
   // asymmetry data (musr_upload_asymmetry): d_counts holds a, weights_own the chi^2 weights
   bool asym = false;
   musr::DevBuf weights_own;
+  musr::DevBuf asym32_own;         // FP32 a and w ([2][H][stride]) for the SPLIT path
   std::vector<double> asym_par;    // alpha, bkg_f, bkg_b of the pairs, the source of their copy
   std::vector<int64_t> shift;      // whole bins each histogram's row moved left on the device
   unsigned check_seq = 0;

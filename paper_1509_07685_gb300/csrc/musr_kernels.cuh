@@ -174,7 +174,7 @@ struct ChunkCache {
   double t0;
   int row[kGroupMax];
   const void* rowp[kGroupMax];       // first count of each histogram's row
-  const double* roww[kGroupMax];     // first chi^2 weight of the row (asymmetry data), else nullptr
+  const void* roww[kGroupMax];       // first chi^2 weight of the row (asymmetry data), else nullptr
   double loc[kGroupMax][kMaxSlots];  // local slot values (FP64)
   double ldir[kGroupMax][kMaxSlots]; // local slot components of a Gauss-Newton direction (else 0)
   // SPLIT: [Nbkg, Gam_0 .. Gam_{M-1}] of each histogram (16-byte rows: vector loads)
@@ -305,7 +305,8 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
       cc.row[hl] = h;
       const size_t esz = hs.store == kStoreF64 ? sizeof(double) : sizeof(float);
       cc.rowp[hl] = static_cast<const char*>(hs.counts) + static_cast<size_t>(h) * hs.stride * esz;
-      cc.roww[hl] = hs.weights ? hs.weights + static_cast<size_t>(h) * hs.stride : nullptr;
+      cc.roww[hl] = hs.weights ? static_cast<const char*>(hs.weights) + static_cast<size_t>(h) * hs.stride * esz
+                               : nullptr;
     }
   }
   __syncthreads();
@@ -496,7 +497,8 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Smem& sm)
     const double d = store == kStoreF64 ? rowd[n] : static_cast<double>(rowf[n]);
     const double E = hs.envelope ? exp(-t / kTauMuUs) : 1.0;
     // chi^2 weight: 1 / max(d, 1) for counts (Eq. chisq), given for asymmetry data
-    const double iv = hs.weights ? hs.weights[static_cast<int64_t>(h) * hs.stride + n] : 1.0 / fmax(d, 1.0);
+    const double iv = hs.weights ? static_cast<const double*>(hs.weights)[static_cast<int64_t>(h) * hs.stride + n]
+                                 : 1.0 / fmax(d, 1.0);
     // gd[k][m][q]: derivative of term k with respect to slot q of primitive m.
     double gd[kMaxTerms][kMaxPrims][2];
     double A = 0.0;
@@ -909,12 +911,17 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
         gm[4 * q + 3] = x.w;
       }
     };
+    auto fetch_w = [&](int hl) {  // the thread's two weights of histogram hl < nh
+      return __ldg(reinterpret_cast<const float2*>(static_cast<const float*>(cc.roww[hl]) + n0));
+    };
     auto hist_loop = [&](auto masked_tag) {
       constexpr bool MASKED = decltype(masked_tag)::value;
       // One histogram ahead: the shared-memory loads of histogram hl + 1 are in flight while
       // histogram hl is evaluated.
       float dn[BPT], gn[4 * NG4];
+      float2 wn = make_float2(0.0f, 0.0f);  // chi^2 weights of asymmetry data (MODE 4), one ahead
       fetch(0, dn, gn);
+      if (MODE == 4) wn = fetch_w(0);
 #pragma unroll
       for (int hl = 0; hl < G; ++hl) {
         if (hl >= nh) break;
@@ -923,7 +930,9 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
         for (int j = 0; j < BPT; ++j) d[j] = dn[j];
 #pragma unroll
         for (int q = 0; q < 4 * NG4; ++q) gm[q] = gn[q];
+        const float2 wc = wn;
         if (hl + 1 < G) fetch(hl + 1, dn, gn);
+        if (MODE == 4 && hl + 1 < nh) wn = fetch_w(hl + 1);  // weight rows exist up to nh only
         if (GN) {  // Gauss-Newton product: N' = J v, u = (d^2 (cost/2)/dN^2) N', value u N'
           float gdv[4 * NG4];
           fetch_dot(hl, gdv);
@@ -968,9 +977,8 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
           if (MODE == 0 || MODE == 4) {
             // chi^2 weight: 1 / max(d, 1) (Eq. chisq), or the asymmetry data's own (MODE 4)
             float2 iv2;
-            if (MODE == 4) {
-              const double2 wq = __ldg(reinterpret_cast<const double2*>(cc.roww[hl] + n0));
-              iv2 = make_float2(static_cast<float>(wq.x), static_cast<float>(wq.y));
+            if (MODE == 4) {  // FP32 weights beside FP32 asymmetry values
+              iv2 = wc;
             } else {
               iv2 = make_float2(rcpa(fmaxf(dd2.x, 1.0f)), rcpa(fmaxf(dd2.y, 1.0f)));
             }
