@@ -65,7 +65,11 @@ enum {
   MUSR_PRIM_GAUSS = 3,
   MUSR_PRIM_KT = 4,
   MUSR_PRIM_TFCOS = 5, /* slot[0] = nu (MHz), slot[1] = phi (degrees) */
-  MUSR_PRIM_LKT = 6    /* static Lorentzian Kubo-Toyabe 1/3 + 2/3 (1 - a t) exp(-a t); slot[0] = a (1/us) */
+  MUSR_PRIM_LKT = 6,   /* static Lorentzian Kubo-Toyabe 1/3 + 2/3 (1 - a t) exp(-a t); slot[0] = a (1/us) */
+  MUSR_PRIM_STREXP = 7, /* stretched exponential exp(-(|lambda| t)^beta) for t > 0, 1 for t <= 0;
+                           slot[0] = lambda (1/us), slot[1] = beta.  MUSR_FP64 precision only */
+  MUSR_PRIM_BESSEL = 8  /* J0(2 pi (nu t + phi / 360)), Bessel precession (incommensurate order);
+                           slot[0] = nu (MHz), slot[1] = phi (degrees).  MUSR_FP64 precision only */
 };
 
 #define MUSR_MAX_PRIMS 4

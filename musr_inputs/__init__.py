@@ -88,11 +88,14 @@ class Component:
     """One physical signal component of the simulated run."""
 
     amp: float
-    kind: str = "TF"  # "TF", "ZF" (static Gaussian fields) or "ZFL" (static Lorentzian fields)
+    # "TF", "ZF" (static Gaussian fields), "ZFL" (static Lorentzian fields), "INC" (fields of an
+    # incommensurate structure, gamma B = 2 pi nu cos(U), U uniform) or "LF" (no precession)
+    kind: str = "TF"
     nu_mhz: float = 0.0
     sigma: float = 0.0  # TF field-width (Gaussian dephasing rate), 1/us
     lam: float = 0.0  # depolarisation rate, 1/us
     delta: float = 0.0  # ZF / ZFL static field width, 1/us
+    levy: float = 0.0  # depolarisation at a rate r = levy / (2 Z^2), Z ~ N(0, 1) per muon, 1/us
 
 
 @dataclasses.dataclass
@@ -134,6 +137,11 @@ def simulate_histogram(rng: np.random.Generator, det: Detector, comps: Sequence[
             if c.kind == "TF":
                 omega = 2.0 * math.pi * c.nu_mhz + c.sigma * rng.standard_normal(sel.size)
                 sk = np.cos(omega * tk + phase)
+            elif c.kind == "INC":
+                omega = 2.0 * math.pi * c.nu_mhz * np.cos(rng.uniform(0.0, 2.0 * math.pi, sel.size))
+                sk = np.cos(omega * tk + phase)
+            elif c.kind == "LF":
+                sk = np.ones(sel.size)
             elif c.kind in ("ZF", "ZFL"):
                 # fields in units of gamma_mu: Gaussian, or the 3-D Lorentzian of dilute moments
                 # (a multivariate Cauchy: a Gaussian vector divided by |N(0, 1)|)
@@ -147,6 +155,11 @@ def simulate_histogram(rng: np.random.Generator, det: Detector, comps: Sequence[
                 raise ValueError(c.kind)
             if c.lam > 0:
                 alive = rng.exponential(1.0 / c.lam, sel.size) > tk
+                sk = np.where(alive, sk, 0.0)
+            if c.levy > 0:  # a one-sided Levy distribution of rates
+                z = rng.standard_normal(sel.size)
+                rate = c.levy / (2.0 * np.maximum(z * z, 1e-300))
+                alive = rng.exponential(1.0, sel.size) > rate * tk
                 sk = np.where(alive, sk, 0.0)
             s[sel] = sk
         keep = rng.random(m) * (1.0 + a_tot) < 1.0 + a_tot * s
@@ -358,6 +371,43 @@ def paper_tf16(nhist: int = 16, nbins: int = 81920, bin_width_ns: Optional[float
     return Problem(counts, np.zeros(nhist), bin_width_ns, _full_range(nbins, bin_width_ns), terms,
                    np.array(rows, np.int32), np.zeros(0), len(truth), np.array(truth), names,
                    "paper_tf16")
+
+
+def inc_bessel(nhist: int = 2, nbins: int = 1600, bin_width_ns: float = 8.0, seed: int = 8, n0: float = 3000.0,
+               dtype=np.float32) -> Problem:
+    """Incommensurate magnetic order: fields gamma B = 2 pi nu cos(U) with U uniform give the
+    polarisation J0(2 pi nu t) (detector phase 0; the second detector at 180 degrees sees
+    -J0).  Model A_j = A0_j J0(2 pi nu t) e^{-lambda t} (BESSEL phase fixed at 0 through a
+    constant); per detector N0, Nbkg, A0; shared nu, lambda."""
+    dets, comps, names, truth = [], [], ["nu", "lambda"], [2.5, 0.3]
+    rows = []
+    for j in range(nhist):
+        ph = 0.0 if j % 2 == 0 else 180.0
+        dets.append(Detector(n0, 2.0, ph))
+        comps.append([Component(0.22, "INC", nu_mhz=2.5, lam=0.3)])
+        names += [f"N0_{j}", f"Nbkg_{j}", f"A0_{j}"]
+        truth += [n0, 2.0, 0.22 if ph == 0.0 else -0.22]
+        rows.append([2 + 3 * j, 3 + 3 * j, 4 + 3 * j, 0, -1, 1])
+    counts = simulate(seed, dets, comps, nbins, bin_width_ns, dtype)
+    terms = [[("AMP", (2,)), ("BESSEL", (3, 4)), ("EXP", (5,))]]
+    return Problem(counts, np.zeros(nhist), bin_width_ns, _full_range(nbins, bin_width_ns), terms,
+                   np.array(rows, np.int32), np.array([0.0]), len(truth), np.array(truth), names, "inc_bessel")
+
+
+def levy_lf(nhist: int = 2, nbins: int = 1600, bin_width_ns: float = 8.0, seed: int = 9, n0: float = 3000.0,
+            dtype=np.float32) -> Problem:
+    """Depolarisation at rates drawn from a one-sided Levy distribution (r = lambda / (2 Z^2)),
+    whose average exp(-r t) is exp(-(lambda t)^(1/2)): model A = A0 exp(-(lambda t)^beta) with
+    beta fitted (truth 1/2); shared A0, lambda, beta; per detector N0, Nbkg."""
+    dets = [Detector(n0, 2.0, 0.0) for _ in range(nhist)]
+    comps = [[Component(0.25, "LF", levy=0.8)] for _ in range(nhist)]
+    counts = simulate(seed, dets, comps, nbins, bin_width_ns, dtype)
+    terms = [[("AMP", (2,)), ("STREXP", (3, 4))]]
+    rows = [[3 + 2 * j, 4 + 2 * j, 0, 1, 2] for j in range(nhist)]
+    names = ["A0", "lambda", "beta"] + [n for j in range(nhist) for n in (f"N0_{j}", f"Nbkg_{j}")]
+    truth = [0.25, 0.8, 0.5] + [v for _ in range(nhist) for v in (n0, 2.0)]
+    return Problem(counts, np.zeros(nhist), bin_width_ns, _full_range(nbins, bin_width_ns), terms,
+                   np.array(rows, np.int32), np.zeros(0), len(truth), np.array(truth), names, "levy_lf")
 
 
 @dataclasses.dataclass

@@ -37,7 +37,7 @@ _LIB_PATH = os.path.join(_HERE, "_musr_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-KIND = {"AMP": 1, "EXP": 2, "GAUSS": 3, "KT": 4, "TFCOS": 5, "LKT": 6}
+KIND = {"AMP": 1, "EXP": 2, "GAUSS": 3, "KT": 4, "TFCOS": 5, "LKT": 6, "STREXP": 7, "BESSEL": 8}
 CHI2, MLE = 0, 1
 
 
@@ -95,8 +95,9 @@ def theory_arrays(terms):
     """Term list -> (nprim[T], kind[T,4], slot[T,4,2]) int32 arrays.
 
     ``terms`` is a sequence of terms; a term is a sequence of (kind, slots)
-    with kind in AMP, EXP, GAUSS, KT, TFCOS, LKT and slots a tuple of local slot
-    indices (two for TFCOS: frequency, phase; one otherwise).
+    with kind in AMP, EXP, GAUSS, KT, TFCOS, LKT, STREXP, BESSEL and slots a tuple of local
+    slot indices (two for TFCOS and BESSEL: frequency, phase; two for STREXP: rate, exponent;
+    one otherwise).
     """
     T = len(terms)
     nprim = np.zeros(max(T, 1), np.int32)

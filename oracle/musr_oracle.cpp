@@ -30,6 +30,10 @@
 //   * KT(Delta) = 1/3 + 2/3 (1 - Delta^2 t^2) exp(-Delta^2 t^2 / 2).
 //   * LKT(a) = 1/3 + 2/3 (1 - a t) exp(-a t), the static Lorentzian Kubo-Toyabe
 //     relaxation (a: the Lorentzian field width times gamma_mu).
+//   * STREXP(lambda, beta) = exp(-(|lambda| t)^beta) for t > 0 and 1 for t <= 0 (the
+//     relaxation starts at time zero), the stretched exponential.
+//   * BESSEL(nu, phi) = J0(2 pi (nu t + phi / 360)), precession in an incommensurate
+//     field distribution, the phase inside the argument like TFCOS.
 //   * Local slot 0 is N0, slot 1 is Nbkg; terms reference any slot.
 //   * MLE with N <= 0 in a bin with d > 0 is +infinity (status 1).
 //
@@ -64,7 +68,7 @@ namespace {
 constexpr double kTauMu = 2.197019;  // muon lifetime in microseconds
 constexpr double kPi = 3.14159265358979323846;
 
-enum PrimKind { kAmp = 1, kExp = 2, kGauss = 3, kKT = 4, kTFCos = 5, kLKT = 6 };
+enum PrimKind { kAmp = 1, kExp = 2, kGauss = 3, kKT = 4, kTFCos = 5, kLKT = 6, kStrExp = 7, kBessel = 8 };
 constexpr int kMaxPrim = 4;
 
 using cplx = std::complex<double>;
@@ -137,6 +141,17 @@ T slot_value(const Problem& pb, const T* x, int h, int s) {
   return T(pb.consts[-1 - m]);
 }
 
+// J0 and J1 (C++17 special functions, defined for x >= 0; J0 is even and J1 odd).
+inline double bessel_j0(double x) { return std::cyl_bessel_j(0.0, std::fabs(x)); }
+inline double bessel_j1(double x) { return x < 0.0 ? -std::cyl_bessel_j(1.0, -x) : std::cyl_bessel_j(1.0, x); }
+// J0 at a complex argument x + i y with |y| tiny (the complex step): J0(x) - i y J1(x),
+// exact to O(y^2).
+inline cplx bessel_j0(const cplx& z) { return cplx(bessel_j0(z.real()), -z.imag() * bessel_j1(z.real())); }
+
+// |lambda| for the stretched exponential: the sign folded analytically on each side.
+inline double fold_sign(double v) { return v < 0.0 ? -v : v; }
+inline cplx fold_sign(const cplx& v) { return v.real() < 0.0 ? -v : v; }
+
 // One primitive factor of a term of A(t) (Eq. asymmetry and its generalisation).
 template <class T>
 T primitive(int kind, const T& p0, const T& p1, double t) {
@@ -157,6 +172,13 @@ T primitive(int kind, const T& p0, const T& p1, double t) {
       T u = p0 * t;
       return 1.0 / 3.0 + (2.0 / 3.0) * (1.0 - u) * std::exp(-u);
     }
+    case kStrExp: {
+      const T x = fold_sign(p0) * t;
+      if (!(t > 0.0) || re(x) == 0.0) return T(1.0);
+      return std::exp(-std::pow(x, p1));
+    }
+    case kBessel:
+      return bessel_j0(2.0 * kPi * (p0 * t + p1 / 360.0));
     default:
       return T(std::numeric_limits<double>::quiet_NaN());
   }
@@ -192,12 +214,26 @@ inline void primitive_deriv(int kind, double p0, double p1, double t, double* d0
       *d0 = (2.0 / 3.0) * t * std::exp(-u) * (u - 2.0);
       break;
     }
+    case kStrExp: {
+      const double lam = std::fabs(p0), x = lam * t;
+      if (!(t > 0.0) || x == 0.0) break;
+      const double xb = std::pow(x, p1), f = std::exp(-xb);
+      *d0 = (p0 < 0.0 ? -1.0 : 1.0) * (-p1 * xb / lam) * f;  // d/dlambda
+      *d1 = -xb * std::log(x) * f;                             // d/dbeta
+      break;
+    }
+    case kBessel: {
+      const double j1 = bessel_j1(2.0 * kPi * (p0 * t + p1 / 360.0));  // J0' = -J1
+      *d0 = -j1 * 2.0 * kPi * t;
+      *d1 = -j1 * 2.0 * kPi / 360.0;
+      break;
+    }
     default:
       break;
   }
 }
 
-inline int nslots_of(int kind) { return kind == kTFCos ? 2 : 1; }
+inline int nslots_of(int kind) { return kind == kTFCos || kind == kStrExp || kind == kBessel ? 2 : 1; }
 
 // Eq. positron_histo for histogram h at time t.
 template <class T>

@@ -44,6 +44,11 @@ MUTANTS = {
     "Lorentzian KT derivative": ("*d0 = (2.0 / 3.0) * t * std::exp(-u) * (u - 2.0);",
                                  "*d0 = (2.0 / 3.0) * t * std::exp(-u) * (u - 3.0);"),
     "Gauss-Newton weight of -2lnL": ("        c2 = 2.0 * d / (N * N);", "        c2 = 2.0 / N;"),
+    "Bessel argument misses 2 pi": ("return bessel_j0(2.0 * kPi * (p0 * t + p1 / 360.0));",
+                                    "return bessel_j0(p0 * t + p1 / 360.0);"),
+    "Bessel derivative sign": ("      *d0 = -j1 * 2.0 * kPi * t;", "      *d0 = j1 * 2.0 * kPi * t;"),
+    "stretched exponent derivative drops the log": ("*d1 = -xb * std::log(x) * f;", "*d1 = -xb * f;"),
+    "stretched rate derivative drops beta": ("(-p1 * xb / lam) * f;", "(-xb / lam) * f;"),
     "asymmetry variance drops the 4": ("const double var = 4.0 * al * al *", "const double var = al * al *"),
     "asymmetry alpha on the forward count": ("a[i] = (f - al * b) / D;", "a[i] = (al * f - b) / D;"),
     "asymmetry variances exchanged": ("(b * b * std::fmax(F[i], 1.0) + f * f * std::fmax(B[i], 1.0))",

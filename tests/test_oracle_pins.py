@@ -488,3 +488,79 @@ def test_asymmetry_gauss_newton_equals_hessian_when_data_equal_model():
     Hc = oracle.hessian(q, p.truth, CHI2)
     scale = np.sqrt(np.outer(np.diag(Hg), np.diag(Hg)))
     assert np.max(np.abs(Hg - Hc) / scale) < 1e-6
+
+
+# ------------------------------------------------------------------------------------------
+# Stretched exponential and Bessel precession
+# ------------------------------------------------------------------------------------------
+
+def test_stretched_exponential_special_cases():
+    """exp(-(lambda t)^beta) is EXP at beta = 1 and GAUSS with sigma = sqrt(2) lambda at
+    beta = 2; 1 at and before time zero; even in lambda.  Catches a missing exponent, a
+    rate inside the power taken as lambda^beta t, and a wrong branch at t <= 0."""
+    for lam in (0.2, 0.9, 3.0):
+        for t in (0.05, 0.7, 4.0):
+            assert oracle.primitive("STREXP", lam, 1.0, t) == pytest.approx(oracle.primitive("EXP", lam, 0.0, t),
+                                                                            rel=1e-14)
+            assert oracle.primitive("STREXP", lam, 2.0, t) == pytest.approx(
+                oracle.primitive("GAUSS", math.sqrt(2.0) * lam, 0.0, t), rel=1e-13)
+            assert oracle.primitive("STREXP", -lam, 0.6, t) == oracle.primitive("STREXP", lam, 0.6, t)
+        assert oracle.primitive("STREXP", lam, 0.5, 0.0) == 1.0
+        assert oracle.primitive("STREXP", lam, 0.5, -1.0) == 1.0
+    # exp(-(lambda t)^beta) = 1/e at t = 1/lambda for every beta
+    for beta in (0.3, 0.5, 1.7):
+        assert oracle.primitive("STREXP", 0.4, beta, 2.5) == pytest.approx(math.exp(-1.0), rel=1e-14)
+
+
+def test_bessel_precession_against_a_library_j0():
+    """BESSEL(nu, phi) = J0(2 pi (nu t + phi / 360)) against scipy's J0, including the first zero
+    2.404825557695773 and large arguments.  Catches a missing 2 pi, a phase in radians and
+    a J1 in place of J0."""
+    from scipy.special import j0
+    rng = np.random.default_rng(17)
+    for _ in range(400):
+        nu, phi, t = rng.uniform(0.0, 30.0), rng.uniform(-360.0, 360.0), rng.uniform(-2.0, 12.0)
+        x = 2.0 * math.pi * (nu * t + phi / 360.0)
+        assert abs(oracle.primitive("BESSEL", nu, phi, t) - j0(x)) < 1e-12  # two libraries, arguments to ~2000
+    assert oracle.primitive("BESSEL", 3.0, 0.0, 0.0) == 1.0
+    assert abs(oracle.primitive("BESSEL", 2.404825557695773 / (2.0 * math.pi), 0.0, 1.0)) < 1e-15
+
+
+def _new_primitive_problem(mode_seed=0):
+    import musr_inputs as mi
+    p = mi.cfg3(nhist=2, nbins=400, bin_width_ns=25.0, seed=29)
+    terms = [[("AMP", (2,)), ("STREXP", (3, 4))], [("AMP", (5,)), ("BESSEL", (6, 7)), ("EXP", (8,))]]
+    rows = [[0, 1, 2, 3, 4, 5, 6, 7, 8], [9, 10, 2, 3, 4, 5, 6, 11, 8]]
+    x = np.array([300.0, 2.0, 0.12, 0.7, 0.55, 0.1, 1.3, 25.0, 0.2, 310.0, 2.5, -40.0])
+    q = Problem(p.counts, p.t0, p.bin_width_ns, p.fit_range_us, terms, np.array(rows, np.int32), np.zeros(0), 12,
+                np.zeros(12), [f"p{i}" for i in range(12)])
+    return q, x
+
+
+@pytest.mark.parametrize("mode", [CHI2, MLE])
+def test_gradient_matches_complex_step_new_primitives(mode):
+    """Complex-step derivative of a theory with a stretched exponential and a Bessel term
+    (the chain factors 2 pi t, 2 pi / 360, beta (lambda t)^beta / lambda, ln(lambda t))."""
+    q, x = _new_primitive_problem()
+    v, g, gs, st = oracle.cost(q, x, mode)
+    assert st == 0
+    for i in range(q.nparams):
+        e = np.zeros(q.nparams)
+        e[i] = 1.0
+        cs = oracle.cost_cstep(q, x, e, mode)
+        assert abs(cs - g[i]) <= 1e-11 * gs[i] + 1e-300, (i, cs, g[i], gs[i])
+
+
+def test_gradient_of_new_primitives_matches_central_differences():
+    """Central differences of the value (no derivative formula involved): pins J0' = -J1 and
+    the exponent derivative of the stretched exponential."""
+    q, x = _new_primitive_problem()
+    for mode in (CHI2, MLE):
+        _, g, gs, _ = oracle.cost(q, x, mode)
+        for i in range(q.nparams):
+            h = 1e-6 * max(abs(x[i]), 1e-3)
+            xp, xm = x.copy(), x.copy()
+            xp[i] += h
+            xm[i] -= h
+            fd = (oracle.cost(q, xp, mode, grad=False)[0] - oracle.cost(q, xm, mode, grad=False)[0]) / (2 * h)
+            assert abs(fd - g[i]) <= 1e-6 * gs[i], (i, fd, g[i])
