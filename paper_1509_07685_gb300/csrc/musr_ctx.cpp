@@ -293,7 +293,7 @@ int compile(musr_ctx* ctx, int prec, int var) {
     for (int m = 0; m < musr::kMaxPrims; ++m) {
       hs.raw[k].kind[m] = m < t.nprim ? t.kind[m] : 0;
       hs.raw[k].slot[m][0] = m < t.nprim ? t.slot[m][0] : 0;
-      hs.raw[k].slot[m][1] = m < t.nprim && t.kind[m] == MUSR_PRIM_TFCOS ? t.slot[m][1] : 0;
+      hs.raw[k].slot[m][1] = m < t.nprim && musr::prim_nslots(t.kind[m]) == 2 ? t.slot[m][1] : 0;
     }
   }
   const int H = ctx->H;
@@ -981,9 +981,9 @@ int musr_set_theory(musr_ctx* ctx, const musr_term* terms, int nterms) {
     const musr_term& t = terms[k];
     if (t.nprim < 1 || t.nprim > MUSR_MAX_PRIMS) return fail(ctx, MUSR_EINVAL, "a term needs 1..4 primitives");
     for (int m = 0; m < t.nprim; ++m) {
-      if (t.kind[m] < MUSR_PRIM_AMP || t.kind[m] > MUSR_PRIM_LKT)
+      if (t.kind[m] < MUSR_PRIM_AMP || t.kind[m] > MUSR_PRIM_BESSEL)
         return fail(ctx, MUSR_EINVAL, "unknown primitive kind");
-      const int ns = t.kind[m] == MUSR_PRIM_TFCOS ? 2 : 1;
+      const int ns = musr::prim_nslots(t.kind[m]);
       for (int q = 0; q < ns; ++q)
         if (t.slot[m][q] < 0 || t.slot[m][q] >= MUSR_MAX_SLOTS)
           return fail(ctx, MUSR_EINVAL, "slot index out of range");
@@ -1011,7 +1011,7 @@ int musr_set_map(musr_ctx* ctx, const int32_t* map, int nslots, int nparams, con
   if (nconsts < 0 || (nconsts > 0 && !consts)) return fail(ctx, MUSR_EINVAL, "bad consts");
   for (const auto& t : ctx->terms)
     for (int m = 0; m < t.nprim; ++m)
-      for (int q = 0; q < (t.kind[m] == MUSR_PRIM_TFCOS ? 2 : 1); ++q)
+      for (int q = 0; q < musr::prim_nslots(t.kind[m]); ++q)
         if (t.slot[m][q] >= nslots) return fail(ctx, MUSR_EINVAL, "theory references a slot >= nslots");
   for (int i = 0; i < nconsts; ++i)
     if (!std::isfinite(consts[i])) return fail(ctx, MUSR_EINVAL, "consts must be finite");

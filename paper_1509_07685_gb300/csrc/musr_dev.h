@@ -32,7 +32,12 @@ constexpr int kMaxSlots = 32;
 constexpr int kMaxContrib = 64;
 
 enum StoreType : int { kStoreF32 = 1, kStoreF64 = 2 };
-enum PrimKind : int { kAmp = 1, kExp = 2, kGauss = 3, kKT = 4, kTFCos = 5, kLKT = 6 };
+enum PrimKind : int { kAmp = 1, kExp = 2, kGauss = 3, kKT = 4, kTFCos = 5, kLKT = 6, kStrExp = 7, kBessel = 8 };
+// Parameter slots of a primitive: frequency and phase (TFCOS, BESSEL), rate and exponent
+// (STREXP), else one.
+__host__ __device__ inline int prim_nslots(int kind) {
+  return kind == kTFCos || kind == kStrExp || kind == kBessel ? 2 : 1;
+}
 enum TermKind : int { kTermNone = 0, kTermPlain = 1, kTermTF = 2, kTermKT = 3, kTermLKT = 4 };
 
 // SPLIT shapes.  Every model the SPLIT path accepts is, for each histogram j of a

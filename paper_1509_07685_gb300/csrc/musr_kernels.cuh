@@ -535,6 +535,22 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Smem& sm)
           const double g = exp(-u);
           f[m] = 1.0 / 3.0 + (2.0 / 3.0) * (1.0 - u) * g;
           df[m][0] = (2.0 / 3.0) * t * g * (u - 2.0);
+        } else if (kind == kStrExp) {  // exp(-(|lambda| t)^beta) for t > 0, else 1
+          const double p1 = cc.loc[0][hs.raw[k].slot[m][1]];
+          const double lam = fabs(p0), x = lam * t;
+          if (t > 0.0 && x > 0.0) {
+            const double xb = pow(x, p1), e = exp(-xb);
+            f[m] = e;
+            df[m][0] = (p0 < 0.0 ? -1.0 : 1.0) * (-p1 * xb / lam) * e;
+            df[m][1] = -xb * log(x) * e;
+          }
+        } else if (kind == kBessel) {  // J0(2 pi (nu t + phi / 360)); J0' = -J1
+          const double p1 = cc.loc[0][hs.raw[k].slot[m][1]];
+          const double x = kTwoPi * (p0 * t + p1 / 360.0);
+          f[m] = j0(x);
+          const double j1x = j1(x);
+          df[m][0] = -j1x * kTwoPi * t;
+          df[m][1] = -j1x * kTwoPi / 360.0;
         } else if (kind == kTFCos) {
           const double p1 = cc.loc[0][hs.raw[k].slot[m][1]];
           // Phase in turns, range-reduced exactly before sin/cos.
@@ -573,7 +589,7 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Smem& sm)
         for (int m = 0; m < kMaxPrims; ++m) {
           if (m >= np) continue;
           Nd += N0 * E * gd[k][m][0] * cc.ldir[0][hs.raw[k].slot[m][0]];
-          if (hs.raw[k].kind[m] == kTFCos) Nd += N0 * E * gd[k][m][1] * cc.ldir[0][hs.raw[k].slot[m][1]];
+          if (prim_nslots(hs.raw[k].kind[m]) == 2) Nd += N0 * E * gd[k][m][1] * cc.ldir[0][hs.raw[k].slot[m][1]];
         }
       }
       double c2;
@@ -659,7 +675,7 @@ __device__ double fp64_slot(const HistSet& hs, const double* tot, int s) {
   for (int k = 0; k < hs.nterms; ++k)
     for (int m = 0; m < hs.raw[k].nprim; ++m) {
       if (hs.raw[k].slot[m][0] == s) g += tot[3 + (k * kMaxPrims + m) * 2 + 0];
-      if (hs.raw[k].kind[m] == kTFCos && hs.raw[k].slot[m][1] == s) g += tot[3 + (k * kMaxPrims + m) * 2 + 1];
+      if (prim_nslots(hs.raw[k].kind[m]) == 2 && hs.raw[k].slot[m][1] == s) g += tot[3 + (k * kMaxPrims + m) * 2 + 1];
     }
   return g;
 }

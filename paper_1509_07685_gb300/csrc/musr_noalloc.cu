@@ -100,8 +100,8 @@ extern "C" int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int
   for (int k = 0; k < nterms; ++k) {
     if (terms[k].nprim < 1 || terms[k].nprim > MUSR_MAX_PRIMS) return na_fail("a term needs 1..4 primitives");
     for (int m = 0; m < terms[k].nprim; ++m) {
-      if (terms[k].kind[m] < MUSR_PRIM_AMP || terms[k].kind[m] > MUSR_PRIM_LKT) return na_fail("unknown primitive");
-      for (int q = 0; q < (terms[k].kind[m] == MUSR_PRIM_TFCOS ? 2 : 1); ++q)
+      if (terms[k].kind[m] < MUSR_PRIM_AMP || terms[k].kind[m] > MUSR_PRIM_BESSEL) return na_fail("unknown primitive");
+      for (int q = 0; q < prim_nslots(terms[k].kind[m]); ++q)
         if (terms[k].slot[m][q] < 0 || terms[k].slot[m][q] >= nslots) return na_fail("slot index out of range");
     }
   }
@@ -142,7 +142,7 @@ extern "C" int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int
     for (int m = 0; m < kMaxPrims; ++m) {
       hs.raw[k].kind[m] = m < terms[k].nprim ? terms[k].kind[m] : 0;
       hs.raw[k].slot[m][0] = m < terms[k].nprim ? terms[k].slot[m][0] : 0;
-      hs.raw[k].slot[m][1] = m < terms[k].nprim && terms[k].kind[m] == MUSR_PRIM_TFCOS ? terms[k].slot[m][1] : 0;
+      hs.raw[k].slot[m][1] = m < terms[k].nprim && prim_nslots(terms[k].kind[m]) == 2 ? terms[k].slot[m][1] : 0;
     }
   }
   int nlo[kNaMaxHist], nhi[kNaMaxHist];

@@ -43,6 +43,8 @@ inline bool canonical_term(const musr_term& t, CanonTerm* ct) {
         ct->kt_slot = t.slot[m][0];
         ++nlkt;
         break;
+      default:  // STREXP, BESSEL: no basis form (FP64 path only)
+        return false;
     }
   }
   if (namp > 1 || nkt + nlkt + ntf > 1) return false;
@@ -112,7 +114,8 @@ inline const char* plan_split(const musr_term* terms, int nterms, const int32_t*
   CanonTerm canon[kMaxTerms];
   for (int k = 0; k < nterms; ++k)
     if (!canonical_term(terms[k], &canon[k]))
-      return "SPLIT precision needs every term to hold at most one AMP, and at most one of KT, LKT or TFCOS";
+      return "SPLIT precision needs every term to hold at most one AMP, and at most one of KT, LKT or TFCOS "
+             "(STREXP and BESSEL terms run at MUSR_FP64 precision)";
   // Cosine terms first (the model is a sum: the order of its terms is free).
   int ntf = 0, nn = 0;
   hs->nterms = nterms;

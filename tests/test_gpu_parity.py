@@ -374,6 +374,30 @@ def test_shifted_upload_every_dtype_and_check(B):
         B.musr_ctx_destroy(ctx)
 
 
+def test_fp64_only_primitives(B):
+    """The stretched exponential and the Bessel precession: the FP64 path against the oracle
+    (single and batched, both costs) for Monte Carlo configurations and a theory mixing them
+    with the other primitives; the SPLIT path refuses them (no basis form)."""
+    import test_oracle_pins as pins
+    q, xq = pins._new_primitive_problem()
+    cases = [(mi.inc_bessel(nhist=2, nbins=3000, bin_width_ns=4.0, seed=71), None),
+             (mi.levy_lf(nhist=3, nbins=2500, bin_width_ns=5.0, seed=72), None), (q, xq)]
+    for p, x in cases:
+        x = mi.start_point(p, 2) if x is None else x
+        X = mi.jitter(x, 4, seed=3, lo=0.98, hi=1.02)
+        with B.Context(p) as ctx:
+            for mode in (0, 1):
+                v, g, _ = ctx.eval(x, mode, B.MUSR_FP64)
+                _check_fp64(v, g, oracle.cost(p, x, mode))
+                vals, grads, st = ctx.eval_batch(X, mode, B.MUSR_FP64)
+                assert st == 0
+                for i in (0, 3):
+                    _check_fp64(vals[i], grads[i], oracle.cost(p, X[i], mode))
+            with pytest.raises(B.MusrError) as e:
+                ctx.eval(x, 1, B.MUSR_SPLIT)
+            assert e.value.status == B.MUSR_EINVAL and "STREXP" in str(e.value)
+
+
 def test_hbm_budget_is_enforced(B):
     p = mi.cfg2(nhist=8, nbins=65536, seed=2)
     ctx = B.musr_ctx_create(0, hbm_budget_bytes=1 << 20)
