@@ -79,6 +79,11 @@ def _load():
             lib.oracle_fit.argtypes = prob + [ctypes.c_int, P(d), P(d), ctypes.c_int, d, P(d), P(d),
                                               P(d), P(ctypes.c_int)]
             lib.oracle_fit.restype = ctypes.c_int
+            lib.oracle_poisson_direct.argtypes = [P(d), ctypes.c_int, ctypes.c_int, ctypes.c_int, d, d, d, P(d)]
+            lib.oracle_poisson_direct.restype = None
+            lib.oracle_poisson_points.argtypes = [P(d), ctypes.c_int, ctypes.c_int, ctypes.c_int, d, d, d, P(i32),
+                                                  ctypes.c_int, P(d)]
+            lib.oracle_poisson_points.restype = None
             lib.oracle_asymmetry.argtypes = [P(d), P(d), ctypes.c_int, i64, P(d), P(d), P(d), P(d), P(d)]
             lib.oracle_asymmetry.restype = None
             lib.oracle_neumaier_sum.argtypes = [P(d), i64]
@@ -262,3 +267,23 @@ def fit(prob, x0, mode: int = CHI2, maxit: int = 1000, gtol: float = 1e-8, fd_st
 def neumaier_sum(v) -> float:
     v = np.ascontiguousarray(v, dtype=np.float64)
     return _load().oracle_neumaier_sum(_ptr(v, ctypes.c_double), v.size)
+
+
+def poisson_direct(rho, h):
+    """phi [mx][my][mz] of Eq. openbruteforceconv by direct summation (oracle_poisson_direct);
+    h = (hx, hy, hz)."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    phi = np.zeros_like(rho)
+    _load().oracle_poisson_direct(_ptr(rho, ctypes.c_double), *rho.shape, float(h[0]), float(h[1]), float(h[2]),
+                                  _ptr(phi, ctypes.c_double))
+    return phi
+
+
+def poisson_points(rho, h, ijk):
+    """phi at the mesh points ijk [n][3] only (oracle_poisson_points)."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    ijk = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+    out = np.zeros(len(ijk))
+    _load().oracle_poisson_points(_ptr(rho, ctypes.c_double), *rho.shape, float(h[0]), float(h[1]), float(h[2]),
+                                  _ptr(ijk, ctypes.c_int32), len(ijk), _ptr(out, ctypes.c_double))
+    return out

@@ -48,6 +48,9 @@
 //     T(t) = N0 A(t) + Nbkg   (N0 a scale, usually the constant 1; Nbkg a baseline),
 // and the cost is chi^2 = sum w (a - T)^2.  -2lnL is not defined for it (status 2).
 //
+// The file also holds the direct-summation oracle of the paper's particle-mesh Poisson
+// solve (Section 3, Eq. openbruteforceconv), at its end.
+//
 // Summation: every sum over bins is Neumaier-compensated, in bin order
 // (histogram-major), so that the oracle's own rounding stays far below the
 // 1e-12 relative tolerance used against the GPU path.
@@ -691,6 +694,48 @@ void oracle_asymmetry(const double* F, const double* B, int npairs, int64_t nbin
       const double var = 4.0 * al * al * (b * b * std::fmax(F[i], 1.0) + f * f * std::fmax(B[i], 1.0)) / (D * D * D * D);
       w[i] = var > 0.0 ? 1.0 / var : 0.0;
     }
+}
+
+// ---------------------------------------------------------------------------------------
+// The particle-mesh Poisson solve of Section 3 (the second workload): the discretised
+// convolution of Eq. openbruteforceconv for an isolated (open-boundary) charge density,
+//   phi_{i,j,k} = hx hy hz sum_{i',j',k'} rho_{i',j',k'} G_{i-i',j-j',k-k'},
+//   G_{a,b,c} = 1 / sqrt((a hx)^2 + (b hy)^2 + (c hz)^2),
+// summed directly (no FFT).  Reading: G_{0,0,0}, where 1/r is singular, is 1 / min(h).
+// Arrays are [mx][my][mz], z fastest.
+// ---------------------------------------------------------------------------------------
+double poisson_green(int a, int b, int c, double hx, double hy, double hz) {
+  if (a == 0 && b == 0 && c == 0) return 1.0 / std::fmin(hx, std::fmin(hy, hz));
+  const double u = a * hx, v = b * hy, w = c * hz;
+  return 1.0 / std::sqrt(u * u + v * v + w * w);
+}
+
+double poisson_at(const double* rho, int mx, int my, int mz, double hx, double hy, double hz, int i, int j,
+                  int k) {
+  Neumaier acc;
+  for (int a = 0; a < mx; ++a)
+    for (int b = 0; b < my; ++b)
+      for (int c = 0; c < mz; ++c) {
+        const double q = rho[(static_cast<int64_t>(a) * my + b) * mz + c];
+        if (q != 0.0) acc.add(q * poisson_green(std::abs(i - a), std::abs(j - b), std::abs(k - c), hx, hy, hz));
+      }
+  return hx * hy * hz * acc.value();
+}
+
+// phi on the whole mesh.
+void oracle_poisson_direct(const double* rho, int mx, int my, int mz, double hx, double hy, double hz,
+                           double* phi) {
+  for (int i = 0; i < mx; ++i)
+    for (int j = 0; j < my; ++j)
+      for (int k = 0; k < mz; ++k)
+        phi[(static_cast<int64_t>(i) * my + j) * mz + k] = poisson_at(rho, mx, my, mz, hx, hy, hz, i, j, k);
+}
+
+// phi at npts mesh points ijk[npts][3] only (for samples of large meshes).
+void oracle_poisson_points(const double* rho, int mx, int my, int mz, double hx, double hy, double hz,
+                           const int32_t* ijk, int npts, double* out) {
+  for (int p = 0; p < npts; ++p)
+    out[p] = poisson_at(rho, mx, my, mz, hx, hy, hz, ijk[3 * p], ijk[3 * p + 1], ijk[3 * p + 2]);
 }
 
 // Neumaier-compensated sum of n doubles, exposed so that the summation itself

@@ -49,6 +49,12 @@ MUTANTS = {
     "Bessel derivative sign": ("      *d0 = -j1 * 2.0 * kPi * t;", "      *d0 = j1 * 2.0 * kPi * t;"),
     "stretched exponent derivative drops the log": ("*d1 = -xb * std::log(x) * f;", "*d1 = -xb * f;"),
     "stretched rate derivative drops beta": ("(-p1 * xb / lam) * f;", "(-xb / lam) * f;"),
+    "Poisson spacings transposed": ("const double u = a * hx, v = b * hy, w = c * hz;",
+                                    "const double u = a * hy, v = b * hx, w = c * hz;"),
+    "Poisson volume factor dropped": ("return hx * hy * hz * acc.value();", "return acc.value();"),
+    "Poisson self term": ("return 1.0 / std::fmin(hx, std::fmin(hy, hz));", "return 0.0;"),
+    "Poisson source offset": ("std::abs(i - a), std::abs(j - b), std::abs(k - c)",
+                              "std::abs(i - a), std::abs(j - b), std::abs(k - c + 1)"),
     "asymmetry variance drops the 4": ("const double var = 4.0 * al * al *", "const double var = al * al *"),
     "asymmetry alpha on the forward count": ("a[i] = (f - al * b) / D;", "a[i] = (al * f - b) / D;"),
     "asymmetry variances exchanged": ("(b * b * std::fmax(F[i], 1.0) + f * f * std::fmax(B[i], 1.0))",

@@ -564,3 +564,55 @@ def test_gradient_of_new_primitives_matches_central_differences():
             xm[i] -= h
             fd = (oracle.cost(q, xp, mode, grad=False)[0] - oracle.cost(q, xm, mode, grad=False)[0]) / (2 * h)
             assert abs(fd - g[i]) <= 1e-6 * gs[i], (i, fd, g[i])
+
+
+# ------------------------------------------------------------------------------------------
+# The particle-mesh Poisson solve (Section 3, Eq. openbruteforceconv), the second workload
+# ------------------------------------------------------------------------------------------
+
+def test_poisson_point_charge():
+    """One charge q at a mesh point: phi = hx hy hz q / r at every other point (anisotropic
+    spacing) and hx hy hz q / min(h) at the charge (the reading of the singular self term).
+    Catches transposed spacings, a missing volume factor and an offset of the source."""
+    h = (0.5, 0.7, 1.1)
+    rho = np.zeros((7, 6, 5))
+    rho[2, 4, 1] = 3.0
+    phi = oracle.poisson_direct(rho, h)
+    V = h[0] * h[1] * h[2]
+    i, j, k = np.meshgrid(np.arange(7), np.arange(6), np.arange(5), indexing="ij")
+    r = np.sqrt(((i - 2) * h[0]) ** 2 + ((j - 4) * h[1]) ** 2 + ((k - 1) * h[2]) ** 2)
+    far = r > 0
+    assert np.max(np.abs(phi[far] * r[far] / (V * 3.0) - 1.0)) < 1e-14
+    assert phi[2, 4, 1] == pytest.approx(V * 3.0 / 0.5, rel=1e-15)
+
+
+def test_poisson_direct_sum_equals_fft_convolution():
+    """The direct sum equals the linear convolution computed by numpy's FFT on the doubled,
+    zero-padded mesh (an independent algorithm for the same sum)."""
+    rng = np.random.default_rng(19)
+    h = (0.3, 0.45, 0.2)
+    rho = rng.normal(size=(9, 7, 6))
+    phi = oracle.poisson_direct(rho, h)
+    M = rho.shape
+    N = tuple(2 * m for m in M)
+    a, b, c = np.meshgrid(*[np.minimum(np.arange(n), n - np.arange(n)) for n in N], indexing="ij")
+    G = 1.0 / np.sqrt((a * h[0]) ** 2 + (b * h[1]) ** 2 + (c * h[2]) ** 2 + (a + b + c == 0))
+    G[0, 0, 0] = 1.0 / min(h)
+    ax = (0, 1, 2)
+    conv = np.fft.irfftn(np.fft.rfftn(rho, N, axes=ax) * np.fft.rfftn(G, axes=ax), N, axes=ax)[: M[0], : M[1], : M[2]]
+    ref = h[0] * h[1] * h[2] * conv
+    assert np.max(np.abs(phi - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_poisson_far_field_is_the_monopole():
+    """Far from a compact, symmetric charge the potential is that of its total charge,
+    hx hy hz Q / r, to the order (size / r)^4 (the dipole and quadrupole vanish)."""
+    h = (1.0, 1.0, 1.0)
+    rho = np.zeros((26, 26, 26))
+    rho[11:14, 11:14, 11:14] = 1.0
+    rho[12, 12, 12] = 5.0
+    Q = rho.sum()
+    ijk = np.array([[0, 0, 0], [25, 12, 12], [12, 0, 25], [25, 25, 0]])
+    phi = oracle.poisson_points(rho, h, ijk)
+    r = np.sqrt(((ijk - 12) ** 2).sum(axis=1))
+    assert np.max(np.abs(phi * r / Q - 1.0)) < 2e-3
