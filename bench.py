@@ -375,10 +375,11 @@ def run_ours(args, rank, world, local_rank):
                 "algorithmic_bytes": algo_bytes,
                 "hbm_frac": algo_bytes / t_kernel / 1e9 / float(peaks.get("hbm_gbs", 6800.0))}
 
-    fits = asym = None
+    fits = asym = poisson = None
     if not args.no_fits and rank == 0:
         fits = _fits(p, ctx, B, mode)
         asym = _asymmetry(B, flush, stream)
+        poisson = _poisson(B, peaks, cpu=not args.no_cpu)
     serving = None
     if args.serving_requests > 0 and rank == 0:
         serving = _serving(B, args.serving_requests)
@@ -397,7 +398,7 @@ def run_ours(args, rank, world, local_rank):
                 "gpu_launches": args.steps, "wall_s_timed_region": t_wall,
                 "fp64_path": {"value": fp64_gbins, "unit": "Gbins/s", "split_speedup": value / world / fp64_gbins,
                               "max_rel_value_diff_split_vs_fp64": rel_err},
-                "fits": fits, "asymmetry": asym, "serving": serving, "cpu_baseline": cpu}
+                "fits": fits, "asymmetry": asym, "poisson": poisson, "serving": serving, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -438,6 +439,80 @@ def _asymmetry(B, flush, stream, steps=10):
     out["split_speedup"] = out["split_gbins_per_s"] / out["fp64_gbins_per_s"]
     out["max_rel_value_diff_split_vs_fp64"] = float(np.max(np.abs(res["split"][:, 0] - res["fp64"][:, 0]) /
                                                            np.abs(res["fp64"][:, 0])))
+    return out
+
+
+# Algorithmic bytes of one particle-mesh Poisson solve per mesh point (M points, doubled mesh
+# N = 8 M with N/2 complex points, FP64 density in and potential out, r bytes per real of the
+# transforms): pad (read 8 M, write r N), forward FFT (read r N, write r N), Hadamard product
+# (read r N + r N / 2, write r N), inverse FFT (read r N, write r N), extraction (read r M,
+# write 8 M), each array touched once: 504 bytes per mesh point in FP64, 264 in FP32.
+POISSON_BYTES_PER_POINT = {0: 504, 1: 264}
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 nominal FP64 (not measured on this machine)
+
+
+def _poisson(B, peaks, cpu=True):
+    """The particle-mesh Poisson solve of Section 3 on the meshes of the paper's benchmark
+    table, FP64 and FP32 transforms: device time per solve (CUDA events on the solver's
+    stream, median of 7), end to end through the host-array call, achieved GB/s of the
+    algorithmic bytes (and, for FP64, the transforms' FLOP rate, 2 x 2.5 N log2 N, against the
+    nominal FP64 peak); the oracle's direct sum timed on sampled points of the smallest mesh."""
+    import torch
+    import oracle
+    out = {"workload": "open-boundary Poisson solve (Hockney, doubled mesh) of a Gaussian bunch",
+           "bytes_per_mesh_point": {"fp64": 504, "fp32_transforms": 264}, "meshes": []}
+    stream = torch.cuda.Stream()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    for shape in ((64, 64, 32), (128, 128, 64), (256, 256, 128), (512, 512, 256)):
+        M = int(np.prod(shape))
+        N = 8 * M
+        x, y, z = np.meshgrid(*[np.arange(n, dtype=np.float64) for n in shape], indexing="ij", sparse=True)
+        rho = np.exp(-0.5 * (((x - 0.45 * shape[0]) / (0.1 * shape[0])) ** 2 +
+                             ((y - 0.5 * shape[1]) / (0.1 * shape[1])) ** 2 +
+                             ((z - 0.55 * shape[2]) / (0.1 * shape[2])) ** 2))
+        rho = np.ascontiguousarray(rho)
+        h = (1.0 / shape[0], 1.0 / shape[1], 2.0 / shape[2])
+        entry = {"mesh": list(shape), "e2e_h2d_d2h_bytes": 16 * M}
+        phis = {}
+        for prec, name in ((B.MUSR_SPLIT, "fp32_transforms"), (B.MUSR_FP64, "fp64")):
+            with B.Poisson(shape, h, prec, cuda_stream=stream.cuda_stream) as ps:
+                d_rho = torch.tensor(rho, device="cuda")
+                d_phi = torch.empty_like(d_rho)
+                for _ in range(2):
+                    ps.solve_device(d_rho.data_ptr(), d_phi.data_ptr())
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(7)]
+                for a, b in ev:
+                    a.record(stream)
+                    ps.solve_device(d_rho.data_ptr(), d_phi.data_ptr())
+                    b.record(stream)
+                torch.cuda.synchronize()
+                t = float(np.median([a.elapsed_time(b) * 1e-3 for a, b in ev]))
+                phis[name] = ps.solve(rho)
+                t0 = time.perf_counter()
+                for _ in range(3):
+                    ps.solve(rho)
+                t_e2e = (time.perf_counter() - t0) / 3
+                del d_rho, d_phi
+            gbs = POISSON_BYTES_PER_POINT[prec] * M / t / 1e9
+            r = {"ms_per_solve": t * 1e3, "e2e_ms_per_solve": t_e2e * 1e3, "achieved_gbs": gbs, "hbm_frac": gbs / hbm}
+            if prec == B.MUSR_FP64:
+                tf = 2 * 2.5 * N * math.log2(N) / t / 1e12
+                r |= {"fft_tflops": tf, "fp64_nominal_frac": tf / FP64_NOMINAL_TFLOPS}
+            entry[name] = r
+        entry["max_rel_diff_fp32_vs_fp64"] = float(np.max(np.abs(phis["fp32_transforms"] - phis["fp64"])) /
+                                                   np.max(np.abs(phis["fp64"])))
+        entry["fp32_speedup"] = entry["fp64"]["ms_per_solve"] / entry["fp32_transforms"]["ms_per_solve"]
+        out["meshes"].append(entry)
+        if cpu and shape == (64, 64, 32):
+            ijk = np.stack([np.random.default_rng(6).integers(0, n, 24) for n in shape], axis=1)
+            t0 = time.perf_counter()
+            oracle.poisson_points(rho, h, ijk)
+            per_point = (time.perf_counter() - t0) / len(ijk)
+            out["cpu_baseline"] = {"kind": "oracle", "cores": 1, "mesh": list(shape),
+                                   "direct_sum_s_per_solve": per_point * M,
+                                   "sample": f"{len(ijk)} mesh points by direct summation, scaled to the {M} points"}
+    out["peak_hbm_gbs"] = hbm
+    out["fp64_nominal_tflops"] = FP64_NOMINAL_TFLOPS
     return out
 
 

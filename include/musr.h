@@ -354,6 +354,47 @@ int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int64_t nbins,
                       const double* consts, int nconsts, const double* d_params, int mode,
                       int precision, int with_grad, double* d_out, void* cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * The particle-mesh Poisson solve of Section 3 ("FFT Based Particle-Mesh
+ * Solver"): the potential of an isolated charge density on an mx x my x mz
+ * mesh with spacings hx, hy, hz,
+ *     phi_{i,j,k} = hx hy hz sum rho_{i',j',k'} G_{i-i',j-j',k-k'},
+ *     G_{a,b,c} = 1 / sqrt((a hx)^2 + (b hy)^2 + (c hz)^2)
+ * (Eq. openbruteforceconv; G_{0,0,0}, where 1/r is singular, is 1/min(h)),
+ * computed by Hockney's method (Eq. oneterm): the density zero-padded to the
+ * doubled mesh, FP64 FFTs, the Hadamard product with the transform of G (real,
+ * computed once per solver), the inverse FFT, the original block kept.
+ * Arrays are [mx][my][mz] FP64, z fastest.
+ * ------------------------------------------------------------------------- */
+
+typedef struct musr_poisson musr_poisson;
+
+/* Creates a solver for one mesh on CUDA device `device` (cuda_stream as for
+ * musr_ctx_create; NULL: its own stream): allocates the doubled-mesh buffers
+ * (about 40 mx my mz reals) and the FFT plans, and transforms G.  precision:
+ * MUSR_FP64 (FP64 transforms) or MUSR_SPLIT (FP32 transforms between the FP64
+ * density and potential; 2-norm relative error of phi below about
+ * 10 log2(8 mx my mz) 2^-24, first-order FFT error bounds).  mx, my, mz >= 1
+ * with 8 mx my mz < 2^31; spacings finite and > 0.  *out is NULL on failure
+ * (MUSR_ENOMEM when the device has no room). */
+int musr_poisson_create(musr_poisson** out, int device, int mx, int my, int mz, double hx, double hy, double hz,
+                        int precision, void* cuda_stream);
+
+/* Frees the solver.  NULL is ignored. */
+void musr_poisson_destroy(musr_poisson* ps);
+
+/* Text of the last error of the solver ("" if none); ps NULL: of the last
+ * failed musr_poisson_create on this thread. */
+const char* musr_poisson_last_error(const musr_poisson* ps);
+
+/* phi [mx][my][mz] of rho [mx][my][mz], host arrays.  Synchronous: copies rho
+ * in, solves, copies phi out. */
+int musr_poisson_solve(musr_poisson* ps, const double* rho, double* phi);
+
+/* The same on device arrays of the solver's device, enqueued on its stream
+ * (returns before the solve ends; the arrays must stay valid until then). */
+int musr_poisson_solve_device(musr_poisson* ps, const double* d_rho, double* d_phi);
+
 #ifdef __cplusplus
 }
 #endif

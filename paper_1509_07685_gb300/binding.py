@@ -34,7 +34,8 @@ EXPORTS = (
     "musr_gauss_newton",
     "musr_launches_per_eval", "musr_eval_noalloc", "musr_fit", "musr_server_create",
     "musr_server_destroy", "musr_server_submit", "musr_server_poll", "musr_server_wait",
-    "musr_server_stats_get",
+    "musr_server_stats_get", "musr_poisson_create", "musr_poisson_destroy", "musr_poisson_last_error",
+    "musr_poisson_solve", "musr_poisson_solve_device",
 )
 
 
@@ -90,6 +91,12 @@ def _declare(lib):
         "musr_ctx_destroy": ([vp], None),
         "musr_last_error": ([vp], ctypes.c_char_p),
         "musr_upload_histograms": ([vp, vp, ctypes.c_int, ctypes.c_int, i64, P(d), d, P(d)], ctypes.c_int),
+        "musr_poisson_create": ([P(vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, d, d, d,
+                                 ctypes.c_int, vp], ctypes.c_int),
+        "musr_poisson_destroy": ([vp], None),
+        "musr_poisson_last_error": ([vp], ctypes.c_char_p),
+        "musr_poisson_solve": ([vp, P(d), P(d)], ctypes.c_int),
+        "musr_poisson_solve_device": ([vp, vp, vp], ctypes.c_int),
         "musr_upload_asymmetry": ([vp, vp, vp, ctypes.c_int, ctypes.c_int, i64, P(d), d, P(d), P(d), P(d), P(d)],
                                   ctypes.c_int),
         "musr_upload_histograms_device": ([vp, vp, ctypes.c_int, ctypes.c_int, i64, i64, P(d), d, P(d)],
@@ -548,6 +555,56 @@ class Server:
         if self.srv:
             musr_server_destroy(self.srv)
             self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Poisson:
+    """Owns one musr_poisson: the open-boundary particle-mesh Poisson solve of Section 3 on an
+    (mx, my, mz) mesh with spacings h = (hx, hy, hz); precision MUSR_FP64 (FP64 transforms) or
+    MUSR_SPLIT (FP32 transforms)."""
+
+    def __init__(self, shape, h, precision: int = MUSR_FP64, device: int = 0, cuda_stream: Optional[int] = None):
+        self.shape = tuple(int(v) for v in shape)
+        out = ctypes.c_void_p()
+        st = load().musr_poisson_create(ctypes.byref(out), device, *self.shape, float(h[0]), float(h[1]),
+                                        float(h[2]), int(precision),
+                                        ctypes.c_void_p(cuda_stream) if cuda_stream else None)
+        if st != MUSR_OK:
+            msg = load().musr_poisson_last_error(None)
+            raise MusrError(st, msg.decode() if msg else "musr_poisson_create failed")
+        self.ps = out
+
+    def _check(self, st):
+        if st != MUSR_OK:
+            msg = load().musr_poisson_last_error(self.ps)
+            raise MusrError(st, msg.decode() if msg else "musr_poisson call failed")
+
+    def solve(self, rho: np.ndarray) -> np.ndarray:
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        if rho.shape != self.shape:
+            raise ValueError(f"rho must have shape {self.shape}")
+        phi = np.empty_like(rho)
+        self._check(load().musr_poisson_solve(self.ps, _dptr(rho), _dptr(phi)))
+        return phi
+
+    def solve_device(self, d_rho: int, d_phi: int) -> None:
+        self._check(load().musr_poisson_solve_device(self.ps, ctypes.c_void_p(d_rho), ctypes.c_void_p(d_phi)))
+
+    def close(self) -> None:
+        if self.ps:
+            load().musr_poisson_destroy(self.ps)
+            self.ps = None
 
     def __del__(self):
         try:

@@ -55,7 +55,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 raise RuntimeError(f"nvcc failed: {' '.join(j)}")
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"])
+        subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread", "-lcufft"])
         os.replace(tmp, LIB)
     return LIB
 
