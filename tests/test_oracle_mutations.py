@@ -71,13 +71,13 @@ MUTANTS = {
 SCRATCH = os.path.join(ROOT, "tests", "_mutants")  # git-ignored
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_catch_planted_mistake(name):
+def _run_mutant(name):
+    """Builds the mutant and runs the pins against it; returns (caught, pytest output tail)."""
     old, new = MUTANTS[name]
     src = open(SRC).read()
-    assert src.count(old) >= 1, f"mutation site not found: {name}"
+    if src.count(old) < 1:
+        return None, f"mutation site not found: {name}"
     mutated = src.replace(old, new, 1)
-    os.makedirs(SCRATCH, exist_ok=True)
     tag = "".join(c if c.isalnum() else "_" for c in name)
     cpp = os.path.join(SCRATCH, tag + ".cpp")
     lib = os.path.join(SCRATCH, tag + ".so")
@@ -89,4 +89,21 @@ def test_pins_catch_planted_mistake(name):
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert r.returncode != 0, f"no pin caught the mutant '{name}':\n{r.stdout[-2000:]}"
+    return r.returncode != 0, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def outcomes():
+    """Every mutant built and pinned once, several at a time (each in its own processes)."""
+    from concurrent.futures import ThreadPoolExecutor
+    os.makedirs(SCRATCH, exist_ok=True)
+    names = sorted(MUTANTS)
+    with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        return dict(zip(names, ex.map(_run_mutant, names)))
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, outcomes):
+    caught, tail = outcomes[name]
+    assert caught is not None, tail
+    assert caught, f"no pin caught the mutant '{name}':\n{tail}"
