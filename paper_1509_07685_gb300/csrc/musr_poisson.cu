@@ -48,6 +48,9 @@ int64_t grid_for(int64_t n, int num_sms) {
   return want < 8LL * num_sms ? (want > 0 ? want : 1) : 8LL * num_sms;
 }
 
+// Row-wise kernels: one CTA per row at a time, up to 32 CTAs per SM's worth of rows.
+int64_t rows_grid(int64_t rows, int num_sms) { return rows < 32LL * num_sms ? (rows > 0 ? rows : 1) : 32LL * num_sms; }
+
 template <class R>
 struct Cx;  // the complex type of each real type
 template <>
@@ -80,17 +83,21 @@ __global__ void real_part_kernel(const typename Cx<R>::type* in, R* out, int64_t
     out[e] = in[e].x;
 }
 
-// rho [mx][my][mz] (FP64) into the doubled mesh, zeros elsewhere.  One thread per z row
-// segment would avoid the divisions; the mesh index is split once per element here.
+// rho [mx][my][mz] (FP64) into the doubled mesh, zeros elsewhere: one CTA per (a, b) row of
+// the doubled mesh at a time, threads along z (coalesced, one index split per row).
 template <class R>
 __global__ void pad_kernel(const double* __restrict__ rho, R* __restrict__ pad, int mx, int my, int mz, int nx,
                            int ny, int nz) {
-  const int64_t total = static_cast<int64_t>(nx) * ny * nz;
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t a = e / (static_cast<int64_t>(ny) * nz), r = e - a * ny * static_cast<int64_t>(nz);
-    const int64_t b = r / nz, c = r - b * nz;
-    pad[e] = a < mx && b < my && c < mz ? static_cast<R>(rho[(a * my + b) * mz + c]) : R(0);
+  const int64_t rows = static_cast<int64_t>(nx) * ny;
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int64_t a = row / ny, b = row - a * ny;
+    R* dst = pad + row * nz;
+    if (a < mx && b < my) {
+      const double* src = rho + (a * my + b) * mz;
+      for (int c = threadIdx.x; c < nz; c += blockDim.x) dst[c] = c < mz ? static_cast<R>(src[c]) : R(0);
+    } else {
+      for (int c = threadIdx.x; c < nz; c += blockDim.x) dst[c] = R(0);
+    }
   }
 }
 
@@ -108,16 +115,16 @@ __global__ void hadamard_kernel(typename Cx<R>::type* __restrict__ hat, const R*
   }
 }
 
-// The M block of the doubled mesh, as FP64.
+// The M block of the doubled mesh, as FP64: one CTA per (i, j) row of M at a time.
 template <class R>
 __global__ void extract_kernel(const R* __restrict__ pad, double* __restrict__ phi, int mx, int my, int mz, int ny,
                                int nz) {
-  const int64_t total = static_cast<int64_t>(mx) * my * mz;
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t i = e / (static_cast<int64_t>(my) * mz), r = e - i * my * static_cast<int64_t>(mz);
-    const int64_t j = r / mz, k = r - j * mz;
-    phi[e] = static_cast<double>(pad[(i * ny + j) * nz + k]);
+  const int64_t rows = static_cast<int64_t>(mx) * my;
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int64_t i = row / my, j = row - i * my;
+    const R* src = pad + (i * ny + j) * nz;
+    double* dst = phi + row * mz;
+    for (int k = threadIdx.x; k < mz; k += blockDim.x) dst[k] = static_cast<double>(src[k]);
   }
 }
 
@@ -178,11 +185,10 @@ template <class R>
 int enqueue_solve_t(musr_poisson* ps, const double* d_rho, double* d_phi) {
   const int64_t total = static_cast<int64_t>(ps->nx) * ps->ny * ps->nz;
   const int64_t nhat = static_cast<int64_t>(ps->nx) * ps->ny * (ps->nz / 2 + 1);
-  const int64_t nm = static_cast<int64_t>(ps->mx) * ps->my * ps->mz;
   R* pad = static_cast<R*>(ps->pad);
   auto* hat = static_cast<typename Cx<R>::type*>(ps->hat);
-  pad_kernel<R><<<grid_for(total, ps->num_sms), 256, 0, ps->stream>>>(d_rho, pad, ps->mx, ps->my, ps->mz, ps->nx,
-                                                                      ps->ny, ps->nz);
+  pad_kernel<R><<<rows_grid(static_cast<int64_t>(ps->nx) * ps->ny, ps->num_sms), 256, 0, ps->stream>>>(
+      d_rho, pad, ps->mx, ps->my, ps->mz, ps->nx, ps->ny, ps->nz);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(ps, e, "pad kernel");
   cufftResult r = exec_fwd(ps);
@@ -194,8 +200,8 @@ int enqueue_solve_t(musr_poisson* ps, const double* d_rho, double* d_phi) {
   if (e != cudaSuccess) return cuda_err(ps, e, "hadamard kernel");
   r = exec_inv(ps);
   if (r != CUFFT_SUCCESS) return fft_err(ps, r, "inverse FFT");
-  extract_kernel<R><<<grid_for(nm, ps->num_sms), 256, 0, ps->stream>>>(pad, d_phi, ps->mx, ps->my, ps->mz, ps->ny,
-                                                                       ps->nz);
+  extract_kernel<R><<<rows_grid(static_cast<int64_t>(ps->mx) * ps->my, ps->num_sms), 256, 0, ps->stream>>>(
+      pad, d_phi, ps->mx, ps->my, ps->mz, ps->ny, ps->nz);
   e = cudaGetLastError();
   return e == cudaSuccess ? MUSR_OK : cuda_err(ps, e, "extract kernel");
 }
