@@ -87,6 +87,10 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=10000,
                     help="fit requests of the serving measurement (0: skip)")
+    ap.add_argument("--poisson-only", action="store_true",
+                    help="run only the particle-mesh Poisson leg and print its JSON")
+    ap.add_argument("--poisson-meshes", default="64x64x32,128x128x64,256x256x128,512x512x256",
+                    help="comma-separated mx x my x mz meshes of the Poisson leg")
     ap.add_argument("--precision-report", action="store_true",
                     help="instead of timing: the SPLIT path's error against FP64 for every config "
                          "(cost value, gradient, fitted parameters in units of sigma)")
@@ -379,7 +383,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_fits and rank == 0:
         fits = _fits(p, ctx, B, mode)
         asym = _asymmetry(B, flush, stream)
-        poisson = _poisson(B, peaks, cpu=not args.no_cpu)
+        poisson = _poisson(B, peaks, cpu=not args.no_cpu, meshes=_meshes(args))
     serving = None
     if args.serving_requests > 0 and rank == 0:
         serving = _serving(B, args.serving_requests)
@@ -443,15 +447,16 @@ def _asymmetry(B, flush, stream, steps=10):
 
 
 # Algorithmic bytes of one particle-mesh Poisson solve per mesh point (M points, doubled mesh
-# N = 8 M with N/2 complex points, FP64 density in and potential out, r bytes per real of the
-# transforms): pad (read 8 M, write r N), forward FFT (read r N, write r N), Hadamard product
-# (read r N + r N / 2, write r N), inverse FFT (read r N, write r N), extraction (read r M,
-# write 8 M), each array touched once: 504 bytes per mesh point in FP64, 264 in FP32.
-POISSON_BYTES_PER_POINT = {0: 504, 1: 264}
+# N = 8 M with N/2 complex points, r bytes per real of the transforms, FP64 density in and
+# potential out): pad (read 8 M, write r M: the zeros stay), forward FFT (read r N, write r N),
+# Hadamard product (read r N + r N / 2, write r N), inverse FFT (read r N, write r N),
+# extraction (read r M, write 8 M), each array touched once: (16 + 54 r) M, i.e. 448 bytes per
+# mesh point with FP64 transforms and 232 with FP32 ones.
+POISSON_BYTES_PER_POINT = {0: 448, 1: 232}
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 nominal FP64 (not measured on this machine)
 
 
-def _poisson(B, peaks, cpu=True):
+def _poisson(B, peaks, cpu=True, meshes=((64, 64, 32), (128, 128, 64), (256, 256, 128), (512, 512, 256))):
     """The particle-mesh Poisson solve of Section 3 on the meshes of the paper's benchmark
     table, FP64 and FP32 transforms: device time per solve (CUDA events on the solver's
     stream, median of 7), end to end through the host-array call, achieved GB/s of the
@@ -460,10 +465,11 @@ def _poisson(B, peaks, cpu=True):
     import torch
     import oracle
     out = {"workload": "open-boundary Poisson solve (Hockney, doubled mesh) of a Gaussian bunch",
-           "bytes_per_mesh_point": {"fp64": 504, "fp32_transforms": 264}, "meshes": []}
+           "bytes_per_mesh_point": {"fp64": 448, "fp32_transforms": 232}, "meshes": []}
     stream = torch.cuda.Stream()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    for shape in ((64, 64, 32), (128, 128, 64), (256, 256, 128), (512, 512, 256)):
+    for shape in meshes:
+        shape = tuple(shape)
         M = int(np.prod(shape))
         N = 8 * M
         x, y, z = np.meshgrid(*[np.arange(n, dtype=np.float64) for n in shape], indexing="ij", sparse=True)
@@ -672,10 +678,31 @@ def precision_report(args):
     print(json.dumps({"precision_report": out}), flush=True)
 
 
+def _meshes(args):
+    return [tuple(int(v) for v in m.split("x")) for m in args.poisson_meshes.split(",") if m]
+
+
+def poisson_only(args):
+    """The particle-mesh Poisson leg alone (one GPU): its JSON object on one line."""
+    import torch
+    from paper_1509_07685_gb300 import binding as B
+    torch.cuda.set_device(0)
+    B.load()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    print(json.dumps({"poisson": _poisson(B, peaks, cpu=not args.no_cpu, meshes=_meshes(args))}), flush=True)
+
+
 def main():
     args = _args()
     if args.precision_report:
         precision_report(args)
+        return
+    if args.poisson_only:
+        poisson_only(args)
         return
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)

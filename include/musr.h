@@ -371,7 +371,7 @@ typedef struct musr_poisson musr_poisson;
 
 /* Creates a solver for one mesh on CUDA device `device` (cuda_stream as for
  * musr_ctx_create; NULL: its own stream): allocates the doubled-mesh buffers
- * (about 40 mx my mz reals) and the FFT plans, and transforms G.  precision:
+ * (about 48 mx my mz reals) and the FFT plans, and transforms G.  precision:
  * MUSR_FP64 (FP64 transforms) or MUSR_SPLIT (FP32 transforms between the FP64
  * density and potential; 2-norm relative error of phi below about
  * 10 log2(8 mx my mz) 2^-24, first-order FFT error bounds).  mx, my, mz >= 1

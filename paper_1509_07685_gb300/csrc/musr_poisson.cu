@@ -9,7 +9,8 @@
 // at MUSR_SPLIT precision, in FP32 (R2C, C2R; FP64 density in and potential out): GB300's
 // FP64 rate makes the FP64 transforms arithmetic-bound, the FP32 ones are memory-bound;
 // padding, the Green's function, the Hadamard product (with the 1/N^3 of the inverse
-// transform and hx hy hz folded in) and the extraction are kernels of this file.
+// transform and hx hy hz folded in) and the extraction are kernels of this file.  The padded
+// density's zeros are written once (solves write the M block only).
 // Reading: G_{0,0,0}, where 1/r is singular, is 1 / min(hx, hy, hz).
 #include <cuda_runtime.h>
 #include <cufft.h>
@@ -30,7 +31,8 @@ struct musr_poisson {
   double hx = 0, hy = 0, hz = 0;
   cufftHandle fwd = 0, inv = 0;
   bool have_fwd = false, have_inv = false;
-  void* pad = nullptr;   // [nx][ny][nz] real: padded density, then the potential
+  void* pad = nullptr;   // [nx][ny][nz] real: the padded density (its zeros written once)
+  void* out = nullptr;   // [nx][ny][nz] real: the inverse transform's result
   void* hat = nullptr;   // [nx][ny][nz / 2 + 1] complex
   void* ghat = nullptr;  // FT{G}, real, [nx][ny][nz / 2 + 1]
   double* rho = nullptr;  // [mx][my][mz] staging of the host entry point
@@ -48,8 +50,15 @@ int64_t grid_for(int64_t n, int num_sms) {
   return want < 8LL * num_sms ? (want > 0 ? want : 1) : 8LL * num_sms;
 }
 
-// Row-wise kernels: one CTA per row at a time, up to 32 CTAs per SM's worth of rows.
-int64_t rows_grid(int64_t rows, int num_sms) { return rows < 32LL * num_sms ? (rows > 0 ? rows : 1) : 32LL * num_sms; }
+// Threads of a row-wise kernel: one per work unit of the row, a multiple of 32, at most 256.
+int row_block(int units) { return units >= 256 ? 256 : ((units + 31) / 32) * 32; }
+
+// Grid of the row-wise kernels: x over the inner row index (ny or my <= 2^11 here), y over
+// the outer one, up to about 32 CTAs per SM in all.
+dim3 rows_grid(int inner, int outer, int num_sms) {
+  const int want = (32 * num_sms + inner - 1) / inner;
+  return dim3(static_cast<unsigned>(inner), static_cast<unsigned>(want < outer ? (want > 0 ? want : 1) : outer));
+}
 
 template <class R>
 struct Cx;  // the complex type of each real type
@@ -83,21 +92,29 @@ __global__ void real_part_kernel(const typename Cx<R>::type* in, R* out, int64_t
     out[e] = in[e].x;
 }
 
-// rho [mx][my][mz] (FP64) into the doubled mesh, zeros elsewhere: one CTA per (a, b) row of
-// the doubled mesh at a time, threads along z (coalesced, one index split per row).
 template <class R>
-__global__ void pad_kernel(const double* __restrict__ rho, R* __restrict__ pad, int mx, int my, int mz, int nx,
-                           int ny, int nz) {
-  const int64_t rows = static_cast<int64_t>(nx) * ny;
-  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-    const int64_t a = row / ny, b = row - a * ny;
-    R* dst = pad + row * nz;
-    if (a < mx && b < my) {
-      const double* src = rho + (a * my + b) * mz;
-      for (int c = threadIdx.x; c < nz; c += blockDim.x) dst[c] = c < mz ? static_cast<R>(src[c]) : R(0);
-    } else {
-      for (int c = threadIdx.x; c < nz; c += blockDim.x) dst[c] = R(0);
-    }
+struct Pair;  // two consecutive reals, one vector store
+template <>
+struct Pair<double> {
+  using type = double2;
+};
+template <>
+struct Pair<float> {
+  using type = float2;
+};
+
+// rho [mx][my][mz] (FP64) into the M block of the doubled mesh.  The rest of the doubled
+// mesh holds zeros written once: the forward transform is out of place and leaves its
+// input as it is (the inverse writes to a buffer of its own).  CTA (b, y0) takes the rows
+// (a, b) for a = y0, y0 + gridDim.y, ... < mx.
+template <class R>
+__global__ void pad_kernel(const double* __restrict__ rho, R* __restrict__ pad, int mx, int my, int mz, int ny,
+                           int nz) {
+  const int b = blockIdx.x;
+  for (int a = blockIdx.y; a < mx; a += gridDim.y) {
+    R* dst = pad + (static_cast<int64_t>(a) * ny + b) * nz;
+    const double* src = rho + (static_cast<int64_t>(a) * my + b) * mz;
+    for (int c = threadIdx.x; c < mz; c += blockDim.x) dst[c] = static_cast<R>(src[c]);
   }
 }
 
@@ -115,15 +132,15 @@ __global__ void hadamard_kernel(typename Cx<R>::type* __restrict__ hat, const R*
   }
 }
 
-// The M block of the doubled mesh, as FP64: one CTA per (i, j) row of M at a time.
+// The M block of the doubled mesh, as FP64.  CTA (j, y0) takes the rows (i, j) of M for
+// i = y0, y0 + gridDim.y, ...
 template <class R>
 __global__ void extract_kernel(const R* __restrict__ pad, double* __restrict__ phi, int mx, int my, int mz, int ny,
                                int nz) {
-  const int64_t rows = static_cast<int64_t>(mx) * my;
-  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-    const int64_t i = row / my, j = row - i * my;
-    const R* src = pad + (i * ny + j) * nz;
-    double* dst = phi + row * mz;
+  const int j = blockIdx.x;
+  for (int i = blockIdx.y; i < mx; i += gridDim.y) {
+    const R* src = pad + (static_cast<int64_t>(i) * ny + j) * nz;
+    double* dst = phi + (static_cast<int64_t>(i) * my + j) * mz;
     for (int k = threadIdx.x; k < mz; k += blockDim.x) dst[k] = static_cast<double>(src[k]);
   }
 }
@@ -161,6 +178,7 @@ void release(musr_poisson* ps) {
   if (ps->have_fwd) cufftDestroy(ps->fwd);
   if (ps->have_inv) cufftDestroy(ps->inv);
   cudaFree(ps->pad);
+  cudaFree(ps->out);
   cudaFree(ps->hat);
   cudaFree(ps->ghat);
   cudaFree(ps->rho);
@@ -176,8 +194,8 @@ cufftResult exec_fwd(musr_poisson* ps) {
 
 cufftResult exec_inv(musr_poisson* ps) {
   return ps->precision == MUSR_FP64
-             ? cufftExecZ2D(ps->inv, static_cast<cufftDoubleComplex*>(ps->hat), static_cast<double*>(ps->pad))
-             : cufftExecC2R(ps->inv, static_cast<cufftComplex*>(ps->hat), static_cast<float*>(ps->pad));
+             ? cufftExecZ2D(ps->inv, static_cast<cufftDoubleComplex*>(ps->hat), static_cast<double*>(ps->out))
+             : cufftExecC2R(ps->inv, static_cast<cufftComplex*>(ps->hat), static_cast<float*>(ps->out));
 }
 
 // Enqueues one solve: d_rho [mx][my][mz] -> d_phi [mx][my][mz].
@@ -187,8 +205,8 @@ int enqueue_solve_t(musr_poisson* ps, const double* d_rho, double* d_phi) {
   const int64_t nhat = static_cast<int64_t>(ps->nx) * ps->ny * (ps->nz / 2 + 1);
   R* pad = static_cast<R*>(ps->pad);
   auto* hat = static_cast<typename Cx<R>::type*>(ps->hat);
-  pad_kernel<R><<<rows_grid(static_cast<int64_t>(ps->nx) * ps->ny, ps->num_sms), 256, 0, ps->stream>>>(
-      d_rho, pad, ps->mx, ps->my, ps->mz, ps->nx, ps->ny, ps->nz);
+  pad_kernel<R><<<rows_grid(ps->my, ps->mx, ps->num_sms), row_block(ps->mz), 0, ps->stream>>>(
+      d_rho, pad, ps->mx, ps->my, ps->mz, ps->ny, ps->nz);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(ps, e, "pad kernel");
   cufftResult r = exec_fwd(ps);
@@ -200,8 +218,8 @@ int enqueue_solve_t(musr_poisson* ps, const double* d_rho, double* d_phi) {
   if (e != cudaSuccess) return cuda_err(ps, e, "hadamard kernel");
   r = exec_inv(ps);
   if (r != CUFFT_SUCCESS) return fft_err(ps, r, "inverse FFT");
-  extract_kernel<R><<<rows_grid(static_cast<int64_t>(ps->mx) * ps->my, ps->num_sms), 256, 0, ps->stream>>>(
-      pad, d_phi, ps->mx, ps->my, ps->mz, ps->ny, ps->nz);
+  extract_kernel<R><<<rows_grid(ps->my, ps->mx, ps->num_sms), row_block(ps->mz), 0, ps->stream>>>(
+      static_cast<const R*>(ps->out), d_phi, ps->mx, ps->my, ps->mz, ps->ny, ps->nz);
   e = cudaGetLastError();
   return e == cudaSuccess ? MUSR_OK : cuda_err(ps, e, "extract kernel");
 }
@@ -226,6 +244,9 @@ int setup_green(musr_poisson* ps) {
   real_part_kernel<R><<<grid_for(nhat, ps->num_sms), 256, 0, ps->stream>>>(
       static_cast<const typename Cx<R>::type*>(ps->hat), static_cast<R*>(ps->ghat), nhat);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(ps, e, "real-part kernel");
+  // the padded density's zeros, once (solves write only the M block)
+  if ((e = cudaMemsetAsync(ps->pad, 0, sizeof(R) * total, ps->stream)) != cudaSuccess)
+    return cuda_err(ps, e, "cudaMemsetAsync(pad)");
   if ((e = cudaStreamSynchronize(ps->stream)) != cudaSuccess) return cuda_err(ps, e, "Green setup");
   return MUSR_OK;
 }
@@ -286,6 +307,7 @@ int musr_poisson_create(musr_poisson** out, int device, int mx, int my, int mz, 
   const int64_t nhat = static_cast<int64_t>(ps->nx) * ps->ny * (ps->nz / 2 + 1);
   const int64_t nm = static_cast<int64_t>(mx) * my * mz;
   cudaError_t e = cudaMalloc(&ps->pad, rsz * total);
+  if (e == cudaSuccess) e = cudaMalloc(&ps->out, rsz * total);
   if (e == cudaSuccess) e = cudaMalloc(&ps->hat, 2 * rsz * nhat);
   if (e == cudaSuccess) e = cudaMalloc(&ps->ghat, rsz * nhat);
   if (e == cudaSuccess) e = cudaMalloc(&ps->rho, sizeof(double) * nm);
