@@ -379,10 +379,11 @@ def run_ours(args, rank, world, local_rank):
                 "algorithmic_bytes": algo_bytes,
                 "hbm_frac": algo_bytes / t_kernel / 1e9 / float(peaks.get("hbm_gbs", 6800.0))}
 
-    fits = asym = poisson = None
+    fits = asym = poisson = lists = None
     if not args.no_fits and rank == 0:
         fits = _fits(p, ctx, B, mode)
         asym = _asymmetry(B, flush, stream)
+        lists = _term_lists(B, flush, stream)
         poisson = _poisson(B, peaks, cpu=not args.no_cpu, meshes=_meshes(args))
     serving = None
     if args.serving_requests > 0 and rank == 0:
@@ -402,7 +403,7 @@ def run_ours(args, rank, world, local_rank):
                 "gpu_launches": args.steps, "wall_s_timed_region": t_wall,
                 "fp64_path": {"value": fp64_gbins, "unit": "Gbins/s", "split_speedup": value / world / fp64_gbins,
                               "max_rel_value_diff_split_vs_fp64": rel_err},
-                "fits": fits, "asymmetry": asym, "poisson": poisson, "serving": serving, "cpu_baseline": cpu}
+                "fits": fits, "asymmetry": asym, "term_lists": lists, "poisson": poisson, "serving": serving, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -443,6 +444,53 @@ def _asymmetry(B, flush, stream, steps=10):
     out["split_speedup"] = out["split_gbins_per_s"] / out["fp64_gbins_per_s"]
     out["max_rel_value_diff_split_vs_fp64"] = float(np.max(np.abs(res["split"][:, 0] - res["fp64"][:, 0]) /
                                                            np.abs(res["fp64"][:, 0])))
+    return out
+
+
+def _term_lists(B, flush, stream, steps=10):
+    """Theories without a basis form on the paper's benchmark workload (16 x 81920 bins): its
+    model with the cosine replaced by a Bessel precession, and with the Gaussian replaced by a
+    stretched exponential (exponent shared); SPLIT (the term list per bin in FP32) and FP64,
+    chi^2 value+grad of 64 parameter vectors per launch (CUDA events, L2 flushed)."""
+    import dataclasses
+    import torch
+    import musr_inputs as mi
+    base = mi.paper_tf16(seed=33, n0=60.0)
+    P = base.nparams
+    theories = {
+        "bessel": dataclasses.replace(base, terms=[[("AMP", (2,)), ("GAUSS", (3,)), ("BESSEL", (4, 5))]]),
+        "stretched_exponential": dataclasses.replace(
+            base, terms=[[("AMP", (2,)), ("STREXP", (3, 6)), ("TFCOS", (4, 5))]],
+            map=np.hstack([base.map, np.full((base.H, 1), P, np.int32)]), nparams=P + 1,
+            truth=np.append(base.truth, 1.5), names=base.names + ["beta"]),
+    }
+    out = {"workload": "paper benchmark (16 x 81920 bins) with a Bessel precession or a stretched exponential, "
+                       "chi^2, fused value+grad, 64 parameter vectors per launch"}
+    for name, p in theories.items():
+        X = mi.jitter(p.truth, NVEC, seed=8, lo=0.97, hi=1.03)
+        with torch.cuda.stream(stream):
+            with B.Context(p, cuda_stream=stream.cuda_stream) as ctx:
+                bins = ctx.bins_in_fit()
+                dx = torch.tensor(X, dtype=torch.float64, device="cuda")
+                do = torch.empty((NVEC, 1 + p.nparams), dtype=torch.float64, device="cuda")
+                res, rate = {}, {}
+                for prec, pn in ((B.MUSR_SPLIT, "split"), (B.MUSR_FP64, "fp64")):
+                    for _ in range(2):
+                        B.musr_eval_device(ctx.ctx, dx.data_ptr(), NVEC, 0, prec, True, do.data_ptr())
+                    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                          for _ in range(steps if prec == B.MUSR_SPLIT else 2)]
+                    for a, b in ev:
+                        flush.zero_()
+                        a.record(stream)
+                        B.musr_eval_device(ctx.ctx, dx.data_ptr(), NVEC, 0, prec, True, do.data_ptr())
+                        b.record(stream)
+                    torch.cuda.synchronize()
+                    rate[pn] = bins * NVEC / float(np.mean([a.elapsed_time(b) * 1e-3 for a, b in ev])) / 1e9
+                    res[pn] = do.cpu().numpy().copy()
+        out[name] = {"split_gbins_per_s": rate["split"], "fp64_gbins_per_s": rate["fp64"],
+                     "split_speedup": rate["split"] / rate["fp64"],
+                     "max_rel_value_diff_split_vs_fp64": float(np.max(np.abs(res["split"][:, 0] - res["fp64"][:, 0]) /
+                                                                      np.abs(res["fp64"][:, 0])))}
     return out
 
 

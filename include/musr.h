@@ -57,7 +57,10 @@ enum { MUSR_CHI2 = 0, MUSR_MLE = 1 };
 /* MUSR_FP64: every per-bin operation in FP64 (the plain path).
  * MUSR_SPLIT: per-bin theory, residuals and gradient terms in FP32; FP64 for
  * the phase range reduction of 2 pi (nu t + phi/360) and for every
- * accumulation above the thread (block, grid, final sum). */
+ * accumulation above the thread (block, grid, final sum).  Theories whose
+ * terms factor into shared time functions with per-histogram coefficients use
+ * that basis form; others (a stretched exponential, a Bessel precession, two
+ * cosines in one term) evaluate the term list per bin in FP32. */
 enum { MUSR_FP64 = 0, MUSR_SPLIT = 1 };
 enum {
   MUSR_PRIM_AMP = 1,
@@ -67,9 +70,9 @@ enum {
   MUSR_PRIM_TFCOS = 5, /* slot[0] = nu (MHz), slot[1] = phi (degrees) */
   MUSR_PRIM_LKT = 6,   /* static Lorentzian Kubo-Toyabe 1/3 + 2/3 (1 - a t) exp(-a t); slot[0] = a (1/us) */
   MUSR_PRIM_STREXP = 7, /* stretched exponential exp(-(|lambda| t)^beta) for t > 0, 1 for t <= 0;
-                           slot[0] = lambda (1/us), slot[1] = beta.  MUSR_FP64 precision only */
+                           slot[0] = lambda (1/us), slot[1] = beta */
   MUSR_PRIM_BESSEL = 8  /* J0(2 pi (nu t + phi / 360)), Bessel precession (incommensurate order);
-                           slot[0] = nu (MHz), slot[1] = phi (degrees).  MUSR_FP64 precision only */
+                           slot[0] = nu (MHz), slot[1] = phi (degrees) */
 };
 
 #define MUSR_MAX_PRIMS 4
@@ -177,7 +180,8 @@ int musr_eval(musr_ctx* ctx, const double* params, int nparams, int mode, int pr
  * params[nparams]: out[ndir][1 + nparams] (host) receives v^T H v and H v.
  * One launch for all directions; synchronous on the context's stream.
  * Returns MUSR_ENONFINITE (row zeros after an infinite first entry) where the
- * likelihood is undefined. */
+ * likelihood is undefined.  At MUSR_SPLIT precision only for theories with a
+ * basis form and histogram data (else MUSR_EINVAL: use MUSR_FP64). */
 int musr_gn_product(musr_ctx* ctx, const double* params, int nparams, const double* dirs, int ndir, int mode,
                     int precision, double* out);
 
@@ -306,7 +310,7 @@ int musr_server_create(musr_server** out, int device, size_t hbm_budget_bytes, i
 void musr_server_destroy(musr_server* s);
 
 /* Queues a fit; *out_id identifies it.  Thread-safe.  A fit that can never run
- * (larger than the whole budget, SPLIT asked of a theory it cannot run) ends
+ * (larger than the whole budget, bad arguments) ends
  * with a negative status instead of being queued forever. */
 int musr_server_submit(musr_server* s, const musr_fit_request* req, int64_t* out_id);
 

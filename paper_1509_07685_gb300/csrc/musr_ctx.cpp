@@ -299,14 +299,11 @@ int compile(musr_ctx* ctx, int prec, int var) {
   const int H = ctx->H;
   std::vector<std::vector<int>> groups;
   int group_cap = 1;
-  if (prec == MUSR_SPLIT) {
-    const char* why = musr::plan_split(ctx->terms.data(), hs.nterms, ctx->map.data(), H, ctx->nslots,
+  const bool basis = prec == MUSR_SPLIT &&
+                     !musr::plan_split(ctx->terms.data(), hs.nterms, ctx->map.data(), H, ctx->nslots,
                                        ctx->consts.data(), &hs, !ctx->asym);
-    if (why) {
-      c.reason = why;
-      c.planned = true;
-      return MUSR_OK;  // SPLIT unavailable for this theory; FP64 still is
-    }
+  if (prec == MUSR_SPLIT && !basis) hs.shape = musr::kShapeList;  // the term list per bin in FP32
+  if (basis) {
     group_cap = musr::shape_group(hs.shape);
     // Group histograms that share t0, the fit window and every time-dependent parameter.
     std::map<std::vector<int64_t>, int> key_to_group;
@@ -600,8 +597,6 @@ int check_ready(musr_ctx* ctx, int mode, int prec) {
     return fail(ctx, MUSR_EINVAL, "precision must be MUSR_FP64 or MUSR_SPLIT");
   if (ctx->asym && mode != MUSR_CHI2)
     return fail(ctx, MUSR_EINVAL, "asymmetry data have the chi^2 cost only (MUSR_CHI2)");
-  if (prec == MUSR_SPLIT && !ctx->split_reason.empty())
-    return fail(ctx, MUSR_EINVAL, "precision unavailable for this theory: " + ctx->split_reason);
   return MUSR_OK;
 }
 
@@ -1103,6 +1098,10 @@ int musr_gn_product(musr_ctx* ctx, const double* params, int nparams, const doub
   if (rc) return rc;
   if (ctx->asym && precision == MUSR_SPLIT)
     return fail(ctx, MUSR_EINVAL, "Gauss-Newton products of asymmetry data run at MUSR_FP64 precision");
+  if (!ctx->split_reason.empty() && precision == MUSR_SPLIT)
+    return fail(ctx, MUSR_EINVAL,
+                "Gauss-Newton products of a theory without a basis form run at MUSR_FP64 precision (" +
+                    ctx->split_reason + ")");
   if (ndir < 1) return fail(ctx, MUSR_EINVAL, "ndir must be >= 1");
   if (nparams != ctx->P) return fail(ctx, MUSR_EINVAL, "nparams does not match the map");
   if (!params || !dirs || !out) return fail(ctx, MUSR_EINVAL, "params, dirs and out must not be NULL");

@@ -127,7 +127,8 @@ struct musr_ctx {
   bool have_map = false;
   std::vector<int32_t> map;
   int nslots = 0, P = 0;
-  std::string split_reason;  // why the SPLIT path cannot run this theory (empty: it can)
+  std::string split_reason;  // why the theory has no basis form (empty: it has); SPLIT then
+                             // evaluates the term list per bin (list_item)
   std::vector<double> consts;
   // [precision][decomposition]: tiles of (bins per CTA iteration) << v bins; a
   // launch picks the largest that still fills the GPU (pick_decomposition).

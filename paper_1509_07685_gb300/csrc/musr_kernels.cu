@@ -21,6 +21,7 @@ int shape_group_of(int shape) {
 }  // namespace
 
 int shape_group(int shape) {
+  if (shape == kShapeList) return 1;
   switch (shape) {
 #define MUSR_CASE(S) \
   case S:            \
@@ -39,6 +40,7 @@ int shape_group(int shape) {
 }
 
 int shape_channels(int shape) {
+  if (shape == kShapeList) return kFp64Channels;
   switch (shape) {
 #define MUSR_CASE(S) \
   case S:            \

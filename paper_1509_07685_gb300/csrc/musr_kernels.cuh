@@ -258,6 +258,10 @@ template <>
 struct Basis<kShapeT2m> : BasisBase<2, 2, 3, 8, true> {};
 template <>
 struct Basis<kShapeT2N1m> : BasisBase<3, 2, 3, 8, true> {};
+// Term lists without a basis form (list_item): the traits only let the shared setup code
+// compile; that code does not run for them.
+template <>
+struct Basis<kShapeList> : BasisBase<1, 0, 2, 1, false> {};
 
 // cos and sin of a phase given in degrees: reduced to [-1/2, 1/2] turns in FP64, then
 // evaluated in FP32 (the SPLIT coefficients and their derivatives need no more; FP64
@@ -678,6 +682,204 @@ __device__ double fp64_slot(const HistSet& hs, const double* tot, int s) {
       if (prim_nslots(hs.raw[k].kind[m]) == 2 && hs.raw[k].slot[m][1] == s) g += tot[3 + (k * kMaxPrims + m) * 2 + 1];
     }
   return g;
+}
+
+// ---------------------------------------------------------------------------------------------
+// SPLIT path for term lists without a basis form (a stretched exponential, a Bessel
+// precession, two cosines in one term): the FP64 path's per-bin evaluation of the term list
+// in FP32 arithmetic, except the bin time and the phase argument, formed in FP64 (the cosine
+// reduced to [-1/2, 1/2] turns there, the Bessel argument rounded once); FP32 sums per
+// thread (the value Kahan-compensated), FP64 from the warp on; the row layout of the FP64
+// path.  MODE 0 (chi^2), 1 (-2lnL), 4 (weighted chi^2 of asymmetry data).
+// ---------------------------------------------------------------------------------------------
+template <int MODE, bool GRAD>
+__device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm) {
+  const int tid = threadIdx.x;
+  const ChunkCache& cc = sm.cc;
+  const int h = cc.row[0], nlo = cc.nlo, nhi = cc.nhi, ts = sm.ts.tile_start;
+  const double t0 = cc.t0, dt = hs.dt_us;
+  const int nterms = hs.nterms;
+  const float N0 = static_cast<float>(cc.loc[0][0]), Nbkg = static_cast<float>(cc.loc[0][1]);
+  const float* rowf = static_cast<const float*>(hs.counts) + static_cast<int64_t>(h) * hs.stride;
+  const double* rowd = static_cast<const double*>(hs.counts) + static_cast<int64_t>(h) * hs.stride;
+  const float* roww =
+      hs.weights ? static_cast<const float*>(hs.weights) + static_cast<int64_t>(h) * hs.stride : nullptr;
+  const int store = hs.store;
+  const float rate = hs.envelope ? static_cast<float>(1.0 / kTauMuUs) : 0.0f;
+
+  float acc_v = 0.0f, acc_c = 0.0f, acc_n0 = 0.0f, acc_bkg = 0.0f;
+  float acc_p[kMaxTerms][kMaxPrims][2];
+#pragma unroll
+  for (int k = 0; k < kMaxTerms; ++k)
+#pragma unroll
+    for (int m = 0; m < kMaxPrims; ++m) acc_p[k][m][0] = acc_p[k][m][1] = 0.0f;
+  int bad = 0;
+
+  const int end = min(nhi, ts + hs.tile_bins);
+  for (int n = ts + tid; n < end; n += kBlock) {
+    if (n < nlo) continue;
+    const double t = (static_cast<double>(n) - t0) * dt;  // Section 4.1: t = n dt, shifted by t0
+    const float tf = static_cast<float>(t);
+    const float d = store == kStoreF64 ? static_cast<float>(rowd[n]) : rowf[n];
+    const float E = __expf(-rate * tf);
+    float gd[kMaxTerms][kMaxPrims][2];
+    float A = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kMaxTerms; ++k) {
+      float f[kMaxPrims], df[kMaxPrims][2];
+      const int np = k < nterms ? hs.raw[k].nprim : 0;
+      float term = 1.0f;
+#pragma unroll
+      for (int m = 0; m < kMaxPrims; ++m) {
+        f[m] = 1.0f;
+        df[m][0] = df[m][1] = 0.0f;
+        if (m >= np) continue;
+        const int kind = hs.raw[k].kind[m];
+        const float p0 = static_cast<float>(cc.loc[0][hs.raw[k].slot[m][0]]);
+        if (kind == kAmp) {
+          f[m] = p0;
+          df[m][0] = 1.0f;
+        } else if (kind == kExp) {
+          const float e = __expf(-p0 * tf);
+          f[m] = e;
+          df[m][0] = -tf * e;
+        } else if (kind == kGauss) {
+          const float x = p0 * tf, e = __expf(-0.5f * x * x);
+          f[m] = e;
+          df[m][0] = -p0 * tf * tf * e;
+        } else if (kind == kKT) {
+          const float u = (p0 * tf) * (p0 * tf), g = __expf(-0.5f * u);
+          f[m] = 1.0f / 3.0f + (2.0f / 3.0f) * (1.0f - u) * g;
+          df[m][0] = (2.0f / 3.0f) * p0 * tf * tf * g * (u - 3.0f);
+        } else if (kind == kLKT) {
+          const float u = p0 * tf, g = __expf(-u);
+          f[m] = 1.0f / 3.0f + (2.0f / 3.0f) * (1.0f - u) * g;
+          df[m][0] = (2.0f / 3.0f) * tf * g * (u - 2.0f);
+        } else if (kind == kStrExp) {  // exp(-(|lambda| t)^beta) for t > 0, else 1
+          const float p1 = static_cast<float>(cc.loc[0][hs.raw[k].slot[m][1]]);
+          const float lam = fabsf(p0), x = lam * tf;
+          if (tf > 0.0f && x > 0.0f) {
+            const float lx = logf(x), xb = __expf(p1 * lx), e = __expf(-xb);
+            f[m] = e;
+            df[m][0] = (p0 < 0.0f ? -1.0f : 1.0f) * (-p1 * xb / lam) * e;
+            df[m][1] = -xb * lx * e;
+          }
+        } else if (kind == kTFCos || kind == kBessel) {
+          const double p1 = cc.loc[0][hs.raw[k].slot[m][1]];
+          const double x = cc.loc[0][hs.raw[k].slot[m][0]] * t + p1 / 360.0;  // turns, FP64
+          if (kind == kTFCos) {
+            float sn, cs;
+            sincospif(2.0f * static_cast<float>(x - rint(x)), &sn, &cs);
+            f[m] = cs;
+            df[m][0] = -sn * kTwoPiF * tf;
+            df[m][1] = -sn * (kTwoPiF / 360.0f);
+          } else {  // J0' = -J1; the argument is not periodic: rounded once from FP64
+            const float X = static_cast<float>(kTwoPi * x), j1x = j1f(X);
+            f[m] = j0f(X);
+            df[m][0] = -j1x * kTwoPiF * tf;
+            df[m][1] = -j1x * (kTwoPiF / 360.0f);
+          }
+        }
+        term *= f[m];
+      }
+      if (np > 0) A += term;
+      if (GRAD) {
+#pragma unroll
+        for (int m = 0; m < kMaxPrims; ++m) {
+          float rest = 1.0f;
+#pragma unroll
+          for (int q = 0; q < kMaxPrims; ++q)
+            if (q != m) rest *= f[q];
+          gd[k][m][0] = df[m][0] * rest;
+          gd[k][m][1] = df[m][1] * rest;
+        }
+      }
+    }
+    const float Ae = hs.envelope ? 1.0f + A : A;
+    const float N = N0 * E * Ae + Nbkg;
+    float v, W;  // per-bin cost and dcost/dN
+    if (MODE == 0 || MODE == 4) {
+      const float w = MODE == 4 ? roww[n] : 1.0f / fmaxf(d, 1.0f);
+      const float r = d - N;
+      v = r * r * w;
+      W = -2.0f * r * w;
+    } else if (d > 0.0f) {
+      if (!(N > 0.0f)) {
+        bad = 1;
+        v = W = 0.0f;
+      } else {
+        // (N - d) + d ln(d/N) = N phi(u), u = (N - d)/N: the series of phi for small |u|
+        // (no cancellation), the logarithm otherwise
+        const float r = N - d, u = r / N;
+        if (fabsf(u) < 0.2f) {
+          float p = fmaf(u, 1.0f / 90.0f, 1.0f / 72.0f);
+          p = fmaf(u, p, 1.0f / 56.0f);
+          p = fmaf(u, p, 1.0f / 42.0f);
+          p = fmaf(u, p, 1.0f / 30.0f);
+          p = fmaf(u, p, 1.0f / 20.0f);
+          p = fmaf(u, p, 1.0f / 12.0f);
+          p = fmaf(u, p, 1.0f / 6.0f);
+          p = fmaf(u, p, 0.5f);
+          v = 2.0f * r * u * p;
+        } else {
+          v = 2.0f * (r + d * logf(d / N));
+        }
+        W = 2.0f * u;
+      }
+    } else {
+      v = 2.0f * (N - d);
+      W = 2.0f;
+    }
+    {  // Kahan-compensated running sum
+      const float y = v - acc_c;
+      const float s = acc_v + y;
+      acc_c = (s - acc_v) - y;
+      acc_v = s;
+    }
+    if (GRAD) {
+      acc_n0 += W * E * Ae;
+      acc_bkg += W;
+      const float wNE = W * N0 * E;
+#pragma unroll
+      for (int k = 0; k < kMaxTerms; ++k)
+#pragma unroll
+        for (int m = 0; m < kMaxPrims; ++m) {
+          acc_p[k][m][0] = fmaf(wNE, gd[k][m][0], acc_p[k][m][0]);
+          acc_p[k][m][1] = fmaf(wNE, gd[k][m][1], acc_p[k][m][1]);
+        }
+    }
+  }
+
+  // Warp (FP64 shuffles), then the CTA's warps in a fixed order (FP64): the FP64 path's rows.
+  bad = __syncthreads_or(bad);
+  const int w = tid >> 5, lane = tid & 31;
+  const double r0 = warp_sum_d(static_cast<double>(acc_v) - static_cast<double>(acc_c));
+  if (lane == 0) sm.dred[w][0] = r0;
+  if (GRAD) {
+    const double r1 = warp_sum_d(acc_n0), r2 = warp_sum_d(acc_bkg);
+    if (lane == 0) {
+      sm.dred[w][1] = r1;
+      sm.dred[w][2] = r2;
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxTerms; ++k)
+#pragma unroll
+      for (int m = 0; m < kMaxPrims; ++m)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const double r = warp_sum_d(acc_p[k][m][q]);
+          if (lane == 0) sm.dred[w][3 + (k * kMaxPrims + m) * 2 + q] = r;
+        }
+  }
+  __syncthreads();
+  double* row = job.partials + static_cast<int64_t>(item) * hs.pstride;
+  const int nout = GRAD ? 1 + kFp64Channels : 1;
+  for (int c = tid; c < nout; c += kBlock) {
+    double s = 0.0;
+    for (int i = 0; i < kWarps; ++i) s += sm.dred[i][c];
+    if (c == 0 && bad) s = __longlong_as_double(0x7ff0000000000000LL);
+    row[c] = s;
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1249,7 +1451,7 @@ __device__ void chunk_finalize(const Job& job, const HistSet& hs, Smem& sm) {
     for (int i = tid; i < cc.nh * nsl; i += kBlock) {
       const int hl = i / nsl, s = i - hl * nsl;
       double g;
-      if (PREC == 0)
+      if constexpr (PREC == 0 || SHAPE == kShapeList)
         g = fp64_slot(hs, sm.tot, s);
       else
         g = split_slot<SHAPE>(hs, cc, sm.tot, hl, s);
@@ -1331,7 +1533,8 @@ __device__ void complete_item(const Job& job, const HistSet& hs, Smem& sm) {
 // Persistent kernel: each CTA takes a contiguous range of the launch's items.
 // ---------------------------------------------------------------------------------------------
 template <int PREC, int SHAPE, int MODE, bool GRAD>
-__global__ void __launch_bounds__(kBlock, PREC == 1 ? 2 : 1) eval_kernel(const Job* __restrict__ jobs, int njobs,
+__global__ void __launch_bounds__(kBlock, PREC == 1 && SHAPE != kShapeList ? 2 : 1) eval_kernel(
+    const Job* __restrict__ jobs, int njobs,
                                                       int total_items) {
   __shared__ Smem sm;
   const int per = (total_items + gridDim.x - 1) / gridDim.x;
@@ -1365,13 +1568,17 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? 2 : 1) eval_kernel(const J
     }
     const HistSet& hs = *job.hs;
     const int item = gi - job.item_begin;
+    // term lists without a basis form take the FP64 path's chunk and tile setup
+    constexpr int kSetupPrec = SHAPE == kShapeList ? 0 : PREC;
     if (sm.cc.job != ji || item < sm.cc.item0 || item >= sm.cc.item0 + sm.cc.ntiles) {
       __syncthreads();
-      load_chunk<SHAPE>(job, hs, ji, hs.items[item].x, PREC, sm);
+      load_chunk<SHAPE>(job, hs, ji, hs.items[item].x, kSetupPrec, sm);
     }
-    load_tile(hs, item - sm.cc.item0, PREC, sm);
-    if (PREC == 0)
+    load_tile(hs, item - sm.cc.item0, kSetupPrec, sm);
+    if constexpr (PREC == 0)
       fp64_item<MODE, GRAD>(job, hs, item, sm);
+    else if constexpr (SHAPE == kShapeList)
+      list_item<MODE, GRAD>(job, hs, item, sm);
     else
       split_item<SHAPE, MODE, GRAD>(job, hs, item, sm, parity);
     complete_item<PREC, SHAPE, GRAD>(job, hs, sm);
@@ -1406,8 +1613,12 @@ int occupancy_one() {
 template <int PREC, int SHAPE>
 int dispatch_mode(int mode, int grad, const Job* j, int n, int items, int sms, cudaStream_t s,
                   LaunchInfo* info) {
-  if (mode == 2) return launch_one<PREC, SHAPE, 2, true>(j, n, items, sms, s, info);
-  if (mode == 3) return launch_one<PREC, SHAPE, 3, true>(j, n, items, sms, s, info);
+  if constexpr (SHAPE == kShapeList) {  // no Gauss-Newton kernels for term lists (FP64 path)
+    if (mode == 2 || mode == 3) return -1;
+  } else {
+    if (mode == 2) return launch_one<PREC, SHAPE, 2, true>(j, n, items, sms, s, info);
+    if (mode == 3) return launch_one<PREC, SHAPE, 3, true>(j, n, items, sms, s, info);
+  }
   if (PREC == 1 && mode == 4)  // weighted chi^2 of asymmetry data (SPLIT)
     return grad ? launch_one<PREC, SHAPE, PREC == 1 ? 4 : 0, true>(j, n, items, sms, s, info)
                 : launch_one<PREC, SHAPE, PREC == 1 ? 4 : 0, false>(j, n, items, sms, s, info);
@@ -1420,8 +1631,12 @@ int dispatch_mode(int mode, int grad, const Job* j, int n, int items, int sms, c
 
 template <int PREC, int SHAPE>
 int occupancy_mode(int mode, int grad) {
-  if (mode == 2) return occupancy_one<PREC, SHAPE, 2, true>();
-  if (mode == 3) return occupancy_one<PREC, SHAPE, 3, true>();
+  if constexpr (SHAPE == kShapeList) {
+    if (mode == 2 || mode == 3) return 0;
+  } else {
+    if (mode == 2) return occupancy_one<PREC, SHAPE, 2, true>();
+    if (mode == 3) return occupancy_one<PREC, SHAPE, 3, true>();
+  }
   if (PREC == 1 && mode == 4)
     return grad ? occupancy_one<PREC, SHAPE, PREC == 1 ? 4 : 0, true>()
                 : occupancy_one<PREC, SHAPE, PREC == 1 ? 4 : 0, false>();

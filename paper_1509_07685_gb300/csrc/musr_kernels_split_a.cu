@@ -1,4 +1,4 @@
-// musr_kernels_split_a.cu -- instantiates the SPLIT (kShapeGeneric, kShapeT1, kShapeN1, kShapeT1N1) kernels of musr_kernels.cuh.
+// musr_kernels_split_a.cu -- instantiates the SPLIT (kShapeGeneric, kShapeT1, kShapeN1, kShapeT1N1, kShapeList) kernels of musr_kernels.cuh.
 #include "musr_kernels.cuh"
 
 namespace musr {
@@ -14,6 +14,8 @@ int launch_group_a(int shape, int mode, int grad, const Job* j, int n, int items
       return kern::dispatch_mode<1, kShapeN1>(mode, grad, j, n, items, sms, s, info);
     case kShapeT1N1:
       return kern::dispatch_mode<1, kShapeT1N1>(mode, grad, j, n, items, sms, s, info);
+    case kShapeList:
+      return kern::dispatch_mode<1, kShapeList>(mode, grad, j, n, items, sms, s, info);
     default:
       return -1;
   }
@@ -28,6 +30,8 @@ int occupancy_group_a(int shape, int mode, int grad) {
       return kern::occupancy_mode<1, kShapeN1>(mode, grad);
     case kShapeT1N1:
       return kern::occupancy_mode<1, kShapeT1N1>(mode, grad);
+    case kShapeList:
+      return kern::occupancy_mode<1, kShapeList>(mode, grad);
     default:
       return 0;
   }

@@ -104,8 +104,8 @@ inline bool shared_constant_amplitude(const CanonTerm& ct, const int32_t* map, c
 }
 
 // Plans the SPLIT path of a theory and map into hs (canon in cosine-first order,
-// nterms, shape, merged, bamp, contributions).  Returns nullptr, or why the SPLIT
-// path cannot evaluate this theory (the FP64 path still can).
+// nterms, shape, merged, bamp, contributions).  Returns nullptr, or why the theory has no
+// basis form (the SPLIT path then evaluates its term list per bin).
 // Without the decay envelope (asymmetry data) no shape is merged: a merged shape folds the
 // non-cosine terms into the basis function that carries the 1 of (1 + A).
 inline const char* plan_split(const musr_term* terms, int nterms, const int32_t* map, int H, int nslots,
@@ -115,7 +115,7 @@ inline const char* plan_split(const musr_term* terms, int nterms, const int32_t*
   for (int k = 0; k < nterms; ++k)
     if (!canonical_term(terms[k], &canon[k]))
       return "SPLIT precision needs every term to hold at most one AMP, and at most one of KT, LKT or TFCOS "
-             "(STREXP and BESSEL terms run at MUSR_FP64 precision)";
+             "(STREXP and BESSEL have no basis form)";
   // Cosine terms first (the model is a sum: the order of its terms is free).
   int ntf = 0, nn = 0;
   hs->nterms = nterms;

@@ -126,3 +126,19 @@ def test_large_fit_split_vs_fp64(B):
     assert r64["status"] == 0 and r32["status"] == 0
     dev = np.abs(r32["x"] - r64["x"]) / sig
     assert np.all(dev < 0.01), float(dev.max())
+
+
+@pytest.mark.parametrize("name", ["levy_lf", "inc_bessel"])
+def test_split_fit_of_term_lists_without_basis_form(B, name):
+    """Theories without a basis form (a stretched exponential, a Bessel precession): the SPLIT
+    fit, through the term list kernel, lands within 0.01 sigma of the FP64 fit."""
+    from paper_1509_07685_gb300 import fit as F
+    p = mi.levy_lf(seed=109) if name == "levy_lf" else mi.inc_bessel(seed=108)
+    x0 = mi.start_point(p, 1)
+    with B.Context(p) as ctx:
+        r64 = F.fit_context(ctx, x0, 1, B.MUSR_FP64)
+        r32 = F.fit_context(ctx, x0, 1, B.MUSR_SPLIT)
+        sig = F.sigmas_context(ctx, r64["x"], 1)
+    assert r64["status"] == 0 and r32["status"] == 0
+    dev = np.abs(r32["x"] - r64["x"]) / sig
+    assert np.all(dev < 0.01), dict(zip(p.names, np.round(dev, 4)))

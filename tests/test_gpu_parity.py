@@ -219,7 +219,7 @@ def test_mle_undefined_is_nonfinite(B):
 
 def test_generic_and_noncanonical_theories(B):
     """A term list outside the compiled SPLIT shapes runs the generic SPLIT kernel; a term
-    with two cosines is FP64-only (SPLIT refuses it with MUSR_EINVAL)."""
+    with two cosines has no basis form: SPLIT evaluates its term list per bin."""
     base = mi.cfg1(nbins=3000, bin_width_ns=3.0, seed=5, dtype=np.float32)
     terms = [[("AMP", (2,)), ("EXP", (3,))], [("AMP", (4,)), ("GAUSS", (5,)), ("EXP", (3,))],
              [("AMP", (6,)), ("KT", (7,))], [("AMP", (8,)), ("TFCOS", (9, 10))]]
@@ -240,12 +240,12 @@ def test_generic_and_noncanonical_theories(B):
     p2 = mi.Problem(base.counts, base.t0, base.bin_width_ns, base.fit_range_us, terms2, mp2, np.zeros(0), 6,
                     x2, [f"p{i}" for i in range(6)])
     with B.Context(p2) as ctx:
-        ref = oracle.cost(p2, x2, 0)
-        v, g, _ = ctx.eval(x2, 0, B.MUSR_FP64)
-        _check_fp64(v, g, ref)
-        with pytest.raises(B.MusrError) as e:
-            ctx.eval(x2, 0, B.MUSR_SPLIT)
-        assert e.value.status == B.MUSR_EINVAL
+        for mode in (0, 1):
+            ref = oracle.cost(p2, x2, mode)
+            v, g, _ = ctx.eval(x2, mode, B.MUSR_FP64)
+            _check_fp64(v, g, ref)
+            v, g, _ = ctx.eval(x2, mode, B.MUSR_SPLIT)  # no basis form: the term list per bin
+            _check_split(v, g, ref)
 
 
 def test_invalid_arguments(B):
@@ -374,10 +374,11 @@ def test_shifted_upload_every_dtype_and_check(B):
         B.musr_ctx_destroy(ctx)
 
 
-def test_fp64_only_primitives(B):
-    """The stretched exponential and the Bessel precession: the FP64 path against the oracle
-    (single and batched, both costs) for Monte Carlo configurations and a theory mixing them
-    with the other primitives; the SPLIT path refuses them (no basis form)."""
+def test_term_lists_without_basis_form(B):
+    """The stretched exponential and the Bessel precession (no basis form): both paths against
+    the oracle (single and batched, both costs) for Monte Carlo configurations and a theory
+    mixing them with the other primitives; SPLIT evaluates the term list per bin in FP32, and
+    its Gauss-Newton products are refused (FP64 only)."""
     import test_oracle_pins as pins
     q, xq = pins._new_primitive_problem()
     cases = [(mi.inc_bessel(nhist=2, nbins=3000, bin_width_ns=4.0, seed=71), None),
@@ -387,15 +388,19 @@ def test_fp64_only_primitives(B):
         X = mi.jitter(x, 4, seed=3, lo=0.98, hi=1.02)
         with B.Context(p) as ctx:
             for mode in (0, 1):
+                ref = oracle.cost(p, x, mode)
                 v, g, _ = ctx.eval(x, mode, B.MUSR_FP64)
-                _check_fp64(v, g, oracle.cost(p, x, mode))
-                vals, grads, st = ctx.eval_batch(X, mode, B.MUSR_FP64)
-                assert st == 0
-                for i in (0, 3):
-                    _check_fp64(vals[i], grads[i], oracle.cost(p, X[i], mode))
+                _check_fp64(v, g, ref)
+                v, g, _ = ctx.eval(x, mode, B.MUSR_SPLIT)
+                _check_split(v, g, ref)
+                for prec, check in ((B.MUSR_FP64, _check_fp64), (B.MUSR_SPLIT, _check_split)):
+                    vals, grads, st = ctx.eval_batch(X, mode, prec)
+                    assert st == 0
+                    for i in (0, 3):
+                        check(vals[i], grads[i], oracle.cost(p, X[i], mode))
             with pytest.raises(B.MusrError) as e:
-                ctx.eval(x, 1, B.MUSR_SPLIT)
-            assert e.value.status == B.MUSR_EINVAL and "STREXP" in str(e.value)
+                ctx.gauss_newton(x, 1, B.MUSR_SPLIT)
+            assert e.value.status == B.MUSR_EINVAL and "basis form" in str(e.value)
 
 
 def test_hbm_budget_is_enforced(B):
