@@ -765,8 +765,8 @@ __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm)
             df[m][1] = -xb * lx * e;
           }
         } else if (kind == kTFCos || kind == kBessel) {
-          const double p1 = cc.loc[0][hs.raw[k].slot[m][1]];
-          const double x = cc.loc[0][hs.raw[k].slot[m][0]] * t + p1 / 360.0;  // turns, FP64
+          // turns, FP64 (times 1/360 rather than a division: FP64 is this GPU's slow pipe)
+          const double x = fma(cc.loc[0][hs.raw[k].slot[m][0]], t, cc.loc[0][hs.raw[k].slot[m][1]] * (1.0 / 360.0));
           if (kind == kTFCos) {
             float sn, cs;
             sincospif(2.0f * static_cast<float>(x - rint(x)), &sn, &cs);
