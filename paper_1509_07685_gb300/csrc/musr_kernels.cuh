@@ -184,6 +184,10 @@ struct ChunkCache {
   // term the directional derivatives of its exponent rates (-t dLambda - t^2 dSigma), of its
   // frequency and (scaled by 2/3 Delta) of its Kubo-Toyabe width
   alignas(16) float gdot[kGroupMax][kGamStride];
+  // term lists without a basis form (list_item), per (term k, primitive m) = k * kMaxPrims + m:
+  // the phase step per bin of a cosine or Bessel primitive in turns, split so that
+  // (bin offset < 2^14) * lhi is exact in FP32
+  float lhi[kMaxTerms * kMaxPrims], llo[kMaxTerms * kMaxPrims], lstep[kMaxTerms * kMaxPrims];
   float dlam[kMaxTerms], dsig[kMaxTerms], dnu[kMaxTerms], ddel[kMaxTerms];
   // SPLIT per-term constants of the chunk
   int kinds[kMaxTerms];
@@ -199,6 +203,9 @@ struct TileState {
   int tile_start;
   float tbase;
   float base[kMaxTerms];  // phase (turns, in [-1/2, 1/2]) of each TF term at the tile's first bin
+  // term lists without a basis form, per (term, primitive): the cosine's phase at the tile's
+  // first bin (turns, in [-1/2, 1/2]) or the Bessel argument there (radians)
+  float lbase[kMaxTerms * kMaxPrims];
 };
 
 struct Smem {
@@ -684,6 +691,47 @@ __device__ double fp64_slot(const HistSet& hs, const double* tot, int s) {
   return g;
 }
 
+// Term lists without a basis form: per (term, primitive) with a phase, its step per bin in
+// turns (FP64, then split so that (bin offset < 2^14) * lhi is exact in FP32; the Bessel
+// step in radians), once per chunk.
+__device__ void load_chunk_list(const HistSet& hs, Smem& sm) {
+  const int tid = threadIdx.x;
+  if (tid < kMaxTerms * kMaxPrims) {
+    const int k = tid / kMaxPrims, m = tid - k * kMaxPrims;
+    float hi = 0.0f, lo = 0.0f, st = 0.0f;
+    if (k < hs.nterms && m < hs.raw[k].nprim &&
+        (hs.raw[k].kind[m] == kTFCos || hs.raw[k].kind[m] == kBessel)) {
+      const double step = sm.cc.loc[0][hs.raw[k].slot[m][0]] * hs.dt_us;
+      hi = __uint_as_float(__float_as_uint(static_cast<float>(step)) & 0xFFFFC000u);
+      lo = static_cast<float>(step - static_cast<double>(hi));
+      st = static_cast<float>(hs.raw[k].kind[m] == kBessel ? kTwoPi * step : step);
+    }
+    sm.cc.lhi[tid] = hi;
+    sm.cc.llo[tid] = lo;
+    sm.cc.lstep[tid] = st;
+  }
+  __syncthreads();
+}
+
+// ... and the phase at the tile's first bin (FP64, then rounded once), and the tile's time.
+__device__ void load_tile_list(const HistSet& hs, Smem& sm) {
+  const int tid = threadIdx.x;
+  const double t_start = (static_cast<double>(sm.ts.tile_start) - sm.cc.t0) * hs.dt_us;
+  if (tid == 0) sm.ts.tbase = static_cast<float>(t_start);
+  if (tid < kMaxTerms * kMaxPrims) {
+    const int k = tid / kMaxPrims, m = tid - k * kMaxPrims;
+    float b = 0.0f;
+    if (k < hs.nterms && m < hs.raw[k].nprim &&
+        (hs.raw[k].kind[m] == kTFCos || hs.raw[k].kind[m] == kBessel)) {
+      const double x = fma(sm.cc.loc[0][hs.raw[k].slot[m][0]], t_start,
+                           sm.cc.loc[0][hs.raw[k].slot[m][1]] * (1.0 / 360.0));  // turns
+      b = static_cast<float>(hs.raw[k].kind[m] == kTFCos ? x - rint(x) : kTwoPi * x);
+    }
+    sm.ts.lbase[tid] = b;
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------------------------
 // SPLIT path for term lists without a basis form (a stretched exponential, a Bessel
 // precession, two cosines in one term): the FP64 path's per-bin evaluation of the term list
@@ -697,7 +745,7 @@ __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm)
   const int tid = threadIdx.x;
   const ChunkCache& cc = sm.cc;
   const int h = cc.row[0], nlo = cc.nlo, nhi = cc.nhi, ts = sm.ts.tile_start;
-  const double t0 = cc.t0, dt = hs.dt_us;
+  const double dt = hs.dt_us;
   const int nterms = hs.nterms;
   const float N0 = static_cast<float>(cc.loc[0][0]), Nbkg = static_cast<float>(cc.loc[0][1]);
   const float* rowf = static_cast<const float*>(hs.counts) + static_cast<int64_t>(h) * hs.stride;
@@ -706,6 +754,7 @@ __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm)
       hs.weights ? static_cast<const float*>(hs.weights) + static_cast<int64_t>(h) * hs.stride : nullptr;
   const int store = hs.store;
   const float rate = hs.envelope ? static_cast<float>(1.0 / kTauMuUs) : 0.0f;
+  const float tbase = sm.ts.tbase, dtf = static_cast<float>(dt);
 
   float acc_v = 0.0f, acc_c = 0.0f, acc_n0 = 0.0f, acc_bkg = 0.0f;
   float acc_p[kMaxTerms][kMaxPrims][2];
@@ -716,10 +765,12 @@ __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm)
   int bad = 0;
 
   const int end = min(nhi, ts + hs.tile_bins);
-  for (int n = ts + tid; n < end; n += kBlock) {
+  // The bin offset in the tile is carried as an exact float (< 2^14 here): time and phases
+  // come from the tile's FP64 bases plus FP32 increments, with no FP64 work per bin.
+  float fm = static_cast<float>(tid);
+  for (int n = ts + tid; n < end; n += kBlock, fm += static_cast<float>(kBlock)) {
     if (n < nlo) continue;
-    const double t = (static_cast<double>(n) - t0) * dt;  // Section 4.1: t = n dt, shifted by t0
-    const float tf = static_cast<float>(t);
+    const float tf = fmaf(fm, dtf, tbase);  // Section 4.1: t = n dt, shifted by t0
     const float d = store == kStoreF64 ? static_cast<float>(rowd[n]) : rowf[n];
     const float E = __expf(-rate * tf);
     float gd[kMaxTerms][kMaxPrims][2];
@@ -764,21 +815,23 @@ __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm)
             df[m][0] = (p0 < 0.0f ? -1.0f : 1.0f) * (-p1 * xb / lam) * e;
             df[m][1] = -xb * lx * e;
           }
-        } else if (kind == kTFCos || kind == kBessel) {
-          // turns, FP64 (times 1/360 rather than a division: FP64 is this GPU's slow pipe)
-          const double x = fma(cc.loc[0][hs.raw[k].slot[m][0]], t, cc.loc[0][hs.raw[k].slot[m][1]] * (1.0 / 360.0));
-          if (kind == kTFCos) {
-            float sn, cs;
-            sincospif(2.0f * static_cast<float>(x - rint(x)), &sn, &cs);
-            f[m] = cs;
-            df[m][0] = -sn * kTwoPiF * tf;
-            df[m][1] = -sn * (kTwoPiF / 360.0f);
-          } else {  // J0' = -J1; the argument is not periodic: rounded once from FP64
-            const float X = static_cast<float>(kTwoPi * x), j1x = j1f(X);
-            f[m] = j0f(X);
-            df[m][0] = -j1x * kTwoPiF * tf;
-            df[m][1] = -j1x * (kTwoPiF / 360.0f);
-          }
+        } else if (kind == kTFCos) {  // phase: tile base + fm * step, reduced exactly
+          const int j = k * kMaxPrims + m;
+          float fr = __fmul_rn(fm, cc.lhi[j]);
+          fr = __fsub_rn(fr, rint_small(fr));
+          float r = __fadd_rn(fmaf(fm, cc.llo[j], sm.ts.lbase[j]), fr);
+          r = __fsub_rn(r, rint_small(r));
+          float sn, cs;
+          sincospif(2.0f * r, &sn, &cs);
+          f[m] = cs;
+          df[m][0] = -sn * kTwoPiF * tf;
+          df[m][1] = -sn * (kTwoPiF / 360.0f);
+        } else if (kind == kBessel) {  // J0' = -J1; the argument (not periodic) in radians
+          const int j = k * kMaxPrims + m;
+          const float X = fmaf(fm, cc.lstep[j], sm.ts.lbase[j]), j1x = j1f(X);
+          f[m] = j0f(X);
+          df[m][0] = -j1x * kTwoPiF * tf;
+          df[m][1] = -j1x * (kTwoPiF / 360.0f);
         }
         term *= f[m];
       }
@@ -1573,8 +1626,10 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 && SHAPE != kShapeList ? 2 :
     if (sm.cc.job != ji || item < sm.cc.item0 || item >= sm.cc.item0 + sm.cc.ntiles) {
       __syncthreads();
       load_chunk<SHAPE>(job, hs, ji, hs.items[item].x, kSetupPrec, sm);
+      if constexpr (PREC == 1 && SHAPE == kShapeList) load_chunk_list(hs, sm);
     }
     load_tile(hs, item - sm.cc.item0, kSetupPrec, sm);
+    if constexpr (PREC == 1 && SHAPE == kShapeList) load_tile_list(hs, sm);
     if constexpr (PREC == 0)
       fp64_item<MODE, GRAD>(job, hs, item, sm);
     else if constexpr (SHAPE == kShapeList)
