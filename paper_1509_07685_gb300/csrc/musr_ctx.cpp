@@ -183,16 +183,6 @@ struct CheckFlag {
 };
 thread_local CheckFlag tl_flag;
 
-int upload(musr_ctx* ctx, DevBuf& b, const void* src, size_t bytes) {
-  int rc = dalloc(ctx, b, bytes);
-  if (rc) return rc;
-  if (bytes) {
-    cudaError_t e = copy_h2d(b.p, src, bytes);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync");
-  }
-  return MUSR_OK;
-}
-
 DeviceScope::DeviceScope(int dev) {
   cudaGetDevice(&prev_);
   if (prev_ != dev) cudaSetDevice(dev);

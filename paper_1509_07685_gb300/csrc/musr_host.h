@@ -84,7 +84,6 @@ int fail(musr_ctx* ctx, int code, const std::string& msg);
 int cuda_fail(musr_ctx* ctx, cudaError_t e, const char* what);
 int dalloc(musr_ctx* ctx, DevBuf& b, size_t bytes);
 void dfree(musr_ctx* ctx, DevBuf& b);
-int upload(musr_ctx* ctx, DevBuf& b, const void* src, size_t bytes);
 void fit_bins(double t0, double dt_us, int64_t B, double lo, double hi, int* nlo, int* nhi);
 int wait_stream(musr_ctx* ctx, int timeout_ms);
 int check_ready(musr_ctx* ctx, int mode, int prec);
