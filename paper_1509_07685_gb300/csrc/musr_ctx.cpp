@@ -292,7 +292,11 @@ int compile(musr_ctx* ctx, int prec, int var) {
   const bool basis = prec == MUSR_SPLIT &&
                      !musr::plan_split(ctx->terms.data(), hs.nterms, ctx->map.data(), H, ctx->nslots,
                                        ctx->consts.data(), &hs, !ctx->asym);
-  if (prec == MUSR_SPLIT && !basis) hs.shape = musr::kShapeList;  // the term list per bin in FP32
+  if (prec == MUSR_SPLIT && !basis) {  // the term list per bin in FP32
+    bool small = hs.nterms <= 2;
+    for (int k = 0; k < hs.nterms; ++k) small = small && ctx->terms[k].nprim <= 3;
+    hs.shape = small ? musr::kShapeListS : musr::kShapeList;
+  }
   if (basis) {
     group_cap = musr::shape_group(hs.shape);
     // Group histograms that share t0, the fit window and every time-dependent parameter.

@@ -61,7 +61,8 @@ enum Shape : int {
   kShapeT2N1 = 5,     // two cosine terms + other (M = 6)
   kShapeT2m = 6,      // merged two cosine terms (M = 3)
   kShapeT2N1m = 7,    // merged two cosine terms + other (M = 3)
-  kShapeList = 8      // no basis form: the term list per bin in FP32 (one histogram per chunk)
+  kShapeList = 8,     // no basis form: the term list per bin in FP32 (one histogram per chunk)
+  kShapeListS = 9     // the same for at most 2 terms of at most 3 primitives (fewer registers)
 };
 
 // A term as given: the product of nprim primitives (FP64 path).

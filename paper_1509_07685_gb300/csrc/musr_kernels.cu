@@ -21,7 +21,7 @@ int shape_group_of(int shape) {
 }  // namespace
 
 int shape_group(int shape) {
-  if (shape == kShapeList) return 1;
+  if (shape == kShapeList || shape == kShapeListS) return 1;
   switch (shape) {
 #define MUSR_CASE(S) \
   case S:            \
@@ -40,7 +40,7 @@ int shape_group(int shape) {
 }
 
 int shape_channels(int shape) {
-  if (shape == kShapeList) return kFp64Channels;
+  if (shape == kShapeList || shape == kShapeListS) return kFp64Channels;
   switch (shape) {
 #define MUSR_CASE(S) \
   case S:            \

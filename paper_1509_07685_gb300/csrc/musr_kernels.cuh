@@ -269,6 +269,9 @@ struct Basis<kShapeT2N1m> : BasisBase<3, 2, 3, 8, true> {};
 // compile; that code does not run for them.
 template <>
 struct Basis<kShapeList> : BasisBase<1, 0, 2, 1, false> {};
+template <>
+struct Basis<kShapeListS> : BasisBase<1, 0, 2, 1, false> {};
+__host__ __device__ constexpr bool is_list(int shape) { return shape == kShapeList || shape == kShapeListS; }
 
 // cos and sin of a phase given in degrees: reduced to [-1/2, 1/2] turns in FP64, then
 // evaluated in FP32 (the SPLIT coefficients and their derivatives need no more; FP64
@@ -740,7 +743,7 @@ __device__ void load_tile_list(const HistSet& hs, Smem& sm) {
 // thread (the value Kahan-compensated), FP64 from the warp on; the row layout of the FP64
 // path.  MODE 0 (chi^2), 1 (-2lnL), 4 (weighted chi^2 of asymmetry data).
 // ---------------------------------------------------------------------------------------------
-template <int MODE, bool GRAD>
+template <int MODE, bool GRAD, int LT, int LP>
 __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm) {
   const int tid = threadIdx.x;
   const ChunkCache& cc = sm.cc;
@@ -757,11 +760,11 @@ __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm)
   const float tbase = sm.ts.tbase, dtf = static_cast<float>(dt);
 
   float acc_v = 0.0f, acc_c = 0.0f, acc_n0 = 0.0f, acc_bkg = 0.0f;
-  float acc_p[kMaxTerms][kMaxPrims][2];
+  float acc_p[LT][LP][2];  // per (term, primitive, slot) of the first LT terms' first LP primitives
 #pragma unroll
-  for (int k = 0; k < kMaxTerms; ++k)
+  for (int k = 0; k < LT; ++k)
 #pragma unroll
-    for (int m = 0; m < kMaxPrims; ++m) acc_p[k][m][0] = acc_p[k][m][1] = 0.0f;
+    for (int m = 0; m < LP; ++m) acc_p[k][m][0] = acc_p[k][m][1] = 0.0f;
   int bad = 0;
 
   const int end = min(nhi, ts + hs.tile_bins);
@@ -773,15 +776,15 @@ __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm)
     const float tf = fmaf(fm, dtf, tbase);  // Section 4.1: t = n dt, shifted by t0
     const float d = store == kStoreF64 ? static_cast<float>(rowd[n]) : rowf[n];
     const float E = __expf(-rate * tf);
-    float gd[kMaxTerms][kMaxPrims][2];
+    float gd[LT][LP][2];
     float A = 0.0f;
 #pragma unroll
-    for (int k = 0; k < kMaxTerms; ++k) {
-      float f[kMaxPrims], df[kMaxPrims][2];
+    for (int k = 0; k < LT; ++k) {
+      float f[LP], df[LP][2];
       const int np = k < nterms ? hs.raw[k].nprim : 0;
       float term = 1.0f;
 #pragma unroll
-      for (int m = 0; m < kMaxPrims; ++m) {
+      for (int m = 0; m < LP; ++m) {
         f[m] = 1.0f;
         df[m][0] = df[m][1] = 0.0f;
         if (m >= np) continue;
@@ -838,10 +841,10 @@ __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm)
       if (np > 0) A += term;
       if (GRAD) {
 #pragma unroll
-        for (int m = 0; m < kMaxPrims; ++m) {
+        for (int m = 0; m < LP; ++m) {
           float rest = 1.0f;
 #pragma unroll
-          for (int q = 0; q < kMaxPrims; ++q)
+          for (int q = 0; q < LP; ++q)
             if (q != m) rest *= f[q];
           gd[k][m][0] = df[m][0] * rest;
           gd[k][m][1] = df[m][1] * rest;
@@ -894,9 +897,9 @@ __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm)
       acc_bkg += W;
       const float wNE = W * N0 * E;
 #pragma unroll
-      for (int k = 0; k < kMaxTerms; ++k)
+      for (int k = 0; k < LT; ++k)
 #pragma unroll
-        for (int m = 0; m < kMaxPrims; ++m) {
+        for (int m = 0; m < LP; ++m) {
           acc_p[k][m][0] = fmaf(wNE, gd[k][m][0], acc_p[k][m][0]);
           acc_p[k][m][1] = fmaf(wNE, gd[k][m][1], acc_p[k][m][1]);
         }
@@ -919,8 +922,8 @@ __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm)
 #pragma unroll
       for (int m = 0; m < kMaxPrims; ++m)
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const double r = warp_sum_d(acc_p[k][m][q]);
+        for (int q = 0; q < 2; ++q) {  // the FP64 path's row layout; slots beyond LT x LP are 0
+          const double r = k < LT && m < LP ? warp_sum_d(acc_p[k < LT ? k : 0][m < LP ? m : 0][q]) : 0.0;
           if (lane == 0) sm.dred[w][3 + (k * kMaxPrims + m) * 2 + q] = r;
         }
   }
@@ -1504,7 +1507,7 @@ __device__ void chunk_finalize(const Job& job, const HistSet& hs, Smem& sm) {
     for (int i = tid; i < cc.nh * nsl; i += kBlock) {
       const int hl = i / nsl, s = i - hl * nsl;
       double g;
-      if constexpr (PREC == 0 || SHAPE == kShapeList)
+      if constexpr (PREC == 0 || is_list(SHAPE))
         g = fp64_slot(hs, sm.tot, s);
       else
         g = split_slot<SHAPE>(hs, cc, sm.tot, hl, s);
@@ -1622,18 +1625,20 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 && SHAPE != kShapeList ? 2 :
     const HistSet& hs = *job.hs;
     const int item = gi - job.item_begin;
     // term lists without a basis form take the FP64 path's chunk and tile setup
-    constexpr int kSetupPrec = SHAPE == kShapeList ? 0 : PREC;
+    constexpr int kSetupPrec = is_list(SHAPE) ? 0 : PREC;
     if (sm.cc.job != ji || item < sm.cc.item0 || item >= sm.cc.item0 + sm.cc.ntiles) {
       __syncthreads();
       load_chunk<SHAPE>(job, hs, ji, hs.items[item].x, kSetupPrec, sm);
-      if constexpr (PREC == 1 && SHAPE == kShapeList) load_chunk_list(hs, sm);
+      if constexpr (PREC == 1 && is_list(SHAPE)) load_chunk_list(hs, sm);
     }
     load_tile(hs, item - sm.cc.item0, kSetupPrec, sm);
-    if constexpr (PREC == 1 && SHAPE == kShapeList) load_tile_list(hs, sm);
+    if constexpr (PREC == 1 && is_list(SHAPE)) load_tile_list(hs, sm);
     if constexpr (PREC == 0)
       fp64_item<MODE, GRAD>(job, hs, item, sm);
     else if constexpr (SHAPE == kShapeList)
-      list_item<MODE, GRAD>(job, hs, item, sm);
+      list_item<MODE, GRAD, kMaxTerms, kMaxPrims>(job, hs, item, sm);
+    else if constexpr (SHAPE == kShapeListS)  // at most 2 terms of at most 3 primitives
+      list_item<MODE, GRAD, 2, 3>(job, hs, item, sm);
     else
       split_item<SHAPE, MODE, GRAD>(job, hs, item, sm, parity);
     complete_item<PREC, SHAPE, GRAD>(job, hs, sm);
@@ -1668,7 +1673,7 @@ int occupancy_one() {
 template <int PREC, int SHAPE>
 int dispatch_mode(int mode, int grad, const Job* j, int n, int items, int sms, cudaStream_t s,
                   LaunchInfo* info) {
-  if constexpr (SHAPE == kShapeList) {  // no Gauss-Newton kernels for term lists (FP64 path)
+  if constexpr (is_list(SHAPE)) {  // no Gauss-Newton kernels for term lists (FP64 path)
     if (mode == 2 || mode == 3) return -1;
   } else {
     if (mode == 2) return launch_one<PREC, SHAPE, 2, true>(j, n, items, sms, s, info);
@@ -1686,7 +1691,7 @@ int dispatch_mode(int mode, int grad, const Job* j, int n, int items, int sms, c
 
 template <int PREC, int SHAPE>
 int occupancy_mode(int mode, int grad) {
-  if constexpr (SHAPE == kShapeList) {
+  if constexpr (is_list(SHAPE)) {
     if (mode == 2 || mode == 3) return 0;
   } else {
     if (mode == 2) return occupancy_one<PREC, SHAPE, 2, true>();

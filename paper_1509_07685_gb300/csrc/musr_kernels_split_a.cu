@@ -1,4 +1,4 @@
-// musr_kernels_split_a.cu -- instantiates the SPLIT (kShapeGeneric, kShapeT1, kShapeN1, kShapeT1N1, kShapeList) kernels of musr_kernels.cuh.
+// musr_kernels_split_a.cu -- instantiates the SPLIT (kShapeGeneric, kShapeT1, kShapeN1, kShapeT1N1, kShapeList, kShapeListS) kernels of musr_kernels.cuh.
 #include "musr_kernels.cuh"
 
 namespace musr {
@@ -16,6 +16,8 @@ int launch_group_a(int shape, int mode, int grad, const Job* j, int n, int items
       return kern::dispatch_mode<1, kShapeT1N1>(mode, grad, j, n, items, sms, s, info);
     case kShapeList:
       return kern::dispatch_mode<1, kShapeList>(mode, grad, j, n, items, sms, s, info);
+    case kShapeListS:
+      return kern::dispatch_mode<1, kShapeListS>(mode, grad, j, n, items, sms, s, info);
     default:
       return -1;
   }
@@ -32,6 +34,8 @@ int occupancy_group_a(int shape, int mode, int grad) {
       return kern::occupancy_mode<1, kShapeT1N1>(mode, grad);
     case kShapeList:
       return kern::occupancy_mode<1, kShapeList>(mode, grad);
+    case kShapeListS:
+      return kern::occupancy_mode<1, kShapeListS>(mode, grad);
     default:
       return 0;
   }

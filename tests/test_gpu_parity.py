@@ -381,8 +381,15 @@ def test_term_lists_without_basis_form(B):
     its Gauss-Newton products are refused (FP64 only)."""
     import test_oracle_pins as pins
     q, xq = pins._new_primitive_problem()
+    # three terms, one of four primitives: the general term-list kernel (the others fit the
+    # kernel for at most two terms of at most three primitives)
+    big_terms = q.terms + [[("AMP", (9,)), ("STREXP", (10, 4)), ("GAUSS", (6,)), ("TFCOS", (6, 7))]]
+    big_map = np.hstack([q.map, np.array([[12, 13], [12, 14]], np.int32)])
+    qb = mi.Problem(q.counts, q.t0, q.bin_width_ns, q.fit_range_us, big_terms, big_map, q.consts, 15, np.zeros(15),
+                    [f"p{i}" for i in range(15)])
+    xb = np.concatenate([xq, [0.05, 0.9, 1.2]])
     cases = [(mi.inc_bessel(nhist=2, nbins=3000, bin_width_ns=4.0, seed=71), None),
-             (mi.levy_lf(nhist=3, nbins=2500, bin_width_ns=5.0, seed=72), None), (q, xq)]
+             (mi.levy_lf(nhist=3, nbins=2500, bin_width_ns=5.0, seed=72), None), (q, xq), (qb, xb)]
     for p, x in cases:
         x = mi.start_point(p, 2) if x is None else x
         X = mi.jitter(x, 4, seed=3, lo=0.98, hi=1.02)
