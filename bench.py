@@ -123,7 +123,7 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(ROOT, ".clocks", f"clocks_bench_{os.getpid()}.csv")  # git-ignored
 
     def __enter__(self):
         try:
