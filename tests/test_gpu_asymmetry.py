@@ -48,12 +48,18 @@ def _cases():
                                      backward=base.backward.astype(np.int32)),
         "fp64": dataclasses.replace(base, forward=base.forward.astype(np.float64),
                                     backward=base.backward.astype(np.float64)),
+        # a few counts per bin over a larger background: many bins with f + alpha b <= 0
+        # (weight 0) and many with one count only
+        "low_counts": mi.asym_tf(npairs=3, nbins=5000, bin_width_ns=2.0, seed=64, n0=3.0, nbkg=2.0),
     }
 
 
-@pytest.mark.parametrize("name", ["tf_pairs", "two_terms", "t0_offsets", "int32", "fp64"])
+@pytest.mark.parametrize("name", ["tf_pairs", "two_terms", "t0_offsets", "int32", "fp64", "low_counts"])
 def test_asymmetry_matches_oracle(B, name):
     p = _cases()[name]
+    if name == "low_counts":  # the case does what it is there for
+        _, w = oracle.asymmetry(p.forward, p.backward, p.alpha, p.bkg_f, p.bkg_b)
+        assert 0.2 < np.mean(w == 0.0) < 0.9
     x = mi.start_point(p, 4)
     X = mi.jitter(x, 6, seed=9, lo=0.98, hi=1.02)
     ref = oracle.cost(p, x, 0)

@@ -410,6 +410,23 @@ def test_term_lists_without_basis_form(B):
             assert e.value.status == B.MUSR_EINVAL and "basis form" in str(e.value)
 
 
+def test_full_size_in_the_benchmark_launch_configuration(B):
+    """cfg2 at its full size (8 x 65536 bins) with 64 parameter vectors per launch of -2lnL
+    value+gradient, the launch the benchmark times (its decomposition: tiles of 16384 bins):
+    sampled vectors of the batch against the oracle, SPLIT and FP64."""
+    p = mi.cfg2()
+    X = mi.jitter(p.truth, 64, seed=1, lo=0.95, hi=1.05)
+    with B.Context(p) as ctx:
+        vs, gs, st = ctx.eval_batch(X, 1, B.MUSR_SPLIT)
+        assert st == 0
+        v64, g64, st = ctx.eval_batch(X, 1, B.MUSR_FP64)
+        assert st == 0
+    for i in (0, 31, 63):
+        ref = oracle.cost(p, X[i], 1)
+        _check_split(vs[i], gs[i], ref)
+        _check_fp64(v64[i], g64[i], ref)
+
+
 def test_hbm_budget_is_enforced(B):
     p = mi.cfg2(nhist=8, nbins=65536, seed=2)
     ctx = B.musr_ctx_create(0, hbm_budget_bytes=1 << 20)
