@@ -91,6 +91,9 @@ def _args():
                     help="run only the particle-mesh Poisson leg and print its JSON")
     ap.add_argument("--poisson-meshes", default="64x64x32,128x128x64,256x256x128,512x512x256",
                     help="comma-separated mx x my x mz meshes of the Poisson leg")
+    ap.add_argument("--config-sweep", action="store_true",
+                    help="instead of the contract line: SPLIT and FP64 Gbins/s of every config at 1, 8 "
+                         "and 64 parameter vectors, both costs, with the oracle on one host thread")
     ap.add_argument("--precision-report", action="store_true",
                     help="instead of timing: the SPLIT path's error against FP64 for every config "
                          "(cost value, gradient, fitted parameters in units of sigma)")
@@ -264,7 +267,7 @@ def cpu_baseline(p, X, mode, budget_s=6.0):
     single = bins * n / (time.perf_counter() - t) / 1e9
     n_all, t_all, ncores = _oracle_all_cores(p, X, mode, budget_s)
     return {"value": bins * n_all / t_all / 1e9, "unit": "Gbins/s", "cores": ncores, "kind": "oracle",
-            "single_thread_value": single,
+            "single_thread_value": single, "cpu_model": _cpu_model()["model"],
             "sample": f"value+grad evaluations of the cfg2 workload ({bins} bins each) for {budget_s:.0f} s: "
                       f"{n} on one thread, {n_all} over {ncores} processes"}
 
@@ -726,6 +729,103 @@ def precision_report(args):
     print(json.dumps({"precision_report": out}), flush=True)
 
 
+def _sweep_time(B, ctx, dx, nvec, mode, prec, grad, do, flush, stream, reps):
+    """Mean CUDA-event seconds of one musr_eval_device launch (L2 flushed before each)."""
+    import torch
+    for _ in range(2):
+        B.musr_eval_device(ctx.ctx, dx.data_ptr(), nvec, mode, prec, grad, do.data_ptr())
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        B.musr_eval_device(ctx.ctx, dx.data_ptr(), nvec, mode, prec, grad, do.data_ptr())
+        b.record(stream)
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) * 1e-3 for a, b in ev]))
+
+
+def config_sweep(args):
+    """Throughput of every configuration: the SPLIT path at 1, 8 and 64 parameter vectors per
+    launch and the plain FP64 path at 8 (value+grad, chi^2 and -2lnL), the value-only scan of
+    cfg1 (1000 random vectors, FP64 and SPLIT), and the oracle on one host thread (value+grad;
+    for cfg5 on its first 4 histograms, 4 x 2^20 bins).  CUDA events on the launching stream,
+    L2 flushed before every launch.  One JSON line."""
+    import dataclasses
+    import torch
+    import musr_inputs as mi
+    import oracle
+    from paper_1509_07685_gb300 import binding as B
+    torch.cuda.set_device(0)
+    B.load()
+    oracle.build()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    cfgs = {"cfg1": mi.cfg1(), "cfg2": mi.cfg2(), "cfg3": mi.cfg3(), "cfg5": mi.cfg5(), "paper_tf16": mi.paper_tf16()}
+    out = {}
+    for name, p in cfgs.items():
+        row = {"nhist": p.H, "nbins": p.B, "params": p.nparams}
+        with torch.cuda.stream(stream):
+            with B.Context(p, cuda_stream=stream.cuda_stream) as ctx:
+                bins = ctx.bins_in_fit()
+                row["bins_in_fit"] = bins
+                for mode, mname in ((0, "chi2"), (1, "mle")):
+                    for nvec in (1, 8, 64):
+                        X = mi.jitter(p.truth, nvec, seed=1, lo=0.95, hi=1.05)
+                        dx = torch.tensor(X, dtype=torch.float64, device="cuda")
+                        do = torch.empty((nvec, 1 + p.nparams), dtype=torch.float64, device="cuda")
+                        t = _sweep_time(B, ctx, dx, nvec, mode, B.MUSR_SPLIT, True, do, flush, stream, 10)
+                        row[f"split_{mname}_{nvec}v_gbins_per_s"] = bins * nvec / t / 1e9
+                        if nvec == 8:
+                            t = _sweep_time(B, ctx, dx, nvec, mode, B.MUSR_FP64, True, do, flush, stream, 2)
+                            row[f"fp64_{mname}_8v_gbins_per_s"] = bins * nvec / t / 1e9
+                    if name == "cfg1":  # value-only scan of 1000 random vectors (truth x U(0.8, 1.2))
+                        X = mi.jitter(p.truth, 1000, seed=1, lo=0.8, hi=1.2)
+                        dx = torch.tensor(X, dtype=torch.float64, device="cuda")
+                        do = torch.empty((1000, 1 + p.nparams), dtype=torch.float64, device="cuda")
+                        for prec, pname in ((B.MUSR_SPLIT, "split"), (B.MUSR_FP64, "fp64")):
+                            t = _sweep_time(B, ctx, dx, 1000, mode, prec, False, do, flush, stream, 5)
+                            row[f"{pname}_{mname}_scan1000_value_only_gbins_per_s"] = bins * 1000 / t / 1e9
+                            row[f"{pname}_{mname}_scan1000_value_only_ms"] = t * 1e3
+        q = p
+        if p.H > 16:
+            q = dataclasses.replace(p, counts=p.counts[:4], t0=p.t0[:4], map=p.map[:4])
+            row["oracle_sample"] = "first 4 histograms"
+        qbins = _bins_in_fit(q)
+        x = mi.start_point(q, 100)
+        for mode, mname in ((0, "chi2"), (1, "mle")):
+            oracle.cost(q, x, mode)
+            n, t = 0, time.perf_counter()
+            while n < 3 or time.perf_counter() - t < 1.0:
+                oracle.cost(q, x, mode)
+                n += 1
+            row[f"oracle_1thread_{mname}_gbins_per_s"] = qbins * n / (time.perf_counter() - t) / 1e9
+        out[name] = row
+        print(name, json.dumps(row), flush=True)
+    print(json.dumps({"config_sweep": out, "cpu": _cpu_model(), "l2": "flushed before every launch"}), flush=True)
+
+
+def _cpu_model():
+    """Host CPU model name and core count (lscpu, else /proc/cpuinfo)."""
+    name = None
+    try:
+        txt = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in txt.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                name = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if name is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.startswith("model name"):
+                    name = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"model": name, "cores": os.cpu_count()}
+
+
 def _meshes(args):
     return [tuple(int(v) for v in m.split("x")) for m in args.poisson_meshes.split(",") if m]
 
@@ -748,6 +848,9 @@ def main():
     args = _args()
     if args.precision_report:
         precision_report(args)
+        return
+    if args.config_sweep:
+        config_sweep(args)
         return
     if args.poisson_only:
         poisson_only(args)
