@@ -562,3 +562,54 @@ def test_every_split_shape_matches_oracle(B, name):
             _check_split(v, g, ref)
             v2, _, _ = ctx.eval(x, mode, B.MUSR_SPLIT, grad=False)
             assert v2 == v
+
+
+def _limits_problem(nhist=1360, nbins=48, seed=71):
+    """A problem at the ABI's limits: MUSR_MAX_PARAMS (4096) parameters, MUSR_MAX_SLOTS (32)
+    slots with the phase in the last one, MUSR_MAX_TERMS (4) terms of MUSR_MAX_PRIMS (4)
+    primitives each; 1360 short histograms with N0, Nbkg and the phase per histogram, 16
+    shared parameters, slots 18 ... 30 mapped to a constant."""
+    terms = [[("AMP", (2,)), ("EXP", (3,)), ("GAUSS", (4,)), ("TFCOS", (5, 31))],
+             [("AMP", (6,)), ("EXP", (7,)), ("GAUSS", (8,)), ("TFCOS", (9, 31))],
+             [("AMP", (10,)), ("EXP", (11,)), ("KT", (12,)), ("EXP", (13,))],
+             [("AMP", (14,)), ("GAUSS", (15,)), ("LKT", (16,)), ("EXP", (17,))]]
+    shared = [0.10, 0.3, 0.2, 1.5, 0.08, 0.2, 0.1, 2.2, 0.05, 0.1, 0.4, 0.05, 0.04, 0.1, 0.3, 0.1]
+    rng = np.random.default_rng(seed)
+    mp = np.full((nhist, 32), -1, np.int32)
+    mp[:, 2:18] = np.arange(16)
+    h = np.arange(nhist)
+    mp[:, 0] = 16 + 3 * h
+    mp[:, 1] = 16 + 3 * h + 1
+    mp[:, 31] = 16 + 3 * h + 2
+    P = 16 + 3 * nhist
+    truth = np.empty(P)
+    truth[:16] = shared
+    truth[16::3] = 400.0 * (1.0 + 0.2 * h / nhist)
+    truth[17::3] = 3.0
+    truth[18::3] = 360.0 * h / nhist
+    dt_ns = 250.0
+    t = (np.arange(nbins) * dt_ns * 1e-3)[None, :]
+    shape = np.exp(-t / 2.197019) * (1.0 + 0.1 * np.exp(-0.3 * t) * np.cos(2 * np.pi * (1.5 * t + h[:, None] / nhist)))
+    counts = rng.poisson(truth[16::3, None] * shape + 3.0).astype(np.float32)
+    return mi.Problem(counts, np.zeros(nhist), dt_ns, (0.2, 11.8), terms, mp, np.zeros(1), P, truth,
+                      [f"p{i}" for i in range(P)])
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_abi_limits_match_oracle(B, mode):
+    """Every size limit of the ABI at once (4096 parameters, 32 slots, 4 terms of 4
+    primitives, 1360 histograms): both paths against the oracle, single and batched."""
+    p = _limits_problem()
+    assert p.nparams == 4096 and p.nslots == 32
+    X = mi.jitter(p.truth, 3, seed=72 + mode, lo=0.97, hi=1.03)
+    with B.Context(p) as ctx:
+        for prec, check in ((B.MUSR_FP64, _check_fp64), (B.MUSR_SPLIT, _check_split)):
+            ref = oracle.cost(p, X[0], mode)
+            assert ref[3] == 0
+            v, g, st = ctx.eval(X[0], mode, prec)
+            assert st == 0
+            check(v, g, ref)
+            vals, grads, st = ctx.eval_batch(X, mode, prec)
+            assert st == 0
+            for i in (1, 2):
+                check(vals[i], grads[i], oracle.cost(p, X[i], mode))

@@ -63,3 +63,48 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(musr_lib):
                              p.fit_range_us, p.terms, p.map, p.nparams, p.consts, d_x.data_ptr(), 0,
                              B.MUSR_FP64, True, d_out.data_ptr(), None)
     assert st == B.MUSR_EINVAL
+
+
+def test_noalloc_at_its_limits_matches_oracle(musr_lib):
+    """64 histograms, 1024 parameters and 256 constants (the scratch's limits), 32 slots and
+    4 terms of 4 primitives: both precisions against the oracle.  Slots the theory does not
+    read carry parameters of their own, whose derivatives must come out as zero."""
+    import dataclasses
+
+    import torch
+
+    from paper_1509_07685_gb300 import binding as B
+    from test_gpu_parity import _check_fp64, _check_split, _limits_problem
+    p = _limits_problem(nhist=64, nbins=700, seed=63)
+    mp = p.map.copy()
+    H, P0 = p.H, p.nparams  # 16 shared + 3 per histogram
+    extra = np.arange(12 * H, dtype=np.int32).reshape(H, 12) + P0
+    mp[:, 18:30] = extra  # unread slots
+    P = P0 + 12 * H
+    mp[:48, 30] = P + np.arange(48)
+    P += 48
+    mp[48:, 30] = -256  # consts[255]
+    consts = np.linspace(0.0, 1.0, 256)
+    rng = np.random.default_rng(64)
+    truth = np.concatenate([p.truth, rng.uniform(-1.0, 1.0, P - P0)])
+    q = dataclasses.replace(p, map=mp, consts=consts, nparams=P, truth=truth)
+    assert q.H == 64 and q.nparams == 1024 and len(q.consts) == 256 and q.nslots == 32
+    stride = (q.B + 3) // 4 * 4
+    d_counts = torch.zeros((q.H, stride), dtype=torch.float32, device="cuda")
+    d_counts[:, :q.B] = torch.from_numpy(np.ascontiguousarray(q.counts, dtype=np.float32)).cuda()
+    x = q.truth * np.random.default_rng(65).uniform(0.98, 1.02, q.nparams)
+    d_x = torch.tensor(x, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    for prec, check in ((B.MUSR_FP64, _check_fp64), (B.MUSR_SPLIT, _check_split)):
+        for mode in (B.MUSR_CHI2, B.MUSR_MLE):
+            d_out = torch.full((1 + q.nparams,), float("nan"), dtype=torch.float64, device="cuda")
+            st = B.musr_eval_noalloc(d_counts.data_ptr(), B.MUSR_DTYPE_FP32, q.H, q.B, stride, q.t0,
+                                     q.bin_width_ns, q.fit_range_us, q.terms, q.map, q.nparams, q.consts,
+                                     d_x.data_ptr(), mode, prec, True, d_out.data_ptr(), stream)
+            assert st == B.MUSR_OK
+            torch.cuda.synchronize()
+            out = d_out.cpu().numpy()
+            ref = oracle.cost(q, x, mode)
+            assert ref[3] == 0
+            check(out[0], out[1:], ref)
+            assert np.all(out[1 + P0:1 + P0 + 12 * H] == 0.0) and np.all(out[1 + P0 + 12 * H:] == 0.0)
