@@ -94,6 +94,12 @@ def _args():
     ap.add_argument("--config-sweep", action="store_true",
                     help="instead of the contract line: SPLIT and FP64 Gbins/s of every config at 1, 8 "
                          "and 64 parameter vectors, both costs, with the oracle on one host thread")
+    ap.add_argument("--sweep-configs", default="cfg1,cfg2,cfg3,cfg5,paper_tf16",
+                    help="configs of --config-sweep")
+    ap.add_argument("--sweep-vectors", default="1,8,64", help="parameter vectors per launch of --config-sweep")
+    ap.add_argument("--sweep-modes", default="0,1", help="costs of --config-sweep (0 chi^2, 1 -2lnL)")
+    ap.add_argument("--sweep-split-only", action="store_true",
+                    help="--config-sweep: the SPLIT launches only (no FP64 path, cfg1 scan or oracle)")
     ap.add_argument("--precision-report", action="store_true",
                     help="instead of timing: the SPLIT path's error against FP64 for every config "
                          "(cost value, gradient, fitted parameters in units of sigma)")
@@ -749,36 +755,45 @@ def config_sweep(args):
     launch and the plain FP64 path at 8 (value+grad, chi^2 and -2lnL), the value-only scan of
     cfg1 (1000 random vectors, FP64 and SPLIT), and the oracle on one host thread (value+grad;
     for cfg5 on its first 4 histograms, 4 x 2^20 bins).  CUDA events on the launching stream,
-    L2 flushed before every launch.  One JSON line."""
+    L2 flushed before every launch.  One JSON line.  ``--sweep-configs``, ``--sweep-vectors``
+    and ``--sweep-modes`` narrow it; ``--sweep-split-only`` keeps the SPLIT launches alone
+    (per config: 2 untimed, then 10 timed launches per vector count and cost)."""
     import dataclasses
     import torch
     import musr_inputs as mi
-    import oracle
     from paper_1509_07685_gb300 import binding as B
+    full = not args.sweep_split_only
     torch.cuda.set_device(0)
     B.load()
-    oracle.build()
+    if full:
+        import oracle
+        oracle.build()
     stream = torch.cuda.Stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    cfgs = {"cfg1": mi.cfg1(), "cfg2": mi.cfg2(), "cfg3": mi.cfg3(), "cfg5": mi.cfg5(), "paper_tf16": mi.paper_tf16()}
+    make = {"cfg1": mi.cfg1, "cfg2": mi.cfg2, "cfg3": mi.cfg3, "cfg5": mi.cfg5, "paper_tf16": mi.paper_tf16}
+    names = [n for n in args.sweep_configs.split(",") if n]
+    vectors = [int(v) for v in args.sweep_vectors.split(",") if v]
+    modes = [int(m) for m in args.sweep_modes.split(",") if m]
     out = {}
-    for name, p in cfgs.items():
+    for name in names:
+        p = make[name]()
         row = {"nhist": p.H, "nbins": p.B, "params": p.nparams}
         with torch.cuda.stream(stream):
             with B.Context(p, cuda_stream=stream.cuda_stream) as ctx:
                 bins = ctx.bins_in_fit()
                 row["bins_in_fit"] = bins
-                for mode, mname in ((0, "chi2"), (1, "mle")):
-                    for nvec in (1, 8, 64):
+                for mode in modes:
+                    mname = "mle" if mode else "chi2"
+                    for nvec in vectors:
                         X = mi.jitter(p.truth, nvec, seed=1, lo=0.95, hi=1.05)
                         dx = torch.tensor(X, dtype=torch.float64, device="cuda")
                         do = torch.empty((nvec, 1 + p.nparams), dtype=torch.float64, device="cuda")
                         t = _sweep_time(B, ctx, dx, nvec, mode, B.MUSR_SPLIT, True, do, flush, stream, 10)
                         row[f"split_{mname}_{nvec}v_gbins_per_s"] = bins * nvec / t / 1e9
-                        if nvec == 8:
+                        if nvec == 8 and full:
                             t = _sweep_time(B, ctx, dx, nvec, mode, B.MUSR_FP64, True, do, flush, stream, 2)
                             row[f"fp64_{mname}_8v_gbins_per_s"] = bins * nvec / t / 1e9
-                    if name == "cfg1":  # value-only scan of 1000 random vectors (truth x U(0.8, 1.2))
+                    if name == "cfg1" and full:  # value-only scan of 1000 random vectors (truth x U(0.8, 1.2))
                         X = mi.jitter(p.truth, 1000, seed=1, lo=0.8, hi=1.2)
                         dx = torch.tensor(X, dtype=torch.float64, device="cuda")
                         do = torch.empty((1000, 1 + p.nparams), dtype=torch.float64, device="cuda")
@@ -786,13 +801,18 @@ def config_sweep(args):
                             t = _sweep_time(B, ctx, dx, 1000, mode, prec, False, do, flush, stream, 5)
                             row[f"{pname}_{mname}_scan1000_value_only_gbins_per_s"] = bins * 1000 / t / 1e9
                             row[f"{pname}_{mname}_scan1000_value_only_ms"] = t * 1e3
+        if not full:
+            out[name] = row
+            print(name, json.dumps(row), flush=True)
+            continue
         q = p
         if p.H > 16:
             q = dataclasses.replace(p, counts=p.counts[:4], t0=p.t0[:4], map=p.map[:4])
             row["oracle_sample"] = "first 4 histograms"
         qbins = _bins_in_fit(q)
         x = mi.start_point(q, 100)
-        for mode, mname in ((0, "chi2"), (1, "mle")):
+        for mode in modes:
+            mname = "mle" if mode else "chi2"
             oracle.cost(q, x, mode)
             n, t = 0, time.perf_counter()
             while n < 3 or time.perf_counter() - t < 1.0:
