@@ -267,7 +267,7 @@ int musr_poisson_create(musr_poisson** out, int device, int mx, int my, int mz, 
     g_poisson_create_error = "mesh sizes must be >= 1";
     return MUSR_EINVAL;
   }
-  if (static_cast<double>(2 * mx) * (2 * my) * (2 * mz) >= 2147483648.0) {
+  if (8.0 * mx * my * mz >= 2147483648.0) {  // in double: 2 * mx may not fit an int
     g_poisson_create_error = "the doubled mesh must hold fewer than 2^31 points";
     return MUSR_EINVAL;
   }
