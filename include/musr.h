@@ -358,6 +358,20 @@ int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int64_t nbins,
                       const double* consts, int nconsts, const double* d_params, int mode,
                       int precision, int with_grad, double* d_out, void* cuda_stream);
 
+/* Self-check of the evaluation kernels' bounded waits (failure detection without a GPU
+ * fault).  Each staging wait of the SPLIT kernels waits on a shared-memory mbarrier with an
+ * iteration limit.  If a copy never lands, the wait gives up, the CTA records an error and
+ * the evaluation returns MUSR_ETIMEOUT; nothing faults, traps or hangs.  This call runs one
+ * CTA on `device` that performs that wait on a barrier nothing arrives on. The wait must give
+ * up. Then the CTA arrives on the barrier itself, and the same wait must see the completed
+ * phase.
+ * out_try_s: seconds per unsatisfied try (nullable); out_wait_s: seconds until the wait gave
+ * up, or -1 when its limit would take longer than 5 s at the measured rate and it was not run
+ * (nullable).
+ * Returns MUSR_OK when the wait gave up and the completed phase was seen; MUSR_ESTATE when
+ * any of that failed or the wait was not run; MUSR_EINVAL for a bad device; MUSR_ECUDA. */
+int musr_check_bounded_wait(int device, double* out_try_s, double* out_wait_s);
+
 /* ---------------------------------------------------------------------------
  * The particle-mesh Poisson solve of Section 3 ("FFT Based Particle-Mesh
  * Solver"): the potential of an isolated charge density on an mx x my x mz

@@ -32,7 +32,7 @@ EXPORTS = (
     "musr_upload_asymmetry", "musr_upload_histograms_device", "musr_set_theory", "musr_set_map", "musr_eval",
     "musr_eval_batch", "musr_eval_device", "musr_sync", "musr_bins_in_fit", "musr_gn_product",
     "musr_gauss_newton",
-    "musr_launches_per_eval", "musr_eval_noalloc", "musr_fit", "musr_server_create",
+    "musr_launches_per_eval", "musr_eval_noalloc", "musr_check_bounded_wait", "musr_fit", "musr_server_create",
     "musr_server_destroy", "musr_server_submit", "musr_server_poll", "musr_server_wait",
     "musr_server_stats_get", "musr_poisson_create", "musr_poisson_destroy", "musr_poisson_last_error",
     "musr_poisson_solve", "musr_poisson_solve_device",
@@ -116,6 +116,7 @@ def _declare(lib):
         "musr_eval_noalloc": ([vp, ctypes.c_int, ctypes.c_int, i64, i64, P(d), d, P(d), P(musr_term),
                                ctypes.c_int, P(i32), ctypes.c_int, ctypes.c_int, P(d), ctypes.c_int, vp,
                                ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
+        "musr_check_bounded_wait": ([ctypes.c_int, P(d), P(d)], ctypes.c_int),
         "musr_fit": ([vp, P(d), ctypes.c_int, ctypes.c_int, ctypes.c_int, d, P(d), P(musr_fit_result)],
                      ctypes.c_int),
         "musr_server_create": ([P(vp), ctypes.c_int, ctypes.c_size_t, ctypes.c_int], ctypes.c_int),
@@ -349,6 +350,13 @@ def musr_eval_noalloc(d_counts: int, dtype: int, nhist: int, nbins: int, row_str
                                     mp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), mp.shape[1],
                                     int(nparams), _dptr(c), len(consts), ctypes.c_void_p(d_params), mode,
                                     precision, int(bool(with_grad)), ctypes.c_void_p(d_out), stream)
+
+
+def musr_check_bounded_wait(device: int = 0):
+    """(status, seconds per unsatisfied try, seconds until the kernels' wait gave up)."""
+    t_try, t_wait = ctypes.c_double(-1.0), ctypes.c_double(-1.0)
+    st = load().musr_check_bounded_wait(int(device), ctypes.byref(t_try), ctypes.byref(t_wait))
+    return st, t_try.value, t_wait.value
 
 
 # --------------------------------------------------------------------------------------------
