@@ -10,16 +10,18 @@ Each case draws:
 * 1 to 6 histograms of 700 to 3000 bins, with per-histogram time zeros (whole or fractional
   bins, or all equal), a random fit window and a random count dtype.
 
-The values keep |A(t)| below 1/2, so N > 0 and -2lnL is defined.  The SPLIT planner then
-picks a basis shape, the generic shape or the term-list kernel.  Tolerances are those of
-test_gpu_parity: FP64 1e-12, SPLIT 2^-16, relative to the value and to the gradient scale.
+Amplitudes of at most 0.12 in at most 4 terms keep |A(t)| well below 1 (below 0.7 even at
+the few negative times of a window that starts before time zero), so N > 0 and -2lnL is
+defined.  The SPLIT planner then picks a basis shape, the generic shape or the term-list
+kernel.  Tolerances are those of test_gpu_parity: FP64 1e-12, SPLIT 2^-16, relative to
+the value and to the gradient scale; the Gauss-Newton matrices against sqrt(H_pp H_qq).
 """
 import numpy as np
 import pytest
 
 import musr_inputs as mi
 import oracle
-from test_gpu_parity import _check_fp64, _check_split
+from test_gpu_parity import SPLIT_EPS, _check_fp64, _check_split
 
 pytestmark = pytest.mark.gpu
 
@@ -130,3 +132,41 @@ def test_random_theory_matches_oracle(B, seed):
                 vals, grads, st = ctx.eval_batch(X, mode, prec)
                 assert st == 0
                 check(vals[1], grads[1], oracle.cost(p, X[1], mode))
+
+
+def _check_gn(H, ref, tol):
+    scale = np.sqrt(np.outer(np.abs(np.diag(ref)), np.abs(np.diag(ref))))
+    bad = np.abs(H - ref) > tol * scale + 1e-300
+    assert not bad.any(), (np.argwhere(bad)[:5], float(np.max(np.abs(H - ref) / (scale + 1e-300))))
+
+
+# J0 and J1 come from two libraries, CUDA's j0/j1 on the device and libstdc++'s
+# std::cyl_bessel_j in the oracle.  At the arguments met here (up to 2 pi (8 MHz x 30 us + 1),
+# about 1500 rad) they agree to ~5e-13 absolute; the oracle against scipy, a third library,
+# differs by 4.4e-13 at most over [0, 2000].  There |J| has the envelope sqrt(2 / (pi x)), about
+# 0.02, so the relative difference per bin is up to 5e-13 / 0.02 = 2.5e-11.  A Gauss-Newton
+# diagonal squares a derivative carrying that factor: 2 x 2.5e-11 = 5e-11.  The cost and the
+# gradient keep 1e-12: there the per-bin differences enter with the residual's changing sign.
+BESSEL_GN_TOL = 5e-11
+
+
+@pytest.mark.parametrize("seed", range(0, NCASES, 2))
+def test_random_theory_gauss_newton_matches_oracle(B, seed):
+    """Gauss-Newton matrices of the same random theories: the FP64 path for every theory
+    (1e-12 of sqrt(H_pp H_qq); BESSEL_GN_TOL with a Bessel factor); SPLIT (2^-16) where the
+    theory has a basis form, and MUSR_EINVAL where it has none."""
+    p = random_problem(1000 + seed)
+    x = mi.jitter(p.truth, 1, seed=seed, lo=0.97, hi=1.03)[0]
+    bessel = any(k == "BESSEL" for term in p.terms for k, _ in term)
+    with B.Context(p) as ctx:
+        if ctx.bins_in_fit() == 0:
+            pytest.skip("empty fit window")
+        for mode in (0, 1):
+            ref = oracle.gauss_newton(p, x, mode)
+            _check_gn(ctx.gauss_newton(x, mode, B.MUSR_FP64), ref, BESSEL_GN_TOL if bessel else 1e-12)
+            try:
+                H = ctx.gauss_newton(x, mode, B.MUSR_SPLIT)
+            except B.MusrError as e:  # no basis form: the term-list kernel has no products
+                assert e.status == B.MUSR_EINVAL
+                continue
+            _check_gn(H, ref, SPLIT_EPS)
