@@ -65,6 +65,15 @@ MUTANTS = {
     "asymmetry weight missing from the gradient": ("        W = -2.0 * w * r;", "        W = -2.0 * r;"),
     "asymmetry scale derivative": ("    dslot[0] += A;", "    dslot[0] += 1.0 + A;"),
     "Gauss-Newton weight of chi^2": ("        c2 = 2.0 / std::fmax(d, 1.0);", "        c2 = 1.0 / std::fmax(d, 1.0);"),
+    "-2lnL gradient weight inverted": ("        W = 2.0 * (1.0 - d / N);", "        W = 2.0 * (1.0 - N / d);"),
+    "chi^2 gradient weight sign": ("        W = -2.0 * r / std::fmax(d, 1.0);", "        W = 2.0 * r / std::fmax(d, 1.0);"),
+    "exponential derivative sign": ("      *d0 = -t * std::exp(-p0 * t);", "      *d0 = t * std::exp(-p0 * t);"),
+    "Gaussian derivative drops sigma": ("      *d0 = -p0 * t * t * std::exp(-0.5 * (p0 * t) * (p0 * t));",
+                                        "      *d0 = -t * t * std::exp(-0.5 * (p0 * t) * (p0 * t));"),
+    "-2lnL empty bin halved": ("        acc.add(2.0 * (N - d));", "        acc.add(N - d);"),
+    "-2lnL empty-bin gradient halved": ("        W = 2.0;", "        W = 1.0;"),
+    "stretched exponential is 0 before time zero": ("if (!(t > 0.0) || re(x) == 0.0) return T(1.0);",
+                                                    "if (!(t > 0.0) || re(x) == 0.0) return T(0.0);"),
 }
 
 
