@@ -36,7 +36,7 @@ from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
 
-TAU_MU_US = 2.197019  # muon lifetime in microseconds (the value this build fixes)
+TAU_MU_US = 2.197019  # muon lifetime in microseconds (the paper gives no value; this one is used throughout)
 
 # --------------------------------------------------------------------------------------------
 # Problem description (plain data)
