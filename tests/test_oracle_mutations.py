@@ -74,6 +74,9 @@ MUTANTS = {
     "-2lnL empty-bin gradient halved": ("        W = 2.0;", "        W = 1.0;"),
     "stretched exponential is 0 before time zero": ("if (!(t > 0.0) || re(x) == 0.0) return T(1.0);",
                                                     "if (!(t > 0.0) || re(x) == 0.0) return T(0.0);"),
+    "asymmetry Gauss-Newton weight": ("        c2 = 2.0 * w;", "        c2 = 2.0;"),
+    "Gauss-Newton Jacobian overwrites a parameter read by two slots": (
+        "        if (m >= 0) J[m] += dslot[s];", "        if (m >= 0) J[m] = dslot[s];"),
 }
 
 

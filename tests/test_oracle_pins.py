@@ -352,18 +352,20 @@ def test_gauss_newton_equals_hessian_when_data_equal_model():
     wrong weight (d^2 cost/dN^2) or a wrong Jacobian."""
     terms = [[("AMP", (2,)), ("EXP", (3,)), ("TFCOS", (4, 5))], [("AMP", (6,)), ("KT", (7,))],
              [("AMP", (8,)), ("GAUSS", (9,))]]
-    mp = [[0, 1, 2, 3, 4, 5, 6, 7, 8, 9]]
-    x = np.array([250.0, 3.0, 0.2, 0.4, 3.0, 20.0, 0.1, 0.5, 0.08, 0.7])
-    p = _problem(np.zeros((1, 700)), terms, mp, 10, bin_width_ns=10.0, fit=(0.0, 6.0))
-    dt = p.bin_width_ns / 1000.0
-    p = p.with_counts(np.array([[oracle.model(p, x, 0, n * dt) for n in range(700)]]))
-    for mode in (CHI2, MLE):
-        gn = oracle.gauss_newton(p, x, mode)
-        h = oracle.hessian(p, x, mode, steps=1e-6 * np.maximum(np.abs(x), 1e-2))
-        scale = np.sqrt(np.outer(np.diag(gn), np.diag(gn)))
-        assert np.all(np.abs(gn - h) <= 1e-6 * scale + 1e-9), np.max(np.abs(gn - h) / scale)
-        assert np.allclose(gn, gn.T, rtol=1e-14, atol=0)
-        assert np.linalg.eigvalsh(gn).min() > -1e-9 * np.abs(gn).max()
+    x10 = np.array([250.0, 3.0, 0.2, 0.4, 3.0, 20.0, 0.1, 0.5, 0.08, 0.7])
+    # second map: one parameter in two slots of the row (the first and third amplitudes, the
+    # exponential rate and the Gaussian width), whose Jacobian entries must add
+    for mp, x in (([[0, 1, 2, 3, 4, 5, 6, 7, 8, 9]], x10), ([[0, 1, 2, 3, 4, 5, 6, 7, 2, 3]], x10[:8])):
+        p = _problem(np.zeros((1, 700)), terms, mp, len(x), bin_width_ns=10.0, fit=(0.0, 6.0))
+        dt = p.bin_width_ns / 1000.0
+        p = p.with_counts(np.array([[oracle.model(p, x, 0, n * dt) for n in range(700)]]))
+        for mode in (CHI2, MLE):
+            gn = oracle.gauss_newton(p, x, mode)
+            h = oracle.hessian(p, x, mode, steps=1e-6 * np.maximum(np.abs(x), 1e-2))
+            scale = np.sqrt(np.outer(np.diag(gn), np.diag(gn)))
+            assert np.all(np.abs(gn - h) <= 1e-6 * scale + 1e-9), np.max(np.abs(gn - h) / scale)
+            assert np.allclose(gn, gn.T, rtol=1e-14, atol=0)
+            assert np.linalg.eigvalsh(gn).min() > -1e-9 * np.abs(gn).max()
 
 
 def test_gauss_newton_of_constant_model_closed_form():
