@@ -77,6 +77,14 @@ MUTANTS = {
     "asymmetry Gauss-Newton weight": ("        c2 = 2.0 * w;", "        c2 = 2.0;"),
     "Gauss-Newton Jacobian overwrites a parameter read by two slots": (
         "        if (m >= 0) J[m] += dslot[s];", "        if (m >= 0) J[m] = dslot[s];"),
+    "product rule drops the other factors": ("      dslot[sl[0]] += N0 * E * d0 * rest;",
+                                             "      dslot[sl[0]] += N0 * E * d0;"),
+    "second slot's derivative to the first slot": (
+        "      if (nslots_of(kind) == 2) dslot[sl[1]] += N0 * E * d1 * rest;",
+        "      if (nslots_of(kind) == 2) dslot[sl[0]] += N0 * E * d1 * rest;"),
+    "background derivative carries the decay": ("  dslot[0] += E * (1.0 + A);\n  dslot[1] += 1.0;",
+                                                 "  dslot[0] += E * (1.0 + A);\n  dslot[1] += E;"),
+    "product rule keeps the differentiated factor": ("        if (q != m) rest *= f[q];", "        rest *= f[q];"),
 }
 
 
