@@ -1,24 +1,27 @@
 #!/usr/bin/env python
 """Benchmark of the muSR fused value+gradient cost (arXiv 1509.07685, Section 4).
 
-Workload (one GPU): the global two-term TF fit -- 8 histograms x 65536 bins of
-0.1953125 ns, FP32 counts from the seeded event-level Monte Carlo, 28
-parameters -- evaluated with the fused value+analytic-gradient kernel in the
-FP32/FP64-split precision.  One step is one launch that evaluates a batch of
-64 parameter vectors (the trial points a fitter or a multi-start scan hands
-over at once): params in, 64 x (1 + 28) doubles out.  The L2 is flushed
-(a 512 MiB write) between timed steps.
+Workload of the contract line (one GPU): the large single fit -- 64 histograms x 2^20
+bins (12.8 us at 12.2 ps per bin), FP32 counts from the seeded event-level Monte Carlo
+(256 MiB, N0 = 2 counts per bin: the maximum-likelihood regime), two precession terms
+plus a static Gaussian Kubo-Toyabe term, 197 parameters -- evaluated with the fused
+value+analytic-gradient kernel in the FP32/FP64-split precision.  One step is one launch
+that evaluates a batch of 64 parameter vectors (the trial points a fitter or a
+multi-start scan hands over at once): params in, 64 x (1 + 197) doubles out.  The counts
+(256 MiB) are larger than the L2; the L2 is also flushed (a 512 MiB write) between
+timed steps.
 
-Printed JSON line (rank 0): value = (histogram, bin) pairs x vectors per
-second of device time (Gbins/s), measured with CUDA events on the launching
-stream; e2e = the same through the C ABI with host buffers (params H2D and
-results D2H inside the timed region); roofline of the fused kernel against the
-SM instruction-issue rate; the plain FP64 path on the same batch; BFGS fits/s;
-the serving loop; the oracle timed on the host cores.
+Printed JSON line (rank 0): value = (histogram, bin) pairs x vectors per second of
+device time (Gbins/s), measured with CUDA events on the launching stream; e2e = the same
+through the C ABI with host buffers (params H2D and results D2H inside the timed
+region); roofline of the fused kernel against the SM instruction-issue rate; the plain
+FP64 path on the same workload; the global TF fit (8 x 65536 bins) as a second workload;
+BFGS fits/s of both precisions; the serving loop (SPLIT and FP64); the oracle timed on
+the host cores.
 
 ``--impl reference`` times the FP64 CPU oracle instead (the reference arm).
-Multi-GPU (torchrun): each rank evaluates its own independent fits (weak
-scaling, no collective on the data path); timing is max over ranks.
+Multi-GPU (torchrun): each rank evaluates its own independent fits (weak scaling, no
+collective on the data path); timing is max over ranks.
 """
 from __future__ import annotations
 
@@ -39,34 +42,46 @@ NVEC = 64
 LOAD_S = 1.5  # seconds of untimed back-to-back steps under the clock sampler before the timed ones
 # Roofline of the fused SPLIT kernel.  It is bound by instruction issue (one warp
 # instruction per SM sub-partition per clock: 152 SMs x 4 x 32 lanes x clock), not by HBM
-# (the batch re-reads one 2 MiB histogram set).  Algorithmic lane instructions per
-# (histogram, bin) of the basis form for the two-term TF model with a shared phase per
-# histogram (M = 3 basis functions, 8 histograms share the per-bin work), value+gradient:
-#   per (histogram, bin): 1 shared-memory load (two per two bins), 3 FMA for N,
+# (the counts are read once per launch, 4 bytes per (histogram, bin) against ~40 lane
+# operations).  Algorithmic lane operations per (histogram, bin) of the basis form,
+# value+gradient, with 8 histograms of a chunk sharing each bin's time-only work:
+#   per (histogram, bin): 1 shared-memory load, 3 FMA for N (M = 3 basis functions),
 #     cost (-2lnL: reciprocal, residual, u, 10-term series, log branch 4, 5 compares and
 #     selects = 22; chi^2: max, reciprocal, residual, u, value = 5), 1 value add,
-#     7 gradient accumulations (G_m, W, V_m);
+#     7 gradient accumulations (G_m 3, W 1, V_m 3);
 #   per bin / 8: time 2, E 2, per cosine term 17 (exponent 4, phase 9, sin and cos 2,
-#     cosine and sine parts 2), basis sums 2, value compensation 2, shared channels 17.
-ALGO_INST = {0: 24.0, 1: 41.0}
+#     cosine and sine parts 2), basis sums (one per term merged into a basis function),
+#     value compensation 2, shared channels (3 + 7 per cosine term + 4 per other term);
+#     the Kubo-Toyabe term: exponent 4, KT factor 12 (t^2, its exponential 2, u, the
+#     derivative factor 4, the factor itself 4).
+# Two cosine terms (the global TF fit, merged shape M = 3): 34 + 59/8 = 41 (-2lnL), 24 (chi^2).
+# Two cosine terms + Kubo-Toyabe (the large single fit): 34 + 80/8 = 44 (-2lnL), 27 (chi^2).
+ALGO_INST = {"cfg5": {0: 27.0, 1: 44.0}, "cfg2": {0: 24.0, 1: 41.0}}
 LANES_PER_SMSP, SMSP_PER_SM = 32, 4
-# DRAM bytes of one launch of the timed kernel from an ncu capture of this workload
+# DRAM bytes of one launch of the timed kernel from an ncu capture of the workload
 # (dram__bytes_read.sum + dram__bytes_write.sum, one -2lnL value+grad launch of 64 vectors),
-# valid for the kernel source and cost it was taken on.
-TRAFFIC = {"kernel_sha256": "879a6dcc0875abf094e81477de516b460f85ebc596798c2d0855cec008222c43",
-           "mode": 1, "bytes": 2231808}
+# valid for the kernel source and cost they were taken on (None: not captured for it).
+TRAFFIC = {
+    "cfg5": {"kernel_sha256": None, "mode": 1, "bytes": None},
+    "cfg2": {"kernel_sha256": "879a6dcc0875abf094e81477de516b460f85ebc596798c2d0855cec008222c43",
+             "mode": 1, "bytes": 2231808},
+}
 
 
-def _traffic(mode):
-    """Per-launch DRAM bytes of the timed kernel (ncu), or None when the kernel source or
-    the cost has changed since the capture."""
+def _kernel_sha():
     import hashlib
     src = os.path.join(ROOT, "paper_1509_07685_gb300", "csrc", "musr_kernels.cuh")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        return hashlib.sha256(open(src, "rb").read()).hexdigest()
     except OSError:
         return None
-    return TRAFFIC["bytes"] if TRAFFIC["kernel_sha256"] == sha and TRAFFIC["mode"] == mode else None
+
+
+def _traffic(name, mode):
+    """Per-launch DRAM bytes of the timed kernel (ncu), or None when the kernel source or
+    the cost has changed since the capture."""
+    t = TRAFFIC[name]
+    return t["bytes"] if t["kernel_sha256"] == _kernel_sha() and t["mode"] == mode else None
 
 
 def _env_int(name, default):
@@ -106,18 +121,34 @@ def _args():
     return ap.parse_args()
 
 
-def _workload(rank: int):
+WORKLOADS = {
+    "cfg5": "large single fit {H}x{B} FP32 counts (256 MiB), two TF terms + Kubo-Toyabe, {P} params, "
+            "fused value+grad, {V} param vectors per step",
+    "cfg2": "global TF fit {H}x{B} FP32 counts, two TF terms, {P} params, fused value+grad, "
+            "{V} param vectors per step",
+}
+
+
+def _problem(name: str, rank: int = 0):
+    """The seeded workload (a rank draws its own histograms) and its 64 parameter vectors."""
     import musr_inputs as mi
-    p = mi.cfg2(seed=2 + 1000 * rank)
+    if name == "cfg5":
+        p = mi.cfg5(seed=5 + 1000 * rank)
+    else:
+        p = mi.cfg2(seed=2 + 1000 * rank)
     X = mi.jitter(p.truth, NVEC, seed=1 + rank, lo=0.9, hi=1.1)
     return p, X
 
 
-def _workload_desc(p, mode):
-    return {"workload": f"cfg2 global TF fit {p.H}x{p.B} FP32 counts, {p.nparams} params, "
-                        f"fused value+grad, {NVEC} param vectors per step",
+def _workload(rank: int):
+    return _problem("cfg5", rank)
+
+
+def _workload_desc(p, mode, name="cfg5"):
+    return {"workload": WORKLOADS[name].format(H=p.H, B=p.B, P=p.nparams, V=NVEC),
             "mode": "chi2" if mode == 0 else "mle", "nhist": p.H, "nbins": p.B,
-            "params": p.nparams, "vectors_per_step": NVEC, "l2": "flushed between steps (512 MiB write)"}
+            "params": p.nparams, "vectors_per_step": NVEC,
+            "l2": "counts larger than L2; flushed between steps (512 MiB write)"}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -176,51 +207,90 @@ class ClockSampler:
 # Reference arm: the FP64 CPU oracle
 # ---------------------------------------------------------------------------------------------
 
+# The reference arm's step: value+grad of REF_VECTORS of the 64 vectors over all 64
+# histograms, split over the host cores by (vector, group of REF_GROUP histograms); the cost
+# and its gradient are sums over histograms, so the groups' results add up to the whole.
+REF_VECTORS = 4
+REF_GROUP = 16
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
     import multiprocessing as mp
 
     p, X = _workload(0)
-    bins_per_eval = _bins_in_fit(p)
+    groups = [list(range(g, min(g + REF_GROUP, p.H))) for g in range(0, p.H, REF_GROUP)]
+    tasks = [(k, g, args.mode) for k in range(REF_VECTORS) for g in range(len(groups))]
+    bins_per_step = _bins_in_fit(p) * REF_VECTORS
     ncores = os.cpu_count() or 1
-    # One step is the same step as the GPU arm's: value+grad of the batch's NVEC parameter
-    # vectors, spread over one oracle process per host core.
-    with mp.get_context("spawn").Pool(ncores, initializer=_pool_init, initargs=(p, X)) as pool:
-        for w in range(max(args.warmup, 1)):
-            pool.map(_oracle_one, [(k, args.mode) for k in range(NVEC)], chunksize=1)
-        t = time.perf_counter()
-        for s in range(args.steps):
-            pool.map(_oracle_one, [(k, args.mode) for k in range(NVEC)], chunksize=1)
-        dt = (time.perf_counter() - t) / max(args.steps, 1)
-    val = bins_per_eval * NVEC / dt / 1e9
+    with _SharedCounts(p) as shm:
+        with mp.get_context("spawn").Pool(ncores, initializer=_pool_init,
+                                          initargs=(shm.spec(), p, X, groups)) as pool:
+            for w in range(max(args.warmup, 1)):
+                pool.map(_oracle_task, tasks, chunksize=1)
+            t = time.perf_counter()
+            for s_ in range(args.steps):
+                pool.map(_oracle_task, tasks, chunksize=1)
+            dt = (time.perf_counter() - t) / max(args.steps, 1)
+    val = bins_per_step / dt / 1e9
+    sample = (f"each step: value+grad of {REF_VECTORS} of the {NVEC} parameter vectors over all {p.H} "
+              f"histograms ({bins_per_step} (histogram, bin) pairs), {len(tasks)} tasks (vector x group of "
+              f"{REF_GROUP} histograms) over {ncores} processes")
     line = {"metric": "value+grad Gbins/s", "value": val, "unit": "Gbins/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference", "config": _workload_desc(p, args.mode),
             "cpu_baseline": {"value": val, "unit": "Gbins/s", "cores": ncores, "kind": "oracle",
-                             "cpu_model": _cpu_model()["model"],
-                             "sample": f"every step whole: {NVEC} cfg2 value+grad evaluations ({bins_per_eval} "
-                                       f"bins each) over {ncores} processes"},
+                             "cpu_model": _cpu_model()["model"], "sample": sample},
             "e2e": {"value": val, "unit": "Gbins/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+class _SharedCounts:
+    """The workload's counts in a shared-memory block, so that spawned oracle processes map
+    them instead of each receiving a pickled copy."""
+
+    def __init__(self, p):
+        from multiprocessing import shared_memory
+        c = np.ascontiguousarray(p.counts)
+        self.shape, self.dtype = c.shape, c.dtype.str
+        self.shm = shared_memory.SharedMemory(create=True, size=max(c.nbytes, 1))
+        np.ndarray(c.shape, c.dtype, buffer=self.shm.buf)[...] = c
+
+    def spec(self):
+        return (self.shm.name, self.shape, self.dtype)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.shm.close()
+        self.shm.unlink()
 
 
 _POOL_WORK = {}
 
 
-def _pool_init(p, X):
-    """Spawned oracle worker: keep the problem and the vectors, load the library."""
+def _pool_init(spec, p, X, groups):
+    """Spawned oracle worker: map the shared counts, keep the vectors, load the library."""
+    import dataclasses
+    from multiprocessing import shared_memory
     import oracle
-    _POOL_WORK["p"], _POOL_WORK["X"] = p, X
+    name, shape, dtype = spec
+    shm = shared_memory.SharedMemory(name=name)
+    counts = np.ndarray(shape, np.dtype(dtype), buffer=shm.buf)
+    _POOL_WORK["shm"] = shm
+    _POOL_WORK["X"] = X
+    _POOL_WORK["sub"] = [dataclasses.replace(p, counts=counts[g], t0=p.t0[g], map=p.map[g]) for g in groups]
     oracle.build()
 
 
-def _oracle_one(args):
-    """One oracle value+grad evaluation of vector k (in a pool worker)."""
+def _oracle_task(args):
+    """One oracle value+grad evaluation of vector k on histogram group g (in a pool worker)."""
     import oracle
-    k, mode = args
-    oracle.cost(_POOL_WORK["p"], _POOL_WORK["X"][k % len(_POOL_WORK["X"])], mode)
+    k, g, mode = args
+    oracle.cost(_POOL_WORK["sub"][g], _POOL_WORK["X"][k % len(_POOL_WORK["X"])], mode)
 
 
 def _bins_in_fit(p):
@@ -258,30 +328,79 @@ def _oracle_all_cores(p, X, mode, seconds):
     return sum(n for n, _ in res), max(t for _, t in res), ncores
 
 
-def cpu_baseline(p, X, mode, budget_s=6.0):
-    """The oracle as it stands on a bounded sample of the same workload: one thread, then
-    one process per host core (the figure reported)."""
+def cpu_baseline(p, X, mode, budget_s=6.0, nhist=4):
+    """The oracle as it stands on a bounded sample of the same workload -- its first `nhist`
+    histograms, value+grad of the 64 vectors in turn -- on one thread, then one process per
+    host core (the figure reported)."""
+    import dataclasses
     import oracle
-    bins = _bins_in_fit(p)
-    oracle.cost(p, X[0], mode)
+    q = dataclasses.replace(p, counts=np.ascontiguousarray(p.counts[:nhist]), t0=p.t0[:nhist], map=p.map[:nhist])
+    bins = _bins_in_fit(q)
+    oracle.cost(q, X[0], mode)
     n = 0
     t = time.perf_counter()
     while True:
-        oracle.cost(p, X[n % len(X)], mode)
+        oracle.cost(q, X[n % len(X)], mode)
         n += 1
         if time.perf_counter() - t > budget_s or n >= 200:
             break
     single = bins * n / (time.perf_counter() - t) / 1e9
-    n_all, t_all, ncores = _oracle_all_cores(p, X, mode, budget_s)
+    n_all, t_all, ncores = _oracle_all_cores(q, X, mode, budget_s)
     return {"value": bins * n_all / t_all / 1e9, "unit": "Gbins/s", "cores": ncores, "kind": "oracle",
             "single_thread_value": single, "cpu_model": _cpu_model()["model"],
-            "sample": f"value+grad evaluations of the cfg2 workload ({bins} bins each) for {budget_s:.0f} s: "
-                      f"{n} on one thread, {n_all} over {ncores} processes"}
+            "sample": f"value+grad evaluations of the workload's first {nhist} histograms ({bins} bins each) for "
+                      f"{budget_s:.0f} s: {n} on one thread, {n_all} over {ncores} processes"}
 
 
 # ---------------------------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------------------------
+
+def _timed(B, ctx, d_x, nvec, mode, prec, d_out, flush, stream, steps, warmup, world=1):
+    """CUDA-event seconds of `steps` launches of nvec evaluations (L2 flushed before each)."""
+    import torch
+
+    def step():
+        B.musr_eval_device(ctx.ctx, d_x.data_ptr(), nvec, mode, prec, True, d_out.data_ptr())
+
+    for _ in range(warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for s_ in range(steps):
+        flush.zero_()
+        ev[s_][0].record(stream)
+        step()
+        ev[s_][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    return [a_.elapsed_time(b_) * 1e-3 for a_, b_ in ev]
+
+
+def _roofline(name, p, bins, mode, t_kernel, peaks, nsm):
+    """Roofline of one launch of the fused kernel: algorithmic lane operations per (histogram,
+    bin) x pairs per launch / CUDA-event time, against the SM instruction-issue rate."""
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_inst = nsm * SMSP_PER_SM * LANES_PER_SMSP * sm_max * 1e6
+    ach_inst = ALGO_INST[name][mode] * bins * NVEC / t_kernel
+    algo_bytes = 4 * p.H * p.B + 8 * NVEC * (p.nparams + 1 + p.nparams)  # counts once, params in, value+grad out
+    shape = "two TF terms + KT merged (M = 3)" if name == "cfg5" else "two TF terms merged (M = 3)"
+    return {"bound": "alu", "achieved": ach_inst / 1e12, "peak": peak_inst / 1e12, "unit": "Tinst/s",
+            "frac": ach_inst / peak_inst, "traffic": _traffic(name, mode),
+            "kernel": f"eval_kernel<SPLIT, {shape}, {'MLE' if mode else 'chi2'}, grad>",
+            "measure": "lane operations of the algorithm per (histogram, bin) x (histogram, bin) pairs "
+                       "per launch / CUDA-event time of the launch",
+            "instructions_per_hist_bin": ALGO_INST[name][mode],
+            "peak_source": f"instruction issue: {nsm} SMs x {SMSP_PER_SM} sub-partitions x "
+                           f"{LANES_PER_SMSP} lanes x {sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json)",
+            "algorithmic_bytes": algo_bytes,
+            "hbm_frac": algo_bytes / t_kernel / 1e9 / float(peaks.get("hbm_gbs", 6800.0)),
+            "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0))}
+
 
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -302,44 +421,23 @@ def run_ours(args, rank, world, local_rank):
     d_x = torch.tensor(X, dtype=torch.float64, device="cuda")
     d_out = torch.empty((NVEC, 1 + P), dtype=torch.float64, device="cuda")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    launches0 = B.musr_launches_per_eval(ctx.ctx)
 
-    def step(prec):
-        B.musr_eval_device(ctx.ctx, d_x.data_ptr(), NVEC, mode, prec, True, d_out.data_ptr())
-
-    def timed(prec, steps, warmup):
-        for _ in range(warmup):
-            flush.zero_()
-            step(prec)
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        times = []
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        for s in range(steps):
-            flush.zero_()
-            ev[s][0].record(stream)
-            step(prec)
-            ev[s][1].record(stream)
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        times = [a.elapsed_time(b) * 1e-3 for a, b in ev]
-        return times
-
-    # Main measurement (SPLIT).  The timed region lasts milliseconds, shorter than one
-    # nvidia-smi sample, so the sampler also covers LOAD_S seconds of the same steps run
-    # back to back just before it (untimed): the clocks the timed steps start from.
+    # Main measurement (SPLIT).  The sampler also covers LOAD_S seconds of the same steps
+    # run back to back just before the timed ones (untimed): the clocks they start from.
     with ClockSampler(local_rank) as clk:
         t_load = time.perf_counter()
         while time.perf_counter() - t_load < LOAD_S:
-            for _ in range(50):
+            for _ in range(10):
                 flush.zero_()
-                step(B.MUSR_SPLIT)
+                B.musr_eval_device(ctx.ctx, d_x.data_ptr(), NVEC, mode, B.MUSR_SPLIT, True, d_out.data_ptr())
             torch.cuda.synchronize()
         t_wall = time.perf_counter()
-        times = timed(B.MUSR_SPLIT, args.steps, max(args.warmup, 3))
+        times = _timed(B, ctx, d_x, NVEC, mode, B.MUSR_SPLIT, d_out, flush, stream, args.steps,
+                       max(args.warmup, 3), world)
         t_wall = time.perf_counter() - t_wall
     mean_t = float(np.mean(times))
+    t_kernel = mean_t
     if world > 1:
         tt = torch.tensor([mean_t], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
@@ -347,11 +445,13 @@ def run_ours(args, rank, world, local_rank):
     value = bins * NVEC * world / mean_t / 1e9
     out_split = d_out.cpu().numpy().copy()
 
-    # Plain FP64 path on the same batch (fewer steps: it is slow).
-    t64 = timed(B.MUSR_FP64, max(3, min(args.steps, 5)), 2)
-    fp64_gbins = bins * NVEC / float(np.mean(t64)) / 1e9
-    out_fp64 = d_out.cpu().numpy().copy()
-    rel_err = float(np.max(np.abs(out_split[:, 0] - out_fp64[:, 0]) / np.abs(out_fp64[:, 0])))
+    # Plain FP64 path on the same workload: the first 8 vectors (it is ~300x slower).
+    n64 = 8
+    d_o64 = torch.empty((n64, 1 + P), dtype=torch.float64, device="cuda")
+    t64 = _timed(B, ctx, d_x[:n64].contiguous(), n64, mode, B.MUSR_FP64, d_o64, flush, stream, 2, 1)
+    fp64_gbins = bins * n64 / float(np.mean(t64)) / 1e9
+    out_fp64 = d_o64.cpu().numpy()
+    rel_err = float(np.max(np.abs(out_split[:n64, 0] - out_fp64[:, 0]) / np.abs(out_fp64[:, 0])))
 
     # End to end through the C ABI with host buffers.
     Xh = np.ascontiguousarray(X)
@@ -362,7 +462,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.steps):
         ctx.eval_batch(Xh, mode, B.MUSR_SPLIT)
     e2e_t = (time.perf_counter() - t) / args.steps
-    if world > 1:  # whole job: every rank's fits over the slowest rank's time
+    if world > 1:  # whole job: every rank's evaluations over the slowest rank's time
         tt = torch.tensor([e2e_t], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         e2e_t = float(tt.item())
@@ -376,26 +476,25 @@ def run_ours(args, rank, world, local_rank):
     except Exception:
         pass
     clocks = clk.summary() | {"window": f"{LOAD_S} s of back-to-back steps, then the timed steps"}
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     nsm = torch.cuda.get_device_properties(local_rank).multi_processor_count
-    peak_inst = nsm * SMSP_PER_SM * LANES_PER_SMSP * sm_max * 1e6
-    t_kernel = mean_t if world == 1 else float(np.mean(times))
-    ach_inst = ALGO_INST[mode] * bins * NVEC / t_kernel
-    algo_bytes = 4 * p.H * p.B + 8 * NVEC * (P + 1 + P)  # counts once, params in, value+grad out
-    roofline = {"bound": "alu", "achieved": ach_inst / 1e12, "peak": peak_inst / 1e12, "unit": "Tinst/s",
-                "frac": ach_inst / peak_inst, "traffic": _traffic(mode),
-                "kernel": f"eval_kernel<SPLIT, two TF terms merged (M = 3), {'MLE' if mode else 'chi2'}, grad>",
-                "measure": "lane instructions of the algorithm per (histogram, bin) x (histogram, bin) pairs "
-                           "per launch / CUDA-event time of the launch",
-                "instructions_per_hist_bin": ALGO_INST[mode],
-                "peak_source": f"instruction issue: {nsm} SMs x {SMSP_PER_SM} sub-partitions x "
-                               f"{LANES_PER_SMSP} lanes x {sm_max:.0f} MHz (max SM clock)",
-                "algorithmic_bytes": algo_bytes,
-                "hbm_frac": algo_bytes / t_kernel / 1e9 / float(peaks.get("hbm_gbs", 6800.0))}
+    roofline = _roofline("cfg5", p, bins, mode, t_kernel, peaks, nsm)
+
+    # The second workload (the global TF fit, 8 x 65536 bins): same measurement.
+    q, Xq = _problem("cfg2", rank)
+    with B.Context(q, device=local_rank, cuda_stream=stream.cuda_stream) as cq:
+        bq = cq.bins_in_fit()
+        dq = torch.tensor(Xq, dtype=torch.float64, device="cuda")
+        doq = torch.empty((NVEC, 1 + q.nparams), dtype=torch.float64, device="cuda")
+        tq = float(np.mean(_timed(B, cq, dq, NVEC, mode, B.MUSR_SPLIT, doq, flush, stream, args.steps,
+                                  max(args.warmup, 3))))
+        tq64 = float(np.mean(_timed(B, cq, dq, NVEC, mode, B.MUSR_FP64, doq, flush, stream, 2, 1)))
+    second = {"config": _workload_desc(q, mode, "cfg2"), "value": bq * NVEC / tq / 1e9, "unit": "Gbins/s",
+              "ms_per_step": tq * 1e3, "roofline": _roofline("cfg2", q, bq, mode, tq, peaks, nsm),
+              "fp64_path": {"value": bq * NVEC / tq64 / 1e9, "unit": "Gbins/s", "split_speedup": tq64 / tq}}
 
     fits = asym = poisson = lists = None
     if not args.no_fits and rank == 0:
-        fits = _fits(p, ctx, B, mode)
+        fits = _fits(B, mode)
         asym = _asymmetry(B, flush, stream)
         lists = _term_lists(B, flush, stream)
         poisson = _poisson(B, peaks, cpu=not args.no_cpu, meshes=_meshes(args))
@@ -412,12 +511,16 @@ def run_ours(args, rank, world, local_rank):
                 "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": mean_t * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64-split",
                 "data": "synthetic (seeded event-level Monte Carlo muSR histograms)",
-                "config": _workload_desc(p, mode) | {"parallelism": f"dp{world} (independent fits per rank)"},
+                "config": _workload_desc(p, mode),
                 "e2e": e2e, "roofline": roofline, "clocks": clocks,
-                "gpu_launches": args.steps, "wall_s_timed_region": t_wall,
-                "fp64_path": {"value": fp64_gbins, "unit": "Gbins/s", "split_speedup": value / world / fp64_gbins,
+                "gpu_launches": args.steps * launches0, "wall_s_timed_region": t_wall,
+                "parallelism": f"dp{world} (independent fits per rank)",
+                "fp64_path": {"value": fp64_gbins, "unit": "Gbins/s", "vectors": n64,
+                              "split_speedup": value / world / fp64_gbins,
                               "max_rel_value_diff_split_vs_fp64": rel_err},
-                "fits": fits, "asymmetry": asym, "term_lists": lists, "poisson": poisson, "serving": serving, "cpu_baseline": cpu}
+                "global_tf_fit": second,
+                "fits": fits, "asymmetry": asym, "term_lists": lists, "poisson": poisson, "serving": serving,
+                "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -584,96 +687,110 @@ def _poisson(B, peaks, cpu=True, meshes=((64, 64, 32), (128, 128, 64), (256, 256
     return out
 
 
-def _fits(p, ctx, B, mode):
-    """fits/s of the SPLIT path: BFGS fits one after another through the C ABI's native
-    fit (musr_fit: C++ BFGS driving the fused kernel), and through the Python BFGS of
-    fit.py; the agreement with the FP64 fit."""
+def _fits(B, mode, nfits=8):
+    """fits/s of both precisions on the global TF fit (8 x 65536 bins, 28 parameters): BFGS
+    fits one after another through the C ABI's native fit (musr_fit: C++ BFGS driving the
+    fused kernel) from the same 8 start points, SPLIT and FP64; the Python BFGS of fit.py;
+    the agreement of the SPLIT fit with the FP64 fit; parameter errors."""
     try:
         from paper_1509_07685_gb300 import fit as F
     except Exception:
         return None
     import musr_inputs as mi
-    lat, nfev, xs = [], [], []
-    for s in range(8):
-        x0 = mi.start_point(p, 100 + s)
+    p = mi.cfg2()
+    out = {"workload": f"global TF fit {p.H}x{p.B}, {p.nparams} params, {'MLE' if mode else 'chi2'}, "
+                       f"{nfits} fits from the same start points per precision"}
+    with B.Context(p) as ctx:
+        res = {}
+        for prec, name in ((B.MUSR_SPLIT, "split"), (B.MUSR_FP64, "fp64")):
+            B.musr_fit(ctx.ctx, mi.start_point(p, 99), mode, prec)  # warm-up: tables, buffers
+            lat, nfev, xs = [], [], []
+            for s_ in range(nfits):
+                x0 = mi.start_point(p, 100 + s_)
+                t = time.perf_counter()
+                r = B.musr_fit(ctx.ctx, x0, mode, prec)
+                lat.append(time.perf_counter() - t)
+                nfev.append(r["nfev"])
+                xs.append(r["x"])
+            res[name] = xs
+            out[name] = {"fits_per_s": len(lat) / sum(lat), "latency_ms_p50": 1e3 * float(np.median(lat)),
+                         "latency_ms_max": 1e3 * float(np.max(lat)), "evals_per_fit": float(np.mean(nfev))}
+        out["split_speedup_fits_per_s"] = out["split"]["fits_per_s"] / out["fp64"]["fits_per_s"]
+        out["path"] = "musr_fit (C++ BFGS through the C ABI)"
+        lat_py = []
+        for s_ in range(4):
+            t = time.perf_counter()
+            F.fit_context(ctx, mi.start_point(p, 100 + s_), mode, B.MUSR_SPLIT)
+            lat_py.append(time.perf_counter() - t)
+        out["python_bfgs_split_fits_per_s"] = len(lat_py) / sum(lat_py)
+        x64 = res["fp64"][0]
         t = time.perf_counter()
-        r = B.musr_fit(ctx.ctx, x0, mode, B.MUSR_SPLIT)
-        lat.append(time.perf_counter() - t)
-        nfev.append(r["nfev"])
-        xs.append(r["x"])
-    lat_py = []
-    for s in range(4):
+        sig = F.sigmas_context(ctx, x64, mode)  # central differences of FP64 gradients (2P)
+        t_fd = time.perf_counter() - t
+        out["max_param_dev_split_vs_fp64_sigma"] = float(max(np.max(np.abs(a_ - b_) / sig)
+                                                             for a_, b_ in zip(res["split"], res["fp64"])))
+        for _ in range(2):
+            F.sigmas_gauss_newton(ctx, x64, mode, B.MUSR_SPLIT)
         t = time.perf_counter()
-        F.fit_context(ctx, mi.start_point(p, 100 + s), mode, B.MUSR_SPLIT)
-        lat_py.append(time.perf_counter() - t)
-    r64 = F.fit_context(ctx, mi.start_point(p, 100), mode, B.MUSR_FP64)
-    t = time.perf_counter()
-    sig = F.sigmas_context(ctx, r64["x"], mode)  # central differences of FP64 gradients (2P)
-    t_fd = time.perf_counter() - t
-    dev = float(np.max(np.abs(xs[0] - r64["x"]) / sig))
-    # Parameter errors from the fused Gauss-Newton matrix (one launch of P products).
-    for _ in range(2):
-        F.sigmas_gauss_newton(ctx, r64["x"], mode, B.MUSR_SPLIT)
-    t = time.perf_counter()
-    sig_gn = F.sigmas_gauss_newton(ctx, r64["x"], mode, B.MUSR_SPLIT)
-    t_gn = time.perf_counter() - t
-    t = time.perf_counter()
-    sig_gn64 = F.sigmas_gauss_newton(ctx, r64["x"], mode, B.MUSR_FP64)
-    t_gn64 = time.perf_counter() - t
-    errors = {"gauss_newton_split_ms": 1e3 * t_gn, "gauss_newton_fp64_ms": 1e3 * t_gn64,
-              "central_differences_fp64_ms": 1e3 * t_fd,
-              "max_rel_diff_sigma_gn_vs_fd": float(np.max(np.abs(sig_gn / sig - 1.0))),
-              "max_rel_diff_sigma_gn_split_vs_fp64": float(np.max(np.abs(sig_gn / sig_gn64 - 1.0)))}
-    return {"fits_per_s": len(lat) / sum(lat), "path": "musr_fit (C++ BFGS through the C ABI)",
-            "latency_ms_p50": 1e3 * float(np.median(lat)), "latency_ms_max": 1e3 * float(np.max(lat)),
-            "evals_per_fit": float(np.mean(nfev)), "python_bfgs_fits_per_s": len(lat_py) / sum(lat_py),
-            "max_param_dev_split_vs_fp64_sigma": dev, "fp64_fit_s": r64["time_s"], "parameter_errors": errors}
+        sig_gn = F.sigmas_gauss_newton(ctx, x64, mode, B.MUSR_SPLIT)
+        t_gn = time.perf_counter() - t
+        t = time.perf_counter()
+        sig_gn64 = F.sigmas_gauss_newton(ctx, x64, mode, B.MUSR_FP64)
+        t_gn64 = time.perf_counter() - t
+    out["parameter_errors"] = {"gauss_newton_split_ms": 1e3 * t_gn, "gauss_newton_fp64_ms": 1e3 * t_gn64,
+                               "central_differences_fp64_ms": 1e3 * t_fd,
+                               "max_rel_diff_sigma_gn_vs_fd": float(np.max(np.abs(sig_gn / sig - 1.0))),
+                               "max_rel_diff_sigma_gn_split_vs_fp64": float(np.max(np.abs(sig_gn / sig_gn64 - 1.0)))}
+    return out
 
 
-def _serving(B, n_requests, window=1024, seed=4):
-    """Serving: fits/s at saturation (closed loop, at most `window` in flight), then
-    Poisson arrivals at 0.5x and 0.9x that rate with p50/p99 latency (server clock,
-    submission to completion).  Requests draw from a pool of 32 seeded fits (H, B
-    log-uniform, theory from cfg1/cfg2/cfg3, truths jittered); SPLIT precision, -2lnL
-    or chi^2 at random."""
-    import threading
-
-    import musr_inputs as mi
-    pool = mi.serving_pool(32, seed=seed)
-    out = {"requests": n_requests, "pool": len(pool), "precision": "split",
-           "hbm_budget_gib": 8, "max_active": 1024}
-    with B.Server(hbm_budget_bytes=8 << 30, max_active=1024) as srv:
-        reqs = mi.request_stream(pool, n_requests, 0.0, seed=seed)
+def _saturation(B, reqs, precision, budget, window=1024):
+    """Closed loop (at most `window` fits in flight): fits/s, converged count, stats."""
+    with B.Server(hbm_budget_bytes=budget, max_active=1024) as srv:
         t = time.perf_counter()
-        pending = []
-        lat, statuses = [], []
+        pending, statuses = [], []
         i = 0
         while i < len(reqs) or pending:
             while i < len(reqs) and len(pending) < window:
                 r = reqs[i]
-                pending.append(srv.submit(r.problem, r.x0, r.mode, B.MUSR_SPLIT))
+                pending.append(srv.submit(r.problem, r.x0, r.mode, precision))
                 i += 1
             res = srv.wait(pending.pop(0))
             statuses.append(res["status"])
-            lat.append(res["t_done"] - res["t_submit"])
-        sat_s = time.perf_counter() - t
+        wall = time.perf_counter() - t
         st = srv.stats()
-    rate = n_requests / sat_s
-    out["saturation"] = {"fits_per_s": rate, "wall_s": sat_s, "converged": int(sum(s == 0 for s in statuses)),
-                         "gbins_per_s": st["bin_evals"] / sat_s / 1e9, "steps": st["steps"],
+    return len(reqs) / wall, wall, int(sum(s_ == 0 for s_ in statuses)), st
+
+
+def _serving(B, n_requests, window=1024, seed=4, pool_size=256):
+    """Serving: fits/s at saturation (closed loop, at most `window` in flight), then
+    Poisson arrivals at 0.5x and 0.9x that rate with p50/p99 latency (server clock,
+    submission to completion); the same saturation run for the FP64 path against SPLIT on
+    the first 1000 requests; saturation at smaller HBM budgets.  Requests draw from a pool
+    of 256 seeded fits (H, B log-uniform, theory from cfg1/cfg2/cfg3, truths jittered, each
+    fit its own event-level Monte Carlo), each request with its own start point and cost."""
+    import threading
+
+    import musr_inputs as mi
+    pool = mi.serving_pool(pool_size, seed=seed, workers=os.cpu_count() or 1)
+    out = {"requests": n_requests, "pool": len(pool), "precision": "split", "hbm_budget_gib": 8, "max_active": 1024}
+    reqs = mi.request_stream(pool, n_requests, 0.0, seed=seed)
+    rate, wall, conv, st = _saturation(B, reqs, B.MUSR_SPLIT, 8 << 30, window)
+    out["saturation"] = {"fits_per_s": rate, "wall_s": wall, "converged": conv,
+                         "gbins_per_s": st["bin_evals"] / wall / 1e9, "steps": st["steps"],
                          "launches": st["launches"], "evals": st["evals"],
                          "worker_s": {"busy": st["busy_s"], "minimizer": st["minimizer_s"],
                                       "admit": st["admit_s"], "device_wait": st["wait_s"]},
                          "configure_thread_s": {"context": st["cfg_create_s"], "upload": st["cfg_upload_s"],
                                                 "plan": st["cfg_plan_s"], "buffers": st["cfg_buffers_s"]}}
     for frac in (0.5, 0.9):
-        reqs = mi.request_stream(pool, n_requests, frac * rate, seed=seed + 10)
+        rq = mi.request_stream(pool, n_requests, frac * rate, seed=seed + 10)
         with B.Server(hbm_budget_bytes=8 << 30, max_active=1024) as srv:
-            ids = [None] * len(reqs)
+            ids = [None] * len(rq)
             t0 = time.perf_counter()
 
             def submitter():
-                for k, r in enumerate(reqs):
+                for k, r in enumerate(rq):
                     delay = r.arrival_s - (time.perf_counter() - t0)
                     if delay > 0:
                         time.sleep(delay)
@@ -682,7 +799,7 @@ def _serving(B, n_requests, window=1024, seed=4):
             th = threading.Thread(target=submitter)
             th.start()
             lat = []
-            for k in range(len(reqs)):
+            for k in range(len(rq)):
                 while ids[k] is None:
                     time.sleep(0.0005)
                 res = srv.wait(ids[k])
@@ -693,6 +810,18 @@ def _serving(B, n_requests, window=1024, seed=4):
         out[f"load_{frac}"] = {"rate_fits_per_s": frac * rate, "fits_per_s": n_requests / wall,
                                "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
                                "latency_ms_p99": 1e3 * float(np.percentile(lat, 99))}
+    # SPLIT against the plain FP64 path on the same 1000 requests (the FP64 path is far
+    # slower per evaluation, so the whole stream would take minutes)
+    sub = reqs[:min(1000, len(reqs))]
+    r32, w32, c32, _ = _saturation(B, sub, B.MUSR_SPLIT, 8 << 30, window)
+    r64, w64, c64, _ = _saturation(B, sub, B.MUSR_FP64, 8 << 30, window)
+    out["split_vs_fp64"] = {"requests": len(sub), "split_fits_per_s": r32, "fp64_fits_per_s": r64,
+                            "split_speedup": r32 / r64, "converged": [c32, c64]}
+    sweep = {}
+    for gib in (1, 2, 4):
+        rate_b, wall_b, conv_b, st_b = _saturation(B, reqs[:min(3000, len(reqs))], B.MUSR_SPLIT, gib << 30, window)
+        sweep[f"{gib}GiB"] = {"fits_per_s": rate_b, "converged": conv_b, "arena_bytes": int(st_b["arena_bytes"])}
+    out["hbm_budget_sweep"] = {"requests": min(3000, len(reqs)), **sweep}
     return out
 
 

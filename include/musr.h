@@ -49,7 +49,8 @@ typedef enum {
   MUSR_ENONFINITE = -4, /* -2lnL is +infinity: N <= 0 in a bin with d > 0 */
   MUSR_ETIMEOUT = -5,   /* a bounded wait ran out */
   MUSR_ESTATE = -6,     /* call order violated (e.g. eval before upload) */
-  MUSR_EAGAIN = -7      /* result not ready yet (serving poll) */
+  MUSR_EAGAIN = -7,     /* result not ready yet (serving poll) */
+  MUSR_ECANCELED = -8   /* a served fit was canceled (musr_server_cancel) */
 } musr_status;
 
 enum { MUSR_DTYPE_INT32 = 0, MUSR_DTYPE_FP32 = 1, MUSR_DTYPE_FP64 = 2 };
@@ -102,8 +103,9 @@ int musr_ctx_create(musr_ctx** out, int device, size_t hbm_budget_bytes, void* c
 /* Frees everything the context owns.  NULL is ignored. */
 void musr_ctx_destroy(musr_ctx* ctx);
 
-/* Text of the last error on this context ("" if none).  ctx may be NULL for
- * errors of musr_ctx_create.  The pointer stays valid until the next call. */
+/* Text of the last error on this context ("" if none).  ctx NULL: the last error
+ * of musr_ctx_create or musr_eval_noalloc on the calling thread.  The pointer stays
+ * valid until the next call. */
 const char* musr_last_error(const musr_ctx* ctx);
 
 /* Copies nhist histograms of nbins bins (host, row-major [nhist][nbins]) to
@@ -150,8 +152,13 @@ int musr_upload_histograms_device(musr_ctx* ctx, const void* d_counts, int dtype
                                   int64_t nbins, int64_t row_stride, const double* t0,
                                   double bin_width_ns, const double fit_range_us[2]);
 
-/* Sets A(t) as nterms (<= MUSR_MAX_TERMS) terms.  Every slot referenced must
- * be < the nslots given to musr_set_map. */
+/* Sets A(t) as nterms (<= MUSR_MAX_TERMS) terms (Section 4.1: Eq. asymmetry writes
+ * A(t) as an amplitude times relaxation and precession factors; the paper's fits take
+ * any "user defined function" of the parameters in its place, here any sum of up to
+ * four products of up to four of the primitives above).  terms is a host array, copied.
+ * Every slot referenced must be < the nslots given to musr_set_map.  MUSR_EINVAL for an
+ * unknown primitive, a slot out of range or more than four terms or primitives; the
+ * map must be set again after a new theory. */
 int musr_set_theory(musr_ctx* ctx, const musr_term* terms, int nterms);
 
 /* Sets the per-histogram parameter map (Section 4.1: the parameter set
@@ -285,7 +292,7 @@ typedef struct musr_fit_request {
 } musr_fit_request;
 
 typedef struct musr_server_stats {
-  int64_t submitted, completed, rejected;
+  int64_t submitted, completed, rejected, canceled;
   int64_t steps, launches, evals;
   int64_t active, queued;
   double bin_evals; /* (histogram, bin) pairs evaluated, summed over evaluations */
@@ -322,7 +329,18 @@ int musr_server_poll(musr_server* s, int64_t id, musr_fit_result* res, double* x
  * MUSR_ETIMEOUT if the fit is not done by then. */
 int musr_server_wait(musr_server* s, int64_t id, int timeout_ms, musr_fit_result* res, double* x_out);
 
-/* Counters of the server. */
+/* Asks fit `id` to stop.  A fit still queued ends at once without running; one being
+ * admitted or running ends at its next step boundary, when none of its work is on the
+ * device (its memory then goes back to the budget).  Either way its result, taken with
+ * musr_server_poll / musr_server_wait as usual, has status MUSR_ECANCELED and the point it
+ * had reached (x0 if it never ran).  Returns MUSR_OK when the fit was queued or running,
+ * MUSR_ESTATE when it had finished already (its result stands), MUSR_EINVAL for an id
+ * never issued or whose result was taken.  Thread-safe; it does not wait. */
+int musr_server_cancel(musr_server* s, int64_t id);
+
+/* Counters of the server.  completed counts fits that ran to an end of their own
+ * (converged or stopped by the minimiser, or a device error); canceled the fits ended by
+ * musr_server_cancel; rejected the fits refused at admission. */
 int musr_server_stats_get(musr_server* s, musr_server_stats* out);
 
 /* The paper has no counterpart to this entry point.
@@ -335,22 +353,33 @@ int musr_server_stats_get(musr_server* s, musr_server_stats* out);
  * create a musr_ctx (a context allocates), so everything comes from them:
  * d_counts [nhist][row_stride] FP32 or FP64 on the current device (16-byte
  * aligned, row_stride a multiple of 4), d_params [nparams] FP64 on the device,
- * d_out [1 + nparams] FP64 on the device (value, then gradient); t0, the fit
- * range, terms, map and consts are host arrays, read before the call returns.
- * Their meaning is that of musr_upload_histograms, musr_set_theory and
- * musr_set_map.  The call is asynchronous on cuda_stream (NULL: the legacy
- * default stream); an undefined likelihood writes +inf as the value.
+ * d_out [1 + nparams] FP64 on the device (value, then gradient); t0 [nhist], the
+ * fit range, terms [nterms], map [nhist][nslots] and consts [nconsts] are host
+ * arrays, read before the call returns.  Their meaning is that of
+ * musr_upload_histograms, musr_set_theory and musr_set_map, and every theory
+ * those accept runs here too (at MUSR_SPLIT, one without a basis form evaluates
+ * its term list per bin).  The call is asynchronous on cuda_stream (NULL: the
+ * legacy default stream).  Values written to d_out[0]: +inf where the likelihood
+ * is undefined; NaN when a staging wait inside the kernel ran out (the call has
+ * returned MUSR_OK by then: read the value before trusting the gradient).
  *
  * All scratch (work tables, partial sums, completion counters) lives in one
  * file-scope device array of MUSR_NOALLOC_SCRATCH_BYTES that every GPU which
- * loads the library holds until the process exits.  Limits: nhist <= 64,
+ * loads the library holds until the process exits; with lazy module loading
+ * the array is placed on a device at the first call there, so make that call
+ * before a memory pool reserves the rest of the device.  Limits: nhist <= 64,
  * nparams <= 1024, nconsts <= 256, at most 8192 work items, and the scratch
- * size; anything beyond returns MUSR_EINVAL without touching the GPU.  The
- * first call on a device looks up the array's device address (set-up): make
- * that first call before any stream capture.  Every call on a device uses the
- * same array and leaves its contents behind (the counters are cleared at the
- * start of each call): calls that overlap on the GPU race, so serialise them
- * (one stream, or an event between them). */
+ * size.  Every argument and limit check runs on the host before any CUDA call,
+ * except the work-item count and the scratch size, which depend on the
+ * device's SM count and are checked after the set-up below; every failure
+ * returns MUSR_EINVAL (or MUSR_ECUDA) with its reason in musr_last_error(NULL)
+ * on the calling thread, and enqueues nothing.  The first call on a device
+ * looks up the array's device address (set-up).  The tables are staged from a
+ * host buffer that each call overwrites, so a call on a stream that is
+ * capturing returns MUSR_EINVAL.  Every call on a device uses the same array
+ * and leaves its contents behind (the counters are cleared at the start of each
+ * call): calls that overlap on the GPU race, so serialise them (one stream, or
+ * an event between them). */
 #define MUSR_NOALLOC_SCRATCH_BYTES (8u << 20)
 int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int64_t nbins, int64_t row_stride,
                       const double* t0, double bin_width_ns, const double fit_range_us[2],
@@ -359,18 +388,23 @@ int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int64_t nbins,
                       int precision, int with_grad, double* d_out, void* cuda_stream);
 
 /* Self-check of the evaluation kernels' bounded waits (failure detection without a GPU
- * fault).  Each staging wait of the SPLIT kernels waits on a shared-memory mbarrier with an
- * iteration limit.  If a copy never lands, the wait gives up, the CTA records an error and
- * the evaluation returns MUSR_ETIMEOUT; nothing faults, traps or hangs.  This call runs one
- * CTA on `device` that performs that wait on a barrier nothing arrives on. The wait must give
- * up. Then the CTA arrives on the barrier itself, and the same wait must see the completed
- * phase.
+ * fault; no counterpart in the paper).  Each staging wait of the SPLIT kernels waits on a
+ * shared-memory mbarrier for at most 100 ms of the GPU's global timer.  If a copy never
+ * lands, the wait gives up, the CTA records an error and the evaluation returns
+ * MUSR_ETIMEOUT; nothing faults, traps or hangs.  This call runs one CTA on `device` that
+ * performs that wait on a barrier nothing arrives on.  The wait must give up.  Then the CTA
+ * arrives on the barrier itself, and the same wait must see the completed phase.
  * out_try_s: seconds per unsatisfied try (nullable); out_wait_s: seconds until the wait gave
- * up, or -1 when its limit would take longer than 5 s at the measured rate and it was not run
- * (nullable).
+ * up (about 0.1), or -1 when it was not run (nullable).
  * Returns MUSR_OK when the wait gave up and the completed phase was seen; MUSR_ESTATE when
  * any of that failed or the wait was not run; MUSR_EINVAL for a bad device; MUSR_ECUDA. */
 int musr_check_bounded_wait(int device, double* out_try_s, double* out_wait_s);
+
+/* The compute capability the library's kernels were compiled for, as the CUDA runtime
+ * reports it for the code loaded on `device` (cudaFuncAttributes::binaryVersion: 103 for
+ * sm_103a).  No counterpart in the paper: a build check.  MUSR_EINVAL for a bad device or a
+ * NULL out; MUSR_ECUDA if the runtime cannot load the code for the device. */
+int musr_binary_version(int device, int* out);
 
 /* ---------------------------------------------------------------------------
  * The particle-mesh Poisson solve of Section 3 ("FFT Based Particle-Mesh

@@ -485,17 +485,26 @@ class Request:
     mode: int  # 0 chi^2, 1 -2lnL
 
 
+def _pool_member(spec) -> Problem:
+    kind, H, B, dtw, n0, sub, jit, dtype = spec
+    if kind == 0:
+        return cfg1(nbins=B, bin_width_ns=dtw, seed=sub, dtype=dtype, n0=n0, jitter_seed=jit)
+    if kind == 1:
+        return cfg2(nhist=H, nbins=B, bin_width_ns=dtw, seed=sub, dtype=dtype, n0=n0, jitter_seed=jit)
+    return cfg3(nhist=H, nbins=B, bin_width_ns=dtw, seed=sub, dtype=dtype, n0=n0, jitter_seed=jit)
+
+
 def serving_pool(n_pool: int, seed: int = 4, hist_range=(1, 64), bin_range=(4096, 262144),
-                 span_ns: float = 12800.0,
-                 dtype=np.float32) -> List[Problem]:
+                 span_ns: float = 12800.0, dtype=np.float32, workers: int = 1) -> List[Problem]:
     """A pool of distinct fits: H ~ logU(hist_range), B ~ logU(bin_range), theory drawn from
-    cfg1/cfg2/cfg3, truths jittered by U(0.8, 1.2).
+    cfg1/cfg2/cfg3, truths jittered by U(0.8, 1.2), each fit its own seeded Monte Carlo.
 
     N0 is scaled by min(1, 4096 / B) so that every histogram holds about the same
-    number of events whatever its binning (a fixed-length run binned finer).
+    number of events whatever its binning (a fixed-length run binned finer).  With
+    workers > 1 the fits are simulated by that many spawned processes (the same fits).
     """
     rng = np.random.default_rng(seed)
-    pool = []
+    specs = []
     for i in range(n_pool):
         H = int(round(math.exp(rng.uniform(math.log(hist_range[0]), math.log(hist_range[1])))))
         B = int(round(math.exp(rng.uniform(math.log(bin_range[0]), math.log(bin_range[1])))))
@@ -504,14 +513,12 @@ def serving_pool(n_pool: int, seed: int = 4, hist_range=(1, 64), bin_range=(4096
         n0 = 300.0 * min(1.0, 4096.0 / B)
         sub = int(rng.integers(0, 2**31))
         jit = int(rng.integers(0, 2**31))
-        if kind == 0:
-            p = cfg1(nbins=B, bin_width_ns=dtw, seed=sub, dtype=dtype, n0=n0, jitter_seed=jit)
-        elif kind == 1:
-            p = cfg2(nhist=H, nbins=B, bin_width_ns=dtw, seed=sub, dtype=dtype, n0=n0, jitter_seed=jit)
-        else:
-            p = cfg3(nhist=H, nbins=B, bin_width_ns=dtw, seed=sub, dtype=dtype, n0=n0, jitter_seed=jit)
-        pool.append(p)
-    return pool
+        specs.append((kind, H, B, dtw, n0, sub, jit, dtype))
+    if workers > 1 and n_pool > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(workers, n_pool)) as pool:
+            return pool.map(_pool_member, specs, chunksize=1)
+    return [_pool_member(sp) for sp in specs]
 
 
 def request_stream(pool: Sequence[Problem], n_requests: int, rate_per_s: float, seed: int = 4,

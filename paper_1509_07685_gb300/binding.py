@@ -18,7 +18,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libmusr.so")
 
 MUSR_OK, MUSR_EINVAL, MUSR_ENOMEM, MUSR_ECUDA = 0, -1, -2, -3
-MUSR_ENONFINITE, MUSR_ETIMEOUT, MUSR_ESTATE, MUSR_EAGAIN = -4, -5, -6, -7
+MUSR_ENONFINITE, MUSR_ETIMEOUT, MUSR_ESTATE, MUSR_EAGAIN, MUSR_ECANCELED = -4, -5, -6, -7, -8
 MUSR_DTYPE_INT32, MUSR_DTYPE_FP32, MUSR_DTYPE_FP64 = 0, 1, 2
 MUSR_REQ_BORROW_COUNTS = 1  # musr_fit_request.flags: the server reads the caller's counts at admission
 MUSR_CHI2, MUSR_MLE = 0, 1
@@ -32,9 +32,9 @@ EXPORTS = (
     "musr_upload_asymmetry", "musr_upload_histograms_device", "musr_set_theory", "musr_set_map", "musr_eval",
     "musr_eval_batch", "musr_eval_device", "musr_sync", "musr_bins_in_fit", "musr_gn_product",
     "musr_gauss_newton",
-    "musr_launches_per_eval", "musr_eval_noalloc", "musr_check_bounded_wait", "musr_fit", "musr_server_create",
+    "musr_launches_per_eval", "musr_eval_noalloc", "musr_check_bounded_wait", "musr_binary_version", "musr_fit", "musr_server_create",
     "musr_server_destroy", "musr_server_submit", "musr_server_poll", "musr_server_wait",
-    "musr_server_stats_get", "musr_poisson_create", "musr_poisson_destroy", "musr_poisson_last_error",
+    "musr_server_cancel", "musr_server_stats_get", "musr_poisson_create", "musr_poisson_destroy", "musr_poisson_last_error",
     "musr_poisson_solve", "musr_poisson_solve_device",
 )
 
@@ -70,7 +70,7 @@ class musr_fit_request(ctypes.Structure):
 
 class musr_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
-                ("steps", ctypes.c_int64), ("launches", ctypes.c_int64), ("evals", ctypes.c_int64),
+                ("canceled", ctypes.c_int64), ("steps", ctypes.c_int64), ("launches", ctypes.c_int64), ("evals", ctypes.c_int64),
                 ("active", ctypes.c_int64), ("queued", ctypes.c_int64), ("bin_evals", ctypes.c_double),
                 ("busy_s", ctypes.c_double), ("clock_s", ctypes.c_double), ("arena_bytes", ctypes.c_uint64),
                 ("arena_used", ctypes.c_uint64), ("minimizer_s", ctypes.c_double), ("admit_s", ctypes.c_double),
@@ -117,6 +117,7 @@ def _declare(lib):
                                ctypes.c_int, P(i32), ctypes.c_int, ctypes.c_int, P(d), ctypes.c_int, vp,
                                ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
         "musr_check_bounded_wait": ([ctypes.c_int, P(d), P(d)], ctypes.c_int),
+        "musr_binary_version": ([ctypes.c_int, P(ctypes.c_int)], ctypes.c_int),
         "musr_fit": ([vp, P(d), ctypes.c_int, ctypes.c_int, ctypes.c_int, d, P(d), P(musr_fit_result)],
                      ctypes.c_int),
         "musr_server_create": ([P(vp), ctypes.c_int, ctypes.c_size_t, ctypes.c_int], ctypes.c_int),
@@ -124,6 +125,7 @@ def _declare(lib):
         "musr_server_submit": ([vp, P(musr_fit_request), P(i64)], ctypes.c_int),
         "musr_server_poll": ([vp, i64, P(musr_fit_result), P(d)], ctypes.c_int),
         "musr_server_wait": ([vp, i64, ctypes.c_int, P(musr_fit_result), P(d)], ctypes.c_int),
+        "musr_server_cancel": ([vp, i64], ctypes.c_int),
         "musr_server_stats_get": ([vp, P(musr_server_stats)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -343,6 +345,9 @@ def musr_eval_noalloc(d_counts: int, dtype: int, nhist: int, nbins: int, row_str
     fr = np.ascontiguousarray(fit_range_us, dtype=np.float64)
     arr, n = terms_to_c(terms)
     mp = np.ascontiguousarray(mp, dtype=np.int32)
+    # the library reads map[nhist][nslots], t0[nhist] and the fit range's two ends
+    if mp.ndim != 2 or mp.shape[0] != nhist or t0.shape != (nhist,) or fr.shape != (2,):
+        raise ValueError("musr_eval_noalloc: map must be [nhist][nslots], t0 [nhist], fit_range_us [2]")
     c = np.ascontiguousarray(consts if len(consts) else np.zeros(1), dtype=np.float64)
     stream = None if not cuda_stream else ctypes.c_void_p(cuda_stream)
     return load().musr_eval_noalloc(ctypes.c_void_p(d_counts), dtype, nhist, nbins, row_stride, _dptr(t0),
@@ -350,6 +355,13 @@ def musr_eval_noalloc(d_counts: int, dtype: int, nhist: int, nbins: int, row_str
                                     mp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), mp.shape[1],
                                     int(nparams), _dptr(c), len(consts), ctypes.c_void_p(d_params), mode,
                                     precision, int(bool(with_grad)), ctypes.c_void_p(d_out), stream)
+
+
+def musr_binary_version(device: int = 0):
+    """(status, compute capability the loaded kernels were built for: 103 for sm_103a)."""
+    out = ctypes.c_int(-1)
+    st = load().musr_binary_version(int(device), ctypes.byref(out))
+    return st, out.value
 
 
 def musr_check_bounded_wait(device: int = 0):
@@ -517,6 +529,11 @@ def musr_server_wait(srv, fid: int, nparams: int, timeout_ms: int = 0):
     return _result_dict(r, x)
 
 
+def musr_server_cancel(srv, fid: int) -> int:
+    """Asks fit `fid` to stop; returns the status (MUSR_OK, MUSR_ESTATE if it had finished)."""
+    return load().musr_server_cancel(srv, int(fid))
+
+
 def musr_server_stats_get(srv) -> dict:
     s = musr_server_stats()
     st = load().musr_server_stats_get(srv, ctypes.byref(s))
@@ -555,6 +572,11 @@ class Server:
             self.nparams.pop(fid, None)
             self.lent.pop(fid, None)
         return r
+
+    def cancel(self, fid: int) -> int:
+        """Asks fit `fid` to stop (its result, taken with poll / wait, has status
+        MUSR_ECANCELED); returns the status of the request."""
+        return musr_server_cancel(self.srv, fid)
 
     def stats(self) -> dict:
         return musr_server_stats_get(self.srv)

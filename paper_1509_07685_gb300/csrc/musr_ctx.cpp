@@ -41,6 +41,8 @@ int fail(musr_ctx* ctx, int code, const std::string& msg) {
   return code;
 }
 
+void set_thread_error(const std::string& msg) { g_create_error = msg; }
+
 int cuda_fail(musr_ctx* ctx, cudaError_t e, const char* what) {
   return fail(ctx, MUSR_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }

@@ -81,6 +81,8 @@ class DeviceScope {
 };
 
 int fail(musr_ctx* ctx, int code, const std::string& msg);
+// The calling thread's error text for calls without a context (musr_last_error(NULL)).
+void set_thread_error(const std::string& msg);
 int cuda_fail(musr_ctx* ctx, cudaError_t e, const char* what);
 int dalloc(musr_ctx* ctx, DevBuf& b, size_t bytes);
 void dfree(musr_ctx* ctx, DevBuf& b);

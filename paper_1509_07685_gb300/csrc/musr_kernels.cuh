@@ -118,10 +118,26 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "memory");
   return ok != 0;
 }
-// Waits for phase `parity` of the barrier; false when the iteration limit ran out.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Limit of every wait on a staging barrier: a copy of at most 8 x 4 KiB that has not landed
+// after this long never will.  The limit is on the global timer; a cap on the number of tries
+// (2^24, tens of seconds at the suspend time of an unsatisfied try) bounds the wait even if
+// that timer stood still.
+constexpr unsigned long long kWaitLimitNs = 100000000ull;  // 100 ms
+// Waits for phase `parity` of the barrier; false when the limit ran out.
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-  for (int i = 0; i < (1 << 20); ++i)
-    if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (int i = 0; i < (1 << 18); ++i) {
+#pragma unroll 1
+    for (int k = 0; k < 64; ++k)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  }
   return false;
 }
 

@@ -11,14 +11,24 @@
 // decomposition tables, per-item partial rows, per-chunk sums, completion
 // counters -- in one file-scope __device__ array of fixed size.
 //
-// The work decomposition is built exactly as a context builds it for a single
-// evaluation, so the result equals musr_eval's for the same inputs.
+// The work decomposition is built as a context builds it for a single evaluation (the
+// same grouping of histograms, the same tiles, the same kernels), so for histograms on one
+// time grid the result equals musr_eval's for the same inputs and device.  A context also
+// moves histograms whose time zeros differ by whole bins onto one grid at upload; the
+// borrowed rows here stay as they are, so such histograms form chunks of their own and
+// the sums run in another order (equal within the precision's tolerance).
+//
+// The tables are staged in a host buffer that every call overwrites, and copied from
+// there on the caller's stream.  A copy recorded into a CUDA graph would read that
+// buffer when the graph is replayed, by then holding another call's tables, so a call
+// on a stream that is capturing is refused.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <string>
 
 #include "musr.h"
 #include "musr_dev.h"
@@ -60,8 +70,15 @@ Tables g_tab;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Rejections return MUSR_EINVAL; the message names the check for readers of this file.
-constexpr int na_fail(const char* /*why*/) { return MUSR_EINVAL; }
+// Rejections return MUSR_EINVAL and leave the reason for musr_last_error(NULL).
+int na_fail(const char* why) {
+  set_thread_error(std::string("musr_eval_noalloc: ") + why);
+  return MUSR_EINVAL;
+}
+int na_cuda(cudaError_t e, const char* what) {
+  set_thread_error(std::string("musr_eval_noalloc: ") + what + ": " + cudaGetErrorString(e));
+  return MUSR_ECUDA;
+}
 
 int64_t tiles_total(const Chunk* ch, int n, int64_t T) {
   int64_t s = 0;
@@ -110,22 +127,9 @@ extern "C" int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int
   for (int h = 0; h < nhist; ++h)
     if (!std::isfinite(t0[h])) return na_fail("t0 must be finite");
 
+  set_thread_error("");
   std::lock_guard<std::mutex> lock(g_mutex);
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return na_fail("no current CUDA device");
-  // ---- set-up, once per device, with that device current
-  if (!g_scratch_ptr[dev]) {
-    void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess || !ptr) return MUSR_ECUDA;  // set-up failed: the scratch has no device address
-    g_scratch_ptr[dev] = ptr;
-  }
-  unsigned char* scratch = static_cast<unsigned char*>(g_scratch_ptr[dev]);
-  int num_sms = 1;
-  cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-
-  // ---- tables (same decomposition as a context's single evaluation)
+  // ---- tables (same decomposition as a context's single evaluation); host work only
   Tables& T = g_tab;
   HistSet& hs = T.hs;
   std::memset(&hs, 0, sizeof(hs));
@@ -150,18 +154,34 @@ extern "C" int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int
   int group_of[kNaMaxHist];
   int ngroups = 0;
   int group_cap = 1;
-  if (precision == MUSR_SPLIT) {
-    if (plan_split(terms, nterms, map, nhist, nslots, consts, &hs))
-      return na_fail("SPLIT precision needs every term to hold at most one AMP, and at most one of KT or TFCOS");
+  // Theories without a basis form evaluate their term list per bin in FP32 (one histogram
+  // per chunk), as a context does.
+  const bool basis = precision == MUSR_SPLIT && !plan_split(terms, nterms, map, nhist, nslots, consts, &hs);
+  if (precision == MUSR_SPLIT && !basis) {
+    bool small = nterms <= 2;
+    for (int k = 0; k < nterms; ++k) small = small && terms[k].nprim <= 3;
+    hs.shape = small ? kShapeListS : kShapeList;
+  }
+  if (basis) {
     group_cap = shape_group(hs.shape);
-    // Group histograms sharing t0 and every time-dependent parameter (first appearance order).
-    int64_t keys[kNaMaxHist][2 + 2 * MUSR_MAX_TERMS * 10];
+    // Group histograms sharing t0 (to 2^-24 bins), the fit window and every time-dependent
+    // parameter, in order of first appearance: the key a context builds.
+    int64_t keys[kNaMaxHist][6 + 2 * MUSR_MAX_TERMS * 10];
     int keylen[kNaMaxHist];
     for (int h = 0; h < nhist; ++h) {
       int n = 0;
-      int64_t tb;
-      std::memcpy(&tb, &t0[h], sizeof(tb));
-      keys[h][n++] = tb;
+      const double q = std::nearbyint(t0[h] * 16777216.0);
+      if (std::fabs(q) < 4e18) {
+        keys[h][n++] = 0;
+        keys[h][n++] = static_cast<int64_t>(q);
+      } else {
+        int64_t tb;
+        std::memcpy(&tb, &t0[h], sizeof(tb));
+        keys[h][n++] = 1;
+        keys[h][n++] = tb;
+      }
+      keys[h][n++] = nlo[h];
+      keys[h][n++] = nhi[h];
       auto push = [&](int s) {
         const int32_t m = map[h * nslots + s];
         if (m >= 0) {
@@ -215,9 +235,34 @@ extern "C" int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int
       ch.tile0 = ch.nlo & ~3;
     }
   }
+  // ---- device set-up: once per device, with that device current (the first call on a
+  // device looks up the scratch array's address; with lazy module loading, that is also
+  // when the library's module, and with it the array, is loaded onto the device)
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(stream, &cap);
+  if (e != cudaSuccess) return na_cuda(e, "cudaStreamIsCapturing");
+  if (cap != cudaStreamCaptureStatusNone)
+    return na_fail("cuda_stream is capturing: the tables are staged in a host buffer that later calls "
+                   "overwrite, so a recorded copy would read another call's tables");
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return na_cuda(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return na_fail("device index beyond 63");
+  if (!g_scratch_ptr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) return na_cuda(e, "cudaGetSymbolAddress(scratch)");
+    g_scratch_ptr[dev] = ptr;
+  }
+  unsigned char* scratch = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+  int num_sms = 1;
+  e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return na_cuda(e, "cudaDeviceGetAttribute");
+
   if (nchunks == 0) {  // no bin in the fit range
-    e = cudaMemsetAsync(d_out, 0, sizeof(double) * (1 + nparams), static_cast<cudaStream_t>(cuda_stream));
-    return e == cudaSuccess ? MUSR_OK : MUSR_ECUDA;
+    e = cudaMemsetAsync(d_out, 0, sizeof(double) * (1 + nparams), stream);
+    return e == cudaSuccess ? MUSR_OK : na_cuda(e, "cudaMemsetAsync(out)");
   }
   // The decomposition a context picks for one evaluation.
   int items_per_var[kVariants];
@@ -302,15 +347,14 @@ extern "C" int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int
   job.grad = with_grad ? 1 : 0;
   job.prec = precision;
 
-  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   // Pageable source: the copy has consumed the staging buffer when the call returns.
   e = cudaMemcpyAsync(d_tab, &T, sizeof(Tables), cudaMemcpyHostToDevice, stream);
-  if (e != cudaSuccess) return MUSR_ECUDA;
+  if (e != cudaSuccess) return na_cuda(e, "cudaMemcpyAsync(tables)");
   // The completion counters must start at zero; the previous call's values stay otherwise.
   e = cudaMemsetAsync(d_zero, 0, sizeof(unsigned) * (nchunks + 1), stream);
-  if (e != cudaSuccess) return MUSR_ECUDA;
+  if (e != cudaSuccess) return na_cuda(e, "cudaMemsetAsync(counters)");
   LaunchInfo info;
   if (launch_eval(precision, hs.shape, mode, job.grad, &dT->job, 1, nitems, num_sms, cuda_stream, &info))
-    return MUSR_ECUDA;
+    return na_cuda(cudaGetLastError(), "kernel launch");
   return MUSR_OK;
 }

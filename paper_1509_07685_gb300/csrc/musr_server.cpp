@@ -35,6 +35,7 @@
 #include <string>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "musr.h"
@@ -195,6 +196,8 @@ struct musr_server {
   bool stop = false;
   std::deque<std::unique_ptr<Request>> queue;
   std::unordered_map<int64_t, Done> done;
+  std::unordered_set<int64_t> live;    // submitted, not finished (queued, being admitted or active)
+  std::unordered_set<int64_t> cancel;  // live fits asked to stop that the worker has not ended yet
   int64_t next_id = 1;
   std::chrono::steady_clock::time_point t0;
   musr_server_stats stats{};
@@ -259,12 +262,15 @@ void finish(musr_server* s, Active* a, int status) {
   a->ctx = nullptr;
   std::lock_guard<std::mutex> lock(s->mu);
   s->done[a->req->id] = std::move(d);
+  s->live.erase(a->req->id);
+  s->cancel.erase(a->req->id);
   s->stats.completed += 1;
   s->stats.active -= 1;
   s->cv_done.notify_all();
 }
 
-void reject(musr_server* s, std::unique_ptr<Request> r, int status) {
+// Ends a fit that never ran (refused, or canceled before it ran); s->mu held.
+void reject_locked(musr_server* s, std::unique_ptr<Request> r, int status) {
   Done d;
   d.res.status = status;
   d.res.nparams = r->P;
@@ -272,10 +278,19 @@ void reject(musr_server* s, std::unique_ptr<Request> r, int status) {
   d.res.t_submit = r->t_submit;
   d.res.t_done = s->now();
   d.x = r->x0;
-  std::lock_guard<std::mutex> lock(s->mu);
   s->done[r->id] = std::move(d);
-  s->stats.rejected += 1;
+  s->live.erase(r->id);
+  s->cancel.erase(r->id);
+  if (status == MUSR_ECANCELED)
+    s->stats.canceled += 1;
+  else
+    s->stats.rejected += 1;
   s->cv_done.notify_all();
+}
+
+void reject(musr_server* s, std::unique_ptr<Request> r, int status) {
+  std::lock_guard<std::mutex> lock(s->mu);
+  reject_locked(s, std::move(r), status);
 }
 
 // Configures a context for the request inside the arena; MUSR_ENOMEM when the
@@ -408,6 +423,16 @@ void admit(musr_server* s, bool during_step = false) {
         reject(s, std::move(batch[i]), rcs[i]);
         continue;
       }
+      bool canceled;
+      {
+        std::lock_guard<std::mutex> lock(s->mu);
+        canceled = s->cancel.count(batch[i]->id) > 0;
+      }
+      if (canceled) {  // canceled while it was configured: its setup was waited for
+        release(ctxs[i]);
+        reject(s, std::move(batch[i]), MUSR_ECANCELED);
+        continue;
+      }
       activate(s, std::move(batch[i]), ctxs[i]);
     }
   }
@@ -418,6 +443,34 @@ void admit(musr_server* s, bool during_step = false) {
 // other lane has in flight; the results come back to the lane's pinned buffer.
 int launch_lane(musr_server* s, int L) {
   Lane& lane = s->lanes[L];
+  // Fits of lane L asked to stop end here: lane L's last results were delivered in the
+  // previous half-step, so none of their work is on the device.
+  bool any_cancel;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    any_cancel = !s->cancel.empty();
+  }
+  if (any_cancel) {
+    std::vector<Active*> stop;
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      for (auto& a : s->active)
+        if (a->lane == L && s->cancel.count(a->req->id)) stop.push_back(a.get());
+    }
+    if (!stop.empty()) {
+      for (Active* a : stop) {
+        lane.load -= a->load;
+        finish(s, a, MUSR_ECANCELED);
+      }
+      std::lock_guard<std::mutex> lock(s->mu);
+      s->stats.canceled += static_cast<int64_t>(stop.size());
+      s->stats.completed -= static_cast<int64_t>(stop.size());
+      std::vector<std::unique_ptr<Active>> keep;
+      for (auto& a : s->active)
+        if (a->ctx) keep.push_back(std::move(a));
+      s->active.swap(keep);
+    }
+  }
   std::vector<Active*> fits;
   for (auto& a : s->active)
     if (a->lane == L) fits.push_back(a.get());
@@ -728,6 +781,7 @@ int musr_server_submit(musr_server* s, const musr_fit_request* req, int64_t* out
   r->id = s->next_id++;
   r->t_submit = s->now();
   *out_id = r->id;
+  s->live.insert(r->id);
   s->queue.push_back(std::move(r));
   s->stats.submitted += 1;
   s->stats.queued += 1;
@@ -762,6 +816,26 @@ int musr_server_wait(musr_server* s, int64_t id, int timeout_ms, musr_fit_result
     s->cv_done.wait(lock, ready);
   }
   return take_result(s, id, res, x_out);
+}
+
+int musr_server_cancel(musr_server* s, int64_t id) {
+  if (!s || id <= 0) return MUSR_EINVAL;
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (id >= s->next_id) return MUSR_EINVAL;
+  if (s->done.count(id)) return MUSR_ESTATE;  // finished: its result stands
+  if (!s->live.count(id)) return MUSR_EINVAL;  // its result was taken already
+  for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+    if ((*it)->id == id) {  // still queued: ends now, without running
+      std::unique_ptr<Request> r = std::move(*it);
+      s->queue.erase(it);
+      s->stats.queued -= 1;
+      reject_locked(s, std::move(r), MUSR_ECANCELED);
+      return MUSR_OK;
+    }
+  // being admitted or active: the worker ends it at its next step boundary
+  s->cancel.insert(id);
+  s->cv_work.notify_one();
+  return MUSR_OK;
 }
 
 int musr_server_stats_get(musr_server* s, musr_server_stats* out) {

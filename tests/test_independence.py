@@ -71,7 +71,7 @@ def test_input_generators_import_neither_side():
 def test_bench_imports_the_oracle_only_inside_its_cpu_legs():
     path = os.path.join(ROOT, "bench.py")
     tree = ast.parse(open(path).read(), path)
-    allowed = {"run_reference", "_pool_init", "_oracle_one", "_oracle_worker", "cpu_baseline", "config_sweep",
+    allowed = {"run_reference", "_pool_init", "_oracle_task", "_oracle_worker", "cpu_baseline", "config_sweep",
                "precision_report", "_poisson"}  # _poisson: its direct-sum CPU baseline
     for node in tree.body:  # module level
         if isinstance(node, (ast.Import, ast.ImportFrom)):

@@ -108,3 +108,67 @@ def test_noalloc_at_its_limits_matches_oracle(musr_lib):
             assert ref[3] == 0
             check(out[0], out[1:], ref)
             assert np.all(out[1 + P0:1 + P0 + 12 * H] == 0.0) and np.all(out[1 + P0 + 12 * H:] == 0.0)
+
+
+def test_noalloc_term_list_without_basis_form_matches_context(musr_lib):
+    """A theory without a basis form (a stretched exponential) at SPLIT precision: the entry
+    point evaluates the term list per bin, as a context does, and matches it."""
+    import torch
+
+    from paper_1509_07685_gb300 import binding as B
+    p = mi.levy_lf(nhist=2, nbins=1600, bin_width_ns=8.0, seed=66)
+    stride = (p.B + 3) // 4 * 4
+    d_counts = torch.zeros((p.H, stride), dtype=torch.float32, device="cuda")
+    d_counts[:, :p.B] = torch.from_numpy(np.ascontiguousarray(p.counts, dtype=np.float32)).cuda()
+    stream = torch.cuda.current_stream().cuda_stream
+    with B.Context(p) as ctx:
+        for mode in (B.MUSR_CHI2, B.MUSR_MLE):
+            for seed in (1, 2):  # two calls in a row
+                x = mi.start_point(p, seed)
+                d_x = torch.tensor(x, dtype=torch.float64, device="cuda")
+                d_out = torch.full((1 + p.nparams,), float("nan"), dtype=torch.float64, device="cuda")
+                st = B.musr_eval_noalloc(d_counts.data_ptr(), B.MUSR_DTYPE_FP32, p.H, p.B, stride, p.t0,
+                                         p.bin_width_ns, p.fit_range_us, p.terms, p.map, p.nparams, p.consts,
+                                         d_x.data_ptr(), mode, B.MUSR_SPLIT, True, d_out.data_ptr(), stream)
+                assert st == B.MUSR_OK, B.musr_last_error(None)
+                torch.cuda.synchronize()
+                out = d_out.cpu().numpy()
+                v, g, _ = ctx.eval(x, mode, B.MUSR_SPLIT)
+                gs = oracle.cost(p, x, mode)[2]
+                assert abs(out[0] - v) <= SPLIT_EPS * abs(v)
+                assert np.all(np.abs(out[1:] - g) <= SPLIT_EPS * gs + 1e-300)
+
+
+def test_noalloc_refuses_a_capturing_stream_and_names_its_reasons(musr_lib):
+    """The tables are staged from a host buffer that later calls overwrite, so a call on a
+    stream that is capturing returns MUSR_EINVAL and enqueues nothing; every refusal leaves
+    its reason for musr_last_error(NULL).  The scratch still works afterwards."""
+    import torch
+
+    from paper_1509_07685_gb300 import binding as B
+    p = mi.cfg3(nhist=2, nbins=2048, bin_width_ns=6.0, seed=67)
+    stride = (p.B + 3) // 4 * 4
+    d_counts = torch.zeros((p.H, stride), dtype=torch.float32, device="cuda")
+    d_counts[:, :p.B] = torch.from_numpy(np.ascontiguousarray(p.counts, dtype=np.float32)).cuda()
+    x = mi.start_point(p, 3)
+    d_x = torch.tensor(x, dtype=torch.float64, device="cuda")
+    d_out = torch.full((1 + p.nparams,), float("nan"), dtype=torch.float64, device="cuda")
+    args = lambda stream: (d_counts.data_ptr(), B.MUSR_DTYPE_FP32, p.H, p.B, stride, p.t0, p.bin_width_ns,
+                           p.fit_range_us, p.terms, p.map, p.nparams, p.consts, d_x.data_ptr(), 0,
+                           B.MUSR_FP64, True, d_out.data_ptr(), stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        st = B.musr_eval_noalloc(*args(torch.cuda.current_stream().cuda_stream))
+        msg = B.musr_last_error(None)
+    assert st == B.MUSR_EINVAL and "capturing" in msg
+    bad = list(args(None))
+    bad[4] = stride + 2  # row stride not a multiple of 4
+    assert B.musr_eval_noalloc(*bad) == B.MUSR_EINVAL
+    assert "row_stride" in B.musr_last_error(None)
+    st = B.musr_eval_noalloc(*args(torch.cuda.current_stream().cuda_stream))
+    assert st == B.MUSR_OK and B.musr_last_error(None) == ""
+    torch.cuda.synchronize()
+    ref = oracle.cost(p, x, 0)
+    out = d_out.cpu().numpy()
+    assert abs(out[0] - ref[0]) <= FP64_TOL * abs(ref[0])
