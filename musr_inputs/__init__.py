@@ -11,6 +11,9 @@ Monte Carlo of a muSR run (Section 4.1 describes the experiment):
     ensemble dephases; zero-field (ZF) components draw a 3-D static field
     b ~ N(0, Delta^2 I) and the spin component along the initial polarisation
     follows (b_z^2 + (b_x^2 + b_y^2) cos(|b| t)) / |b|^2;
+  * dynamic zero-field (DZF) components draw such a field anew at the events of a
+    Poisson process of rate nu (strong collisions); between events the spin vector
+    precesses about the current field (a rotation by |b| times the interval);
   * a component with rate lambda loses its polarisation at an
     Exponential(1/lambda) time;
   * the positron is counted by detector j with probability
@@ -88,7 +91,8 @@ class Component:
     """One physical signal component of the simulated run."""
 
     amp: float
-    # "TF", "ZF" (static Gaussian fields), "ZFL" (static Lorentzian fields), "INC" (fields of an
+    # "TF", "ZF" (static Gaussian fields), "ZFL" (static Lorentzian fields), "DZF" (Gaussian
+    # fields drawn anew at the events of a Poisson process of rate nu_c), "INC" (fields of an
     # incommensurate structure, gamma B = 2 pi nu cos(U), U uniform) or "LF" (no precession)
     kind: str = "TF"
     nu_mhz: float = 0.0
@@ -96,6 +100,7 @@ class Component:
     lam: float = 0.0  # depolarisation rate, 1/us
     delta: float = 0.0  # ZF / ZFL static field width, 1/us
     levy: float = 0.0  # depolarisation at a rate r = levy / (2 Z^2), Z ~ N(0, 1) per muon, 1/us
+    nu_c: float = 0.0  # DZF: rate of the field's renewals, 1/us
 
 
 @dataclasses.dataclass
@@ -151,6 +156,8 @@ def simulate_histogram(rng: np.random.Generator, det: Detector, comps: Sequence[
                 b2 = np.einsum("ij,ij->i", b, b)
                 bt2 = b[:, 0] ** 2 + b[:, 1] ** 2
                 sk = (b[:, 2] ** 2 + bt2 * np.cos(np.sqrt(b2) * tk)) / np.maximum(b2, 1e-300)
+            elif c.kind == "DZF":
+                sk = _dynamic_spin_z(rng, tk, c.delta, c.nu_c)
             else:
                 raise ValueError(c.kind)
             if c.lam > 0:
@@ -169,6 +176,33 @@ def simulate_histogram(rng: np.random.Generator, det: Detector, comps: Sequence[
     if det.nbkg > 0:
         counts += rng.poisson(det.nbkg, nbins)
     return counts
+
+
+def _dynamic_spin_z(rng: np.random.Generator, t: np.ndarray, delta: float, nu_c: float) -> np.ndarray:
+    """Spin component along the initial polarisation (z) at times t of muons whose local
+    field, drawn from N(0, delta^2 I) (in units of gamma_mu), is drawn anew at the events of
+    a Poisson process of rate nu_c: the spin vector is rotated about each interval's field by
+    |b| times the interval's length (Rodrigues' formula)."""
+    m = t.size
+    S = np.zeros((m, 3))
+    S[:, 2] = 1.0
+    left = t.astype(np.float64).copy()
+    active = np.nonzero(left > 0.0)[0]
+    while active.size:
+        seg = left[active]
+        if nu_c > 0.0:
+            seg = np.minimum(seg, rng.exponential(1.0 / nu_c, active.size))
+        b = delta * rng.standard_normal((active.size, 3))
+        bn = np.sqrt(np.einsum("ij,ij->i", b, b))
+        k = b / np.maximum(bn, 1e-300)[:, None]
+        th = bn * seg
+        c, s_ = np.cos(th)[:, None], np.sin(th)[:, None]
+        v = S[active]
+        kv = np.einsum("ij,ij->i", k, v)[:, None]
+        S[active] = v * c + np.cross(k, v) * s_ + k * kv * (1.0 - c)
+        left[active] -= seg
+        active = active[left[active] > 0.0]
+    return S[:, 2]
 
 
 def simulate(seed: int, dets: Sequence[Detector], comps_per_det: Sequence[Sequence[Component]],
@@ -408,6 +442,21 @@ def levy_lf(nhist: int = 2, nbins: int = 1600, bin_width_ns: float = 8.0, seed: 
     truth = [0.25, 0.8, 0.5] + [v for _ in range(nhist) for v in (n0, 2.0)]
     return Problem(counts, np.zeros(nhist), bin_width_ns, _full_range(nbins, bin_width_ns), terms,
                    np.array(rows, np.int32), np.zeros(0), len(truth), np.array(truth), names, "levy_lf")
+
+
+def dkt_zf(nhist: int = 2, nbins: int = 1600, bin_width_ns: float = 8.0, seed: int = 10, n0: float = 3000.0,
+           delta: float = 0.4, nu_c: float = 0.8, dtype=np.float32) -> Problem:
+    """Zero-field run in fluctuating Gaussian fields (strong collisions at rate nu_c): model
+    A = A0 DKT(Delta, nu) with shared A0, Delta, nu; per detector N0, Nbkg."""
+    dets = [Detector(n0, 2.0, 0.0) for _ in range(nhist)]
+    comps = [[Component(0.25, "DZF", delta=delta, nu_c=nu_c)] for _ in range(nhist)]
+    counts = simulate(seed, dets, comps, nbins, bin_width_ns, dtype)
+    terms = [[("AMP", (2,)), ("DKT", (3, 4))]]
+    rows = [[3 + 2 * j, 4 + 2 * j, 0, 1, 2] for j in range(nhist)]
+    names = ["A0", "Delta", "nu"] + [n for j in range(nhist) for n in (f"N0_{j}", f"Nbkg_{j}")]
+    truth = [0.25, delta, nu_c] + [v for _ in range(nhist) for v in (n0, 2.0)]
+    return Problem(counts, np.zeros(nhist), bin_width_ns, _full_range(nbins, bin_width_ns), terms,
+                   np.array(rows, np.int32), np.zeros(0), len(truth), np.array(truth), names, "dkt_zf")
 
 
 @dataclasses.dataclass

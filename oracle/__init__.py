@@ -13,7 +13,9 @@ Every function here follows Section 4.1 of the paper:
   * Eq. positron_histo  -- :func:`model`
   * Eq. chisq           -- :func:`cost` with ``mode=0``
   * Eq. log-likelihood  -- :func:`cost` with ``mode=1``
-  * Eq. asymmetry       -- :func:`primitive` (the primitive factors of A(t))
+  * Eq. asymmetry       -- :func:`primitive` (the primitive factors of A(t)), and
+                           :func:`dkt` (the dynamic Kubo-Toyabe relaxation, a renewal
+                           equation solved on a grid; a "user defined function" of 4.1)
   * the host-side minimiser that replaces migrad -- :func:`fit`
   * the Gauss-Newton matrix of the cost (error estimates) -- :func:`gauss_newton`
 
@@ -37,7 +39,7 @@ _LIB_PATH = os.path.join(_HERE, "_musr_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-KIND = {"AMP": 1, "EXP": 2, "GAUSS": 3, "KT": 4, "TFCOS": 5, "LKT": 6, "STREXP": 7, "BESSEL": 8}
+KIND = {"AMP": 1, "EXP": 2, "GAUSS": 3, "KT": 4, "TFCOS": 5, "LKT": 6, "STREXP": 7, "BESSEL": 8, "DKT": 9}
 CHI2, MLE = 0, 1
 
 
@@ -86,6 +88,8 @@ def _load():
             lib.oracle_poisson_points.restype = None
             lib.oracle_asymmetry.argtypes = [P(d), P(d), ctypes.c_int, i64, P(d), P(d), P(d), P(d), P(d)]
             lib.oracle_asymmetry.restype = None
+            lib.oracle_dkt.argtypes = [d, d, d, P(d), ctypes.c_int, P(d), P(d), P(d)]
+            lib.oracle_dkt.restype = ctypes.c_int
             lib.oracle_neumaier_sum.argtypes = [P(d), i64]
             lib.oracle_neumaier_sum.restype = d
             _lib = lib
@@ -100,9 +104,9 @@ def theory_arrays(terms):
     """Term list -> (nprim[T], kind[T,4], slot[T,4,2]) int32 arrays.
 
     ``terms`` is a sequence of terms; a term is a sequence of (kind, slots)
-    with kind in AMP, EXP, GAUSS, KT, TFCOS, LKT, STREXP, BESSEL and slots a tuple of local
-    slot indices (two for TFCOS and BESSEL: frequency, phase; two for STREXP: rate, exponent;
-    one otherwise).
+    with kind in AMP, EXP, GAUSS, KT, TFCOS, LKT, STREXP, BESSEL, DKT and slots a tuple of
+    local slot indices (two for TFCOS and BESSEL: frequency, phase; two for STREXP: rate,
+    exponent; two for DKT: static width, fluctuation rate; one otherwise).
     """
     T = len(terms)
     nprim = np.zeros(max(T, 1), np.int32)
@@ -170,6 +174,22 @@ def asymmetry(forward, backward, alpha, bkg_f, bkg_b):
 def primitive(kind: str, p0: float, p1: float, t: float) -> float:
     """One primitive factor of A(t) at time t (us)."""
     return _load().oracle_primitive(KIND[kind], p0, p1, t)
+
+
+def dkt(delta: float, nu: float, span: float, ts, derivs: bool = False):
+    """The dynamic Gaussian Kubo-Toyabe relaxation (strong-collision model) of static width
+    delta and fluctuation rate nu (both 1/us) at the times ts (us), on the oracle's grid over
+    [0, span] (span >= max ts): G, or (G, dG/ddelta, dG/dnu) with derivs."""
+    ts = np.ascontiguousarray(np.atleast_1d(ts), dtype=np.float64)
+    if ts.size and ts.max() > span:
+        raise ValueError("times beyond the grid's span")
+    G = np.zeros(ts.size)
+    dD = np.zeros(ts.size) if derivs else None
+    dn = np.zeros(ts.size) if derivs else None
+    _load().oracle_dkt(float(delta), float(nu), float(span), _ptr(ts, ctypes.c_double), ts.size,
+                       _ptr(G, ctypes.c_double), None if dD is None else _ptr(dD, ctypes.c_double),
+                       None if dn is None else _ptr(dn, ctypes.c_double))
+    return (G, dD, dn) if derivs else G
 
 
 def model(prob, x, h: int, t: float) -> float:

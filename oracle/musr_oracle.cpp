@@ -34,6 +34,8 @@
 //     relaxation starts at time zero), the stretched exponential.
 //   * BESSEL(nu, phi) = J0(2 pi (nu t + phi / 360)), precession in an incommensurate
 //     field distribution, the phase inside the argument like TFCOS.
+//   * DKT(Delta, nu): the dynamic Gaussian Kubo-Toyabe relaxation of the strong-collision
+//     model, the solution of a renewal equation (see dkt_solve below); 1 for t <= 0.
 //   * Local slot 0 is N0, slot 1 is Nbkg; terms reference any slot.
 //   * MLE with N <= 0 in a bin with d > 0 is +infinity (status 1).
 //
@@ -64,6 +66,9 @@
 #include <cstdint>
 #include <cstring>
 #include <limits>
+#include <map>
+#include <memory>
+#include <tuple>
 #include <vector>
 
 namespace {
@@ -71,7 +76,7 @@ namespace {
 constexpr double kTauMu = 2.197019;  // muon lifetime in microseconds
 constexpr double kPi = 3.14159265358979323846;
 
-enum PrimKind { kAmp = 1, kExp = 2, kGauss = 3, kKT = 4, kTFCos = 5, kLKT = 6, kStrExp = 7, kBessel = 8 };
+enum PrimKind { kAmp = 1, kExp = 2, kGauss = 3, kKT = 4, kTFCos = 5, kLKT = 6, kStrExp = 7, kBessel = 8, kDKT = 9 };
 constexpr int kMaxPrim = 4;
 
 using cplx = std::complex<double>;
@@ -151,6 +156,164 @@ inline double bessel_j1(double x) { return x < 0.0 ? -std::cyl_bessel_j(1.0, -x)
 // exact to O(y^2).
 inline cplx bessel_j0(const cplx& z) { return cplx(bessel_j0(z.real()), -z.imag() * bessel_j1(z.real())); }
 
+// ---------------------------------------------------------------------------------------
+// Dynamic Gaussian Kubo-Toyabe relaxation, strong-collision model (primitive DKT; slot 0 the
+// static width Delta, slot 1 the fluctuation rate nu, both in 1/us).  Not in the paper: one
+// of the "user defined functions" of Section 4.1.  The local field is drawn from the
+// isotropic Gaussian of width Delta / gamma_mu and drawn anew at the events of a Poisson
+// process of rate nu.  Between two events the muon precesses in a static field; averaged
+// over that field, an interval of length s multiplies the polarisation by the static
+// function g(s) = 1/3 + 2/3 (1 - Delta^2 s^2) exp(-Delta^2 s^2 / 2).  Summing over the
+// number of events gives the renewal (Volterra) equation of the second kind
+//     G(t) = f(t) + nu int_0^t f(s) G(t - s) ds,    f(t) = g(t) exp(-nu t),
+// whose solution G is the relaxation.  It has no closed form.  The oracle solves it on the
+// uniform grid t_k = k h of [0, span] by the trapezoidal rule (f_0 = G_0 = 1):
+//     (1 - nu h / 2) G_k = (1 + nu h / 2) f_k + nu h sum_{j=1}^{k-1} f_j G_{k-j},
+// removes the rule's h^2 error term by Richardson extrapolation, (4 G_{h/2} - G_h) / 3 at the
+// points of the coarser grid, and interpolates with the cubic through the four nearest grid
+// points.  The derivatives with respect to Delta and nu solve the same recursion
+// differentiated (df/dDelta = dg/dDelta exp(-nu t), df/dnu = -t f).  For t <= 0 the
+// relaxation is 1: it starts at time zero.
+// ---------------------------------------------------------------------------------------
+
+// The grid's end (microseconds): the last time in the fit of the problem being evaluated
+// (set by every entry point; the oracle is single-threaded).
+double g_dkt_span = 1.0;
+
+// The static function g and its Delta-derivative at time t.
+template <class T>
+T dkt_static(const T& D, double t) {
+  const T u = (D * t) * (D * t);
+  return 1.0 / 3.0 + (2.0 / 3.0) * (1.0 - u) * std::exp(-0.5 * u);
+}
+inline double dkt_static_dD(double D, double t) {
+  const double u = (D * t) * (D * t);
+  return (2.0 / 3.0) * D * t * t * std::exp(-0.5 * u) * (u - 3.0);
+}
+
+// Trapezoidal solution on K + 1 points t_k = k h: G, and when dG is given the derivatives
+// dG[0] (Delta) and dG[1] (nu) (real arithmetic only).
+template <class T>
+void dkt_solve(const T& D, const T& nu, double h, int K, std::vector<T>* G, std::vector<double>* dG) {
+  std::vector<T> f(K + 1);
+  for (int k = 0; k <= K; ++k) f[k] = dkt_static(D, k * h) * std::exp(-nu * (k * h));
+  const T a = 1.0 - nu * (0.5 * h), b = 1.0 + nu * (0.5 * h), c = nu * h;
+  G->assign(K + 1, T(0.0));
+  (*G)[0] = T(1.0);
+  std::vector<double> S;  // S_k = sum_{j=1}^{k-1} f_j G_{k-j}, kept for the nu-derivative
+  if (dG) S.assign(K + 1, 0.0);
+  for (int k = 1; k <= K; ++k) {
+    T sk = T(0.0);
+    for (int j = 1; j < k; ++j) sk = sk + f[j] * (*G)[k - j];
+    (*G)[k] = (b * f[k] + c * sk) / a;
+    if (dG) S[k] = re(sk);
+  }
+  if (!dG) return;
+  const double Dr = re(D), nr = re(nu), ar = re(a), br = re(b), cr = re(c);
+  std::vector<double> fD(K + 1), fn(K + 1);
+  for (int k = 0; k <= K; ++k) {
+    fD[k] = dkt_static_dD(Dr, k * h) * std::exp(-nr * (k * h));
+    fn[k] = -(k * h) * re(f[k]);
+  }
+  dG[0].assign(K + 1, 0.0);
+  dG[1].assign(K + 1, 0.0);
+  for (int k = 1; k <= K; ++k) {
+    double sD = 0.0, sn = 0.0;
+    for (int j = 1; j < k; ++j) {
+      sD += fD[j] * re((*G)[k - j]) + re(f[j]) * dG[0][k - j];
+      sn += fn[j] * re((*G)[k - j]) + re(f[j]) * dG[1][k - j];
+    }
+    dG[0][k] = (br * fD[k] + cr * sD) / ar;
+    // d/dnu of a G_k = b f_k + c S_k, with da/dnu = -h/2, db/dnu = h/2, dc/dnu = h
+    dG[1][k] = (0.5 * h * (re((*G)[k]) + re(f[k])) + br * fn[k] + h * S[k] + cr * sn) / ar;
+  }
+}
+
+// Points of the coarse grid over [0, span]: enough that h max(Delta, nu) stays near 0.004.
+inline int dkt_points(double D, double nu, double span) {
+  const double rate = std::fmax(std::fmax(std::fabs(D), std::fabs(nu)), 0.05);
+  const double k = std::ceil(span * rate / 0.004);
+  return static_cast<int>(std::fmin(std::fmax(k, 1024.0), 32768.0));
+}
+
+template <class T>
+struct DktTable {
+  double h = 0.0;
+  int K = 0;
+  std::vector<T> G;      // Richardson-extrapolated values at t_k = k h, k = 0..K
+  std::vector<double> dG[2];  // derivatives (real tables only)
+};
+
+template <class T>
+std::shared_ptr<DktTable<T>> dkt_build(const T& D, const T& nu, double span, bool derivs) {
+  auto tab = std::make_shared<DktTable<T>>();
+  const int K = dkt_points(re(D), re(nu), span);
+  const double h = span / K;
+  std::vector<T> Gh, Gh2;
+  std::vector<double> dh[2], dh2[2];
+  dkt_solve(D, nu, h, K, &Gh, derivs ? dh : nullptr);
+  dkt_solve(D, nu, 0.5 * h, 2 * K, &Gh2, derivs ? dh2 : nullptr);
+  tab->h = h;
+  tab->K = K;
+  tab->G.resize(K + 1);
+  for (int k = 0; k <= K; ++k) tab->G[k] = (4.0 * Gh2[2 * k] - Gh[k]) / 3.0;
+  if (derivs)
+    for (int q = 0; q < 2; ++q) {
+      tab->dG[q].resize(K + 1);
+      for (int k = 0; k <= K; ++k) tab->dG[q][k] = (4.0 * dh2[q][2 * k] - dh[q][k]) / 3.0;
+    }
+  return tab;
+}
+
+// Cubic through the four grid points nearest to t (one-sided at the ends of the grid).
+template <class T, class V>
+T dkt_interp(const V& y, double h, int K, double t) {
+  const double x = t / h;
+  int i = static_cast<int>(std::floor(x)) - 1;  // stencil i .. i + 3 around [i + 1, i + 2]
+  if (i < 0) i = 0;
+  if (i > K - 3) i = K - 3;
+  const double u = x - i;  // position in units of h from point i
+  const double w0 = -(u - 1.0) * (u - 2.0) * (u - 3.0) / 6.0, w1 = u * (u - 2.0) * (u - 3.0) / 2.0;
+  const double w2 = -u * (u - 1.0) * (u - 3.0) / 2.0, w3 = u * (u - 1.0) * (u - 2.0) / 6.0;
+  return w0 * y[i] + w1 * y[i + 1] + w2 * y[i + 2] + w3 * y[i + 3];
+}
+
+inline double key_im(double) { return 0.0; }
+inline double key_im(const cplx& z) { return z.imag(); }
+
+// The table of (Delta, nu) over [0, span], built on first use (a cache of recent ones).
+template <class T>
+std::shared_ptr<DktTable<T>> dkt_table(const T& D, const T& nu, double span, bool derivs) {
+  using Key = std::tuple<double, double, double, double, double, bool>;
+  static std::map<Key, std::shared_ptr<DktTable<T>>> cache;
+  const Key key(re(D), key_im(D), re(nu), key_im(nu), span, derivs);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  if (cache.size() > 64) cache.clear();
+  auto tab = dkt_build(D, nu, span, derivs);
+  cache[key] = tab;
+  return tab;
+}
+
+template <class T>
+T dkt_value(const T& D, const T& nu, double t) {
+  if (!(t > 0.0)) return T(1.0);
+  const double span = std::fmax(g_dkt_span, t);
+  auto tab = dkt_table(D, nu, span, false);
+  return dkt_interp<T>(tab->G, tab->h, tab->K, t);
+}
+
+inline void dkt_derivs(double D, double nu, double t, double* dD, double* dnu) {
+  if (!(t > 0.0)) {
+    *dD = *dnu = 0.0;
+    return;
+  }
+  const double span = std::fmax(g_dkt_span, t);
+  auto tab = dkt_table(D, nu, span, true);
+  *dD = dkt_interp<double>(tab->dG[0], tab->h, tab->K, t);
+  *dnu = dkt_interp<double>(tab->dG[1], tab->h, tab->K, t);
+}
+
 // |lambda| for the stretched exponential: the sign folded analytically on each side.
 inline double fold_sign(double v) { return v < 0.0 ? -v : v; }
 inline cplx fold_sign(const cplx& v) { return v.real() < 0.0 ? -v : v; }
@@ -182,6 +345,8 @@ T primitive(int kind, const T& p0, const T& p1, double t) {
     }
     case kBessel:
       return bessel_j0(2.0 * kPi * (p0 * t + p1 / 360.0));
+    case kDKT:
+      return dkt_value(p0, p1, t);
     default:
       return T(std::numeric_limits<double>::quiet_NaN());
   }
@@ -231,12 +396,17 @@ inline void primitive_deriv(int kind, double p0, double p1, double t, double* d0
       *d1 = -j1 * 2.0 * kPi / 360.0;
       break;
     }
+    case kDKT:
+      dkt_derivs(p0, p1, t, d0, d1);
+      break;
     default:
       break;
   }
 }
 
-inline int nslots_of(int kind) { return kind == kTFCos || kind == kStrExp || kind == kBessel ? 2 : 1; }
+inline int nslots_of(int kind) {
+  return kind == kTFCos || kind == kStrExp || kind == kBessel || kind == kDKT ? 2 : 1;
+}
 
 // Eq. positron_histo for histogram h at time t.
 template <class T>
@@ -482,6 +652,16 @@ Problem make_problem(const double* data, int H, int64_t B, const double* t0, dou
   return pb;
 }
 
+// The dynamic Kubo-Toyabe grid spans the problem's fit times: up to its last in-fit time.
+void set_dkt_span(const Problem& pb) {
+  double span = 0.0;
+  for (int h = 0; h < pb.H; ++h) {
+    const double t_last = bin_time(pb, h, pb.B - 1);
+    span = std::fmax(span, std::fmin(t_last, pb.hi));
+  }
+  g_dkt_span = span > 0.0 ? span : 1.0;
+}
+
 double inf_norm(const std::vector<double>& v) {
   double m = 0.0;
   for (double a : v) m = std::fmax(m, std::fabs(a));
@@ -497,12 +677,14 @@ double inf_norm(const std::vector<double>& v) {
       int envelope
 #define ORACLE_PROBLEM                                                                                  \
   make_problem(data, H, B, t0, bin_width_ns, lo, hi, nterms, nprim, kind, slot, map, nslots, consts, nconsts, P, \
-               weight, envelope)
+               weight, envelope);                                                                               \
+  set_dkt_span(pb)
 
 extern "C" {
 
 // One primitive at time t (Section 4.1, Eq. asymmetry and its generalisation).
 double oracle_primitive(int kind, double p0, double p1, double t) {
+  if (kind == kDKT) g_dkt_span = t;  // a grid over [0, t]
   return primitive<double>(kind, p0, p1, t);
 }
 
@@ -736,6 +918,23 @@ void oracle_poisson_points(const double* rho, int mx, int my, int mz, double hx,
                            const int32_t* ijk, int npts, double* out) {
   for (int p = 0; p < npts; ++p)
     out[p] = poisson_at(rho, mx, my, mz, hx, hy, hz, ijk[3 * p], ijk[3 * p + 1], ijk[3 * p + 2]);
+}
+
+// The dynamic Kubo-Toyabe relaxation of (Delta, nu) on the grid over [0, span], at the n
+// times ts: G[n], and its derivatives dD[n] (Delta), dnu[n] (nu) when those are not NULL.
+// Returns the number of coarse grid intervals used.
+int oracle_dkt(double D, double nu, double span, const double* ts, int n, double* G, double* dD, double* dnu) {
+  g_dkt_span = span;
+  for (int i = 0; i < n; ++i) {
+    G[i] = dkt_value<double>(D, nu, ts[i]);
+    if (dD || dnu) {
+      double a, b;
+      dkt_derivs(D, nu, ts[i], &a, &b);
+      if (dD) dD[i] = a;
+      if (dnu) dnu[i] = b;
+    }
+  }
+  return dkt_points(D, nu, span);
 }
 
 // Neumaier-compensated sum of n doubles, exposed so that the summation itself

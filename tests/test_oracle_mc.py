@@ -106,11 +106,14 @@ def test_asymmetry_pulls_have_unit_spread():
     assert np.all((sd > 0.5) & (sd < 1.6)), sd
 
 
-@pytest.mark.parametrize("name", ["inc_bessel", "levy_lf"])
+@pytest.mark.parametrize("name", ["inc_bessel", "levy_lf", "dkt_zf"])
 def test_new_primitives_fit_simulated_fields(name):
     """The Bessel precession emerges from simulated incommensurate fields (gamma B = 2 pi nu
-    cos U) and the stretched exponential with beta = 1/2 from depolarisation rates drawn from
-    a one-sided Levy distribution; fits land within a few sigma of the truth (beta = 1/2)."""
-    p = mi.inc_bessel(seed=108) if name == "inc_bessel" else mi.levy_lf(seed=109)
+    cos U), the stretched exponential with beta = 1/2 from depolarisation rates drawn from
+    a one-sided Levy distribution, and the dynamic Kubo-Toyabe relaxation from Gaussian
+    fields drawn anew at Poisson times (spin vectors rotated interval by interval, nothing
+    of the renewal equation); fits land within a few sigma of the truth."""
+    p = {"inc_bessel": lambda: mi.inc_bessel(seed=108), "levy_lf": lambda: mi.levy_lf(seed=109),
+         "dkt_zf": lambda: mi.dkt_zf(seed=110)}[name]()
     z = _pulls(p, 1)
     assert np.all(np.abs(z) < 4.5), dict(zip(p.names, np.round(z, 2)))

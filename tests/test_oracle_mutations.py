@@ -85,6 +85,20 @@ MUTANTS = {
     "background derivative carries the decay": ("  dslot[0] += E * (1.0 + A);\n  dslot[1] += 1.0;",
                                                  "  dslot[0] += E * (1.0 + A);\n  dslot[1] += E;"),
     "product rule keeps the differentiated factor": ("        if (q != m) rest *= f[q];", "        rest *= f[q];"),
+    "dynamic KT drops the trapezoid's end weights": (
+        "const T a = 1.0 - nu * (0.5 * h), b = 1.0 + nu * (0.5 * h), c = nu * h;",
+        "const T a = 1.0, b = 1.0, c = nu * h;"),
+    "dynamic KT without Richardson extrapolation": ("tab->G[k] = (4.0 * Gh2[2 * k] - Gh[k]) / 3.0;", "tab->G[k] = Gh[k];"),
+    "dynamic KT kernel misses the renewal decay": ("f[k] = dkt_static(D, k * h) * std::exp(-nu * (k * h));",
+                                                  "f[k] = dkt_static(D, k * h);"),
+    "dynamic KT convolution lags one point": ("sk = sk + f[j] * (*G)[k - j];", "sk = sk + f[j] * (*G)[k - j - 1];"),
+    "dynamic KT nu-derivative drops the convolution": ("+ h * S[k] + cr * sn) / ar;", "+ cr * sn) / ar;"),
+    "dynamic KT Delta-derivative misses a t": (
+        "return (2.0 / 3.0) * D * t * t * std::exp(-0.5 * u) * (u - 3.0);",
+        "return (2.0 / 3.0) * D * t * std::exp(-0.5 * u) * (u - 3.0);"),
+    "dynamic KT interpolation weights exchanged": (
+        "return w0 * y[i] + w1 * y[i + 1] + w2 * y[i + 2] + w3 * y[i + 3];",
+        "return w0 * y[i] + w2 * y[i + 1] + w1 * y[i + 2] + w3 * y[i + 3];"),
 }
 
 

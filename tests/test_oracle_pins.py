@@ -569,6 +569,104 @@ def test_gradient_of_new_primitives_matches_central_differences():
 
 
 # ------------------------------------------------------------------------------------------
+# Dynamic Gaussian Kubo-Toyabe relaxation (strong collisions): the renewal equation
+# G = f + nu f * G, f = g exp(-nu t), g the static function, solved on a grid by the oracle
+# ------------------------------------------------------------------------------------------
+
+def _static_kt(D, t):
+    """The textbook static Gaussian Kubo-Toyabe function (the test's own statement of g)."""
+    u = (D * t) ** 2
+    return 1.0 / 3.0 + 2.0 / 3.0 * (1.0 - u) * math.exp(-0.5 * u)
+
+
+def test_dkt_without_fluctuations_is_the_static_function():
+    """nu = 0: no renewals, so G is the static function: G(0) = 1 and the minimum
+    1/3 - (4/3) e^{-3/2} at t = sqrt(3) / Delta (catches a solver that drops f's first
+    term or misplaces the grid)."""
+    D = 0.7
+    tmin = math.sqrt(3.0) / D
+    G = oracle.dkt(D, 0.0, 6.0, [0.0, tmin, 1.0, 5.9])
+    assert G[0] == 1.0
+    assert abs(G[1] - (1.0 / 3.0 - 4.0 / 3.0 * math.exp(-1.5))) < 1e-11
+    assert abs(G[2] - _static_kt(D, 1.0)) < 1e-11 and abs(G[3] - _static_kt(D, 5.9)) < 1e-11
+    assert oracle.dkt(D, 0.9, 6.0, [0.0])[0] == 1.0
+    assert oracle.primitive("DKT", D, 0.9, -1.0) == 1.0  # the relaxation starts at time zero
+
+
+def test_dkt_laplace_transform_of_the_renewal_equation():
+    """The Laplace transform of G = f + nu f * G is L[G](s) = F(s) / (1 - nu F(s)) with
+    F(s) = L[g](s + nu): F by adaptive quadrature of the static function, L[G] by Simpson's
+    rule on the oracle's G.  Catches a wrong trapezoidal weight, sign, rate or Richardson
+    step in the solver (each moves L[G] by far more than 1e-10)."""
+    from scipy.integrate import quad
+    D, nu, span = 0.6, 0.9, 16.0
+    ts = np.linspace(0.0, span, 16001)
+    G = oracle.dkt(D, nu, span, ts)
+    hs = ts[1] - ts[0]
+    for s in (2.0, 3.5):
+        y = G * np.exp(-s * ts)
+        lhs = hs / 3.0 * (y[0] + y[-1] + 4.0 * y[1:-1:2].sum() + 2.0 * y[2:-1:2].sum())
+        F = quad(lambda t: _static_kt(D, t) * math.exp(-(s + nu) * t), 0.0, 60.0, limit=400, epsabs=1e-15,
+                 epsrel=1e-13)[0]
+        rhs = F / (1.0 - nu * F)
+        assert abs(lhs / rhs - 1.0) < 1e-10, (s, lhs, rhs)
+
+
+def test_dkt_motional_narrowing():
+    """Fast fluctuations (nu >> Delta) narrow the relaxation to exp(-2 Delta^2 t / nu): the
+    log-slope of G at late times is 2 Delta^2 / nu to second order in Delta / nu."""
+    for D, nu in ((0.1, 5.0), (0.2, 5.0)):
+        G = oracle.dkt(D, nu, 8.0, [4.0, 8.0])
+        lam = -math.log(G[1] / G[0]) / 4.0
+        assert abs(lam / (2.0 * D * D / nu) - 1.0) <= 2.0 * (D / nu) ** 2, (D, nu, lam)
+
+
+def test_dkt_grid_refinement():
+    """Grids over different spans (other spacings and nodes) give the same relaxation."""
+    ts = np.linspace(0.3, 7.9, 50)
+    a = oracle.dkt(0.6, 0.9, 8.0, ts)
+    b = oracle.dkt(0.6, 0.9, 9.3, ts)
+    assert np.max(np.abs(a - b)) < 1e-10
+
+
+def test_dkt_derivatives_central_differences():
+    """The derivative recursions against central differences of the value (no derivative
+    formula involved); parameters away from a change of the grid's size."""
+    D, nu, span = 0.4137, 0.8123, 8.0
+    ts = np.linspace(0.2, 7.8, 30)
+    G, dD, dn = oracle.dkt(D, nu, span, ts, derivs=True)
+    e = 1e-6
+    fdD = (oracle.dkt(D + e, nu, span, ts) - oracle.dkt(D - e, nu, span, ts)) / (2 * e)
+    fdn = (oracle.dkt(D, nu + e, span, ts) - oracle.dkt(D, nu - e, span, ts)) / (2 * e)
+    assert np.max(np.abs(fdD - dD)) < 1e-8 and np.max(np.abs(fdn - dn)) < 1e-8
+
+
+def _dkt_problem():
+    import musr_inputs as mi
+    p = mi.cfg3(nhist=2, nbins=300, bin_width_ns=25.0, seed=31)
+    terms = [[("AMP", (2,)), ("DKT", (3, 4))], [("AMP", (5,)), ("EXP", (6,))]]
+    rows = [[0, 1, 2, 3, 4, 5, 6], [7, 8, 2, 3, 4, 5, 6]]
+    x = np.array([300.0, 2.0, 0.2, 0.45, 0.7, 0.05, 0.3, 310.0, 2.5])
+    q = Problem(p.counts, p.t0, p.bin_width_ns, p.fit_range_us, terms, np.array(rows, np.int32), np.zeros(0), 9,
+                np.zeros(9), [f"p{i}" for i in range(9)])
+    return q, x
+
+
+@pytest.mark.parametrize("mode", [CHI2, MLE])
+def test_gradient_matches_complex_step_dynamic_kt(mode):
+    """Complex step through the whole cost, the renewal equation solved in complex
+    arithmetic: pins the derivative recursions and their scatter to Delta and nu."""
+    q, x = _dkt_problem()
+    v, g, gs, st = oracle.cost(q, x, mode)
+    assert st == 0
+    for i in range(q.nparams):
+        e = np.zeros(q.nparams)
+        e[i] = 1.0
+        cs = oracle.cost_cstep(q, x, e, mode)
+        assert abs(cs - g[i]) <= 1e-10 * gs[i] + 1e-300, (i, cs, g[i], gs[i])
+
+
+# ------------------------------------------------------------------------------------------
 # The particle-mesh Poisson solve (Section 3, Eq. openbruteforceconv), the second workload
 # ------------------------------------------------------------------------------------------
 
