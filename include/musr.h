@@ -72,8 +72,15 @@ enum {
   MUSR_PRIM_LKT = 6,   /* static Lorentzian Kubo-Toyabe 1/3 + 2/3 (1 - a t) exp(-a t); slot[0] = a (1/us) */
   MUSR_PRIM_STREXP = 7, /* stretched exponential exp(-(|lambda| t)^beta) for t > 0, 1 for t <= 0;
                            slot[0] = lambda (1/us), slot[1] = beta */
-  MUSR_PRIM_BESSEL = 8  /* J0(2 pi (nu t + phi / 360)), Bessel precession (incommensurate order);
+  MUSR_PRIM_BESSEL = 8, /* J0(2 pi (nu t + phi / 360)), Bessel precession (incommensurate order);
                            slot[0] = nu (MHz), slot[1] = phi (degrees) */
+  MUSR_PRIM_DKT = 9     /* dynamic Gaussian Kubo-Toyabe relaxation of the strong-collision model
+                           (fields of width Delta drawn anew at rate nu): the solution G of
+                           G(t) = f(t) + nu int_0^t f(s) G(t - s) ds, f = KT(Delta, t) exp(-nu t),
+                           1 for t <= 0; slot[0] = Delta (1/us), slot[1] = nu (1/us).  Evaluated
+                           from a table solved on the device per evaluation (relative accuracy
+                           of order 1e-6); at most 8 distinct (Delta, nu) pairs per context;
+                           not in serving requests or musr_eval_noalloc */
 };
 
 #define MUSR_MAX_PRIMS 4
@@ -82,7 +89,8 @@ enum {
 #define MUSR_MAX_PARAMS 4096
 
 /* One term of A(t): the product of nprim primitives (Eq. asymmetry,
- * generalised).  slot[m][0] (and slot[m][1] for TFCOS) are local slots. */
+ * generalised).  slot[m][0] (and slot[m][1] for the two-slot primitives TFCOS, STREXP,
+ * BESSEL, DKT) are local slots. */
 typedef struct musr_term {
   int32_t nprim;
   int32_t kind[MUSR_MAX_PRIMS];

@@ -23,7 +23,7 @@ MUSR_DTYPE_INT32, MUSR_DTYPE_FP32, MUSR_DTYPE_FP64 = 0, 1, 2
 MUSR_REQ_BORROW_COUNTS = 1  # musr_fit_request.flags: the server reads the caller's counts at admission
 MUSR_CHI2, MUSR_MLE = 0, 1
 MUSR_FP64, MUSR_SPLIT = 0, 1
-PRIM = {"AMP": 1, "EXP": 2, "GAUSS": 3, "KT": 4, "TFCOS": 5, "LKT": 6, "STREXP": 7, "BESSEL": 8}
+PRIM = {"AMP": 1, "EXP": 2, "GAUSS": 3, "KT": 4, "TFCOS": 5, "LKT": 6, "STREXP": 7, "BESSEL": 8, "DKT": 9}
 MAX_PRIMS = 4
 
 # Every symbol include/musr.h declares (checked by the ABI test).

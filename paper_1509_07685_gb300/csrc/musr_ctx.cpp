@@ -251,6 +251,7 @@ void free_compiled(musr_ctx* ctx, Compiled& c) {
   c.col_chunk.clear();
   c.p_ptr.clear();
   c.p_cols.clear();
+  c.dkt_of.clear();
   c.valid = false;
   c.planned = false;
   c.reason.clear();
@@ -289,6 +290,29 @@ int compile(musr_ctx* ctx, int prec, int var) {
     }
   }
   const int H = ctx->H;
+  // Dynamic Kubo-Toyabe sources: the distinct (Delta, nu) map entries of every DKT factor.
+  std::vector<int> dkt_of(static_cast<size_t>(H) * musr::kMaxTerms * musr::kMaxPrims, -1);
+  hs.ndkt = 0;
+  for (int h = 0; h < H; ++h)
+    for (int k = 0; k < hs.nterms; ++k)
+      for (int m = 0; m < ctx->terms[k].nprim; ++m) {
+        if (ctx->terms[k].kind[m] != MUSR_PRIM_DKT) continue;
+        const int32_t* row = ctx->map.data() + static_cast<size_t>(h) * ctx->nslots;
+        const int2 key = make_int2(row[ctx->terms[k].slot[m][0]], row[ctx->terms[k].slot[m][1]]);
+        int src = -1;
+        for (int q = 0; q < hs.ndkt && src < 0; ++q)
+          if (hs.dkt_src[q].x == key.x && hs.dkt_src[q].y == key.y) src = q;
+        if (src < 0 && hs.ndkt < musr::kMaxDkt) {
+          src = hs.ndkt++;
+          hs.dkt_src[src] = key;
+        }
+        dkt_of[(static_cast<size_t>(h) * musr::kMaxTerms + k) * musr::kMaxPrims + m] = src;
+      }
+  // the tables span the last in-fit time of every histogram
+  hs.dkt_span = 0.0;
+  for (int h = 0; h < H; ++h)
+    if (ctx->nhi[h] > ctx->nlo[h])
+      hs.dkt_span = std::max(hs.dkt_span, (static_cast<double>(ctx->nhi[h] - 1) - ctx->t0[h]) * ctx->dt_us);
   std::vector<std::vector<int>> groups;
   int group_cap = 1;
   const bool basis = prec == MUSR_SPLIT &&
@@ -414,6 +438,7 @@ int compile(musr_ctx* ctx, int prec, int var) {
   if (items.empty()) items.push_back(make_int2(0, 0));
   if (chunks.empty()) chunks.push_back(Chunk{});
   if (hist_index.empty()) hist_index.push_back(0);
+  c.dkt_of = std::move(dkt_of);
   c.chunks = std::move(chunks);
   c.items = std::move(items);
   c.hist_index = std::move(hist_index);
@@ -456,6 +481,7 @@ int ensure_uploaded(musr_ctx* ctx, int prec, int var) {
   const size_t o_pc = place(sizeof(int) * c.p_cols.size());
   const size_t o_mp = place(sizeof(int32_t) * ctx->map.size());
   const size_t o_cs = place(sizeof(double) * nconsts);
+  const size_t o_dk = place(sizeof(int) * std::max<size_t>(c.dkt_of.size(), 1));
   int rc = dalloc(ctx, c.tables, off);
   if (rc) return rc;
   char* base = static_cast<char*>(c.tables.p);
@@ -468,6 +494,7 @@ int ensure_uploaded(musr_ctx* ctx, int prec, int var) {
   hs.p_cols = reinterpret_cast<const int*>(base + o_pc);
   hs.map = reinterpret_cast<const int32_t*>(base + o_mp);
   hs.consts = reinterpret_cast<const double*>(base + o_cs);
+  hs.dkt_of = reinterpret_cast<const int*>(base + o_dk);
   std::vector<char>& blob = c.blob;  // kept until the tables are freed: the copy's source
   blob.assign(off, 0);
   std::memcpy(blob.data() + o_hs, &hs, sizeof(hs));
@@ -479,6 +506,7 @@ int ensure_uploaded(musr_ctx* ctx, int prec, int var) {
   std::memcpy(blob.data() + o_pc, c.p_cols.data(), sizeof(int) * c.p_cols.size());
   std::memcpy(blob.data() + o_mp, ctx->map.data(), sizeof(int32_t) * ctx->map.size());
   if (!ctx->consts.empty()) std::memcpy(blob.data() + o_cs, ctx->consts.data(), sizeof(double) * ctx->consts.size());
+  if (!c.dkt_of.empty()) std::memcpy(blob.data() + o_dk, c.dkt_of.data(), sizeof(int) * c.dkt_of.size());
   cudaError_t e = cudaMemcpyAsync(base, blob.data(), off, cudaMemcpyHostToDevice,
                                   ctx->setup_stream ? ctx->setup_stream : ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(tables)");
@@ -527,6 +555,11 @@ int ensure_eval(musr_ctx* ctx, int prec, int var, int nvec) {
   if ((rc = grow(ev.chunk_val, nck * sizeof(double), false))) return rc;
   if ((rc = grow(ev.chunk_count, nck * sizeof(unsigned), true))) return rc;
   if ((rc = grow(ev.counters, nvec * sizeof(unsigned), true))) return rc;
+  if (hs.ndkt > 0) {
+    const size_t nt = static_cast<size_t>(nvec) * hs.ndkt;
+    if ((rc = grow(ev.dkt, nt * musr::kDktTable * sizeof(double), false))) return rc;
+    if ((rc = grow(ev.dkt_work, nt * musr::kDktWork * sizeof(double), false))) return rc;
+  }
   return MUSR_OK;
 }
 
@@ -551,6 +584,11 @@ void fill_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, c
     j.grad = grad;
     j.prec = prec;
     j.dir = d_dirs ? d_dirs + static_cast<size_t>(v) * ctx->P : nullptr;
+    if (hs.ndkt > 0) {  // tables of this evaluation: FP64 values for prec 0, FP32 for SPLIT
+      const size_t esz = prec == MUSR_SPLIT ? sizeof(float) : sizeof(double);
+      j.dkt = static_cast<char*>(ev.dkt.p) + static_cast<size_t>(v) * hs.ndkt * musr::kDktTable * esz;
+      j.dkt_work = static_cast<char*>(ev.dkt_work.p) + static_cast<size_t>(v) * hs.ndkt * musr::kDktWork * esz;
+    }
   }
 }
 
@@ -609,6 +647,12 @@ int enqueue_eval(musr_ctx* ctx, int prec, int mode, int grad, int nvec, const do
   int rc = prepare_jobs(ctx, prec, var, mode, grad, nvec, d_params, d_out, d_dirs);
   if (rc) return rc;
   musr::LaunchInfo info;
+  if (hs.ndkt > 0 &&
+      musr::launch_dkt_tables(prec, static_cast<const Job*>(ctx->ev.jobs.p), nvec, hs.ndkt, ctx->stream)) {
+    cudaError_t e = cudaGetLastError();
+    ctx->ev.key_valid = false;
+    return cuda_fail(ctx, e, "dynamic Kubo-Toyabe table launch");
+  }
   if (musr::launch_eval(prec, hs.shape, mode, grad, static_cast<const Job*>(ctx->ev.jobs.p), nvec,
                         nvec * hs.nitems, ctx->num_sms, ctx->stream, &info)) {
     cudaError_t e = cudaGetLastError();
@@ -972,7 +1016,7 @@ int musr_set_theory(musr_ctx* ctx, const musr_term* terms, int nterms) {
     const musr_term& t = terms[k];
     if (t.nprim < 1 || t.nprim > MUSR_MAX_PRIMS) return fail(ctx, MUSR_EINVAL, "a term needs 1..4 primitives");
     for (int m = 0; m < t.nprim; ++m) {
-      if (t.kind[m] < MUSR_PRIM_AMP || t.kind[m] > MUSR_PRIM_BESSEL)
+      if (t.kind[m] < MUSR_PRIM_AMP || t.kind[m] > MUSR_PRIM_DKT)
         return fail(ctx, MUSR_EINVAL, "unknown primitive kind");
       const int ns = musr::prim_nslots(t.kind[m]);
       for (int q = 0; q < ns; ++q)
@@ -1004,6 +1048,19 @@ int musr_set_map(musr_ctx* ctx, const int32_t* map, int nslots, int nparams, con
     for (int m = 0; m < t.nprim; ++m)
       for (int q = 0; q < musr::prim_nslots(t.kind[m]); ++q)
         if (t.slot[m][q] >= nslots) return fail(ctx, MUSR_EINVAL, "theory references a slot >= nslots");
+  {  // at most kMaxDkt distinct (Delta, nu) pairs of dynamic Kubo-Toyabe factors
+    std::vector<std::pair<int32_t, int32_t>> src;
+    for (int h = 0; h < ctx->H; ++h)
+      for (const auto& t : ctx->terms)
+        for (int m = 0; m < t.nprim; ++m) {
+          if (t.kind[m] != MUSR_PRIM_DKT) continue;
+          const std::pair<int32_t, int32_t> key(map[static_cast<size_t>(h) * nslots + t.slot[m][0]],
+                                                map[static_cast<size_t>(h) * nslots + t.slot[m][1]]);
+          if (std::find(src.begin(), src.end(), key) == src.end()) src.push_back(key);
+        }
+    if (static_cast<int>(src.size()) > musr::kMaxDkt)
+      return fail(ctx, MUSR_EINVAL, "at most 8 distinct (Delta, nu) pairs of dynamic Kubo-Toyabe factors");
+  }
   for (int i = 0; i < nconsts; ++i)
     if (!std::isfinite(consts[i])) return fail(ctx, MUSR_EINVAL, "consts must be finite");
   const size_t n = static_cast<size_t>(ctx->H) * nslots;
@@ -1202,7 +1259,10 @@ int musr_bins_in_fit(musr_ctx* ctx, int64_t* out) {
 
 int musr_launches_per_eval(musr_ctx* ctx, int* out) {
   if (!ctx || !out) return MUSR_EINVAL;
-  *out = 1;
+  bool dkt = false;  // a dynamic Kubo-Toyabe factor adds the launch that solves its tables
+  for (const auto& t : ctx->terms)
+    for (int m = 0; m < t.nprim; ++m) dkt = dkt || t.kind[m] == MUSR_PRIM_DKT;
+  *out = dkt ? 2 : 1;
   return MUSR_OK;
 }
 

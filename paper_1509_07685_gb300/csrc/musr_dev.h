@@ -32,12 +32,29 @@ constexpr int kMaxSlots = 32;
 constexpr int kMaxContrib = 64;
 
 enum StoreType : int { kStoreF32 = 1, kStoreF64 = 2 };
-enum PrimKind : int { kAmp = 1, kExp = 2, kGauss = 3, kKT = 4, kTFCos = 5, kLKT = 6, kStrExp = 7, kBessel = 8 };
+enum PrimKind : int {
+  kAmp = 1, kExp = 2, kGauss = 3, kKT = 4, kTFCos = 5, kLKT = 6, kStrExp = 7, kBessel = 8, kDKT = 9
+};
 // Parameter slots of a primitive: frequency and phase (TFCOS, BESSEL), rate and exponent
-// (STREXP), else one.
+// (STREXP), static width and fluctuation rate (DKT), else one.
 __host__ __device__ inline int prim_nslots(int kind) {
-  return kind == kTFCos || kind == kStrExp || kind == kBessel ? 2 : 1;
+  return kind == kTFCos || kind == kStrExp || kind == kBessel || kind == kDKT ? 2 : 1;
 }
+
+// Dynamic Kubo-Toyabe relaxation (DKT): the renewal equation G = f + nu f * G of the
+// strong-collision model is solved per evaluation and per distinct (Delta, nu) pair (a
+// "source") on a grid of K + 1 points over [0, span] (trapezoidal rule, Richardson
+// extrapolation from the grid and its halving), K = ceil(span max(Delta, nu, 0.05) / kDktStep)
+// clamped to [kDktMinK, kDktMaxK]; the bins interpolate the table with the cubic through the
+// four nearest points.  Table of one source: header {h, 1/h, K} then G, dG/dDelta, dG/dnu,
+// each kDktMaxK + 1 values, in the path's arithmetic type.
+constexpr int kMaxDkt = 8;        // distinct (Delta, nu) sources of one histogram set
+constexpr int kDktMaxK = 4096;
+constexpr int kDktMinK = 64;
+constexpr double kDktStep = 0.02; // grid spacing times the faster of Delta and nu
+constexpr int kDktHeader = 4;
+constexpr int kDktTable = kDktHeader + 3 * (kDktMaxK + 1);   // values per source table
+constexpr int kDktWork = 7 * (2 * kDktMaxK + 1);              // scratch values per source (finer grid)
 enum TermKind : int { kTermNone = 0, kTermPlain = 1, kTermTF = 2, kTermKT = 3, kTermLKT = 4 };
 
 // SPLIT shapes.  Every model the SPLIT path accepts is, for each histogram j of a
@@ -140,6 +157,12 @@ struct HistSet {
   float bamp[kMaxTerms];       // SPLIT basis amplitude of each term (its constant if merged, else 1)
   int ncontrib;
   Contrib contrib[kMaxContrib];
+  // dynamic Kubo-Toyabe sources: map entries of (Delta, nu) of each, and per (histogram,
+  // term, primitive) the source index or -1 ([H][kMaxTerms][kMaxPrims]); span of the tables
+  int ndkt;
+  int2 dkt_src[kMaxDkt];
+  const int* dkt_of;
+  double dkt_span;
   // parameter map
   const int32_t* map;  // [H][nslots]
   int nslots;
@@ -175,6 +198,8 @@ struct Job {
   int grad;                  // 0: value only
   int prec;                  // 0 FP64, 1 SPLIT
   const double* dir;         // [P] direction v of a Gauss-Newton product, else nullptr
+  void* dkt;                 // [ndkt][kDktTable] tables of this evaluation (double: FP64 path, float: SPLIT)
+  void* dkt_work;            // [ndkt][kDktWork] scratch of the table solve, same type
 };
 
 // Launchers (host side of musr_kernels.cu).  All enqueue on `stream`.
@@ -185,6 +210,9 @@ struct LaunchInfo {
 int launch_eval(int precision, int shape, int mode, int grad, const Job* d_jobs, int njobs,
                 int total_items, int num_sms, void* stream, LaunchInfo* info);
 int max_ctas_per_sm(int precision, int shape, int mode, int grad);
+// The dynamic Kubo-Toyabe tables of njobs evaluations of one histogram set (precision 0:
+// FP64, 1: FP32), one CTA per (job, source); enqueued on `stream` before the evaluation.
+int launch_dkt_tables(int precision, const Job* d_jobs, int njobs, int ndkt, void* stream);
 // Turns raw histogram rows copied to buf ([nhist][stride], dtype as uploaded) into the
 // stored image in place: INT32 -> FP32, zero padding beyond nbins; writes seq to *flag
 // (host-mapped) if a count is not representable (|INT32| >= 2^24, non-finite float).

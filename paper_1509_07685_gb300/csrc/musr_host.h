@@ -51,6 +51,7 @@ struct Compiled {
   std::vector<Chunk> chunks;
   std::vector<int2> items;
   std::vector<int> hist_index, col_chunk, p_ptr, p_cols;
+  std::vector<int> dkt_of;  // [H][kMaxTerms][kMaxPrims] dynamic Kubo-Toyabe source or -1
   bool uploaded = false;
   DevBuf tables;        // HistSet + all tables + map + consts, 256-byte aligned pieces
   std::vector<char> blob;  // host image of `tables`, the source of their copy
@@ -60,6 +61,7 @@ struct Compiled {
 // Buffers of the eval entry points and the cached job table of the last launch.
 struct EvalBufs {
   DevBuf params, out, partials, colsum, chunk_val, chunk_count, counters, jobs, dirs;
+  DevBuf dkt, dkt_work;  // dynamic Kubo-Toyabe tables and their solve's scratch, per evaluation
   double* h_in = nullptr;
   double* h_out = nullptr;
   size_t h_in_bytes = 0, h_out_bytes = 0;

@@ -141,6 +141,19 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
   return false;
 }
 
+// Per-thread asynchronous copies global -> shared (cp.async, documented PTX ISA): 8 bytes,
+// zero-filled beyond src_bytes; completion tracked per thread in commit groups.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, unsigned src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)),
+               "l"(__cvta_generic_to_global(src)), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Counter increment with acquire-release semantics at GPU scope (PTX atom.acq_rel).
 __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
   unsigned old;
@@ -171,6 +184,35 @@ __device__ __forceinline__ void warp_sum_ff(float& hi, float& lo) {
     hi = s;
     lo = __fadd_rn(lo, __fadd_rn(l2, e));
   }
+}
+
+// Dynamic Kubo-Toyabe relaxation of one (Delta, nu) source at time t from its table (header
+// {h, 1/h, K}, then G, dG/dDelta, dG/dnu on the grid k h): the cubic through the four nearest
+// grid points; 1 with zero derivatives for t <= 0 (the relaxation starts at time zero).
+__device__ __forceinline__ double dkt_floor(double x) { return floor(x); }
+__device__ __forceinline__ float dkt_floor(float x) { return floorf(x); }
+template <class T>
+__device__ __forceinline__ void dkt_lookup(const T* tab, T t, T* G, T* dD, T* dN) {
+  if (!(t > T(0))) {
+    *G = T(1);
+    *dD = *dN = T(0);
+    return;
+  }
+  int K = static_cast<int>(tab[2]);  // written by the table kernel earlier on the stream
+  K = K < 4 ? 4 : (K > kDktMaxK ? kDktMaxK : K);
+  const T x = t * tab[1];
+  int i = x < T(K) ? static_cast<int>(dkt_floor(x)) - 1 : K - 3;
+  i = i < 0 ? 0 : (i > K - 3 ? K - 3 : i);
+  const T u = x - static_cast<T>(i);
+  const T u1 = u - T(1), u2 = u - T(2), u3 = u - T(3);
+  const T w0 = -u1 * u2 * u3 * (T(1) / T(6)), w1 = u * u2 * u3 * T(0.5), w2 = -u * u1 * u3 * T(0.5),
+          w3 = u * u1 * u2 * (T(1) / T(6));
+  const T* g = tab + kDktHeader + i;
+  *G = fma(w0, g[0], fma(w1, g[1], fma(w2, g[2], w3 * g[3])));
+  g += kDktMaxK + 1;
+  *dD = fma(w0, g[0], fma(w1, g[1], fma(w2, g[2], w3 * g[3])));
+  g += kDktMaxK + 1;
+  *dN = fma(w0, g[0], fma(w1, g[1], fma(w2, g[2], w3 * g[3])));
 }
 
 // Local value of slot s of histogram h.
@@ -581,6 +623,10 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Smem& sm)
           const double j1x = j1(x);
           df[m][0] = -j1x * kTwoPi * t;
           df[m][1] = -j1x * kTwoPi / 360.0;
+        } else if (kind == kDKT) {  // dynamic Kubo-Toyabe: this evaluation's table of the pair
+          const int src = hs.dkt_of[(h * kMaxTerms + k) * kMaxPrims + m];
+          dkt_lookup(static_cast<const double*>(job.dkt) + static_cast<size_t>(src) * kDktTable, t, &f[m],
+                     &df[m][0], &df[m][1]);
         } else if (kind == kTFCos) {
           const double p1 = cc.loc[0][hs.raw[k].slot[m][1]];
           // Phase in turns, range-reduced exactly before sin/cos.
@@ -845,6 +891,10 @@ __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm)
           f[m] = cs;
           df[m][0] = -sn * kTwoPiF * tf;
           df[m][1] = -sn * (kTwoPiF / 360.0f);
+        } else if (kind == kDKT) {  // dynamic Kubo-Toyabe: this evaluation's FP32 table of the pair
+          const int src = hs.dkt_of[(h * kMaxTerms + k) * kMaxPrims + m];
+          dkt_lookup(static_cast<const float*>(job.dkt) + static_cast<size_t>(src) * kDktTable, tf, &f[m],
+                     &df[m][0], &df[m][1]);
         } else if (kind == kBessel) {  // J0' = -J1; the argument (not periodic) in radians
           const int j = k * kMaxPrims + m;
           const float X = fmaf(fm, cc.lstep[j], sm.ts.lbase[j]), j1x = j1f(X);
@@ -995,23 +1045,27 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
   constexpr int CHUNK_BINS = kBlock * BPT;  // bins of one CTA iteration
   // Iterations of this tile that hold any bin of the fit range (the same for every thread).
   const int iters = min(hs.tile_bins / CHUNK_BINS, (nhi - ts + CHUNK_BINS - 1) / CHUNK_BINS);
-  // FP32 counts are staged into shared memory one iteration ahead by TMA bulk copies.
+  // FP32 counts are staged into shared memory one iteration ahead, each thread copying its
+  // own two bins of every histogram (cp.async, 8 bytes) and reading back only those: no
+  // CTA-wide barrier per iteration, the warps run independently through the tile.
   const bool staged = store == kStoreF32;
   const int64_t stride = hs.stride;
-  auto issue = [&](int itn, int b) {  // one thread: the rows of iteration itn into buffer b
-    const int64_t nstart = ts + static_cast<int64_t>(itn) * CHUNK_BINS;
-    const int64_t avail = stride - nstart;  // > 0: nstart < nhi <= stride
-    const unsigned bytes = static_cast<unsigned>((avail < CHUNK_BINS ? avail : CHUNK_BINS) * sizeof(float));
-    mbar_expect_tx(&sm.bar[b], bytes * nh);
-    for (int hl = 0; hl < nh; ++hl)
-      tma_load_1d(&sm.stage[b][hl][0], static_cast<const float*>(cc.rowp[hl]) + nstart, bytes, &sm.bar[b]);
+  auto issue = [&](int itn) {  // this thread's bins of iteration itn into buffer itn & 1
+    if (itn < iters) {
+      // n is even and stride a multiple of 64, so n < stride means both bins lie in the row
+      const int64_t n = ts + static_cast<int64_t>(itn) * CHUNK_BINS + tid * BPT;
+      const bool in = n < stride;
+#pragma unroll
+      for (int hl = 0; hl < G; ++hl) {
+        if (hl >= nh) break;
+        cp_async8(&sm.stage[itn & 1][hl][tid * BPT], static_cast<const float*>(cc.rowp[hl]) + (in ? n : 0),
+                  in ? 8u : 0u);
+      }
+    }
+    cp_async_commit();  // one group per iteration (empty past the tile's end)
   };
-  int stall = 0;          // a staging wait ran out (CTA-uniform from the next iteration on)
-  unsigned inflight = 0;  // buffers holding a copy this thread has not yet seen complete
-  if (staged && iters > 0) {
-    if (tid == 0) issue(0, 0);
-    inflight = 1u;
-  }
+  const int stall = 0;  // (no waits that can run out on this path)
+  if (staged) issue(0);
   // The bin offset in the tile is carried as an exact float (integers < 2^24): an
   // int-to-float conversion per bin would occupy this GPU's slow FP64/conversion pipe.
   float fm0 = static_cast<float>(tid * BPT);
@@ -1020,23 +1074,10 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     const int n0 = ts + m0;
     const int b = it & 1;
     if (staged) {
-      if (it + 1 < iters) {
-        // Every thread is done with buffer b ^ 1 (iteration it - 1).  No copy is issued
-        // once any wait of the CTA has run out.
-        stall = __syncthreads_or(stall);
-        if (!stall) {
-          if (tid == 0) issue(it + 1, b ^ 1);
-          inflight |= 2u >> b;
-        }
-      }
-      if (inflight & (1u << b)) {
-        if (mbar_wait(&sm.bar[b], (parity >> b) & 1u)) {
-          inflight &= ~(1u << b);
-          parity ^= 1u << b;
-        } else {
-          stall = 1;
-        }
-      }
+      // buffer b ^ 1 was read by this thread in iteration it - 1: refill it for it + 1, then
+      // wait for this thread's copies of iteration it (all but the newest group)
+      issue(it + 1);
+      cp_async_wait<1>();
     }
     float t[BPT];
     bool valid[BPT];
@@ -1351,13 +1392,10 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     }
   }
 
-  // After a wait that ran out, wait once more (bounded) for every copy still in flight, so
-  // that none lands in shared memory once the CTA has moved on.
-#pragma unroll
-  for (int bb = 0; bb < 2; ++bb)
-    if ((inflight & (1u << bb)) && mbar_wait(&sm.bar[bb], (parity >> bb) & 1u)) parity ^= 1u << bb;
+  // Every copy of this thread has landed before the staging space is used again.
+  if (staged) cp_async_wait<0>();
   // ---- thread (FP32) -> warp (FP32; the value as float-float) -> CTA (FP64 trees) -> row.
-  stall = __syncthreads_or(stall);
+  __syncthreads();
   const int w = tid >> 5, lane = tid & 31;
   float vh = acc_v, vl = -acc_c;
   warp_sum_ff(vh, vl);

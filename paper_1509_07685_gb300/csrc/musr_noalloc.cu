@@ -117,6 +117,8 @@ extern "C" int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int
   for (int k = 0; k < nterms; ++k) {
     if (terms[k].nprim < 1 || terms[k].nprim > MUSR_MAX_PRIMS) return na_fail("a term needs 1..4 primitives");
     for (int m = 0; m < terms[k].nprim; ++m) {
+      if (terms[k].kind[m] == MUSR_PRIM_DKT)
+        return na_fail("the dynamic Kubo-Toyabe primitive needs tables solved per evaluation: use a context");
       if (terms[k].kind[m] < MUSR_PRIM_AMP || terms[k].kind[m] > MUSR_PRIM_BESSEL) return na_fail("unknown primitive");
       for (int q = 0; q < prim_nslots(terms[k].kind[m]); ++q)
         if (terms[k].slot[m][q] < 0 || terms[k].slot[m][q] >= nslots) return na_fail("slot index out of range");

@@ -674,6 +674,12 @@ bool copy_request(const musr_fit_request* q, Request* r, std::string* why) {
     *why = "bad mode or precision";
     return false;
   }
+  for (int k = 0; k < q->nterms; ++k)
+    for (int m = 0; m < q->terms[k].nprim && m < MUSR_MAX_PRIMS; ++m)
+      if (q->terms[k].kind[m] == MUSR_PRIM_DKT) {
+        *why = "the dynamic Kubo-Toyabe primitive needs tables solved per evaluation: fit it with a context";
+        return false;
+      }
   const size_t n = static_cast<size_t>(q->nhist) * q->nbins * dtype_size(q->dtype);
   if (q->flags & ~MUSR_REQ_BORROW_COUNTS) {
     *why = "unknown request flags";
