@@ -528,6 +528,35 @@ int pick_variant(musr_ctx* ctx, int prec, int nvec) {
   return musr::pick_decomposition(items, nvec, prec, ctx->num_sms);
 }
 
+// The vector-group schedule of a SPLIT launch of nvec evaluations (each CTA item one tile for
+// 8 evaluations, one warp each): the decomposition it would use, or -1 when the one-job
+// schedule of decomposition `var` is expected to be as fast.  Both are costed in CTA
+// iterations of 512 bins of one evaluation for the busiest CTA: one-job items of 512 << v
+// bins cost (1 << v) + 1.3, vector-group items 8 (1 << v) + kVgItemCost.  Tiles of the
+// vector-group schedule stay at or below 4096 bins: a thread then sums at most 128 bins of a
+// chunk's histograms in FP32 before the warp sum (twice the one-job kernel's 64).
+constexpr double kVgItemCost = 1.5;
+constexpr int kVgMaxVariant = 3;
+int pick_vg_variant(musr_ctx* ctx, int nvec, int var) {
+  const int grid = musr::persistent_grid(MUSR_SPLIT, ctx->num_sms);
+  auto busiest = [&](int64_t items) { return (items + grid - 1) / grid; };
+  const double one = static_cast<double>(busiest(static_cast<int64_t>(nvec) * ctx->comp[MUSR_SPLIT][var].hs.nitems)) *
+                     (static_cast<double>(1 << var) + musr::kSplitItemCost);
+  const int64_t groups = (nvec + musr::kWarps - 1) / musr::kWarps;
+  int best = -1;
+  double best_t = one;
+  for (int v = 0; v <= kVgMaxVariant; ++v) {
+    ensure_compiled(ctx, MUSR_SPLIT, v);
+    const double t = static_cast<double>(busiest(groups * ctx->comp[MUSR_SPLIT][v].hs.nitems)) *
+                     (8.0 * static_cast<double>(1 << v) + kVgItemCost);
+    if (t <= best_t) {
+      best = v;
+      best_t = t;
+    }
+  }
+  return best;
+}
+
 // Buffers for nvec evaluations; rebuilds the job table when the launch's key
 // (precision, decomposition, mode, grad, nvec, pointers) changes.
 int ensure_eval(musr_ctx* ctx, int prec, int var, int nvec) {
@@ -638,7 +667,17 @@ int check_ready(musr_ctx* ctx, int mode, int prec) {
 int enqueue_eval(musr_ctx* ctx, int prec, int mode, int grad, int nvec, const double* d_params,
                  double* d_out, const double* d_dirs = nullptr) {
   if (ctx->asym && prec == MUSR_SPLIT && mode == MUSR_CHI2) mode = 4;  // SPLIT kernels: weighted chi^2
-  const int var = pick_variant(ctx, prec, nvec);
+  int var = pick_variant(ctx, prec, nvec);
+  // A batch of SPLIT evaluations of a basis-form theory may take the vector-group schedule.
+  bool vg = false;
+  if (prec == MUSR_SPLIT && nvec >= musr::kWarps && !d_dirs && ctx->comp[prec][var].hs.ndkt == 0 &&
+      musr::has_vg(ctx->comp[prec][var].hs.shape, mode)) {
+    const int v = pick_vg_variant(ctx, nvec, var);
+    if (v >= 0) {
+      var = v;
+      vg = true;
+    }
+  }
   const HistSet& hs = ctx->comp[prec][var].hs;
   if (hs.nitems == 0) {  // no bin in the fit range: cost 0, gradient 0
     cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(double) * nvec * (1 + ctx->P), ctx->stream);
@@ -653,8 +692,11 @@ int enqueue_eval(musr_ctx* ctx, int prec, int mode, int grad, int nvec, const do
     ctx->ev.key_valid = false;
     return cuda_fail(ctx, e, "dynamic Kubo-Toyabe table launch");
   }
-  if (musr::launch_eval(prec, hs.shape, mode, grad, static_cast<const Job*>(ctx->ev.jobs.p), nvec,
-                        nvec * hs.nitems, ctx->num_sms, ctx->stream, &info)) {
+  const int lrc = vg ? musr::launch_eval_vg(hs.shape, mode, grad, static_cast<const Job*>(ctx->ev.jobs.p), nvec,
+                                            hs.nitems, ctx->num_sms, ctx->stream, &info)
+                     : musr::launch_eval(prec, hs.shape, mode, grad, static_cast<const Job*>(ctx->ev.jobs.p), nvec,
+                                         nvec * hs.nitems, ctx->num_sms, ctx->stream, &info);
+  if (lrc) {
     cudaError_t e = cudaGetLastError();
     ctx->ev.key_valid = false;
     return cuda_fail(ctx, e, "kernel launch");

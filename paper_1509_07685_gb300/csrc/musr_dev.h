@@ -210,6 +210,12 @@ struct LaunchInfo {
 int launch_eval(int precision, int shape, int mode, int grad, const Job* d_jobs, int njobs,
                 int total_items, int num_sms, void* stream, LaunchInfo* info);
 int max_ctas_per_sm(int precision, int shape, int mode, int grad);
+// The vector-group schedule of the SPLIT basis kernels (modes 0 and 1): njobs evaluations of
+// one histogram set whose decomposition has nitems work items; each CTA item is one (chunk,
+// tile) for a group of 8 jobs, one warp per job.  has_vg: whether the shape and mode have it.
+bool has_vg(int shape, int mode);
+int launch_eval_vg(int shape, int mode, int grad, const Job* d_jobs, int njobs, int nitems, int num_sms,
+                   void* stream, LaunchInfo* info);
 // The dynamic Kubo-Toyabe tables of njobs evaluations of one histogram set (precision 0:
 // FP64, 1: FP32), one CTA per (job, source); enqueued on `stream` before the evaluation.
 int launch_dkt_tables(int precision, const Job* d_jobs, int njobs, int ndkt, void* stream);

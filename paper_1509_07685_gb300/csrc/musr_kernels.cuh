@@ -225,6 +225,22 @@ __device__ __forceinline__ double slot_value(const HistSet& hs, const double* x,
 // Shared memory
 // ---------------------------------------------------------------------------------------------
 
+// One evaluation's constants of the SPLIT basis kernels on one chunk and tile: what the
+// per-bin loop reads.  The one-evaluation path keeps one in its chunk cache; the
+// vector-group path keeps one per warp (each warp evaluates its own parameter vector).
+struct VecConst {
+  // [Nbkg, Gam_0 .. Gam_{M-1}] of each histogram (16-byte rows: vector loads)
+  alignas(16) float gam[kGroupMax][kGamStride];
+  int kinds[kMaxTerms];
+  float ca[kMaxTerms], cb[kMaxTerms];  // E*X_k = ex2(-(ca t + cb t^2))  (ca includes 1/tau)
+  float dh[kMaxTerms], d2[kMaxTerms];  // KT: g = ex2(-dh t^2), u = d2 t^2
+  float shi[kMaxTerms], slo[kMaxTerms], sstep[kMaxTerms];
+  float bamp[kMaxTerms];               // amplitude carried by the basis (merged shapes), else 1
+  float base[kMaxTerms];               // phase (turns, in [-1/2, 1/2]) of each TF term at the tile's first bin
+  float tbase;                         // time of the tile's first bin
+  float aE, dt;
+};
+
 // Chunk-level constants, cached while a CTA stays on one chunk of one job.
 struct ChunkCache {
   int job, chunk;  // cache key (-1: empty)
@@ -235,8 +251,6 @@ struct ChunkCache {
   const void* roww[kGroupMax];       // first chi^2 weight of the row (asymmetry data), else nullptr
   double loc[kGroupMax][kMaxSlots];  // local slot values (FP64)
   double ldir[kGroupMax][kMaxSlots]; // local slot components of a Gauss-Newton direction (else 0)
-  // SPLIT: [Nbkg, Gam_0 .. Gam_{M-1}] of each histogram (16-byte rows: vector loads)
-  alignas(16) float gam[kGroupMax][kGamStride];
   double cph[kGroupMax][kMaxTerms], sph[kGroupMax][kMaxTerms];  // cos, sin of each cosine term's phase
   // SPLIT Gauss-Newton products: [v_Nbkg, dGam_0 .. dGam_{M-1}] along the direction v, and per
   // term the directional derivatives of its exponent rates (-t dLambda - t^2 dSigma), of its
@@ -247,30 +261,24 @@ struct ChunkCache {
   // (bin offset < 2^14) * lhi is exact in FP32
   float lhi[kMaxTerms * kMaxPrims], llo[kMaxTerms * kMaxPrims], lstep[kMaxTerms * kMaxPrims];
   float dlam[kMaxTerms], dsig[kMaxTerms], dnu[kMaxTerms], ddel[kMaxTerms];
-  // SPLIT per-term constants of the chunk
-  int kinds[kMaxTerms];
-  float ca[kMaxTerms], cb[kMaxTerms];  // E*X_k = ex2(-(ca t + cb t^2))  (ca includes 1/tau)
-  float dh[kMaxTerms], d2[kMaxTerms];  // KT: g = ex2(-dh t^2), u = d2 t^2
-  float shi[kMaxTerms], slo[kMaxTerms], sstep[kMaxTerms];
-  float bamp[kMaxTerms];               // amplitude carried by the basis (merged shapes), else 1
   double nu[kMaxTerms];
-  float aE, dt;
+  VecConst v;  // the SPLIT basis kernels' constants of this job
 };
 
 struct TileState {
   int tile_start;
+  // term lists without a basis form: the tile's first bin time, and per (term, primitive) the
+  // cosine's phase at the tile's first bin (turns, in [-1/2, 1/2]) or the Bessel argument there
+  // (radians)
   float tbase;
-  float base[kMaxTerms];  // phase (turns, in [-1/2, 1/2]) of each TF term at the tile's first bin
-  // term lists without a basis form, per (term, primitive): the cosine's phase at the tile's
-  // first bin (turns, in [-1/2, 1/2]) or the Bessel argument there (radians)
   float lbase[kMaxTerms * kMaxPrims];
 };
 
 struct Smem {
-  // SPLIT, FP32 counts: the rows of the current and the next CTA iteration, staged
-  // by TMA bulk copies (one per histogram row segment), one mbarrier per buffer.
+  // SPLIT, FP32 counts: the rows of the current and the next CTA iteration, each thread's two
+  // bins of every histogram copied by that thread (cp.async)
   alignas(128) float stage[2][kGroupMax][kBlock * kBinsPerThread];
-  unsigned long long bar[2];
+  __device__ float* stage_slot(int b, int hl, int /*warp*/, int bin) { return &stage[b][hl][bin]; }
   ChunkCache cc;
   TileState ts;
   float cred[kWarps][kMaxChan];  // per-warp FP32 channel sums
@@ -342,12 +350,98 @@ __device__ __forceinline__ void phase_cs(double phi_deg, double* c, double* s) {
   *s = sf;
 }
 
+// Coefficients [Nbkg, Gam_0 .. Gam_{M-1}] of one histogram's basis expansion from its slot
+// values slot(s), computed in FP64 and rounded once; cos and sin of each cosine term's phase.
+template <int SHAPE, class Slot>
+__device__ void coef_row(const HistSet& hs, Slot slot, float* gam, double* cph, double* sph) {
+  using Bs = Basis<SHAPE>;
+  double g[kGamStride];
+#pragma unroll
+  for (int i = 0; i < kGamStride; ++i) g[i] = 0.0;
+  const double N0 = slot(0);
+  g[0] = slot(1);
+  g[1] = hs.envelope ? N0 : 0.0;  // the basis function E carries the 1 of (1 + A)
+#pragma unroll
+  for (int k = 0; k < kMaxTerms; ++k) {
+    double c = 1.0, sn = 0.0;
+    if (k < hs.nterms && hs.canon[k].kind == kTermTF) phase_cs(slot(hs.canon[k].phi_slot), &c, &sn);
+    cph[k] = c;
+    sph[k] = sn;
+  }
+  if (Bs::MERGED) {  // one phase per histogram: that of the first cosine term
+    g[2] = N0 * cph[0];
+    g[3] = -N0 * sph[0];
+  } else {
+#pragma unroll
+    for (int k = 0; k < Bs::NT; ++k) {
+      if (k >= hs.nterms) break;
+      const CanonTerm& ct = hs.canon[k];
+      const double a = ct.amp_slot >= 0 ? slot(ct.amp_slot) : 1.0;
+      if (ct.kind == kTermTF) {
+        g[1 + Bs::bc(k)] = N0 * a * cph[k];
+        g[1 + Bs::bs(k)] = -N0 * a * sph[k];
+      } else {
+        g[1 + Bs::bc(k)] = N0 * a;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kGamStride; ++i) gam[i] = static_cast<float>(g[i]);
+}
+
+// Constants of term k shared by a chunk's histograms (from the slot values slot(s) of its
+// first histogram): its kind, exponent rates, Kubo-Toyabe width and phase step per bin.
+// Returns the term's frequency (MHz; 0 without a cosine).
+template <class Slot>
+__device__ double term_consts(const HistSet& hs, Slot slot, int k, VecConst& v) {
+  v.kinds[k] = k < hs.nterms ? hs.canon[k].kind : kTermNone;
+  v.ca[k] = v.cb[k] = v.d2[k] = v.dh[k] = v.shi[k] = v.slo[k] = v.sstep[k] = 0.0f;
+  v.bamp[k] = 1.0f;
+  if (k >= hs.nterms) return 0.0;
+  const CanonTerm& ct = hs.canon[k];
+  float lam = 0.0f, S = 0.0f;
+  for (int i = 0; i < ct.nexp; ++i) lam += static_cast<float>(slot(ct.exp_slot[i]));
+  for (int i = 0; i < ct.ngauss; ++i) {
+    const float sg = static_cast<float>(slot(ct.gauss_slot[i]));
+    S = fmaf(sg, sg, S);
+  }
+  v.bamp[k] = hs.bamp[k];
+  // the term's exponent carries the decay envelope E = exp(-t / tau_mu) (none for the
+  // asymmetry model)
+  v.ca[k] = kLog2eF * ((hs.envelope ? static_cast<float>(1.0 / kTauMuUs) : 0.0f) + lam);
+  v.cb[k] = kLog2eF * 0.5f * S;
+  if (ct.kind == kTermKT) {
+    const float D = static_cast<float>(slot(ct.kt_slot));
+    v.d2[k] = D * D;
+    v.dh[k] = kLog2eF * 0.5f * D * D;
+  } else if (ct.kind == kTermLKT) {  // g = ex2(-dh t) = exp(-a t), u = d2 t = a t
+    const float a = static_cast<float>(slot(ct.kt_slot));
+    v.d2[k] = a;
+    v.dh[k] = kLog2eF * a;
+  }
+  if (ct.kind != kTermTF) return 0.0;
+  const double nu = slot(ct.nu_slot);
+  const double step = nu * hs.dt_us;  // turns per bin (FP64)
+  // Exact split: hi keeps 10 significant bits, so (bin offset < 2^14) * hi is exact in FP32.
+  const float hi = __uint_as_float(__float_as_uint(static_cast<float>(step)) & 0xFFFFC000u);
+  v.shi[k] = hi;
+  v.slo[k] = static_cast<float>(step - static_cast<double>(hi));
+  v.sstep[k] = static_cast<float>(step);
+  return nu;
+}
+
+// Phase (turns, reduced to [-1/2, 1/2] in FP64) of a cosine of frequency nu at time t_start.
+__device__ __forceinline__ float tile_phase(double nu, double t_start) {
+  const double x = nu * t_start;
+  return static_cast<float>(x - rint(x));
+}
+
 // ---------------------------------------------------------------------------------------------
 // Chunk cache fill (only when a CTA moves to another chunk or job).
 // ---------------------------------------------------------------------------------------------
-template <int SHAPE>
+template <int SHAPE, class SM>
 __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int chunk_index, int prec,
-                           Smem& sm) {
+                           SM& sm) {
   using Bs = Basis<SHAPE>;
   ChunkCache& cc = sm.cc;
   const int tid = threadIdx.x;
@@ -385,40 +479,9 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
   if (prec == 0) return;
   const double dt = hs.dt_us;
   if (tid < nh) {
-    // Coefficients of the histogram's basis expansion, computed in FP64 and rounded once.
     const int hl = tid;
-    double g[kGamStride];
-#pragma unroll
-    for (int i = 0; i < kGamStride; ++i) g[i] = 0.0;
+    coef_row<SHAPE>(hs, [&](int q) { return cc.loc[hl][q]; }, cc.v.gam[hl], cc.cph[hl], cc.sph[hl]);
     const double N0 = cc.loc[hl][0];
-    g[0] = cc.loc[hl][1];
-    g[1] = hs.envelope ? N0 : 0.0;  // the basis function E carries the 1 of (1 + A)
-#pragma unroll
-    for (int k = 0; k < kMaxTerms; ++k) {
-      double c = 1.0, sn = 0.0;
-      if (k < hs.nterms && hs.canon[k].kind == kTermTF) phase_cs(cc.loc[hl][hs.canon[k].phi_slot], &c, &sn);
-      cc.cph[hl][k] = c;
-      cc.sph[hl][k] = sn;
-    }
-    if (Bs::MERGED) {  // one phase per histogram: that of the first cosine term
-      g[2] = N0 * cc.cph[hl][0];
-      g[3] = -N0 * cc.sph[hl][0];
-    } else {
-#pragma unroll
-      for (int k = 0; k < Bs::NT; ++k) {
-        if (k >= hs.nterms) break;
-        const CanonTerm& ct = hs.canon[k];
-        const double a = ct.amp_slot >= 0 ? cc.loc[hl][ct.amp_slot] : 1.0;
-        if (ct.kind == kTermTF) {
-          g[1 + Bs::bc(k)] = N0 * a * cc.cph[hl][k];
-          g[1 + Bs::bs(k)] = -N0 * a * cc.sph[hl][k];
-        } else {
-          g[1 + Bs::bc(k)] = N0 * a;
-        }
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < kGamStride; ++i) cc.gam[hl][i] = static_cast<float>(g[i]);
     // Directional derivative of the coefficients along a Gauss-Newton direction (zeros without).
     double gd[kGamStride];
 #pragma unroll
@@ -456,80 +519,39 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
     for (int i = 0; i < kGamStride; ++i) cc.gdot[hl][i] = static_cast<float>(gd[i]);
   } else if (tid >= 32 && tid < 32 + kMaxTerms) {
     const int k = tid - 32;
-    cc.kinds[k] = k < hs.nterms ? hs.canon[k].kind : kTermNone;
-    if (k < hs.nterms) {
+    cc.nu[k] = term_consts(hs, [&](int q) { return cc.loc[0][q]; }, k, cc.v);
+    if (k < hs.nterms) {  // directional derivatives of the term's shared parameters (Gauss-Newton products)
       const CanonTerm& ct = hs.canon[k];
-      float lam = 0.0f, S = 0.0f;
-      for (int i = 0; i < ct.nexp; ++i) lam += static_cast<float>(cc.loc[0][ct.exp_slot[i]]);
-      for (int i = 0; i < ct.ngauss; ++i) {
-        const float sg = static_cast<float>(cc.loc[0][ct.gauss_slot[i]]);
-        S = fmaf(sg, sg, S);
-      }
-      cc.bamp[k] = hs.bamp[k];
-      {  // directional derivatives of the term's shared parameters (Gauss-Newton products)
-        double dl = 0.0, ds = 0.0;
-        for (int i = 0; i < ct.nexp; ++i) dl += cc.ldir[0][ct.exp_slot[i]];
-        for (int i = 0; i < ct.ngauss; ++i) ds += cc.loc[0][ct.gauss_slot[i]] * cc.ldir[0][ct.gauss_slot[i]];
-        cc.dlam[k] = static_cast<float>(dl);
-        cc.dsig[k] = static_cast<float>(ds);
-        cc.dnu[k] = ct.kind == kTermTF ? static_cast<float>(cc.ldir[0][ct.nu_slot]) : 0.0f;
-        cc.ddel[k] = ct.kind == kTermKT
-                         ? static_cast<float>((2.0 / 3.0) * cc.loc[0][ct.kt_slot] * cc.ldir[0][ct.kt_slot])
-                         : (ct.kind == kTermLKT ? static_cast<float>((2.0 / 3.0) * cc.ldir[0][ct.kt_slot]) : 0.0f);
-      }
-      // the term's exponent carries the decay envelope E = exp(-t / tau_mu) (none for the
-      // asymmetry model)
-      cc.ca[k] = kLog2eF * ((hs.envelope ? static_cast<float>(1.0 / kTauMuUs) : 0.0f) + lam);
-      cc.cb[k] = kLog2eF * 0.5f * S;
-      if (ct.kind == kTermKT) {
-        const float D = static_cast<float>(cc.loc[0][ct.kt_slot]);
-        cc.d2[k] = D * D;
-        cc.dh[k] = kLog2eF * 0.5f * D * D;
-      } else if (ct.kind == kTermLKT) {  // g = ex2(-dh t) = exp(-a t), u = d2 t = a t
-        const float a = static_cast<float>(cc.loc[0][ct.kt_slot]);
-        cc.d2[k] = a;
-        cc.dh[k] = kLog2eF * a;
-      } else {
-        cc.d2[k] = cc.dh[k] = 0.0f;
-      }
-      if (ct.kind == kTermTF) {
-        const double nu = cc.loc[0][ct.nu_slot];
-        const double step = nu * dt;  // turns per bin (FP64)
-        // Exact split: hi keeps 10 significant bits, so (bin offset < 2^14) * hi is exact in FP32.
-        const float hi = __uint_as_float(__float_as_uint(static_cast<float>(step)) & 0xFFFFC000u);
-        cc.shi[k] = hi;
-        cc.slo[k] = static_cast<float>(step - static_cast<double>(hi));
-        cc.sstep[k] = static_cast<float>(step);
-        cc.nu[k] = nu;
-      } else {
-        cc.shi[k] = cc.slo[k] = cc.sstep[k] = 0.0f;
-        cc.nu[k] = 0.0;
-      }
+      double dl = 0.0, ds = 0.0;
+      for (int i = 0; i < ct.nexp; ++i) dl += cc.ldir[0][ct.exp_slot[i]];
+      for (int i = 0; i < ct.ngauss; ++i) ds += cc.loc[0][ct.gauss_slot[i]] * cc.ldir[0][ct.gauss_slot[i]];
+      cc.dlam[k] = static_cast<float>(dl);
+      cc.dsig[k] = static_cast<float>(ds);
+      cc.dnu[k] = ct.kind == kTermTF ? static_cast<float>(cc.ldir[0][ct.nu_slot]) : 0.0f;
+      cc.ddel[k] = ct.kind == kTermKT
+                       ? static_cast<float>((2.0 / 3.0) * cc.loc[0][ct.kt_slot] * cc.ldir[0][ct.kt_slot])
+                       : (ct.kind == kTermLKT ? static_cast<float>((2.0 / 3.0) * cc.ldir[0][ct.kt_slot]) : 0.0f);
     }
   } else if (tid == 64) {
     // log2(e) / tau_mu: E = 2^(-aE t); without the decay envelope E = 1
-    cc.aE = hs.envelope ? static_cast<float>(1.4426950408889634 / kTauMuUs) : 0.0f;
-    cc.dt = static_cast<float>(dt);
+    cc.v.aE = hs.envelope ? static_cast<float>(1.4426950408889634 / kTauMuUs) : 0.0f;
+    cc.v.dt = static_cast<float>(dt);
   }
   __syncthreads();
 }
 
 // Tile-level constants: the tile's first bin time and, in FP64, each precession
 // phase at that bin reduced to [-1/2, 1/2] turns.
-__device__ void load_tile(const HistSet& hs, int tile, int prec, Smem& sm) {
+template <class SM>
+__device__ void load_tile(const HistSet& hs, int tile, int prec, SM& sm) {
   const int tid = threadIdx.x;
   if (tid == 0) sm.ts.tile_start = sm.cc.tile0 + tile * hs.tile_bins;
   if (prec == 1 && tid >= 32 && tid < 32 + kMaxTerms) {
     const int k = tid - 32;
     const int ts = sm.cc.tile0 + tile * hs.tile_bins;
     const double t_start = (static_cast<double>(ts) - sm.cc.t0) * hs.dt_us;
-    if (k == 0) sm.ts.tbase = static_cast<float>(t_start);
-    float b = 0.0f;
-    if (sm.cc.kinds[k] == kTermTF) {
-      const double x = sm.cc.nu[k] * t_start;
-      b = static_cast<float>(x - rint(x));
-    }
-    sm.ts.base[k] = b;
+    if (k == 0) sm.cc.v.tbase = static_cast<float>(t_start);
+    sm.cc.v.base[k] = sm.cc.v.kinds[k] == kTermTF ? tile_phase(sm.cc.nu[k], t_start) : 0.0f;
   }
   __syncthreads();
 }
@@ -1011,8 +1033,12 @@ __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm)
 // u = d(cost/2)/dN, then the channels G_m += u B_m, W += u and the per-bin sums
 // V_m = sum_j u_j Gam_jm that carry the shared time parameters' derivatives.
 // ---------------------------------------------------------------------------------------------
-template <int SHAPE, int MODE, bool GRAD>
-__device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm, uint32_t& parity) {
+// VG: the vector-group schedule -- each warp evaluates its own job (parameter vector) on the
+// tile, 64 bins per iteration, with vc that job's constants, and writes the item's row of its
+// job itself; otherwise the CTA's 8 warps share one job, 512 bins per iteration, and the row
+// is the FP64 sum of the 8 warps' partial sums.
+template <int SHAPE, int MODE, bool GRAD, bool VG, class SM>
+__device__ void split_item(const Job& job, const HistSet& hs, int item, SM& sm, const VecConst& vc) {
   using Bs = Basis<SHAPE>;
   constexpr int NT = Bs::NT;
   constexpr int M = Bs::M;
@@ -1027,7 +1053,9 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
   const int tid = threadIdx.x;
   const int nh = cc.nh, nlo = cc.nlo, nhi = cc.nhi, ts = sm.ts.tile_start;
   const int nterms = Bs::NTF < 0 ? hs.nterms : NT;
-  const float aE = cc.aE, tbase = sm.ts.tbase, dtf = cc.dt;
+  const float aE = vc.aE, tbase = vc.tbase, dtf = vc.dt;
+  const int lane = tid & 31, w = tid >> 5;
+  const int tb = VG ? lane : tid;  // the thread's position in an iteration's bins
   const int store = hs.store;
 
   float acc_v = 0.0f, acc_c = 0.0f;  // Kahan-compensated cost value
@@ -1042,7 +1070,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
 #pragma unroll
     for (int q = 0; q < 4; ++q) sh[k][q] = 0.0f;
 
-  constexpr int CHUNK_BINS = kBlock * BPT;  // bins of one CTA iteration
+  constexpr int CHUNK_BINS = (VG ? 32 : kBlock) * BPT;  // bins of one iteration
   // Iterations of this tile that hold any bin of the fit range (the same for every thread).
   const int iters = min(hs.tile_bins / CHUNK_BINS, (nhi - ts + CHUNK_BINS - 1) / CHUNK_BINS);
   // FP32 counts are staged into shared memory one iteration ahead, each thread copying its
@@ -1053,12 +1081,12 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
   auto issue = [&](int itn) {  // this thread's bins of iteration itn into buffer itn & 1
     if (itn < iters) {
       // n is even and stride a multiple of 64, so n < stride means both bins lie in the row
-      const int64_t n = ts + static_cast<int64_t>(itn) * CHUNK_BINS + tid * BPT;
+      const int64_t n = ts + static_cast<int64_t>(itn) * CHUNK_BINS + tb * BPT;
       const bool in = n < stride;
 #pragma unroll
       for (int hl = 0; hl < G; ++hl) {
         if (hl >= nh) break;
-        cp_async8(&sm.stage[itn & 1][hl][tid * BPT], static_cast<const float*>(cc.rowp[hl]) + (in ? n : 0),
+        cp_async8(sm.stage_slot(itn & 1, hl, w, tb * BPT), static_cast<const float*>(cc.rowp[hl]) + (in ? n : 0),
                   in ? 8u : 0u);
       }
     }
@@ -1068,9 +1096,9 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
   if (staged) issue(0);
   // The bin offset in the tile is carried as an exact float (integers < 2^24): an
   // int-to-float conversion per bin would occupy this GPU's slow FP64/conversion pipe.
-  float fm0 = static_cast<float>(tid * BPT);
+  float fm0 = static_cast<float>(tb * BPT);
   for (int it = 0; it < iters; ++it, fm0 += static_cast<float>(CHUNK_BINS)) {
-    const int m0 = it * CHUNK_BINS + tid * BPT;  // offset in the tile (< 2^14)
+    const int m0 = it * CHUNK_BINS + tb * BPT;  // offset in the tile (< 2^14)
     const int n0 = ts + m0;
     const int b = it & 1;
     if (staged) {
@@ -1097,22 +1125,22 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
 #pragma unroll
       for (int j = 0; j < BPT; ++j) Pc[k][j] = Ps[k][j] = dK[k][j] = 0.0f;
       if (k >= nterms) continue;
-      const float ca = cc.ca[k], cb = cc.cb[k], ba = cc.bamp[k];
-      const bool istf = Bs::tf(cc.kinds, k);
-      const bool iskt = !istf && cc.kinds[k] == kTermKT;
-      const bool islkt = !istf && cc.kinds[k] == kTermLKT;
+      const float ca = vc.ca[k], cb = vc.cb[k], ba = vc.bamp[k];
+      const bool istf = Bs::tf(vc.kinds, k);
+      const bool iskt = !istf && vc.kinds[k] == kTermKT;
+      const bool islkt = !istf && vc.kinds[k] == kTermLKT;
 #pragma unroll
       for (int j = 0; j < BPT; ++j) {
         float X = __fmul_rn(ba, ex2a(__fmul_rn(-fmaf(cb, t[j], ca), t[j])));  // a E X_k
         if (iskt) {
           const float tt = __fmul_rn(t[j], t[j]);
-          const float g = ex2a(__fmul_rn(-cc.dh[k], tt));
-          const float u = __fmul_rn(cc.d2[k], tt);
+          const float g = ex2a(__fmul_rn(-vc.dh[k], tt));
+          const float u = __fmul_rn(vc.d2[k], tt);
           dK[k][j] = X * tt * g * (u - 3.0f);
           X = __fmul_rn(X, fmaf(__fmul_rn(2.0f / 3.0f, __fsub_rn(1.0f, u)), g, 1.0f / 3.0f));
         } else if (islkt) {  // static Lorentzian Kubo-Toyabe
-          const float g = ex2a(__fmul_rn(-cc.dh[k], t[j]));
-          const float u = __fmul_rn(cc.d2[k], t[j]);
+          const float g = ex2a(__fmul_rn(-vc.dh[k], t[j]));
+          const float u = __fmul_rn(vc.d2[k], t[j]);
           dK[k][j] = X * t[j] * g * (u - 2.0f);
           X = __fmul_rn(X, fmaf(__fmul_rn(2.0f / 3.0f, __fsub_rn(1.0f, u)), g, 1.0f / 3.0f));
         }
@@ -1120,13 +1148,13 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
       }
       if (istf) {
         // Phase (turns) of the thread's first bin: base + m0 * step, reduced exactly.
-        float f = __fmul_rn(fm0, cc.shi[k]);
+        float f = __fmul_rn(fm0, vc.shi[k]);
         f = __fsub_rn(f, rint_small(f));
-        float r = __fadd_rn(fmaf(fm0, cc.slo[k], sm.ts.base[k]), f);
+        float r = __fadd_rn(fmaf(fm0, vc.slo[k], vc.base[k]), f);
         r = __fsub_rn(r, rint_small(r));
 #pragma unroll
         for (int j = 0; j < BPT; ++j) {
-          float rj = fmaf(static_cast<float>(j), cc.sstep[k], r);
+          float rj = fmaf(static_cast<float>(j), vc.sstep[k], r);
           rj = __fsub_rn(rj, rint_small(rj));  // |rj| <= 1/2: sin/cos arguments in [-pi, pi]
           const float a = __fmul_rn(rj, kTwoPiF);
           Ps[k][j] = __fmul_rn(Pc[k][j], sina(a));
@@ -1143,7 +1171,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
       if (k >= nterms) continue;
-      const bool istf = Bs::tf(cc.kinds, k);
+      const bool istf = Bs::tf(vc.kinds, k);
 #pragma unroll
       for (int j = 0; j < BPT; ++j) {
         if (Bs::MERGED) {
@@ -1171,7 +1199,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
 #pragma unroll
       for (int k = 0; k < NT; ++k) {
         if (k >= nterms) continue;
-        const bool istf = Bs::tf(cc.kinds, k);
+        const bool istf = Bs::tf(vc.kinds, k);
 #pragma unroll
         for (int j = 0; j < BPT; ++j) {
           const float g = -t[j] * fmaf(t[j], cc.dsig[k], cc.dlam[k]);  // d ln(X_k) along v
@@ -1224,26 +1252,29 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     };
     auto fetch = [&](int hl, float (&d)[BPT], float (&gm)[4 * NG4]) {
       if (staged) {
-        const float2 q = *reinterpret_cast<const float2*>(&sm.stage[b][hl][tid * BPT]);
+        const float2 q = *reinterpret_cast<const float2*>(sm.stage_slot(b, hl, w, tb * BPT));
         d[0] = q.x;
         d[1] = q.y;
       } else if (hl < nh) {
-        const double2 q =
-            __ldg(reinterpret_cast<const double2*>(static_cast<const double*>(cc.rowp[hl]) + n0));
+        // n0 is even and the row stride a multiple of 64: n0 < stride holds both bins
+        const double2 q = n0 < stride ? __ldg(reinterpret_cast<const double2*>(
+                                            static_cast<const double*>(cc.rowp[hl]) + n0))
+                                      : make_double2(0.0, 0.0);
         d[0] = static_cast<float>(q.x);
         d[1] = static_cast<float>(q.y);
       }
 #pragma unroll
       for (int q = 0; q < NG4; ++q) {
-        const float4 x = *reinterpret_cast<const float4*>(&cc.gam[hl][4 * q]);
+        const float4 x = *reinterpret_cast<const float4*>(&vc.gam[hl][4 * q]);
         gm[4 * q] = x.x;
         gm[4 * q + 1] = x.y;
         gm[4 * q + 2] = x.z;
         gm[4 * q + 3] = x.w;
       }
     };
-    auto fetch_w = [&](int hl) {  // the thread's two weights of histogram hl < nh
-      return __ldg(reinterpret_cast<const float2*>(static_cast<const float*>(cc.roww[hl]) + n0));
+    auto fetch_w = [&](int hl) {  // the thread's two weights of histogram hl < nh (0 past the row)
+      return n0 < stride ? __ldg(reinterpret_cast<const float2*>(static_cast<const float*>(cc.roww[hl]) + n0))
+                         : make_float2(0.0f, 0.0f);
     };
     auto hist_loop = [&](auto masked_tag) {
       constexpr bool MASKED = decltype(masked_tag)::value;
@@ -1374,7 +1405,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
 #pragma unroll
         for (int k = 0; k < NT; ++k) {
           if (k >= nterms) continue;
-          const bool istf = Bs::tf(cc.kinds, k);
+          const bool istf = Bs::tf(vc.kinds, k);
           const float Vc = V[Bs::bc(k)][j];
           float D;
           if (Bs::NTF < 0 || k < Bs::NTF) {
@@ -1394,11 +1425,37 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
 
   // Every copy of this thread has landed before the staging space is used again.
   if (staged) cp_async_wait<0>();
-  // ---- thread (FP32) -> warp (FP32; the value as float-float) -> CTA (FP64 trees) -> row.
-  __syncthreads();
-  const int w = tid >> 5, lane = tid & 31;
   float vh = acc_v, vl = -acc_c;
   warp_sum_ff(vh, vl);
+  if constexpr (VG) {
+    // ---- thread (FP32) -> warp (FP32; the value as float-float) -> the job's row (FP64)
+    double* row = job.partials + static_cast<int64_t>(item) * hs.pstride;
+    if (GRAD) {
+#pragma unroll
+      for (int hl = 0; hl < G; ++hl)
+#pragma unroll
+        for (int q = 0; q < NPH; ++q) {
+          const float r = warp_sum_f(gacc[hl][q]);
+          if (lane == (hl * NPH + q) % 32) row[1 + hl * NPH + q] = static_cast<double>(r);
+        }
+#pragma unroll
+      for (int k = 0; k < NT; ++k)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float r = warp_sum_f(sh[k][q]);
+          if (lane == (G * NPH + k * 4 + q) % 32) row[1 + G * NPH + k * 4 + q] = static_cast<double>(r);
+        }
+    }
+    if (lane == 0) {
+      const double a = static_cast<double>(vh) + static_cast<double>(vl);
+      // +inf: the likelihood is undefined (N <= 0 where d > 0) or the parameters were not finite
+      row[0] = isfinite(a) ? a * (MODE == 0 || MODE == 4 ? 1.0 : 2.0) : __longlong_as_double(0x7ff0000000000000LL);
+    }
+    (void)stall;
+    return;
+  } else {
+  // ---- thread (FP32) -> warp (FP32; the value as float-float) -> CTA (FP64 trees) -> row.
+  __syncthreads();
   if (lane == 0) {
     sm.vred[w][0] = vh;
     sm.vred[w][1] = vl;
@@ -1434,12 +1491,12 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     double a = l < kWarps ? static_cast<double>(sm.vred[l][0]) + static_cast<double>(sm.vred[l][1]) : 0.0;
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    // NaN: a staging wait ran out (the host reports a timeout); +inf: the likelihood is
-    // undefined (N <= 0 where d > 0) or the parameters were not finite.
+    // +inf: the likelihood is undefined (N <= 0 where d > 0) or the parameters were not finite.
     if (l == 0)
       row[0] = stall ? __longlong_as_double(0x7ff8000000000000LL)
                      : (isfinite(a) ? a * (MODE == 0 || MODE == 4 ? 1.0 : 2.0)
                                     : __longlong_as_double(0x7ff0000000000000LL));
+  }
   }
 }
 
@@ -1518,8 +1575,8 @@ __device__ double split_slot(const HistSet& hs, const ChunkCache& cc, const doub
 // ---------------------------------------------------------------------------------------------
 // Completion: chunk finalize, then job finalize.
 // ---------------------------------------------------------------------------------------------
-template <int PREC, int SHAPE, bool GRAD>
-__device__ void chunk_finalize(const Job& job, const HistSet& hs, Smem& sm) {
+template <int PREC, int SHAPE, bool GRAD, class SM>
+__device__ void chunk_finalize(const Job& job, const HistSet& hs, SM& sm) {
   const ChunkCache& cc = sm.cc;
   const int tid = threadIdx.x;
   const int ps = hs.pstride;
@@ -1574,7 +1631,8 @@ __device__ void chunk_finalize(const Job& job, const HistSet& hs, Smem& sm) {
   }
 }
 
-__device__ void job_finalize(const Job& job, const HistSet& hs, Smem& sm) {
+template <class SM>
+__device__ void job_finalize(const Job& job, const HistSet& hs, SM& sm) {
   const int tid = threadIdx.x;
   double v = 0.0;
   for (int c = tid; c < hs.nchunks; c += kBlock) v += __ldcg(job.chunk_val + c);
@@ -1606,20 +1664,12 @@ __device__ void job_finalize(const Job& job, const HistSet& hs, Smem& sm) {
   }
 }
 
-// Publishes the item's row; the CTA that completes a chunk's last item finalizes the
-// chunk, and the one that completes a job's last chunk finalizes the job.  Release: the
-// CTA barrier orders every thread's row writes before thread 0's acquire-release counter
-// increment (cumulative over what the barrier ordered before it); acquire: that same
-// atomic, and a fence by every thread of the finalizing CTA.
-template <int PREC, int SHAPE, bool GRAD>
-__device__ void complete_item(const Job& job, const HistSet& hs, Smem& sm) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned prev = atom_add_acq_rel(job.chunk_count + sm.cc.chunk, 1u);
-    sm.flag = prev == static_cast<unsigned>(sm.cc.ntiles - 1);
-  }
-  __syncthreads();
-  if (!sm.flag) return;
+// The chunk of a job whose last row has just been published: the CTA sums the chunk's rows
+// (chunk finalize) and, if that chunk was the job's last, the job's chunks (job finalize).
+// Acquire: every thread fences after the acquire-release counter increment that found the
+// chunk complete.
+template <int PREC, int SHAPE, bool GRAD, class SM>
+__device__ void finish_chunk(const Job& job, const HistSet& hs, SM& sm) {
   fence_acq_rel();
   chunk_finalize<PREC, SHAPE, GRAD>(job, hs, sm);
   __syncthreads();
@@ -1639,6 +1689,172 @@ __device__ void complete_item(const Job& job, const HistSet& hs, Smem& sm) {
   __syncthreads();
 }
 
+// Publishes the item's row; the CTA that completes a chunk's last item finalizes the
+// chunk, and the one that completes a job's last chunk finalizes the job.  Release: the
+// CTA barrier orders every thread's row writes before thread 0's acquire-release counter
+// increment (cumulative over what the barrier ordered before it); acquire: that same
+// atomic, and a fence by every thread of the finalizing CTA.
+template <int PREC, int SHAPE, bool GRAD>
+__device__ void complete_item(const Job& job, const HistSet& hs, Smem& sm) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atom_add_acq_rel(job.chunk_count + sm.cc.chunk, 1u);
+    sm.flag = prev == static_cast<unsigned>(sm.cc.ntiles - 1);
+  }
+  __syncthreads();
+  if (!sm.flag) return;
+  finish_chunk<PREC, SHAPE, GRAD>(job, hs, sm);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Vector-group schedule (SPLIT basis shapes, large batches of one histogram set): a work item
+// is (chunk, tile, group of 8 jobs); warp w evaluates job 8 g + w on the tile, so the 8 warps
+// of a CTA read the same counts (one L1/L2 fetch serves 8 parameter vectors), keep no
+// cross-warp reduction, and each writes its job's row for the item.  Items are numbered
+// tile-major (the groups of one tile consecutive) and taken round-robin by the persistent
+// CTAs, so the CTAs running at any moment work on a few tiles and every tile of counts
+// comes from DRAM about once per launch.
+// ---------------------------------------------------------------------------------------------
+constexpr int kVgBins = 32 * kBinsPerThread;  // bins of one warp iteration
+
+struct SmemVG {
+  // each warp's threads' bins of every histogram, current and next iteration (cp.async)
+  alignas(128) float stage[kWarps][2][kGroupMax][kVgBins];
+  __device__ float* stage_slot(int b, int hl, int w, int bin) { return &stage[w][b][hl][bin]; }
+  ChunkCache cc;           // the chunk's shared fields; the per-job fields for one job's finalize
+  TileState ts;
+  VecConst vg[kWarps];     // the constants of each warp's job
+  double tot[kMaxChan + 1];
+  double wsum[kWarps];
+  int flag;
+  int last[kWarps];        // which of the group's jobs completed the chunk with this item
+};
+
+// The chunk's shared fields, the row pointers, and the constants of jobs j0 .. j0 + nj - 1
+// on tile `tile` (one thread per (job, histogram) coefficient row, one per (job, term)).
+template <int SHAPE>
+__device__ void load_group(const Job* jobs, int j0, int nj, const HistSet& hs, int chunk_index, int tile,
+                           SmemVG& sm) {
+  ChunkCache& cc = sm.cc;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    const Chunk ch = hs.chunks[chunk_index];
+    cc.job = -1;  // the per-job fields are not this chunk's
+    cc.chunk = chunk_index;
+    cc.nh = ch.nh;
+    cc.nlo = ch.nlo;
+    cc.nhi = ch.nhi;
+    cc.tile0 = ch.tile0;
+    cc.item0 = ch.item0;
+    cc.ntiles = ch.ntiles;
+    cc.col0 = ch.col0;
+    cc.first = ch.first;
+    cc.t0 = ch.t0;
+    sm.ts.tile_start = ch.tile0 + tile * hs.tile_bins;
+  }
+  __syncthreads();
+  const int nh = cc.nh;
+  if (tid < kWarps * kGroupMax) {
+    const int j = tid / kGroupMax, hl = tid - j * kGroupMax;
+    if (j < nj && hl < nh) {
+      const int h = hs.hist_index[cc.first + hl];
+      const double* x = jobs[j0 + j].params;
+      double cph[kMaxTerms], sph[kMaxTerms];
+      coef_row<SHAPE>(hs, [&](int q) { return slot_value(hs, x, h, q); }, sm.vg[j].gam[hl], cph, sph);
+    }
+  } else if (tid < kWarps * kGroupMax + kWarps * kMaxTerms) {
+    const int i = tid - kWarps * kGroupMax, j = i / kMaxTerms, k = i - j * kMaxTerms;
+    if (j < nj) {
+      const int h0 = hs.hist_index[cc.first];
+      const double* x = jobs[j0 + j].params;
+      VecConst& v = sm.vg[j];
+      const double nu = term_consts(hs, [&](int q) { return slot_value(hs, x, h0, q); }, k, v);
+      const double t_start = (static_cast<double>(cc.tile0 + tile * hs.tile_bins) - cc.t0) * hs.dt_us;
+      v.base[k] = v.kinds[k] == kTermTF ? tile_phase(nu, t_start) : 0.0f;
+      if (k == 0) {
+        v.tbase = static_cast<float>(t_start);
+        // log2(e) / tau_mu: E = 2^(-aE t); without the decay envelope E = 1
+        v.aE = hs.envelope ? static_cast<float>(1.4426950408889634 / kTauMuUs) : 0.0f;
+        v.dt = static_cast<float>(hs.dt_us);
+      }
+    }
+  } else if (tid < kWarps * kGroupMax + kWarps * kMaxTerms + kGroupMax) {
+    const int hl = tid - kWarps * kGroupMax - kWarps * kMaxTerms;
+    if (hl < nh) {
+      const int h = hs.hist_index[cc.first + hl];
+      cc.row[hl] = h;
+      const size_t esz = hs.store == kStoreF64 ? sizeof(double) : sizeof(float);
+      cc.rowp[hl] = static_cast<const char*>(hs.counts) + static_cast<size_t>(h) * hs.stride * esz;
+      cc.roww[hl] = hs.weights ? static_cast<const char*>(hs.weights) + static_cast<size_t>(h) * hs.stride * esz
+                               : nullptr;
+    }
+  }
+  __syncthreads();
+}
+
+template <int SHAPE, int MODE, bool GRAD>
+__global__ void __launch_bounds__(kBlock, 2) eval_vg_kernel(const Job* __restrict__ jobs, int njobs, int ngroups,
+                                                            int total) {
+  __shared__ SmemVG sm;
+  const HistSet& hs = *jobs[0].hs;  // the jobs of one vector-group launch share their histogram set
+  const int w = threadIdx.x >> 5;
+  for (int gi = blockIdx.x; gi < total; gi += gridDim.x) {
+    const int item = gi / ngroups, grp = gi - item * ngroups;
+    const int j0 = grp * kWarps, nj = min(kWarps, njobs - j0);
+    const int2 it = hs.items[item];
+    __syncthreads();  // the previous item's readers of the shared memory are done
+    load_group<SHAPE>(jobs, j0, nj, hs, it.x, it.y, sm);
+    if (w < nj) split_item<SHAPE, MODE, GRAD, true>(jobs[j0 + w], hs, item, sm, sm.vg[w]);
+    // Release: the barrier orders every warp's row writes before the counter increments.
+    __syncthreads();
+    if (threadIdx.x < nj) {
+      const unsigned prev = atom_add_acq_rel(jobs[j0 + threadIdx.x].chunk_count + it.x, 1u);
+      sm.last[threadIdx.x] = prev == static_cast<unsigned>(sm.cc.ntiles - 1);
+    }
+    __syncthreads();
+    for (int j = 0; j < nj; ++j) {
+      if (!sm.last[j]) continue;
+      const Job& jb = jobs[j0 + j];
+      load_chunk<SHAPE>(jb, hs, j0 + j, it.x, 1, sm);
+      finish_chunk<1, SHAPE, GRAD>(jb, hs, sm);
+    }
+  }
+}
+
+template <int SHAPE, int MODE, bool GRAD>
+int launch_vg_one(const Job* d_jobs, int njobs, int nitems, int num_sms, cudaStream_t stream, LaunchInfo* info) {
+  auto kern = eval_vg_kernel<SHAPE, MODE, GRAD>;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0) != cudaSuccess) return -1;
+  if (per_sm < 1) per_sm = 1;
+  const int ngroups = (njobs + kWarps - 1) / kWarps;
+  const int total = nitems * ngroups;
+  int grid = num_sms * per_sm;
+  if (grid > total) grid = total;
+  if (grid < 1) grid = 1;
+  kern<<<grid, kBlock, 0, stream>>>(d_jobs, njobs, ngroups, total);
+  if (info) {
+    info->grid = grid;
+    info->block = kBlock;
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <int SHAPE>
+int dispatch_vg(int mode, int grad, const Job* j, int n, int items, int sms, cudaStream_t s, LaunchInfo* info) {
+  if constexpr (is_list(SHAPE)) {
+    return -1;
+  } else {
+    if (mode == 0)
+      return grad ? launch_vg_one<SHAPE, 0, true>(j, n, items, sms, s, info)
+                  : launch_vg_one<SHAPE, 0, false>(j, n, items, sms, s, info);
+    if (mode == 1)
+      return grad ? launch_vg_one<SHAPE, 1, true>(j, n, items, sms, s, info)
+                  : launch_vg_one<SHAPE, 1, false>(j, n, items, sms, s, info);
+    return -1;
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Persistent kernel: each CTA takes a contiguous range of the launch's items.
 // ---------------------------------------------------------------------------------------------
@@ -1653,14 +1869,8 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 && SHAPE != kShapeList ? 2 :
   if (threadIdx.x == 0) {
     sm.cc.job = -1;
     sm.cc.chunk = -1;
-    if (PREC == 1) {
-      mbar_init(&sm.bar[0], 1);
-      mbar_init(&sm.bar[1], 1);
-      mbar_init_fence();
-    }
   }
   __syncthreads();
-  uint32_t parity = 0;  // phase parity of each staging barrier (bit b: buffer b)
   int ji = -1;
   Job job;
   for (int gi = beg; gi < end; ++gi) {
@@ -1694,7 +1904,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 && SHAPE != kShapeList ? 2 :
     else if constexpr (SHAPE == kShapeListS)  // at most 2 terms of at most 3 primitives
       list_item<MODE, GRAD, 2, 3>(job, hs, item, sm);
     else
-      split_item<SHAPE, MODE, GRAD>(job, hs, item, sm, parity);
+      split_item<SHAPE, MODE, GRAD, false>(job, hs, item, sm, sm.cc.v);
     complete_item<PREC, SHAPE, GRAD>(job, hs, sm);
   }
 }
@@ -1772,5 +1982,11 @@ MUSR_DECLARE_GROUP(a)
 MUSR_DECLARE_GROUP(b)
 MUSR_DECLARE_GROUP(c)
 #undef MUSR_DECLARE_GROUP
+// vector-group kernels (modes 0 and 1): shapes T1, N1, T1N1, T2 in one translation unit, T2N1,
+// T2m, T2N1m in the other; -1 for a shape without them
+int launch_vg_group_a(int shape, int mode, int grad, const Job* j, int n, int items, int sms, cudaStream_t s,
+                      LaunchInfo* info);
+int launch_vg_group_b(int shape, int mode, int grad, const Job* j, int n, int items, int sms, cudaStream_t s,
+                      LaunchInfo* info);
 
 }  // namespace musr
