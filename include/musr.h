@@ -46,8 +46,9 @@ typedef enum {
   MUSR_EINVAL = -1,     /* invalid argument or inconsistent configuration */
   MUSR_ENOMEM = -2,     /* host or device allocation failed, or HBM budget exceeded */
   MUSR_ECUDA = -3,      /* a CUDA runtime call failed (see musr_last_error) */
-  MUSR_ENONFINITE = -4, /* -2lnL is +infinity: N <= 0 in a bin with d > 0 */
-  MUSR_ETIMEOUT = -5,   /* a bounded wait ran out */
+  MUSR_ENONFINITE = -4, /* the cost is not finite: -2lnL with N <= 0 in a bin with d > 0, or a
+                           parameter that is not finite */
+  MUSR_ETIMEOUT = -5,   /* a bounded wait on the host ran out (musr_sync, musr_server_wait) */
   MUSR_ESTATE = -6,     /* call order violated (e.g. eval before upload) */
   MUSR_EAGAIN = -7,     /* result not ready yet (serving poll) */
   MUSR_ECANCELED = -8   /* a served fit was canceled (musr_server_cancel) */
@@ -227,6 +228,17 @@ int musr_sync(musr_ctx* ctx, int timeout_ms);
 /* Number of (histogram, bin) pairs inside the fit range. */
 int musr_bins_in_fit(musr_ctx* ctx, int64_t* out);
 
+/* The error word of the kernels' index checks (no counterpart in the paper).  The library
+ * built with MUSR_DEBUG_CHECKS (paper_1509_07685_gb300/build.py, debug=True: libmusr_debug.so)
+ * tests every computed index against its bounds on the device; a check that fails ORs its
+ * bit into the context's word and skips the access, nothing traps.  Bits: 1 a count or
+ * weight beyond its row, 2 a histogram index, 4 a chunk or item index, 8 a partial row,
+ * 16 a parameter-map entry, 32 a dynamic Kubo-Toyabe table, 64 a finalize column, 128 a
+ * job index.  Waits for the context's stream and returns the word accumulated since the
+ * context's first evaluation (0: no check failed).  The release build returns MUSR_ESTATE
+ * and 0. */
+int musr_debug_word(musr_ctx* ctx, uint32_t* out);
+
 /* Number of kernel launches one musr_eval/musr_eval_batch/musr_eval_device
  * call makes (for launch accounting). */
 int musr_launches_per_eval(musr_ctx* ctx, int* out);
@@ -367,9 +379,9 @@ int musr_server_stats_get(musr_server* s, musr_server_stats* out);
  * musr_upload_histograms, musr_set_theory and musr_set_map, and every theory
  * those accept runs here too (at MUSR_SPLIT, one without a basis form evaluates
  * its term list per bin).  The call is asynchronous on cuda_stream (NULL: the
- * legacy default stream).  Values written to d_out[0]: +inf where the likelihood
- * is undefined; NaN when a staging wait inside the kernel ran out (the call has
- * returned MUSR_OK by then: read the value before trusting the gradient).
+ * legacy default stream).  d_out[0] is +inf where the likelihood is undefined or a
+ * parameter is not finite (the call has returned MUSR_OK by then: read the value before
+ * trusting the gradient).
  *
  * All scratch (work tables, partial sums, completion counters) lives in one
  * file-scope device array of MUSR_NOALLOC_SCRATCH_BYTES that every GPU which
@@ -394,19 +406,6 @@ int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int64_t nbins,
                       const musr_term* terms, int nterms, const int32_t* map, int nslots, int nparams,
                       const double* consts, int nconsts, const double* d_params, int mode,
                       int precision, int with_grad, double* d_out, void* cuda_stream);
-
-/* Self-check of the evaluation kernels' bounded waits (failure detection without a GPU
- * fault; no counterpart in the paper).  Each staging wait of the SPLIT kernels waits on a
- * shared-memory mbarrier for at most 100 ms of the GPU's global timer.  If a copy never
- * lands, the wait gives up, the CTA records an error and the evaluation returns
- * MUSR_ETIMEOUT; nothing faults, traps or hangs.  This call runs one CTA on `device` that
- * performs that wait on a barrier nothing arrives on.  The wait must give up.  Then the CTA
- * arrives on the barrier itself, and the same wait must see the completed phase.
- * out_try_s: seconds per unsatisfied try (nullable); out_wait_s: seconds until the wait gave
- * up (about 0.1), or -1 when it was not run (nullable).
- * Returns MUSR_OK when the wait gave up and the completed phase was seen; MUSR_ESTATE when
- * any of that failed or the wait was not run; MUSR_EINVAL for a bad device; MUSR_ECUDA. */
-int musr_check_bounded_wait(int device, double* out_try_s, double* out_wait_s);
 
 /* The compute capability the library's kernels were compiled for, as the CUDA runtime
  * reports it for the code loaded on `device` (cudaFuncAttributes::binaryVersion: 103 for

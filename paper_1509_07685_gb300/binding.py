@@ -32,7 +32,7 @@ EXPORTS = (
     "musr_upload_asymmetry", "musr_upload_histograms_device", "musr_set_theory", "musr_set_map", "musr_eval",
     "musr_eval_batch", "musr_eval_device", "musr_sync", "musr_bins_in_fit", "musr_gn_product",
     "musr_gauss_newton",
-    "musr_launches_per_eval", "musr_eval_noalloc", "musr_check_bounded_wait", "musr_binary_version", "musr_fit", "musr_server_create",
+    "musr_launches_per_eval", "musr_debug_word", "musr_eval_noalloc", "musr_binary_version", "musr_fit", "musr_server_create",
     "musr_server_destroy", "musr_server_submit", "musr_server_poll", "musr_server_wait",
     "musr_server_cancel", "musr_server_stats_get", "musr_poisson_create", "musr_poisson_destroy", "musr_poisson_last_error",
     "musr_poisson_solve", "musr_poisson_solve_device",
@@ -113,10 +113,10 @@ def _declare(lib):
         "musr_gauss_newton": ([vp, P(d), ctypes.c_int, ctypes.c_int, ctypes.c_int, P(d)], ctypes.c_int),
         "musr_bins_in_fit": ([vp, P(i64)], ctypes.c_int),
         "musr_launches_per_eval": ([vp, P(ctypes.c_int)], ctypes.c_int),
+        "musr_debug_word": ([vp, P(ctypes.c_uint32)], ctypes.c_int),
         "musr_eval_noalloc": ([vp, ctypes.c_int, ctypes.c_int, i64, i64, P(d), d, P(d), P(musr_term),
                                ctypes.c_int, P(i32), ctypes.c_int, ctypes.c_int, P(d), ctypes.c_int, vp,
                                ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
-        "musr_check_bounded_wait": ([ctypes.c_int, P(d), P(d)], ctypes.c_int),
         "musr_binary_version": ([ctypes.c_int, P(ctypes.c_int)], ctypes.c_int),
         "musr_fit": ([vp, P(d), ctypes.c_int, ctypes.c_int, ctypes.c_int, d, P(d), P(musr_fit_result)],
                      ctypes.c_int),
@@ -330,6 +330,13 @@ def musr_bins_in_fit(ctx) -> int:
     return out.value
 
 
+def musr_debug_word(ctx):
+    """(status, the error word of the kernels' index checks); MUSR_ESTATE in a release build."""
+    out = ctypes.c_uint32(0)
+    st = load().musr_debug_word(ctx, ctypes.byref(out))
+    return st, out.value
+
+
 def musr_launches_per_eval(ctx) -> int:
     out = ctypes.c_int()
     _check(ctx, load().musr_launches_per_eval(ctx, ctypes.byref(out)))
@@ -362,13 +369,6 @@ def musr_binary_version(device: int = 0):
     out = ctypes.c_int(-1)
     st = load().musr_binary_version(int(device), ctypes.byref(out))
     return st, out.value
-
-
-def musr_check_bounded_wait(device: int = 0):
-    """(status, seconds per unsatisfied try, seconds until the kernels' wait gave up)."""
-    t_try, t_wait = ctypes.c_double(-1.0), ctypes.c_double(-1.0)
-    st = load().musr_check_bounded_wait(int(device), ctypes.byref(t_try), ctypes.byref(t_wait))
-    return st, t_try.value, t_wait.value
 
 
 # --------------------------------------------------------------------------------------------

@@ -12,6 +12,11 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmusr.so")
+# The checking build: every kernel tests its computed indices against their bounds and, on a
+# violation, records it in the evaluation's error word and skips the access (no trap);
+# musr_debug_word reads the word.  Built on demand, beside the release library.
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+LIB_DEBUG = os.path.join(PKG, "libmusr_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-fast-math",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -33,18 +38,21 @@ def _headers():
             glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compiles the library (debug: the checking build, libmusr_debug.so) and returns its path."""
+    build_dir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    flags = FLAGS + (["-DMUSR_DEBUG_CHECKS"] if debug else [])
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     srcs = _sources()
     newest_hdr = max(os.path.getmtime(h) for h in _headers())
     jobs = []
     objs = []
     for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s) + ".o")
+        o = os.path.join(build_dir, os.path.basename(s) + ".o")
         objs.append(o)
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), newest_hdr):
-            jobs.append([nvcc, *ARCH, *FLAGS, "-c", s, "-o", o])
+            jobs.append([nvcc, *ARCH, *flags, "-c", s, "-o", o])
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         futs = [ex.submit(subprocess.run, j, capture_output=True, text=True) for j in jobs]
         for j, f in zip(jobs, futs):
@@ -53,11 +61,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 print(r.stdout + r.stderr)
             if r.returncode:
                 raise RuntimeError(f"nvcc failed: {' '.join(j)}")
-    if force or jobs or not os.path.exists(LIB):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or not os.path.exists(lib):
+        tmp = lib + f".tmp{os.getpid()}"
         subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread", "-lcufft"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -280,6 +280,7 @@ int compile(musr_ctx* ctx, int prec, int var) {
   hs.nterms = static_cast<int>(ctx->terms.size());
   hs.nslots = ctx->nslots;
   hs.P = ctx->P;  // map and consts: device copies in the tables (ensure_uploaded)
+  hs.nconsts = static_cast<int>(ctx->consts.size());
   for (int k = 0; k < hs.nterms; ++k) {
     const musr_term& t = ctx->terms[k];
     hs.raw[k].nprim = t.nprim;
@@ -528,35 +529,6 @@ int pick_variant(musr_ctx* ctx, int prec, int nvec) {
   return musr::pick_decomposition(items, nvec, prec, ctx->num_sms);
 }
 
-// The vector-group schedule of a SPLIT launch of nvec evaluations (each CTA item one tile for
-// 8 evaluations, one warp each): the decomposition it would use, or -1 when the one-job
-// schedule of decomposition `var` is expected to be as fast.  Both are costed in CTA
-// iterations of 512 bins of one evaluation for the busiest CTA: one-job items of 512 << v
-// bins cost (1 << v) + 1.3, vector-group items 8 (1 << v) + kVgItemCost.  Tiles of the
-// vector-group schedule stay at or below 4096 bins: a thread then sums at most 128 bins of a
-// chunk's histograms in FP32 before the warp sum (twice the one-job kernel's 64).
-constexpr double kVgItemCost = 1.5;
-constexpr int kVgMaxVariant = 3;
-int pick_vg_variant(musr_ctx* ctx, int nvec, int var) {
-  const int grid = musr::persistent_grid(MUSR_SPLIT, ctx->num_sms);
-  auto busiest = [&](int64_t items) { return (items + grid - 1) / grid; };
-  const double one = static_cast<double>(busiest(static_cast<int64_t>(nvec) * ctx->comp[MUSR_SPLIT][var].hs.nitems)) *
-                     (static_cast<double>(1 << var) + musr::kSplitItemCost);
-  const int64_t groups = (nvec + musr::kWarps - 1) / musr::kWarps;
-  int best = -1;
-  double best_t = one;
-  for (int v = 0; v <= kVgMaxVariant; ++v) {
-    ensure_compiled(ctx, MUSR_SPLIT, v);
-    const double t = static_cast<double>(busiest(groups * ctx->comp[MUSR_SPLIT][v].hs.nitems)) *
-                     (8.0 * static_cast<double>(1 << v) + kVgItemCost);
-    if (t <= best_t) {
-      best = v;
-      best_t = t;
-    }
-  }
-  return best;
-}
-
 // Buffers for nvec evaluations; rebuilds the job table when the launch's key
 // (precision, decomposition, mode, grad, nvec, pointers) changes.
 int ensure_eval(musr_ctx* ctx, int prec, int var, int nvec) {
@@ -584,6 +556,9 @@ int ensure_eval(musr_ctx* ctx, int prec, int var, int nvec) {
   if ((rc = grow(ev.chunk_val, nck * sizeof(double), false))) return rc;
   if ((rc = grow(ev.chunk_count, nck * sizeof(unsigned), true))) return rc;
   if ((rc = grow(ev.counters, nvec * sizeof(unsigned), true))) return rc;
+#ifdef MUSR_DEBUG_CHECKS
+  if (!ctx->dbg_word.p && (rc = grow(ctx->dbg_word, sizeof(unsigned), true))) return rc;
+#endif
   if (hs.ndkt > 0) {
     const size_t nt = static_cast<size_t>(nvec) * hs.ndkt;
     if ((rc = grow(ev.dkt, nt * musr::kDktTable * sizeof(double), false))) return rc;
@@ -613,6 +588,7 @@ void fill_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, c
     j.grad = grad;
     j.prec = prec;
     j.dir = d_dirs ? d_dirs + static_cast<size_t>(v) * ctx->P : nullptr;
+    j.dbg = static_cast<unsigned*>(ctx->dbg_word.p);  // checking build only (else null)
     if (hs.ndkt > 0) {  // tables of this evaluation: FP64 values for prec 0, FP32 for SPLIT
       const size_t esz = prec == MUSR_SPLIT ? sizeof(float) : sizeof(double);
       j.dkt = static_cast<char*>(ev.dkt.p) + static_cast<size_t>(v) * hs.ndkt * musr::kDktTable * esz;
@@ -667,17 +643,7 @@ int check_ready(musr_ctx* ctx, int mode, int prec) {
 int enqueue_eval(musr_ctx* ctx, int prec, int mode, int grad, int nvec, const double* d_params,
                  double* d_out, const double* d_dirs = nullptr) {
   if (ctx->asym && prec == MUSR_SPLIT && mode == MUSR_CHI2) mode = 4;  // SPLIT kernels: weighted chi^2
-  int var = pick_variant(ctx, prec, nvec);
-  // A batch of SPLIT evaluations of a basis-form theory may take the vector-group schedule.
-  bool vg = false;
-  if (prec == MUSR_SPLIT && nvec >= musr::kWarps && !d_dirs && ctx->comp[prec][var].hs.ndkt == 0 &&
-      musr::has_vg(ctx->comp[prec][var].hs.shape, mode)) {
-    const int v = pick_vg_variant(ctx, nvec, var);
-    if (v >= 0) {
-      var = v;
-      vg = true;
-    }
-  }
+  const int var = pick_variant(ctx, prec, nvec);
   const HistSet& hs = ctx->comp[prec][var].hs;
   if (hs.nitems == 0) {  // no bin in the fit range: cost 0, gradient 0
     cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(double) * nvec * (1 + ctx->P), ctx->stream);
@@ -692,11 +658,8 @@ int enqueue_eval(musr_ctx* ctx, int prec, int mode, int grad, int nvec, const do
     ctx->ev.key_valid = false;
     return cuda_fail(ctx, e, "dynamic Kubo-Toyabe table launch");
   }
-  const int lrc = vg ? musr::launch_eval_vg(hs.shape, mode, grad, static_cast<const Job*>(ctx->ev.jobs.p), nvec,
-                                            hs.nitems, ctx->num_sms, ctx->stream, &info)
-                     : musr::launch_eval(prec, hs.shape, mode, grad, static_cast<const Job*>(ctx->ev.jobs.p), nvec,
-                                         nvec * hs.nitems, ctx->num_sms, ctx->stream, &info);
-  if (lrc) {
+  if (musr::launch_eval(prec, hs.shape, mode, grad, static_cast<const Job*>(ctx->ev.jobs.p), nvec,
+                        nvec * hs.nitems, ctx->num_sms, ctx->stream, &info)) {
     cudaError_t e = cudaGetLastError();
     ctx->ev.key_valid = false;
     return cuda_fail(ctx, e, "kernel launch");
@@ -1166,12 +1129,11 @@ int musr_eval_batch(musr_ctx* ctx, const double* params, int nvec, int nparams, 
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(out)");
   e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
-  bool nonfinite = false, timed_out = false;
+  bool nonfinite = false;
   for (int v = 0; v < nvec; ++v) {
     const double* o = ev.h_out + static_cast<size_t>(v) * (1 + P);
     out_values[v] = o[0];
     if (!std::isfinite(o[0])) nonfinite = true;
-    if (std::isnan(o[0])) timed_out = true;  // a kernel's bounded wait ran out
     if (out_grads) {
       double* g = out_grads + static_cast<size_t>(v) * P;
       if (std::isfinite(o[0]))
@@ -1180,8 +1142,8 @@ int musr_eval_batch(musr_ctx* ctx, const double* params, int nvec, int nparams, 
         std::memset(g, 0, P * sizeof(double));
     }
   }
-  if (timed_out) return fail(ctx, MUSR_ETIMEOUT, "a device-side wait for staged counts ran out (value NaN)");
-  if (nonfinite) return fail(ctx, MUSR_ENONFINITE, "-2lnL is +inf: N <= 0 in a bin with d > 0");
+  if (nonfinite)
+    return fail(ctx, MUSR_ENONFINITE, "cost not finite: N <= 0 in a bin with d > 0 (-2lnL), or a parameter not finite");
   return MUSR_OK;
 }
 
@@ -1235,12 +1197,11 @@ int musr_gn_product(musr_ctx* ctx, const double* params, int nparams, const doub
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(out)");
   e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
-  bool nonfinite = false, timed_out = false;
+  bool nonfinite = false;
   for (int v = 0; v < ndir; ++v) {
     const double* o = ev.h_out + static_cast<size_t>(v) * (1 + P);
     double* r = out + static_cast<size_t>(v) * (1 + P);
     r[0] = o[0];
-    if (std::isnan(o[0])) timed_out = true;
     if (!std::isfinite(o[0])) {
       nonfinite = true;
       std::memset(r + 1, 0, P * sizeof(double));
@@ -1248,8 +1209,7 @@ int musr_gn_product(musr_ctx* ctx, const double* params, int nparams, const doub
       std::memcpy(r + 1, o + 1, P * sizeof(double));
     }
   }
-  if (timed_out) return fail(ctx, MUSR_ETIMEOUT, "a device-side wait for staged counts ran out (value NaN)");
-  if (nonfinite) return fail(ctx, MUSR_ENONFINITE, "-2lnL undefined: N <= 0 in a bin with d > 0");
+  if (nonfinite) return fail(ctx, MUSR_ENONFINITE, "-2lnL undefined: N <= 0 in a bin with d > 0, or a parameter not finite");
   return MUSR_OK;
 }
 
@@ -1297,6 +1257,23 @@ int musr_bins_in_fit(musr_ctx* ctx, int64_t* out) {
   for (int h = 0; h < ctx->H; ++h) s += ctx->nhi[h] - ctx->nlo[h];
   *out = s;
   return MUSR_OK;
+}
+
+int musr_debug_word(musr_ctx* ctx, uint32_t* out) {
+  if (!ctx || !out) return MUSR_EINVAL;
+  *out = 0;
+#ifdef MUSR_DEBUG_CHECKS
+  DeviceScope ds(ctx->device);
+  if (!ctx->dbg_word.p) return MUSR_OK;  // no evaluation yet
+  unsigned w = 0;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(&w, ctx->dbg_word.p, sizeof(w), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "musr_debug_word");
+  *out = w;
+  return MUSR_OK;
+#else
+  return fail(ctx, MUSR_ESTATE, "this library was built without the index checks (MUSR_DEBUG_CHECKS)");
+#endif
 }
 
 int musr_launches_per_eval(musr_ctx* ctx, int* out) {

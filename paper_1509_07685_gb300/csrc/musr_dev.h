@@ -167,6 +167,7 @@ struct HistSet {
   const int32_t* map;  // [H][nslots]
   int nslots;
   const double* consts;
+  int nconsts;
   int P;
   // decomposition
   const Chunk* chunks;
@@ -200,6 +201,21 @@ struct Job {
   const double* dir;         // [P] direction v of a Gauss-Newton product, else nullptr
   void* dkt;                 // [ndkt][kDktTable] tables of this evaluation (double: FP64 path, float: SPLIT)
   void* dkt_work;            // [ndkt][kDktWork] scratch of the table solve, same type
+  unsigned* dbg;             // checking build: the context's error word (bits of DebugCheck), else nullptr
+};
+
+// Index checks of the checking build (compiled with MUSR_DEBUG_CHECKS): a kernel that finds a
+// computed index out of its bounds ORs the check's bit into the evaluation's error word and
+// skips the access (no trap); musr_debug_word reads the word.
+enum DebugCheck : unsigned {
+  kDbgRow = 1u,       // a count, weight or staging index beyond the histogram row
+  kDbgHist = 2u,      // a histogram index >= H
+  kDbgChunk = 4u,     // a chunk or work-item index beyond the decomposition
+  kDbgPartial = 8u,   // a partial row beyond the job's rows
+  kDbgMap = 16u,      // a parameter-map entry beyond the parameters or constants
+  kDbgDkt = 32u,      // a dynamic Kubo-Toyabe source beyond the tables
+  kDbgCol = 64u,      // a finalize column beyond the job's columns
+  kDbgJob = 128u      // a job index beyond the launch's jobs
 };
 
 // Launchers (host side of musr_kernels.cu).  All enqueue on `stream`.
@@ -210,12 +226,6 @@ struct LaunchInfo {
 int launch_eval(int precision, int shape, int mode, int grad, const Job* d_jobs, int njobs,
                 int total_items, int num_sms, void* stream, LaunchInfo* info);
 int max_ctas_per_sm(int precision, int shape, int mode, int grad);
-// The vector-group schedule of the SPLIT basis kernels (modes 0 and 1): njobs evaluations of
-// one histogram set whose decomposition has nitems work items; each CTA item is one (chunk,
-// tile) for a group of 8 jobs, one warp per job.  has_vg: whether the shape and mode have it.
-bool has_vg(int shape, int mode);
-int launch_eval_vg(int shape, int mode, int grad, const Job* d_jobs, int njobs, int nitems, int num_sms,
-                   void* stream, LaunchInfo* info);
 // The dynamic Kubo-Toyabe tables of njobs evaluations of one histogram set (precision 0:
 // FP64, 1: FP32), one CTA per (job, source); enqueued on `stream` before the evaluation.
 int launch_dkt_tables(int precision, const Job* d_jobs, int njobs, int ndkt, void* stream);

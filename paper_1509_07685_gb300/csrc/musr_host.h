@@ -137,6 +137,7 @@ struct musr_ctx {
   // launch picks the largest that still fills the GPU (pick_decomposition).
   musr::Compiled comp[2][musr::kVariants];
   musr::EvalBufs ev;
+  musr::DevBuf dbg_word;  // checking build: the error word of the kernels' index checks
   int last_grid = 0;
   musr::Arena* arena = nullptr;  // when set, device memory comes from it (serving)
   // Stream of one-time setup work (histogram copy and check, tables, zeroed buffers);

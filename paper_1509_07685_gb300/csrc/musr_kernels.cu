@@ -72,36 +72,6 @@ int launch_eval(int precision, int shape, int mode, int grad, const Job* d_jobs,
   }
 }
 
-bool has_vg(int shape, int mode) {
-  if (mode != 0 && mode != 1) return false;
-  switch (shape) {
-    case kShapeT1:
-    case kShapeN1:
-    case kShapeT1N1:
-    case kShapeT2:
-    case kShapeT2N1:
-    case kShapeT2m:
-    case kShapeT2N1m:
-      return true;
-    default:
-      return false;
-  }
-}
-
-int launch_eval_vg(int shape, int mode, int grad, const Job* d_jobs, int njobs, int nitems, int num_sms,
-                   void* stream, LaunchInfo* info) {
-  if (!has_vg(shape, mode)) return -1;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  switch (shape) {
-    case kShapeT2N1:
-    case kShapeT2m:
-    case kShapeT2N1m:
-      return launch_vg_group_b(shape, mode, grad, d_jobs, njobs, nitems, num_sms, s, info);
-    default:
-      return launch_vg_group_a(shape, mode, grad, d_jobs, njobs, nitems, num_sms, s, info);
-  }
-}
-
 int max_ctas_per_sm(int precision, int shape, int mode, int grad) {
   if (precision == 0) return occupancy_group_fp64(mode, grad);
   switch (shape_group_of(shape)) {

@@ -87,58 +87,10 @@ __device__ __forceinline__ float rint_small(float x) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// TMA bulk copies global -> shared with mbarrier completion (documented PTX ISA).
+// Shared-memory addresses, asynchronous copies, atomics (documented PTX ISA).
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_init_fence() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Limit of every wait on a staging barrier: a copy of at most 8 x 4 KiB that has not landed
-// after this long never will.  The limit is on the global timer; a cap on the number of tries
-// (2^24, tens of seconds at the suspend time of an unsatisfied try) bounds the wait even if
-// that timer stood still.
-constexpr unsigned long long kWaitLimitNs = 100000000ull;  // 100 ms
-// Waits for phase `parity` of the barrier; false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  for (int i = 0; i < (1 << 18); ++i) {
-#pragma unroll 1
-    for (int k = 0; k < 64; ++k)
-      if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitLimitNs) return false;
-  }
-  return false;
 }
 
 // Per-thread asynchronous copies global -> shared (cp.async, documented PTX ISA): 8 bytes,
@@ -215,9 +167,26 @@ __device__ __forceinline__ void dkt_lookup(const T* tab, T t, T* G, T* dD, T* dN
   *dN = fma(w0, g[0], fma(w1, g[1], fma(w2, g[2], w3 * g[3])));
 }
 
+// Checks of the checking build: true when cond holds; otherwise the check's bit goes into
+// the error word w (when there is one) and the caller skips the access.  Always true in the
+// release build (the checks compile away).
+__device__ __forceinline__ bool dbg_ok(unsigned* w, bool cond, unsigned code) {
+#ifdef MUSR_DEBUG_CHECKS
+  if (!cond && w) atomicOr(w, code);
+  return cond;
+#else
+  (void)w;
+  (void)cond;
+  (void)code;
+  return true;
+#endif
+}
+
 // Local value of slot s of histogram h.
-__device__ __forceinline__ double slot_value(const HistSet& hs, const double* x, int h, int s) {
+__device__ __forceinline__ double slot_value(const HistSet& hs, const double* x, int h, int s,
+                                             unsigned* dbg = nullptr) {
   const int m = hs.map[static_cast<int64_t>(h) * hs.nslots + s];
+  if (!dbg_ok(dbg, m >= 0 ? m < hs.P : -1 - m < hs.nconsts, kDbgMap)) return 0.0;
   return m >= 0 ? x[m] : hs.consts[-1 - m];
 }
 
@@ -226,8 +195,7 @@ __device__ __forceinline__ double slot_value(const HistSet& hs, const double* x,
 // ---------------------------------------------------------------------------------------------
 
 // One evaluation's constants of the SPLIT basis kernels on one chunk and tile: what the
-// per-bin loop reads.  The one-evaluation path keeps one in its chunk cache; the
-// vector-group path keeps one per warp (each warp evaluates its own parameter vector).
+// per-bin loop reads (kept in the chunk cache).
 struct VecConst {
   // [Nbkg, Gam_0 .. Gam_{M-1}] of each histogram (16-byte rows: vector loads)
   alignas(16) float gam[kGroupMax][kGamStride];
@@ -278,7 +246,7 @@ struct Smem {
   // SPLIT, FP32 counts: the rows of the current and the next CTA iteration, each thread's two
   // bins of every histogram copied by that thread (cp.async)
   alignas(128) float stage[2][kGroupMax][kBlock * kBinsPerThread];
-  __device__ float* stage_slot(int b, int hl, int /*warp*/, int bin) { return &stage[b][hl][bin]; }
+  __device__ float* stage_slot(int b, int hl, int bin) { return &stage[b][hl][bin]; }
   ChunkCache cc;
   TileState ts;
   float cred[kWarps][kMaxChan];  // per-warp FP32 channel sums
@@ -446,7 +414,7 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
   ChunkCache& cc = sm.cc;
   const int tid = threadIdx.x;
   if (tid == 0) {
-    const Chunk ch = hs.chunks[chunk_index];
+    const Chunk ch = hs.chunks[dbg_ok(job.dbg, chunk_index >= 0 && chunk_index < hs.nchunks, kDbgChunk) ? chunk_index : 0];
     cc.job = job_index;
     cc.chunk = chunk_index;
     cc.nh = ch.nh;
@@ -463,8 +431,9 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
   const int nh = cc.nh, nsl = hs.nslots;
   for (int i = tid; i < nh * nsl; i += kBlock) {
     const int hl = i / nsl, s = i - hl * nsl;
-    const int h = hs.hist_index[cc.first + hl];
-    cc.loc[hl][s] = slot_value(hs, job.params, h, s);
+    int h = hs.hist_index[cc.first + hl];
+    if (!dbg_ok(job.dbg, h >= 0 && h < hs.H, kDbgHist)) h = 0;
+    cc.loc[hl][s] = slot_value(hs, job.params, h, s, job.dbg);
     const int mi = hs.map[static_cast<int64_t>(h) * hs.nslots + s];
     cc.ldir[hl][s] = job.dir && mi >= 0 ? job.dir[mi] : 0.0;
     if (s == 0) {
@@ -588,6 +557,7 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Smem& sm)
     if (n < nlo) continue;
     // Bin time (Section 4.1: t = n dt, shifted by t0).
     const double t = (static_cast<double>(n) - t0) * dt;
+    if (!dbg_ok(job.dbg, n < hs.stride, kDbgRow)) continue;
     const double d = store == kStoreF64 ? rowd[n] : static_cast<double>(rowf[n]);
     const double E = hs.envelope ? exp(-t / kTauMuUs) : 1.0;
     // chi^2 weight: 1 / max(d, 1) for counts (Eq. chisq), given for asymmetry data
@@ -647,6 +617,7 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Smem& sm)
           df[m][1] = -j1x * kTwoPi / 360.0;
         } else if (kind == kDKT) {  // dynamic Kubo-Toyabe: this evaluation's table of the pair
           const int src = hs.dkt_of[(h * kMaxTerms + k) * kMaxPrims + m];
+          if (!dbg_ok(job.dbg, src >= 0 && src < hs.ndkt, kDbgDkt)) continue;
           dkt_lookup(static_cast<const double*>(job.dkt) + static_cast<size_t>(src) * kDktTable, t, &f[m],
                      &df[m][0], &df[m][1]);
         } else if (kind == kTFCos) {
@@ -755,6 +726,7 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Smem& sm)
         }
   }
   __syncthreads();
+  if (!dbg_ok(job.dbg, item >= 0 && item < hs.nitems, kDbgPartial)) return;
   double* row = job.partials + static_cast<int64_t>(item) * hs.pstride;
   const int nout = GRAD ? 1 + kFp64Channels : 1;
   for (int c = tid; c < nout; c += kBlock) {
@@ -858,6 +830,7 @@ __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm)
   for (int n = ts + tid; n < end; n += kBlock, fm += static_cast<float>(kBlock)) {
     if (n < nlo) continue;
     const float tf = fmaf(fm, dtf, tbase);  // Section 4.1: t = n dt, shifted by t0
+    if (!dbg_ok(job.dbg, n < hs.stride, kDbgRow)) continue;
     const float d = store == kStoreF64 ? static_cast<float>(rowd[n]) : rowf[n];
     const float E = __expf(-rate * tf);
     float gd[LT][LP][2];
@@ -915,6 +888,7 @@ __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm)
           df[m][1] = -sn * (kTwoPiF / 360.0f);
         } else if (kind == kDKT) {  // dynamic Kubo-Toyabe: this evaluation's FP32 table of the pair
           const int src = hs.dkt_of[(h * kMaxTerms + k) * kMaxPrims + m];
+          if (!dbg_ok(job.dbg, src >= 0 && src < hs.ndkt, kDbgDkt)) continue;
           dkt_lookup(static_cast<const float*>(job.dkt) + static_cast<size_t>(src) * kDktTable, tf, &f[m],
                      &df[m][0], &df[m][1]);
         } else if (kind == kBessel) {  // J0' = -J1; the argument (not periodic) in radians
@@ -1016,6 +990,7 @@ __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm)
         }
   }
   __syncthreads();
+  if (!dbg_ok(job.dbg, item >= 0 && item < hs.nitems, kDbgPartial)) return;
   double* row = job.partials + static_cast<int64_t>(item) * hs.pstride;
   const int nout = GRAD ? 1 + kFp64Channels : 1;
   for (int c = tid; c < nout; c += kBlock) {
@@ -1033,12 +1008,9 @@ __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm)
 // u = d(cost/2)/dN, then the channels G_m += u B_m, W += u and the per-bin sums
 // V_m = sum_j u_j Gam_jm that carry the shared time parameters' derivatives.
 // ---------------------------------------------------------------------------------------------
-// VG: the vector-group schedule -- each warp evaluates its own job (parameter vector) on the
-// tile, 64 bins per iteration, with vc that job's constants, and writes the item's row of its
-// job itself; otherwise the CTA's 8 warps share one job, 512 bins per iteration, and the row
-// is the FP64 sum of the 8 warps' partial sums.
-template <int SHAPE, int MODE, bool GRAD, bool VG, class SM>
-__device__ void split_item(const Job& job, const HistSet& hs, int item, SM& sm, const VecConst& vc) {
+// vc: the job's constants on this chunk and tile.
+template <int SHAPE, int MODE, bool GRAD>
+__device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm, const VecConst& vc) {
   using Bs = Basis<SHAPE>;
   constexpr int NT = Bs::NT;
   constexpr int M = Bs::M;
@@ -1055,7 +1027,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, SM& sm, 
   const int nterms = Bs::NTF < 0 ? hs.nterms : NT;
   const float aE = vc.aE, tbase = vc.tbase, dtf = vc.dt;
   const int lane = tid & 31, w = tid >> 5;
-  const int tb = VG ? lane : tid;  // the thread's position in an iteration's bins
+  const int tb = tid;  // the thread's position in an iteration's bins
   const int store = hs.store;
 
   float acc_v = 0.0f, acc_c = 0.0f;  // Kahan-compensated cost value
@@ -1070,7 +1042,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, SM& sm, 
 #pragma unroll
     for (int q = 0; q < 4; ++q) sh[k][q] = 0.0f;
 
-  constexpr int CHUNK_BINS = (VG ? 32 : kBlock) * BPT;  // bins of one iteration
+  constexpr int CHUNK_BINS = kBlock * BPT;  // bins of one CTA iteration
   // Iterations of this tile that hold any bin of the fit range (the same for every thread).
   const int iters = min(hs.tile_bins / CHUNK_BINS, (nhi - ts + CHUNK_BINS - 1) / CHUNK_BINS);
   // FP32 counts are staged into shared memory one iteration ahead, each thread copying its
@@ -1086,13 +1058,13 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, SM& sm, 
 #pragma unroll
       for (int hl = 0; hl < G; ++hl) {
         if (hl >= nh) break;
-        cp_async8(sm.stage_slot(itn & 1, hl, w, tb * BPT), static_cast<const float*>(cc.rowp[hl]) + (in ? n : 0),
-                  in ? 8u : 0u);
+        const bool ok = dbg_ok(job.dbg, cc.row[hl] >= 0 && cc.row[hl] < hs.H && n >= 0, kDbgHist);
+        cp_async8(sm.stage_slot(itn & 1, hl, tb * BPT),
+                  static_cast<const float*>(cc.rowp[hl]) + (in && ok ? n : 0), in && ok ? 8u : 0u);
       }
     }
     cp_async_commit();  // one group per iteration (empty past the tile's end)
   };
-  const int stall = 0;  // (no waits that can run out on this path)
   if (staged) issue(0);
   // The bin offset in the tile is carried as an exact float (integers < 2^24): an
   // int-to-float conversion per bin would occupy this GPU's slow FP64/conversion pipe.
@@ -1252,7 +1224,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, SM& sm, 
     };
     auto fetch = [&](int hl, float (&d)[BPT], float (&gm)[4 * NG4]) {
       if (staged) {
-        const float2 q = *reinterpret_cast<const float2*>(sm.stage_slot(b, hl, w, tb * BPT));
+        const float2 q = *reinterpret_cast<const float2*>(sm.stage_slot(b, hl, tb * BPT));
         d[0] = q.x;
         d[1] = q.y;
       } else if (hl < nh) {
@@ -1427,33 +1399,6 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, SM& sm, 
   if (staged) cp_async_wait<0>();
   float vh = acc_v, vl = -acc_c;
   warp_sum_ff(vh, vl);
-  if constexpr (VG) {
-    // ---- thread (FP32) -> warp (FP32; the value as float-float) -> the job's row (FP64)
-    double* row = job.partials + static_cast<int64_t>(item) * hs.pstride;
-    if (GRAD) {
-#pragma unroll
-      for (int hl = 0; hl < G; ++hl)
-#pragma unroll
-        for (int q = 0; q < NPH; ++q) {
-          const float r = warp_sum_f(gacc[hl][q]);
-          if (lane == (hl * NPH + q) % 32) row[1 + hl * NPH + q] = static_cast<double>(r);
-        }
-#pragma unroll
-      for (int k = 0; k < NT; ++k)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float r = warp_sum_f(sh[k][q]);
-          if (lane == (G * NPH + k * 4 + q) % 32) row[1 + G * NPH + k * 4 + q] = static_cast<double>(r);
-        }
-    }
-    if (lane == 0) {
-      const double a = static_cast<double>(vh) + static_cast<double>(vl);
-      // +inf: the likelihood is undefined (N <= 0 where d > 0) or the parameters were not finite
-      row[0] = isfinite(a) ? a * (MODE == 0 || MODE == 4 ? 1.0 : 2.0) : __longlong_as_double(0x7ff0000000000000LL);
-    }
-    (void)stall;
-    return;
-  } else {
   // ---- thread (FP32) -> warp (FP32; the value as float-float) -> CTA (FP64 trees) -> row.
   __syncthreads();
   if (lane == 0) {
@@ -1478,6 +1423,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, SM& sm, 
   }
   __syncthreads();
   static_assert(kWarps == 8, "the FP64 trees below sum 8 warps");
+  if (!dbg_ok(job.dbg, item >= 0 && item < hs.nitems, kDbgPartial)) return;
   double* row = job.partials + static_cast<int64_t>(item) * hs.pstride;
   if (GRAD && tid < NCH) {
     double a[kWarps];
@@ -1493,10 +1439,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, SM& sm, 
     for (int o = 4; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     // +inf: the likelihood is undefined (N <= 0 where d > 0) or the parameters were not finite.
     if (l == 0)
-      row[0] = stall ? __longlong_as_double(0x7ff8000000000000LL)
-                     : (isfinite(a) ? a * (MODE == 0 || MODE == 4 ? 1.0 : 2.0)
-                                    : __longlong_as_double(0x7ff0000000000000LL));
-  }
+      row[0] = isfinite(a) ? a * (MODE == 0 || MODE == 4 ? 1.0 : 2.0) : __longlong_as_double(0x7ff0000000000000LL);
   }
 }
 
@@ -1581,6 +1524,7 @@ __device__ void chunk_finalize(const Job& job, const HistSet& hs, SM& sm) {
   const int tid = threadIdx.x;
   const int ps = hs.pstride;
   const int nout = GRAD ? 1 + hs.nch : 1;
+  if (!dbg_ok(job.dbg, cc.item0 >= 0 && cc.item0 + cc.ntiles <= hs.nitems, kDbgPartial)) return;
   const double* part = job.partials + static_cast<int64_t>(cc.item0) * ps;
   // The chunk's item rows, summed per column in a fixed order: each column's rows are cut
   // into `tpc` contiguous segments, one thread sums a segment (its loads all in flight),
@@ -1650,7 +1594,10 @@ __device__ void job_finalize(const Job& job, const HistSet& hs, SM& sm) {
       for (int j = hs.p_ptr[p]; j < j1; j += 8) {  // eight loads in flight, summed in column order
         double x[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) x[q] = j + q < j1 ? __ldcg(job.colsum + hs.p_cols[j + q]) : 0.0;
+        for (int q = 0; q < 8; ++q) {
+          const int col = j + q < j1 ? hs.p_cols[j + q] : 0;
+          x[q] = j + q < j1 && dbg_ok(job.dbg, col >= 0 && col < hs.ncols, kDbgCol) ? __ldcg(job.colsum + col) : 0.0;
+        }
 #pragma unroll
         for (int q = 0; q < 8; ++q)
           if (j + q < j1) g += x[q];
@@ -1707,155 +1654,6 @@ __device__ void complete_item(const Job& job, const HistSet& hs, Smem& sm) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Vector-group schedule (SPLIT basis shapes, large batches of one histogram set): a work item
-// is (chunk, tile, group of 8 jobs); warp w evaluates job 8 g + w on the tile, so the 8 warps
-// of a CTA read the same counts (one L1/L2 fetch serves 8 parameter vectors), keep no
-// cross-warp reduction, and each writes its job's row for the item.  Items are numbered
-// tile-major (the groups of one tile consecutive) and taken round-robin by the persistent
-// CTAs, so the CTAs running at any moment work on a few tiles and every tile of counts
-// comes from DRAM about once per launch.
-// ---------------------------------------------------------------------------------------------
-constexpr int kVgBins = 32 * kBinsPerThread;  // bins of one warp iteration
-
-struct SmemVG {
-  // each warp's threads' bins of every histogram, current and next iteration (cp.async)
-  alignas(128) float stage[kWarps][2][kGroupMax][kVgBins];
-  __device__ float* stage_slot(int b, int hl, int w, int bin) { return &stage[w][b][hl][bin]; }
-  ChunkCache cc;           // the chunk's shared fields; the per-job fields for one job's finalize
-  TileState ts;
-  VecConst vg[kWarps];     // the constants of each warp's job
-  double tot[kMaxChan + 1];
-  double wsum[kWarps];
-  int flag;
-  int last[kWarps];        // which of the group's jobs completed the chunk with this item
-};
-
-// The chunk's shared fields, the row pointers, and the constants of jobs j0 .. j0 + nj - 1
-// on tile `tile` (one thread per (job, histogram) coefficient row, one per (job, term)).
-template <int SHAPE>
-__device__ void load_group(const Job* jobs, int j0, int nj, const HistSet& hs, int chunk_index, int tile,
-                           SmemVG& sm) {
-  ChunkCache& cc = sm.cc;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    const Chunk ch = hs.chunks[chunk_index];
-    cc.job = -1;  // the per-job fields are not this chunk's
-    cc.chunk = chunk_index;
-    cc.nh = ch.nh;
-    cc.nlo = ch.nlo;
-    cc.nhi = ch.nhi;
-    cc.tile0 = ch.tile0;
-    cc.item0 = ch.item0;
-    cc.ntiles = ch.ntiles;
-    cc.col0 = ch.col0;
-    cc.first = ch.first;
-    cc.t0 = ch.t0;
-    sm.ts.tile_start = ch.tile0 + tile * hs.tile_bins;
-  }
-  __syncthreads();
-  const int nh = cc.nh;
-  if (tid < kWarps * kGroupMax) {
-    const int j = tid / kGroupMax, hl = tid - j * kGroupMax;
-    if (j < nj && hl < nh) {
-      const int h = hs.hist_index[cc.first + hl];
-      const double* x = jobs[j0 + j].params;
-      double cph[kMaxTerms], sph[kMaxTerms];
-      coef_row<SHAPE>(hs, [&](int q) { return slot_value(hs, x, h, q); }, sm.vg[j].gam[hl], cph, sph);
-    }
-  } else if (tid < kWarps * kGroupMax + kWarps * kMaxTerms) {
-    const int i = tid - kWarps * kGroupMax, j = i / kMaxTerms, k = i - j * kMaxTerms;
-    if (j < nj) {
-      const int h0 = hs.hist_index[cc.first];
-      const double* x = jobs[j0 + j].params;
-      VecConst& v = sm.vg[j];
-      const double nu = term_consts(hs, [&](int q) { return slot_value(hs, x, h0, q); }, k, v);
-      const double t_start = (static_cast<double>(cc.tile0 + tile * hs.tile_bins) - cc.t0) * hs.dt_us;
-      v.base[k] = v.kinds[k] == kTermTF ? tile_phase(nu, t_start) : 0.0f;
-      if (k == 0) {
-        v.tbase = static_cast<float>(t_start);
-        // log2(e) / tau_mu: E = 2^(-aE t); without the decay envelope E = 1
-        v.aE = hs.envelope ? static_cast<float>(1.4426950408889634 / kTauMuUs) : 0.0f;
-        v.dt = static_cast<float>(hs.dt_us);
-      }
-    }
-  } else if (tid < kWarps * kGroupMax + kWarps * kMaxTerms + kGroupMax) {
-    const int hl = tid - kWarps * kGroupMax - kWarps * kMaxTerms;
-    if (hl < nh) {
-      const int h = hs.hist_index[cc.first + hl];
-      cc.row[hl] = h;
-      const size_t esz = hs.store == kStoreF64 ? sizeof(double) : sizeof(float);
-      cc.rowp[hl] = static_cast<const char*>(hs.counts) + static_cast<size_t>(h) * hs.stride * esz;
-      cc.roww[hl] = hs.weights ? static_cast<const char*>(hs.weights) + static_cast<size_t>(h) * hs.stride * esz
-                               : nullptr;
-    }
-  }
-  __syncthreads();
-}
-
-template <int SHAPE, int MODE, bool GRAD>
-__global__ void __launch_bounds__(kBlock, 2) eval_vg_kernel(const Job* __restrict__ jobs, int njobs, int ngroups,
-                                                            int total) {
-  __shared__ SmemVG sm;
-  const HistSet& hs = *jobs[0].hs;  // the jobs of one vector-group launch share their histogram set
-  const int w = threadIdx.x >> 5;
-  for (int gi = blockIdx.x; gi < total; gi += gridDim.x) {
-    const int item = gi / ngroups, grp = gi - item * ngroups;
-    const int j0 = grp * kWarps, nj = min(kWarps, njobs - j0);
-    const int2 it = hs.items[item];
-    __syncthreads();  // the previous item's readers of the shared memory are done
-    load_group<SHAPE>(jobs, j0, nj, hs, it.x, it.y, sm);
-    if (w < nj) split_item<SHAPE, MODE, GRAD, true>(jobs[j0 + w], hs, item, sm, sm.vg[w]);
-    // Release: the barrier orders every warp's row writes before the counter increments.
-    __syncthreads();
-    if (threadIdx.x < nj) {
-      const unsigned prev = atom_add_acq_rel(jobs[j0 + threadIdx.x].chunk_count + it.x, 1u);
-      sm.last[threadIdx.x] = prev == static_cast<unsigned>(sm.cc.ntiles - 1);
-    }
-    __syncthreads();
-    for (int j = 0; j < nj; ++j) {
-      if (!sm.last[j]) continue;
-      const Job& jb = jobs[j0 + j];
-      load_chunk<SHAPE>(jb, hs, j0 + j, it.x, 1, sm);
-      finish_chunk<1, SHAPE, GRAD>(jb, hs, sm);
-    }
-  }
-}
-
-template <int SHAPE, int MODE, bool GRAD>
-int launch_vg_one(const Job* d_jobs, int njobs, int nitems, int num_sms, cudaStream_t stream, LaunchInfo* info) {
-  auto kern = eval_vg_kernel<SHAPE, MODE, GRAD>;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0) != cudaSuccess) return -1;
-  if (per_sm < 1) per_sm = 1;
-  const int ngroups = (njobs + kWarps - 1) / kWarps;
-  const int total = nitems * ngroups;
-  int grid = num_sms * per_sm;
-  if (grid > total) grid = total;
-  if (grid < 1) grid = 1;
-  kern<<<grid, kBlock, 0, stream>>>(d_jobs, njobs, ngroups, total);
-  if (info) {
-    info->grid = grid;
-    info->block = kBlock;
-  }
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
-}
-
-template <int SHAPE>
-int dispatch_vg(int mode, int grad, const Job* j, int n, int items, int sms, cudaStream_t s, LaunchInfo* info) {
-  if constexpr (is_list(SHAPE)) {
-    return -1;
-  } else {
-    if (mode == 0)
-      return grad ? launch_vg_one<SHAPE, 0, true>(j, n, items, sms, s, info)
-                  : launch_vg_one<SHAPE, 0, false>(j, n, items, sms, s, info);
-    if (mode == 1)
-      return grad ? launch_vg_one<SHAPE, 1, true>(j, n, items, sms, s, info)
-                  : launch_vg_one<SHAPE, 1, false>(j, n, items, sms, s, info);
-    return -1;
-  }
-}
-
-// ---------------------------------------------------------------------------------------------
 // Persistent kernel: each CTA takes a contiguous range of the launch's items.
 // ---------------------------------------------------------------------------------------------
 template <int PREC, int SHAPE, int MODE, bool GRAD>
@@ -1904,7 +1702,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 && SHAPE != kShapeList ? 2 :
     else if constexpr (SHAPE == kShapeListS)  // at most 2 terms of at most 3 primitives
       list_item<MODE, GRAD, 2, 3>(job, hs, item, sm);
     else
-      split_item<SHAPE, MODE, GRAD, false>(job, hs, item, sm, sm.cc.v);
+      split_item<SHAPE, MODE, GRAD>(job, hs, item, sm, sm.cc.v);
     complete_item<PREC, SHAPE, GRAD>(job, hs, sm);
   }
 }
@@ -1982,11 +1780,5 @@ MUSR_DECLARE_GROUP(a)
 MUSR_DECLARE_GROUP(b)
 MUSR_DECLARE_GROUP(c)
 #undef MUSR_DECLARE_GROUP
-// vector-group kernels (modes 0 and 1): shapes T1, N1, T1N1, T2 in one translation unit, T2N1,
-// T2m, T2N1m in the other; -1 for a shape without them
-int launch_vg_group_a(int shape, int mode, int grad, const Job* j, int n, int items, int sms, cudaStream_t s,
-                      LaunchInfo* info);
-int launch_vg_group_b(int shape, int mode, int grad, const Job* j, int n, int items, int sms, cudaStream_t s,
-                      LaunchInfo* info);
 
 }  // namespace musr

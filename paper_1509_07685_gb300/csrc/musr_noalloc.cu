@@ -143,6 +143,7 @@ extern "C" int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int
   hs.nterms = nterms;
   hs.nslots = nslots;
   hs.P = nparams;
+  hs.nconsts = nconsts;
   for (int k = 0; k < nterms; ++k) {
     hs.raw[k].nprim = terms[k].nprim;
     for (int m = 0; m < kMaxPrims; ++m) {

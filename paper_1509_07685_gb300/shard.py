@@ -47,20 +47,33 @@ def combine(rank_results: Sequence[np.ndarray]) -> np.ndarray:
     return out
 
 
+def bins_in_fit(problem) -> List[int]:
+    """Bins of each histogram inside the fit range: those with lo <= (n - t0) dt <= hi."""
+    dt = problem.bin_width_ns / 1000.0
+    lo, hi = problem.fit_range_us
+    n = np.arange(problem.B, dtype=np.float64)
+    out = []
+    for h in range(problem.H):
+        t = (n - float(problem.t0[h])) * dt
+        out.append(int(np.count_nonzero((t >= lo) & (t <= hi))))
+    return out
+
+
 def distributed_eval(problem, x, rank: int, world: int, evaluate: Callable, group=None) -> np.ndarray:
     """Cost and gradient of the whole fit on every rank.
 
-    ``evaluate(sub_problem, x)`` returns this rank's (1 + P) vector (value, gradient);
-    with torch.distributed initialised, the vectors are all-gathered and summed in
+    Histograms go to ranks balanced by their bins in the fit.  ``evaluate(sub_problem, x)``
+    returns this rank's (1 + P) vector (value, gradient); the vectors are all-gathered --
+    on the current CUDA device for an NCCL group, on the host otherwise -- and summed in
     rank order.  A rank without histograms contributes zeros."""
     import torch
     import torch.distributed as dist
-    bins = [problem.B] * problem.H
-    parts = partition_histograms(bins, world)
+    parts = partition_histograms(bins_in_fit(problem), world)
     P = int(problem.nparams)
     mine = parts[rank]
     local = np.zeros(1 + P) if not mine else np.asarray(evaluate(sub_problem(problem, mine), x), np.float64)
-    t = torch.tensor(local, dtype=torch.float64)
+    device = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend(group) == "nccl" else "cpu"
+    t = torch.tensor(local, dtype=torch.float64, device=device)
     gathered = [torch.zeros_like(t) for _ in range(world)]
     dist.all_gather(gathered, t, group=group)
-    return combine([g.numpy() for g in gathered])
+    return combine([g.cpu().numpy() for g in gathered])

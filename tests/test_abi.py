@@ -66,12 +66,3 @@ def test_server_create_without_gpu_reports_error(lib):
     with pytest.raises(binding.MusrError) as e:
         binding.musr_server_create(0, 1 << 30, 4)
     assert e.value.status == binding.MUSR_ECUDA
-
-
-def test_bounded_wait_check_without_gpu_reports_error(lib):
-    from conftest import cuda_available
-    if cuda_available():
-        pytest.skip("a GPU is present")
-    from paper_1509_07685_gb300 import binding
-    st, _, _ = binding.musr_check_bounded_wait(0)
-    assert st == binding.MUSR_EINVAL

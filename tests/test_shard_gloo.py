@@ -70,6 +70,19 @@ def test_histogram_split_over_two_gloo_ranks_matches_single_rank():
     assert all(tmax == 1.5 for _, _, tmax in out)
 
 
+def test_partition_follows_the_bins_in_the_fit():
+    """A histogram whose fit window holds few bins counts for those bins only."""
+    import dataclasses
+    from paper_1509_07685_gb300 import shard
+    p = mi.cfg2(nhist=4, nbins=1000, bin_width_ns=10.0, seed=52)
+    q = dataclasses.replace(p, t0=np.array([0.0, 0.0, 0.0, 900.0]))  # the last starts 900 bins late
+    bins = shard.bins_in_fit(q)
+    assert bins[:3] == [bins[0]] * 3 and bins[3] < bins[0] // 5
+    parts = shard.partition_histograms(bins, 2)
+    loads = sorted(sum(bins[h] for h in part) for part in parts)
+    assert loads[1] - loads[0] <= max(bins)
+
+
 def test_partition_is_balanced_and_complete():
     from paper_1509_07685_gb300 import shard
     bins = [100, 90, 80, 10, 10, 10, 5]
