@@ -197,8 +197,9 @@ __device__ __forceinline__ double slot_value(const HistSet& hs, const double* x,
 // One evaluation's constants of the SPLIT basis kernels on one chunk and tile: what the
 // per-bin loop reads (kept in the chunk cache).
 struct VecConst {
-  // [Nbkg, Gam_0 .. Gam_{M-1}] of each histogram (16-byte rows: vector loads)
-  alignas(16) float gam[kGroupMax][kGamStride];
+  // [Nbkg, Gam_0 .. Gam_{M-1}] of each histogram, each value twice (the (x, x) pair that the
+  // packed FP32x2 instructions take as an operand; 16-byte rows: vector loads)
+  alignas(16) float2 gam2[kGroupMax][kGamStride];
   int kinds[kMaxTerms];
   float ca[kMaxTerms], cb[kMaxTerms];  // E*X_k = ex2(-(ca t + cb t^2))  (ca includes 1/tau)
   float dh[kMaxTerms], d2[kMaxTerms];  // KT: g = ex2(-dh t^2), u = d2 t^2
@@ -321,7 +322,7 @@ __device__ __forceinline__ void phase_cs(double phi_deg, double* c, double* s) {
 // Coefficients [Nbkg, Gam_0 .. Gam_{M-1}] of one histogram's basis expansion from its slot
 // values slot(s), computed in FP64 and rounded once; cos and sin of each cosine term's phase.
 template <int SHAPE, class Slot>
-__device__ void coef_row(const HistSet& hs, Slot slot, float* gam, double* cph, double* sph) {
+__device__ void coef_row(const HistSet& hs, Slot slot, float2* gam2, double* cph, double* sph) {
   using Bs = Basis<SHAPE>;
   double g[kGamStride];
 #pragma unroll
@@ -354,7 +355,10 @@ __device__ void coef_row(const HistSet& hs, Slot slot, float* gam, double* cph, 
     }
   }
 #pragma unroll
-  for (int i = 0; i < kGamStride; ++i) gam[i] = static_cast<float>(g[i]);
+  for (int i = 0; i < kGamStride; ++i) {
+    const float v = static_cast<float>(g[i]);
+    gam2[i] = make_float2(v, v);
+  }
 }
 
 // Constants of term k shared by a chunk's histograms (from the slot values slot(s) of its
@@ -449,7 +453,7 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
   const double dt = hs.dt_us;
   if (tid < nh) {
     const int hl = tid;
-    coef_row<SHAPE>(hs, [&](int q) { return cc.loc[hl][q]; }, cc.v.gam[hl], cc.cph[hl], cc.sph[hl]);
+    coef_row<SHAPE>(hs, [&](int q) { return cc.loc[hl][q]; }, cc.v.gam2[hl], cc.cph[hl], cc.sph[hl]);
     const double N0 = cc.loc[hl][0];
     // Directional derivative of the coefficients along a Gauss-Newton direction (zeros without).
     double gd[kGamStride];
@@ -1017,7 +1021,8 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
   constexpr int G = Bs::G;
   constexpr int NPH = Bs::NPH;
   constexpr int NCH = Bs::NCH;
-  constexpr int NG4 = (M + 1 + 3) / 4;  // float4 loads per coefficient row
+  constexpr int NG4 = (M + 1 + 3) / 4;  // float4 loads per row of Gauss-Newton coefficient derivatives
+  constexpr int NQ = (M + 2) / 2;       // float4 loads per coefficient row (two duplicated values each)
   constexpr int BPT = kBinsPerThread;   // consecutive bins per thread per iteration
   static_assert(BPT == 2, "the loads below read float2 / double2");
 
@@ -1222,7 +1227,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
         gd[4 * q + 3] = x.w;
       }
     };
-    auto fetch = [&](int hl, float (&d)[BPT], float (&gm)[4 * NG4]) {
+    auto fetch = [&](int hl, float (&d)[BPT], float2 (&gm)[2 * NQ]) {
       if (staged) {
         const float2 q = *reinterpret_cast<const float2*>(sm.stage_slot(b, hl, tb * BPT));
         d[0] = q.x;
@@ -1236,12 +1241,10 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
         d[1] = static_cast<float>(q.y);
       }
 #pragma unroll
-      for (int q = 0; q < NG4; ++q) {
-        const float4 x = *reinterpret_cast<const float4*>(&vc.gam[hl][4 * q]);
-        gm[4 * q] = x.x;
-        gm[4 * q + 1] = x.y;
-        gm[4 * q + 2] = x.z;
-        gm[4 * q + 3] = x.w;
+      for (int q = 0; q < NQ; ++q) {
+        const float4 x = *reinterpret_cast<const float4*>(&vc.gam2[hl][2 * q]);
+        gm[2 * q] = make_float2(x.x, x.y);
+        gm[2 * q + 1] = make_float2(x.z, x.w);
       }
     };
     auto fetch_w = [&](int hl) {  // the thread's two weights of histogram hl < nh (0 past the row)
@@ -1252,18 +1255,20 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
       constexpr bool MASKED = decltype(masked_tag)::value;
       // One histogram ahead: the shared-memory loads of histogram hl + 1 are in flight while
       // histogram hl is evaluated.
-      float dn[BPT], gn[4 * NG4];
+      float dn[BPT];
+      float2 gn[2 * NQ];
       float2 wn = make_float2(0.0f, 0.0f);  // chi^2 weights of asymmetry data (MODE 4), one ahead
       fetch(0, dn, gn);
       if (MODE == 4) wn = fetch_w(0);
 #pragma unroll
       for (int hl = 0; hl < G; ++hl) {
         if (hl >= nh) break;
-        float d[BPT], gm[4 * NG4];  // counts; Nbkg, Gam_0 .. Gam_{M-1}
+        float d[BPT];
+        float2 gm[2 * NQ];  // counts; (x, x) pairs of Nbkg, Gam_0 .. Gam_{M-1}
 #pragma unroll
         for (int j = 0; j < BPT; ++j) d[j] = dn[j];
 #pragma unroll
-        for (int q = 0; q < 4 * NG4; ++q) gm[q] = gn[q];
+        for (int q = 0; q < 2 * NQ; ++q) gm[q] = gn[q];
         const float2 wc = wn;
         if (hl + 1 < G) fetch(hl + 1, dn, gn);
         if (MODE == 4 && hl + 1 < nh) wn = fetch_w(hl + 1);  // weight rows exist up to nh only
@@ -1272,11 +1277,11 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
           fetch_dot(hl, gdv);
 #pragma unroll
           for (int j = 0; j < BPT; ++j) {
-            float N = gm[0], Nd = gdv[0];
+            float N = gm[0].x, Nd = gdv[0];
 #pragma unroll
             for (int m = 0; m < M; ++m) {
-              N = fmaf(gm[1 + m], B[m][j], N);
-              Nd = fmaf(gdv[1 + m], B[m][j], fmaf(gm[1 + m], Bd[m % (GN ? M : 1)][j], Nd));
+              N = fmaf(gm[1 + m].x, B[m][j], N);
+              Nd = fmaf(gdv[1 + m], B[m][j], fmaf(gm[1 + m].x, Bd[m % (GN ? M : 1)][j], Nd));
             }
             const float dd = d[j];
             float w;
@@ -1296,16 +1301,16 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
             for (int m = 0; m < M; ++m) gacc[hl][m] = fmaf(u, B[m][j], gacc[hl][m]);
             gacc[hl][M] += u;
 #pragma unroll
-            for (int m = 0; m < M; ++m) V[m][j] = fmaf(u, gm[1 + m], V[m][j]);
+            for (int m = 0; m < M; ++m) V[m][j] = fmaf(u, gm[1 + m].x, V[m][j]);
           }
           continue;
         }
         {  // the thread's two bins as one float2: packed FP32 (two lanes' work per instruction)
           const float2 dd2 = make_float2(d[0], d[1]);
-          float2 N2 = make_float2(gm[0], gm[0]);
+          float2 N2 = gm[0];
 #pragma unroll
           for (int m = 0; m < M; ++m)
-            N2 = __ffma2_rn(make_float2(gm[1 + m], gm[1 + m]), make_float2(B[m][0], B[m][1]), N2);
+            N2 = __ffma2_rn(gm[1 + m], make_float2(B[m][0], B[m][1]), N2);
           const float2 r2 = __fadd2_rn(N2, make_float2(-dd2.x, -dd2.y));
           float2 v2, u2;
           if (MODE == 0 || MODE == 4) {
@@ -1350,7 +1355,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
             gacc[hl][M] = (gacc[hl][M] + u2.x) + u2.y;
 #pragma unroll
             for (int m = 0; m < M; ++m) {
-              const float2 Vm = __ffma2_rn(u2, make_float2(gm[1 + m], gm[1 + m]), make_float2(V[m][0], V[m][1]));
+              const float2 Vm = __ffma2_rn(u2, gm[1 + m], make_float2(V[m][0], V[m][1]));
               V[m][0] = Vm.x;
               V[m][1] = Vm.y;
             }
