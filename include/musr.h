@@ -378,7 +378,9 @@ int musr_server_stats_get(musr_server* s, musr_server_stats* out);
  * arrays, read before the call returns.  Their meaning is that of
  * musr_upload_histograms, musr_set_theory and musr_set_map, and every theory
  * those accept runs here too (at MUSR_SPLIT, one without a basis form evaluates
- * its term list per bin).  The call is asynchronous on cuda_stream (NULL: the
+ * its term list per bin), except one with the dynamic Kubo-Toyabe primitive
+ * MUSR_PRIM_DKT, whose per-evaluation tables have no room here (MUSR_EINVAL).
+ * The call is asynchronous on cuda_stream (NULL: the
  * legacy default stream).  d_out[0] is +inf where the likelihood is undefined or a
  * parameter is not finite (the call has returned MUSR_OK by then: read the value before
  * trusting the gradient).
