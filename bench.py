@@ -818,6 +818,9 @@ def _serving(B, n_requests, window=1024, seed=4, pool_size=256):
     pool = mi.serving_pool(pool_size, seed=seed, workers=os.cpu_count() or 1)
     out = {"requests": n_requests, "pool": len(pool), "precision": "split", "hbm_budget_gib": 8, "max_active": 1024}
     reqs = mi.request_stream(pool, n_requests, 0.0, seed=seed)
+    # Warm-up (untimed): one pass over the pool's fits, so that the timed runs do not include
+    # the first touch of the pool's host memory and the helper threads' first copies.
+    _saturation(B, mi.request_stream(pool, len(pool) + 64, 0.0, seed=seed + 99), B.MUSR_SPLIT, 2 << 30, window)
     rate, wall, conv, st = _saturation(B, reqs, B.MUSR_SPLIT, 8 << 30, window)
     out["saturation"] = {"fits_per_s": rate, "wall_s": wall, "converged": conv,
                          "gbins_per_s": st["bin_evals"] / wall / 1e9, "steps": st["steps"],

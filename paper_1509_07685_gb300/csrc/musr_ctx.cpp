@@ -394,8 +394,8 @@ int compile(musr_ctx* ctx, int prec, int var) {
       ch.tile0 = ch.nlo & ~3;
       chunks.push_back(ch);
     }
-  // Tiles: at most 16 iterations of the CTA per tile (the SPLIT phase split
-  // needs tile offsets below 2^14 bins).
+  // Tiles: at most 64 iterations of the CTA per tile (the SPLIT phase split
+  // needs tile offsets below 2^15 bins).
   std::vector<int64_t> ranges;
   for (const auto& ch : chunks) ranges.push_back(ch.nhi - ch.tile0);
   hs.tile_bins = musr::bins_per_iteration(prec) << var;

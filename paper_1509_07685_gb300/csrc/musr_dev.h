@@ -24,7 +24,7 @@ constexpr double kTauMuUs = 2.197019;  // muon lifetime, microseconds
 constexpr int kBlock = 256;            // threads per CTA
 constexpr int kWarps = kBlock / 32;
 constexpr int kBinsPerThread = 2;      // SPLIT: one 8-byte load of FP32 counts per histogram
-constexpr int kMaxTileBins = 16384;    // SPLIT phase split: bin offsets in a tile stay below 2^14
+constexpr int kMaxTileBins = 32768;    // SPLIT phase split: bin offsets in a tile stay below 2^15
 constexpr int kGroupMax = 8;           // histograms per SPLIT chunk
 constexpr int kMaxTerms = 4;
 constexpr int kMaxPrims = 4;
@@ -247,8 +247,8 @@ int launch_prepare_counts_shifted(const void* raw, void* img, const int64_t* shi
                                   int64_t nbins, int64_t stride, unsigned* flag, unsigned seq, int num_sms,
                                   void* stream);
 // Decompositions compiled per precision: tile v holds (bins per CTA iteration) << v
-// bins -- SPLIT 512 ... 16384 (the phase-split limit), FP64 256 ... 8192.
-constexpr int kVariants = 6;
+// bins -- SPLIT 512 ... 32768 (the phase-split limit), FP64 256 ... 16384.
+constexpr int kVariants = 7;
 inline int bins_per_iteration(int precision) { return precision == 1 ? kBlock * kBinsPerThread : kBlock; }
 
 // The decomposition of a launch of nvec evaluations (items[v]: work items of one

@@ -253,7 +253,7 @@ struct ChunkCache {
   alignas(16) float gdot[kGroupMax][kGamStride];
   // term lists without a basis form (list_item), per (term k, primitive m) = k * kMaxPrims + m:
   // the phase step per bin of a cosine or Bessel primitive in turns, split so that
-  // (bin offset < 2^14) * lhi is exact in FP32
+  // (bin offset < 2^15) * lhi is exact in FP32
   float lhi[kMaxTerms * kMaxPrims], llo[kMaxTerms * kMaxPrims], lstep[kMaxTerms * kMaxPrims];
   float dlam[kMaxTerms], dsig[kMaxTerms], dnu[kMaxTerms], ddel[kMaxTerms];
   double nu[kMaxTerms];
@@ -417,8 +417,8 @@ __device__ double term_consts(const HistSet& hs, Slot slot, int k, VecConst& v) 
   if (ct.kind != kTermTF) return 0.0;
   const double nu = slot(ct.nu_slot);
   const double step = nu * hs.dt_us;  // turns per bin (FP64)
-  // Exact split: hi keeps 10 significant bits, so (bin offset < 2^14) * hi is exact in FP32.
-  const float hi = __uint_as_float(__float_as_uint(static_cast<float>(step)) & 0xFFFFC000u);
+  // Exact split: hi keeps 9 significant bits, so (bin offset < 2^15) * hi is exact in FP32.
+  const float hi = __uint_as_float(__float_as_uint(static_cast<float>(step)) & 0xFFFF8000u);
   v.shi[k] = hi;
   v.slo[k] = static_cast<float>(step - static_cast<double>(hi));
   v.sstep[k] = static_cast<float>(step);
@@ -778,7 +778,7 @@ __device__ double fp64_slot(const HistSet& hs, const double* tot, int s) {
 }
 
 // Term lists without a basis form: per (term, primitive) with a phase, its step per bin in
-// turns (FP64, then split so that (bin offset < 2^14) * lhi is exact in FP32; the Bessel
+// turns (FP64, then split so that (bin offset < 2^15) * lhi is exact in FP32; the Bessel
 // step in radians), once per chunk.
 __device__ void load_chunk_list(const HistSet& hs, Smem& sm) {
   const int tid = threadIdx.x;
@@ -788,7 +788,7 @@ __device__ void load_chunk_list(const HistSet& hs, Smem& sm) {
     if (k < hs.nterms && m < hs.raw[k].nprim &&
         (hs.raw[k].kind[m] == kTFCos || hs.raw[k].kind[m] == kBessel)) {
       const double step = sm.cc.loc[0][hs.raw[k].slot[m][0]] * hs.dt_us;
-      hi = __uint_as_float(__float_as_uint(static_cast<float>(step)) & 0xFFFFC000u);
+      hi = __uint_as_float(__float_as_uint(static_cast<float>(step)) & 0xFFFF8000u);
       lo = static_cast<float>(step - static_cast<double>(hi));
       st = static_cast<float>(hs.raw[k].kind[m] == kBessel ? kTwoPi * step : step);
     }
@@ -851,7 +851,7 @@ __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm)
   int bad = 0;
 
   const int end = min(nhi, ts + hs.tile_bins);
-  // The bin offset in the tile is carried as an exact float (< 2^14 here): time and phases
+  // The bin offset in the tile is carried as an exact float (< 2^15 here): time and phases
   // come from the tile's FP64 bases plus FP32 increments, with no FP64 work per bin.
   float fm = static_cast<float>(tid);
   for (int n = ts + tid; n < end; n += kBlock, fm += static_cast<float>(kBlock)) {
@@ -1089,7 +1089,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
   // int-to-float conversion per bin would occupy this GPU's slow FP64/conversion pipe.
   float fm0 = static_cast<float>(tb * BPT);
   for (int it = 0; it < iters; ++it, fm0 += static_cast<float>(CHUNK_BINS)) {
-    const int m0 = it * CHUNK_BINS + tb * BPT;  // offset in the tile (< 2^14)
+    const int m0 = it * CHUNK_BINS + tb * BPT;  // offset in the tile (< 2^15)
     const int n0 = ts + m0;
     const int b = it & 1;
     if (staged) {

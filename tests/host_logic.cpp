@@ -146,11 +146,11 @@ void plan_cases() {
 
 void pick_cases() {
   // Items of one evaluation for tiles of 512 << v bins.
-  const int cfg2[6] = {128, 64, 32, 16, 8, 4};
+  const int cfg2[musr::kVariants] = {128, 64, 32, 16, 8, 4, 2};
   for (int nvec : {1, 8, 64, 152}) {
     std::printf("{\"name\": \"pick\", \"nvec\": %d, \"v\": %d, \"costs\": [", nvec,
                 musr::pick_decomposition(cfg2, nvec, 304, 1.3));
-    for (int v = 0; v < 6; ++v) {
+    for (int v = 0; v < musr::kVariants; ++v) {
       const long long per = (static_cast<long long>(nvec) * cfg2[v] + 303) / 304;
       std::printf("%s%.6g", v ? ", " : "", per * ((1 << v) + 1.3));
     }

@@ -427,6 +427,20 @@ def test_full_size_in_the_benchmark_launch_configuration(B):
         _check_fp64(v64[i], g64[i], ref)
 
 
+@pytest.mark.slow
+def test_large_fit_in_the_benchmark_launch_configuration(B):
+    """64 x 2^20 bins with 64 parameter vectors per launch of -2lnL value+gradient, the launch
+    the benchmark's contract line times (tiles of 32768 bins, the longest FP32 runs per
+    thread): the first and the last vector of the batch against the oracle's full sums."""
+    p = mi.cfg5()
+    X = mi.jitter(p.truth, 64, seed=1, lo=0.98, hi=1.02)
+    with B.Context(p) as ctx:
+        vs, gs, st = ctx.eval_batch(X, 1, B.MUSR_SPLIT)
+        assert st == 0
+    for i in (0, 63):
+        _check_split(vs[i], gs[i], oracle.cost(p, X[i], 1))
+
+
 def test_hbm_budget_is_enforced(B):
     p = mi.cfg2(nhist=8, nbins=65536, seed=2)
     ctx = B.musr_ctx_create(0, hbm_budget_bytes=1 << 20)

@@ -80,4 +80,4 @@ def test_decomposition_cost_model(run):
     for nvec, d in r.items():
         costs = d["costs"]
         assert d["v"] == int(np.argmin(costs))  # the first (smallest-tile) minimum
-    assert r[1]["v"] == 0 and r[8]["v"] == 2 and r[64]["v"] == 5
+    assert r[1]["v"] == 0 and r[8]["v"] == 2 and r[64]["v"] == 5 and r[152]["v"] == 6
