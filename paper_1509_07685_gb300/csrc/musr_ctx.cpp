@@ -60,25 +60,34 @@ int Arena::init(size_t bytes) {
   }
   cap_ = bytes;
   free_.clear();
+  by_size_.clear();
   live_.clear();
-  free_[0] = bytes;
+  insert_free(0, bytes);
   used_ = 0;
   return MUSR_OK;
+}
+
+void Arena::insert_free(size_t off, size_t size) {
+  free_[off] = size;
+  by_size_.insert({size, off});
+}
+
+void Arena::erase_free(std::map<size_t, size_t>::iterator it) {
+  by_size_.erase({it->second, it->first});
+  free_.erase(it);
 }
 
 void* Arena::alloc(size_t bytes) {
   bytes = (bytes + 255) & ~size_t(255);
   std::lock_guard<std::mutex> lock(mu_);
-  for (auto it = free_.begin(); it != free_.end(); ++it) {
-    if (it->second < bytes) continue;
-    const size_t off = it->first, rest = it->second - bytes;
-    free_.erase(it);
-    if (rest) free_[off + bytes] = rest;
-    live_[off] = bytes;
-    used_ += bytes;
-    return base_ + off;
-  }
-  return nullptr;
+  const auto best = by_size_.lower_bound({bytes, 0});
+  if (best == by_size_.end()) return nullptr;
+  const size_t off = best->second, rest = best->first - bytes;
+  erase_free(free_.find(off));
+  if (rest) insert_free(off + bytes, rest);
+  live_[off] = bytes;
+  used_ += bytes;
+  return base_ + off;
 }
 
 void Arena::release(void* p) {
@@ -92,17 +101,18 @@ void Arena::release(void* p) {
   auto next = free_.lower_bound(start);
   if (next != free_.end() && next->first == start + size) {  // merge with the following range
     size += next->second;
-    free_.erase(next);
+    erase_free(next);
   }
   auto prev = free_.lower_bound(start);
   if (prev != free_.begin()) {
     --prev;
     if (prev->first + prev->second == start) {  // merge with the preceding range
-      prev->second += size;
-      return;
+      start = prev->first;
+      size += prev->second;
+      erase_free(prev);
     }
   }
-  free_[start] = size;
+  insert_free(start, size);
 }
 
 size_t Arena::used() const {

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <map>
+#include <set>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -20,7 +21,7 @@ struct DevBuf {
   bool from_arena = false;
 };
 
-// A device memory arena: one cudaMalloc of the HBM budget, carved first-fit in
+// A device memory arena: one cudaMalloc of the HBM budget, carved best-fit in
 // 256-byte units.  Allocation fails (nullptr) when no free range is large enough,
 // which is how the serving loop admits fits by budget.  Thread-safe.
 class Arena {
@@ -33,10 +34,16 @@ class Arena {
   size_t used() const;
 
  private:
+  void insert_free(size_t off, size_t size);
+  void erase_free(std::map<size_t, size_t>::iterator it);
+
   char* base_ = nullptr;
   size_t cap_ = 0, used_ = 0;
-  std::map<size_t, size_t> free_;  // offset -> size
-  std::map<size_t, size_t> live_;  // offset -> size
+  // Free ranges twice: by offset (to merge neighbours on release) and by (size, offset)
+  // (best fit in O(log n): the smallest range that holds the request, lowest offset first).
+  std::map<size_t, size_t> free_;              // offset -> size
+  std::set<std::pair<size_t, size_t>> by_size_;  // (size, offset)
+  std::map<size_t, size_t> live_;              // offset -> size
   mutable std::mutex mu_;
 };
 

@@ -120,10 +120,11 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Per-thread asynchronous copies global -> shared (cp.async, documented PTX ISA): 8 bytes,
-// zero-filled beyond src_bytes; completion tracked per thread in commit groups.
-__device__ __forceinline__ void cp_async8(void* dst, const void* src, unsigned src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)),
+// Per-thread asynchronous copy global -> shared (cp.async, documented PTX ISA): 16 bytes
+// through the L2 only (.cg), both addresses 16-byte aligned, zero-filled beyond src_bytes;
+// completion tracked per thread in commit groups.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, unsigned src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)),
                "l"(__cvta_generic_to_global(src)), "r"(src_bytes)
                : "memory");
 }
@@ -1064,22 +1065,28 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
   constexpr int CHUNK_BINS = kBlock * BPT;  // bins of one CTA iteration
   // Iterations of this tile that hold any bin of the fit range (the same for every thread).
   const int iters = min(hs.tile_bins / CHUNK_BINS, (nhi - ts + CHUNK_BINS - 1) / CHUNK_BINS);
-  // FP32 counts are staged into shared memory one iteration ahead, each thread copying its
-  // own two bins of every histogram (cp.async, 8 bytes) and reading back only those: no
-  // CTA-wide barrier per iteration, the warps run independently through the tile.
+  // FP32 counts are staged into shared memory one iteration ahead by 16-byte cp.async copies,
+  // each pair of lanes copying the 4 bins it reads of every histogram (half the histograms
+  // each) and meeting at a warp barrier: no CTA-wide barrier per iteration, the warps run
+  // independently through the tile.  Borrowed rows are 16-byte aligned with a stride of a
+  // multiple of 4, and tiles start at multiples of 4 bins, so every copy is aligned.
   const bool staged = store == kStoreF32;
   const int64_t stride = hs.stride;
-  auto issue = [&](int itn) {  // this thread's bins of iteration itn into buffer itn & 1
+  // Lanes 2q and 2q + 1 of a warp share the 16-byte block of bins [4q, 4q + 4) of the
+  // iteration: the even lane copies it for the even histograms, the odd lane for the odd.
+  const int par = tb & 1, q4 = (tb >> 1) * 4;
+  auto issue = [&](int itn) {  // bins [4q, 4q + 4) of iteration itn into buffer itn & 1
     if (itn < iters) {
-      // n is even and stride a multiple of 64, so n < stride means both bins lie in the row
-      const int64_t n = ts + static_cast<int64_t>(itn) * CHUNK_BINS + tb * BPT;
+      // n is a multiple of 4 and so is stride, so n < stride means all 4 bins lie in the row
+      const int64_t n = ts + static_cast<int64_t>(itn) * CHUNK_BINS + q4;
       const bool in = n < stride;
 #pragma unroll
-      for (int hl = 0; hl < G; ++hl) {
+      for (int i = 0; i < (G + 1) / 2; ++i) {
+        const int hl = 2 * i + par;
         if (hl >= nh) break;
         const bool ok = dbg_ok(job.dbg, cc.row[hl] >= 0 && cc.row[hl] < hs.H && n >= 0, kDbgHist);
-        cp_async8(sm.stage_slot(itn & 1, hl, tb * BPT),
-                  static_cast<const float*>(cc.rowp[hl]) + (in && ok ? n : 0), in && ok ? 8u : 0u);
+        cp_async16(sm.stage_slot(itn & 1, hl, q4),
+                   static_cast<const float*>(cc.rowp[hl]) + (in && ok ? n : 0), in && ok ? 16u : 0u);
       }
     }
     cp_async_commit();  // one group per iteration (empty past the tile's end)
@@ -1093,10 +1100,13 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     const int n0 = ts + m0;
     const int b = it & 1;
     if (staged) {
-      // buffer b ^ 1 was read by this thread in iteration it - 1: refill it for it + 1, then
-      // wait for this thread's copies of iteration it (all but the newest group)
+      // buffer b ^ 1 was read by this lane and its partner in iteration it - 1: once both
+      // are past it, refill it for it + 1, then wait for this lane's copies of iteration it
+      // (all but the newest group) and for the partner's
+      __syncwarp();
       issue(it + 1);
       cp_async_wait<1>();
+      __syncwarp();
     }
     float t[BPT];
     bool valid[BPT];
