@@ -195,6 +195,47 @@ struct CheckFlag {
 };
 thread_local CheckFlag tl_flag;
 
+// A pinned staging buffer of the calling thread for uploads made with setup_stream set (the
+// serving loop's helper threads).  Copies from pageable memory go through the driver's own
+// staging, which concurrent threads share; each helper instead copies the rows into its own
+// pinned buffer (host memcpy, in parallel on the host cores) and the device reads them from
+// there asynchronously.  The helper waits for its stream before its next upload, so the
+// buffer is free again by then.  Requests larger than kMaxBounce take the pageable copy.
+struct Bounce {
+  static constexpr size_t kMaxBounce = size_t(256) << 20;
+  void* p = nullptr;
+  size_t cap = 0;
+  ~Bounce() {
+    if (p) cudaFreeHost(p);
+  }
+  void* get(size_t bytes) {
+    if (bytes > kMaxBounce) return nullptr;
+    if (bytes <= cap) return p;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    const size_t want = std::max(bytes, size_t(16) << 20);
+    if (cudaHostAlloc(&p, want, cudaHostAllocPortable) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return nullptr;
+    }
+    cap = want;
+    return p;
+  }
+};
+thread_local Bounce tl_bounce;
+
+// The host rows `counts` ([nhist][nbins] of esz bytes) as the source of an asynchronous copy:
+// the thread's pinned staging buffer when the upload is a serving helper's, else as given.
+const void* stage_rows(musr_ctx* ctx, const void* counts, size_t bytes) {
+  if (!ctx->setup_stream) return counts;
+  void* b = tl_bounce.get(bytes);
+  if (!b) return counts;
+  std::memcpy(b, counts, bytes);
+  return b;
+}
+
 DeviceScope::DeviceScope(int dev) {
   cudaGetDevice(&prev_);
   if (prev_ != dev) cudaSetDevice(dev);
@@ -863,9 +904,10 @@ int musr_upload_histograms(musr_ctx* ctx, const void* counts, int dtype, int nhi
   if (!flag.ready()) return cuda_fail(ctx, cudaGetLastError(), "cudaHostAlloc(check flag)");
   const unsigned seq = flag.next();
   cudaError_t e;
+  const void* src = stage_rows(ctx, counts, row * static_cast<size_t>(nhist));
   if (!shifted) {
-    e = stride == nbins ? cudaMemcpyAsync(ctx->counts_own.p, counts, total, cudaMemcpyHostToDevice, st)
-                        : cudaMemcpy2DAsync(ctx->counts_own.p, static_cast<size_t>(stride) * esz, counts, row, row,
+    e = stride == nbins ? cudaMemcpyAsync(ctx->counts_own.p, src, total, cudaMemcpyHostToDevice, st)
+                        : cudaMemcpy2DAsync(ctx->counts_own.p, static_cast<size_t>(stride) * esz, src, row, row,
                                             static_cast<size_t>(nhist), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(counts)");
     if (launch_prepare_counts(ctx->counts_own.p, dtype, nhist, nbins, stride, flag.dev, seq, ctx->num_sms, st))
@@ -875,7 +917,7 @@ int musr_upload_histograms(musr_ctx* ctx, const void* counts, int dtype, int nhi
     if ((rc = dalloc(ctx, ctx->upload_scratch, raw + sizeof(int64_t) * nhist))) return rc;
     char* sp = static_cast<char*>(ctx->upload_scratch.p);
     ctx->shift = std::move(shift);  // the copy's source, kept until the check is read
-    e = cudaMemcpyAsync(sp, counts, row * nhist, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(sp, src, row * nhist, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(sp + raw, ctx->shift.data(), sizeof(int64_t) * nhist, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(counts)");
