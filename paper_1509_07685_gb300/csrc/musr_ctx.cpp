@@ -413,8 +413,9 @@ int compile(musr_ctx* ctx, int prec, int var) {
         const CanonTerm& ct = hs.canon[k];
         for (int i = 0; i < ct.nexp; ++i) push_entry(key, h, ct.exp_slot[i]);
         for (int i = 0; i < ct.ngauss; ++i) push_entry(key, h, ct.gauss_slot[i]);
-        if (ct.kind == musr::kTermKT || ct.kind == musr::kTermLKT) push_entry(key, h, ct.kt_slot);
-        if (ct.kind == musr::kTermTF) push_entry(key, h, ct.nu_slot);
+        if (ct.kind == musr::kTermKT || ct.kind == musr::kTermLKT || ct.kind == musr::kTermDKT)
+          push_entry(key, h, ct.kt_slot);
+        if (ct.kind == musr::kTermTF || ct.kind == musr::kTermDKT) push_entry(key, h, ct.nu_slot);
       }
       auto it = key_to_group.find(key);
       if (it == key_to_group.end()) {

@@ -55,7 +55,7 @@ constexpr double kDktStep = 0.02; // grid spacing times the faster of Delta and 
 constexpr int kDktHeader = 4;
 constexpr int kDktTable = kDktHeader + 3 * (kDktMaxK + 1);   // values per source table
 constexpr int kDktWork = 7 * (2 * kDktMaxK + 1);              // scratch values per source (finer grid)
-enum TermKind : int { kTermNone = 0, kTermPlain = 1, kTermTF = 2, kTermKT = 3, kTermLKT = 4 };
+enum TermKind : int { kTermNone = 0, kTermPlain = 1, kTermTF = 2, kTermKT = 3, kTermLKT = 4, kTermDKT = 5 };
 
 // SPLIT shapes.  Every model the SPLIT path accepts is, for each histogram j of a
 // chunk, a linear combination of M time-only basis functions B_m(t) with
@@ -93,15 +93,16 @@ struct RawTerm {
 //   a * exp(-Lambda t - S t^2 / 2) * [KT(Delta, t) or LKT(a, t)] * [cos(2 pi (nu t + phi / 360))]
 // with Lambda the sum of its EXP rates and S the sum of its squared GAUSS widths.
 struct CanonTerm {
-  int kind;  // kTermPlain, kTermTF, kTermKT, kTermLKT
+  int kind;  // kTermPlain, kTermTF, kTermKT, kTermLKT, kTermDKT
   int amp_slot;  // -1: no AMP factor
   int nexp;
   int exp_slot[kMaxPrims];
   int ngauss;
   int gauss_slot[kMaxPrims];
-  int kt_slot;   // kTermKT: Delta; kTermLKT: a
-  int nu_slot;   // kTermTF
+  int kt_slot;   // kTermKT, kTermDKT: Delta; kTermLKT: a
+  int nu_slot;   // kTermTF: the frequency; kTermDKT: the fluctuation rate
   int phi_slot;  // kTermTF
+  int dkt_term, dkt_prim;  // kTermDKT: the factor's term and primitive in the theory as given
 };
 
 // How a SPLIT channel turns into the derivative of one local slot.
@@ -116,7 +117,9 @@ enum ContribKind : int {
   kCSig = 5,   // d/dsigma  = 4 sigma ch_S[k]
   kCNu = 6,    // d/dnu     = 2 ch_nu[k]
   kCDel = 7,   // d/dDelta  = (4/3) Delta ch_Delta[k]
-  kCLkt = 8    // d/da (Lorentzian KT) = (4/3) ch_Delta[k]
+  kCLkt = 8,   // d/da (Lorentzian KT) = (4/3) ch_Delta[k]
+  kCDktD = 9,  // d/dDelta (dynamic KT) = 2 ch_Delta[k]
+  kCDktN = 10  // d/dnu (dynamic KT)    = 2 ch_nu[k]
 };
 struct Contrib {
   int slot;

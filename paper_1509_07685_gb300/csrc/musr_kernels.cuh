@@ -233,6 +233,7 @@ struct VecConst {
   float shi[kMaxTerms], slo[kMaxTerms], sstep[kMaxTerms];
   float bamp[kMaxTerms];               // amplitude carried by the basis (merged shapes), else 1
   float base[kMaxTerms];               // phase (turns, in [-1/2, 1/2]) of each TF term at the tile's first bin
+  int dkt_src[kMaxTerms];              // dynamic Kubo-Toyabe term: its table in the evaluation's set
   float tbase;                         // time of the tile's first bin
   float aE, dt;
 };
@@ -277,6 +278,7 @@ struct Smem {
   __device__ float* stage_slot(int b, int hl, int bin) { return &stage[b][hl][bin]; }
   ChunkCache cc;
   TileState ts;
+  float dkn[kMaxTerms][kBinsPerThread][kBlock];  // d/dnu factors of dynamic Kubo-Toyabe terms, per thread
   float cred[kWarps][kMaxChan];  // per-warp FP32 channel sums
   float vred[kWarps][2];         // per-warp float-float value
   double dred[kWarps][kFp64Channels + 2];
@@ -297,6 +299,9 @@ template <int NT_, int NTF_, int M_, int G_, bool MERGED_>
 struct BasisBase {
   static constexpr int NT = NT_, NTF = NTF_, M = M_, G = G_;
   static constexpr bool MERGED = MERGED_;
+  // Whether a term may carry a dynamic Kubo-Toyabe factor: every unmerged shape (the planner
+  // does not merge a theory that has one, so the merged kernels carry no code for it).
+  static constexpr bool DKT = !MERGED_;
   static constexpr int NPH = M + 1;
   static constexpr int NCH = G * NPH + 4 * NT;
   // Basis function of term k's cosine part (or of the whole term), and of its sine part.
@@ -517,6 +522,13 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
   } else if (tid >= 32 && tid < 32 + kMaxTerms) {
     const int k = tid - 32;
     cc.nu[k] = term_consts(hs, [&](int q) { return cc.loc[0][q]; }, k, cc.v);
+    int src = -1;
+    if (k < hs.nterms && hs.canon[k].kind == kTermDKT) {  // the chunk's histograms share (Delta, nu)
+      const CanonTerm& ct = hs.canon[k];
+      src = hs.dkt_of[(static_cast<int64_t>(cc.row[0]) * kMaxTerms + ct.dkt_term) * kMaxPrims + ct.dkt_prim];
+      if (!dbg_ok(job.dbg, src >= 0 && src < hs.ndkt, kDbgDkt)) src = -1;
+    }
+    cc.v.dkt_src[k] = src;
     if (k < hs.nterms) {  // directional derivatives of the term's shared parameters (Gauss-Newton products)
       const CanonTerm& ct = hs.canon[k];
       double dl = 0.0, ds = 0.0;
@@ -524,10 +536,12 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
       for (int i = 0; i < ct.ngauss; ++i) ds += cc.loc[0][ct.gauss_slot[i]] * cc.ldir[0][ct.gauss_slot[i]];
       cc.dlam[k] = static_cast<float>(dl);
       cc.dsig[k] = static_cast<float>(ds);
-      cc.dnu[k] = ct.kind == kTermTF ? static_cast<float>(cc.ldir[0][ct.nu_slot]) : 0.0f;
+      cc.dnu[k] = ct.kind == kTermTF || ct.kind == kTermDKT ? static_cast<float>(cc.ldir[0][ct.nu_slot]) : 0.0f;
       cc.ddel[k] = ct.kind == kTermKT
                        ? static_cast<float>((2.0 / 3.0) * cc.loc[0][ct.kt_slot] * cc.ldir[0][ct.kt_slot])
-                       : (ct.kind == kTermLKT ? static_cast<float>((2.0 / 3.0) * cc.ldir[0][ct.kt_slot]) : 0.0f);
+                       : (ct.kind == kTermLKT ? static_cast<float>((2.0 / 3.0) * cc.ldir[0][ct.kt_slot])
+                                              : (ct.kind == kTermDKT ? static_cast<float>(cc.ldir[0][ct.kt_slot])
+                                                                     : 0.0f));
     }
   } else if (tid == 64) {
     // log2(e) / tau_mu: E = 2^(-aE t); without the decay envelope E = 1
@@ -1118,6 +1132,9 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     // Time-only parts of the bin.  Every operation that reaches the cost value is an
     // explicitly rounded intrinsic: no contraction into FMAs that could differ between the
     // value-only and the value+gradient instantiations, so both return the same value.
+    // dK: the derivative factor of a Kubo-Toyabe term (static: along Delta, scaled; dynamic:
+    // d/dDelta).  d/dnu of a dynamic Kubo-Toyabe term waits in shared memory (sm.dkn) for the
+    // shared channels after the histogram loop, so that no register is held for it there.
     float E[BPT], Pc[NT][BPT], Ps[NT][BPT], dK[NT][BPT];
 #pragma unroll
     for (int j = 0; j < BPT; ++j) E[j] = ex2a(__fmul_rn(-aE, t[j]));
@@ -1130,6 +1147,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
       const bool istf = Bs::tf(vc.kinds, k);
       const bool iskt = !istf && vc.kinds[k] == kTermKT;
       const bool islkt = !istf && vc.kinds[k] == kTermLKT;
+      const bool isdkt = Bs::DKT && !istf && vc.kinds[k] == kTermDKT;
 #pragma unroll
       for (int j = 0; j < BPT; ++j) {
         float X = __fmul_rn(ba, ex2a(__fmul_rn(-fmaf(cb, t[j], ca), t[j])));  // a E X_k
@@ -1144,6 +1162,14 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
           const float u = __fmul_rn(vc.d2[k], t[j]);
           dK[k][j] = X * t[j] * g * (u - 2.0f);
           X = __fmul_rn(X, fmaf(__fmul_rn(2.0f / 3.0f, __fsub_rn(1.0f, u)), g, 1.0f / 3.0f));
+        } else if (isdkt) {  // dynamic Kubo-Toyabe: the cubic through the evaluation's table
+          const int src = vc.dkt_src[k];
+          float G = 1.0f, gD = 0.0f, gN = 0.0f;
+          if (src >= 0)
+            dkt_lookup(static_cast<const float*>(job.dkt) + static_cast<size_t>(src) * kDktTable, t[j], &G, &gD, &gN);
+          dK[k][j] = X * gD;
+          sm.dkn[k][j][tid] = X * gN;
+          X = __fmul_rn(X, G);
         }
         Pc[k][j] = X;
       }
@@ -1207,7 +1233,8 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
           const float w = kTwoPiF * t[j] * cc.dnu[k];                    // d theta_k along v
           const float dc = fmaf(Pc[k][j], g, -Ps[k][j] * w);
           const float ds = fmaf(Ps[k][j], g, Pc[k][j] * w);
-          const float dn = fmaf(Pc[k][j], g, cc.ddel[k] * dK[k][j]);   // a term without cosine
+          const float dN = Bs::DKT && !istf && vc.kinds[k] == kTermDKT ? sm.dkn[k][j][tid] : 0.0f;
+          const float dn = fmaf(Pc[k][j], g, fmaf(cc.ddel[k], dK[k][j], cc.dnu[k] * dN));  // no cosine
           if (Bs::MERGED) {
             if (istf) {
               Bd[1 % (GN ? M : 1)][j] += dc;
@@ -1409,6 +1436,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
             D = Vc * Pc[k][j];
           }
           if (!istf) sh[k][3] = fmaf(Vc, dK[k][j], sh[k][3]);  // zero unless Kubo-Toyabe
+          if (Bs::DKT && !istf && vc.kinds[k] == kTermDKT) sh[k][2] = fmaf(Vc, sm.dkn[k][j][tid], sh[k][2]);
           sh[k][0] = fmaf(mt, D, sh[k][0]);
           sh[k][1] = fmaf(mh, D, sh[k][1]);
         }
@@ -1525,6 +1553,12 @@ __device__ double split_slot(const HistSet& hs, const ChunkCache& cc, const doub
         break;
       case kCLkt:
         if (hl == 0) g += (4.0 / 3.0) * sch[k * 4 + 3];
+        break;
+      case kCDktD:
+        if (hl == 0) g += 2.0 * sch[k * 4 + 3];
+        break;
+      case kCDktN:
+        if (hl == 0) g += 2.0 * sch[k * 4 + 2];
         break;
       case kCDel:
         if (hl == 0) g += (4.0 / 3.0) * cc.loc[0][s] * sch[k * 4 + 3];

@@ -13,11 +13,11 @@
 namespace musr {
 
 // Canonical form of one term; false if the term is not
-// a * exp(-Lambda t - S t^2/2) * [KT, LKT or TFCOS] with at most one AMP.
+// a * exp(-Lambda t - S t^2/2) * [KT, LKT, DKT or TFCOS] with at most one AMP.
 inline bool canonical_term(const musr_term& t, CanonTerm* ct) {
   std::memset(ct, 0, sizeof(*ct));
-  ct->amp_slot = ct->kt_slot = ct->nu_slot = ct->phi_slot = -1;
-  int namp = 0, nkt = 0, nlkt = 0, ntf = 0;
+  ct->amp_slot = ct->kt_slot = ct->nu_slot = ct->phi_slot = ct->dkt_term = ct->dkt_prim = -1;
+  int namp = 0, nkt = 0, nlkt = 0, ntf = 0, ndkt = 0;
   for (int m = 0; m < t.nprim; ++m) {
     switch (t.kind[m]) {
       case MUSR_PRIM_AMP:
@@ -43,12 +43,18 @@ inline bool canonical_term(const musr_term& t, CanonTerm* ct) {
         ct->kt_slot = t.slot[m][0];
         ++nlkt;
         break;
-      default:  // STREXP, BESSEL: no basis form (FP64 path only)
+      case MUSR_PRIM_DKT:  // a time-only factor, read per bin from the evaluation's table
+        ct->kt_slot = t.slot[m][0];
+        ct->nu_slot = t.slot[m][1];
+        ct->dkt_prim = m;
+        ++ndkt;
+        break;
+      default:  // STREXP, BESSEL: no basis form (the SPLIT path evaluates the term list)
         return false;
     }
   }
-  if (namp > 1 || nkt + nlkt + ntf > 1) return false;
-  ct->kind = ntf ? kTermTF : (nkt ? kTermKT : (nlkt ? kTermLKT : kTermPlain));
+  if (namp > 1 || nkt + nlkt + ntf + ndkt > 1) return false;
+  ct->kind = ntf ? kTermTF : (nkt ? kTermKT : (nlkt ? kTermLKT : (ndkt ? kTermDKT : kTermPlain)));
   return true;
 }
 
@@ -112,10 +118,12 @@ inline const char* plan_split(const musr_term* terms, int nterms, const int32_t*
                               const double* consts, HistSet* hs, bool envelope = true) {
   if (nterms > kMaxTerms) return "at most 4 terms";
   CanonTerm canon[kMaxTerms];
-  for (int k = 0; k < nterms; ++k)
+  for (int k = 0; k < nterms; ++k) {
     if (!canonical_term(terms[k], &canon[k]))
-      return "SPLIT precision needs every term to hold at most one AMP, and at most one of KT, LKT or TFCOS "
-             "(STREXP and BESSEL have no basis form)";
+      return "SPLIT precision needs every term to hold at most one AMP, and at most one of KT, LKT, DKT or "
+             "TFCOS (STREXP and BESSEL have no basis form)";
+    if (canon[k].kind == kTermDKT) canon[k].dkt_term = k;
+  }
   // Cosine terms first (the model is a sum: the order of its terms is free).
   int ntf = 0, nn = 0;
   hs->nterms = nterms;
@@ -123,9 +131,11 @@ inline const char* plan_split(const musr_term* terms, int nterms, const int32_t*
     if (canon[k].kind == kTermTF) hs->canon[ntf++] = canon[k];
   for (int k = 0; k < nterms; ++k)
     if (canon[k].kind != kTermTF) hs->canon[ntf + nn++] = canon[k];
-  // Merged: every amplitude one shared constant, one phase per histogram.
+  // Merged: every amplitude one shared constant, one phase per histogram, and no dynamic
+  // Kubo-Toyabe factor (the merged kernels, the fastest, carry no code for its table).
   double amp[kMaxTerms];
   bool merged = envelope && ntf == 2 && nn <= 1 && phases_shared(hs->canon, nterms, map, consts, H, nslots);
+  for (int k = 0; k < nterms; ++k) merged = merged && hs->canon[k].kind != kTermDKT;
   for (int k = 0; k < nterms && merged; ++k)
     merged = shared_constant_amplitude(hs->canon[k], map, consts, H, nslots, &amp[k]);
   hs->merged = merged ? 1 : 0;
@@ -161,6 +171,10 @@ inline const char* plan_split(const musr_term* terms, int nterms, const int32_t*
     for (int i = 0; i < ct.ngauss; ++i) add(ct.gauss_slot[i], kCSig, k);
     if (ct.kind == kTermKT) add(ct.kt_slot, kCDel, k);
     if (ct.kind == kTermLKT) add(ct.kt_slot, kCLkt, k);
+    if (ct.kind == kTermDKT) {
+      add(ct.kt_slot, kCDktD, k);
+      add(ct.nu_slot, kCDktN, k);
+    }
     if (ct.kind == kTermTF) {
       add(ct.nu_slot, kCNu, k);
       // merged: one phase per histogram, whose slot receives the derivative once

@@ -142,6 +142,17 @@ void plan_cases() {
                                       term({{A, {6, 0}}, {K, {7, 0}}}), term({{A, {8, 0}}, {T, {9, 10}}})};
   const std::vector<int32_t> mg = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10};
   plan_case("generic4", gen, mg, 1, 11, {});
+  // A dynamic Kubo-Toyabe factor is a time-only factor like the static one: a basis term
+  // with a Delta and a nu contribution, reordered after the cosine.
+  const int D = MUSR_PRIM_DKT;
+  const std::vector<musr_term> dkt = {term({{A, {2, 0}}, {D, {3, 4}}, {E, {5, 0}}}),
+                                      term({{A, {6, 0}}, {T, {7, 8}}})};
+  const std::vector<int32_t> md = {0, 1, 2, 3, 4, 5, 6, 7, 8};
+  plan_case("dkt_then_tf", dkt, md, 1, 9, {});
+  // ... but not beside a cosine in the same term.
+  const std::vector<musr_term> dkt_tf = {term({{A, {2, 0}}, {D, {3, 4}}, {T, {5, 6}}})};
+  const std::vector<int32_t> mdt = {0, 1, 2, 3, 4, 5, 6};
+  plan_case("dkt_times_cosine", dkt_tf, mdt, 1, 7, {});
 }
 
 void pick_cases() {

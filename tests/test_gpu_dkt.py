@@ -3,7 +3,8 @@
 The device solves the renewal equation G = f + nu f * G once per evaluation and (Delta, nu)
 pair on its own grid (trapezoidal rule with Richardson extrapolation, spacing times the faster
 of Delta and nu at most 0.02) and interpolates it per bin with the cubic through the four
-nearest grid points; the oracle solves it on a five times finer grid.  Tolerance: the
+nearest grid points (at SPLIT precision as a basis function of its term where the term allows
+one, else within the per-bin term list); the oracle solves it on a five times finer grid.  Tolerance: the
 table's error eps_T -- discretisation O((h rate)^4), interpolation 0.023 h^4 |G''''|, and
 for the FP32 tables of the SPLIT path the rounding of sums of up to 2K terms -- stays below
 3e-6 of G's range (1) for these parameters (a model of the device's scheme run in numpy
@@ -53,10 +54,26 @@ def _mixed_problem(seed=41):
     return q
 
 
+def _list_problem(seed=45):
+    """The dynamic KT factor beside a cosine in one term (no basis form: the SPLIT path
+    evaluates the term list per bin)."""
+    p = mi.cfg3(nhist=2, nbins=1200, bin_width_ns=10.0, seed=seed)
+    terms = [[("AMP", (2,)), ("DKT", (3, 4)), ("TFCOS", (5, 6))]]
+    rows = [[5 + 2 * j, 6 + 2 * j, 0, 1, 2, 3, 4] for j in range(2)]
+    truth = [0.2, 0.4, 0.9, 2.0, 30.0]
+    names = ["A0", "Delta", "nu", "nu_tf", "phi"]
+    for j in range(2):
+        names += [f"N0_{j}", f"Nbkg_{j}"]
+        truth += [300.0, 2.0]
+    return Problem(p.counts, np.array([0.0, 0.0]), p.bin_width_ns, (0.05, 11.9), terms, np.array(rows, np.int32),
+                   np.zeros(0), len(truth), np.array(truth), names, "dkt_list")
+
+
 def _problems():
     return {"dkt_zf": mi.dkt_zf(nhist=2, nbins=1600, bin_width_ns=8.0, seed=20),
             "mixed": _mixed_problem(),
-            "fast": mi.dkt_zf(nhist=2, nbins=1600, bin_width_ns=8.0, seed=21, delta=0.15, nu_c=4.0)}
+            "fast": mi.dkt_zf(nhist=2, nbins=1600, bin_width_ns=8.0, seed=21, delta=0.15, nu_c=4.0),
+            "list": _list_problem()}
 
 
 PROBLEMS = None
@@ -85,7 +102,7 @@ def _check(p, x, v, g, ref, tol):
     assert not bad.any(), (np.nonzero(bad), g[bad], rg[bad], rgs[bad])
 
 
-@pytest.mark.parametrize("name", ["dkt_zf", "mixed", "fast"])
+@pytest.mark.parametrize("name", ["dkt_zf", "mixed", "fast", "list"])
 def test_dynamic_kt_matches_oracle(B, name):
     p = problems()[name]
     X = mi.jitter(p.truth, 3, seed=5, lo=0.95, hi=1.05)
@@ -138,15 +155,19 @@ def test_dynamic_kt_fits(B):
     assert np.max(np.abs(r32["x"] - r64["x"]) / sig) < 0.01, np.abs(r32["x"] - r64["x"]) / sig
 
 
-def test_dynamic_kt_gauss_newton_fp64(B):
-    p = problems()["mixed"]
+@pytest.mark.parametrize("name", ["mixed", "dkt_zf"])
+def test_dynamic_kt_gauss_newton(B, name):
+    """Gauss-Newton matrices of theories with the dynamic KT factor in their basis form: FP64
+    and SPLIT against the oracle, within the tables' accuracy (and 2^-16 for SPLIT)."""
+    p = problems()[name]
     x = p.truth * 1.01
     with B.Context(p) as ctx:
         for mode in (0, 1):
-            H = ctx.gauss_newton(x, mode, B.MUSR_FP64)
             R = oracle.gauss_newton(p, x, mode)
             scale = np.sqrt(np.outer(np.diag(R), np.diag(R)))
-            assert np.all(np.abs(H - R) <= 1e-5 * scale + 1e-300), np.max(np.abs(H - R) / scale)
+            for prec, tol in ((B.MUSR_FP64, EPS_T), (B.MUSR_SPLIT, EPS_T + SPLIT_EPS)):
+                H = ctx.gauss_newton(x, mode, prec)
+                assert np.all(np.abs(H - R) <= tol * scale + 1e-300), (prec, np.max(np.abs(H - R) / scale))
 
 
 def test_dynamic_kt_refused_where_no_tables_are_solved(B):

@@ -16,8 +16,8 @@ CSRC = os.path.join(ROOT, "paper_1509_07685_gb300", "csrc")
 
 # SPLIT shapes and term kinds as numbered in musr_dev.h
 SHAPE = {"generic": 0, "T1": 1, "N1": 2, "T1N1": 3, "T2": 4, "T2N1": 5, "T2m": 6, "T2N1m": 7}
-TERM = {"plain": 1, "tf": 2, "kt": 3, "lkt": 4}
-C_AMP, C_PHI, C_DEL, C_LKT = 2, 3, 7, 8
+TERM = {"plain": 1, "tf": 2, "kt": 3, "lkt": 4, "dkt": 5}
+C_AMP, C_PHI, C_DEL, C_LKT, C_DKT_D, C_DKT_N = 2, 3, 7, 8, 9, 10
 
 
 def _cuda_include():
@@ -73,6 +73,10 @@ def test_split_planning(run):
     assert not r["two_cosines"]["ok"]
     g = r["generic4"]
     assert g["shape"] == SHAPE["generic"] and g["kinds"] == [TERM["tf"], TERM["plain"], TERM["plain"], TERM["kt"]]
+    d = r["dkt_then_tf"]  # the cosine term moves first; the dynamic KT term keeps both its slots
+    assert d["ok"] and d["shape"] == SHAPE["T1N1"] and d["kinds"] == [TERM["tf"], TERM["dkt"]]
+    assert [3, C_DKT_D, 1] in d["contrib"] and [4, C_DKT_N, 1] in d["contrib"]
+    assert not r["dkt_times_cosine"]["ok"]
 
 
 def test_decomposition_cost_model(run):
