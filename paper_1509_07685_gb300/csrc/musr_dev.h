@@ -44,14 +44,19 @@ __host__ __device__ inline int prim_nslots(int kind) {
 // Dynamic Kubo-Toyabe relaxation (DKT): the renewal equation G = f + nu f * G of the
 // strong-collision model is solved per evaluation and per distinct (Delta, nu) pair (a
 // "source") on a grid of K + 1 points over [0, span] (trapezoidal rule, Richardson
-// extrapolation from the grid and its halving), K = ceil(span max(Delta, nu, 0.05) / kDktStep)
+// extrapolation from the grid and its halving), K = ceil(span max(Delta, nu, 0.05) / step)
 // clamped to [kDktMinK, kDktMaxK]; the bins interpolate the table with the cubic through the
 // four nearest points.  Table of one source: header {h, 1/h, K} then G, dG/dDelta, dG/dnu,
-// each kDktMaxK + 1 values, in the path's arithmetic type.
+// each kDktMaxK + 1 values, in the path's arithmetic type.  The step (grid spacing times the
+// faster of Delta and nu) is 0.02 for FP64 tables; FP32 tables cannot resolve more than a few
+// 1e-7 of G, and at 0.03 their discretisation and interpolation error stays below that
+// rounding (a model of the scheme against the oracle: at most 6e-7, against 8e-7 at 0.02 and
+// 4e-6 at 0.04), at (2/3)^2 of the work.
 constexpr int kMaxDkt = 8;        // distinct (Delta, nu) sources of one histogram set
 constexpr int kDktMaxK = 4096;
 constexpr int kDktMinK = 64;
-constexpr double kDktStep = 0.02; // grid spacing times the faster of Delta and nu
+constexpr double kDktStep = 0.02;    // FP64 tables
+constexpr double kDktStep32 = 0.03;  // FP32 tables (SPLIT)
 constexpr int kDktHeader = 4;
 constexpr int kDktTable = kDktHeader + 3 * (kDktMaxK + 1);   // values per source table
 constexpr int kDktWork = 7 * (2 * kDktMaxK + 1);              // scratch values per source (finer grid)

@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kB) dkt_table_kernel(const Job* __restrict__ j
   const double Dd = value(hs.dkt_src[src].x), nd = value(hs.dkt_src[src].y);
   const double rate = fmax(fmax(fabs(Dd), fabs(nd)), 0.05);
   const double span = hs.dkt_span > 0.0 ? hs.dkt_span : 1.0;
-  double kf = ceil(span * rate / kDktStep);
+  double kf = ceil(span * rate / (sizeof(T) == sizeof(float) ? kDktStep32 : kDktStep));
   if (!(kf >= kDktMinK)) kf = kDktMinK;  // also NaN parameters
   if (kf > kDktMaxK) kf = kDktMaxK;
   const int K = static_cast<int>(kf);

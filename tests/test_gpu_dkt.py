@@ -2,7 +2,7 @@
 
 The device solves the renewal equation G = f + nu f * G once per evaluation and (Delta, nu)
 pair on its own grid (trapezoidal rule with Richardson extrapolation, spacing times the faster
-of Delta and nu at most 0.02) and interpolates it per bin with the cubic through the four
+of Delta and nu at most 0.02 for FP64 tables and 0.03 for the FP32 tables of the SPLIT path) and interpolates it per bin with the cubic through the four
 nearest grid points (at SPLIT precision as a basis function of its term where the term allows
 one, else within the per-bin term list); the oracle solves it on a five times finer grid.  Tolerance: the
 table's error eps_T -- discretisation O((h rate)^4), interpolation 0.023 h^4 |G''''|, and
