@@ -17,12 +17,14 @@
 // Delta and nu satisfy the same equation with other right-hand sides (the recursion
 // differentiated), so three solves share one operator.
 //
-// Blocked solve: the points are taken in blocks of 256, one thread per point.  Each thread
-// sums the block's history (the terms with i before the block) -- the O(K^2) part, in
-// parallel -- and the block's own lower-triangular Toeplitz system, a I - c L with
-// L_{rs} = f_{r-s}, is solved by multiplying with its inverse, again lower-triangular
-// Toeplitz, whose first column is computed once per grid by one warp.  The arithmetic type is
-// that of the path the table serves: FP64 for the plain path, FP32 for the SPLIT path.
+// Blocked solve: the points are taken in blocks of 256, four threads per point (1024 per
+// CTA).  The block's history (the terms with i before the block) -- the O(K^2) part -- is
+// summed in parallel, each of a point's threads taking a fixed quarter of it, and the
+// block's own lower-triangular Toeplitz system, a I - c L with L_{rs} = f_{r-s}, is solved by
+// multiplying with its inverse, again lower-triangular Toeplitz, whose first column is
+// computed once per grid by one warp; the quarters' partial sums are added in a fixed order.
+// The arithmetic type is that of the path the table serves: FP64 for the plain path, FP32 for
+// the SPLIT path.
 #include <cuda_runtime.h>
 
 #include "musr_dev.h"
@@ -30,36 +32,39 @@
 namespace musr {
 namespace {
 
-constexpr int kB = 256;  // threads per CTA, points per block of the solve
+constexpr int kB = 256;       // points per block of the solve
+constexpr int kQ = 4;         // threads per point
+constexpr int kT = kB * kQ;   // threads per CTA
 
 template <class T>
 struct DktSmem {
-  T tinv[kB];  // first column of the inverse of the block's Toeplitz matrix
+  T tinv[kB];          // first column of the inverse of the block's Toeplitz matrix
   T rhs[kB];
+  T part[kQ][3][kB];   // partial sums of the quarters of a point's threads
 };
 
 __device__ __forceinline__ double dexp(double x) { return exp(x); }
 __device__ __forceinline__ float dexp(float x) { return expf(x); }
 
-template <class T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+// Quarter q of [lo, hi): the range [lo + q n / kQ, lo + (q + 1) n / kQ), n = hi - lo.
+__device__ __forceinline__ void quarter(int lo, int hi, int q, int* b, int* e) {
+  const int n = hi > lo ? hi - lo : 0;
+  *b = lo + (q * n) / kQ;
+  *e = lo + ((q + 1) * n) / kQ;
 }
 
-// sum_{i=1}^{n-1} w[n - i] x[i] with four partial sums (independent FMA chains).
+// sum_{i=b}^{e-1} w[n - i] x[i] with four partial sums (independent FMA chains).
 template <class T>
-__device__ __forceinline__ T conv_sum(const T* w, const T* x, int n) {
+__device__ __forceinline__ T conv_range(const T* w, const T* x, int n, int b, int e) {
   T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-  int i = 1;
-  for (; i + 3 < n; i += 4) {
+  int i = b;
+  for (; i + 3 < e; i += 4) {
     s0 = fma(w[n - i], x[i], s0);
     s1 = fma(w[n - i - 1], x[i + 1], s1);
     s2 = fma(w[n - i - 2], x[i + 2], s2);
     s3 = fma(w[n - i - 3], x[i + 3], s3);
   }
-  for (; i < n; ++i) s0 = fma(w[n - i], x[i], s0);
+  for (; i < e; ++i) s0 = fma(w[n - i], x[i], s0);
   return (s0 + s1) + (s2 + s3);
 }
 
@@ -67,18 +72,23 @@ __device__ __forceinline__ T conv_sum(const T* w, const T* x, int n) {
 // a X_k - c sum_{i=1}^{k-1} f_{k-i} X_i = R_k on exit (X[0] is not read).
 template <class T>
 __device__ void solve_blocks(const T* f, T* X, int K, T c, DktSmem<T>& sm) {
-  const int r = threadIdx.x;
+  const int r = threadIdx.x % kB, q = threadIdx.x / kB;
   for (int k0 = 1; k0 <= K; k0 += kB) {
     const int k = k0 + r;
-    T rhs = T(0);
-    if (k <= K) rhs = X[k] + c * conv_sum(f + (k - k0), X, k0);
-    sm.rhs[r] = rhs;
+    int b, e;
+    quarter(1, k0, q, &b, &e);  // this thread's quarter of the history i = 1 .. k0 - 1
+    sm.part[q][0][r] = k <= K ? conv_range(f, X, k, b, e) : T(0);
     __syncthreads();
-    if (k <= K) {
-      T x = T(0);
-      for (int s = 0; s <= r; ++s) x = fma(sm.tinv[r - s], sm.rhs[s], x);
-      X[k] = x;
-    }
+    if (q == 0)
+      sm.rhs[r] = k <= K ? X[k] + c * ((sm.part[0][0][r] + sm.part[1][0][r]) + (sm.part[2][0][r] + sm.part[3][0][r]))
+                         : T(0);
+    __syncthreads();
+    quarter(0, r + 1, q, &b, &e);  // this thread's quarter of s = 0 .. r
+    T x = T(0);
+    for (int s = b; s < e; ++s) x = fma(sm.tinv[r - s], sm.rhs[s], x);
+    sm.part[q][0][r] = x;
+    __syncthreads();
+    if (q == 0 && k <= K) X[k] = (sm.part[0][0][r] + sm.part[1][0][r]) + (sm.part[2][0][r] + sm.part[3][0][r]);
     __syncthreads();
   }
 }
@@ -89,7 +99,7 @@ template <class T>
 __device__ void solve_grid(T D, T nu, T h, int K, T* f, T* fD, T* fN, T* G, T* GD, T* GN, DktSmem<T>& sm) {
   const int tid = threadIdx.x;
   const T a = T(1) - nu * (T(0.5) * h), b = T(1) + nu * (T(0.5) * h), c = nu * h;
-  for (int k = tid; k <= K; k += kB) {
+  for (int k = tid; k <= K; k += kT) {
     const T t = static_cast<T>(k) * h;
     const T u = (D * t) * (D * t), gg = dexp(T(-0.5) * u), e = dexp(-nu * t);
     const T g = T(1) / T(3) + (T(2) / T(3)) * (T(1) - u) * gg;
@@ -98,42 +108,76 @@ __device__ void solve_grid(T D, T nu, T h, int K, T* f, T* fD, T* fN, T* G, T* G
     fN[k] = -t * g * e;
   }
   __syncthreads();
-  // t_0 = 1/a, t_r = (c/a) sum_{s<r} f_{r-s} t_s (warp 0; the block never reaches past K)
+  // t_0 = 1/a, t_r = (c/a) sum_{s<r} f_{r-s} t_s (warp 0; the block never reaches past K),
+  // 32 entries at a time: each lane first sums the finished entries s < r0 for its r, then the
+  // chunk's entries become final in order, each broadcast to the lanes above it.
   if (tid < 32) {
     const int nr = K + 1 < kB ? K + 1 : kB;
-    if (tid == 0) sm.tinv[0] = T(1) / a;
-    __syncwarp();
-    for (int rr = 1; rr < nr; ++rr) {
-      T acc = T(0);
-      for (int s = tid; s < rr; s += 32) acc = fma(f[rr - s], sm.tinv[s], acc);
-      acc = warp_sum(acc);
-      if (tid == 0) sm.tinv[rr] = (c / a) * acc;
+    const T ca = c / a;
+    for (int r0 = 0; r0 < nr; r0 += 32) {
+      const int rr = r0 + tid;
+      const bool live = rr < nr;
+      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+      if (live) {
+        int q = 0;
+        for (; q + 3 < r0; q += 4) {
+          s0 = fma(f[rr - q], sm.tinv[q], s0);
+          s1 = fma(f[rr - q - 1], sm.tinv[q + 1], s1);
+          s2 = fma(f[rr - q - 2], sm.tinv[q + 2], s2);
+          s3 = fma(f[rr - q - 3], sm.tinv[q + 3], s3);
+        }
+        for (; q < r0; ++q) s0 = fma(f[rr - q], sm.tinv[q], s0);
+      }
+      T acc = (s0 + s1) + (s2 + s3), tr = T(0);
+      for (int j = 0; j < 32 && r0 + j < nr; ++j) {
+        if (tid == j) tr = rr == 0 ? T(1) / a : ca * acc;
+        const T tj = __shfl_sync(0xffffffffu, tr, j);
+        if (live && tid > j) acc = fma(f[tid - j], tj, acc);
+      }
+      if (live) sm.tinv[rr] = tr;
       __syncwarp();
     }
   }
   // G: right-hand side b f_k (G_0 = 1 enters it through the trapezoid's end term)
-  for (int k = tid; k <= K; k += kB) G[k] = k == 0 ? T(1) : b * f[k];
+  for (int k = tid; k <= K; k += kT) G[k] = k == 0 ? T(1) : b * f[k];
   __syncthreads();
   solve_blocks(f, G, K, c, sm);
   // right-hand sides of the derivatives, from the whole G:
   //   Delta: b fD_k + c sum fD_{k-i} G_i
   //   nu:    (h/2)(G_k + f_k) + b fN_k + h sum f_{k-i} G_i + c sum fN_{k-i} G_i
-  for (int k = tid; k <= K; k += kB) {
-    if (k == 0) {
-      GD[0] = T(0);
-      GN[0] = T(0);
-      continue;
+  const int r = tid % kB, q = tid / kB;
+  for (int k0 = 0; k0 <= K; k0 += kB) {  // the point's four threads each sum a quarter
+    const int k = k0 + r;
+    int lo, hi;
+    quarter(1, k, q, &lo, &hi);
+    T sD = T(0), sf = T(0), sN = T(0);
+    if (k <= K) {
+      sD = conv_range(fD, G, k, lo, hi);
+      sf = conv_range(f, G, k, lo, hi);
+      sN = conv_range(fN, G, k, lo, hi);
     }
-    GD[k] = b * fD[k] + c * conv_sum(fD, G, k);
-    GN[k] = T(0.5) * h * (G[k] + f[k]) + b * fN[k] + h * conv_sum(f, G, k) + c * conv_sum(fN, G, k);
+    sm.part[q][0][r] = sD;
+    sm.part[q][1][r] = sf;
+    sm.part[q][2][r] = sN;
+    __syncthreads();
+    if (q == 0 && k <= K) {
+      auto sum4 = [&](int v) { return (sm.part[0][v][r] + sm.part[1][v][r]) + (sm.part[2][v][r] + sm.part[3][v][r]); };
+      if (k == 0) {
+        GD[0] = T(0);
+        GN[0] = T(0);
+      } else {
+        GD[k] = b * fD[k] + c * sum4(0);
+        GN[k] = T(0.5) * h * (G[k] + f[k]) + b * fN[k] + h * sum4(1) + c * sum4(2);
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
   solve_blocks(f, GD, K, c, sm);
   solve_blocks(f, GN, K, c, sm);
 }
 
 template <class T>
-__global__ void __launch_bounds__(kB) dkt_table_kernel(const Job* __restrict__ jobs, int ndkt) {
+__global__ void __launch_bounds__(kT) dkt_table_kernel(const Job* __restrict__ jobs, int ndkt) {
   __shared__ DktSmem<T> sm;
   const Job& job = jobs[blockIdx.x / ndkt];
   const int src = blockIdx.x % ndkt;
@@ -159,7 +203,7 @@ __global__ void __launch_bounds__(kB) dkt_table_kernel(const Job* __restrict__ j
   __syncthreads();
   solve_grid<T>(D, nu, static_cast<T>(h), K, f, fD, fN, G, GD, GN, sm);
   __syncthreads();
-  for (int k = threadIdx.x; k <= K; k += kB) {  // Richardson extrapolation at the coarse points
+  for (int k = threadIdx.x; k <= K; k += kT) {  // Richardson extrapolation at the coarse points
     G[k] = (T(4) * G2[2 * k] - G[k]) / T(3);
     GD[k] = (T(4) * GD2[2 * k] - GD[k]) / T(3);
     GN[k] = (T(4) * GN2[2 * k] - GN[k]) / T(3);
@@ -178,9 +222,9 @@ int launch_dkt_tables(int precision, const Job* d_jobs, int njobs, int ndkt, voi
   if (ndkt <= 0 || njobs <= 0) return 0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (precision == 0)
-    dkt_table_kernel<double><<<njobs * ndkt, kB, 0, s>>>(d_jobs, ndkt);
+    dkt_table_kernel<double><<<njobs * ndkt, kT, 0, s>>>(d_jobs, ndkt);
   else
-    dkt_table_kernel<float><<<njobs * ndkt, kB, 0, s>>>(d_jobs, ndkt);
+    dkt_table_kernel<float><<<njobs * ndkt, kT, 0, s>>>(d_jobs, ndkt);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
