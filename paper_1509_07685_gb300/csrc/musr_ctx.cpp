@@ -615,6 +615,7 @@ int ensure_eval(musr_ctx* ctx, int prec, int var, int nvec) {
     const size_t nt = static_cast<size_t>(nvec) * hs.ndkt;
     if ((rc = grow(ev.dkt, nt * musr::kDktTable * sizeof(double), false))) return rc;
     if ((rc = grow(ev.dkt_work, nt * musr::kDktWork * sizeof(double), false))) return rc;
+    if ((rc = grow(ev.dkt_count, nt * sizeof(unsigned), true))) return rc;
   }
   return MUSR_OK;
 }
@@ -645,6 +646,7 @@ void fill_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, c
       const size_t esz = prec == MUSR_SPLIT ? sizeof(float) : sizeof(double);
       j.dkt = static_cast<char*>(ev.dkt.p) + static_cast<size_t>(v) * hs.ndkt * musr::kDktTable * esz;
       j.dkt_work = static_cast<char*>(ev.dkt_work.p) + static_cast<size_t>(v) * hs.ndkt * musr::kDktWork * esz;
+      j.dkt_count = static_cast<unsigned*>(ev.dkt_count.p) + static_cast<size_t>(v) * hs.ndkt;
     }
   }
 }
@@ -820,6 +822,11 @@ void musr_ctx_destroy(musr_ctx* ctx) {
   dfree(ctx, ev.chunk_count);
   dfree(ctx, ev.counters);
   dfree(ctx, ev.jobs);
+  dfree(ctx, ev.dirs);
+  dfree(ctx, ev.dkt);
+  dfree(ctx, ev.dkt_work);
+  dfree(ctx, ev.dkt_count);
+  dfree(ctx, ctx->dbg_word);
   if (ev.h_in) cudaFreeHost(ev.h_in);
   if (ev.h_out) cudaFreeHost(ev.h_out);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);

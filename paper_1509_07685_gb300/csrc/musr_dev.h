@@ -59,7 +59,9 @@ constexpr double kDktStep = 0.02;    // FP64 tables
 constexpr double kDktStep32 = 0.03;  // FP32 tables (SPLIT)
 constexpr int kDktHeader = 4;
 constexpr int kDktTable = kDktHeader + 3 * (kDktMaxK + 1);   // values per source table
-constexpr int kDktWork = 7 * (2 * kDktMaxK + 1);              // scratch values per source (finer grid)
+// scratch values per source: the finer grid's kernel and solution (6 arrays of 2 kDktMaxK + 1),
+// the coarse grid's kernel (3 arrays of kDktMaxK + 1) and room to spare
+constexpr int kDktWork = 8 * (2 * kDktMaxK + 1);
 enum TermKind : int { kTermNone = 0, kTermPlain = 1, kTermTF = 2, kTermKT = 3, kTermLKT = 4, kTermDKT = 5 };
 
 // SPLIT shapes.  Every model the SPLIT path accepts is, for each histogram j of a
@@ -209,6 +211,7 @@ struct Job {
   const double* dir;         // [P] direction v of a Gauss-Newton product, else nullptr
   void* dkt;                 // [ndkt][kDktTable] tables of this evaluation (double: FP64 path, float: SPLIT)
   void* dkt_work;            // [ndkt][kDktWork] scratch of the table solve, same type
+  unsigned* dkt_count;       // [ndkt] completion counters of the table solve's two grids
   unsigned* dbg;             // checking build: the context's error word (bits of DebugCheck), else nullptr
 };
 

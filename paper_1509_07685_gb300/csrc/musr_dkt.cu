@@ -9,11 +9,11 @@
 // whose solution G is the relaxation (no closed form).  It is one of the "user defined
 // functions" of Section 4.1's fits, not written in the paper.
 //
-// Per evaluation and per distinct (Delta, nu) pair, one CTA solves the equation on the grid
+// Per evaluation and per distinct (Delta, nu) pair, two CTAs solve the equation on the grid
 // t_k = k h over [0, span] by the trapezoidal rule (f_0 = G_0 = 1),
 //     a G_k - c sum_{i=1}^{k-1} f_{k-i} G_i = b f_k,   a = 1 - nu h/2, b = 1 + nu h/2, c = nu h,
-// on that grid and on its halving, and keeps the Richardson extrapolation (4 G_{h/2} - G_h) / 3
-// at the coarse points (the rule's h^2 error term removed).  The derivatives with respect to
+// on that grid and on its halving (one CTA each), and keeps the Richardson extrapolation
+// (4 G_{h/2} - G_h) / 3 at the coarse points (the rule's h^2 error term removed).  The derivatives with respect to
 // Delta and nu satisfy the same equation with other right-hand sides (the recursion
 // differentiated), so three solves share one operator.
 //
@@ -176,11 +176,28 @@ __device__ void solve_grid(T D, T nu, T h, int K, T* f, T* fD, T* fN, T* G, T* G
   solve_blocks(f, GN, K, c, sm);
 }
 
+// Counter increment with acquire-release semantics at GPU scope, and the matching fence
+// (documented PTX instructions).
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// Two CTAs per (evaluation, source): part 0 solves the halved grid, part 1 the grid itself
+// (each with its own kernel arrays), and whichever finishes second forms the Richardson
+// extrapolation.  The source's counter gains 2 per solve (it starts at 0), so an odd value
+// before the increment means the other part is done.  Release: the CTA barrier orders every
+// thread's writes before thread 0's acquire-release increment; acquire: that increment and a
+// fence by every thread of the finishing CTA (no CTA waits for the other).
 template <class T>
 __global__ void __launch_bounds__(kT) dkt_table_kernel(const Job* __restrict__ jobs, int ndkt) {
   __shared__ DktSmem<T> sm;
-  const Job& job = jobs[blockIdx.x / ndkt];
-  const int src = blockIdx.x % ndkt;
+  __shared__ int second;
+  const int pair = blockIdx.x >> 1, part = blockIdx.x & 1;
+  const Job& job = jobs[pair / ndkt];
+  const int src = pair % ndkt;
   const HistSet& hs = *job.hs;
   auto value = [&](int m) { return m >= 0 ? job.params[m] : hs.consts[-1 - m]; };
   const double Dd = value(hs.dkt_src[src].x), nd = value(hs.dkt_src[src].y);
@@ -193,16 +210,23 @@ __global__ void __launch_bounds__(kT) dkt_table_kernel(const Job* __restrict__ j
   const double h = span / K;
   T* tab = static_cast<T*>(job.dkt) + static_cast<size_t>(src) * kDktTable;
   T* w = static_cast<T*>(job.dkt_work) + static_cast<size_t>(src) * kDktWork;
-  constexpr int L = 2 * kDktMaxK + 1;
-  T *f = w, *fD = w + L, *fN = w + 2 * L, *G2 = w + 3 * L, *GD2 = w + 4 * L, *GN2 = w + 5 * L;
+  constexpr int L = 2 * kDktMaxK + 1, Lc = kDktMaxK + 1;
+  T *G2 = w + 3 * L, *GD2 = w + 4 * L, *GN2 = w + 5 * L;
   T* G = tab + kDktHeader;
   T* GD = G + (kDktMaxK + 1);
   T* GN = GD + (kDktMaxK + 1);
   const T D = static_cast<T>(Dd), nu = static_cast<T>(nd);
-  solve_grid<T>(D, nu, static_cast<T>(0.5 * h), 2 * K, f, fD, fN, G2, GD2, GN2, sm);  // halved grid
+  if (part == 0) {
+    solve_grid<T>(D, nu, static_cast<T>(0.5 * h), 2 * K, w, w + L, w + 2 * L, G2, GD2, GN2, sm);  // halved grid
+  } else {
+    T* fc = w + 6 * L;
+    solve_grid<T>(D, nu, static_cast<T>(h), K, fc, fc + Lc, fc + 2 * Lc, G, GD, GN, sm);
+  }
   __syncthreads();
-  solve_grid<T>(D, nu, static_cast<T>(h), K, f, fD, fN, G, GD, GN, sm);
+  if (threadIdx.x == 0) second = (atom_add_acq_rel_u32(job.dkt_count + src, 1u) & 1u) != 0u;
   __syncthreads();
+  if (!second) return;
+  fence_acq_rel_gpu();
   for (int k = threadIdx.x; k <= K; k += kT) {  // Richardson extrapolation at the coarse points
     G[k] = (T(4) * G2[2 * k] - G[k]) / T(3);
     GD[k] = (T(4) * GD2[2 * k] - GD[k]) / T(3);
@@ -222,9 +246,9 @@ int launch_dkt_tables(int precision, const Job* d_jobs, int njobs, int ndkt, voi
   if (ndkt <= 0 || njobs <= 0) return 0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (precision == 0)
-    dkt_table_kernel<double><<<njobs * ndkt, kT, 0, s>>>(d_jobs, ndkt);
+    dkt_table_kernel<double><<<2 * njobs * ndkt, kT, 0, s>>>(d_jobs, ndkt);
   else
-    dkt_table_kernel<float><<<njobs * ndkt, kT, 0, s>>>(d_jobs, ndkt);
+    dkt_table_kernel<float><<<2 * njobs * ndkt, kT, 0, s>>>(d_jobs, ndkt);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

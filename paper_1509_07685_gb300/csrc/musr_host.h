@@ -69,6 +69,7 @@ struct Compiled {
 struct EvalBufs {
   DevBuf params, out, partials, colsum, chunk_val, chunk_count, counters, jobs, dirs;
   DevBuf dkt, dkt_work;  // dynamic Kubo-Toyabe tables and their solve's scratch, per evaluation
+  DevBuf dkt_count;      // their completion counters (zeroed once; each solve adds 2)
   double* h_in = nullptr;
   double* h_out = nullptr;
   size_t h_in_bytes = 0, h_out_bytes = 0;
