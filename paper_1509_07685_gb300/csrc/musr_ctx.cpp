@@ -632,6 +632,7 @@ void fill_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, c
     j.params = d_params + static_cast<size_t>(v) * ctx->P;
     j.out = d_out + static_cast<size_t>(v) * (1 + ctx->P);
     j.partials = static_cast<double*>(ev.partials.p) + static_cast<size_t>(v) * hs.nitems * hs.pstride;
+    j.nrows = hs.nitems;
     j.colsum = static_cast<double*>(ev.colsum.p) + static_cast<size_t>(v) * std::max(hs.ncols, 1);
     j.chunk_val = static_cast<double*>(ev.chunk_val.p) + static_cast<size_t>(v) * std::max(hs.nchunks, 1);
     j.chunk_count = static_cast<unsigned*>(ev.chunk_count.p) + static_cast<size_t>(v) * std::max(hs.nchunks, 1);
@@ -651,8 +652,94 @@ void fill_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, c
   }
 }
 
+// Launch-level partition of a batch for the SPLIT basis kernels.  A compiled decomposition
+// hands out whole items (a chunk's tile for one parameter vector), so a batch whose items do
+// not divide evenly over the persistent grid leaves CTAs idle (8 x 65536 bins at 64 vectors:
+// 256 items for 304 CTAs).  The partition instead cuts the batch's CTA iterations -- in the
+// order job, chunk, iteration -- into one contiguous, equal range per CTA; a range's share of a
+// chunk becomes pieces of at most kMaxPieceIters iterations (the phase split's limit of 2^15
+// bins), each with a partial row of its own.  A job's rows follow its pieces' order, so every
+// chunk's rows are contiguous and are summed in a fixed order.
+struct Partition {
+  int grid = 0;
+  std::vector<musr::Piece> pieces;
+  std::vector<int> cta;          // [grid + 1] first piece of each CTA
+  std::vector<int2> chunk_rows;  // [nvec][nchunks] first row, rows
+  std::vector<int> rows;         // [nvec] rows of each job
+};
+constexpr int kMaxPieceIters = musr::kMaxTileBins / (musr::kBlock * musr::kBinsPerThread);
+
+// Fills `part` and returns true when the partition's busiest CTA beats the compiled
+// decomposition `var` by 3 % or more.  Costs in CTA iterations: the iterations, a fixed cost
+// per item or piece (row reduction, completion, staging start-up: kSplitItemCost) and a cost
+// per change of chunk within a CTA (the chunk's FP64 coefficients and constants: 2.4
+// iterations of a full chunk of 8 histograms, more for fewer); both fixed costs weigh 1.5x
+// for the chi^2 kernels, whose iterations are shorter (measured on GB300).
+bool plan_partition(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, Partition* part) {
+  const Compiled& c = ctx->comp[prec][var];
+  const HistSet& hs = c.hs;
+  const int per_sm = musr::max_ctas_per_sm(prec, hs.shape, mode, grad);
+  if (per_sm < 1) return false;
+  const int G = ctx->num_sms * per_sm;
+  const int bpi = musr::bins_per_iteration(prec);
+  const int nck = static_cast<int>(c.chunks.size());
+  const double scale = mode == MUSR_MLE ? 1.0 : 1.5;
+  const double item_cost = musr::kSplitItemCost * scale;
+  std::vector<int64_t> it(nck), pre(nck + 1, 0);
+  std::vector<double> load(nck);
+  for (int k = 0; k < nck; ++k) {
+    it[k] = (static_cast<int64_t>(c.chunks[k].nhi) - c.chunks[k].tile0 + bpi - 1) / bpi;
+    pre[k + 1] = pre[k] + it[k];
+    load[k] = 2.4 * scale * musr::kGroupMax / std::max(c.chunks[k].nh, 1);
+  }
+  const int64_t S = pre[nck], I = S * nvec;
+  // Below 8 iterations per CTA a launch is latency, not work: the decomposition stays.
+  if (S <= 0 || nck == 0 || I < 8 * static_cast<int64_t>(G)) return false;
+  part->grid = G;
+  part->pieces.clear();
+  part->cta.assign(G + 1, 0);
+  part->chunk_rows.assign(static_cast<size_t>(nvec) * nck, make_int2(0, 0));
+  part->rows.assign(nvec, 0);
+  double worst = 0.0;
+  for (int b = 0; b < G; ++b) {
+    part->cta[b] = static_cast<int>(part->pieces.size());
+    const int64_t lo = I * b / G, hi = I * (b + 1) / G;
+    double cost = static_cast<double>(hi - lo);
+    int pj = -1, pk = -1;
+    for (int64_t q = lo; q < hi;) {
+      const int j = static_cast<int>(q / S);
+      const int64_t off = q - static_cast<int64_t>(j) * S;
+      const int k = static_cast<int>(std::upper_bound(pre.begin(), pre.end(), off) - pre.begin()) - 1;
+      const int64_t i0 = off - pre[k];
+      const int64_t n = std::min<int64_t>({hi - q, it[k] - i0, kMaxPieceIters});
+      int2& cr = part->chunk_rows[static_cast<size_t>(j) * nck + k];
+      if (cr.y == 0) cr.x = part->rows[j];
+      ++cr.y;
+      part->pieces.push_back({j, k, static_cast<int>(i0), static_cast<int>(n), part->rows[j]++});
+      cost += item_cost + (j != pj || k != pk ? load[k] : 0.0);
+      pj = j;
+      pk = k;
+      q += n;
+    }
+    worst = std::max(worst, cost);
+  }
+  part->cta[G] = static_cast<int>(part->pieces.size());
+  // The decomposition's busiest CTA: ceil(items / G) whole items in a row, loading a chunk
+  // for the first and again each time the row crosses into another chunk.
+  const int64_t per = (static_cast<int64_t>(nvec) * hs.nitems + G - 1) / G;
+  double max_load = 0.0;
+  int min_tiles = INT32_MAX;
+  for (int k = 0; k < nck; ++k) {
+    max_load = std::max(max_load, load[k]);
+    min_tiles = std::min(min_tiles, std::max(c.chunks[k].ntiles, 1));
+  }
+  const double switches = static_cast<double>(1 + (per - 1 + min_tiles - 1) / min_tiles);
+  const double items = static_cast<double>(per) * (hs.tile_bins / bpi + item_cost) + switches * max_load;
+  return worst < 0.97 * items;
+}
+
 int prepare_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, const double* d_params,
-                 double* d_out, const double* d_dirs) {
+                 double* d_out, const double* d_dirs, const Partition* part = nullptr) {
   EvalBufs& ev = ctx->ev;
   int rc;
   if ((rc = ensure_eval(ctx, prec, var, nvec))) return rc;
@@ -660,13 +747,48 @@ int prepare_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec,
     if ((rc = dalloc(ctx, ev.jobs, nvec * sizeof(Job)))) return rc;
     ev.key_valid = false;
   }
+  const bool pieces = part != nullptr;
   if (ev.key_valid && ev.k_prec == prec && ev.k_var == var && ev.k_mode == mode && ev.k_grad == grad &&
-      ev.k_nvec == nvec && ev.k_params == d_params && ev.k_out == d_out && ev.k_dirs == d_dirs)
+      ev.k_nvec == nvec && ev.k_params == d_params && ev.k_out == d_out && ev.k_dirs == d_dirs &&
+      ev.k_pieces == pieces)
     return MUSR_OK;
   std::vector<Job> jobs(nvec);
   fill_jobs(ctx, prec, var, mode, grad, nvec, d_params, d_out, jobs.data(), 0, d_dirs);
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+  if (pieces) {  // the partition's rows, tables and the jobs' pointers into them
+    const HistSet& hs = ctx->comp[prec][var].hs;
+    size_t total_rows = 0;
+    for (int r : part->rows) total_rows += static_cast<size_t>(r);
+    if (ev.partials.bytes < total_rows * hs.pstride * sizeof(double)) {
+      if ((rc = dalloc(ctx, ev.partials, total_rows * hs.pstride * sizeof(double)))) return rc;
+    }
+    const size_t b_rows = part->chunk_rows.size() * sizeof(int2);
+    const size_t b_cta = ((part->cta.size() * sizeof(int)) + 15) & ~size_t(15);
+    const size_t b_pcs = part->pieces.size() * sizeof(musr::Piece);
+    const size_t o_cta = (b_rows + 15) & ~size_t(15), o_pcs = o_cta + b_cta;
+    if (ev.part.bytes < o_pcs + b_pcs) {
+      if ((rc = dalloc(ctx, ev.part, o_pcs + b_pcs))) return rc;
+    }
+    std::vector<char> blob(o_pcs + b_pcs, 0);
+    std::memcpy(blob.data(), part->chunk_rows.data(), b_rows);
+    std::memcpy(blob.data() + o_cta, part->cta.data(), part->cta.size() * sizeof(int));
+    std::memcpy(blob.data() + o_pcs, part->pieces.data(), b_pcs);
+    char* base = static_cast<char*>(ev.part.p);
+    size_t row0 = 0;
+    for (int v = 0; v < nvec; ++v) {
+      Job& j = jobs[v];
+      j.partials = static_cast<double*>(ev.partials.p) + row0 * hs.pstride;
+      j.nrows = part->rows[v];
+      j.chunk_rows = reinterpret_cast<const int2*>(base) + static_cast<size_t>(v) * hs.nchunks;
+      j.piece_cta = reinterpret_cast<const int*>(base + o_cta);
+      j.pieces = reinterpret_cast<const musr::Piece*>(base + o_pcs);
+      j.npiece_ctas = part->grid;
+      row0 += static_cast<size_t>(part->rows[v]);
+    }
+    e = cudaMemcpy(ev.part.p, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy(partition)");
+  }
   e = copy_h2d(ev.jobs.p, jobs.data(), sizeof(Job) * nvec);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(jobs)");
   ev.key_valid = true;
@@ -678,6 +800,7 @@ int prepare_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec,
   ev.k_params = d_params;
   ev.k_out = d_out;
   ev.k_dirs = d_dirs;
+  ev.k_pieces = pieces;
   return MUSR_OK;
 }
 
@@ -703,7 +826,12 @@ int enqueue_eval(musr_ctx* ctx, int prec, int mode, int grad, int nvec, const do
     cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(double) * nvec * (1 + ctx->P), ctx->stream);
     return e == cudaSuccess ? MUSR_OK : cuda_fail(ctx, e, "cudaMemsetAsync");
   }
-  int rc = prepare_jobs(ctx, prec, var, mode, grad, nvec, d_params, d_out, d_dirs);
+  // Batches of plain evaluations on the SPLIT basis kernels may take a launch-level partition.
+  Partition part;
+  const bool pieces = prec == MUSR_SPLIT && nvec >= 2 && (mode == 0 || mode == 1 || mode == 4) &&
+                      hs.shape != musr::kShapeList && hs.shape != musr::kShapeListS &&
+                      plan_partition(ctx, prec, var, mode, grad, nvec, &part);
+  int rc = prepare_jobs(ctx, prec, var, mode, grad, nvec, d_params, d_out, d_dirs, pieces ? &part : nullptr);
   if (rc) return rc;
   musr::LaunchInfo info;
   if (hs.ndkt > 0 &&
@@ -713,10 +841,14 @@ int enqueue_eval(musr_ctx* ctx, int prec, int mode, int grad, int nvec, const do
     return cuda_fail(ctx, e, "dynamic Kubo-Toyabe table launch");
   }
   if (musr::launch_eval(prec, hs.shape, mode, grad, static_cast<const Job*>(ctx->ev.jobs.p), nvec,
-                        nvec * hs.nitems, ctx->num_sms, ctx->stream, &info)) {
+                        pieces ? part.grid : nvec * hs.nitems, ctx->num_sms, ctx->stream, &info)) {
     cudaError_t e = cudaGetLastError();
     ctx->ev.key_valid = false;
     return cuda_fail(ctx, e, "kernel launch");
+  }
+  if (pieces && info.grid != part.grid) {  // every CTA range of the partition must run
+    ctx->ev.key_valid = false;
+    return fail(ctx, MUSR_ECUDA, "launch grid differs from the partition's");
   }
   ctx->last_grid = info.grid;
   return MUSR_OK;
@@ -826,6 +958,7 @@ void musr_ctx_destroy(musr_ctx* ctx) {
   dfree(ctx, ev.dkt);
   dfree(ctx, ev.dkt_work);
   dfree(ctx, ev.dkt_count);
+  dfree(ctx, ev.part);
   dfree(ctx, ctx->dbg_word);
   if (ev.h_in) cudaFreeHost(ev.h_in);
   if (ev.h_out) cudaFreeHost(ev.h_out);

@@ -195,11 +195,19 @@ struct HistSet {
   const int* p_cols;
 };
 
+// A work piece of a launch-level partition (SPLIT basis kernels, batches): nit CTA iterations
+// of chunk `chunk` of job `job`, from iteration it0 of the chunk, into the job's partial row
+// `row`.  Pieces are cut from one contiguous, equal range of the batch's iterations per CTA.
+struct Piece {
+  int job, chunk, it0, nit, row;
+};
+
 struct Job {
   const HistSet* hs;
   const double* params;      // [P]
   double* out;               // [1 + P]
-  double* partials;          // [hs->nitems][hs->pstride]
+  double* partials;          // [nrows][hs->pstride]
+  int nrows;                 // partial rows of this job: hs->nitems, or its pieces' count
   double* colsum;            // [hs->ncols]
   double* chunk_val;         // [hs->nchunks]
   unsigned int* chunk_count; // [hs->nchunks], zero between launches
@@ -213,6 +221,13 @@ struct Job {
   void* dkt_work;            // [ndkt][kDktWork] scratch of the table solve, same type
   unsigned* dkt_count;       // [ndkt] completion counters of the table solve's two grids
   unsigned* dbg;             // checking build: the context's error word (bits of DebugCheck), else nullptr
+  // Launch-level partition (read from the launch's first job; nullptr: the decomposition's
+  // items): the pieces, CTA b's pieces [piece_cta[b], piece_cta[b + 1]) for b < npiece_ctas,
+  // and per chunk of this job its first partial row and row count.
+  const Piece* pieces;
+  const int* piece_cta;
+  int npiece_ctas;
+  const int2* chunk_rows;
 };
 
 // Index checks of the checking build (compiled with MUSR_DEBUG_CHECKS): a kernel that finds a
@@ -238,7 +253,7 @@ int launch_eval(int precision, int shape, int mode, int grad, const Job* d_jobs,
                 int total_items, int num_sms, void* stream, LaunchInfo* info);
 int max_ctas_per_sm(int precision, int shape, int mode, int grad);
 // The dynamic Kubo-Toyabe tables of njobs evaluations of one histogram set (precision 0:
-// FP64, 1: FP32), one CTA per (job, source); enqueued on `stream` before the evaluation.
+// FP64, 1: FP32), two CTAs per (job, source); enqueued on `stream` before the evaluation.
 int launch_dkt_tables(int precision, const Job* d_jobs, int njobs, int ndkt, void* stream);
 // Turns raw histogram rows copied to buf ([nhist][stride], dtype as uploaded) into the
 // stored image in place: INT32 -> FP32, zero padding beyond nbins; writes seq to *flag

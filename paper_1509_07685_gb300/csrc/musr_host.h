@@ -70,6 +70,7 @@ struct EvalBufs {
   DevBuf params, out, partials, colsum, chunk_val, chunk_count, counters, jobs, dirs;
   DevBuf dkt, dkt_work;  // dynamic Kubo-Toyabe tables and their solve's scratch, per evaluation
   DevBuf dkt_count;      // their completion counters (zeroed once; each solve adds 2)
+  DevBuf part;           // a launch-level partition: chunk rows, CTA offsets, pieces
   double* h_in = nullptr;
   double* h_out = nullptr;
   size_t h_in_bytes = 0, h_out_bytes = 0;
@@ -77,6 +78,7 @@ struct EvalBufs {
   int k_prec = -1, k_var = -1, k_mode = -1, k_grad = -1, k_nvec = -1;
   const double* k_params = nullptr;
   const double* k_dirs = nullptr;
+  bool k_pieces = false;
   double* k_out = nullptr;
 };
 

@@ -551,20 +551,23 @@ __device__ void load_chunk(const Job& job, const HistSet& hs, int job_index, int
   __syncthreads();
 }
 
-// Tile-level constants: the tile's first bin time and, in FP64, each precession
-// phase at that bin reduced to [-1/2, 1/2] turns.
+// Tile-level constants for a tile (or piece) starting at bin ts: its first bin time and, in
+// FP64, each precession phase at that bin reduced to [-1/2, 1/2] turns.
 template <class SM>
-__device__ void load_tile(const HistSet& hs, int tile, int prec, SM& sm) {
+__device__ void load_tile_at(int ts, const HistSet& hs, int prec, SM& sm) {
   const int tid = threadIdx.x;
-  if (tid == 0) sm.ts.tile_start = sm.cc.tile0 + tile * hs.tile_bins;
+  if (tid == 0) sm.ts.tile_start = ts;
   if (prec == 1 && tid >= 32 && tid < 32 + kMaxTerms) {
     const int k = tid - 32;
-    const int ts = sm.cc.tile0 + tile * hs.tile_bins;
     const double t_start = (static_cast<double>(ts) - sm.cc.t0) * hs.dt_us;
     if (k == 0) sm.cc.v.tbase = static_cast<float>(t_start);
     sm.cc.v.base[k] = sm.cc.v.kinds[k] == kTermTF ? tile_phase(sm.cc.nu[k], t_start) : 0.0f;
   }
   __syncthreads();
+}
+template <class SM>
+__device__ void load_tile(const HistSet& hs, int tile, int prec, SM& sm) {
+  load_tile_at(sm.cc.tile0 + tile * hs.tile_bins, hs, prec, sm);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -768,7 +771,7 @@ __device__ void fp64_item(const Job& job, const HistSet& hs, int item, Smem& sm)
         }
   }
   __syncthreads();
-  if (!dbg_ok(job.dbg, item >= 0 && item < hs.nitems, kDbgPartial)) return;
+  if (!dbg_ok(job.dbg, item >= 0 && item < job.nrows, kDbgPartial)) return;
   double* row = job.partials + static_cast<int64_t>(item) * hs.pstride;
   const int nout = GRAD ? 1 + kFp64Channels : 1;
   for (int c = tid; c < nout; c += kBlock) {
@@ -1024,7 +1027,7 @@ __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm)
         }
   }
   __syncthreads();
-  if (!dbg_ok(job.dbg, item >= 0 && item < hs.nitems, kDbgPartial)) return;
+  if (!dbg_ok(job.dbg, item >= 0 && item < job.nrows, kDbgPartial)) return;
   double* row = job.partials + static_cast<int64_t>(item) * hs.pstride;
   const int nout = GRAD ? 1 + kFp64Channels : 1;
   for (int c = tid; c < nout; c += kBlock) {
@@ -1044,7 +1047,7 @@ __device__ void list_item(const Job& job, const HistSet& hs, int item, Smem& sm)
 // ---------------------------------------------------------------------------------------------
 // vc: the job's constants on this chunk and tile.
 template <int SHAPE, int MODE, bool GRAD>
-__device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm, const VecConst& vc) {
+__device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm, const VecConst& vc, int nit = -1) {
   using Bs = Basis<SHAPE>;
   constexpr int NT = Bs::NT;
   constexpr int M = Bs::M;
@@ -1077,8 +1080,9 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
     for (int q = 0; q < 4; ++q) sh[k][q] = 0.0f;
 
   constexpr int CHUNK_BINS = kBlock * BPT;  // bins of one CTA iteration
-  // Iterations of this tile that hold any bin of the fit range (the same for every thread).
-  const int iters = min(hs.tile_bins / CHUNK_BINS, (nhi - ts + CHUNK_BINS - 1) / CHUNK_BINS);
+  // Iterations of this tile that hold any bin of the fit range (the same for every thread);
+  // a piece of a launch-level partition brings its own count.
+  const int iters = nit >= 0 ? nit : min(hs.tile_bins / CHUNK_BINS, (nhi - ts + CHUNK_BINS - 1) / CHUNK_BINS);
   // FP32 counts are staged into shared memory one iteration ahead by 16-byte cp.async copies,
   // each pair of lanes copying the 4 bins it reads of every histogram (half the histograms
   // each) and meeting at a warp barrier: no CTA-wide barrier per iteration, the warps run
@@ -1472,7 +1476,7 @@ __device__ void split_item(const Job& job, const HistSet& hs, int item, Smem& sm
   }
   __syncthreads();
   static_assert(kWarps == 8, "the FP64 trees below sum 8 warps");
-  if (!dbg_ok(job.dbg, item >= 0 && item < hs.nitems, kDbgPartial)) return;
+  if (!dbg_ok(job.dbg, item >= 0 && item < job.nrows, kDbgPartial)) return;
   double* row = job.partials + static_cast<int64_t>(item) * hs.pstride;
   if (GRAD && tid < NCH) {
     double a[kWarps];
@@ -1579,7 +1583,7 @@ __device__ void chunk_finalize(const Job& job, const HistSet& hs, SM& sm) {
   const int tid = threadIdx.x;
   const int ps = hs.pstride;
   const int nout = GRAD ? 1 + hs.nch : 1;
-  if (!dbg_ok(job.dbg, cc.item0 >= 0 && cc.item0 + cc.ntiles <= hs.nitems, kDbgPartial)) return;
+  if (!dbg_ok(job.dbg, cc.item0 >= 0 && cc.item0 + cc.ntiles <= job.nrows, kDbgPartial)) return;
   const double* part = job.partials + static_cast<int64_t>(cc.item0) * ps;
   // The chunk's item rows, summed per column in a fixed order: each column's rows are cut
   // into `tpc` contiguous segments, one thread sums a segment (its loads all in flight),
@@ -1724,6 +1728,31 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 && SHAPE != kShapeList ? 2 :
     sm.cc.chunk = -1;
   }
   __syncthreads();
+  if constexpr (PREC == 1 && !is_list(SHAPE)) {
+    if (jobs[0].pieces) {  // launch-level partition: this CTA's pieces, in order
+      if (static_cast<int>(blockIdx.x) >= jobs[0].npiece_ctas) return;
+      const int pb = jobs[0].piece_cta[blockIdx.x], pe = jobs[0].piece_cta[blockIdx.x + 1];
+      for (int p = pb; p < pe; ++p) {
+        const Piece pc = jobs[0].pieces[p];
+        if (!dbg_ok(jobs[0].dbg, pc.job >= 0 && pc.job < njobs, kDbgJob)) continue;
+        const Job job = jobs[pc.job];
+        const HistSet& hs = *job.hs;
+        if (sm.cc.job != pc.job || sm.cc.chunk != pc.chunk) {
+          __syncthreads();
+          load_chunk<SHAPE>(job, hs, pc.job, pc.chunk, PREC, sm);
+          if (threadIdx.x == 0) {  // the chunk's rows in this partition (load_tile_at's barrier publishes them)
+            const int2 r = job.chunk_rows[pc.chunk];
+            sm.cc.item0 = r.x;
+            sm.cc.ntiles = r.y;
+          }
+        }
+        load_tile_at(sm.cc.tile0 + pc.it0 * (kBlock * kBinsPerThread), hs, PREC, sm);
+        split_item<SHAPE, MODE, GRAD>(job, hs, pc.row, sm, sm.cc.v, pc.nit);
+        complete_item<PREC, SHAPE, GRAD>(job, hs, sm);
+      }
+      return;
+    }
+  }
   int ji = -1;
   Job job;
   for (int gi = beg; gi < end; ++gi) {

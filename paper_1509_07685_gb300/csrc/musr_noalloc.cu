@@ -341,6 +341,7 @@ extern "C" int musr_eval_noalloc(const void* d_counts, int dtype, int nhist, int
   job.params = d_params;
   job.out = d_out;
   job.partials = d_part;
+  job.nrows = nitems;
   job.colsum = d_cols;
   job.chunk_val = d_cval;
   job.chunk_count = d_zero;

@@ -185,3 +185,28 @@ def test_dynamic_kt_refused_where_no_tables_are_solved(B):
                              p.fit_range_us, p.terms, p.map, p.nparams, p.consts, d_x.data_ptr(), 0,
                              B.MUSR_FP64, True, d_out.data_ptr(), None)
     assert st == B.MUSR_EINVAL and "Kubo-Toyabe" in B.musr_last_error(None)
+
+
+def test_context_releases_its_evaluation_buffers(B):
+    """A context gives back every device buffer it allocated, the per-evaluation tables of the
+    dynamic KT factor, their solve's scratch and counters and the Gauss-Newton directions
+    included: contexts made, used and destroyed in turn leave the device's free memory where
+    it was."""
+    import torch
+    p = problems()["mixed"]
+    X = mi.jitter(p.truth, 32, seed=7, lo=0.98, hi=1.02)
+
+    def cycle():
+        with B.Context(p) as ctx:
+            for prec in (B.MUSR_FP64, B.MUSR_SPLIT):
+                ctx.eval_batch(X, 1, prec)
+                ctx.gauss_newton(X[0], 1, prec)
+        torch.cuda.synchronize()
+
+    cycle()  # first use: the library's own one-time allocations
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        cycle()
+    free1 = torch.cuda.mem_get_info()[0]
+    # 32 vectors of FP64 table scratch alone are ~17 MB per cycle: nothing of that may stay
+    assert free0 - free1 < 4 << 20, (free0, free1)
