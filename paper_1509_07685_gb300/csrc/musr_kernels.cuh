@@ -1791,12 +1791,26 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 && SHAPE != kShapeList ? 2 :
   }
 }
 
+// Resident CTAs per SM of one instantiation (the occupancy query, made once: a driver call
+// per launch would add its latency to every single evaluation).
+template <int PREC, int SHAPE, int MODE, bool GRAD>
+int resident_ctas() {
+  static const int per_sm = [] {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, eval_kernel<PREC, SHAPE, MODE, GRAD>, kBlock, 0) !=
+        cudaSuccess)
+      return -1;
+    return n;
+  }();
+  return per_sm;
+}
+
 template <int PREC, int SHAPE, int MODE, bool GRAD>
 int launch_one(const Job* d_jobs, int njobs, int total_items, int num_sms, cudaStream_t stream,
                LaunchInfo* info) {
   auto kern = eval_kernel<PREC, SHAPE, MODE, GRAD>;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0) != cudaSuccess) return -1;
+  int per_sm = resident_ctas<PREC, SHAPE, MODE, GRAD>();
+  if (per_sm < 0) return -1;
   if (per_sm < 1) per_sm = 1;
   int grid = num_sms * per_sm;
   if (grid > total_items) grid = total_items;
@@ -1811,9 +1825,8 @@ int launch_one(const Job* d_jobs, int njobs, int total_items, int num_sms, cudaS
 
 template <int PREC, int SHAPE, int MODE, bool GRAD>
 int occupancy_one() {
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval_kernel<PREC, SHAPE, MODE, GRAD>, kBlock, 0);
-  return per_sm;
+  const int per_sm = resident_ctas<PREC, SHAPE, MODE, GRAD>();
+  return per_sm < 0 ? 0 : per_sm;
 }
 
 template <int PREC, int SHAPE>
