@@ -817,41 +817,70 @@ int check_ready(musr_ctx* ctx, int mode, int prec) {
 }
 
 // Enqueues one launch of nvec evaluations reading d_params, writing d_out.
-int enqueue_eval(musr_ctx* ctx, int prec, int mode, int grad, int nvec, const double* d_params,
-                 double* d_out, const double* d_dirs = nullptr) {
+// One evaluation launch in two steps: the host's planning (decomposition, partition, job
+// table; it may synchronise the stream and copy) and the issue of its asynchronous work alone
+// (the dynamic Kubo-Toyabe tables, the evaluation kernel).
+struct LaunchPlan {
+  int prec = 0, mode = 0, grad = 0, nvec = 0, var = 0;
+  bool empty = false, pieces = false;
+  int grid = 0;
+  double* d_out = nullptr;
+};
+
+int plan_launch(musr_ctx* ctx, int prec, int mode, int grad, int nvec, const double* d_params, double* d_out,
+                const double* d_dirs, LaunchPlan* L) {
   if (ctx->asym && prec == MUSR_SPLIT && mode == MUSR_CHI2) mode = 4;  // SPLIT kernels: weighted chi^2
-  const int var = pick_variant(ctx, prec, nvec);
-  const HistSet& hs = ctx->comp[prec][var].hs;
-  if (hs.nitems == 0) {  // no bin in the fit range: cost 0, gradient 0
-    cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(double) * nvec * (1 + ctx->P), ctx->stream);
-    return e == cudaSuccess ? MUSR_OK : cuda_fail(ctx, e, "cudaMemsetAsync");
-  }
+  L->prec = prec;
+  L->mode = mode;
+  L->grad = grad;
+  L->nvec = nvec;
+  L->d_out = d_out;
+  L->var = pick_variant(ctx, prec, nvec);
+  const HistSet& hs = ctx->comp[prec][L->var].hs;
+  L->empty = hs.nitems == 0;  // no bin in the fit range: cost 0, gradient 0
+  if (L->empty) return MUSR_OK;
+  musr::max_ctas_per_sm(prec, hs.shape, mode, grad);  // the occupancy query, before any capture
   // Batches of plain evaluations on the SPLIT basis kernels may take a launch-level partition.
   Partition part;
-  const bool pieces = prec == MUSR_SPLIT && nvec >= 2 && (mode == 0 || mode == 1 || mode == 4) &&
-                      hs.shape != musr::kShapeList && hs.shape != musr::kShapeListS &&
-                      plan_partition(ctx, prec, var, mode, grad, nvec, &part);
-  int rc = prepare_jobs(ctx, prec, var, mode, grad, nvec, d_params, d_out, d_dirs, pieces ? &part : nullptr);
-  if (rc) return rc;
+  L->pieces = prec == MUSR_SPLIT && nvec >= 2 && (mode == 0 || mode == 1 || mode == 4) &&
+              hs.shape != musr::kShapeList && hs.shape != musr::kShapeListS &&
+              plan_partition(ctx, prec, L->var, mode, grad, nvec, &part);
+  L->grid = L->pieces ? part.grid : 0;
+  return prepare_jobs(ctx, prec, L->var, mode, grad, nvec, d_params, d_out, d_dirs, L->pieces ? &part : nullptr);
+}
+
+int issue_launch(musr_ctx* ctx, const LaunchPlan& L) {
+  const HistSet& hs = ctx->comp[L.prec][L.var].hs;
+  if (L.empty) {
+    cudaError_t e = cudaMemsetAsync(L.d_out, 0, sizeof(double) * L.nvec * (1 + ctx->P), ctx->stream);
+    return e == cudaSuccess ? MUSR_OK : cuda_fail(ctx, e, "cudaMemsetAsync");
+  }
   musr::LaunchInfo info;
   if (hs.ndkt > 0 &&
-      musr::launch_dkt_tables(prec, static_cast<const Job*>(ctx->ev.jobs.p), nvec, hs.ndkt, ctx->stream)) {
+      musr::launch_dkt_tables(L.prec, static_cast<const Job*>(ctx->ev.jobs.p), L.nvec, hs.ndkt, ctx->stream)) {
     cudaError_t e = cudaGetLastError();
     ctx->ev.key_valid = false;
     return cuda_fail(ctx, e, "dynamic Kubo-Toyabe table launch");
   }
-  if (musr::launch_eval(prec, hs.shape, mode, grad, static_cast<const Job*>(ctx->ev.jobs.p), nvec,
-                        pieces ? part.grid : nvec * hs.nitems, ctx->num_sms, ctx->stream, &info)) {
+  if (musr::launch_eval(L.prec, hs.shape, L.mode, L.grad, static_cast<const Job*>(ctx->ev.jobs.p), L.nvec,
+                        L.pieces ? L.grid : L.nvec * hs.nitems, ctx->num_sms, ctx->stream, &info)) {
     cudaError_t e = cudaGetLastError();
     ctx->ev.key_valid = false;
     return cuda_fail(ctx, e, "kernel launch");
   }
-  if (pieces && info.grid != part.grid) {  // every CTA range of the partition must run
+  if (L.pieces && info.grid != L.grid) {  // every CTA range of the partition must run
     ctx->ev.key_valid = false;
     return fail(ctx, MUSR_ECUDA, "launch grid differs from the partition's");
   }
   ctx->last_grid = info.grid;
   return MUSR_OK;
+}
+
+int enqueue_eval(musr_ctx* ctx, int prec, int mode, int grad, int nvec, const double* d_params,
+                 double* d_out, const double* d_dirs = nullptr) {
+  LaunchPlan L;
+  int rc = plan_launch(ctx, prec, mode, grad, nvec, d_params, d_out, d_dirs, &L);
+  return rc ? rc : issue_launch(ctx, L);
 }
 
 int wait_stream(musr_ctx* ctx, int timeout_ms) {
@@ -1313,11 +1342,13 @@ int musr_eval_batch(musr_ctx* ctx, const double* params, int nvec, int nparams, 
   }
   const int grad = out_grads != nullptr;
   std::memcpy(ev.h_in, params, np * sizeof(double));
+  LaunchPlan L;
+  if ((rc = plan_launch(ctx, precision, mode, grad, nvec, static_cast<const double*>(ev.params.p),
+                        static_cast<double*>(ev.out.p), nullptr, &L)))
+    return rc;
   cudaError_t e = cudaMemcpyAsync(ev.params.p, ev.h_in, np * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(params)");
-  if ((rc = enqueue_eval(ctx, precision, mode, grad, nvec, static_cast<const double*>(ev.params.p),
-                         static_cast<double*>(ev.out.p))))
-    return rc;
+  if ((rc = issue_launch(ctx, L))) return rc;
   e = cudaMemcpyAsync(ev.h_out, ev.out.p, no * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync(out)");
   e = cudaStreamSynchronize(ctx->stream);

@@ -249,7 +249,7 @@ int launch_dkt_tables(int precision, const Job* d_jobs, int njobs, int ndkt, voi
     dkt_table_kernel<double><<<2 * njobs * ndkt, kT, 0, s>>>(d_jobs, ndkt);
   else
     dkt_table_kernel<float><<<2 * njobs * ndkt, kT, 0, s>>>(d_jobs, ndkt);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;  // the caller reads and clears the error
 }
 
 }  // namespace musr

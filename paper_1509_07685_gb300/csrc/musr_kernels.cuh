@@ -1820,7 +1820,7 @@ int launch_one(const Job* d_jobs, int njobs, int total_items, int num_sms, cudaS
     info->grid = grid;
     info->block = kBlock;
   }
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;  // the caller reads and clears the error
 }
 
 template <int PREC, int SHAPE, int MODE, bool GRAD>

@@ -107,6 +107,35 @@ def test_batch_equals_single_and_is_deterministic(B):
             assert np.array_equal(vals, vals2) and np.array_equal(grads, grads2)
 
 
+def test_repeated_evaluations_follow_every_change(B):
+    """musr_eval_batch replays a recorded launch while nothing it refers to changes: new
+    parameter values, another batch size, new histograms and a new map must each reach the
+    kernels (every result against the oracle)."""
+    p = mi.cfg3(nhist=3, nbins=3001, bin_width_ns=4.0, seed=91)
+    q = mi.cfg3(nhist=3, nbins=3001, bin_width_ns=4.0, seed=92)
+    X = mi.jitter(p.truth, 3, seed=9, lo=0.95, hi=1.05)
+    with B.Context(p) as ctx:
+        for prec, check in ((B.MUSR_SPLIT, _check_split), (B.MUSR_FP64, _check_fp64)):
+            for k in range(3):  # the same launch with new parameter values
+                v, g, _ = ctx.eval(X[k], 1, prec)
+                check(v, g, oracle.cost(p, X[k], 1))
+            for n in (2, 1, 3):  # other batch sizes, then back
+                vals, grads, _ = ctx.eval_batch(X[:n], 1, prec)
+                for k in range(n):
+                    check(vals[k], grads[k], oracle.cost(p, X[k], 1))
+        ctx.configure(q)  # new histograms (same theory and map)
+        for prec, check in ((B.MUSR_SPLIT, _check_split), (B.MUSR_FP64, _check_fp64)):
+            v, g, _ = ctx.eval(X[0], 1, prec)
+            check(v, g, oracle.cost(q, X[0], 1))
+        r = np.array(q.map)
+        r[:, 1] = r[0, 1]  # one shared background: a new map
+        q2 = dataclasses.replace(q, map=r)
+        B.musr_set_map(ctx.ctx, q2.map, q2.nparams, q2.consts)
+        for prec, check in ((B.MUSR_SPLIT, _check_split), (B.MUSR_FP64, _check_fp64)):
+            v, g, _ = ctx.eval(X[0], 1, prec)
+            check(v, g, oracle.cost(q2, X[0], 1))
+
+
 def test_device_resident_eval(B):
     import torch
     p = problems()["cfg3"]
