@@ -470,6 +470,26 @@ def test_large_fit_in_the_benchmark_launch_configuration(B):
         _check_split(vs[i], gs[i], oracle.cost(p, X[i], 1))
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_launch_level_partition_matches_oracle(B, mode):
+    """Batches whose work items do not divide evenly over the grid take the launch-level
+    partition (pieces of CTA ranges crossing vectors and chunks): the paper benchmark's
+    16 x 81920 bins at 64 and 8 parameter vectors, sampled vectors against the oracle, every
+    vector against the plain FP64 path, and bit-identical on repetition."""
+    p = mi.paper_tf16()
+    X = mi.jitter(p.truth, 64, seed=12, lo=0.97, hi=1.03)
+    with B.Context(p) as ctx:
+        for n in (64, 8):
+            vals, grads, st = ctx.eval_batch(X[:n], mode, B.MUSR_SPLIT)
+            assert st == 0
+            v64, g64, _ = ctx.eval_batch(X[:n], mode, B.MUSR_FP64)
+            for i in (0, n // 2, n - 1):
+                _check_split(vals[i], grads[i], oracle.cost(p, X[i], mode))
+            assert np.all(np.abs(vals - v64) <= SPLIT_EPS * np.abs(v64))
+            vals2, grads2, _ = ctx.eval_batch(X[:n], mode, B.MUSR_SPLIT)
+            assert np.array_equal(vals, vals2) and np.array_equal(grads, grads2)
+
+
 def test_hbm_budget_is_enforced(B):
     p = mi.cfg2(nhist=8, nbins=65536, seed=2)
     ctx = B.musr_ctx_create(0, hbm_budget_bytes=1 << 20)
