@@ -1,14 +1,15 @@
 """The checking build of the library (compiled with MUSR_DEBUG_CHECKS).
 
 compute-sanitizer is not available to this suite, so the kernels carry their own index
-checks in a separate build: every computed index of a count, weight, histogram, chunk,
-work item, partial row, map entry, dynamic Kubo-Toyabe table, finalize column and job is
-tested against its bound on the device, and a failed check ORs its bit into the context's
-error word and skips the access (nothing traps).  Here the checking build runs every kind of
-launch -- one-job and vector-group SPLIT schedules, the FP64 path, term lists, dynamic
-Kubo-Toyabe tables, asymmetry data, Gauss-Newton products, ragged tails -- in a process of its
-own, and every launch must leave the word at 0 and still match the oracle.  The release
-build reports that it carries no checks.
+checks in a separate build: every computed index of a count, weight, histogram, chunk, work
+item, partial row, map entry, dynamic Kubo-Toyabe table, finalize column, job and partition
+piece is tested against its bound on the device, and a failed check ORs its bit into the
+context's error word and skips the access (nothing traps).  Here the checking build runs
+every kind of launch -- the SPLIT basis kernels of each shape group, the FP64 path, term
+lists, dynamic Kubo-Toyabe tables, asymmetry data, Gauss-Newton products, ragged tails, a
+batch on the launch-level partition -- in a process of its own, and every launch must leave
+the word at 0 and still match the oracle.  The release build reports that it carries no
+checks.
 """
 import json
 import os
@@ -40,6 +41,7 @@ cases = [
     ("dynamic KT FP64", mi.dkt_zf(nhist=2, nbins=1201, bin_width_ns=10.0, seed=75), FP64, 1, 2),
     ("dynamic KT SPLIT", mi.dkt_zf(nhist=2, nbins=1201, bin_width_ns=10.0, seed=75), SPLIT, 1, 9),
     ("asymmetry SPLIT", mi.asym_tf(npairs=2, nbins=4001, bin_width_ns=3.0, seed=76), SPLIT, 0, 9),
+    ("launch-level partition SPLIT", mi.paper_tf16(seed=77), SPLIT, 1, 64),
 ]
 out = {}
 for name, p, prec, mode, nvec in cases:
