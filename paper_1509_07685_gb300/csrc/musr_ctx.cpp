@@ -20,6 +20,7 @@
 #include "musr.h"
 #include "musr_dev.h"
 #include "musr_host.h"
+#include "musr_partition.h"
 #include "musr_plan.h"
 
 using musr::Chunk;
@@ -652,29 +653,17 @@ void fill_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, c
   }
 }
 
-// Launch-level partition of a batch for the SPLIT basis kernels.  A compiled decomposition
-// hands out whole items (a chunk's tile for one parameter vector), so a batch whose items do
-// not divide evenly over the persistent grid leaves CTAs idle (8 x 65536 bins at 64 vectors:
-// 256 items for 304 CTAs).  The partition instead cuts the batch's CTA iterations -- in the
-// order job, chunk, iteration -- into one contiguous, equal range per CTA; a range's share of a
-// chunk becomes pieces of at most kMaxPieceIters iterations (the phase split's limit of 2^15
-// bins), each with a partial row of its own.  A job's rows follow its pieces' order, so every
-// chunk's rows are contiguous and are summed in a fixed order.
-struct Partition {
-  int grid = 0;
-  std::vector<musr::Piece> pieces;
-  std::vector<int> cta;          // [grid + 1] first piece of each CTA
-  std::vector<int2> chunk_rows;  // [nvec][nchunks] first row, rows
-  std::vector<int> rows;         // [nvec] rows of each job
-};
+using musr::Partition;
 constexpr int kMaxPieceIters = musr::kMaxTileBins / (musr::kBlock * musr::kBinsPerThread);
 
-// Fills `part` and returns true when the partition's busiest CTA beats the compiled
-// decomposition `var` by 3 % or more.  Costs in CTA iterations: the iterations, a fixed cost
-// per item or piece (row reduction, completion, staging start-up: kSplitItemCost) and a cost
-// per change of chunk within a CTA (the chunk's FP64 coefficients and constants: 2.4
-// iterations of a full chunk of 8 histograms, more for fewer); both fixed costs weigh 1.5x
-// for the chi^2 kernels, whose iterations are shorter (measured on GB300).
+// Fills `part` (the launch-level partition of musr_partition.h) and returns true when its
+// busiest CTA beats the compiled decomposition `var` by 3 % or more.  Costs in CTA
+// iterations: the iterations, a fixed cost per item or piece (row reduction, completion,
+// staging start-up: kSplitItemCost) and a cost per change of chunk within a CTA (the chunk's
+// FP64 coefficients and constants: 2.4 iterations of a full chunk of 8 histograms, more for
+// fewer); both fixed costs weigh 1.5x for the chi^2 kernels, whose iterations are shorter
+// (measured on GB300).  Below 8 iterations per CTA a launch is latency, not work: the
+// decomposition stays.
 bool plan_partition(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, Partition* part) {
   const Compiled& c = ctx->comp[prec][var];
   const HistSet& hs = c.hs;
@@ -683,59 +672,24 @@ bool plan_partition(musr_ctx* ctx, int prec, int var, int mode, int grad, int nv
   const int G = ctx->num_sms * per_sm;
   const int bpi = musr::bins_per_iteration(prec);
   const int nck = static_cast<int>(c.chunks.size());
+  if (nck == 0) return false;
   const double scale = mode == MUSR_MLE ? 1.0 : 1.5;
   const double item_cost = musr::kSplitItemCost * scale;
-  std::vector<int64_t> it(nck), pre(nck + 1, 0);
+  std::vector<int64_t> it(nck);
   std::vector<double> load(nck);
-  for (int k = 0; k < nck; ++k) {
-    it[k] = (static_cast<int64_t>(c.chunks[k].nhi) - c.chunks[k].tile0 + bpi - 1) / bpi;
-    pre[k + 1] = pre[k] + it[k];
-    load[k] = 2.4 * scale * musr::kGroupMax / std::max(c.chunks[k].nh, 1);
-  }
-  const int64_t S = pre[nck], I = S * nvec;
-  // Below 8 iterations per CTA a launch is latency, not work: the decomposition stays.
-  if (S <= 0 || nck == 0 || I < 8 * static_cast<int64_t>(G)) return false;
-  part->grid = G;
-  part->pieces.clear();
-  part->cta.assign(G + 1, 0);
-  part->chunk_rows.assign(static_cast<size_t>(nvec) * nck, make_int2(0, 0));
-  part->rows.assign(nvec, 0);
-  double worst = 0.0;
-  for (int b = 0; b < G; ++b) {
-    part->cta[b] = static_cast<int>(part->pieces.size());
-    const int64_t lo = I * b / G, hi = I * (b + 1) / G;
-    double cost = static_cast<double>(hi - lo);
-    int pj = -1, pk = -1;
-    for (int64_t q = lo; q < hi;) {
-      const int j = static_cast<int>(q / S);
-      const int64_t off = q - static_cast<int64_t>(j) * S;
-      const int k = static_cast<int>(std::upper_bound(pre.begin(), pre.end(), off) - pre.begin()) - 1;
-      const int64_t i0 = off - pre[k];
-      const int64_t n = std::min<int64_t>({hi - q, it[k] - i0, kMaxPieceIters});
-      int2& cr = part->chunk_rows[static_cast<size_t>(j) * nck + k];
-      if (cr.y == 0) cr.x = part->rows[j];
-      ++cr.y;
-      part->pieces.push_back({j, k, static_cast<int>(i0), static_cast<int>(n), part->rows[j]++});
-      cost += item_cost + (j != pj || k != pk ? load[k] : 0.0);
-      pj = j;
-      pk = k;
-      q += n;
-    }
-    worst = std::max(worst, cost);
-  }
-  part->cta[G] = static_cast<int>(part->pieces.size());
-  // The decomposition's busiest CTA: ceil(items / G) whole items in a row, loading a chunk
-  // for the first and again each time the row crosses into another chunk.
-  const int64_t per = (static_cast<int64_t>(nvec) * hs.nitems + G - 1) / G;
+  int64_t S = 0;
   double max_load = 0.0;
   int min_tiles = INT32_MAX;
   for (int k = 0; k < nck; ++k) {
+    it[k] = (static_cast<int64_t>(c.chunks[k].nhi) - c.chunks[k].tile0 + bpi - 1) / bpi;
+    S += it[k];
+    load[k] = 2.4 * scale * musr::kGroupMax / std::max(c.chunks[k].nh, 1);
     max_load = std::max(max_load, load[k]);
-    min_tiles = std::min(min_tiles, std::max(c.chunks[k].ntiles, 1));
+    min_tiles = std::min(min_tiles, c.chunks[k].ntiles);
   }
-  const double switches = static_cast<double>(1 + (per - 1 + min_tiles - 1) / min_tiles);
-  const double items = static_cast<double>(per) * (hs.tile_bins / bpi + item_cost) + switches * max_load;
-  return worst < 0.97 * items;
+  if (S <= 0 || S * nvec < 8 * static_cast<int64_t>(G)) return false;
+  const double worst = musr::cut_partition(it, load, nvec, G, kMaxPieceIters, item_cost, part);
+  return worst < 0.97 * musr::items_cost(hs.nitems, nvec, G, hs.tile_bins / bpi, min_tiles, item_cost, max_load);
 }
 
 int prepare_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, const double* d_params,

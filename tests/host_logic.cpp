@@ -13,6 +13,7 @@
 #include "musr.h"
 #include "musr_bfgs.h"
 #include "musr_dev.h"
+#include "musr_partition.h"
 #include "musr_plan.h"
 
 using musr::Bfgs;
@@ -169,6 +170,32 @@ void pick_cases() {
   }
 }
 
+void partition_case(const char* name, const std::vector<int64_t>& iters, const std::vector<double>& load, int nvec,
+                    int G, int max_piece, double item_cost) {
+  musr::Partition part;
+  const double worst = musr::cut_partition(iters, load, nvec, G, max_piece, item_cost, &part);
+  std::printf("{\"name\": \"%s\", \"worst\": %.17g, \"grid\": %d, \"pieces\": [", name, worst, part.grid);
+  for (size_t i = 0; i < part.pieces.size(); ++i) {
+    const musr::Piece& p = part.pieces[i];
+    std::printf("%s[%d, %d, %d, %d, %d]", i ? ", " : "", p.job, p.chunk, p.it0, p.nit, p.row);
+  }
+  std::printf("], \"cta\": [");
+  for (size_t i = 0; i < part.cta.size(); ++i) std::printf("%s%d", i ? ", " : "", part.cta[i]);
+  std::printf("], \"chunk_rows\": [");
+  for (size_t i = 0; i < part.chunk_rows.size(); ++i)
+    std::printf("%s[%d, %d]", i ? ", " : "", part.chunk_rows[i].x, part.chunk_rows[i].y);
+  std::printf("], \"rows\": [");
+  for (size_t i = 0; i < part.rows.size(); ++i) std::printf("%s%d", i ? ", " : "", part.rows[i]);
+  std::printf("], \"items_cost\": %.17g}\n", musr::items_cost(10, nvec, G, 8, 5, item_cost, 2.4));
+}
+
+void partition_cases() {
+  partition_case("paper_64", {160, 160}, {2.4, 2.4}, 64, 304, 64, 1.3);
+  partition_case("cfg2_64", {128}, {2.4}, 64, 304, 64, 1.3);
+  partition_case("uneven", {7, 100, 33}, {1.0, 2.0, 3.0}, 5, 13, 16, 1.3);
+  partition_case("long", {2048, 2048, 2048}, {2.4, 2.4, 2.4}, 3, 7, 64, 1.3);
+}
+
 }  // namespace
 
 int main(int argc, char** argv) {
@@ -176,5 +203,6 @@ int main(int argc, char** argv) {
   if (what == "bfgs") bfgs_cases();
   if (what == "plan") plan_cases();
   if (what == "pick") pick_cases();
+  if (what == "partition") partition_cases();
   return 0;
 }

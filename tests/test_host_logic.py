@@ -29,7 +29,7 @@ def _cuda_include():
 
 @pytest.fixture(scope="module")
 def run():
-    deps = [SRC] + [os.path.join(CSRC, f) for f in ("musr_bfgs.h", "musr_plan.h", "musr_dev.h")] + \
+    deps = [SRC] + [os.path.join(CSRC, f) for f in ("musr_bfgs.h", "musr_plan.h", "musr_dev.h", "musr_partition.h")] + \
         [os.path.join(ROOT, "include", "musr.h")]
     if not os.path.exists(EXE) or os.path.getmtime(EXE) < max(os.path.getmtime(d) for d in deps):
         os.makedirs(os.path.dirname(EXE), exist_ok=True)
@@ -85,3 +85,56 @@ def test_decomposition_cost_model(run):
         costs = d["costs"]
         assert d["v"] == int(np.argmin(costs))  # the first (smallest-tile) minimum
     assert r[1]["v"] == 0 and r[8]["v"] == 2 and r[64]["v"] == 5 and r[152]["v"] == 6
+
+
+PARTITION_CASES = {  # name: chunk iterations, chunk loads, vectors, CTAs, largest piece (host_logic.cpp)
+    "paper_64": ([160, 160], [2.4, 2.4], 64, 304, 64),
+    "cfg2_64": ([128], [2.4], 64, 304, 64),
+    "uneven": ([7, 100, 33], [1.0, 2.0, 3.0], 5, 13, 16),
+    "long": ([2048, 2048, 2048], [2.4, 2.4, 2.4], 3, 7, 64),
+}
+
+
+def test_partition_invariants(run):
+    """The launch-level partition: each job's chunk iterations are covered exactly once, in
+    order, by pieces of at most the largest piece; every CTA takes the next contiguous range of
+    floor(I*b/G) iterations; a job's rows follow its pieces and each chunk's rows are contiguous;
+    the returned cost is the busiest CTA's (iterations, 1.3 per piece, a chunk load per change)."""
+    r = run("partition")
+    for name, (iters, load, nvec, G, max_piece) in PARTITION_CASES.items():
+        p = r[name]
+        pieces, cta, nck = p["pieces"], p["cta"], len(iters)
+        pre = np.concatenate([[0], np.cumsum(iters)])
+        S = int(pre[-1])
+        I = S * nvec
+        assert p["grid"] == G and len(cta) == G + 1 and cta[0] == 0 and cta[-1] == len(pieces)
+        assert all(a <= b for a, b in zip(cta, cta[1:]))
+        q = 0
+        worst = 0.0
+        for b in range(G):
+            lo, hi = I * b // G, I * (b + 1) // G
+            assert q == lo
+            cost, prev = float(hi - lo), None
+            for j, k, it0, nit, row in pieces[cta[b]:cta[b + 1]]:
+                assert 1 <= nit <= max_piece and 0 <= it0 and it0 + nit <= iters[k]
+                assert j * S + pre[k] + it0 == q  # the next iteration of the global order
+                q += nit
+                cost += 1.3 + (load[k] if prev != (j, k) else 0.0)
+                prev = (j, k)
+            assert q == hi
+            worst = max(worst, cost)
+        assert q == I
+        assert p["worst"] == pytest.approx(worst, rel=1e-12)
+        rows = p["rows"]
+        cr = np.array(p["chunk_rows"]).reshape(nvec, nck, 2)
+        for j in range(nvec):
+            own = [pc for pc in pieces if pc[0] == j]
+            assert rows[j] == len(own) and sorted(pc[4] for pc in own) == list(range(rows[j]))
+            for k in range(nck):
+                ck = [pc for pc in own if pc[1] == k]
+                first, count = cr[j, k]
+                assert count == len(ck) and [pc[4] for pc in ck] == list(range(first, first + count))
+                assert sum(pc[3] for pc in ck) == iters[k]
+    # the compiled decomposition's busiest CTA: ceil(640 / 304) = 3 items of 8 iterations, a
+    # piece cost each and a chunk load at the start and after 5 items
+    assert r["paper_64"]["items_cost"] == pytest.approx(3 * (8 + 1.3) + 2 * 2.4, rel=1e-12)
