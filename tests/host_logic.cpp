@@ -194,6 +194,9 @@ void partition_cases() {
   partition_case("cfg2_64", {128}, {2.4}, 64, 304, 64, 1.3);
   partition_case("uneven", {7, 100, 33}, {1.0, 2.0, 3.0}, 5, 13, 16, 1.3);
   partition_case("long", {2048, 2048, 2048}, {2.4, 2.4, 2.4}, 3, 7, 64, 1.3);
+  partition_case("tiny", {3, 5}, {1.0, 2.0}, 3, 4, 2, 0.5);
+  partition_case("cfg2_64_chi2", {128}, {3.6}, 64, 304, 64, 1.95);
+  partition_case("paper_8", {160, 160}, {2.4, 2.4}, 8, 304, 64, 1.3);
 }
 
 }  // namespace

@@ -87,21 +87,41 @@ def test_decomposition_cost_model(run):
     assert r[1]["v"] == 0 and r[8]["v"] == 2 and r[64]["v"] == 5 and r[152]["v"] == 6
 
 
-PARTITION_CASES = {  # name: chunk iterations, chunk loads, vectors, CTAs, largest piece (host_logic.cpp)
-    "paper_64": ([160, 160], [2.4, 2.4], 64, 304, 64),
-    "cfg2_64": ([128], [2.4], 64, 304, 64),
-    "uneven": ([7, 100, 33], [1.0, 2.0, 3.0], 5, 13, 16),
-    "long": ([2048, 2048, 2048], [2.4, 2.4, 2.4], 3, 7, 64),
+PARTITION_CASES = {  # name: chunk iterations, chunk loads, vectors, CTAs, largest piece, piece cost (host_logic.cpp)
+    "paper_64": ([160, 160], [2.4, 2.4], 64, 304, 64, 1.3),
+    "cfg2_64": ([128], [2.4], 64, 304, 64, 1.3),
+    "uneven": ([7, 100, 33], [1.0, 2.0, 3.0], 5, 13, 16, 1.3),
+    "long": ([2048, 2048, 2048], [2.4, 2.4, 2.4], 3, 7, 64, 1.3),
+    "tiny": ([3, 5], [1.0, 2.0], 3, 4, 2, 0.5),
+    "cfg2_64_chi2": ([128], [3.6], 64, 304, 64, 1.95),
+    "paper_8": ([160, 160], [2.4, 2.4], 8, 304, 64, 1.3),
 }
+
+
+def _range_cost(iters, load, max_piece, piece, lo, hi):
+    """Cost of the CTA range [lo, hi) of the batch order: its iterations, a piece cost per
+    piece (cut at the largest piece from the range's start in each chunk) and a chunk load
+    per chunk it starts on."""
+    pre = np.concatenate([[0], np.cumsum(iters)])
+    S = int(pre[-1])
+    c, q = float(hi - lo), lo
+    while q < hi:
+        j, off = divmod(q, S)
+        k = int(np.searchsorted(pre, off, side="right") - 1)
+        n = min(hi - q, iters[k] - (off - int(pre[k])))
+        c += load[k] + piece * -(-n // max_piece)
+        q += n
+    return c
 
 
 def test_partition_invariants(run):
     """The launch-level partition: each job's chunk iterations are covered exactly once, in
-    order, by pieces of at most the largest piece; every CTA takes the next contiguous range of
-    floor(I*b/G) iterations; a job's rows follow its pieces and each chunk's rows are contiguous;
-    the returned cost is the busiest CTA's (iterations, 1.3 per piece, a chunk load per change)."""
+    order, by pieces of at most the largest piece; the CTAs take consecutive ranges of the
+    batch order; a job's rows follow its pieces and each chunk's rows are contiguous; the
+    returned cost is the busiest CTA's.  The ranges hold equal iteration counts (within one)
+    unless ranges of equal cost lower the busiest CTA's cost by 5 % or more."""
     r = run("partition")
-    for name, (iters, load, nvec, G, max_piece) in PARTITION_CASES.items():
+    for name, (iters, load, nvec, G, max_piece, piece) in PARTITION_CASES.items():
         p = r[name]
         pieces, cta, nck = p["pieces"], p["cta"], len(iters)
         pre = np.concatenate([[0], np.cumsum(iters)])
@@ -109,22 +129,25 @@ def test_partition_invariants(run):
         I = S * nvec
         assert p["grid"] == G and len(cta) == G + 1 and cta[0] == 0 and cta[-1] == len(pieces)
         assert all(a <= b for a, b in zip(cta, cta[1:]))
-        q = 0
-        worst = 0.0
+        q, costs, counts = 0, [], []
         for b in range(G):
-            lo, hi = I * b // G, I * (b + 1) // G
-            assert q == lo
-            cost, prev = float(hi - lo), None
+            lo, cost, prev = q, 0.0, None
             for j, k, it0, nit, row in pieces[cta[b]:cta[b + 1]]:
                 assert 1 <= nit <= max_piece and 0 <= it0 and it0 + nit <= iters[k]
-                assert j * S + pre[k] + it0 == q  # the next iteration of the global order
+                assert j * S + pre[k] + it0 == q  # the next iteration of the batch order
                 q += nit
-                cost += 1.3 + (load[k] if prev != (j, k) else 0.0)
+                cost += nit + piece + (load[k] if prev != (j, k) else 0.0)
                 prev = (j, k)
-            assert q == hi
-            worst = max(worst, cost)
+            assert cost == pytest.approx(_range_cost(iters, load, max_piece, piece, lo, q), abs=1e-9)
+            costs.append(cost)
+            counts.append(q - lo)
         assert q == I
-        assert p["worst"] == pytest.approx(worst, rel=1e-12)
+        assert p["worst"] == pytest.approx(max(costs), rel=1e-12)
+        equal = max(_range_cost(iters, load, max_piece, piece, I * b // G, I * (b + 1) // G) for b in range(G))
+        if max(counts) - min(counts) > 1:  # the cost-balanced cut, taken for a gain of 5 % or more
+            assert p["worst"] <= 0.95 * equal + 1e-9
+        else:
+            assert counts == [I * (b + 1) // G - I * b // G for b in range(G)]
         rows = p["rows"]
         cr = np.array(p["chunk_rows"]).reshape(nvec, nck, 2)
         for j in range(nvec):
@@ -135,6 +158,26 @@ def test_partition_invariants(run):
                 first, count = cr[j, k]
                 assert count == len(ck) and [pc[4] for pc in ck] == list(range(first, first + count))
                 assert sum(pc[3] for pc in ck) == iters[k]
+    # which cut each case takes (model costs: 34.4 -> 31.7, 38.1 -> 33.55, 75.4 -> 74.0)
+    assert r["cfg2_64"]["worst"] == pytest.approx(31.7) and r["cfg2_64_chi2"]["worst"] == pytest.approx(33.55)
+    assert r["paper_64"]["worst"] == pytest.approx(75.4) and r["paper_8"]["worst"] == pytest.approx(12.7)
     # the compiled decomposition's busiest CTA: ceil(640 / 304) = 3 items of 8 iterations, a
     # piece cost each and a chunk load at the start and after 5 items
     assert r["paper_64"]["items_cost"] == pytest.approx(3 * (8 + 1.3) + 2 * 2.4, rel=1e-12)
+
+
+def test_partition_balanced_cut_is_optimal_on_a_tiny_batch(run):
+    """Brute force: the smallest busiest-CTA cost over every cut of the 24 iterations of the
+    tiny batch into 4 contiguous ranges (dynamic programming over the range ends) equals the
+    cost-balanced cut's, to the bisection's tolerance."""
+    iters, load, nvec, G, max_piece, piece = PARTITION_CASES["tiny"]
+    I = sum(iters) * nvec
+    best = {(0, 0): 0.0}  # (ranges used, iterations covered) -> smallest busiest cost
+    for g in range(1, G + 1):
+        for e in range(I + 1):
+            cands = [max(best[(g - 1, s)], _range_cost(iters, load, max_piece, piece, s, e) if e > s else 0.0)
+                     for s in range(e + 1) if (g - 1, s) in best]
+            best[(g, e)] = min(cands)
+    opt = best[(G, I)]
+    w = run("partition")["tiny"]["worst"]
+    assert opt - 1e-9 <= w <= opt + 1e-3
