@@ -656,8 +656,9 @@ void fill_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, c
 using musr::Partition;
 constexpr int kMaxPieceIters = musr::kMaxTileBins / (musr::kBlock * musr::kBinsPerThread);
 
-// Fills `part` (the launch-level partition of musr_partition.h) and returns true when its
-// busiest CTA beats the compiled decomposition `var` by 3 % or more.  Costs in CTA
+// Fills `part` (the launch-level partition of musr_partition.h) and returns true when the
+// busiest CTA of its equal-iteration cut beats the compiled decomposition `var` by 3 % or
+// more.  Costs in CTA
 // iterations: the iterations, a fixed cost per item or piece (row reduction, completion,
 // staging start-up: kSplitItemCost) and a cost per change of chunk within a CTA (the chunk's
 // FP64 coefficients and constants: 2.4 iterations of a full chunk of 8 histograms, more for
@@ -688,8 +689,11 @@ bool plan_partition(musr_ctx* ctx, int prec, int var, int mode, int grad, int nv
     min_tiles = std::min(min_tiles, c.chunks[k].ntiles);
   }
   if (S <= 0 || S * nvec < 8 * static_cast<int64_t>(G)) return false;
-  const double worst = musr::cut_partition(it, load, nvec, G, kMaxPieceIters, item_cost, part);
-  return worst < 0.97 * musr::items_cost(hs.nitems, nvec, G, hs.tile_bins / bpi, min_tiles, item_cost, max_load);
+  // The choice weighs the equal-iteration cut (measured against the decomposition on GB300);
+  // the layout may then take ranges of equal cost (musr_partition.h).
+  double equal = 0.0;
+  musr::cut_partition(it, load, nvec, G, kMaxPieceIters, item_cost, part, &equal);
+  return equal < 0.97 * musr::items_cost(hs.nitems, nvec, G, hs.tile_bins / bpi, min_tiles, item_cost, max_load);
 }
 
 int prepare_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, const double* d_params,

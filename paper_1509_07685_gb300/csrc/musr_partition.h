@@ -81,13 +81,14 @@ inline int greedy_bounds(const std::vector<int64_t>& iters, const std::vector<do
 
 // Cuts nvec jobs over chunks of iters[k] CTA iterations (k < nck) into G CTA ranges.
 // Returns the busiest CTA's cost in iterations: its iterations, item_cost per piece and
-// load[k] each time the CTA starts on chunk k of another job or chunk.  The ranges hold
+// load[k] each time the CTA starts on chunk k of another job or chunk; *equal_worst (if
+// given) gets the same for ranges of equal iteration counts.  The ranges hold
 // equal iteration counts, unless ranges of equal cost (those that give the CTAs which
 // cross into another chunk fewer iterations) lower the busiest CTA's cost by 5 % or more;
 // below that the model's error is larger than its gain (measured on GB300: 5 % faster on
 // 8 x 65536 bins at 64 vectors for a model gain of 8 %, 1.5 % slower on 16 x 81920 for 2 %).
 inline double cut_partition(const std::vector<int64_t>& iters, const std::vector<double>& load, int nvec, int G,
-                            int max_piece, double item_cost, Partition* part) {
+                            int max_piece, double item_cost, Partition* part, double* equal_worst = nullptr) {
   const int nck = static_cast<int>(iters.size());
   std::vector<int64_t> pre(nck + 1, 0);
   for (int k = 0; k < nck; ++k) pre[k + 1] = pre[k] + iters[k];
@@ -111,6 +112,7 @@ inline double cut_partition(const std::vector<int64_t>& iters, const std::vector
   double equal = 0.0;
   for (int b = 0; b <= G; ++b) bounds[b] = I * b / G;
   for (int b = 0; b < G; ++b) equal = std::max(equal, range_cost(bounds[b], bounds[b + 1]));
+  if (equal_worst) *equal_worst = equal;
   std::vector<int64_t> gb;
   double lo_t = static_cast<double>(I) / G, hi_t = equal;  // infeasible, feasible
   for (int it = 0; it < 40 && hi_t - lo_t > 1e-3; ++it) {

@@ -173,8 +173,10 @@ void pick_cases() {
 void partition_case(const char* name, const std::vector<int64_t>& iters, const std::vector<double>& load, int nvec,
                     int G, int max_piece, double item_cost) {
   musr::Partition part;
-  const double worst = musr::cut_partition(iters, load, nvec, G, max_piece, item_cost, &part);
-  std::printf("{\"name\": \"%s\", \"worst\": %.17g, \"grid\": %d, \"pieces\": [", name, worst, part.grid);
+  double equal = 0.0;
+  const double worst = musr::cut_partition(iters, load, nvec, G, max_piece, item_cost, &part, &equal);
+  std::printf("{\"name\": \"%s\", \"worst\": %.17g, \"equal\": %.17g, \"grid\": %d, \"pieces\": [", name, worst,
+              equal, part.grid);
   for (size_t i = 0; i < part.pieces.size(); ++i) {
     const musr::Piece& p = part.pieces[i];
     std::printf("%s[%d, %d, %d, %d, %d]", i ? ", " : "", p.job, p.chunk, p.it0, p.nit, p.row);

@@ -144,6 +144,7 @@ def test_partition_invariants(run):
         assert q == I
         assert p["worst"] == pytest.approx(max(costs), rel=1e-12)
         equal = max(_range_cost(iters, load, max_piece, piece, I * b // G, I * (b + 1) // G) for b in range(G))
+        assert p["equal"] == pytest.approx(equal, rel=1e-12)
         if max(counts) - min(counts) > 1:  # the cost-balanced cut, taken for a gain of 5 % or more
             assert p["worst"] <= 0.95 * equal + 1e-9
         else:
