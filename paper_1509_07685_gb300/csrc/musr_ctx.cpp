@@ -691,9 +691,11 @@ bool plan_partition(musr_ctx* ctx, int prec, int var, int mode, int grad, int nv
   if (S <= 0 || S * nvec < 8 * static_cast<int64_t>(G)) return false;
   // The choice weighs the equal-iteration cut (measured against the decomposition on GB300);
   // the layout may then take ranges of equal cost (musr_partition.h).
-  double equal = 0.0;
-  musr::cut_partition(it, load, nvec, G, kMaxPieceIters, item_cost, part, &equal);
-  return equal < 0.97 * musr::items_cost(hs.nitems, nvec, G, hs.tile_bins / bpi, min_tiles, item_cost, max_load);
+  const double equal = musr::equal_cut_worst(it, load, nvec, G, kMaxPieceIters, item_cost);
+  if (equal >= 0.97 * musr::items_cost(hs.nitems, nvec, G, hs.tile_bins / bpi, min_tiles, item_cost, max_load))
+    return false;
+  musr::cut_partition(it, load, nvec, G, kMaxPieceIters, item_cost, part);
+  return true;
 }
 
 int prepare_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec, const double* d_params,
@@ -759,6 +761,7 @@ int prepare_jobs(musr_ctx* ctx, int prec, int var, int mode, int grad, int nvec,
   ev.k_out = d_out;
   ev.k_dirs = d_dirs;
   ev.k_pieces = pieces;
+  ev.k_grid = pieces ? part->grid : 0;
   return MUSR_OK;
 }
 
@@ -798,6 +801,13 @@ int plan_launch(musr_ctx* ctx, int prec, int mode, int grad, int nvec, const dou
   L->empty = hs.nitems == 0;  // no bin in the fit range: cost 0, gradient 0
   if (L->empty) return MUSR_OK;
   musr::max_ctas_per_sm(prec, hs.shape, mode, grad);  // the occupancy query, before any capture
+  const EvalBufs& ev = ctx->ev;
+  if (ev.key_valid && ev.k_prec == prec && ev.k_var == L->var && ev.k_mode == mode && ev.k_grad == grad &&
+      ev.k_nvec == nvec && ev.k_params == d_params && ev.k_out == d_out && ev.k_dirs == d_dirs) {
+    L->pieces = ev.k_pieces;  // the job table and partition on the device are this launch's
+    L->grid = ev.k_grid;
+    return MUSR_OK;
+  }
   // Batches of plain evaluations on the SPLIT basis kernels may take a launch-level partition.
   Partition part;
   L->pieces = prec == MUSR_SPLIT && nvec >= 2 && (mode == 0 || mode == 1 || mode == 4) &&

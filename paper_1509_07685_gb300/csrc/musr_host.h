@@ -79,6 +79,7 @@ struct EvalBufs {
   const double* k_params = nullptr;
   const double* k_dirs = nullptr;
   bool k_pieces = false;
+  int k_grid = 0;  // the partition's grid (k_pieces)
   double* k_out = nullptr;
 };
 

@@ -79,6 +79,36 @@ inline int greedy_bounds(const std::vector<int64_t>& iters, const std::vector<do
   return used;
 }
 
+// Cost of the CTA range [lo, hi) of the batch order over chunks with prefix sums pre
+// (pre[k] = iterations before chunk k of a job, pre[nck] = S): its iterations, item_cost per
+// piece (cut at max_piece from the range's start in each chunk) and load[k] for each chunk k
+// it starts on.  Walks the chunks the range crosses, not its pieces.
+inline double range_cost(const std::vector<int64_t>& pre, const std::vector<double>& load, int max_piece,
+                         double item_cost, int64_t lo, int64_t hi) {
+  const int64_t S = pre.back();
+  double c = static_cast<double>(hi - lo);
+  for (int64_t q = lo; q < hi;) {
+    const int64_t j = q / S, off = q - j * S;
+    const int k = static_cast<int>(std::upper_bound(pre.begin(), pre.end(), off) - pre.begin()) - 1;
+    const int64_t n = std::min<int64_t>(hi - q, pre[k + 1] - off);
+    c += load[k] + item_cost * static_cast<double>((n + max_piece - 1) / max_piece);
+    q += n;
+  }
+  return c;
+}
+
+// The busiest CTA's cost when G CTAs take equal iteration counts (floor(I b / G) onwards).
+inline double equal_cut_worst(const std::vector<int64_t>& iters, const std::vector<double>& load, int nvec, int G,
+                              int max_piece, double item_cost) {
+  std::vector<int64_t> pre(iters.size() + 1, 0);
+  for (size_t k = 0; k < iters.size(); ++k) pre[k + 1] = pre[k] + iters[k];
+  const int64_t I = pre.back() * nvec;
+  double w = 0.0;
+  for (int b = 0; b < G; ++b)
+    w = std::max(w, range_cost(pre, load, max_piece, item_cost, I * b / G, I * (b + 1) / G));
+  return w;
+}
+
 // Cuts nvec jobs over chunks of iters[k] CTA iterations (k < nck) into G CTA ranges.
 // Returns the busiest CTA's cost in iterations: its iterations, item_cost per piece and
 // load[k] each time the CTA starts on chunk k of another job or chunk; *equal_worst (if
@@ -93,25 +123,9 @@ inline double cut_partition(const std::vector<int64_t>& iters, const std::vector
   std::vector<int64_t> pre(nck + 1, 0);
   for (int k = 0; k < nck; ++k) pre[k + 1] = pre[k] + iters[k];
   const int64_t S = pre[nck], I = S * nvec;
-  // Cost of CTA range [lo, hi): its iterations, a piece cost per piece, a load per chunk.
-  auto range_cost = [&](int64_t lo, int64_t hi) {
-    double c = static_cast<double>(hi - lo);
-    int pj = -1, pk = -1;
-    for (int64_t q = lo; q < hi;) {
-      const int j = static_cast<int>(q / S);
-      const int64_t off = q - static_cast<int64_t>(j) * S;
-      const int k = static_cast<int>(std::upper_bound(pre.begin(), pre.end(), off) - pre.begin()) - 1;
-      c += item_cost + (j != pj || k != pk ? load[k] : 0.0);
-      pj = j;
-      pk = k;
-      q += std::min<int64_t>({hi - q, iters[k] - (off - pre[k]), static_cast<int64_t>(max_piece)});
-    }
-    return c;
-  };
   std::vector<int64_t> bounds(G + 1);
-  double equal = 0.0;
   for (int b = 0; b <= G; ++b) bounds[b] = I * b / G;
-  for (int b = 0; b < G; ++b) equal = std::max(equal, range_cost(bounds[b], bounds[b + 1]));
+  const double equal = equal_cut_worst(iters, load, nvec, G, max_piece, item_cost);
   if (equal_worst) *equal_worst = equal;
   std::vector<int64_t> gb;
   double lo_t = static_cast<double>(I) / G, hi_t = equal;  // infeasible, feasible
