@@ -197,7 +197,7 @@ struct HistSet {
 
 // A work piece of a launch-level partition (SPLIT basis kernels, batches): nit CTA iterations
 // of chunk `chunk` of job `job`, from iteration it0 of the chunk, into the job's partial row
-// `row`.  Pieces are cut from one contiguous, equal range of the batch's iterations per CTA.
+// `row`.  Pieces are cut from one contiguous range of the batch's iterations per CTA.
 struct Piece {
   int job, chunk, it0, nit, row;
 };
