@@ -201,6 +201,28 @@ void partition_cases() {
   partition_case("paper_8", {160, 160}, {2.4, 2.4}, 8, 304, 64, 1.3);
 }
 
+// One case per line of standard input: nck, then nck chunk iterations, nck loads, nvec, G,
+// the largest piece and the piece cost; the cases are named by their line number.
+void partition_stdin() {
+  int nck, line = 0;
+  while (std::scanf("%d", &nck) == 1 && nck > 0) {
+    std::vector<int64_t> iters(nck);
+    std::vector<double> load(nck);
+    for (auto& v : iters) {
+      long long x = 0;
+      if (std::scanf("%lld", &x) != 1) return;
+      v = x;
+    }
+    for (auto& v : load)
+      if (std::scanf("%lf", &v) != 1) return;
+    int nvec, G, max_piece;
+    double item_cost;
+    if (std::scanf("%d %d %d %lf", &nvec, &G, &max_piece, &item_cost) != 4) return;
+    const std::string name = std::to_string(line++);
+    partition_case(name.c_str(), iters, load, nvec, G, max_piece, item_cost);
+  }
+}
+
 }  // namespace
 
 int main(int argc, char** argv) {
@@ -209,5 +231,6 @@ int main(int argc, char** argv) {
   if (what == "plan") plan_cases();
   if (what == "pick") pick_cases();
   if (what == "partition") partition_cases();
+  if (what == "partition_stdin") partition_stdin();
   return 0;
 }

@@ -114,6 +114,44 @@ def _range_cost(iters, load, max_piece, piece, lo, hi):
     return c
 
 
+def _check_partition(p, iters, load, nvec, G, max_piece, piece):
+    """Invariants of one cut (see test_partition_invariants)."""
+    pieces, cta, nck = p["pieces"], p["cta"], len(iters)
+    pre = np.concatenate([[0], np.cumsum(iters)])
+    S = int(pre[-1])
+    I = S * nvec
+    assert p["grid"] == G and len(cta) == G + 1 and cta[0] == 0 and cta[-1] == len(pieces)
+    assert all(a <= b for a, b in zip(cta, cta[1:]))
+    q, costs, counts = 0, [], []
+    for b in range(G):
+        lo, cost, prev = q, 0.0, None
+        for j, k, it0, nit, row in pieces[cta[b]:cta[b + 1]]:
+            assert 1 <= nit <= max_piece and 0 <= it0 and it0 + nit <= iters[k]
+            assert j * S + pre[k] + it0 == q  # the next iteration of the batch order
+            q += nit
+            cost += nit + piece + (load[k] if prev != (j, k) else 0.0)
+            prev = (j, k)
+        assert cost == pytest.approx(_range_cost(iters, load, max_piece, piece, lo, q), abs=1e-9)
+        costs.append(cost)
+        counts.append(q - lo)
+    assert q == I
+    assert p["worst"] == pytest.approx(max(costs), rel=1e-12, abs=1e-12)
+    equal = max(_range_cost(iters, load, max_piece, piece, I * b // G, I * (b + 1) // G) for b in range(G))
+    assert p["equal"] == pytest.approx(equal, rel=1e-12, abs=1e-12)
+    if counts != [I * (b + 1) // G - I * b // G for b in range(G)]:  # the cost-balanced cut
+        assert p["worst"] <= 0.95 * equal + 1e-9
+    rows = p["rows"]
+    cr = np.array(p["chunk_rows"]).reshape(nvec, nck, 2)
+    for j in range(nvec):
+        own = [pc for pc in pieces if pc[0] == j]
+        assert rows[j] == len(own) and sorted(pc[4] for pc in own) == list(range(rows[j]))
+        for k in range(nck):
+            ck = [pc for pc in own if pc[1] == k]
+            first, count = cr[j, k]
+            assert count == len(ck) and [pc[4] for pc in ck] == list(range(first, first + count))
+            assert sum(pc[3] for pc in ck) == iters[k]
+
+
 def test_partition_invariants(run):
     """The launch-level partition: each job's chunk iterations are covered exactly once, in
     order, by pieces of at most the largest piece; the CTAs take consecutive ranges of the
@@ -121,50 +159,37 @@ def test_partition_invariants(run):
     returned cost is the busiest CTA's.  The ranges hold equal iteration counts (within one)
     unless ranges of equal cost lower the busiest CTA's cost by 5 % or more."""
     r = run("partition")
-    for name, (iters, load, nvec, G, max_piece, piece) in PARTITION_CASES.items():
-        p = r[name]
-        pieces, cta, nck = p["pieces"], p["cta"], len(iters)
-        pre = np.concatenate([[0], np.cumsum(iters)])
-        S = int(pre[-1])
-        I = S * nvec
-        assert p["grid"] == G and len(cta) == G + 1 and cta[0] == 0 and cta[-1] == len(pieces)
-        assert all(a <= b for a, b in zip(cta, cta[1:]))
-        q, costs, counts = 0, [], []
-        for b in range(G):
-            lo, cost, prev = q, 0.0, None
-            for j, k, it0, nit, row in pieces[cta[b]:cta[b + 1]]:
-                assert 1 <= nit <= max_piece and 0 <= it0 and it0 + nit <= iters[k]
-                assert j * S + pre[k] + it0 == q  # the next iteration of the batch order
-                q += nit
-                cost += nit + piece + (load[k] if prev != (j, k) else 0.0)
-                prev = (j, k)
-            assert cost == pytest.approx(_range_cost(iters, load, max_piece, piece, lo, q), abs=1e-9)
-            costs.append(cost)
-            counts.append(q - lo)
-        assert q == I
-        assert p["worst"] == pytest.approx(max(costs), rel=1e-12)
-        equal = max(_range_cost(iters, load, max_piece, piece, I * b // G, I * (b + 1) // G) for b in range(G))
-        assert p["equal"] == pytest.approx(equal, rel=1e-12)
-        if max(counts) - min(counts) > 1:  # the cost-balanced cut, taken for a gain of 5 % or more
-            assert p["worst"] <= 0.95 * equal + 1e-9
-        else:
-            assert counts == [I * (b + 1) // G - I * b // G for b in range(G)]
-        rows = p["rows"]
-        cr = np.array(p["chunk_rows"]).reshape(nvec, nck, 2)
-        for j in range(nvec):
-            own = [pc for pc in pieces if pc[0] == j]
-            assert rows[j] == len(own) and sorted(pc[4] for pc in own) == list(range(rows[j]))
-            for k in range(nck):
-                ck = [pc for pc in own if pc[1] == k]
-                first, count = cr[j, k]
-                assert count == len(ck) and [pc[4] for pc in ck] == list(range(first, first + count))
-                assert sum(pc[3] for pc in ck) == iters[k]
+    for name, case in PARTITION_CASES.items():
+        _check_partition(r[name], *case)
     # which cut each case takes (model costs: 34.4 -> 31.7, 38.1 -> 33.55, 75.4 -> 74.0)
     assert r["cfg2_64"]["worst"] == pytest.approx(31.7) and r["cfg2_64_chi2"]["worst"] == pytest.approx(33.55)
     assert r["paper_64"]["worst"] == pytest.approx(75.4) and r["paper_8"]["worst"] == pytest.approx(12.7)
     # the compiled decomposition's busiest CTA: ceil(640 / 304) = 3 items of 8 iterations, a
     # piece cost each and a chunk load at the start and after 5 items
     assert r["paper_64"]["items_cost"] == pytest.approx(3 * (8 + 1.3) + 2 * 2.4, rel=1e-12)
+
+
+def test_partition_invariants_on_random_batches(run):  # run: the harness is built
+    """The same invariants on 300 seeded random batches: 1-4 chunks of 1-60 iterations, loads
+    0-5, 1-6 vectors, 1-40 CTAs (some batches smaller than the grid, leaving CTAs empty),
+    pieces of 1-16 iterations, piece costs 0-2."""
+    rng = np.random.default_rng(11)
+    cases = []
+    for _ in range(300):
+        nck = int(rng.integers(1, 5))
+        cases.append(([int(v) for v in rng.integers(1, 61, nck)], [float(v) for v in np.round(rng.uniform(0, 5, nck), 3)],
+                      int(rng.integers(1, 7)), int(rng.integers(1, 41)), int(rng.integers(1, 17)),
+                      float(np.round(rng.uniform(0, 2), 3))))
+    text = "".join(f"{len(it)} {' '.join(map(str, it))} {' '.join(map(str, ld))} {nv} {G} {mp} {pc}\n"
+                   for it, ld, nv, G, mp, pc in cases) + "0\n"
+    out = subprocess.run([EXE, "partition_stdin"], input=text, capture_output=True, text=True, check=True).stdout
+    got = {d["name"]: d for d in map(json.loads, out.splitlines())}
+    assert len(got) == len(cases)
+    balanced = 0
+    for i, case in enumerate(cases):
+        _check_partition(got[str(i)], *case)
+        balanced += got[str(i)]["worst"] < got[str(i)]["equal"] - 1e-9
+    assert balanced > 0  # the cost-balanced cut is exercised
 
 
 def test_partition_balanced_cut_is_optimal_on_a_tiny_batch(run):
